@@ -1,0 +1,159 @@
+"""Level differences, sample statistics and Algorithm 1 (Sec. 2.2-2.3).
+
+Level pair (Eq. MLMC_defn): a level-l sample j draws xi^(j) from the level-l
+stream, synthesises theta on the fine mesh l and on the coarse mesh l-1 from that
+same xi, solves both, and returns Y_l = Q_l - Q_{l-1} (Y_0 = Q_0).
+
+Statistics: the estimator sums the level means (Eq. MLMC_defn); the variance
+estimate is Eq. varianceestim, s_l^2 = mean(Y^2) - mean(Y)^2, evaluated with
+exactly rounded sums (math.fsum).
+
+Algorithm 1 (reading where the printed listing is silent): L starts at -1 and is
+incremented at the top of each pass, so the first pass computes level 0; the
+sample ids of level l are 0, 1, 2, ... in order, a top-up continues from the
+current count; N_hat_l is rounded up and never lowers N_l; the sampling/bias
+split is e_s^2 = theta e^2 and e_b^2 = (1 - theta) e^2 (Eq. tausplit); the bias
+is estimated on the finest level as |Y_hat_L| / (m^alpha - 1) (Eq. bias_estimate,
+c = 1). The cost of one level-l sample is modelled as M_l^gamma + M_{l-1}^gamma
+(DOFs of the solves it needs, Eq. gamma), M_{-1} = 0.
+"""
+import math
+
+import numpy as np
+
+from . import fem, kl, rng
+
+
+def mesh_dims(cfg, level):
+    return cfg["nx0"] << level, cfg["ny0"] << level
+
+
+def dofs(cfg, level):
+    nx, ny = mesh_dims(cfg, level)
+    return 2 * (nx + 1) * (ny + 1)
+
+
+class Basis:
+    """KL basis rows at the element centroids of each mesh, computed on demand."""
+
+    def __init__(self, cfg):
+        self.cfg = cfg
+        self._b = {}
+
+    def __call__(self, mesh_level):
+        if mesh_level not in self._b:
+            nx, ny = mesh_dims(self.cfg, mesh_level)
+            self._b[mesh_level] = kl.basis_for_mesh(self.cfg, nx, ny)
+        return self._b[mesh_level]
+
+
+def solve_on_mesh(cfg, basis, mesh_level, xi_row):
+    nx, ny = mesh_dims(cfg, mesh_level)
+    theta = kl.theta_field(basis(mesh_level), xi_row[None, :])[0]
+    qr, qs, _ = fem.solve_sample(cfg, nx, ny, theta)
+    return np.array([qr, qs])
+
+
+def level_pair_from_xi(cfg, level, xi, basis=None):
+    """Q_fine[n, 2], Q_coarse[n, 2] for level `level` and given xi[n, N_KL]."""
+    basis = basis or Basis(cfg)
+    xi = np.atleast_2d(xi)
+    qf = np.zeros((xi.shape[0], 2))
+    qc = np.zeros((xi.shape[0], 2))
+    for s in range(xi.shape[0]):
+        qf[s] = solve_on_mesh(cfg, basis, level, xi[s])
+        if level > 0:
+            qc[s] = solve_on_mesh(cfg, basis, level - 1, xi[s])
+    return qf, qc
+
+
+def level_pair(cfg, level, ids, basis=None):
+    """Q_fine, Q_coarse for the level-`level` samples `ids` (same xi on both meshes)."""
+    xi = rng.kl_coefficients(cfg["seed"], level, ids, cfg["kl_terms"])
+    return level_pair_from_xi(cfg, level, xi, basis)
+
+
+def _pair_worker(args):
+    cfg, level, ids = args
+    return level_pair(cfg, level, ids)
+
+
+def level_pair_parallel(cfg, level, ids, workers):
+    """level_pair over a 'spawn' process pool (one chunk of ids per task)."""
+    import multiprocessing as mp
+    ids = np.asarray(ids)
+    chunks = [c for c in np.array_split(ids, max(1, min(len(ids), 4 * workers))) if c.size]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        parts = pool.map(_pair_worker, [(cfg, level, c) for c in chunks])
+    return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]))
+
+
+def moments(y):
+    """(n, mean, s^2 of Eq. varianceestim) with exactly rounded sums.
+
+    Eq. varianceestim, mean(Y^2) - mean(Y)^2, is evaluated in the algebraically
+    identical centred form mean((Y - mean(Y))^2): the printed form cancels
+    catastrophically when |mean| >> std (e.g. Y_0 = Q_0).
+    """
+    y = [float(v) for v in np.asarray(y).reshape(-1)]
+    n = len(y)
+    if n == 0:
+        return 0, 0.0, 0.0
+    mean = math.fsum(y) / n
+    return n, mean, math.fsum((v - mean) * (v - mean) for v in y) / n
+
+
+def optimal_samples(V, C, es2):
+    """N_l = ceil(e_s^-2 (sum_k sqrt(V_k C_k)) sqrt(V_l / C_l))  (Eq. optimal_Nl)."""
+    V = np.asarray(V, dtype=np.float64)
+    C = np.asarray(C, dtype=np.float64)
+    total = math.fsum(np.sqrt(V * C))
+    return [int(math.ceil(total * math.sqrt(v / c) / es2)) for v, c in zip(V, C)]
+
+
+def bias_estimate(y_hat_L, m, alpha):
+    """|Y_hat_L| / (m^alpha - 1)  (Eq. bias_estimate with c = 1)."""
+    return abs(y_hat_L) / (m ** alpha - 1.0)
+
+
+def level_cost(cfg, level, gamma):
+    c = dofs(cfg, level) ** gamma
+    if level > 0:
+        c += dofs(cfg, level - 1) ** gamma
+    return float(c)
+
+
+def algorithm1(cfg, e, theta, n_star, max_level, qoi=0, alpha=1.0, gamma=1.0, m=4,
+               sampler=None):
+    """Adaptive MLMC (Algorithm 1). Returns (estimate, per-level Y lists, L, converged).
+
+    `sampler(level, ids) -> Y[len(ids)]` defaults to the FE level pair of this module.
+    """
+    if sampler is None:
+        basis = Basis(cfg)
+
+        def sampler(level, ids):
+            qf, qc = level_pair(cfg, level, ids, basis)
+            return qf[:, qoi] - qc[:, qoi]
+
+    es2 = theta * e * e
+    eb = math.sqrt(1.0 - theta) * e
+    Y = []
+    L = -1
+    converged = False
+    while not converged:
+        if L + 1 > max_level:
+            break
+        L += 1
+        Y.append(list(sampler(L, np.arange(n_star))))
+        V = [moments(y)[2] for y in Y]
+        C = [level_cost(cfg, l, gamma) for l in range(L + 1)]
+        N_hat = optimal_samples(V, C, es2)
+        for l in range(L + 1):
+            if len(Y[l]) < N_hat[l]:
+                Y[l].extend(sampler(l, np.arange(len(Y[l]), N_hat[l])))
+        if bias_estimate(moments(Y[L])[1], m, alpha) < eb:
+            converged = True
+    estimate = math.fsum(moments(y)[1] for y in Y)
+    return estimate, Y, L, converged

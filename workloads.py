@@ -1,0 +1,59 @@
+"""Workload definitions for the laminate-strip level-pair problems.
+
+This module holds only the parameters of the synthetic workloads (mesh ladder,
+material constants, random-field parameters, sample counts, seeds). It holds none
+of the method's arithmetic, so that the CUDA library's Python binding, the CPU
+oracle, the tests and the benchmark can all take their inputs from one place
+without sharing any computation.
+
+Strip problem (both workloads): a unidirectional laminate strip occupying
+[0, lx] x [0, ly] in plane strain, bilinear Q1 elements on a structured grid that
+is refined uniformly (h halved per level, Sec. 2.3), fibre misalignment field
+theta(x) given by a truncated Karhunen-Loeve expansion (Eq. inftyKL) of a
+squared-exponential covariance, clamped at x = 0 and shortened by a prescribed
+end displacement at x = lx.
+"""
+
+# 3-level strip, double precision throughout: 16x4, 32x8, 64x16 elements.
+STRIP_FP64_3LEVEL = dict(
+    name="strip-q1-fp64-3level",
+    lx=1.0, ly=0.25,            # strip length and height
+    nx0=16, ny0=4,              # level-0 mesh (elements); level l has nx0*2^l x ny0*2^l
+    levels=3,
+    E11=135e9, E22=9.5e9, G12=5e9, nu12=0.3,   # ply constants (Pa)
+    E33=9.5e9, nu13=0.3, nu23=0.45,            # transverse isotropy closing plane strain
+    kl_terms=20,                # N_KL
+    kl_std_deg=2.0,             # standard deviation of theta (degrees)
+    kl_corr=0.2,                # correlation length of the squared-exponential kernel
+    kl_quad=128,                # Gauss-Legendre points per axis for the Nystrom eigenproblems
+    shortening=1e-3,            # prescribed end displacement magnitude at x = lx
+    omega_x0=0.25, omega_x1=0.75,  # central region for the stress quantity (element centroids)
+    seed=0,
+    n_per_level=(200, 100, 50),
+    precision="fp64",
+    rtol=1e-10,                 # relative residual of the GPU solve
+)
+
+# 5-level strip, batched mixed precision: 64x16 ... 1024x256 elements.
+STRIP_MIXED_5LEVEL = dict(STRIP_FP64_3LEVEL)
+STRIP_MIXED_5LEVEL.update(
+    name="strip-q1-mixed-5level",
+    nx0=64, ny0=16,
+    levels=5,
+    kl_terms=100,
+    n_per_level=(8192, 2048, 512, 128, 32),
+    precision="mixed",
+    rtol=1e-8,
+)
+
+WORKLOADS = {w["name"]: w for w in (STRIP_FP64_3LEVEL, STRIP_MIXED_5LEVEL)}
+
+
+def mesh_dims(cfg, level):
+    """(nx, ny) element counts of mesh `level` of a workload (h halved per level)."""
+    return cfg["nx0"] << level, cfg["ny0"] << level
+
+
+def n_dofs(cfg, level):
+    nx, ny = mesh_dims(cfg, level)
+    return 2 * (nx + 1) * (ny + 1)
