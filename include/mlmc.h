@@ -1,0 +1,180 @@
+/*
+ * mlmc.h - C ABI of the GB300 level-pair engine for multilevel Monte Carlo on
+ * composite strips with random fibre misalignment (Dodwell et al., MLMC
+ * simulations of composite structures with uncertain manufacturing defects).
+ *
+ * What the library computes. For sample j of level l it draws the KL
+ * coefficients xi^(j) (independent standard normals, Eq. inftyKL) from the
+ * counter stream keyed by (seed, l), synthesises the misalignment field
+ * theta = sum_n sqrt(mu_n) phi_n xi_n at the element centroids of mesh l and of
+ * mesh l-1 from the SAME xi (Sec. 2.2, Eq. MLMC_defn), rotates each element's
+ * orthotropic plane-strain stiffness by its angle (Sec. 3.1, C* = T^-1 C T),
+ * solves K d = f (Eq. matrixinplane) on both meshes, extracts the quantities of
+ * interest and forms Y_l = Q_l - Q_{l-1} (Y_0 = Q_0), which it folds into
+ * per-level running moments (Eq. varianceestim). mlmc_estimate drives
+ * Algorithm 1 on top.
+ *
+ * Quantities of interest (n_qoi = 2, in this order):
+ *   0  reaction: compressive end force per unit depth, -sum over the u-DOFs on
+ *      x = lx of (K d)_i  [N/m];
+ *   1  stress: max over elements whose centroid x lies in [omega_x0, omega_x1]
+ *      of max(0, -sigma_11^fibre) at the centroid [Pa].
+ *
+ * Memory. Every array argument is caller-owned and may be host memory or device
+ * memory of the context's GPU (the library checks with cudaPointerGetAttributes
+ * and copies as needed). Device work is issued on the stream given to
+ * mlmc_create; calls return after that stream has finished the call's work.
+ * The context owns its device workspace, the KL bases and the mesh hierarchy.
+ *
+ * Errors. Every call returns an mlmc_status; none aborts. On failure
+ * mlmc_last_error(ctx) gives a message. Per-sample status arrays receive 0 or
+ * MLMC_ERR_NOT_CONVERGED; a sample that did not converge is left out of the
+ * level moments. A context is used from one host thread at a time.
+ */
+#ifndef MLMC_H
+#define MLMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mlmc_ctx mlmc_ctx;
+
+typedef enum {
+  MLMC_OK = 0,
+  MLMC_ERR_INVALID_ARG = 1,
+  MLMC_ERR_OOM = 2,
+  MLMC_ERR_CUDA = 3,
+  MLMC_ERR_NOT_CONVERGED = 4,
+  MLMC_ERR_TIMEOUT = 5,
+  MLMC_ERR_UNIMPLEMENTED = 6
+} mlmc_status;
+
+typedef enum {
+  MLMC_PREC_FP64 = 0,   /* every step in double precision */
+  MLMC_PREC_MIXED = 1   /* FP32 synthesis, operator and multigrid-PCG; FP64 refinement,
+                           dot products, quantities of interest and moments */
+} mlmc_precision;
+
+/* Problem and solver description (plain values, copied by mlmc_create). */
+typedef struct {
+  double lx, ly;            /* strip [0, lx] x [0, ly] */
+  int32_t nx0, ny0;         /* level-0 mesh; level l has (nx0 << l) x (ny0 << l) elements;
+                               nx0 / ny0 must be equal powers-of-two multiples of a mesh
+                               that halves down to 4 x 1 or 2 x 1 (nx0 = 4 ny0 or 2 ny0) */
+  int32_t levels;           /* number of MLMC levels (meshes 0 .. levels-1) */
+  double E11, E22, G12, nu12, E33, nu13, nu23;   /* ply constants, Pa */
+  int32_t kl_terms;         /* N_KL, 1 .. 512 */
+  double kl_std;            /* standard deviation of theta, radians */
+  double kl_corr;           /* correlation length of the squared-exponential kernel */
+  int32_t kl_quad;          /* Gauss-Legendre points per axis, 8 .. 512 */
+  double shortening;        /* prescribed end displacement magnitude at x = lx */
+  double omega_x0, omega_x1;/* central region for quantity 1 */
+  uint64_t seed;
+  int32_t precision;        /* mlmc_precision */
+  double rtol;              /* relative residual ||f - K d|| / ||f|| to reach */
+  int32_t max_iter;         /* cap on PCG iterations per refinement step (0: 200) */
+  int32_t max_outer;        /* cap on refinement steps (0: 8) */
+  int64_t max_batch;        /* samples per device batch (0: automatic) */
+  double mlmc_alpha;        /* Algorithm 1: bias rate in M (Eq. bias_estimate) */
+  double mlmc_gamma;        /* Algorithm 1: cost model M^gamma (Eq. gamma) */
+  double mlmc_m;            /* DOF growth per level (4 for 2D quads, Sec. 2.3) */
+} mlmc_config;
+
+/* One solve request for mlmc_solve_batch: the misalignment field of sample
+   `sample_id` of level `level` (stream keyed by (seed, level)), solved on mesh
+   `mesh_level` (normally level or level - 1). */
+typedef struct {
+  int32_t level;
+  int32_t mesh_level;
+  uint64_t sample_id;
+} mlmc_item;
+
+/* Running statistics of Y_l for one level (FP64, compensated). */
+typedef struct {
+  int64_t n;                /* converged samples folded in */
+  double mean[2];           /* mean of Y per quantity */
+  double m2[2];             /* sum of squared deviations (Welford/Chan) */
+  double var[2];            /* m2 / n: Eq. varianceestim (1/N form) */
+  double sum_qf[2];         /* sum of Q_l (fine solve) */
+  double sum_qc[2];         /* sum of Q_{l-1} (coarse solve; 0 on level 0) */
+  double cost;              /* modelled cost of one sample (DOFs^gamma of its solves) */
+} mlmc_level_stats;
+
+/* Creates a context: validates cfg, builds the mesh hierarchy and the KL bases
+   of all levels (double precision, host, then uploaded), and allocates the
+   workspace. `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+   Errors: MLMC_ERR_INVALID_ARG (bad cfg), MLMC_ERR_CUDA, MLMC_ERR_OOM. */
+mlmc_status mlmc_create(const mlmc_config* cfg, void* cuda_stream, mlmc_ctx** out);
+
+void mlmc_destroy(mlmc_ctx* ctx);
+
+/* Message of the last failure on ctx (or of the last failed mlmc_create when
+   ctx is NULL). Valid until the next call on the same context. */
+const char* mlmc_last_error(const mlmc_ctx* ctx);
+
+/* Level pair (Sec. 2.2, Eq. MLMC_defn): the n samples of level `level` with ids
+   first_id .. first_id + n - 1. Writes q_fine[n * 2] (Q_l) and, for level > 0,
+   q_coarse[n * 2] (Q_{l-1}; zeros on level 0), row-major [sample][quantity];
+   status[n] (nullable). Folds Y = Q_l - Q_{l-1} of the converged samples into
+   the level's moments. n = 0 is a no-op. */
+mlmc_status mlmc_sample_level(mlmc_ctx* ctx, int32_t level, uint64_t first_id, int64_t n,
+                              double* q_fine, double* q_coarse, int32_t* status);
+
+/* n independent solves of arbitrary (level, mesh_level, sample_id) items,
+   grouped by mesh and run together. Writes q[n * 2] and status[n] (nullable).
+   Does not touch the level moments. */
+mlmc_status mlmc_solve_batch(mlmc_ctx* ctx, const mlmc_item* items, int64_t n,
+                             double* q, int32_t* status);
+
+/* Algorithm 1 (Sec. 2.3): adds levels from 0 until the bias estimate
+   |Y_hat_L| / (m^alpha - 1) (Eq. bias_estimate) falls below sqrt(1 - theta) e,
+   topping each level up to N_hat_l of Eq. optimal_Nl with e_s^2 = theta e^2
+   (Eq. tausplit). Level l's samples are ids 0, 1, 2, ... in order. Uses quantity
+   `qoi` (0 or 1) and starts from the context's current moments; samples a level
+   already holds are reused. Writes the estimate sum_l mean(Y_l), stats[0..L]
+   (array of max_level + 1) and *L_out. Returns MLMC_ERR_NOT_CONVERGED if
+   max_level was reached without passing the bias test (outputs still written). */
+mlmc_status mlmc_estimate(mlmc_ctx* ctx, double e, double theta, int64_t n_star,
+                          int32_t max_level, int32_t qoi, double* estimate,
+                          mlmc_level_stats* stats, int32_t* L_out);
+
+/* Current moments of one level; mlmc_reset_stats clears all levels. */
+mlmc_status mlmc_level_stats_get(mlmc_ctx* ctx, int32_t level, mlmc_level_stats* out);
+mlmc_status mlmc_reset_stats(mlmc_ctx* ctx);
+
+/* ---- step-level entry points (each one step of the per-sample path) ---- */
+
+/* KL coefficients xi[n * kl_terms] (double) of samples first_id.. of `level`:
+   Philox4x32-10 keyed (lo32(seed), hi32(seed) ^ (level * 0x9E3779B9)),
+   counter (lo32(id), hi32(id), draw, 0); Marsaglia polar normals from exact
+   uniforms (2x + 1) 2^-52 - 1, with a series logarithm and no fused
+   multiply-add, so the values are bit-reproducible. */
+mlmc_status mlmc_kl_coefficients(mlmc_ctx* ctx, int32_t level, uint64_t first_id, int64_t n,
+                                 double* xi);
+
+/* KL synthesis theta[n * n_el(mesh_level)] (double; computed in the context's
+   precision) for samples first_id.. of `level` on mesh `mesh_level`
+   (Eq. inftyKL truncated at kl_terms). Element e = j * nx + i. */
+mlmc_status mlmc_theta(mlmc_ctx* ctx, int32_t level, int32_t mesh_level, uint64_t first_id,
+                       int64_t n, double* theta);
+
+/* Matrix-free operator q = K(theta) p on mesh `mesh_level` for n samples
+   (Eq. matrixinplane, rows and columns of all DOFs, no boundary conditions), in
+   the context's precision. theta[n * n_el], p and q [n * n_dofs], DOF 2 * node + c,
+   node = j * (nx + 1) + i. */
+mlmc_status mlmc_apply(mlmc_ctx* ctx, int32_t mesh_level, int64_t n, const double* theta,
+                       const double* p, double* q);
+
+/* Solve on given fields: theta[n * n_el] on mesh `mesh_level` -> q[n * 2],
+   status[n] (nullable), iterations[n] (nullable, total PCG iterations). */
+mlmc_status mlmc_solve_theta(mlmc_ctx* ctx, int32_t mesh_level, int64_t n, const double* theta,
+                             double* q, int32_t* status, int32_t* iterations);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLMC_H */

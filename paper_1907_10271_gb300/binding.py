@@ -1,0 +1,221 @@
+"""ctypes binding of the C ABI in include/mlmc.h (argument marshalling only).
+
+Every function keeps the C name. Array arguments may be numpy arrays (host) or
+torch tensors (host or CUDA); they must be contiguous and of the dtype the C
+signature names (float64, int32, ...). All computation happens in the CUDA
+library; importing this module fails loudly if the library was not built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmlmc_gb300.so")
+
+MLMC_OK = 0
+MLMC_ERR_INVALID_ARG = 1
+MLMC_ERR_OOM = 2
+MLMC_ERR_CUDA = 3
+MLMC_ERR_NOT_CONVERGED = 4
+MLMC_ERR_TIMEOUT = 5
+MLMC_ERR_UNIMPLEMENTED = 6
+MLMC_PREC_FP64 = 0
+MLMC_PREC_MIXED = 1
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "TIMEOUT",
+                6: "UNIMPLEMENTED"}
+
+
+class mlmc_config(ctypes.Structure):
+    _fields_ = [
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+        ("nx0", ctypes.c_int32), ("ny0", ctypes.c_int32), ("levels", ctypes.c_int32),
+        ("E11", ctypes.c_double), ("E22", ctypes.c_double), ("G12", ctypes.c_double),
+        ("nu12", ctypes.c_double), ("E33", ctypes.c_double), ("nu13", ctypes.c_double),
+        ("nu23", ctypes.c_double),
+        ("kl_terms", ctypes.c_int32), ("kl_std", ctypes.c_double), ("kl_corr", ctypes.c_double),
+        ("kl_quad", ctypes.c_int32),
+        ("shortening", ctypes.c_double), ("omega_x0", ctypes.c_double), ("omega_x1", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("precision", ctypes.c_int32), ("rtol", ctypes.c_double),
+        ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("max_batch", ctypes.c_int64),
+        ("mlmc_alpha", ctypes.c_double), ("mlmc_gamma", ctypes.c_double), ("mlmc_m", ctypes.c_double),
+    ]
+
+
+class mlmc_item(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("mesh_level", ctypes.c_int32), ("sample_id", ctypes.c_uint64)]
+
+
+class mlmc_level_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("mean", ctypes.c_double * 2), ("m2", ctypes.c_double * 2),
+                ("var", ctypes.c_double * 2), ("sum_qf", ctypes.c_double * 2),
+                ("sum_qc", ctypes.c_double * 2), ("cost", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(n=self.n, mean=list(self.mean), m2=list(self.m2), var=list(self.var),
+                    sum_qf=list(self.sum_qf), sum_qc=list(self.sum_qc), cost=self.cost)
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run paper_1907_10271_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, U64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        sig = {
+            "mlmc_create": (I32, [ctypes.POINTER(mlmc_config), P, ctypes.POINTER(P)]),
+            "mlmc_destroy": (None, [P]),
+            "mlmc_last_error": (ctypes.c_char_p, [P]),
+            "mlmc_sample_level": (I32, [P, I32, U64, I64, P, P, P]),
+            "mlmc_solve_batch": (I32, [P, P, I64, P, P]),
+            "mlmc_estimate": (I32, [P, D, D, I64, I32, I32, P, P, P]),
+            "mlmc_level_stats_get": (I32, [P, I32, P]),
+            "mlmc_reset_stats": (I32, [P]),
+            "mlmc_kl_coefficients": (I32, [P, I32, U64, I64, P]),
+            "mlmc_theta": (I32, [P, I32, I32, U64, I64, P]),
+            "mlmc_apply": (I32, [P, I32, I64, P, P, P]),
+            "mlmc_solve_theta": (I32, [P, I32, I64, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class MLMCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a, dtype):
+    """Device or host address of a contiguous array of the given numpy dtype."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):          # torch tensor
+        import torch
+        tmap = {np.float64: torch.float64, np.float32: torch.float32, np.int32: torch.int32,
+                np.int64: torch.int64, np.uint64: torch.uint64}
+        if a.dtype != tmap[dtype] or not a.is_contiguous():
+            raise TypeError(f"expected contiguous {dtype.__name__} tensor")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected C-contiguous numpy {dtype.__name__} array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(ctx, status):
+    if status != MLMC_OK:
+        msg = lib().mlmc_last_error(ctx).decode(errors="replace")
+        raise MLMCError(status, msg)
+    return status
+
+
+def config_from_workload(w, **overrides):
+    """mlmc_config from a workload dict (see workloads.py); keyword overrides win."""
+    w = dict(w)
+    w.update(overrides)
+    c = mlmc_config()
+    for f in ("lx", "ly", "E11", "E22", "G12", "nu12", "E33", "nu13", "nu23", "kl_corr", "shortening",
+              "omega_x0", "omega_x1", "rtol"):
+        setattr(c, f, float(w[f]))
+    c.nx0, c.ny0, c.levels = int(w["nx0"]), int(w["ny0"]), int(w["levels"])
+    c.kl_terms, c.kl_quad = int(w["kl_terms"]), int(w["kl_quad"])
+    c.kl_std = float(np.deg2rad(w["kl_std_deg"]))
+    c.seed = int(w["seed"])
+    c.precision = MLMC_PREC_MIXED if w["precision"] == "mixed" else MLMC_PREC_FP64
+    c.max_iter = int(w.get("max_iter", 0))
+    c.max_outer = int(w.get("max_outer", 0))
+    c.max_batch = int(w.get("max_batch", 0))
+    c.mlmc_alpha = float(w.get("mlmc_alpha", 1.0))
+    c.mlmc_gamma = float(w.get("mlmc_gamma", 1.0))
+    c.mlmc_m = float(w.get("mlmc_m", 4.0))
+    return c
+
+
+def current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+def mlmc_create(cfg, stream=None):
+    h = ctypes.c_void_p()
+    st = current_stream() if stream is None else stream
+    s = lib().mlmc_create(ctypes.byref(cfg), ctypes.c_void_p(st), ctypes.byref(h))
+    if s != MLMC_OK:
+        raise MLMCError(s, lib().mlmc_last_error(None).decode(errors="replace"))
+    return h
+
+
+def mlmc_destroy(ctx):
+    lib().mlmc_destroy(ctx)
+
+
+def mlmc_last_error(ctx):
+    return lib().mlmc_last_error(ctx).decode(errors="replace")
+
+
+def mlmc_sample_level(ctx, level, first_id, n, q_fine=None, q_coarse=None, status=None):
+    return _check(ctx, lib().mlmc_sample_level(ctx, level, first_id, n, _ptr(q_fine, np.float64),
+                                                _ptr(q_coarse, np.float64), _ptr(status, np.int32)))
+
+
+def mlmc_solve_batch(ctx, items, q=None, status=None):
+    """items: sequence of (level, mesh_level, sample_id)."""
+    arr = (mlmc_item * len(items))(*[mlmc_item(int(a), int(b), int(c)) for a, b, c in items])
+    return _check(ctx, lib().mlmc_solve_batch(ctx, ctypes.cast(arr, ctypes.c_void_p), len(items),
+                                               _ptr(q, np.float64), _ptr(status, np.int32)))
+
+
+def mlmc_estimate(ctx, e, theta, n_star, max_level, qoi=0):
+    """Returns (status, estimate, [level stats dicts], L)."""
+    est = ctypes.c_double()
+    L = ctypes.c_int32()
+    stats = (mlmc_level_stats * (max_level + 1))()
+    s = lib().mlmc_estimate(ctx, e, theta, n_star, max_level, qoi, ctypes.byref(est),
+                            ctypes.cast(stats, ctypes.c_void_p), ctypes.byref(L))
+    if s not in (MLMC_OK, MLMC_ERR_NOT_CONVERGED):
+        _check(ctx, s)
+    return s, est.value, [stats[i].as_dict() for i in range(L.value + 1)], L.value
+
+
+def mlmc_level_stats_get(ctx, level):
+    out = mlmc_level_stats()
+    _check(ctx, lib().mlmc_level_stats_get(ctx, level, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def mlmc_reset_stats(ctx):
+    return _check(ctx, lib().mlmc_reset_stats(ctx))
+
+
+def mlmc_kl_coefficients(ctx, level, first_id, n, xi):
+    return _check(ctx, lib().mlmc_kl_coefficients(ctx, level, first_id, n, _ptr(xi, np.float64)))
+
+
+def mlmc_theta(ctx, level, mesh_level, first_id, n, theta):
+    return _check(ctx, lib().mlmc_theta(ctx, level, mesh_level, first_id, n, _ptr(theta, np.float64)))
+
+
+def mlmc_apply(ctx, mesh_level, n, theta, p, q):
+    return _check(ctx, lib().mlmc_apply(ctx, mesh_level, n, _ptr(theta, np.float64), _ptr(p, np.float64),
+                                         _ptr(q, np.float64)))
+
+
+def mlmc_solve_theta(ctx, mesh_level, n, theta, q, status=None, iterations=None):
+    return _check(ctx, lib().mlmc_solve_theta(ctx, mesh_level, n, _ptr(theta, np.float64), _ptr(q, np.float64),
+                                               _ptr(status, np.int32), _ptr(iterations, np.int32)))

@@ -1,0 +1,704 @@
+// C ABI of the level-pair engine (see include/mlmc.h for the contract).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "context.h"
+#include "moments.cuh"
+
+struct mlmc_ctx {
+  mlmc::Context c;
+  std::vector<mlmc::LevelAcc> acc_host;
+  mlmc::LevelAcc* acc_dev = nullptr;   // [levels]
+  std::vector<int64_t> next_id;        // ids consumed per level by mlmc_estimate
+};
+
+namespace {
+
+std::string g_create_error;
+
+using mlmc::Context;
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy count values of U from src (host or device) into device dst.
+template <typename U>
+cudaError_t to_device(U* dst, const U* src, size_t count, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, sizeof(U) * count, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+}
+
+template <typename U>
+cudaError_t from_device(U* dst, const U* src, size_t count, cudaStream_t st) {
+  if (count == 0 || !dst) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, sizeof(U) * count, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+}
+
+__global__ void k_convert_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_convert_f2d(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+cudaError_t convert(const double* a, float* b, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_convert_d2f<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+cudaError_t convert(const float* a, double* b, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_convert_f2d<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+mlmc::Invariants invariants(const mlmc_config& c, bool& ok) {
+  // plane-strain fibre-frame stiffness: (1,2) block of the inverse 3D normal compliance
+  double S[3][3] = {{1.0 / c.E11, -c.nu12 / c.E11, -c.nu13 / c.E11},
+                    {-c.nu12 / c.E11, 1.0 / c.E22, -c.nu23 / c.E22},
+                    {-c.nu13 / c.E11, -c.nu23 / c.E22, 1.0 / c.E33}};
+  // inverse by cofactors
+  const double det = S[0][0] * (S[1][1] * S[2][2] - S[1][2] * S[2][1]) -
+                     S[0][1] * (S[1][0] * S[2][2] - S[1][2] * S[2][0]) +
+                     S[0][2] * (S[1][0] * S[2][1] - S[1][1] * S[2][0]);
+  ok = std::isfinite(det) && det > 0.0;
+  const double Q11 = (S[1][1] * S[2][2] - S[1][2] * S[2][1]) / det;
+  const double Q12 = -(S[0][1] * S[2][2] - S[0][2] * S[2][1]) / det;
+  const double Q22 = (S[0][0] * S[2][2] - S[0][2] * S[2][0]) / det;
+  const double Q66 = c.G12;
+  ok = ok && Q11 > 0 && Q22 > 0 && Q66 > 0 && Q11 * Q22 > Q12 * Q12;
+  mlmc::Invariants U;
+  U.U1 = (3.0 * Q11 + 3.0 * Q22 + 2.0 * Q12 + 4.0 * Q66) / 8.0;
+  U.U2 = (Q11 - Q22) / 2.0;
+  U.U3 = (Q11 + Q22 - 2.0 * Q12 - 4.0 * Q66) / 8.0;
+  U.U4 = (Q11 + Q22 + 6.0 * Q12 - 4.0 * Q66) / 8.0;
+  U.U5 = (Q11 + Q22 - 2.0 * Q12 + 4.0 * Q66) / 8.0;
+  return U;
+}
+
+std::string validate(const mlmc_config& c) {
+  if (!(c.lx > 0 && c.ly > 0)) return "lx, ly must be positive";
+  if (c.nx0 < 2 || c.ny0 < 2) return "nx0, ny0 must be >= 2";
+  if (c.levels < 1 || c.levels > 12) return "levels must be in [1, 12]";
+  if ((int64_t)(c.nx0 << (c.levels - 1)) > (1 << 16) || (int64_t)(c.ny0 << (c.levels - 1)) > (1 << 16))
+    return "finest mesh too large";
+  if (c.kl_terms < 1 || c.kl_terms > 512) return "kl_terms must be in [1, 512]";
+  if (!(c.kl_std >= 0) || !(c.kl_corr > 0)) return "kl_std >= 0 and kl_corr > 0 required";
+  if (!(c.rtol > 0 && c.rtol < 1)) return "rtol must be in (0, 1)";
+  if (c.precision != MLMC_PREC_FP64 && c.precision != MLMC_PREC_MIXED) return "unknown precision";
+  if (!(c.E11 > 0 && c.E22 > 0 && c.E33 > 0 && c.G12 > 0)) return "moduli must be positive";
+  // the multigrid hierarchy halves the level-0 mesh down to <= 64 DOFs
+  int nx = c.nx0, ny = c.ny0;
+  while (nx % 2 == 0 && ny % 2 == 0 && ny >= 2) {
+    nx /= 2;
+    ny /= 2;
+  }
+  if (2 * (nx + 1) * (ny + 1) > mlmc::kMaxCoarsestDofs) return "level-0 mesh does not halve down to <= 64 DOFs";
+  return "";
+}
+
+template <typename T>
+struct Scratch {
+  T* p = nullptr;
+};
+
+// Per-call device scratch from the batch arena.
+struct BatchBuffers {
+  double* xi = nullptr;
+  float* xi32 = nullptr;
+  int* fail = nullptr;
+  void* theta_f = nullptr;
+  void* theta_c = nullptr;
+  double* qf = nullptr;
+  double* qc = nullptr;
+  int* st_f = nullptr;
+  int* st_c = nullptr;
+  int* it_f = nullptr;
+  int* it_c = nullptr;
+  int* status = nullptr;
+};
+
+int64_t auto_batch(const Context& c, int level) {
+  if (c.cfg.max_batch > 0) return c.cfg.max_batch;
+  const double tb = c.mixed() ? 4.0 : 8.0;
+  auto dofs = [&](int l) { return l < 0 ? 0.0 : 2.0 * ((c.cfg.nx0 << l) + 1.0) * ((c.cfg.ny0 << l) + 1.0); };
+  const double per = (dofs(level) + dofs(level - 1)) * (14.0 * tb + 16.0) * 1.4 + 64.0;
+  const double budget = 8.0e9;
+  return std::max<int64_t>(1, (int64_t)(budget / per));
+}
+
+// xi, theta on fine (and coarse) meshes, both solves, per-sample outputs in device buffers.
+template <typename T>
+mlmc_status run_pairs(mlmc_ctx* h, int level, uint64_t first_id, int64_t nb, const int* levels_dev,
+                      const uint64_t* ids_dev, int fine_mesh, int coarse_mesh, BatchBuffers& B) {
+  Context& c = h->c;
+  cudaStream_t st = c.stream;
+  const int nkl = c.cfg.kl_terms;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(B.fail, 0, sizeof(int), st)) != cudaSuccess) return c.cuda_fail(e, "memset");
+  if ((e = mlmc::launch_kl_coefficients(c.cfg.seed, level, first_id, levels_dev, ids_dev, nb, nkl, B.xi,
+                                        c.mixed() ? B.xi32 : nullptr, B.fail, st)) != cudaSuccess)
+    return c.cuda_fail(e, "kl_coefficients");
+  const T* xiT = c.mixed() ? (const T*)(const void*)B.xi32 : (const T*)(const void*)B.xi;
+  auto basis = [&](int m) -> const T* {
+    return c.mixed() ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
+  };
+  const mlmc::LevelLayout mf = c.mesh(fine_mesh);
+  if ((e = mlmc::launch_kl_synthesis<T>(xiT, basis(fine_mesh), nb, (int)mf.n_el(), nkl, (T*)B.theta_f, st)) !=
+      cudaSuccess)
+    return c.cuda_fail(e, "kl_synthesis");
+  std::vector<mlmc::SolveGroup<T>> groups;
+  groups.push_back({fine_mesh, nb, (const T*)B.theta_f, B.qf, B.st_f, B.it_f});
+  if (coarse_mesh >= 0) {
+    const mlmc::LevelLayout mc = c.mesh(coarse_mesh);
+    if ((e = mlmc::launch_kl_synthesis<T>(xiT, basis(coarse_mesh), nb, (int)mc.n_el(), nkl, (T*)B.theta_c,
+                                          st)) != cudaSuccess)
+      return c.cuda_fail(e, "kl_synthesis");
+    groups.push_back({coarse_mesh, nb, (const T*)B.theta_c, B.qc, B.st_c, B.it_c});
+  }
+  int fail = 0;
+  if ((e = cudaMemcpyAsync(&fail, B.fail, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return c.cuda_fail(e, "kl_coefficients");
+  if (fail) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
+  return mlmc::solve_groups<T>(c, groups);
+}
+
+__global__ void k_combine_status(const int* a, const int* b, int* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] != 0 ? a[i] : (b ? b[i] : 0);
+}
+
+template <typename T>
+mlmc_status sample_level_t(mlmc_ctx* h, int32_t level, uint64_t first_id, int64_t n, double* q_fine,
+                           double* q_coarse, int32_t* status) {
+  Context& c = h->c;
+  cudaStream_t st = c.stream;
+  const int64_t batch = std::min<int64_t>(n, auto_batch(c, level));
+  const mlmc::LevelLayout mf = c.mesh(level);
+  const int64_t nel_f = mf.n_el(), nel_c = level > 0 ? c.mesh(level - 1).n_el() : 0;
+  size_t bytes = 0;
+  {
+    mlmc::Sizer s;
+    s.add<double>(batch * c.cfg.kl_terms);
+    s.add<float>(batch * c.cfg.kl_terms);
+    s.add<int>(1);
+    s.add<T>(batch * nel_f);
+    s.add<T>(batch * std::max<int64_t>(nel_c, 1));
+    s.add<double>(2 * batch);
+    s.add<double>(2 * batch);
+    for (int k = 0; k < 5; ++k) s.add<int>(batch);
+    bytes = s.used + 256;
+  }
+  cudaError_t e = c.batch_arena.reserve(bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return c.fail(MLMC_ERR_OOM, "batch buffers");
+  }
+  c.batch_arena.reset();
+  BatchBuffers B;
+  B.xi = c.batch_arena.carve<double>(batch * c.cfg.kl_terms);
+  B.xi32 = c.batch_arena.carve<float>(batch * c.cfg.kl_terms);
+  B.fail = c.batch_arena.carve<int>(1);
+  B.theta_f = c.batch_arena.carve<T>(batch * nel_f);
+  B.theta_c = c.batch_arena.carve<T>(batch * std::max<int64_t>(nel_c, 1));
+  B.qf = c.batch_arena.carve<double>(2 * batch);
+  B.qc = c.batch_arena.carve<double>(2 * batch);
+  B.st_f = c.batch_arena.carve<int>(batch);
+  B.st_c = c.batch_arena.carve<int>(batch);
+  B.it_f = c.batch_arena.carve<int>(batch);
+  B.it_c = c.batch_arena.carve<int>(batch);
+  B.status = c.batch_arena.carve<int>(batch);
+  for (int64_t off = 0; off < n; off += batch) {
+    const int64_t nb = std::min(batch, n - off);
+    mlmc_status s = run_pairs<T>(h, level, first_id + (uint64_t)off, nb, nullptr, nullptr, level,
+                                 level > 0 ? level - 1 : -1, B);
+    if (s != MLMC_OK) return s;
+    k_combine_status<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(B.st_f, level > 0 ? B.st_c : nullptr, B.status, nb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return c.cuda_fail(e, "status");
+    if (level == 0 && (e = cudaMemsetAsync(B.qc, 0, sizeof(double) * 2 * nb, st)) != cudaSuccess)
+      return c.cuda_fail(e, "memset");
+    if ((e = mlmc::launch_moments(B.qf, level > 0 ? B.qc : nullptr, B.status, nb, h->acc_dev + level, st)) !=
+        cudaSuccess)
+      return c.cuda_fail(e, "moments");
+    if ((e = from_device(q_fine ? q_fine + 2 * off : nullptr, B.qf, 2 * nb, st)) != cudaSuccess ||
+        (e = from_device(q_coarse ? q_coarse + 2 * off : nullptr, B.qc, 2 * nb, st)) != cudaSuccess ||
+        (e = from_device(status ? status + off : nullptr, B.status, nb, st)) != cudaSuccess)
+      return c.cuda_fail(e, "copy out");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return c.cuda_fail(e, "sample_level");
+  }
+  return MLMC_OK;
+}
+
+mlmc_status sync_stats(mlmc_ctx* h) {
+  Context& c = h->c;
+  cudaError_t e = cudaMemcpyAsync(h->acc_host.data(), h->acc_dev, sizeof(mlmc::LevelAcc) * h->acc_host.size(),
+                                  cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  return e == cudaSuccess ? MLMC_OK : c.cuda_fail(e, "stats");
+}
+
+double level_cost(const Context& c, int l) {
+  auto dofs = [&](int m) { return 2.0 * ((c.cfg.nx0 << m) + 1.0) * ((c.cfg.ny0 << m) + 1.0); };
+  const double g = c.cfg.mlmc_gamma > 0 ? c.cfg.mlmc_gamma : 1.0;
+  double cost = std::pow(dofs(l), g);
+  if (l > 0) cost += std::pow(dofs(l - 1), g);
+  return cost;
+}
+
+void fill_stats(const mlmc_ctx* h, int l, mlmc_level_stats* out) {
+  const mlmc::LevelAcc& a = h->acc_host[l];
+  std::memset(out, 0, sizeof(*out));
+  out->n = a.n;
+  for (int k = 0; k < 2; ++k) {
+    out->mean[k] = a.mean[k];
+    out->m2[k] = a.m2[k];
+    out->var[k] = a.n > 0 ? a.m2[k] / (double)a.n : 0.0;
+    out->sum_qf[k] = a.sum_qf[k] - a.comp_qf[k];
+    out->sum_qc[k] = a.sum_qc[k] - a.comp_qc[k];
+  }
+  out->cost = level_cost(h->c, l);
+}
+
+}  // namespace
+
+extern "C" {
+
+mlmc_status mlmc_create(const mlmc_config* cfg, void* cuda_stream, mlmc_ctx** out) {
+  if (!cfg || !out) {
+    g_create_error = "null argument";
+    return MLMC_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  std::string v = validate(*cfg);
+  if (!v.empty()) {
+    g_create_error = v;
+    return MLMC_ERR_INVALID_ARG;
+  }
+  bool ok = true;
+  mlmc::Invariants U = invariants(*cfg, ok);
+  if (!ok) {
+    g_create_error = "material constants do not give a positive definite plane-strain stiffness";
+    return MLMC_ERR_INVALID_ARG;
+  }
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) {
+    cudaGetLastError();
+    g_create_error = "no CUDA device";
+    return MLMC_ERR_CUDA;
+  }
+  mlmc_ctx* h = new mlmc_ctx();
+  Context& c = h->c;
+  c.cfg = *cfg;
+  c.U = U;
+  c.stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&c.device);
+  std::string msg;
+  if (!mlmc::build_kl_bases(c.cfg, c.bases_host, msg)) {
+    g_create_error = msg;
+    delete h;
+    return MLMC_ERR_INVALID_ARG;
+  }
+  for (int l = 0; l < c.cfg.levels; ++l) {
+    const std::vector<double>& B = c.bases_host[l].B;
+    double* d64 = nullptr;
+    float* d32 = nullptr;
+    if (cudaMalloc(&d64, sizeof(double) * B.size()) != cudaSuccess ||
+        cudaMalloc(&d32, sizeof(float) * B.size()) != cudaSuccess) {
+      cudaGetLastError();
+      g_create_error = "basis allocation failed";
+      if (d64) cudaFree(d64);
+      for (auto p : c.basis64) cudaFree(p);
+      for (auto p : c.basis32) cudaFree(p);
+      delete h;
+      return MLMC_ERR_OOM;
+    }
+    std::vector<float> B32(B.begin(), B.end());
+    cudaMemcpy(d64, B.data(), sizeof(double) * B.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(d32, B32.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice);
+    c.basis64.push_back(d64);
+    c.basis32.push_back(d32);
+  }
+  h->acc_host.assign(c.cfg.levels, mlmc::LevelAcc{});
+  std::memset(h->acc_host.data(), 0, sizeof(mlmc::LevelAcc) * c.cfg.levels);
+  h->next_id.assign(c.cfg.levels, 0);
+  if (cudaMalloc(&h->acc_dev, sizeof(mlmc::LevelAcc) * c.cfg.levels) != cudaSuccess ||
+      cudaMemset(h->acc_dev, 0, sizeof(mlmc::LevelAcc) * c.cfg.levels) != cudaSuccess) {
+    cudaGetLastError();
+    g_create_error = "stats allocation failed";
+    mlmc_destroy(h);
+    return MLMC_ERR_OOM;
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    g_create_error = cudaGetErrorString(e);
+    mlmc_destroy(h);
+    return MLMC_ERR_CUDA;
+  }
+  *out = h;
+  return MLMC_OK;
+}
+
+void mlmc_destroy(mlmc_ctx* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->c.stream);
+  for (auto p : h->c.basis64) cudaFree(p);
+  for (auto p : h->c.basis32) cudaFree(p);
+  h->c.solve_arena.release();
+  h->c.batch_arena.release();
+  if (h->acc_dev) cudaFree(h->acc_dev);
+  delete h;
+}
+
+const char* mlmc_last_error(const mlmc_ctx* h) { return h ? h->c.err.c_str() : g_create_error.c_str(); }
+
+mlmc_status mlmc_sample_level(mlmc_ctx* h, int32_t level, uint64_t first_id, int64_t n, double* q_fine,
+                              double* q_coarse, int32_t* status) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (level < 0 || level >= c.cfg.levels) return c.fail(MLMC_ERR_INVALID_ARG, "level out of range");
+  if (n < 0) return c.fail(MLMC_ERR_INVALID_ARG, "negative sample count");
+  if (n == 0) return MLMC_OK;
+  mlmc_status s = c.mixed() ? sample_level_t<float>(h, level, first_id, n, q_fine, q_coarse, status)
+                            : sample_level_t<double>(h, level, first_id, n, q_fine, q_coarse, status);
+  if (s != MLMC_OK) return s;
+  return sync_stats(h);
+}
+
+mlmc_status mlmc_level_stats_get(mlmc_ctx* h, int32_t level, mlmc_level_stats* out) {
+  if (!h || !out) return MLMC_ERR_INVALID_ARG;
+  if (level < 0 || level >= h->c.cfg.levels) return h->c.fail(MLMC_ERR_INVALID_ARG, "level out of range");
+  mlmc_status s = sync_stats(h);
+  if (s != MLMC_OK) return s;
+  fill_stats(h, level, out);
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_reset_stats(mlmc_ctx* h) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemsetAsync(h->acc_dev, 0, sizeof(mlmc::LevelAcc) * h->c.cfg.levels, h->c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->c.stream);
+  if (e != cudaSuccess) return h->c.cuda_fail(e, "reset");
+  std::memset(h->acc_host.data(), 0, sizeof(mlmc::LevelAcc) * h->acc_host.size());
+  std::fill(h->next_id.begin(), h->next_id.end(), 0);
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_solve_batch(mlmc_ctx* h, const mlmc_item* items, int64_t n, double* q, int32_t* status) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (n < 0 || (n > 0 && !items)) return c.fail(MLMC_ERR_INVALID_ARG, "bad item array");
+  if (n == 0) return MLMC_OK;
+  std::vector<mlmc_item> it(n);
+  if (is_device_ptr(items)) {
+    cudaMemcpy(it.data(), items, sizeof(mlmc_item) * n, cudaMemcpyDeviceToHost);
+  } else {
+    std::memcpy(it.data(), items, sizeof(mlmc_item) * n);
+  }
+  for (const auto& x : it)
+    if (x.level < 0 || x.level >= c.cfg.levels || x.mesh_level < 0 || x.mesh_level >= c.cfg.levels)
+      return c.fail(MLMC_ERR_INVALID_ARG, "item level out of range");
+  // group by mesh, stable order
+  std::vector<int64_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return it[a].mesh_level < it[b].mesh_level; });
+  std::vector<int> lv(n);
+  std::vector<uint64_t> ids(n);
+  for (int64_t k = 0; k < n; ++k) {
+    lv[k] = it[order[k]].level;
+    ids[k] = it[order[k]].sample_id;
+  }
+  const bool mixed = c.mixed();
+  const size_t tb = mixed ? 4 : 8;
+  int64_t nel_total = 0;
+  for (int64_t k = 0; k < n; ++k) nel_total += c.mesh(it[order[k]].mesh_level).n_el();
+  mlmc::Sizer sz;
+  sz.add<double>(n * c.cfg.kl_terms);
+  sz.add<float>(n * c.cfg.kl_terms);
+  sz.add<int>(1);
+  sz.add<int>(n);
+  sz.add<uint64_t>(n);
+  sz.add<char>(nel_total * tb);
+  sz.add<double>(2 * n);
+  sz.add<int>(n);
+  sz.add<int>(n);
+  cudaError_t e = c.batch_arena.reserve(sz.used + 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return c.fail(MLMC_ERR_OOM, "batch buffers");
+  }
+  c.batch_arena.reset();
+  double* xi = c.batch_arena.carve<double>(n * c.cfg.kl_terms);
+  float* xi32 = c.batch_arena.carve<float>(n * c.cfg.kl_terms);
+  int* fail = c.batch_arena.carve<int>(1);
+  int* lv_dev = c.batch_arena.carve<int>(n);
+  uint64_t* id_dev = c.batch_arena.carve<uint64_t>(n);
+  char* theta = c.batch_arena.carve<char>(nel_total * tb);
+  double* qd = c.batch_arena.carve<double>(2 * n);
+  int* sd = c.batch_arena.carve<int>(n);
+  int* itd = c.batch_arena.carve<int>(n);
+  cudaStream_t st = c.stream;
+  if ((e = cudaMemcpyAsync(lv_dev, lv.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(id_dev, ids.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(fail, 0, sizeof(int), st)) != cudaSuccess)
+    return c.cuda_fail(e, "items");
+  if ((e = mlmc::launch_kl_coefficients(c.cfg.seed, 0, 0, lv_dev, id_dev, n, c.cfg.kl_terms, xi,
+                                        mixed ? xi32 : nullptr, fail, st)) != cudaSuccess)
+    return c.cuda_fail(e, "kl_coefficients");
+  auto run = [&](auto tag) -> mlmc_status {
+    using T = decltype(tag);
+    std::vector<mlmc::SolveGroup<T>> groups;
+    const T* xiT = mixed ? (const T*)(const void*)xi32 : (const T*)(const void*)xi;
+    int64_t k = 0, eoff = 0;
+    while (k < n) {
+      const int m = it[order[k]].mesh_level;
+      int64_t k1 = k;
+      while (k1 < n && it[order[k1]].mesh_level == m) ++k1;
+      const int64_t nb = k1 - k;
+      const int64_t nel = c.mesh(m).n_el();
+      T* th = reinterpret_cast<T*>(theta) + eoff;
+      const T* B = mixed ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
+      cudaError_t err = mlmc::launch_kl_synthesis<T>(xiT + k * c.cfg.kl_terms, B, nb, (int)nel, c.cfg.kl_terms, th, st);
+      if (err != cudaSuccess) return c.cuda_fail(err, "kl_synthesis");
+      groups.push_back({m, nb, th, qd + 2 * k, sd + k, itd + k});
+      eoff += nb * nel;
+      k = k1;
+    }
+    return mlmc::solve_groups<T>(c, groups);
+  };
+  mlmc_status s = mixed ? run(float()) : run(double());
+  if (s != MLMC_OK) return s;
+  // scatter back to item order
+  std::vector<double> qh(2 * n), qo(2 * n);
+  std::vector<int> sh(n), so(n);
+  if ((e = cudaMemcpyAsync(qh.data(), qd, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(sh.data(), sd, sizeof(int) * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return c.cuda_fail(e, "copy out");
+  for (int64_t k = 0; k < n; ++k) {
+    qo[2 * order[k]] = qh[2 * k];
+    qo[2 * order[k] + 1] = qh[2 * k + 1];
+    so[order[k]] = sh[k];
+  }
+  if (q) {
+    if (is_device_ptr(q)) e = cudaMemcpy(q, qo.data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice);
+    else std::memcpy(q, qo.data(), sizeof(double) * 2 * n);
+  }
+  if (status) {
+    if (is_device_ptr(status)) e = cudaMemcpy(status, so.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+    else std::memcpy(status, so.data(), sizeof(int) * n);
+  }
+  return e == cudaSuccess ? MLMC_OK : c.cuda_fail(e, "copy out");
+}
+
+mlmc_status mlmc_estimate(mlmc_ctx* h, double e, double theta, int64_t n_star, int32_t max_level, int32_t qoi,
+                          double* estimate, mlmc_level_stats* stats, int32_t* L_out) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (!(e > 0) || !(theta > 0 && theta < 1) || n_star < 1 || max_level < 0 || qoi < 0 || qoi > 1)
+    return c.fail(MLMC_ERR_INVALID_ARG, "bad Algorithm 1 parameters");
+  max_level = std::min<int32_t>(max_level, c.cfg.levels - 1);
+  const double es2 = theta * e * e, eb = std::sqrt(1.0 - theta) * e;
+  const double m = c.cfg.mlmc_m > 0 ? c.cfg.mlmc_m : 4.0;
+  const double alpha = c.cfg.mlmc_alpha > 0 ? c.cfg.mlmc_alpha : 1.0;
+  auto take = [&](int l, int64_t upto) -> mlmc_status {
+    if (h->next_id[l] >= upto) return MLMC_OK;
+    const int64_t cnt = upto - h->next_id[l];
+    mlmc_status s = mlmc_sample_level(h, l, (uint64_t)h->next_id[l], cnt, nullptr, nullptr, nullptr);
+    if (s != MLMC_OK) return s;
+    h->next_id[l] = upto;
+    return MLMC_OK;
+  };
+  int L = -1;
+  bool converged = false;
+  while (!converged) {
+    if (L + 1 > max_level) break;
+    ++L;
+    mlmc_status s = take(L, n_star);
+    if (s != MLMC_OK) return s;
+    std::vector<double> V(L + 1), C(L + 1);
+    for (int l = 0; l <= L; ++l) {
+      const mlmc::LevelAcc& a = h->acc_host[l];
+      V[l] = a.n > 0 ? a.m2[qoi] / (double)a.n : 0.0;
+      C[l] = level_cost(c, l);
+    }
+    double tot = 0.0;
+    for (int l = 0; l <= L; ++l) tot += std::sqrt(V[l] * C[l]);
+    for (int l = 0; l <= L; ++l) {
+      const int64_t nhat = (int64_t)std::ceil(tot * std::sqrt(V[l] / C[l]) / es2);
+      if (h->next_id[l] < nhat) {
+        s = take(l, nhat);
+        if (s != MLMC_OK) return s;
+      }
+    }
+    const double bias = std::fabs(h->acc_host[L].mean[qoi]) / (std::pow(m, alpha) - 1.0);
+    if (bias < eb) converged = true;
+  }
+  double est = 0.0;
+  for (int l = 0; l <= L; ++l) est += h->acc_host[l].mean[qoi];
+  if (estimate) *estimate = est;
+  if (L_out) *L_out = L;
+  if (stats)
+    for (int l = 0; l <= L; ++l) fill_stats(h, l, &stats[l]);
+  return converged ? MLMC_OK : c.fail(MLMC_ERR_NOT_CONVERGED, "max_level reached before the bias test passed");
+}
+
+mlmc_status mlmc_kl_coefficients(mlmc_ctx* h, int32_t level, uint64_t first_id, int64_t n, double* xi) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (level < 0 || n < 0 || (n > 0 && !xi)) return c.fail(MLMC_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return MLMC_OK;
+  const size_t cnt = (size_t)n * c.cfg.kl_terms;
+  cudaError_t e = c.batch_arena.reserve(sizeof(double) * cnt + 1024);
+  if (e != cudaSuccess) return c.fail(MLMC_ERR_OOM, "xi buffer");
+  c.batch_arena.reset();
+  double* d = c.batch_arena.carve<double>(cnt);
+  int* fail = c.batch_arena.carve<int>(1);
+  if ((e = cudaMemsetAsync(fail, 0, sizeof(int), c.stream)) != cudaSuccess ||
+      (e = mlmc::launch_kl_coefficients(c.cfg.seed, level, first_id, nullptr, nullptr, n, c.cfg.kl_terms, d,
+                                        nullptr, fail, c.stream)) != cudaSuccess ||
+      (e = from_device(xi, d, cnt, c.stream)) != cudaSuccess || (e = cudaStreamSynchronize(c.stream)) != cudaSuccess)
+    return c.cuda_fail(e, "kl_coefficients");
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_theta(mlmc_ctx* h, int32_t level, int32_t mesh_level, uint64_t first_id, int64_t n,
+                       double* theta) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (level < 0 || mesh_level < 0 || mesh_level >= c.cfg.levels || n < 0 || (n > 0 && !theta))
+    return c.fail(MLMC_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return MLMC_OK;
+  const int nkl = c.cfg.kl_terms;
+  const int64_t nel = c.mesh(mesh_level).n_el();
+  mlmc::Sizer sz;
+  sz.add<double>(n * nkl);
+  sz.add<float>(n * nkl);
+  sz.add<int>(1);
+  sz.add<double>(n * nel);
+  sz.add<float>(n * nel);
+  cudaError_t e = c.batch_arena.reserve(sz.used + 256);
+  if (e != cudaSuccess) return c.fail(MLMC_ERR_OOM, "theta buffers");
+  c.batch_arena.reset();
+  double* xi = c.batch_arena.carve<double>(n * nkl);
+  float* xi32 = c.batch_arena.carve<float>(n * nkl);
+  int* fail = c.batch_arena.carve<int>(1);
+  double* th = c.batch_arena.carve<double>(n * nel);
+  float* th32 = c.batch_arena.carve<float>(n * nel);
+  cudaStream_t st = c.stream;
+  if ((e = cudaMemsetAsync(fail, 0, sizeof(int), st)) != cudaSuccess ||
+      (e = mlmc::launch_kl_coefficients(c.cfg.seed, level, first_id, nullptr, nullptr, n, nkl, xi, xi32, fail, st)) !=
+          cudaSuccess)
+    return c.cuda_fail(e, "kl_coefficients");
+  if (c.mixed()) {
+    if ((e = mlmc::launch_kl_synthesis<float>(xi32, c.basis32[mesh_level], n, (int)nel, nkl, th32, st)) != cudaSuccess ||
+        (e = convert(th32, th, n * nel, st)) != cudaSuccess)
+      return c.cuda_fail(e, "kl_synthesis");
+  } else if ((e = mlmc::launch_kl_synthesis<double>(xi, c.basis64[mesh_level], n, (int)nel, nkl, th, st)) !=
+             cudaSuccess) {
+    return c.cuda_fail(e, "kl_synthesis");
+  }
+  if ((e = from_device(theta, th, n * nel, st)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return c.cuda_fail(e, "copy out");
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_apply(mlmc_ctx* h, int32_t mesh_level, int64_t n, const double* theta, const double* p, double* q) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (mesh_level < 0 || mesh_level >= c.cfg.levels || n < 0 || (n > 0 && (!theta || !p || !q)))
+    return c.fail(MLMC_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return MLMC_OK;
+  const mlmc::LevelLayout m = c.mesh(mesh_level);
+  const int64_t ne = n * m.n_el(), nd = n * 2 * m.n_nodes();
+  mlmc::Sizer sz;
+  sz.add<double>(ne);
+  sz.add<double>(nd);
+  sz.add<double>(nd);
+  sz.add<float>(ne);
+  sz.add<float>(nd);
+  sz.add<float>(nd);
+  cudaError_t e = c.batch_arena.reserve(sz.used + 256);
+  if (e != cudaSuccess) return c.fail(MLMC_ERR_OOM, "apply buffers");
+  c.batch_arena.reset();
+  double* th = c.batch_arena.carve<double>(ne);
+  double* pd = c.batch_arena.carve<double>(nd);
+  double* qd = c.batch_arena.carve<double>(nd);
+  float* th32 = c.batch_arena.carve<float>(ne);
+  float* p32 = c.batch_arena.carve<float>(nd);
+  float* q32 = c.batch_arena.carve<float>(nd);
+  cudaStream_t st = c.stream;
+  if ((e = to_device(th, theta, ne, st)) != cudaSuccess || (e = to_device(pd, p, nd, st)) != cudaSuccess)
+    return c.cuda_fail(e, "copy in");
+  mlmc_status s;
+  if (c.mixed()) {
+    if ((e = convert(th, th32, ne, st)) != cudaSuccess || (e = convert(pd, p32, nd, st)) != cudaSuccess)
+      return c.cuda_fail(e, "convert");
+    s = mlmc::apply_operator<float>(c, mesh_level, n, th32, p32, q32);
+    if (s != MLMC_OK) return s;
+    if ((e = convert(q32, qd, nd, st)) != cudaSuccess) return c.cuda_fail(e, "convert");
+  } else {
+    s = mlmc::apply_operator<double>(c, mesh_level, n, th, pd, qd);
+    if (s != MLMC_OK) return s;
+  }
+  if ((e = from_device(q, qd, nd, st)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return c.cuda_fail(e, "copy out");
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_solve_theta(mlmc_ctx* h, int32_t mesh_level, int64_t n, const double* theta, double* q,
+                             int32_t* status, int32_t* iterations) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (mesh_level < 0 || mesh_level >= c.cfg.levels || n < 0 || (n > 0 && (!theta || !q)))
+    return c.fail(MLMC_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return MLMC_OK;
+  const int64_t ne = n * c.mesh(mesh_level).n_el();
+  mlmc::Sizer sz;
+  sz.add<double>(ne);
+  sz.add<float>(ne);
+  sz.add<double>(2 * n);
+  sz.add<int>(n);
+  sz.add<int>(n);
+  cudaError_t e = c.batch_arena.reserve(sz.used + 256);
+  if (e != cudaSuccess) return c.fail(MLMC_ERR_OOM, "solve buffers");
+  c.batch_arena.reset();
+  double* th = c.batch_arena.carve<double>(ne);
+  float* th32 = c.batch_arena.carve<float>(ne);
+  double* qd = c.batch_arena.carve<double>(2 * n);
+  int* sd = c.batch_arena.carve<int>(n);
+  int* itd = c.batch_arena.carve<int>(n);
+  cudaStream_t st = c.stream;
+  if ((e = to_device(th, theta, ne, st)) != cudaSuccess) return c.cuda_fail(e, "copy in");
+  mlmc_status s;
+  if (c.mixed()) {
+    if ((e = convert(th, th32, ne, st)) != cudaSuccess) return c.cuda_fail(e, "convert");
+    std::vector<mlmc::SolveGroup<float>> g{{mesh_level, n, th32, qd, sd, itd}};
+    s = mlmc::solve_groups<float>(c, g);
+  } else {
+    std::vector<mlmc::SolveGroup<double>> g{{mesh_level, n, th, qd, sd, itd}};
+    s = mlmc::solve_groups<double>(c, g);
+  }
+  if (s != MLMC_OK) return s;
+  if ((e = from_device(q, qd, 2 * n, st)) != cudaSuccess ||
+      (e = from_device(status, sd, n, st)) != cudaSuccess ||
+      (e = from_device(iterations, itd, n, st)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return c.cuda_fail(e, "copy out");
+  return MLMC_OK;
+}
+
+}  // extern "C"

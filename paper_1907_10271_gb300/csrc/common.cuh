@@ -1,0 +1,148 @@
+// Shared device-side definitions of the level-pair engine.
+//
+// Element operator. Each element of the structured grid is a rectangle hx x hy with
+// one rotated plane-strain stiffness C_bar (6 coefficients). For a rectangle the
+// bilinear strain field splits exactly into its centroid value and two
+// "hourglass" gradients:
+//   e_xx = rx (a_u + eta g_u),  e_yy = ry (b_v + xi g_v),
+//   g_xy = ry (b_u + xi g_u) + rx (a_v + eta g_v),      rx = 1/(2 hx), ry = 1/(2 hy)
+// with a = -n1 + n2 + n3 - n4, b = -n1 - n2 + n3 + n4, g = n1 - n2 + n3 - n4 over the
+// corner values (n1 = (-,-), n2 = (+,-), n3 = (+,+), n4 = (-,+)). The 2x2 Gauss rule
+// of Eq. matrixinplane's element matrices sums xi, eta, xi*eta to zero and xi^2,
+// eta^2 to 4/3, so K_e p = hx hy [D0^T C E0 + (1/3)(Dxi^T C Gxi + Deta^T C Geta)]
+// exactly, at about 60 flops per element instead of an 8x8 matrix.
+//
+// Rotation (Sec. 3.1, C* = T^-1 C T). With the Tsai-Pagano invariants U1..U5 of the
+// fibre-frame plane-strain stiffness, C_bar(theta) is affine in
+// (cos 2t, sin 2t, cos 4t, sin 4t):
+//   C11 = U1 + U2 c2 + U3 c4     C22 = U1 - U2 c2 + U3 c4
+//   C12 = U4 - U3 c4             C66 = U5 - U3 c4
+//   C16 = U2/2 s2 + U3 s4        C26 = U2/2 s2 - U3 s4
+// so the average of C_bar over child elements is C_bar of the averaged trigonometric
+// 4-vector, which is how coarse multigrid levels are rediscretised.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mlmc {
+
+constexpr int kWarp = 32;
+constexpr int kStripCols = 30;     // output node columns per warp strip (32 lanes, 1 halo each side)
+constexpr int kRowChunk = 16;      // output node rows per warp tile
+constexpr int kWarpsPerBlock = 4;
+constexpr double kOmega = 0.5;     // Jacobi damping: element bound of lambda_max(D^-1 K) < 3.9 for any angle
+constexpr int kMaxCoarsestDofs = 64;
+
+struct Invariants {
+  double U1, U2, U3, U4, U5;
+};
+
+template <typename T>
+struct Coef {
+  T c11, c12, c16, c22, c26, c66;
+};
+
+template <typename T>
+struct V2 {
+  T u, v;
+};
+
+template <typename T>
+__device__ __forceinline__ V2<T> v2(T u, T v) {
+  V2<T> r;
+  r.u = u;
+  r.v = v;
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ Coef<T> coef_from_trig(const Invariants& U, T c2, T s2, T c4, T s4) {
+  Coef<T> c;
+  const T u1 = (T)U.U1, u2 = (T)U.U2, u3 = (T)U.U3, u4 = (T)U.U4, u5 = (T)U.U5;
+  c.c11 = u1 + u2 * c2 + u3 * c4;
+  c.c22 = u1 - u2 * c2 + u3 * c4;
+  c.c12 = u4 - u3 * c4;
+  c.c66 = u5 - u3 * c4;
+  c.c16 = (T)0.5 * u2 * s2 + u3 * s4;
+  c.c26 = (T)0.5 * u2 * s2 - u3 * s4;
+  return c;
+}
+
+__device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
+
+// (c2, s2, c4, s4) of an angle.
+template <typename T>
+__device__ __forceinline__ void trig4(T theta, T* c2, T* s2, T* c4, T* s4) {
+  T s, c;
+  sincos_t((T)2 * theta, &s, &c);
+  *c2 = c;
+  *s2 = s;
+  *c4 = (T)2 * c * c - (T)1;
+  *s4 = (T)2 * s * c;
+}
+
+template <typename T>
+__device__ __forceinline__ Coef<T> coef_from_theta(const Invariants& U, T theta) {
+  T c2, s2, c4, s4;
+  trig4(theta, &c2, &s2, &c4, &s4);
+  return coef_from_trig(U, c2, s2, c4, s4);
+}
+
+// Element operator: K_e applied to corner values n1..n4 (u, v each).
+// Outputs the contributions to n1..n4.
+template <typename T>
+__device__ __forceinline__ void element_apply(const Coef<T>& C, T rx, T ry, T w,
+                                              V2<T> n1, V2<T> n2, V2<T> n3, V2<T> n4,
+                                              V2<T>& o1, V2<T>& o2, V2<T>& o3, V2<T>& o4) {
+  const T du21 = n2.u - n1.u, du34 = n3.u - n4.u, du41 = n4.u - n1.u, du32 = n3.u - n2.u;
+  const T dv21 = n2.v - n1.v, dv34 = n3.v - n4.v, dv41 = n4.v - n1.v, dv32 = n3.v - n2.v;
+  const T au = du21 + du34, bu = du41 + du32, gu = du34 - du21;
+  const T av = dv21 + dv34, bv = dv41 + dv32, gv = dv34 - dv21;
+  // centroid strain and stress
+  const T ex = rx * au, ey = ry * bv, exy = ry * bu + rx * av;
+  const T sx = C.c11 * ex + C.c12 * ey + C.c16 * exy;
+  const T sy = C.c12 * ex + C.c22 * ey + C.c26 * exy;
+  const T sxy = C.c16 * ex + C.c26 * ey + C.c66 * exy;
+  // hourglass parts: G_xi = (0, ry gv, ry gu), G_eta = (rx gu, 0, rx gv)
+  const T gxi_y = ry * gv, gxi_g = ry * gu, get_x = rx * gu, get_g = rx * gv;
+  const T sxi_y = C.c22 * gxi_y + C.c26 * gxi_g;      // (C G_xi)_y
+  const T sxi_g = C.c26 * gxi_y + C.c66 * gxi_g;      // (C G_xi)_xy
+  const T set_x = C.c11 * get_x + C.c16 * get_g;      // (C G_eta)_x
+  const T set_g = C.c16 * get_x + C.c66 * get_g;      // (C G_eta)_xy
+  const T third = (T)(1.0 / 3.0);
+  const T A = w * rx * sx, B = w * ry * sy, Cx = w * ry * sxy, Cy = w * rx * sxy;
+  const T Hu = w * third * (ry * sxi_g + rx * set_x);
+  const T Hv = w * third * (ry * sxi_y + rx * set_g);
+  // q_u = xi A + eta Cx + (xi eta) Hu ; q_v = eta B + xi Cy + (xi eta) Hv
+  o1.u = -A - Cx + Hu;  o1.v = -B - Cy + Hv;
+  o2.u = A - Cx - Hu;   o2.v = -B + Cy - Hv;
+  o3.u = A + Cx + Hu;   o3.v = B + Cy + Hv;
+  o4.u = -A + Cx - Hu;  o4.v = B - Cy - Hv;
+}
+
+// Diagonal of K_e at local node with xi*eta = sgn (+1 for n1, n3; -1 for n2, n4).
+template <typename T>
+__device__ __forceinline__ V2<T> element_diag(const Coef<T>& C, T rx, T ry, T w, T sgn) {
+  const T f = (T)(4.0 / 3.0);
+  V2<T> d;
+  d.u = w * (f * (C.c11 * rx * rx + C.c66 * ry * ry) + (T)2 * C.c16 * rx * ry * sgn);
+  d.v = w * (f * (C.c22 * ry * ry + C.c66 * rx * rx) + (T)2 * C.c26 * rx * ry * sgn);
+  return d;
+}
+
+// Geometry of one multigrid level of one solve group.
+struct Geo {
+  int nx, ny;         // elements
+  double rx, ry, w;   // 1/(2hx), 1/(2hy), hx*hy
+  int nodes() const { return (nx + 1) * (ny + 1); }
+};
+
+__host__ __device__ __forceinline__ int strips_of(int nx) { return (nx + 1 + kStripCols - 1) / kStripCols; }
+__host__ __device__ __forceinline__ int chunks_of(int ny) { return (ny + 1 + kRowChunk - 1) / kRowChunk; }
+
+// Dirichlet DOFs: u = v = 0 on column 0, u prescribed on column nx.
+__device__ __forceinline__ bool dir_u(int i, int nx) { return i == 0 || i == nx; }
+__device__ __forceinline__ bool dir_v(int i) { return i == 0; }
+
+}  // namespace mlmc

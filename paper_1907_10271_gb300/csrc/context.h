@@ -1,0 +1,95 @@
+// Library context (host side).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "fem.cuh"
+
+namespace mlmc {
+
+// Grow-only device arena: carve() hands out 256-byte aligned ranges of one allocation.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  cudaError_t reserve(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) return e;
+    cap = bytes;
+    return cudaSuccess;
+  }
+  void reset() { used = 0; }
+  template <typename T>
+  T* carve(size_t count) {
+    const size_t off = (used + 255) & ~(size_t)255;
+    used = off + count * sizeof(T);
+    return reinterpret_cast<T*>(base + off);
+  }
+  void release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = used = 0;
+  }
+};
+
+// Size accounting twin of Arena (same alignment rule).
+struct Sizer {
+  size_t used = 0;
+  template <typename T>
+  void add(size_t count) {
+    used = ((used + 255) & ~(size_t)255) + count * sizeof(T);
+  }
+};
+
+struct LevelLayout {
+  int nx, ny;
+  int64_t n_el() const { return (int64_t)nx * ny; }
+  int64_t n_nodes() const { return (int64_t)(nx + 1) * (ny + 1); }
+};
+
+struct Context {
+  mlmc_config cfg;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  Invariants U;
+  std::vector<KLBasis> bases_host;
+  std::vector<double*> basis64;   // device, per mesh level
+  std::vector<float*> basis32;
+  Arena solve_arena;              // solver workspace
+  Arena batch_arena;              // per-call inputs (xi, theta, outputs)
+  std::vector<mlmc_level_stats> stats;
+  std::vector<double> comp;       // Kahan compensation of sum_qf / sum_qc per level [l][4]
+  std::string err;
+  double floor_tol32 = 3e-6;      // tightest inner relative tolerance of the FP32 solve
+  int check_every = 4;            // PCG iterations between host convergence checks
+  int last_outer = 0;             // refinement steps of the last solve (diagnostic)
+  int last_iters = 0;             // max PCG iterations of the last solve (diagnostic)
+
+  bool mixed() const { return cfg.precision == MLMC_PREC_MIXED; }
+  LevelLayout mesh(int l) const { return LevelLayout{cfg.nx0 << l, cfg.ny0 << l}; }
+  Geo geo(int nx, int ny) const {
+    Geo g;
+    g.nx = nx;
+    g.ny = ny;
+    const double hx = cfg.lx / nx, hy = cfg.ly / ny;
+    g.rx = 0.5 / hx;
+    g.ry = 0.5 / hy;
+    g.w = hx * hy;
+    return g;
+  }
+  mlmc_status fail(mlmc_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  mlmc_status cuda_fail(cudaError_t e, const char* where) {
+    cudaGetLastError();  // clear a non-sticky error so later launch checks do not see it
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return MLMC_ERR_CUDA;
+  }
+};
+
+}  // namespace mlmc

@@ -1,0 +1,54 @@
+// Internal interfaces of the level-pair engine (host side).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mlmc.h"
+#include "common.cuh"
+
+namespace mlmc {
+
+// ---------------------------------------------------------------- kernels (launchers)
+cudaError_t launch_kl_coefficients(uint64_t seed, int level, uint64_t first_id, const int* levels,
+                                   const uint64_t* ids, int64_t n, int n_kl, double* xi, float* xi32, int* fail,
+                                   cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_kl_synthesis(const T* xi, const T* basis, int64_t nsamp, int n_el, int n_kl,
+                                T* theta, cudaStream_t st);
+
+// ---------------------------------------------------------------- KL basis (host)
+struct KLBasis {
+  int nx, ny, n_kl;
+  std::vector<double> B;   // [n_el][n_kl], B[e][n] = sqrt(mu_n) phi_n(centroid_e)
+};
+
+// Builds the basis of every mesh level 0..levels-1. Returns false with msg on failure.
+bool build_kl_bases(const mlmc_config& cfg, std::vector<KLBasis>& out, std::string& msg);
+
+// ---------------------------------------------------------------- solver
+struct Context;  // defined in api.cu
+
+// One set of n samples on one mesh, each with its own field theta (device, T).
+template <typename T>
+struct SolveGroup {
+  int mesh_level;      // MLMC mesh index
+  int64_t nsamp;
+  const T* theta;      // [nsamp][n_el] device
+  double* q;           // [nsamp][2] device output
+  int* status;         // [nsamp] device output
+  int* iters;          // [nsamp] device output (total PCG iterations)
+};
+
+// Solves every group to cfg.rtol (fp64 path: T = double throughout; mixed path:
+// T = float inner solve with double refinement) and writes q, status, iters.
+template <typename T>
+mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups);
+
+template <typename T>
+mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* theta, const T* p, T* q);
+
+}  // namespace mlmc

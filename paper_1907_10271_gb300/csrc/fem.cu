@@ -1,0 +1,856 @@
+// Matrix-free Q1 plane-strain operator (Eq. matrixinplane) and the multigrid-PCG
+// kernels built on it.
+//
+// Warp-strip scheme. A warp owns 32 consecutive node columns of one sample (one halo
+// column each side, 30 output columns) and walks up a chunk of node rows. Lane L
+// computes the element to the upper right of its node from its own column values
+// and its right neighbour's (warp shuffle down); the element's contributions to the
+// right-hand nodes go back by a shuffle up, and the contributions to the upper nodes
+// stay in registers for the next row. No shared memory, every vector read once per
+// row with 256-byte coalesced accesses (FP32), each element evaluated once per warp.
+//
+// The kernels fuse each V-cycle / PCG step with the operator it needs:
+//   Apply    q = K p (all rows; testing)
+//   PreTop   PCG update  x += alpha p, r' = r - alpha q   (r' written to a second buffer),
+//            Jacobi pre-smoothing from zero  x1 = w D^-1 r', residual r1 = r' - K x1,
+//            ||r'||^2 reduced per sample
+//   Pre      the same smoothing step on a coarse level: x1 = w D^-1 b, r1 = b - K x1
+//   Post     prolongation + post-smoothing: x2 = w D^-1 b + P x_c, z = x2 + w D^-1 (b - K x2)
+//   PostTop  Post on the finest level, also reducing b . z
+//   PcgP     search direction p' = z + beta p (second buffer), q = K p', p' . q reduced
+// Homogeneous Dirichlet rows (u, v on x = 0; u on x = lx) are zero in every vector;
+// w D^-1 is stored with zeros there.
+#include <cfloat>
+
+#include "../../include/mlmc.h"
+#include "fem.cuh"
+
+namespace mlmc {
+
+namespace {
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+template <typename T>
+__device__ __forceinline__ V2<T> ld2(const T* p) {
+  const typename Vec2<T>::type t = *reinterpret_cast<const typename Vec2<T>::type*>(p);
+  return v2<T>(t.x, t.y);
+}
+
+template <typename T>
+__device__ __forceinline__ void st2(T* p, V2<T> v) {
+  typename Vec2<T>::type t;
+  t.x = v.u;
+  t.y = v.v;
+  *reinterpret_cast<typename Vec2<T>::type*>(p) = t;
+}
+
+template <typename T>
+__device__ __forceinline__ V2<T> zero2() {
+  return v2<T>((T)0, (T)0);
+}
+
+template <typename T>
+__device__ __forceinline__ V2<T> shfl_down2(V2<T> a) {
+  return v2<T>(__shfl_down_sync(0xffffffffu, a.u, 1), __shfl_down_sync(0xffffffffu, a.v, 1));
+}
+
+template <typename T>
+__device__ __forceinline__ V2<T> shfl_up2(V2<T> a) {
+  return v2<T>(__shfl_up_sync(0xffffffffu, a.u, 1), __shfl_up_sync(0xffffffffu, a.v, 1));
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ Coef<T> load_coef(const Invariants& U, const View<T>& V, int64_t ebase, int i, int j) {
+  const int64_t e = ebase + (int64_t)j * V.g.nx + i;
+  if (V.theta) return coef_from_theta<T>(U, V.theta[e]);
+  const T* t = V.trig + 4 * e;
+  return coef_from_trig<T>(U, t[0], t[1], t[2], t[3]);
+}
+
+// Locate the view and tile of this warp.
+template <typename T>
+__device__ __forceinline__ bool find_tile(const ViewList<T>& L, int gw, int& vi, int& s, int& strip, int& chunk) {
+  vi = 0;
+  while (vi < L.n && gw >= L.v[vi].work_begin + L.v[vi].nwork) ++vi;
+  if (vi >= L.n || gw < L.v[vi].work_begin) return false;
+  const View<T>& V = L.v[vi];
+  const int tile = gw - V.work_begin;
+  const int per_s = V.tiles_x * V.tiles_y;
+  s = tile / per_s;
+  const int r = tile - s * per_s;
+  chunk = r / V.tiles_x;
+  strip = r - chunk * V.tiles_x;
+  return s < V.nsamp;
+}
+
+template <typename T, typename Op>
+__device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V, int strip, int chunk, Op& op) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int nx = V.g.nx, ny = V.g.ny;
+  const int i = strip * kStripCols - 1 + lane;
+  const bool col_in = (i >= 0) && (i <= nx);
+  const bool elem = (i >= 0) && (i < nx) && (lane < kWarp - 1);
+  const bool out_col = col_in && lane >= 1 && lane <= kStripCols;
+  const int j0 = chunk * kRowChunk;
+  const int j1 = min(j0 + kRowChunk - 1, ny);
+  const int er0 = max(j0 - 1, 0);
+  const int er1 = min(j1, ny - 1);
+  const T rx = (T)V.g.rx, ry = (T)V.g.ry, w = (T)V.g.w;
+  V2<T> pb = col_in ? op.in(i, er0) : zero2<T>();
+  op.shift();
+  V2<T> acc = zero2<T>();
+  for (int er = er0; er <= er1; ++er) {
+    const V2<T> pt = col_in ? op.in(i, er + 1) : zero2<T>();
+    const V2<T> pbr = shfl_down2(pb), ptr = shfl_down2(pt);
+    V2<T> o1 = zero2<T>(), o2 = zero2<T>(), o3 = zero2<T>(), o4 = zero2<T>();
+    if (elem) {
+      const Coef<T> C = op.coef(U, i, er);
+      element_apply<T>(C, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
+    }
+    V2<T> fb = shfl_up2(o2), ft = shfl_up2(o3);
+    if (lane == 0) {
+      fb = zero2<T>();
+      ft = zero2<T>();
+    }
+    acc.u += o1.u + fb.u;
+    acc.v += o1.v + fb.v;
+    if (er >= j0 && out_col) op.out(i, er, acc);
+    acc.u = o4.u + ft.u;
+    acc.v = o4.v + ft.v;
+    op.shift();
+    pb = pt;
+  }
+  // the top boundary row (only element row ny - 1 contributes) belongs to the chunk that owns it
+  if (er1 + 1 == ny && ny >= j0 && ny <= j1 && out_col) op.out(i, ny, acc);
+}
+
+// ---------------------------------------------------------------- operand handlers
+
+template <typename T>
+struct OpBase {
+  const View<T>& V;
+  int64_t nbase;   // first value of the sample's vectors
+  int64_t ebase;   // first element of the sample
+  int nxp;         // nx + 1
+  __device__ OpBase(const View<T>& v, int s)
+      : V(v),
+        nbase((int64_t)s * 2 * (v.g.nx + 1) * (v.g.ny + 1)),
+        ebase((int64_t)s * v.g.nx * v.g.ny),
+        nxp(v.g.nx + 1) {}
+  __device__ __forceinline__ int64_t at(int i, int j) const { return nbase + 2 * ((int64_t)j * nxp + i); }
+  __device__ __forceinline__ Coef<T> coef(const Invariants& U, int i, int j) const {
+    return load_coef<T>(U, V, ebase, i, j);
+  }
+  __device__ __forceinline__ V2<T> mask(int i, V2<T> x) const {
+    if (dir_u(i, V.g.nx)) x.u = (T)0;
+    if (dir_v(i)) x.v = (T)0;
+    return x;
+  }
+};
+
+template <typename T>
+struct OpApply : OpBase<T> {
+  __device__ OpApply(const View<T>& v, int s, const SampleState&) : OpBase<T>(v, s) {}
+  __device__ bool live() const { return true; }
+  __device__ V2<T> in(int i, int j) { return ld2(this->V.a + this->at(i, j)); }
+  __device__ void out(int i, int j, V2<T> kp) { st2(this->V.o0 + this->at(i, j), kp); }
+  __device__ void shift() {}
+  __device__ void finish(const SampleState&, int) {}
+};
+
+// a = r (old), b = q, c = p, winvd; o0 = x (updated in place), o1 = r (new), o2 = r1.
+template <typename T>
+struct OpPreTop : OpBase<T> {
+  T alpha;
+  bool act;
+  V2<T> rt, rb;
+  double rr = 0.0;
+  __device__ OpPreTop(const View<T>& v, int s, const SampleState& S) : OpBase<T>(v, s) {
+    act = S.active[v.sbase + s] != 0;
+    alpha = (T)S.alpha[v.sbase + s];
+  }
+  __device__ bool live() const { return act; }
+  __device__ V2<T> in(int i, int j) {
+    const int64_t k = this->at(i, j);
+    const V2<T> r = ld2(this->V.a + k), q = ld2(this->V.b + k), wd = ld2(this->V.winvd + k);
+    rt = v2<T>(r.u - alpha * q.u, r.v - alpha * q.v);
+    return v2<T>(wd.u * rt.u, wd.v * rt.v);
+  }
+  __device__ void out(int i, int j, V2<T> kx) {
+    const int64_t k = this->at(i, j);
+    const V2<T> r1 = this->mask(i, v2<T>(rb.u - kx.u, rb.v - kx.v));
+    st2(this->V.o2 + k, r1);
+    st2(this->V.o1 + k, rb);
+    const V2<T> x = ld2(this->V.o0 + k), p = ld2(this->V.c + k);
+    st2(this->V.o0 + k, v2<T>(x.u + alpha * p.u, x.v + alpha * p.v));
+    rr += (double)rb.u * rb.u + (double)rb.v * rb.v;
+  }
+  __device__ void shift() { rb = rt; }
+  __device__ void finish(const SampleState& S, int s) {
+    const double t = warp_sum(rr);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&S.red_rr[this->V.sbase + s], t);
+  }
+};
+
+// a = b, winvd; o2 = r1.
+template <typename T>
+struct OpPre : OpBase<T> {
+  bool act;
+  V2<T> bt, bb;
+  __device__ OpPre(const View<T>& v, int s, const SampleState& S) : OpBase<T>(v, s) {
+    act = S.active[v.sbase + s] != 0;
+  }
+  __device__ bool live() const { return act; }
+  __device__ V2<T> in(int i, int j) {
+    const int64_t k = this->at(i, j);
+    bt = ld2(this->V.a + k);
+    const V2<T> wd = ld2(this->V.winvd + k);
+    return v2<T>(wd.u * bt.u, wd.v * bt.v);
+  }
+  __device__ void out(int i, int j, V2<T> kx) {
+    st2(this->V.o2 + this->at(i, j), this->mask(i, v2<T>(bb.u - kx.u, bb.v - kx.v)));
+  }
+  __device__ void shift() { bb = bt; }
+  __device__ void finish(const SampleState&, int) {}
+};
+
+// a = b, xc (level below), winvd; o0 = z.  TOP also reduces b . z.
+template <typename T, bool TOP>
+struct OpPost : OpBase<T> {
+  bool act;
+  int nxc;
+  int64_t cbase;
+  V2<T> bt, bb, xt, xb, wt, wb;
+  double rz = 0.0;
+  __device__ OpPost(const View<T>& v, int s, const SampleState& S) : OpBase<T>(v, s) {
+    act = S.active[v.sbase + s] != 0;
+    nxc = v.g.nx / 2;
+    cbase = (int64_t)s * 2 * (nxc + 1) * (v.g.ny / 2 + 1);
+  }
+  __device__ bool live() const { return act; }
+  __device__ V2<T> coarse(int I, int J) const { return ld2(this->V.xc + cbase + 2 * ((int64_t)J * (nxc + 1) + I)); }
+  __device__ V2<T> prolong(int i, int j) const {
+    const int I = i >> 1, J = j >> 1;
+    const bool fi = i & 1, fj = j & 1;
+    V2<T> x = coarse(I, J);
+    if (fi) {
+      const V2<T> r = coarse(I + 1, J);
+      x = v2<T>(x.u + r.u, x.v + r.v);
+    }
+    if (fj) {
+      V2<T> t = coarse(I, J + 1);
+      if (fi) {
+        const V2<T> tr = coarse(I + 1, J + 1);
+        t = v2<T>(t.u + tr.u, t.v + tr.v);
+      }
+      x = v2<T>(x.u + t.u, x.v + t.v);
+    }
+    const T f = (fi && fj) ? (T)0.25 : ((fi || fj) ? (T)0.5 : (T)1);
+    return v2<T>(f * x.u, f * x.v);
+  }
+  __device__ V2<T> in(int i, int j) {
+    const int64_t k = this->at(i, j);
+    bt = ld2(this->V.a + k);
+    wt = ld2(this->V.winvd + k);
+    const V2<T> pc = prolong(i, j);
+    xt = v2<T>(wt.u * bt.u + pc.u, wt.v * bt.v + pc.v);
+    return xt;
+  }
+  __device__ void out(int i, int j, V2<T> kx) {
+    const V2<T> z = this->mask(i, v2<T>(xb.u + wb.u * (bb.u - kx.u), xb.v + wb.v * (bb.v - kx.v)));
+    st2(this->V.o0 + this->at(i, j), z);
+    if (TOP) rz += (double)bb.u * z.u + (double)bb.v * z.v;
+  }
+  __device__ void shift() {
+    bb = bt;
+    xb = xt;
+    wb = wt;
+  }
+  __device__ void finish(const SampleState& S, int s) {
+    if (TOP) {
+      const double t = warp_sum(rz);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&S.red_rz[this->V.sbase + s], t);
+    }
+  }
+};
+
+// a = z, b = p (old); o0 = p (new), o1 = q.
+template <typename T>
+struct OpPcgP : OpBase<T> {
+  bool act;
+  T beta;
+  V2<T> pt, pb;
+  double pq = 0.0;
+  __device__ OpPcgP(const View<T>& v, int s, const SampleState& S) : OpBase<T>(v, s) {
+    act = S.active[v.sbase + s] != 0;
+    beta = (T)S.beta[v.sbase + s];
+  }
+  __device__ bool live() const { return act; }
+  __device__ V2<T> in(int i, int j) {
+    const int64_t k = this->at(i, j);
+    const V2<T> z = ld2(this->V.a + k), p = ld2(this->V.b + k);
+    pt = v2<T>(z.u + beta * p.u, z.v + beta * p.v);
+    return pt;
+  }
+  __device__ void out(int i, int j, V2<T> kp) {
+    const int64_t k = this->at(i, j);
+    const V2<T> q = this->mask(i, kp);
+    st2(this->V.o0 + k, pb);
+    st2(this->V.o1 + k, q);
+    pq += (double)pb.u * q.u + (double)pb.v * q.v;
+  }
+  __device__ void shift() { pb = pt; }
+  __device__ void finish(const SampleState& S, int s) {
+    const double t = warp_sum(pq);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&S.red_pq[this->V.sbase + s], t);
+  }
+};
+
+// Refinement residual in double: a = d; ext0 = angles (TI); ext1 = r output (TI).
+template <typename TI>
+struct OpResid : OpBase<double> {
+  bool act;
+  const TI* th;
+  TI* r;
+  double rr = 0.0, react = 0.0;
+  __device__ OpResid(const View<double>& v, int s, const SampleState& S) : OpBase<double>(v, s) {
+    act = S.outer_active[v.sbase + s] != 0;
+    th = static_cast<const TI*>(v.ext0);
+    r = static_cast<TI*>(v.ext1);
+  }
+  __device__ bool live() const { return act; }
+  __device__ Coef<double> coef(const Invariants& U, int i, int j) const {
+    return coef_from_theta<double>(U, (double)th[ebase + (int64_t)j * V.g.nx + i]);
+  }
+  __device__ V2<double> in(int i, int j) { return ld2(V.a + at(i, j)); }
+  __device__ void out(int i, int j, V2<double> kd) {
+    const V2<double> res = mask(i, v2<double>(-kd.u, -kd.v));
+    const int64_t k = at(i, j);
+    r[k] = (TI)res.u;
+    r[k + 1] = (TI)res.v;
+    rr += res.u * res.u + res.v * res.v;
+    if (i == V.g.nx) react += kd.u;
+  }
+  __device__ void shift() {}
+  __device__ void finish(const SampleState& S, int s) {
+    const double t = warp_sum(rr), u = warp_sum(react);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&S.rr64[V.sbase + s], t);
+      atomicAdd(&S.react[V.sbase + s], u);
+    }
+  }
+};
+
+template <typename T, typename Op>
+__global__ void __launch_bounds__(kWarpsPerBlock * kWarp)
+    k_strip(const __grid_constant__ ViewList<T> L, SampleState S) {
+  const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  int vi, s, strip, chunk;
+  if (!find_tile(L, gw, vi, s, strip, chunk)) return;
+  const View<T>& V = L.v[vi];
+  Op op(V, s, S);
+  if (!op.live()) return;
+  strip_loop<T>(L.U, V, strip, chunk, op);
+  op.finish(S, s);
+}
+
+// ---------------------------------------------------------------- pointwise kernels
+
+template <typename T>
+__device__ __forceinline__ bool find_point(const ViewList<T>& L, int64_t gt, int& vi, int64_t& local) {
+  vi = 0;
+  while (vi < L.n && gt >= (int64_t)L.v[vi].work_begin + L.v[vi].nwork) ++vi;
+  if (vi >= L.n) return false;
+  local = gt - L.v[vi].work_begin;
+  return true;
+}
+
+// Full-weighting restriction b_c = P^T r1: views at the fine level, a = r1 (fine),
+// o0 = b (coarse). One thread per coarse node.
+template <typename T>
+__global__ void k_restrict(const __grid_constant__ ViewList<T> L, SampleState S) {
+  int vi;
+  int64_t loc;
+  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
+  const View<T>& V = L.v[vi];
+  const int nx = V.g.nx, ny = V.g.ny, nxc = nx / 2, nyc = ny / 2;
+  const int per = (nxc + 1) * (nyc + 1);
+  const int s = (int)(loc / per);
+  if (s >= V.nsamp) return;
+  if (!S.active[V.sbase + s]) return;
+  const int node = (int)(loc - (int64_t)s * per);
+  const int J = node / (nxc + 1), I = node - J * (nxc + 1);
+  const int64_t fb = (int64_t)s * 2 * (nx + 1) * (ny + 1);
+  T su = 0, sv = 0;
+#pragma unroll
+  for (int dj = -1; dj <= 1; ++dj) {
+    const int j = 2 * J + dj;
+    if (j < 0 || j > ny) continue;
+    const T wj = dj == 0 ? (T)1 : (T)0.5;
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) {
+      const int i = 2 * I + di;
+      if (i < 0 || i > nx) continue;
+      const T ww = wj * (di == 0 ? (T)1 : (T)0.5);
+      const V2<T> r = ld2(V.a + fb + 2 * ((int64_t)j * (nx + 1) + i));
+      su += ww * r.u;
+      sv += ww * r.v;
+    }
+  }
+  if (dir_u(I, nxc)) su = 0;
+  if (dir_v(I)) sv = 0;
+  st2(V.o0 + (int64_t)s * 2 * per + 2 * node, v2<T>(su, sv));
+}
+
+// Coarse element data: o0 = trig (coarse, 4 per element) from the fine level's
+// theta or trig (view geometry = fine level). One thread per coarse element.
+template <typename T>
+__global__ void k_trig_average(const __grid_constant__ ViewList<T> L) {
+  int vi;
+  int64_t loc;
+  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
+  const View<T>& V = L.v[vi];
+  const int nx = V.g.nx, ny = V.g.ny, nxc = nx / 2, nyc = ny / 2;
+  const int per = nxc * nyc;
+  const int s = (int)(loc / per);
+  if (s >= V.nsamp) return;
+  const int e = (int)(loc - (int64_t)s * per);
+  const int J = e / nxc, I = e - J * nxc;
+  T acc[4] = {0, 0, 0, 0};
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < 2; ++a) {
+      const int64_t fe = (int64_t)s * nx * ny + (int64_t)(2 * J + b) * nx + (2 * I + a);
+      T t4[4];
+      if (V.theta) {
+        trig4<T>(V.theta[fe], &t4[0], &t4[1], &t4[2], &t4[3]);
+      } else {
+        for (int c = 0; c < 4; ++c) t4[c] = V.trig[4 * fe + c];
+      }
+      for (int c = 0; c < 4; ++c) acc[c] += t4[c];
+    }
+  T* o = V.o0 + 4 * ((int64_t)s * per + e);
+  for (int c = 0; c < 4; ++c) o[c] = (T)0.25 * acc[c];
+}
+
+// o0 = w / diag(K) (zero on Dirichlet DOFs). One thread per node.
+template <typename T>
+__global__ void k_invdiag(const __grid_constant__ ViewList<T> L) {
+  int vi;
+  int64_t loc;
+  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
+  const View<T>& V = L.v[vi];
+  const int nx = V.g.nx, ny = V.g.ny;
+  const int per = (nx + 1) * (ny + 1);
+  const int s = (int)(loc / per);
+  if (s >= V.nsamp) return;
+  const int node = (int)(loc - (int64_t)s * per);
+  const int j = node / (nx + 1), i = node - j * (nx + 1);
+  const T rx = (T)V.g.rx, ry = (T)V.g.ry, w = (T)V.g.w;
+  const int64_t eb = (int64_t)s * nx * ny;
+  T du = 0, dv = 0;
+  // (element column, element row, xi*eta of this node in that element)
+  const int ei[4] = {i - 1, i, i - 1, i};
+  const int ej[4] = {j - 1, j - 1, j, j};
+  const T sg[4] = {(T)1, (T)-1, (T)-1, (T)1};
+  for (int k = 0; k < 4; ++k) {
+    if (ei[k] < 0 || ei[k] >= nx || ej[k] < 0 || ej[k] >= ny) continue;
+    Coef<T> C;
+    const int64_t e = eb + (int64_t)ej[k] * nx + ei[k];
+    if (V.theta) {
+      C = coef_from_theta<T>(L.U, V.theta[e]);
+    } else {
+      C = coef_from_trig<T>(L.U, V.trig[4 * e], V.trig[4 * e + 1], V.trig[4 * e + 2], V.trig[4 * e + 3]);
+    }
+    const V2<T> d = element_diag<T>(C, rx, ry, w, sg[k]);
+    du += d.u;
+    dv += d.v;
+  }
+  V2<T> r = v2<T>((T)kOmega / du, (T)kOmega / dv);
+  if (dir_u(i, nx)) r.u = 0;
+  if (dir_v(i)) r.v = 0;
+  st2(V.o0 + (int64_t)s * 2 * per + 2 * node, r);
+}
+
+// Dense inverse of the coarsest operator per sample (Dirichlet rows/columns set to
+// the identity), by in-place Gauss-Jordan in double. o0 = inverse [nsamp][n][n] (T).
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarsest_setup(const __grid_constant__ ViewList<T> L) {
+  __shared__ double A[kMaxCoarsestDofs][kMaxCoarsestDofs];
+  __shared__ double pivrow[kMaxCoarsestDofs];
+  __shared__ double pivcol[kMaxCoarsestDofs];
+  int vi = 0;
+  const int gb = blockIdx.x;
+  while (vi < L.n && gb >= L.v[vi].work_begin + L.v[vi].nwork) ++vi;
+  if (vi >= L.n) return;
+  const View<T>& V = L.v[vi];
+  const int s = gb - V.work_begin;
+  if (s >= V.nsamp) return;
+  const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
+  const int n = 2 * (nx + 1) * (ny + 1);
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k / n][k % n] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double rx = V.g.rx, ry = V.g.ry, w = V.g.w;
+    for (int ej = 0; ej < ny; ++ej)
+      for (int ei = 0; ei < nx; ++ei) {
+        const int64_t e = (int64_t)s * nx * ny + (int64_t)ej * nx + ei;
+        Coef<double> C;
+        if (V.theta) {
+          C = coef_from_theta<double>(L.U, (double)V.theta[e]);
+        } else {
+          C = coef_from_trig<double>(L.U, (double)V.trig[4 * e], (double)V.trig[4 * e + 1],
+                                     (double)V.trig[4 * e + 2], (double)V.trig[4 * e + 3]);
+        }
+        const int nodes[4] = {ej * nxp + ei, ej * nxp + ei + 1, (ej + 1) * nxp + ei + 1, (ej + 1) * nxp + ei};
+        for (int col = 0; col < 8; ++col) {
+          V2<double> in[4];
+          for (int a = 0; a < 4; ++a) in[a] = v2<double>(0.0, 0.0);
+          if (col & 1) in[col >> 1].v = 1.0; else in[col >> 1].u = 1.0;
+          V2<double> o[4];
+          element_apply<double>(C, rx, ry, w, in[0], in[1], in[2], in[3], o[0], o[1], o[2], o[3]);
+          const int gc = 2 * nodes[col >> 1] + (col & 1);
+          for (int a = 0; a < 4; ++a) {
+            A[2 * nodes[a]][gc] += o[a].u;
+            A[2 * nodes[a] + 1][gc] += o[a].v;
+          }
+        }
+      }
+    // Dirichlet DOFs
+    for (int j = 0; j <= ny; ++j) {
+      const int dofs[3] = {2 * (j * nxp), 2 * (j * nxp) + 1, 2 * (j * nxp + nx)};
+      for (int t = 0; t < 3; ++t) {
+        const int d = dofs[t];
+        for (int m = 0; m < n; ++m) {
+          A[d][m] = 0.0;
+          A[m][d] = 0.0;
+        }
+        A[d][d] = 1.0;
+      }
+    }
+  }
+  __syncthreads();
+  // in-place Gauss-Jordan: row k and column k are snapshotted before any update
+  for (int k = 0; k < n; ++k) {
+    const double piv = A[k][k];
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      pivrow[m] = (m == k ? 1.0 : A[k][m]) / piv;
+      pivcol[m] = A[m][k];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int r = idx / n, c = idx % n;
+      if (r == k) {
+        A[r][c] = pivrow[c];
+      } else {
+        A[r][c] = (c == k ? 0.0 : A[r][c]) - pivcol[r] * pivrow[c];
+      }
+    }
+    __syncthreads();
+  }
+  T* out = V.o0 + (int64_t)s * n * n;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) out[idx] = (T)A[idx / n][idx % n];
+}
+
+// x = A^-1 b at the coarsest level: a = b, ext0 = inverse (T), o0 = x. One warp per sample.
+template <typename T>
+__global__ void k_coarsest_solve(const __grid_constant__ ViewList<T> L, SampleState S) {
+  const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  int vi = 0;
+  while (vi < L.n && gw >= L.v[vi].work_begin + L.v[vi].nwork) ++vi;
+  if (vi >= L.n) return;
+  const View<T>& V = L.v[vi];
+  const int s = gw - V.work_begin;
+  if (s >= V.nsamp || !S.active[V.sbase + s]) return;
+  const int n = 2 * (V.g.nx + 1) * (V.g.ny + 1);
+  const T* Ai = static_cast<const T*>(V.ext0) + (int64_t)s * n * n;
+  const T* b = V.a + (int64_t)s * n;
+  const int lane = threadIdx.x & 31;
+  for (int r = lane; r < n; r += 32) {
+    T acc = 0;
+    for (int c = 0; c < n; ++c) acc += Ai[(int64_t)r * n + c] * b[c];
+    V.o0[(int64_t)s * n + r] = acc;
+  }
+}
+
+// d += x on refinement-active samples: o0 = d (double, via ext1), a = x (T).
+template <typename T>
+__global__ void k_update_d(const __grid_constant__ ViewList<T> L, SampleState S) {
+  int vi;
+  int64_t loc;
+  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
+  const View<T>& V = L.v[vi];
+  const int64_t per = 2 * (int64_t)(V.g.nx + 1) * (V.g.ny + 1);
+  const int s = (int)(loc / per);
+  if (s >= V.nsamp || !S.outer_active[V.sbase + s]) return;
+  double* d = static_cast<double*>(V.ext1);
+  d[loc] += (double)V.a[loc];
+}
+
+// Lifting of the Dirichlet data: d = 0 except u = -shortening on x = lx. o0 = d.
+__global__ void k_lift(const __grid_constant__ ViewList<double> L, double shortening) {
+  int vi;
+  int64_t loc;
+  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
+  const View<double>& V = L.v[vi];
+  const int nxp = V.g.nx + 1;
+  const int64_t per = 2 * (int64_t)nxp * (V.g.ny + 1);
+  const int s = (int)(loc / per);
+  if (s >= V.nsamp) return;
+  const int k = (int)(loc - (int64_t)s * per);
+  const int node = k >> 1, i = node % nxp;
+  V.o0[loc] = ((k & 1) == 0 && i == V.g.nx) ? -shortening : 0.0;
+}
+
+// Fibre-direction compressive stress at centroids in [x0, x1]: a = d (double),
+// ext0 = angles (TI). Max into qoi[2 s + 1] through the ordered bit pattern of
+// non-negative doubles. One thread per element.
+template <typename TI>
+__global__ void k_stress(const __grid_constant__ ViewList<double> L, SampleState S, double x0, double x1,
+                         double lx) {
+  int vi;
+  int64_t loc;
+  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
+  const View<double>& V = L.v[vi];
+  const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
+  const int per = nx * ny;
+  const int s = (int)(loc / per);
+  if (s >= V.nsamp) return;
+  const int e = (int)(loc - (int64_t)s * per);
+  const int j = e / nx, i = e - j * nx;
+  const double cx = (i + 0.5) * (lx / nx);
+  if (cx < x0 || cx > x1) return;
+  const double* d = V.a + (int64_t)s * 2 * nxp * (ny + 1);
+  const int n1 = j * nxp + i, n2 = n1 + 1, n3 = n1 + nxp + 1, n4 = n1 + nxp;
+  const double u1 = d[2 * n1], u2 = d[2 * n2], u3 = d[2 * n3], u4 = d[2 * n4];
+  const double v1 = d[2 * n1 + 1], v2_ = d[2 * n2 + 1], v3 = d[2 * n3 + 1], v4 = d[2 * n4 + 1];
+  const double au = (u2 - u1) + (u3 - u4), bu = (u4 - u1) + (u3 - u2);
+  const double av = (v2_ - v1) + (v3 - v4), bv = (v4 - v1) + (v3 - v2_);
+  const double rx = V.g.rx, ry = V.g.ry;
+  const double ex = rx * au, ey = ry * bv, exy = ry * bu + rx * av;
+  const double th = (double)static_cast<const TI*>(V.ext0)[(int64_t)s * per + e];
+  const Coef<double> C = coef_from_theta<double>(L.U, th);
+  const double sx = C.c11 * ex + C.c12 * ey + C.c16 * exy;
+  const double sy = C.c12 * ex + C.c22 * ey + C.c26 * exy;
+  const double sxy = C.c16 * ex + C.c26 * ey + C.c66 * exy;
+  double sn, cs;
+  sincos(th, &sn, &cs);
+  const double s11 = cs * cs * sx + sn * sn * sy + 2.0 * cs * sn * sxy;
+  const double val = fmax(0.0, -s11);
+  atomicMax(reinterpret_cast<unsigned long long*>(&S.qoi[2 * (V.sbase + s) + 1]),
+            (unsigned long long)__double_as_longlong(val));
+}
+
+// ---------------------------------------------------------------- per-sample scalars
+
+__global__ void k_after_post(SampleState S, int total, int iter) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total || !S.active[t]) return;
+  const double rr = S.red_rr[t];
+  if (rr <= S.tol2[t] * S.rr_ref[t]) {
+    S.active[t] = 0;
+    return;
+  }
+  const double rz = S.red_rz[t];
+  if (!(rz > 0.0) || !isfinite(rz)) {   // preconditioned residual lost positivity
+    S.active[t] = 0;
+    S.status[t] = MLMC_ERR_NOT_CONVERGED;
+    return;
+  }
+  const double old = S.rz_old[t];
+  S.beta[t] = old > 0.0 ? rz / old : 0.0;
+  S.rz_old[t] = rz;
+  S.red_pq[t] = 0.0;
+  S.iters[t] += 1;
+  atomicAdd(&S.count[iter], 1);
+}
+
+__global__ void k_after_p(SampleState S, int total) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total || !S.active[t]) return;
+  const double pq = S.red_pq[t];
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    S.active[t] = 0;
+    S.status[t] = MLMC_ERR_NOT_CONVERGED;
+    return;
+  }
+  S.alpha[t] = S.rz_old[t] / pq;
+  S.red_rr[t] = 0.0;
+  S.red_rz[t] = 0.0;
+}
+
+__global__ void k_outer_init(SampleState S, int total) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  S.rrf[t] = S.rr64[t];
+}
+
+// After a refinement residual: record the reaction, stop converged samples, and
+// set up the next inner solve for the rest.
+__global__ void k_outer_check(SampleState S, int total, double rtol, double floor_tol, int* outer_count) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total || !S.outer_active[t]) return;
+  const double rr = S.rr64[t];
+  S.qoi[2 * t] = -S.react[t];
+  S.rr64[t] = 0.0;
+  S.react[t] = 0.0;
+  const double target = rtol * rtol * S.rrf[t];
+  if (rr <= target || S.status[t] != 0) {
+    S.outer_active[t] = 0;
+    S.active[t] = 0;
+    return;
+  }
+  // solve the correction to what the outer target needs (with margin), no tighter
+  // than the inner arithmetic supports
+  double tol2 = 0.25 * target / rr;
+  if (tol2 < floor_tol * floor_tol) tol2 = floor_tol * floor_tol;
+  S.tol2[t] = tol2;
+  S.rr_ref[t] = rr;
+  S.active[t] = 1;
+  S.alpha[t] = 0.0;
+  S.beta[t] = 0.0;
+  S.rz_old[t] = 0.0;
+  S.red_rr[t] = 0.0;
+  S.red_rz[t] = 0.0;
+  S.red_pq[t] = 0.0;
+  atomicAdd(outer_count, 1);
+}
+
+template <typename T, typename Op>
+cudaError_t launch_strip_op(const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st) {
+  if (total_warps <= 0) return cudaSuccess;
+  const int blocks = (total_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  k_strip<T, Op><<<blocks, kWarpsPerBlock * kWarp, 0, st>>>(L, S);
+  return cudaGetLastError();
+}
+
+inline int blocks_for(int64_t threads, int bs) { return (int)((threads + bs - 1) / bs); }
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st) {
+  switch (op) {
+    case StripOp::Apply: return launch_strip_op<T, OpApply<T>>(L, S, total_warps, st);
+    case StripOp::PreTop: return launch_strip_op<T, OpPreTop<T>>(L, S, total_warps, st);
+    case StripOp::Pre: return launch_strip_op<T, OpPre<T>>(L, S, total_warps, st);
+    case StripOp::Post: return launch_strip_op<T, OpPost<T, false>>(L, S, total_warps, st);
+    case StripOp::PostTop: return launch_strip_op<T, OpPost<T, true>>(L, S, total_warps, st);
+    case StripOp::PcgP: return launch_strip_op<T, OpPcgP<T>>(L, S, total_warps, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename TI>
+cudaError_t launch_resid64(const ViewList<double>& L, SampleState S, int total_warps, cudaStream_t st) {
+  return launch_strip_op<double, OpResid<TI>>(L, S, total_warps, st);
+}
+
+template <typename T>
+cudaError_t launch_restrict(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st) {
+  if (total_threads <= 0) return cudaSuccess;
+  k_restrict<T><<<blocks_for(total_threads, 256), 256, 0, st>>>(L, S);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_trig_average(const ViewList<T>& L, int total_threads, cudaStream_t st) {
+  if (total_threads <= 0) return cudaSuccess;
+  k_trig_average<T><<<blocks_for(total_threads, 256), 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_invdiag(const ViewList<T>& L, int total_threads, cudaStream_t st) {
+  if (total_threads <= 0) return cudaSuccess;
+  k_invdiag<T><<<blocks_for(total_threads, 256), 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarsest_setup(const ViewList<T>& L, int total_blocks, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  k_coarsest_setup<T><<<total_blocks, 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarsest_solve(const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st) {
+  if (total_warps <= 0) return cudaSuccess;
+  k_coarsest_solve<T><<<blocks_for(total_warps, kWarpsPerBlock), kWarpsPerBlock * kWarp, 0, st>>>(L, S);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update_d(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st) {
+  if (total_threads <= 0) return cudaSuccess;
+  k_update_d<T><<<blocks_for(total_threads, 256), 256, 0, st>>>(L, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lift(const ViewList<double>& L, double shortening, int total_threads, cudaStream_t st) {
+  if (total_threads <= 0) return cudaSuccess;
+  k_lift<<<blocks_for(total_threads, 256), 256, 0, st>>>(L, shortening);
+  return cudaGetLastError();
+}
+
+template <typename TI>
+cudaError_t launch_stress(const ViewList<double>& L, SampleState S, double x0, double x1, double lx,
+                          int total_threads, cudaStream_t st) {
+  if (total_threads <= 0) return cudaSuccess;
+  k_stress<TI><<<blocks_for(total_threads, 256), 256, 0, st>>>(L, S, x0, x1, lx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_after_post(SampleState S, int total, int iter, cudaStream_t st) {
+  k_after_post<<<blocks_for(total, 256), 256, 0, st>>>(S, total, iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_after_p(SampleState S, int total, cudaStream_t st) {
+  k_after_p<<<blocks_for(total, 256), 256, 0, st>>>(S, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer_init(SampleState S, int total, cudaStream_t st) {
+  k_outer_init<<<blocks_for(total, 256), 256, 0, st>>>(S, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer_check(SampleState S, int total, double rtol, double floor_tol, int* outer_count,
+                               cudaStream_t st) {
+  k_outer_check<<<blocks_for(total, 256), 256, 0, st>>>(S, total, rtol, floor_tol, outer_count);
+  return cudaGetLastError();
+}
+
+#define MLMC_INST(T)                                                                                        \
+  template cudaError_t launch_strip<T>(StripOp, const ViewList<T>&, SampleState, int, cudaStream_t);       \
+  template cudaError_t launch_restrict<T>(const ViewList<T>&, SampleState, int, cudaStream_t);             \
+  template cudaError_t launch_trig_average<T>(const ViewList<T>&, int, cudaStream_t);                      \
+  template cudaError_t launch_invdiag<T>(const ViewList<T>&, int, cudaStream_t);                           \
+  template cudaError_t launch_coarsest_setup<T>(const ViewList<T>&, int, cudaStream_t);                    \
+  template cudaError_t launch_coarsest_solve<T>(const ViewList<T>&, SampleState, int, cudaStream_t);       \
+  template cudaError_t launch_update_d<T>(const ViewList<T>&, SampleState, int, cudaStream_t);             \
+  template cudaError_t launch_resid64<T>(const ViewList<double>&, SampleState, int, cudaStream_t);         \
+  template cudaError_t launch_stress<T>(const ViewList<double>&, SampleState, double, double, double, int, \
+                                        cudaStream_t);
+MLMC_INST(float)
+MLMC_INST(double)
+#undef MLMC_INST
+
+}  // namespace mlmc

@@ -1,0 +1,103 @@
+// Device views and launchers of the matrix-free Q1 operator family.
+#pragma once
+#include "common.cuh"
+
+namespace mlmc {
+
+constexpr int kMaxViews = 12;
+
+// One multigrid level of one solve group, as seen by a kernel. Pointer meaning
+// depends on the kernel (documented at each launcher). Vectors are
+// [nsamp][ny+1][nx+1][2]; element data [nsamp][ny][nx] (theta) or
+// [nsamp][ny][nx][4] (trig = cos 2t, sin 2t, cos 4t, sin 4t).
+template <typename T>
+struct View {
+  Geo g;
+  int nsamp;
+  int sbase;        // first sample of the group in the per-sample arrays
+  int work_begin;   // first warp (strip kernels) or thread (pointwise kernels) of this view
+  int nwork;
+  int tiles_x, tiles_y;
+  const T* theta;
+  const T* trig;
+  const T* a;
+  const T* b;
+  const T* c;
+  const T* winvd;
+  const T* xc;      // prolongation source (level below)
+  T* o0;
+  T* o1;
+  T* o2;
+  const void* ext0; // kernel-specific (e.g. angle array of another precision, dense inverse)
+  void* ext1;
+};
+
+template <typename T>
+struct ViewList {
+  int n;
+  Invariants U;
+  View<T> v[kMaxViews];
+};
+
+// Per-sample solver state (structure of arrays, indexed by sbase + s).
+struct SampleState {
+  double* alpha;
+  double* beta;
+  double* rz_old;
+  double* rr_ref;     // ||b||^2 of the current inner system
+  double* tol2;       // inner relative tolerance squared
+  double* red_rr;
+  double* red_rz;
+  double* red_pq;
+  double* rrf;        // ||f||^2 (residual of the lifting)
+  double* rr64;       // ||f - K d||^2 of the latest refinement residual
+  double* react;      // sum of (K d)_u on x = lx from the latest residual
+  double* qoi;        // [2] per sample
+  int* active;        // inner PCG running
+  int* outer_active;  // refinement running
+  int* iters;         // PCG iterations (all refinement steps)
+  int* status;        // 0 ok, MLMC_ERR_NOT_CONVERGED
+  int* count;         // [max_iter] active samples after each iteration
+};
+
+// Strip kernels (q = K p family); see fem.cu for the operand conventions.
+enum class StripOp { Apply, PreTop, Pre, Post, PostTop, PcgP };
+
+template <typename T>
+cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st);
+
+// Refinement residual r = -(K d) on free DOFs (double d, T output), ||r||^2 and reaction.
+template <typename TI>
+cudaError_t launch_resid64(const ViewList<double>& L, SampleState S, int total_warps, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_restrict(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_trig_average(const ViewList<T>& L, int total_threads, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_invdiag(const ViewList<T>& L, int total_threads, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_coarsest_setup(const ViewList<T>& L, int total_blocks, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_coarsest_solve(const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_update_d(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st);
+
+cudaError_t launch_lift(const ViewList<double>& L, double shortening, int total_threads, cudaStream_t st);
+
+template <typename TI>
+cudaError_t launch_stress(const ViewList<double>& L, SampleState S, double x0, double x1, double lx,
+                          int total_threads, cudaStream_t st);
+
+cudaError_t launch_after_post(SampleState S, int total, int iter, cudaStream_t st);
+cudaError_t launch_after_p(SampleState S, int total, cudaStream_t st);
+cudaError_t launch_outer_init(SampleState S, int total, cudaStream_t st);
+cudaError_t launch_outer_check(SampleState S, int total, double rtol, double floor_tol, int* outer_count,
+                               cudaStream_t st);
+
+}  // namespace mlmc

@@ -1,0 +1,592 @@
+// Batched geometric-multigrid-preconditioned CG with double-precision iterative
+// refinement, for many independent samples on several meshes at once.
+//
+// Outer loop (double): d starts as the lifting of the Dirichlet data; r = f - K d
+// is evaluated in double (f = 0 in the interior, the load comes from the lifting);
+// when ||r|| <= rtol ||f|| the sample is done, otherwise the correction system
+// K e = r is solved in the inner precision T and d += e.
+// Inner loop (T): preconditioned CG, preconditioner one symmetric V(1,1)-cycle:
+// damped Jacobi smoothing (w = 1/2), full weighting restriction = P^T, bilinear
+// prolongation P, coarse operators rediscretised from the child-averaged rotated
+// stiffness, and an exact dense solve on the coarsest mesh.
+//
+// All groups (one mesh size each, any number of samples) advance in lock step:
+// multigrid levels are aligned by their distance from each group's coarsest mesh,
+// so one launch per level serves every group that has that level. Every sample
+// keeps its own CG scalars; converged samples drop out of all kernels.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cmath>
+#include <cstring>
+
+#include "context.h"
+
+namespace mlmc {
+
+namespace {
+
+template <typename T>
+struct GroupBuf {
+  const SolveGroup<T>* grp;
+  int sbase;
+  int nl;                     // multigrid levels, 0 = top
+  std::vector<Geo> geo;
+  // top level
+  T *x, *r[2], *p[2], *z, *q;
+  double* d;
+  // every level k: winvd[k], r1[k]; coarse levels k >= 1: b[k], xl[k], trig[k]
+  std::vector<T*> winvd, r1, b, xl, trig;
+  T* ainv;
+};
+
+template <typename T>
+View<T> base_view(const GroupBuf<T>& g, int k) {
+  View<T> v;
+  std::memset(&v, 0, sizeof(v));
+  v.g = g.geo[k];
+  v.nsamp = (int)g.grp->nsamp;
+  v.sbase = g.sbase;
+  v.tiles_x = strips_of(v.g.nx);
+  v.tiles_y = chunks_of(v.g.ny);
+  if (k == 0) {
+    v.theta = g.grp->theta;
+  } else {
+    v.trig = g.trig[k];
+  }
+  return v;
+}
+
+// Assigns work offsets for strip kernels (warps) and returns the total.
+template <typename T>
+int finalize_warps(ViewList<T>& L) {
+  int acc = 0;
+  for (int i = 0; i < L.n; ++i) {
+    L.v[i].work_begin = acc;
+    L.v[i].nwork = L.v[i].nsamp * L.v[i].tiles_x * L.v[i].tiles_y;
+    acc += L.v[i].nwork;
+  }
+  return acc;
+}
+
+template <typename T>
+int finalize_points(ViewList<T>& L, const std::vector<int64_t>& per_sample) {
+  int64_t acc = 0;
+  for (int i = 0; i < L.n; ++i) {
+    L.v[i].work_begin = (int)acc;
+    L.v[i].nwork = (int)(L.v[i].nsamp * per_sample[i]);
+    acc += L.v[i].nwork;
+  }
+  return (int)acc;
+}
+
+struct SizeAlloc {
+  Sizer s;
+  template <typename U>
+  void vec(U*&, size_t n) { s.add<U>(n); }
+};
+
+struct CarveAlloc {
+  Arena* a;
+  template <typename U>
+  void vec(U*& p, size_t n) { p = a->carve<U>(n); }
+};
+
+template <typename T>
+ViewList<T> empty_list(const Context& ctx) {
+  ViewList<T> L;
+  std::memset(&L, 0, sizeof(L));
+  L.n = 0;
+  L.U = ctx.U;
+  return L;
+}
+
+}  // namespace
+
+template <typename T>
+mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
+  cudaStream_t st = ctx.stream;
+  const bool inner_double = sizeof(T) == sizeof(double);
+  if (groups.empty()) return MLMC_OK;
+  if ((int)groups.size() > kMaxViews) return ctx.fail(MLMC_ERR_INVALID_ARG, "too many mesh groups in one solve");
+
+  // ---- hierarchy and workspace
+  std::vector<GroupBuf<T>> G(groups.size());
+  int total = 0;
+  int amax = 0;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    GroupBuf<T>& g = G[gi];
+    g.grp = &groups[gi];
+    g.sbase = total;
+    total += (int)groups[gi].nsamp;
+    const LevelLayout m = ctx.mesh(groups[gi].mesh_level);
+    int nx = m.nx, ny = m.ny;
+    g.geo.push_back(ctx.geo(nx, ny));
+    // halve as far as the grid allows; the coarsest mesh is solved densely
+    while (nx % 2 == 0 && ny % 2 == 0 && ny >= 2) {
+      nx /= 2;
+      ny /= 2;
+      g.geo.push_back(ctx.geo(nx, ny));
+    }
+    g.nl = (int)g.geo.size();
+    if (g.nl < 2) return ctx.fail(MLMC_ERR_INVALID_ARG, "mesh too small for the multigrid hierarchy");
+    const Geo& c = g.geo.back();
+    if (2 * (c.nx + 1) * (c.ny + 1) > kMaxCoarsestDofs)
+      return ctx.fail(MLMC_ERR_INVALID_ARG, "coarsest mesh too large (mesh must halve down to <= 64 DOFs)");
+    amax = std::max(amax, g.nl - 1);
+  }
+  if (total == 0) return MLMC_OK;
+  const int max_iter = ctx.cfg.max_iter > 0 ? ctx.cfg.max_iter : 200;
+  const int max_outer = ctx.cfg.max_outer > 0 ? ctx.cfg.max_outer : 8;
+
+  auto plan = [&](auto& alloc) {
+    for (auto& g : G) {
+      const int64_t ns = g.grp->nsamp;
+      auto nv = [&](int k) { return (size_t)(ns * 2 * (int64_t)(g.geo[k].nx + 1) * (g.geo[k].ny + 1)); };
+      alloc.template vec<T>(g.x, nv(0));
+      alloc.template vec<T>(g.r[0], nv(0));
+      alloc.template vec<T>(g.r[1], nv(0));
+      alloc.template vec<T>(g.p[0], nv(0));
+      alloc.template vec<T>(g.p[1], nv(0));
+      alloc.template vec<T>(g.z, nv(0));
+      alloc.template vec<T>(g.q, nv(0));
+      alloc.template vec<double>(g.d, nv(0));
+      g.winvd.assign(g.nl, nullptr);
+      g.r1.assign(g.nl, nullptr);
+      g.b.assign(g.nl, nullptr);
+      g.xl.assign(g.nl, nullptr);
+      g.trig.assign(g.nl, nullptr);
+      for (int k = 0; k < g.nl; ++k) {
+        alloc.template vec<T>(g.winvd[k], nv(k));
+        alloc.template vec<T>(g.r1[k], nv(k));
+        if (k >= 1) {
+          alloc.template vec<T>(g.b[k], nv(k));
+          alloc.template vec<T>(g.xl[k], nv(k));
+          alloc.template vec<T>(g.trig[k], (size_t)(ns * 4 * (int64_t)g.geo[k].nx * g.geo[k].ny));
+        }
+      }
+      const int nc = 2 * (g.geo.back().nx + 1) * (g.geo.back().ny + 1);
+      alloc.template vec<T>(g.ainv, (size_t)(ns * nc * nc));
+    }
+  };
+  SampleState S;
+  int* outer_count = nullptr;
+  auto plan_state = [&](auto& alloc) {
+    alloc.template vec<double>(S.alpha, total);
+    alloc.template vec<double>(S.beta, total);
+    alloc.template vec<double>(S.rz_old, total);
+    alloc.template vec<double>(S.rr_ref, total);
+    alloc.template vec<double>(S.tol2, total);
+    alloc.template vec<double>(S.red_rr, total);
+    alloc.template vec<double>(S.red_rz, total);
+    alloc.template vec<double>(S.red_pq, total);
+    alloc.template vec<double>(S.rrf, total);
+    alloc.template vec<double>(S.rr64, total);
+    alloc.template vec<double>(S.react, total);
+    alloc.template vec<double>(S.qoi, 2 * (size_t)total);
+    alloc.template vec<int>(S.active, total);
+    alloc.template vec<int>(S.outer_active, total);
+    alloc.template vec<int>(S.iters, total);
+    alloc.template vec<int>(S.status, total);
+    alloc.template vec<int>(S.count, (size_t)max_iter + 1);
+    alloc.template vec<int>(outer_count, 1);
+  };
+  SizeAlloc sz;
+  plan(sz);
+  plan_state(sz);
+  cudaError_t e = ctx.solve_arena.reserve(sz.s.used + 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ctx.fail(MLMC_ERR_OOM, "solver workspace allocation failed");
+  }
+  ctx.solve_arena.reset();
+  CarveAlloc ca{&ctx.solve_arena};
+  plan(ca);
+  plan_state(ca);
+  {
+    char* state_begin = reinterpret_cast<char*>(S.alpha);
+    char* state_end = reinterpret_cast<char*>(outer_count + 1);
+    if ((e = cudaMemsetAsync(state_begin, 0, (size_t)(state_end - state_begin), st)) != cudaSuccess)
+      return ctx.cuda_fail(e, "memset");
+  }
+
+  // ---- per-level element data, diagonal and coarsest inverse
+  for (int k = 0; k + 1 < 64; ++k) {
+    ViewList<T> L = empty_list<T>(ctx);
+    std::vector<int64_t> per;
+    for (auto& g : G) {
+      if (k + 1 >= g.nl) continue;
+      View<T> v = base_view(g, k);
+      v.o0 = g.trig[k + 1];
+      L.v[L.n++] = v;
+      per.push_back((int64_t)(g.geo[k].nx / 2) * (g.geo[k].ny / 2));
+    }
+    if (L.n == 0) break;
+    const int tt = finalize_points(L, per);
+    if ((e = launch_trig_average<T>(L, tt, st)) != cudaSuccess) return ctx.cuda_fail(e, "trig_average");
+  }
+  for (int k = 0; k < 64; ++k) {
+    ViewList<T> L = empty_list<T>(ctx);
+    std::vector<int64_t> per;
+    for (auto& g : G) {
+      if (k >= g.nl) continue;
+      View<T> v = base_view(g, k);
+      v.o0 = g.winvd[k];
+      L.v[L.n++] = v;
+      per.push_back((int64_t)(g.geo[k].nx + 1) * (g.geo[k].ny + 1));
+    }
+    if (L.n == 0) break;
+    const int tt = finalize_points(L, per);
+    if ((e = launch_invdiag<T>(L, tt, st)) != cudaSuccess) return ctx.cuda_fail(e, "invdiag");
+  }
+  {
+    ViewList<T> L = empty_list<T>(ctx);
+    int acc = 0;
+    for (auto& g : G) {
+      View<T> v = base_view(g, g.nl - 1);
+      v.o0 = g.ainv;
+      v.work_begin = acc;
+      v.nwork = v.nsamp;
+      acc += v.nwork;
+      L.v[L.n++] = v;
+    }
+    if ((e = launch_coarsest_setup<T>(L, acc, st)) != cudaSuccess) return ctx.cuda_fail(e, "coarsest_setup");
+  }
+
+  // ---- view lists reused every iteration
+  // top-level views (PreTop / PostTop / PcgP and the refinement residual)
+  auto top_list = [&](StripOp op, int parity) {
+    ViewList<T> L = empty_list<T>(ctx);
+    for (auto& g : G) {
+      View<T> v = base_view(g, 0);
+      switch (op) {
+        case StripOp::PreTop:
+          v.a = g.r[parity];
+          v.b = g.q;
+          v.c = g.p[parity];
+          v.winvd = g.winvd[0];
+          v.o0 = g.x;
+          v.o1 = g.r[parity ^ 1];
+          v.o2 = g.r1[0];
+          break;
+        case StripOp::PostTop:
+          v.a = g.r[parity ^ 1];
+          v.xc = g.xl[1];
+          v.winvd = g.winvd[0];
+          v.o0 = g.z;
+          break;
+        case StripOp::PcgP:
+          v.a = g.z;
+          v.b = g.p[parity];
+          v.o0 = g.p[parity ^ 1];
+          v.o1 = g.q;
+          break;
+        default:
+          break;
+      }
+      L.v[L.n++] = v;
+    }
+    return L;
+  };
+
+  auto run_vcycle_and_pcg = [&](int parity, int iter) -> mlmc_status {
+    cudaError_t err;
+    // down sweep
+    for (int a = amax; a >= 1; --a) {
+      ViewList<T> Ltop = empty_list<T>(ctx), Lmid = empty_list<T>(ctx), Lres = empty_list<T>(ctx);
+      std::vector<int64_t> per_res;
+      for (auto& g : G) {
+        const int k = (g.nl - 1) - a;
+        if (k < 0) continue;
+        if (k == 0) {
+          View<T> v = base_view(g, 0);
+          v.a = g.r[parity];
+          v.b = g.q;
+          v.c = g.p[parity];
+          v.winvd = g.winvd[0];
+          v.o0 = g.x;
+          v.o1 = g.r[parity ^ 1];
+          v.o2 = g.r1[0];
+          Ltop.v[Ltop.n++] = v;
+        } else {
+          View<T> v = base_view(g, k);
+          v.a = g.b[k];
+          v.winvd = g.winvd[k];
+          v.o2 = g.r1[k];
+          Lmid.v[Lmid.n++] = v;
+        }
+        View<T> r = base_view(g, k);
+        r.a = g.r1[k];
+        r.o0 = g.b[k + 1];
+        Lres.v[Lres.n++] = r;
+        per_res.push_back((int64_t)(g.geo[k].nx / 2 + 1) * (g.geo[k].ny / 2 + 1));
+      }
+      if (Ltop.n) {
+        const int tw = finalize_warps(Ltop);
+        if ((err = launch_strip<T>(StripOp::PreTop, Ltop, S, tw, st)) != cudaSuccess) return ctx.cuda_fail(err, "pre_top");
+      }
+      if (Lmid.n) {
+        const int tw = finalize_warps(Lmid);
+        if ((err = launch_strip<T>(StripOp::Pre, Lmid, S, tw, st)) != cudaSuccess) return ctx.cuda_fail(err, "pre");
+      }
+      if (Lres.n) {
+        const int tt = finalize_points(Lres, per_res);
+        if ((err = launch_restrict<T>(Lres, S, tt, st)) != cudaSuccess) return ctx.cuda_fail(err, "restrict");
+      }
+    }
+    // coarsest
+    {
+      ViewList<T> L = empty_list<T>(ctx);
+      int acc = 0;
+      for (auto& g : G) {
+        const int k = g.nl - 1;
+        View<T> v = base_view(g, k);
+        v.a = g.b[k];
+        v.o0 = g.xl[k];
+        v.ext0 = g.ainv;
+        v.work_begin = acc;
+        v.nwork = v.nsamp;
+        acc += v.nwork;
+        L.v[L.n++] = v;
+      }
+      if ((err = launch_coarsest_solve<T>(L, S, acc, st)) != cudaSuccess) return ctx.cuda_fail(err, "coarsest");
+    }
+    // up sweep
+    for (int a = 1; a <= amax; ++a) {
+      ViewList<T> Ltop = empty_list<T>(ctx), Lmid = empty_list<T>(ctx);
+      for (auto& g : G) {
+        const int k = (g.nl - 1) - a;
+        if (k < 0) continue;
+        View<T> v = base_view(g, k);
+        v.xc = g.xl[k + 1];
+        v.winvd = g.winvd[k];
+        if (k == 0) {
+          v.a = g.r[parity ^ 1];
+          v.o0 = g.z;
+          Ltop.v[Ltop.n++] = v;
+        } else {
+          v.a = g.b[k];
+          v.o0 = g.xl[k];
+          Lmid.v[Lmid.n++] = v;
+        }
+      }
+      if (Lmid.n) {
+        const int tw = finalize_warps(Lmid);
+        if ((err = launch_strip<T>(StripOp::Post, Lmid, S, tw, st)) != cudaSuccess) return ctx.cuda_fail(err, "post");
+      }
+      if (Ltop.n) {
+        const int tw = finalize_warps(Ltop);
+        if ((err = launch_strip<T>(StripOp::PostTop, Ltop, S, tw, st)) != cudaSuccess) return ctx.cuda_fail(err, "post_top");
+      }
+    }
+    if ((err = launch_after_post(S, total, iter, st)) != cudaSuccess) return ctx.cuda_fail(err, "after_post");
+    {
+      ViewList<T> L = top_list(StripOp::PcgP, parity);
+      const int tw = finalize_warps(L);
+      if ((err = launch_strip<T>(StripOp::PcgP, L, S, tw, st)) != cudaSuccess) return ctx.cuda_fail(err, "pcg_p");
+    }
+    if ((err = launch_after_p(S, total, st)) != cudaSuccess) return ctx.cuda_fail(err, "after_p");
+    return MLMC_OK;
+  };
+
+  // double-precision views for lifting, residual and stress
+  auto d_list = [&]() {
+    ViewList<double> L;
+    std::memset(&L, 0, sizeof(L));
+    L.U = ctx.U;
+    for (auto& g : G) {
+      View<double> v;
+      std::memset(&v, 0, sizeof(v));
+      v.g = g.geo[0];
+      v.nsamp = (int)g.grp->nsamp;
+      v.sbase = g.sbase;
+      v.tiles_x = strips_of(v.g.nx);
+      v.tiles_y = chunks_of(v.g.ny);
+      v.a = g.d;
+      v.o0 = g.d;
+      v.ext0 = g.grp->theta;
+      v.ext1 = g.r[0];
+      L.v[L.n++] = v;
+    }
+    return L;
+  };
+  auto resid = [&]() -> mlmc_status {
+    ViewList<double> L = d_list();
+    int acc = 0;
+    for (int i = 0; i < L.n; ++i) {
+      L.v[i].work_begin = acc;
+      L.v[i].nwork = L.v[i].nsamp * L.v[i].tiles_x * L.v[i].tiles_y;
+      acc += L.v[i].nwork;
+    }
+    cudaError_t err = launch_resid64<T>(L, S, acc, st);
+    return err == cudaSuccess ? MLMC_OK : ctx.cuda_fail(err, "resid64");
+  };
+
+  // lifting, initial residual ||f||
+  {
+    ViewList<double> L = d_list();
+    int64_t acc = 0;
+    for (int i = 0; i < L.n; ++i) {
+      L.v[i].work_begin = (int)acc;
+      L.v[i].nwork = (int)(L.v[i].nsamp * 2 * (int64_t)(L.v[i].g.nx + 1) * (L.v[i].g.ny + 1));
+      acc += L.v[i].nwork;
+    }
+    if ((e = launch_lift(L, ctx.cfg.shortening, (int)acc, st)) != cudaSuccess) return ctx.cuda_fail(e, "lift");
+  }
+  {
+    std::vector<int> ones(total, 1);
+    if ((e = cudaMemcpyAsync(S.outer_active, ones.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return ctx.cuda_fail(e, "init");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return ctx.cuda_fail(e, "init");
+  }
+  mlmc_status rs = resid();
+  if (rs != MLMC_OK) return rs;
+  if ((e = launch_outer_init(S, total, st)) != cudaSuccess) return ctx.cuda_fail(e, "outer_init");
+
+  const double floor_tol = inner_double ? 1e-14 : ctx.floor_tol32;
+  int outer = 0, max_it_seen = 0;
+  for (;; ++outer) {
+    if ((e = cudaMemsetAsync(outer_count, 0, sizeof(int), st)) != cudaSuccess) return ctx.cuda_fail(e, "memset");
+    if ((e = launch_outer_check(S, total, ctx.cfg.rtol, floor_tol, outer_count, st)) != cudaSuccess)
+      return ctx.cuda_fail(e, "outer_check");
+    int h_outer = 0;
+    if ((e = cudaMemcpyAsync(&h_outer, outer_count, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return ctx.cuda_fail(e, "outer_count");
+    if (std::getenv("MLMC_TRACE")) {   // diagnostic: refinement progress of the first samples
+      const int m = std::min(total, 4);
+      std::vector<double> rrf(m), tol2(m), rref(m);
+      std::vector<int> its(m), stt(m), oa(m);
+      cudaMemcpy(rrf.data(), S.rrf, sizeof(double) * m, cudaMemcpyDeviceToHost);
+      cudaMemcpy(tol2.data(), S.tol2, sizeof(double) * m, cudaMemcpyDeviceToHost);
+      cudaMemcpy(rref.data(), S.rr_ref, sizeof(double) * m, cudaMemcpyDeviceToHost);
+      cudaMemcpy(its.data(), S.iters, sizeof(int) * m, cudaMemcpyDeviceToHost);
+      cudaMemcpy(stt.data(), S.status, sizeof(int) * m, cudaMemcpyDeviceToHost);
+      cudaMemcpy(oa.data(), S.outer_active, sizeof(int) * m, cudaMemcpyDeviceToHost);
+      for (int t = 0; t < m; ++t)
+        std::fprintf(stderr, "[mlmc] outer %d sample %d active %d status %d iters %d |r|/|f| %.3e inner_tol %.3e\n",
+                     outer, t, oa[t], stt[t], its[t], std::sqrt(rref[t] / std::max(rrf[t], 1e-300)), std::sqrt(tol2[t]));
+    }
+    if (h_outer == 0 || outer >= max_outer) break;
+    // fresh inner solve: x = 0, p = 0, q = 0
+    for (auto& g : G) {
+      const size_t bytes = sizeof(T) * (size_t)g.grp->nsamp * 2 * (g.geo[0].nx + 1) * (g.geo[0].ny + 1);
+      if ((e = cudaMemsetAsync(g.x, 0, bytes, st)) != cudaSuccess ||
+          (e = cudaMemsetAsync(g.p[0], 0, bytes, st)) != cudaSuccess ||
+          (e = cudaMemsetAsync(g.q, 0, bytes, st)) != cudaSuccess)
+        return ctx.cuda_fail(e, "memset");
+    }
+    if ((e = cudaMemsetAsync(S.count, 0, sizeof(int) * (max_iter + 1), st)) != cudaSuccess) return ctx.cuda_fail(e, "memset");
+    int it = 0;
+    while (it < max_iter) {
+      const int batch = std::min(ctx.check_every, max_iter - it);
+      for (int b = 0; b < batch; ++b, ++it) {
+        mlmc_status s2 = run_vcycle_and_pcg(it & 1, it);
+        if (s2 != MLMC_OK) return s2;
+      }
+      int h_count = 0;
+      if ((e = cudaMemcpyAsync(&h_count, S.count + (it - 1), sizeof(int), cudaMemcpyDeviceToHost, st)) !=
+              cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return ctx.cuda_fail(e, "pcg_count");
+      if (h_count == 0) break;
+    }
+    max_it_seen = std::max(max_it_seen, it);
+    // d += x, new residual
+    {
+      ViewList<T> L = empty_list<T>(ctx);
+      std::vector<int64_t> per;
+      for (auto& g : G) {
+        View<T> v = base_view(g, 0);
+        v.a = g.x;
+        v.ext1 = g.d;
+        L.v[L.n++] = v;
+        per.push_back(2 * (int64_t)(g.geo[0].nx + 1) * (g.geo[0].ny + 1));
+      }
+      const int tt = finalize_points(L, per);
+      if ((e = launch_update_d<T>(L, S, tt, st)) != cudaSuccess) return ctx.cuda_fail(e, "update_d");
+    }
+    rs = resid();
+    if (rs != MLMC_OK) return rs;
+  }
+  ctx.last_outer = outer;
+  ctx.last_iters = max_it_seen;
+
+  // not converged: still refinement-active
+  {
+    std::vector<int> oa(total), stv(total);
+    if ((e = cudaMemcpyAsync(oa.data(), S.outer_active, sizeof(int) * total, cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(stv.data(), S.status, sizeof(int) * total, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return ctx.cuda_fail(e, "status");
+    bool changed = false;
+    for (int t = 0; t < total; ++t)
+      if (oa[t] && stv[t] == 0) {
+        stv[t] = MLMC_ERR_NOT_CONVERGED;
+        changed = true;
+      }
+    if (changed &&
+        (e = cudaMemcpyAsync(S.status, stv.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return ctx.cuda_fail(e, "status");
+    if (changed && (e = cudaStreamSynchronize(st)) != cudaSuccess) return ctx.cuda_fail(e, "status");
+  }
+  // stress quantity from the final d
+  {
+    ViewList<double> L = d_list();
+    int64_t acc = 0;
+    for (int i = 0; i < L.n; ++i) {
+      L.v[i].work_begin = (int)acc;
+      L.v[i].nwork = (int)(L.v[i].nsamp * (int64_t)L.v[i].g.nx * L.v[i].g.ny);
+      acc += L.v[i].nwork;
+    }
+    if ((e = launch_stress<T>(L, S, ctx.cfg.omega_x0, ctx.cfg.omega_x1, ctx.cfg.lx, (int)acc, st)) != cudaSuccess)
+      return ctx.cuda_fail(e, "stress");
+  }
+  for (auto& g : G) {
+    const SolveGroup<T>& sg = *g.grp;
+    if ((e = cudaMemcpyAsync(sg.q, S.qoi + 2 * (size_t)g.sbase, sizeof(double) * 2 * sg.nsamp,
+                             cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return ctx.cuda_fail(e, "copy q");
+    if (sg.status &&
+        (e = cudaMemcpyAsync(sg.status, S.status + g.sbase, sizeof(int) * sg.nsamp, cudaMemcpyDeviceToDevice, st)) !=
+            cudaSuccess)
+      return ctx.cuda_fail(e, "copy status");
+    if (sg.iters &&
+        (e = cudaMemcpyAsync(sg.iters, S.iters + g.sbase, sizeof(int) * sg.nsamp, cudaMemcpyDeviceToDevice, st)) !=
+            cudaSuccess)
+      return ctx.cuda_fail(e, "copy iters");
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return ctx.cuda_fail(e, "solve");
+  return MLMC_OK;
+}
+
+template <typename T>
+mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* theta, const T* p, T* q) {
+  ViewList<T> L = empty_list<T>(ctx);
+  const LevelLayout m = ctx.mesh(mesh_level);
+  View<T> v;
+  std::memset(&v, 0, sizeof(v));
+  v.g = ctx.geo(m.nx, m.ny);
+  v.nsamp = (int)n;
+  v.tiles_x = strips_of(m.nx);
+  v.tiles_y = chunks_of(m.ny);
+  v.theta = theta;
+  v.a = p;
+  v.o0 = q;
+  L.v[L.n++] = v;
+  const int tw = finalize_warps(L);
+  SampleState S;
+  std::memset(&S, 0, sizeof(S));
+  cudaError_t e = launch_strip<T>(StripOp::Apply, L, S, tw, ctx.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx.stream);
+  return e == cudaSuccess ? MLMC_OK : ctx.cuda_fail(e, "apply");
+}
+
+template mlmc_status solve_groups<float>(Context&, std::vector<SolveGroup<float>>&);
+template mlmc_status solve_groups<double>(Context&, std::vector<SolveGroup<double>>&);
+template mlmc_status apply_operator<float>(Context&, int, int64_t, const float*, const float*, float*);
+template mlmc_status apply_operator<double>(Context&, int, int64_t, const double*, const double*, double*);
+
+}  // namespace mlmc
