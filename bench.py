@@ -1,0 +1,358 @@
+"""Benchmark of the MLMC level-pair hot path on the 5-level mixed-precision strip.
+
+One step = every level pair of the workload (N_l = 8192/2048/512/128/32 samples on
+64x16 ... 1024x256 Q1 meshes, 100 KL terms): KL coefficients, KL synthesis on both
+meshes, rotated-stiffness multigrid-PCG solves with FP64 refinement to 1e-8,
+quantities of interest, level differences and moments, through mlmc_sample_levels.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank runs the whole workload on
+its own GPU with disjoint sample ids (samples are independent: weak scaling, no
+collective on the data path); value is the total over ranks divided by the slowest
+rank's time. --impl reference times the CPU oracle on a bounded sample of the same
+workload instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from workloads import STRIP_MIXED_5LEVEL  # noqa: E402
+
+METRIC = "level-pair FE solves/s (5-level strip, QoI rtol 1e-8)"
+UNIT = "level-pairs/s"
+
+# Algorithmic bytes per mesh node of each timed operation in the FP32 inner solve
+# (2 DOF per node, float2 vectors 8 B, angle 4 B or averaged trig 16 B per element,
+# one element per node, coarse correction 2 B per fine node).
+BYTES_PER_NODE = {
+    "pcg_update_presmooth": 8 * 5 + 4 + 8 * 3,    # r q x p w/D + theta ; x r' r1
+    "presmooth": 8 * 2 + 16 + 8,                   # b w/D + trig ; r1
+    "postsmooth": 8 * 2 + 16 + 2 + 8,              # b w/D + trig + x_c ; x
+    "postsmooth_top": 8 * 2 + 4 + 2 + 8,           # b w/D + theta + x_c ; z
+    "search_direction": 8 * 2 + 4 + 8 * 2,         # z p + theta ; p' q
+    "refinement_residual": 16 + 4 + 8,             # d (double) + theta ; r (float)
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-fraction", type=float, default=1.0 / 32.0,
+                    help="fraction of each level's samples the CPU oracle times")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fem.cu", "common.cuh", "fem.cuh"):
+        with open(os.path.join(ROOT, "paper_1907_10271_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(op):
+    """DRAM bytes per node of `op` from the committed ncu summary, if it matches this source."""
+    p = os.path.join(ROOT, "profiles", "traffic_per_node.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != kernel_source_hash():
+        return None
+    v = vals.get(op)
+    return float(v) if v else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return None
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+
+def _oracle_worker(args):
+    cfg, level, ids = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import mlmc as om
+    basis = om.Basis(cfg)
+    basis(level)
+    if level > 0:
+        basis(level - 1)
+    times = []
+    for i in ids:
+        t = time.perf_counter()
+        om.level_pair(cfg, level, [int(i)], basis)
+        times.append(time.perf_counter() - t)
+    return times
+
+
+def oracle_throughput(cfg, fraction, cores):
+    """Level-pairs/s of the CPU oracle on the workload mix, from a bounded sample:
+    per-sample times t_l measured on fraction * N_l samples of each level (at least
+    one), then sum_l N_l / (sum_l N_l t_l / cores)."""
+    import multiprocessing as mp
+    counts = cfg["n_per_level"]
+    sample = [max(1, int(round(n * fraction))) for n in counts]
+    jobs = []
+    for l, s in enumerate(sample):
+        ids = np.arange(10_000_000, 10_000_000 + s)
+        for chunk in np.array_split(ids, min(s, cores)):
+            if chunk.size:
+                jobs.append((cfg, l, chunk))
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(cores, len(jobs))) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t0
+    per_level = [[] for _ in counts]
+    for (c, l, _), t in zip(jobs, res):
+        per_level[l] += t
+    t_l = [float(np.mean(x)) for x in per_level]
+    seconds = sum(n * t for n, t in zip(counts, t_l)) / cores
+    return sum(counts) / seconds, dict(sample=sample, t_l=t_l, wall=wall, cores=cores)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(a):
+    import torch
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1907_10271_gb300 import binding as B
+
+    cfg = STRIP_MIXED_5LEVEL
+    counts = list(cfg["n_per_level"])
+    levels = list(range(cfg["levels"]))
+    total = sum(counts)
+    stream = torch.cuda.current_stream()
+    ctx = B.mlmc_create(B.config_from_workload(cfg), stream.cuda_stream)
+    qf = torch.empty(2 * total, dtype=torch.float64, device="cuda")
+    qc = torch.empty_like(qf)
+    st = torch.empty(total, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # > L2 (126 MB)
+    id_stride = 1 << 40
+
+    def first_ids(step):
+        # disjoint ids per rank and per step
+        return [rank * id_stride + step * n for n in counts]
+
+    def step(k, q1, q2, s):
+        B.mlmc_sample_levels(ctx, levels, first_ids(k), counts, q1, q2, s)
+
+    for k in range(a.warmup):
+        step(k, qf, qc, st)
+    torch.cuda.synchronize()
+    bad = int((st != 0).sum())
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    B.mlmc_profile_enable(ctx, True)
+    times = []
+    with ClockSampler(local) as clk:
+        barrier()
+        for k in range(a.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(a.warmup + k, qf, qc, st)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            bad += int((st != 0).sum())
+        barrier()
+    launches = B.mlmc_launch_count(ctx)
+    prof = {name: B.mlmc_profile_get(ctx, i) for i, name in enumerate(B.PROFILE_OPS)}
+    B.mlmc_profile_enable(ctx, False)
+    t_step = sum(times) / len(times)
+
+    # ---- end to end: outputs to pinned host memory, copies inside the timed region
+    hq1 = torch.empty(2 * total, dtype=torch.float64).pin_memory()
+    hq2 = torch.empty_like(hq1).pin_memory()
+    hs = torch.empty(total, dtype=torch.int32).pin_memory()
+    e2e_times = []
+    barrier()
+    for k in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(a.warmup + a.steps + k, hq1, hq2, hs)
+        e2e_times.append((time.perf_counter() - t0) * 1e3)
+        bad += int((hs != 0).sum())
+    barrier()
+    t_e2e = sum(e2e_times) / len(e2e_times)
+
+    worst = t_step
+    worst_e2e = t_e2e
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_step, t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        worst, worst_e2e = float(tt[0]), float(tt[1])
+    value = world * total / (worst / 1e3)
+    e2e_value = world * total / (worst_e2e / 1e3)
+
+    # ---- roofline of the dominant timed kernel
+    peak, peak_kind = peaks()
+    timed = {k: v for k, v in prof.items() if k in BYTES_PER_NODE and v[1] > 0}
+    dom = max(timed, key=lambda k: timed[k][0])
+    ms, nl, nodes = timed[dom]
+    achieved = nodes * BYTES_PER_NODE[dom] / (ms / 1e3) / 1e9
+    tr = recorded_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} hbm_gbs",
+                "traffic": (round(tr * nodes / nl) if tr else None),
+                "algorithmic_bytes_per_launch": round(nodes * BYTES_PER_NODE[dom] / nl),
+                "avg_launch_us": round(ms / nl * 1e3, 2), "launches": nl,
+                "share_of_step": round(ms / (t_step * a.steps), 4)}
+    kernels = {k: {"ms_per_step": round(v[0] / a.steps, 3), "launches_per_step": v[1] // a.steps,
+                   "GB/s": (round(v[2] * BYTES_PER_NODE[k] / (v[0] / 1e3) / 1e9, 1)
+                            if k in BYTES_PER_NODE and v[0] > 0 else None)}
+               for k, v in prof.items() if v[1] > 0}
+    clocks = clk.summary()
+    B.mlmc_destroy(ctx)
+
+    out = None
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": round(worst, 3), "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32 (FP64 refinement, dots, QoI, moments)",
+               "data": "synthetic: Philox KL coefficients per (seed, level, id)",
+               "config": {"workload": cfg["name"], "meshes": "64x16..1024x256 Q1, 2 DOF/node",
+                          "samples_per_level": counts, "kl_terms": cfg["kl_terms"], "rtol": cfg["rtol"],
+                          "parallelism": f"dp{world} (disjoint sample ids)",
+                          "l2": "flushed (256 MB write) between timed steps"},
+               "level_pairs_per_step": total, "samples_failed": bad,
+               "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": total * (2 * 16 + 4),
+                       "note": "mlmc_sample_levels with pinned host outputs; per-sample inputs are "
+                               "(seed, level, id) counters, fields are synthesised on the device"},
+               "roofline": roofline, "kernels": kernels, "gpu_launches": launches // a.steps,
+               "gpu_launches_total": launches, "clocks": clocks}
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def main():
+    a = parse()
+    rank, _, world = dist_env()
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        cores = os.cpu_count() or 1
+        vals = []
+        info = None
+        for k in range(a.warmup + a.steps):
+            v, info = oracle_throughput(STRIP_MIXED_5LEVEL, a.cpu_fraction, cores)
+            if k >= a.warmup:
+                vals.append(v)
+        value = sum(vals) / len(vals)
+        sample = ("per level %s samples of %s (ids from 1e7), per-sample times %s s extrapolated to the "
+                  "workload mix over %d cores" % (info["sample"], list(STRIP_MIXED_5LEVEL["n_per_level"]),
+                                                 [round(t, 4) for t in info["t_l"]], cores))
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+                          "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
+                          "ms_per_step": round(sum(STRIP_MIXED_5LEVEL["n_per_level"]) / value * 1e3, 1),
+                          "config": {"workload": STRIP_MIXED_5LEVEL["name"]}, "dtype": "f64",
+                          "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": round(value, 3),
+                                           "unit": UNIT},
+                          "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+    out = run_gpu(a)
+    if rank == 0 and out is not None:
+        if world == 1 and not a.no_cpu_baseline:
+            cores = os.cpu_count() or 1
+            v, info = oracle_throughput(STRIP_MIXED_5LEVEL, a.cpu_fraction, cores)
+            out["cpu_baseline"] = {"value": round(v, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": "per level %s samples (1/32 of each level), per-sample times %s s, "
+                                             "extrapolated to the workload mix" %
+                                             (info["sample"], [round(t, 4) for t in info["t_l"]]),
+                                   "wall_s": round(info["wall"], 1)}
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

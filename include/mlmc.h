@@ -123,6 +123,16 @@ const char* mlmc_last_error(const mlmc_ctx* ctx);
 mlmc_status mlmc_sample_level(mlmc_ctx* ctx, int32_t level, uint64_t first_id, int64_t n,
                               double* q_fine, double* q_coarse, int32_t* status);
 
+/* Several level pairs in one call: request k asks for counts[k] samples of level
+   levels[k] with ids first_ids[k] ..; levels, first_ids and counts are HOST arrays
+   of n_req entries, each level at most once per call is solved in one lock-stepped
+   batch with the others (all meshes of all requests advance together). Outputs are
+   concatenated in request order (q_fine, q_coarse: [sum counts][2]; status:
+   [sum counts], nullable) and every request is folded into its level's moments,
+   exactly as n_req calls of mlmc_sample_level would (Sec. 2.2, Eq. MLMC_defn). */
+mlmc_status mlmc_sample_levels(mlmc_ctx* ctx, int32_t n_req, const int32_t* levels, const uint64_t* first_ids,
+                               const int64_t* counts, double* q_fine, double* q_coarse, int32_t* status);
+
 /* n independent solves of arbitrary (level, mesh_level, sample_id) items,
    grouped by mesh and run together. Writes q[n * 2] and status[n] (nullable).
    Does not touch the level moments. */
@@ -172,6 +182,34 @@ mlmc_status mlmc_apply(mlmc_ctx* ctx, int32_t mesh_level, int64_t n, const doubl
    status[n] (nullable), iterations[n] (nullable, total PCG iterations). */
 mlmc_status mlmc_solve_theta(mlmc_ctx* ctx, int32_t mesh_level, int64_t n, const double* theta,
                              double* q, int32_t* status, int32_t* iterations);
+
+/* ---- measurement ---- */
+
+/* Operation ids of the kernel timer. */
+enum {
+  MLMC_OP_PCG_UPDATE_PRESMOOTH = 0, /* PCG update + finest-level smoothing + residual */
+  MLMC_OP_PRESMOOTH = 1,            /* coarse-level smoothing + residual */
+  MLMC_OP_POSTSMOOTH = 2,           /* coarse-level prolongation + smoothing */
+  MLMC_OP_POSTSMOOTH_TOP = 3,       /* finest-level prolongation + smoothing + r.z */
+  MLMC_OP_SEARCH_DIRECTION = 4,     /* p = z + beta p, q = K p, p.q */
+  MLMC_OP_REFINEMENT_RESIDUAL = 5,  /* double-precision r = f - K d, reaction */
+  MLMC_OP_RESTRICT = 6,
+  MLMC_OP_COARSEST = 7,
+  MLMC_OP_OTHER = 8,
+  MLMC_OP_COUNT = 9
+};
+
+/* on != 0: from now on record CUDA events around every launch of the operations
+   above (on the context's stream) and count the mesh nodes each one processes
+   (active samples only); resets all counters. on == 0 stops recording. */
+mlmc_status mlmc_profile_enable(mlmc_ctx* ctx, int32_t on);
+
+/* Totals since the last mlmc_profile_enable: summed kernel time in ms, number of
+   launches and nodes processed of operation `op` (each output nullable). */
+mlmc_status mlmc_profile_get(mlmc_ctx* ctx, int32_t op, double* ms_total, int64_t* launches, uint64_t* nodes);
+
+/* Kernel launches the library issued since the last mlmc_profile_enable. */
+mlmc_status mlmc_launch_count(mlmc_ctx* ctx, int64_t* launches);
 
 #ifdef __cplusplus
 }

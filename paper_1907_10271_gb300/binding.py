@@ -82,6 +82,10 @@ def lib():
             "mlmc_theta": (I32, [P, I32, I32, U64, I64, P]),
             "mlmc_apply": (I32, [P, I32, I64, P, P, P]),
             "mlmc_solve_theta": (I32, [P, I32, I64, P, P, P, P]),
+            "mlmc_sample_levels": (I32, [P, I32, P, P, P, P, P, P]),
+            "mlmc_profile_enable": (I32, [P, I32]),
+            "mlmc_profile_get": (I32, [P, I32, P, P, P]),
+            "mlmc_launch_count": (I32, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -219,3 +223,37 @@ def mlmc_apply(ctx, mesh_level, n, theta, p, q):
 def mlmc_solve_theta(ctx, mesh_level, n, theta, q, status=None, iterations=None):
     return _check(ctx, lib().mlmc_solve_theta(ctx, mesh_level, n, _ptr(theta, np.float64), _ptr(q, np.float64),
                                                _ptr(status, np.int32), _ptr(iterations, np.int32)))
+
+
+def mlmc_sample_levels(ctx, levels, first_ids, counts, q_fine=None, q_coarse=None, status=None):
+    """levels, first_ids, counts: sequences (host); outputs concatenated in request order."""
+    n = len(levels)
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    fi = np.ascontiguousarray(first_ids, dtype=np.uint64)
+    ct = np.ascontiguousarray(counts, dtype=np.int64)
+    return _check(ctx, lib().mlmc_sample_levels(ctx, n, _ptr(lv, np.int32), _ptr(fi, np.uint64), _ptr(ct, np.int64),
+                                                 _ptr(q_fine, np.float64), _ptr(q_coarse, np.float64),
+                                                 _ptr(status, np.int32)))
+
+
+PROFILE_OPS = ["pcg_update_presmooth", "presmooth", "postsmooth", "postsmooth_top", "search_direction",
+               "refinement_residual", "restrict", "coarsest", "other"]
+
+
+def mlmc_profile_enable(ctx, on=True):
+    return _check(ctx, lib().mlmc_profile_enable(ctx, 1 if on else 0))
+
+
+def mlmc_profile_get(ctx, op):
+    """(total ms, launches, nodes) of operation index `op` (see PROFILE_OPS)."""
+    ms = ctypes.c_double()
+    la = ctypes.c_int64()
+    nd = ctypes.c_uint64()
+    _check(ctx, lib().mlmc_profile_get(ctx, op, ctypes.byref(ms), ctypes.byref(la), ctypes.byref(nd)))
+    return ms.value, la.value, nd.value
+
+
+def mlmc_launch_count(ctx):
+    n = ctypes.c_int64()
+    _check(ctx, lib().mlmc_launch_count(ctx, ctypes.byref(n)))
+    return n.value

@@ -5,6 +5,7 @@
 #include <map>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "context.h"
@@ -66,6 +67,11 @@ cudaError_t convert(const float* a, double* b, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+__global__ void k_combine_status(const int* a, const int* b, int* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] != 0 ? a[i] : (b ? b[i] : 0);
+}
+
 mlmc::Invariants invariants(const mlmc_config& c, bool& ok) {
   // plane-strain fibre-frame stiffness: (1,2) block of the inverse 3D normal compliance
   double S[3][3] = {{1.0 / c.E11, -c.nu12 / c.E11, -c.nu13 / c.E11},
@@ -111,135 +117,169 @@ std::string validate(const mlmc_config& c) {
   return "";
 }
 
-template <typename T>
-struct Scratch {
-  T* p = nullptr;
+struct LevelReq {
+  int level;
+  uint64_t first_id;
+  int64_t n;
+  int64_t out_off;   // first sample of this request in the caller's output arrays
 };
 
-// Per-call device scratch from the batch arena.
-struct BatchBuffers {
-  double* xi = nullptr;
-  float* xi32 = nullptr;
-  int* fail = nullptr;
-  void* theta_f = nullptr;
-  void* theta_c = nullptr;
-  double* qf = nullptr;
-  double* qc = nullptr;
-  int* st_f = nullptr;
-  int* st_c = nullptr;
-  int* it_f = nullptr;
-  int* it_c = nullptr;
-  int* status = nullptr;
+struct ReqBuffers {
+  double* xi;
+  float* xi32;
+  void* theta_f;
+  void* theta_c;
+  double* qf;
+  double* qc;
+  int* st_f;
+  int* st_c;
+  int* it_f;
+  int* it_c;
+  int* status;
 };
 
-int64_t auto_batch(const Context& c, int level) {
-  if (c.cfg.max_batch > 0) return c.cfg.max_batch;
+// Device bytes the solver needs per sample of `level` (both meshes), with margin.
+double bytes_per_sample(const Context& c, int level) {
   const double tb = c.mixed() ? 4.0 : 8.0;
   auto dofs = [&](int l) { return l < 0 ? 0.0 : 2.0 * ((c.cfg.nx0 << l) + 1.0) * ((c.cfg.ny0 << l) + 1.0); };
-  const double per = (dofs(level) + dofs(level - 1)) * (14.0 * tb + 16.0) * 1.4 + 64.0;
-  const double budget = 8.0e9;
-  return std::max<int64_t>(1, (int64_t)(budget / per));
+  return (dofs(level) + dofs(level - 1)) * (14.0 * tb + 16.0) * 1.4 + 64.0 * c.cfg.kl_terms + 256.0;
 }
 
-// xi, theta on fine (and coarse) meshes, both solves, per-sample outputs in device buffers.
+// One lock-stepped solve of every level pair in `reqs`: xi per level, theta on the
+// fine and coarse meshes from the same xi, all fine and coarse groups solved together,
+// then the per-level moments and the outputs.
 template <typename T>
-mlmc_status run_pairs(mlmc_ctx* h, int level, uint64_t first_id, int64_t nb, const int* levels_dev,
-                      const uint64_t* ids_dev, int fine_mesh, int coarse_mesh, BatchBuffers& B) {
+mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, double* q_fine, double* q_coarse,
+                               int32_t* status) {
   Context& c = h->c;
   cudaStream_t st = c.stream;
   const int nkl = c.cfg.kl_terms;
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(B.fail, 0, sizeof(int), st)) != cudaSuccess) return c.cuda_fail(e, "memset");
-  if ((e = mlmc::launch_kl_coefficients(c.cfg.seed, level, first_id, levels_dev, ids_dev, nb, nkl, B.xi,
-                                        c.mixed() ? B.xi32 : nullptr, B.fail, st)) != cudaSuccess)
-    return c.cuda_fail(e, "kl_coefficients");
-  const T* xiT = c.mixed() ? (const T*)(const void*)B.xi32 : (const T*)(const void*)B.xi;
-  auto basis = [&](int m) -> const T* {
-    return c.mixed() ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
+  int64_t total = 0;
+  mlmc::Sizer sz;
+  for (const auto& r : reqs) {
+    total += r.n;
+  }
+  std::vector<ReqBuffers> B(reqs.size());
+  auto plan = [&](auto& alloc) {
+    for (size_t k = 0; k < reqs.size(); ++k) {
+      const LevelReq& r = reqs[k];
+      const int64_t nel_f = c.mesh(r.level).n_el(), nel_c = r.level > 0 ? c.mesh(r.level - 1).n_el() : 1;
+      alloc(B[k].xi, r.n * nkl);
+      alloc(B[k].xi32, r.n * nkl);
+      alloc(reinterpret_cast<T*&>(B[k].theta_f), r.n * nel_f);
+      alloc(reinterpret_cast<T*&>(B[k].theta_c), r.n * nel_c);
+      alloc(B[k].qf, 2 * r.n);
+      alloc(B[k].qc, 2 * r.n);
+      alloc(B[k].st_f, r.n);
+      alloc(B[k].st_c, r.n);
+      alloc(B[k].it_f, r.n);
+      alloc(B[k].it_c, r.n);
+      alloc(B[k].status, r.n);
+    }
   };
-  const mlmc::LevelLayout mf = c.mesh(fine_mesh);
-  if ((e = mlmc::launch_kl_synthesis<T>(xiT, basis(fine_mesh), nb, (int)mf.n_el(), nkl, (T*)B.theta_f, st)) !=
-      cudaSuccess)
-    return c.cuda_fail(e, "kl_synthesis");
-  std::vector<mlmc::SolveGroup<T>> groups;
-  groups.push_back({fine_mesh, nb, (const T*)B.theta_f, B.qf, B.st_f, B.it_f});
-  if (coarse_mesh >= 0) {
-    const mlmc::LevelLayout mc = c.mesh(coarse_mesh);
-    if ((e = mlmc::launch_kl_synthesis<T>(xiT, basis(coarse_mesh), nb, (int)mc.n_el(), nkl, (T*)B.theta_c,
-                                          st)) != cudaSuccess)
-      return c.cuda_fail(e, "kl_synthesis");
-    groups.push_back({coarse_mesh, nb, (const T*)B.theta_c, B.qc, B.st_c, B.it_c});
-  }
-  int fail = 0;
-  if ((e = cudaMemcpyAsync(&fail, B.fail, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(st)) != cudaSuccess)
-    return c.cuda_fail(e, "kl_coefficients");
-  if (fail) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
-  return mlmc::solve_groups<T>(c, groups);
-}
-
-__global__ void k_combine_status(const int* a, const int* b, int* out, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = a[i] != 0 ? a[i] : (b ? b[i] : 0);
-}
-
-template <typename T>
-mlmc_status sample_level_t(mlmc_ctx* h, int32_t level, uint64_t first_id, int64_t n, double* q_fine,
-                           double* q_coarse, int32_t* status) {
-  Context& c = h->c;
-  cudaStream_t st = c.stream;
-  const int64_t batch = std::min<int64_t>(n, auto_batch(c, level));
-  const mlmc::LevelLayout mf = c.mesh(level);
-  const int64_t nel_f = mf.n_el(), nel_c = level > 0 ? c.mesh(level - 1).n_el() : 0;
-  size_t bytes = 0;
+  int* fail = nullptr;
   {
-    mlmc::Sizer s;
-    s.add<double>(batch * c.cfg.kl_terms);
-    s.add<float>(batch * c.cfg.kl_terms);
-    s.add<int>(1);
-    s.add<T>(batch * nel_f);
-    s.add<T>(batch * std::max<int64_t>(nel_c, 1));
-    s.add<double>(2 * batch);
-    s.add<double>(2 * batch);
-    for (int k = 0; k < 5; ++k) s.add<int>(batch);
-    bytes = s.used + 256;
+    auto count = [&](auto*& p, int64_t n) { sz.add<std::remove_reference_t<decltype(*p)>>((size_t)n); };
+    plan(count);
+    sz.add<int>(1);
   }
-  cudaError_t e = c.batch_arena.reserve(bytes);
+  cudaError_t e = c.batch_arena.reserve(sz.used + 512);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return c.fail(MLMC_ERR_OOM, "batch buffers");
   }
   c.batch_arena.reset();
-  BatchBuffers B;
-  B.xi = c.batch_arena.carve<double>(batch * c.cfg.kl_terms);
-  B.xi32 = c.batch_arena.carve<float>(batch * c.cfg.kl_terms);
-  B.fail = c.batch_arena.carve<int>(1);
-  B.theta_f = c.batch_arena.carve<T>(batch * nel_f);
-  B.theta_c = c.batch_arena.carve<T>(batch * std::max<int64_t>(nel_c, 1));
-  B.qf = c.batch_arena.carve<double>(2 * batch);
-  B.qc = c.batch_arena.carve<double>(2 * batch);
-  B.st_f = c.batch_arena.carve<int>(batch);
-  B.st_c = c.batch_arena.carve<int>(batch);
-  B.it_f = c.batch_arena.carve<int>(batch);
-  B.it_c = c.batch_arena.carve<int>(batch);
-  B.status = c.batch_arena.carve<int>(batch);
-  for (int64_t off = 0; off < n; off += batch) {
-    const int64_t nb = std::min(batch, n - off);
-    mlmc_status s = run_pairs<T>(h, level, first_id + (uint64_t)off, nb, nullptr, nullptr, level,
-                                 level > 0 ? level - 1 : -1, B);
-    if (s != MLMC_OK) return s;
-    k_combine_status<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(B.st_f, level > 0 ? B.st_c : nullptr, B.status, nb);
+  {
+    auto carve = [&](auto*& p, int64_t n) { p = c.batch_arena.carve<std::remove_reference_t<decltype(*p)>>((size_t)n); };
+    plan(carve);
+    fail = c.batch_arena.carve<int>(1);
+  }
+  if ((e = cudaMemsetAsync(fail, 0, sizeof(int), st)) != cudaSuccess) return c.cuda_fail(e, "memset");
+  std::vector<mlmc::SolveGroup<T>> groups;
+  for (size_t k = 0; k < reqs.size(); ++k) {
+    const LevelReq& r = reqs[k];
+    c.timer.begin(mlmc::kProfOther, st);
+    e = mlmc::launch_kl_coefficients(c.cfg.seed, r.level, r.first_id, nullptr, nullptr, r.n, nkl, B[k].xi,
+                                     c.mixed() ? B[k].xi32 : nullptr, fail, st);
+    c.timer.end(st);
+    if (e != cudaSuccess) return c.cuda_fail(e, "kl_coefficients");
+    const T* xiT = c.mixed() ? (const T*)(const void*)B[k].xi32 : (const T*)(const void*)B[k].xi;
+    for (int side = 0; side < (r.level > 0 ? 2 : 1); ++side) {
+      const int m = r.level - side;
+      const T* basis = c.mixed() ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
+      T* th = (T*)(side == 0 ? B[k].theta_f : B[k].theta_c);
+      c.timer.begin(mlmc::kProfOther, st);
+      e = mlmc::launch_kl_synthesis<T>(xiT, basis, r.n, (int)c.mesh(m).n_el(), nkl, th, st);
+      c.timer.end(st);
+      if (e != cudaSuccess) return c.cuda_fail(e, "kl_synthesis");
+      if (side == 0) groups.push_back({m, r.n, th, B[k].qf, B[k].st_f, B[k].it_f});
+      else groups.push_back({m, r.n, th, B[k].qc, B[k].st_c, B[k].it_c});
+    }
+  }
+  int h_fail = 0;
+  if ((e = cudaMemcpyAsync(&h_fail, fail, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return c.cuda_fail(e, "kl_coefficients");
+  if (h_fail) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
+  mlmc_status s = mlmc::solve_groups<T>(c, groups);
+  if (s != MLMC_OK) return s;
+  for (size_t k = 0; k < reqs.size(); ++k) {
+    const LevelReq& r = reqs[k];
+    const int64_t nb = r.n;
+    c.timer.begin(mlmc::kProfOther, st);
+    k_combine_status<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(B[k].st_f, r.level > 0 ? B[k].st_c : nullptr,
+                                                                  B[k].status, nb);
+    c.timer.end(st);
     if ((e = cudaGetLastError()) != cudaSuccess) return c.cuda_fail(e, "status");
-    if (level == 0 && (e = cudaMemsetAsync(B.qc, 0, sizeof(double) * 2 * nb, st)) != cudaSuccess)
+    if (r.level == 0 && (e = cudaMemsetAsync(B[k].qc, 0, sizeof(double) * 2 * nb, st)) != cudaSuccess)
       return c.cuda_fail(e, "memset");
-    if ((e = mlmc::launch_moments(B.qf, level > 0 ? B.qc : nullptr, B.status, nb, h->acc_dev + level, st)) !=
-        cudaSuccess)
-      return c.cuda_fail(e, "moments");
-    if ((e = from_device(q_fine ? q_fine + 2 * off : nullptr, B.qf, 2 * nb, st)) != cudaSuccess ||
-        (e = from_device(q_coarse ? q_coarse + 2 * off : nullptr, B.qc, 2 * nb, st)) != cudaSuccess ||
-        (e = from_device(status ? status + off : nullptr, B.status, nb, st)) != cudaSuccess)
+    c.timer.begin(mlmc::kProfOther, st);
+    e = mlmc::launch_moments(B[k].qf, r.level > 0 ? B[k].qc : nullptr, B[k].status, nb, h->acc_dev + r.level, st);
+    c.timer.end(st);
+    if (e != cudaSuccess) return c.cuda_fail(e, "moments");
+    if ((e = from_device(q_fine ? q_fine + 2 * r.out_off : nullptr, B[k].qf, 2 * nb, st)) != cudaSuccess ||
+        (e = from_device(q_coarse ? q_coarse + 2 * r.out_off : nullptr, B[k].qc, 2 * nb, st)) != cudaSuccess ||
+        (e = from_device(status ? status + r.out_off : nullptr, B[k].status, nb, st)) != cudaSuccess)
       return c.cuda_fail(e, "copy out");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return c.cuda_fail(e, "sample_level");
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return c.cuda_fail(e, "sample_levels");
+  return MLMC_OK;
+}
+
+// Splits the requests into solves that fit the memory budget and mesh-group limit.
+mlmc_status sample_levels_impl(mlmc_ctx* h, std::vector<LevelReq> reqs, double* q_fine, double* q_coarse,
+                               int32_t* status) {
+  Context& c = h->c;
+  const double budget = c.cfg.max_batch > 0 ? 1e300 : 8.0e9;
+  // cut requests larger than the budget (or than max_batch) into pieces
+  std::vector<LevelReq> pieces;
+  for (const auto& r : reqs) {
+    int64_t cap = c.cfg.max_batch > 0 ? c.cfg.max_batch
+                                      : std::max<int64_t>(1, (int64_t)(budget / bytes_per_sample(c, r.level)));
+    for (int64_t off = 0; off < r.n; off += cap)
+      pieces.push_back(LevelReq{r.level, r.first_id + (uint64_t)off, std::min(cap, r.n - off), r.out_off + off});
+  }
+  size_t i = 0;
+  while (i < pieces.size()) {
+    std::vector<LevelReq> solve;
+    double bytes = 0;
+    int groups = 0;
+    while (i < pieces.size()) {
+      const LevelReq& r = pieces[i];
+      const double b = bytes_per_sample(c, r.level) * r.n;
+      const int g = r.level > 0 ? 2 : 1;
+      if (!solve.empty() && (bytes + b > budget || groups + g > mlmc::kMaxViews)) break;
+      bool dup = false;   // one request per level per solve keeps the moment order simple
+      for (const auto& x : solve) dup = dup || x.level == r.level;
+      if (dup) break;
+      solve.push_back(r);
+      bytes += b;
+      groups += g;
+      ++i;
+    }
+    mlmc_status s = c.mixed() ? run_level_requests<float>(h, solve, q_fine, q_coarse, status)
+                              : run_level_requests<double>(h, solve, q_fine, q_coarse, status);
+    if (s != MLMC_OK) return s;
   }
   return MLMC_OK;
 }
@@ -360,6 +400,7 @@ void mlmc_destroy(mlmc_ctx* h) {
   for (auto p : h->c.basis32) cudaFree(p);
   h->c.solve_arena.release();
   h->c.batch_arena.release();
+  h->c.timer.release();
   if (h->acc_dev) cudaFree(h->acc_dev);
   delete h;
 }
@@ -373,10 +414,79 @@ mlmc_status mlmc_sample_level(mlmc_ctx* h, int32_t level, uint64_t first_id, int
   if (level < 0 || level >= c.cfg.levels) return c.fail(MLMC_ERR_INVALID_ARG, "level out of range");
   if (n < 0) return c.fail(MLMC_ERR_INVALID_ARG, "negative sample count");
   if (n == 0) return MLMC_OK;
-  mlmc_status s = c.mixed() ? sample_level_t<float>(h, level, first_id, n, q_fine, q_coarse, status)
-                            : sample_level_t<double>(h, level, first_id, n, q_fine, q_coarse, status);
+  mlmc_status s = sample_levels_impl(h, {LevelReq{level, first_id, n, 0}}, q_fine, q_coarse, status);
   if (s != MLMC_OK) return s;
   return sync_stats(h);
+}
+
+mlmc_status mlmc_sample_levels(mlmc_ctx* h, int32_t n_req, const int32_t* levels, const uint64_t* first_ids,
+                               const int64_t* counts, double* q_fine, double* q_coarse, int32_t* status) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (n_req < 0 || (n_req > 0 && (!levels || !first_ids || !counts)))
+    return c.fail(MLMC_ERR_INVALID_ARG, "bad request arrays");
+  std::vector<LevelReq> reqs;
+  int64_t off = 0;
+  for (int k = 0; k < n_req; ++k) {
+    if (levels[k] < 0 || levels[k] >= c.cfg.levels) return c.fail(MLMC_ERR_INVALID_ARG, "level out of range");
+    if (counts[k] < 0) return c.fail(MLMC_ERR_INVALID_ARG, "negative sample count");
+    if (counts[k] > 0) reqs.push_back(LevelReq{levels[k], first_ids[k], counts[k], off});
+    off += counts[k];
+  }
+  if (reqs.empty()) return MLMC_OK;
+  mlmc_status s = sample_levels_impl(h, reqs, q_fine, q_coarse, status);
+  if (s != MLMC_OK) return s;
+  return sync_stats(h);
+}
+
+mlmc_status mlmc_profile_enable(mlmc_ctx* h, int32_t on) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return c.cuda_fail(e, "profile");
+  if (!c.timer.units_dev) {
+    if ((e = cudaMalloc(&c.timer.units_dev, sizeof(unsigned long long) * mlmc::kProfOps)) != cudaSuccess)
+      return c.cuda_fail(e, "profile");
+  }
+  if ((e = cudaMemset(c.timer.units_dev, 0, sizeof(unsigned long long) * mlmc::kProfOps)) != cudaSuccess)
+    return c.cuda_fail(e, "profile");
+  c.timer.reset();
+  c.timer.on = on != 0;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_profile_get(mlmc_ctx* h, int32_t op, double* ms_total, int64_t* launches, uint64_t* nodes) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (op < 0 || op >= mlmc::kProfOps) return c.fail(MLMC_ERR_INVALID_ARG, "unknown operation id");
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return c.cuda_fail(e, "profile");
+  double ms = 0.0;
+  int64_t cnt = 0;
+  for (const auto& r : c.timer.recs) {
+    if (r.op != op) continue;
+    float t = 0.f;
+    if ((e = cudaEventElapsedTime(&t, c.timer.pool[r.ev], c.timer.pool[r.ev + 1])) != cudaSuccess)
+      return c.cuda_fail(e, "profile");
+    ms += t;
+    ++cnt;
+  }
+  if (ms_total) *ms_total = ms;
+  if (launches) *launches = cnt;
+  if (nodes) {
+    unsigned long long u[mlmc::kProfOps] = {0};
+    if (c.timer.units_dev &&
+        (e = cudaMemcpy(u, c.timer.units_dev, sizeof(u), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return c.cuda_fail(e, "profile");
+    *nodes = u[op];
+  }
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_launch_count(mlmc_ctx* h, int64_t* launches) {
+  if (!h || !launches) return MLMC_ERR_INVALID_ARG;
+  *launches = h->c.timer.launches;
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_level_stats_get(mlmc_ctx* h, int32_t level, mlmc_level_stats* out) {

@@ -45,6 +45,57 @@ struct Sizer {
   }
 };
 
+// Optional per-operation kernel timing (CUDA events on the library stream) and a
+// count of every kernel the library launches.
+struct KernelTimer {
+  bool on = false;
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Rec {
+    int op;
+    size_t ev;
+  };
+  std::vector<Rec> recs;
+  unsigned long long* units_dev = nullptr;   // [kProfOps]
+  int pending_op = -1;
+  size_t pending_ev = 0;
+
+  cudaEvent_t next() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(int op, cudaStream_t st) {
+    ++launches;
+    if (!on || op == kProfOther) return;
+    pending_op = op;
+    pending_ev = used;
+    cudaEventRecord(next(), st);
+  }
+  void end(cudaStream_t st) {
+    if (pending_op < 0) return;
+    cudaEventRecord(next(), st);
+    recs.push_back(Rec{pending_op, pending_ev});
+    pending_op = -1;
+  }
+  void reset() {
+    used = 0;
+    recs.clear();
+    launches = 0;
+    pending_op = -1;
+  }
+  void release() {
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+    if (units_dev) cudaFree(units_dev);
+    units_dev = nullptr;
+  }
+};
+
 struct LevelLayout {
   int nx, ny;
   int64_t n_el() const { return (int64_t)nx * ny; }
@@ -64,6 +115,7 @@ struct Context {
   std::vector<mlmc_level_stats> stats;
   std::vector<double> comp;       // Kahan compensation of sum_qf / sum_qc per level [l][4]
   std::string err;
+  KernelTimer timer;
   double floor_tol32 = 3e-6;      // tightest inner relative tolerance of the FP32 solve
   int check_every = 4;            // PCG iterations between host convergence checks
   int last_outer = 0;             // refinement steps of the last solve (diagnostic)

@@ -366,6 +366,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * kWarp)
   const View<T>& V = L.v[vi];
   Op op(V, s, S);
   if (!op.live()) return;
+  if (S.units && (threadIdx.x & 31) == 0) {
+    const int c0 = max(strip * kStripCols, 0), c1 = min(strip * kStripCols + kStripCols - 1, V.g.nx);
+    const int r0 = chunk * kRowChunk, r1 = min(r0 + kRowChunk - 1, V.g.ny);
+    atomicAdd(&S.units[L.prof_op], (unsigned long long)((c1 - c0 + 1) * (r1 - r0 + 1)));
+  }
   strip_loop<T>(L.U, V, strip, chunk, op);
   op.finish(S, s);
 }

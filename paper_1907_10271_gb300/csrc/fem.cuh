@@ -32,9 +32,14 @@ struct View {
   void* ext1;
 };
 
+// Operation ids of the kernel timer (mlmc_profile_get).
+enum ProfOp { kProfPreTop = 0, kProfPre, kProfPost, kProfPostTop, kProfPcgP, kProfResid, kProfRestrict,
+              kProfCoarsest, kProfOther, kProfOps };
+
 template <typename T>
 struct ViewList {
   int n;
+  int prof_op;      // ProfOp of the launch (node counting when SampleState::units is set)
   Invariants U;
   View<T> v[kMaxViews];
 };
@@ -58,6 +63,7 @@ struct SampleState {
   int* iters;         // PCG iterations (all refinement steps)
   int* status;        // 0 ok, MLMC_ERR_NOT_CONVERGED
   int* count;         // [max_iter] active samples after each iteration
+  unsigned long long* units;   // [kProfOps] nodes processed per operation (null: not counted)
 };
 
 // Strip kernels (q = K p family); see fem.cu for the operand conventions.

@@ -24,6 +24,15 @@
 
 namespace mlmc {
 
+// Launches EXPR (a cudaError_t expression) as timer operation OP, returning on error.
+#define MLMC_LAUNCH(OP, NAME, EXPR)                      \
+  do {                                                   \
+    ctx.timer.begin((OP), st);                           \
+    const cudaError_t launch_err_ = (EXPR);              \
+    ctx.timer.end(st);                                   \
+    if (launch_err_ != cudaSuccess) return ctx.cuda_fail(launch_err_, (NAME)); \
+  } while (0)
+
 namespace {
 
 template <typename T>
@@ -203,6 +212,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   CarveAlloc ca{&ctx.solve_arena};
   plan(ca);
   plan_state(ca);
+  S.units = ctx.timer.on ? ctx.timer.units_dev : nullptr;
   {
     char* state_begin = reinterpret_cast<char*>(S.alpha);
     char* state_end = reinterpret_cast<char*>(outer_count + 1);
@@ -223,7 +233,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     }
     if (L.n == 0) break;
     const int tt = finalize_points(L, per);
-    if ((e = launch_trig_average<T>(L, tt, st)) != cudaSuccess) return ctx.cuda_fail(e, "trig_average");
+    MLMC_LAUNCH(kProfOther, "trig_average", launch_trig_average<T>(L, tt, st));
   }
   for (int k = 0; k < 64; ++k) {
     ViewList<T> L = empty_list<T>(ctx);
@@ -237,7 +247,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     }
     if (L.n == 0) break;
     const int tt = finalize_points(L, per);
-    if ((e = launch_invdiag<T>(L, tt, st)) != cudaSuccess) return ctx.cuda_fail(e, "invdiag");
+    MLMC_LAUNCH(kProfOther, "invdiag", launch_invdiag<T>(L, tt, st));
   }
   {
     ViewList<T> L = empty_list<T>(ctx);
@@ -250,7 +260,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       acc += v.nwork;
       L.v[L.n++] = v;
     }
-    if ((e = launch_coarsest_setup<T>(L, acc, st)) != cudaSuccess) return ctx.cuda_fail(e, "coarsest_setup");
+    MLMC_LAUNCH(kProfOther, "coarsest_setup", launch_coarsest_setup<T>(L, acc, st));
   }
 
   // ---- view lists reused every iteration
@@ -323,15 +333,17 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       }
       if (Ltop.n) {
         const int tw = finalize_warps(Ltop);
-        if ((err = launch_strip<T>(StripOp::PreTop, Ltop, S, tw, st)) != cudaSuccess) return ctx.cuda_fail(err, "pre_top");
+        Ltop.prof_op = kProfPreTop;
+        MLMC_LAUNCH(kProfPreTop, "pre_top", launch_strip<T>(StripOp::PreTop, Ltop, S, tw, st));
       }
       if (Lmid.n) {
         const int tw = finalize_warps(Lmid);
-        if ((err = launch_strip<T>(StripOp::Pre, Lmid, S, tw, st)) != cudaSuccess) return ctx.cuda_fail(err, "pre");
+        Lmid.prof_op = kProfPre;
+        MLMC_LAUNCH(kProfPre, "pre", launch_strip<T>(StripOp::Pre, Lmid, S, tw, st));
       }
       if (Lres.n) {
         const int tt = finalize_points(Lres, per_res);
-        if ((err = launch_restrict<T>(Lres, S, tt, st)) != cudaSuccess) return ctx.cuda_fail(err, "restrict");
+        MLMC_LAUNCH(kProfRestrict, "restrict", launch_restrict<T>(Lres, S, tt, st));
       }
     }
     // coarsest
@@ -349,7 +361,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         acc += v.nwork;
         L.v[L.n++] = v;
       }
-      if ((err = launch_coarsest_solve<T>(L, S, acc, st)) != cudaSuccess) return ctx.cuda_fail(err, "coarsest");
+      MLMC_LAUNCH(kProfCoarsest, "coarsest", launch_coarsest_solve<T>(L, S, acc, st));
     }
     // up sweep
     for (int a = 1; a <= amax; ++a) {
@@ -372,20 +384,23 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       }
       if (Lmid.n) {
         const int tw = finalize_warps(Lmid);
-        if ((err = launch_strip<T>(StripOp::Post, Lmid, S, tw, st)) != cudaSuccess) return ctx.cuda_fail(err, "post");
+        Lmid.prof_op = kProfPost;
+        MLMC_LAUNCH(kProfPost, "post", launch_strip<T>(StripOp::Post, Lmid, S, tw, st));
       }
       if (Ltop.n) {
         const int tw = finalize_warps(Ltop);
-        if ((err = launch_strip<T>(StripOp::PostTop, Ltop, S, tw, st)) != cudaSuccess) return ctx.cuda_fail(err, "post_top");
+        Ltop.prof_op = kProfPostTop;
+        MLMC_LAUNCH(kProfPostTop, "post_top", launch_strip<T>(StripOp::PostTop, Ltop, S, tw, st));
       }
     }
-    if ((err = launch_after_post(S, total, iter, st)) != cudaSuccess) return ctx.cuda_fail(err, "after_post");
+    MLMC_LAUNCH(kProfOther, "after_post", launch_after_post(S, total, iter, st));
     {
       ViewList<T> L = top_list(StripOp::PcgP, parity);
       const int tw = finalize_warps(L);
-      if ((err = launch_strip<T>(StripOp::PcgP, L, S, tw, st)) != cudaSuccess) return ctx.cuda_fail(err, "pcg_p");
+      L.prof_op = kProfPcgP;
+      MLMC_LAUNCH(kProfPcgP, "pcg_p", launch_strip<T>(StripOp::PcgP, L, S, tw, st));
     }
-    if ((err = launch_after_p(S, total, st)) != cudaSuccess) return ctx.cuda_fail(err, "after_p");
+    MLMC_LAUNCH(kProfOther, "after_p", launch_after_p(S, total, st));
     return MLMC_OK;
   };
 
@@ -418,8 +433,9 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       L.v[i].nwork = L.v[i].nsamp * L.v[i].tiles_x * L.v[i].tiles_y;
       acc += L.v[i].nwork;
     }
-    cudaError_t err = launch_resid64<T>(L, S, acc, st);
-    return err == cudaSuccess ? MLMC_OK : ctx.cuda_fail(err, "resid64");
+    L.prof_op = kProfResid;
+    MLMC_LAUNCH(kProfResid, "resid64", launch_resid64<T>(L, S, acc, st));
+    return MLMC_OK;
   };
 
   // lifting, initial residual ||f||
@@ -431,7 +447,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       L.v[i].nwork = (int)(L.v[i].nsamp * 2 * (int64_t)(L.v[i].g.nx + 1) * (L.v[i].g.ny + 1));
       acc += L.v[i].nwork;
     }
-    if ((e = launch_lift(L, ctx.cfg.shortening, (int)acc, st)) != cudaSuccess) return ctx.cuda_fail(e, "lift");
+    MLMC_LAUNCH(kProfOther, "lift", launch_lift(L, ctx.cfg.shortening, (int)acc, st));
   }
   {
     std::vector<int> ones(total, 1);
@@ -442,14 +458,13 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   }
   mlmc_status rs = resid();
   if (rs != MLMC_OK) return rs;
-  if ((e = launch_outer_init(S, total, st)) != cudaSuccess) return ctx.cuda_fail(e, "outer_init");
+  MLMC_LAUNCH(kProfOther, "outer_init", launch_outer_init(S, total, st));
 
   const double floor_tol = inner_double ? 1e-14 : ctx.floor_tol32;
   int outer = 0, max_it_seen = 0;
   for (;; ++outer) {
     if ((e = cudaMemsetAsync(outer_count, 0, sizeof(int), st)) != cudaSuccess) return ctx.cuda_fail(e, "memset");
-    if ((e = launch_outer_check(S, total, ctx.cfg.rtol, floor_tol, outer_count, st)) != cudaSuccess)
-      return ctx.cuda_fail(e, "outer_check");
+    MLMC_LAUNCH(kProfOther, "outer_check", launch_outer_check(S, total, ctx.cfg.rtol, floor_tol, outer_count, st));
     int h_outer = 0;
     if ((e = cudaMemcpyAsync(&h_outer, outer_count, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
@@ -505,7 +520,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         per.push_back(2 * (int64_t)(g.geo[0].nx + 1) * (g.geo[0].ny + 1));
       }
       const int tt = finalize_points(L, per);
-      if ((e = launch_update_d<T>(L, S, tt, st)) != cudaSuccess) return ctx.cuda_fail(e, "update_d");
+      MLMC_LAUNCH(kProfOther, "update_d", launch_update_d<T>(L, S, tt, st));
     }
     rs = resid();
     if (rs != MLMC_OK) return rs;
@@ -541,8 +556,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       L.v[i].nwork = (int)(L.v[i].nsamp * (int64_t)L.v[i].g.nx * L.v[i].g.ny);
       acc += L.v[i].nwork;
     }
-    if ((e = launch_stress<T>(L, S, ctx.cfg.omega_x0, ctx.cfg.omega_x1, ctx.cfg.lx, (int)acc, st)) != cudaSuccess)
-      return ctx.cuda_fail(e, "stress");
+    MLMC_LAUNCH(kProfOther, "stress", launch_stress<T>(L, S, ctx.cfg.omega_x0, ctx.cfg.omega_x1, ctx.cfg.lx, (int)acc, st));
   }
   for (auto& g : G) {
     const SolveGroup<T>& sg = *g.grp;
