@@ -183,6 +183,35 @@ mlmc_status mlmc_apply(mlmc_ctx* ctx, int32_t mesh_level, int64_t n, const doubl
 mlmc_status mlmc_solve_theta(mlmc_ctx* ctx, int32_t mesh_level, int64_t n, const double* theta,
                              double* q, int32_t* status, int32_t* iterations);
 
+/* ---- allocation-free solve ----
+   The paper has no counterpart to this entry point; it exists for callers that
+   cannot call cudaMalloc themselves or have it called on their behalf: code that
+   runs while another component owns all device memory (a server with its own
+   memory pool), plugins whose host framework forbids raw device allocations, and
+   latency-critical paths that must not pay for an allocation or for the implicit
+   synchronisation of cudaFree.
+
+   Same computation as mlmc_solve_theta (fields theta[n * n_el] of mesh
+   `mesh_level` -> q[n * 2], status[n] nullable), but without a context: cfg is
+   read for this call only (its KL fields are unused), work is issued on
+   `cuda_stream`, and the call allocates no device memory. Its workspace is one
+   file-scope device array of 32 MiB that every GPU which loads this library
+   holds until the process exits; theta, q and status are the caller's (host or
+   device memory). A request whose inputs and solver workspace do not fit in the
+   32 MiB (for example more than roughly 250 samples of a 64 x 16 mesh in mixed
+   precision) is rejected with MLMC_ERR_INVALID_ARG and a message naming the
+   limit; nothing is computed then.
+
+   The first call on a device looks up the array's device address with that
+   device current; make that first call before any stream capture. All calls
+   share the one array and every call initialises what it reads, so results do
+   not depend on earlier calls, but calls whose work overlaps on the GPU (other
+   streams, other host threads) race on the array: serialise them.
+   mlmc_static_last_error() describes the last failure of this entry point. */
+mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, int32_t mesh_level, int64_t n,
+                                    const double* theta, double* q, int32_t* status);
+const char* mlmc_static_last_error(void);
+
 /* ---- measurement ---- */
 
 /* Operation ids of the kernel timer. */

@@ -86,6 +86,8 @@ def lib():
             "mlmc_profile_enable": (I32, [P, I32]),
             "mlmc_profile_get": (I32, [P, I32, P, P, P]),
             "mlmc_launch_count": (I32, [P, P]),
+            "mlmc_solve_theta_static": (I32, [ctypes.POINTER(mlmc_config), P, I32, I64, P, P, P]),
+            "mlmc_static_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -257,3 +259,13 @@ def mlmc_launch_count(ctx):
     n = ctypes.c_int64()
     _check(ctx, lib().mlmc_launch_count(ctx, ctypes.byref(n)))
     return n.value
+
+
+def mlmc_solve_theta_static(cfg, mesh_level, n, theta, q, status=None, stream=None):
+    """Allocation-free solve (no context): see include/mlmc.h."""
+    st = current_stream() if stream is None else stream
+    s = lib().mlmc_solve_theta_static(ctypes.byref(cfg), ctypes.c_void_p(st), mesh_level, n,
+                                      _ptr(theta, np.float64), _ptr(q, np.float64), _ptr(status, np.int32))
+    if s != MLMC_OK:
+        raise MLMCError(s, lib().mlmc_static_last_error().decode(errors="replace"))
+    return s

@@ -12,8 +12,10 @@ namespace mlmc {
 struct Arena {
   char* base = nullptr;
   size_t cap = 0, used = 0;
+  bool borrowed = false;   // memory owned by someone else: never reallocated or freed here
   cudaError_t reserve(size_t bytes) {
     if (bytes <= cap) return cudaSuccess;
+    if (borrowed) return cudaErrorMemoryAllocation;
     if (base) cudaFree(base);
     base = nullptr;
     cap = 0;
@@ -30,7 +32,7 @@ struct Arena {
     return reinterpret_cast<T*>(base + off);
   }
   void release() {
-    if (base) cudaFree(base);
+    if (base && !borrowed) cudaFree(base);
     base = nullptr;
     cap = used = 0;
   }

@@ -1,0 +1,158 @@
+// Allocation-free solve on caller-supplied fields.
+//
+// Some callers cannot call cudaMalloc: code that runs while another component owns
+// all device memory (an inference or simulation server with its own pool), plugins
+// whose host framework forbids raw device allocations, or latency-critical paths
+// that must not pay for an allocation or the implicit synchronisation cudaFree
+// brings. mlmc_solve_theta_static serves them: it needs no context and allocates
+// nothing. Its workspace is one file-scope device array of kStaticScratchBytes
+// that every GPU loading this library holds until the process exits; the caller
+// passes the fields and the output buffers.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "context.h"
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;   // 32 MiB
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+std::map<int, char*> g_static_addr;   // device ordinal -> device address of g_static_scratch
+std::string g_static_error;
+
+__global__ void k_static_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+bool device_accessible(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+mlmc_status static_fail(mlmc_status s, const std::string& m) {
+  std::lock_guard<std::mutex> g(g_static_mu);
+  g_static_error = m;
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mlmc_static_last_error(void) { return g_static_error.c_str(); }
+
+mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, int32_t mesh_level, int64_t n,
+                                    const double* theta, double* q, int32_t* status) {
+  if (!cfg) return static_fail(MLMC_ERR_INVALID_ARG, "null config");
+  if (mesh_level < 0 || mesh_level >= cfg->levels || n < 0 || (n > 0 && (!theta || !q)))
+    return static_fail(MLMC_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return MLMC_OK;
+  if (cfg->precision != MLMC_PREC_FP64 && cfg->precision != MLMC_PREC_MIXED)
+    return static_fail(MLMC_ERR_INVALID_ARG, "unknown precision");
+  // device address of the scratch array, looked up once per device with that device current
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return static_fail(MLMC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    auto it = g_static_addr.find(dev);
+    if (it == g_static_addr.end()) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_static_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return MLMC_ERR_CUDA;
+      }
+      it = g_static_addr.emplace(dev, static_cast<char*>(ptr)).first;
+    }
+    scratch = it->second;
+  }
+  // a context on the stack: no KL bases (the fields are given), workspace borrowed
+  mlmc::Context c;
+  c.cfg = *cfg;
+  c.stream = static_cast<cudaStream_t>(cuda_stream);
+  c.device = dev;
+  {
+    const mlmc_config& k = *cfg;
+    const double S[3][3] = {{1.0 / k.E11, -k.nu12 / k.E11, -k.nu13 / k.E11},
+                            {-k.nu12 / k.E11, 1.0 / k.E22, -k.nu23 / k.E22},
+                            {-k.nu13 / k.E11, -k.nu23 / k.E22, 1.0 / k.E33}};
+    const double det = S[0][0] * (S[1][1] * S[2][2] - S[1][2] * S[2][1]) -
+                       S[0][1] * (S[1][0] * S[2][2] - S[1][2] * S[2][0]) +
+                       S[0][2] * (S[1][0] * S[2][1] - S[1][1] * S[2][0]);
+    if (!(std::isfinite(det) && det > 0.0)) return static_fail(MLMC_ERR_INVALID_ARG, "bad material constants");
+    const double Q11 = (S[1][1] * S[2][2] - S[1][2] * S[2][1]) / det;
+    const double Q12 = -(S[0][1] * S[2][2] - S[0][2] * S[2][1]) / det;
+    const double Q22 = (S[0][0] * S[2][2] - S[0][2] * S[2][0]) / det;
+    const double Q66 = k.G12;
+    c.U.U1 = (3.0 * Q11 + 3.0 * Q22 + 2.0 * Q12 + 4.0 * Q66) / 8.0;
+    c.U.U2 = (Q11 - Q22) / 2.0;
+    c.U.U3 = (Q11 + Q22 - 2.0 * Q12 - 4.0 * Q66) / 8.0;
+    c.U.U4 = (Q11 + Q22 + 6.0 * Q12 - 4.0 * Q66) / 8.0;
+    c.U.U5 = (Q11 + Q22 - 2.0 * Q12 + 4.0 * Q66) / 8.0;
+  }
+  // front of the scratch: staged inputs and outputs; the rest: solver workspace
+  const mlmc::LevelLayout m = c.mesh(mesh_level);
+  const int64_t ne = n * m.n_el();
+  mlmc::Arena front;
+  front.base = scratch;
+  front.cap = kStaticScratchBytes;
+  front.borrowed = true;
+  double* th64 = front.carve<double>(device_accessible(theta) ? 0 : ne);
+  float* th32 = front.carve<float>(c.mixed() ? ne : 0);
+  double* qd = front.carve<double>(device_accessible(q) ? 0 : 2 * n);
+  int* sd = front.carve<int>(status && !device_accessible(status) ? n : 0);
+  const size_t front_bytes = (front.used + 255) & ~(size_t)255;
+  if (front_bytes >= kStaticScratchBytes)
+    return static_fail(MLMC_ERR_INVALID_ARG, "fields exceed the 32 MiB static scratch");
+  c.solve_arena.base = scratch + front_bytes;
+  c.solve_arena.cap = kStaticScratchBytes - front_bytes;
+  c.solve_arena.borrowed = true;
+  cudaStream_t st = c.stream;
+  const double* th_dev = theta;
+  if (!device_accessible(theta)) {
+    if ((e = cudaMemcpyAsync(th64, theta, sizeof(double) * ne, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return static_fail(MLMC_ERR_CUDA, std::string("copy in: ") + cudaGetErrorString(e));
+    th_dev = th64;
+  }
+  double* q_dev = device_accessible(q) ? q : qd;
+  int* s_dev = status ? (device_accessible(status) ? status : sd) : nullptr;
+  mlmc_status s;
+  if (c.mixed()) {
+    k_static_d2f<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(th_dev, th32, ne);
+    if ((e = cudaGetLastError()) != cudaSuccess) return static_fail(MLMC_ERR_CUDA, cudaGetErrorString(e));
+    std::vector<mlmc::SolveGroup<float>> g{{mesh_level, n, th32, q_dev, s_dev, nullptr}};
+    s = mlmc::solve_groups<float>(c, g);
+  } else {
+    std::vector<mlmc::SolveGroup<double>> g{{mesh_level, n, th_dev, q_dev, s_dev, nullptr}};
+    s = mlmc::solve_groups<double>(c, g);
+  }
+  if (s == MLMC_ERR_OOM)
+    return static_fail(MLMC_ERR_INVALID_ARG, "n = " + std::to_string(n) + " samples on a " + std::to_string(m.nx) +
+                                                 " x " + std::to_string(m.ny) +
+                                                 " mesh need more than the 32 MiB static scratch");
+  if (s != MLMC_OK) return static_fail(s, c.err);
+  if (q_dev != q && (e = cudaMemcpyAsync(q, q_dev, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return static_fail(MLMC_ERR_CUDA, std::string("copy out: ") + cudaGetErrorString(e));
+  if (s_dev && s_dev != status &&
+      (e = cudaMemcpyAsync(status, s_dev, sizeof(int) * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return static_fail(MLMC_ERR_CUDA, std::string("copy out: ") + cudaGetErrorString(e));
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return static_fail(MLMC_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(e));
+  return MLMC_OK;
+}
+
+}  // extern "C"
