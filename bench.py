@@ -187,6 +187,14 @@ def oracle_throughput(cfg, fraction, cores):
 
 # ---------------------------------------------------------------- GPU arm
 
+ID_STRIDE = 1 << 40   # sample ids of rank r start at r * 2^40: disjoint for any realistic run
+
+
+def shard_first_ids(rank, step, counts):
+    """First sample id of each level for (rank, step): disjoint ranges across ranks and steps."""
+    return [rank * ID_STRIDE + step * n for n in counts]
+
+
 def run_gpu(a):
     import torch
     rank, local, world = dist_env()
@@ -206,11 +214,9 @@ def run_gpu(a):
     qc = torch.empty_like(qf)
     st = torch.empty(total, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # > L2 (126 MB)
-    id_stride = 1 << 40
 
     def first_ids(step):
-        # disjoint ids per rank and per step
-        return [rank * id_stride + step * n for n in counts]
+        return shard_first_ids(rank, step, counts)
 
     def step(k, q1, q2, s):
         B.mlmc_sample_levels(ctx, levels, first_ids(k), counts, q1, q2, s)

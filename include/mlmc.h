@@ -155,6 +155,13 @@ mlmc_status mlmc_estimate(mlmc_ctx* ctx, double e, double theta, int64_t n_star,
 mlmc_status mlmc_level_stats_get(mlmc_ctx* ctx, int32_t level, mlmc_level_stats* out);
 mlmc_status mlmc_reset_stats(mlmc_ctx* ctx);
 
+/* Host-only (no GPU work): merges the moments of two disjoint sample sets of one
+   level, e.g. from two GPUs that sampled disjoint id ranges, with the pairwise
+   update of Chan et al. (n = na + nb, delta = mean_b - mean_a,
+   mean = mean_a + delta nb / n, m2 = m2_a + m2_b + delta^2 na nb / n). out may
+   alias a or b. */
+mlmc_status mlmc_merge_stats(const mlmc_level_stats* a, const mlmc_level_stats* b, mlmc_level_stats* out);
+
 /* ---- step-level entry points (each one step of the per-sample path) ---- */
 
 /* KL coefficients xi[n * kl_terms] (double) of samples first_id.. of `level`:

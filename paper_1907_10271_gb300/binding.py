@@ -86,6 +86,7 @@ def lib():
             "mlmc_profile_enable": (I32, [P, I32]),
             "mlmc_profile_get": (I32, [P, I32, P, P, P]),
             "mlmc_launch_count": (I32, [P, P]),
+            "mlmc_merge_stats": (I32, [P, P, P]),
             "mlmc_solve_theta_static": (I32, [ctypes.POINTER(mlmc_config), P, I32, I64, P, P, P]),
             "mlmc_static_last_error": (ctypes.c_char_p, []),
         }
@@ -269,3 +270,23 @@ def mlmc_solve_theta_static(cfg, mesh_level, n, theta, q, status=None, stream=No
     if s != MLMC_OK:
         raise MLMCError(s, lib().mlmc_static_last_error().decode(errors="replace"))
     return s
+
+
+def stats_from_dict(d):
+    s = mlmc_level_stats()
+    s.n = int(d["n"])
+    for k in range(2):
+        s.mean[k], s.m2[k], s.var[k] = d["mean"][k], d["m2"][k], d["var"][k]
+        s.sum_qf[k], s.sum_qc[k] = d["sum_qf"][k], d["sum_qc"][k]
+    s.cost = d.get("cost", 0.0)
+    return s
+
+
+def mlmc_merge_stats(a, b):
+    """Merged moments (dict) of two disjoint sample sets given as stats dicts."""
+    out = mlmc_level_stats()
+    sa, sb = stats_from_dict(a), stats_from_dict(b)
+    s = lib().mlmc_merge_stats(ctypes.byref(sa), ctypes.byref(sb), ctypes.byref(out))
+    if s != MLMC_OK:
+        raise MLMCError(s, "merge")
+    return out.as_dict()

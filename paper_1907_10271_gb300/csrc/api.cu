@@ -113,6 +113,7 @@ std::string validate(const mlmc_config& c) {
     nx /= 2;
     ny /= 2;
   }
+  if (nx == c.nx0) return "level-0 mesh must halve at least once (nx0, ny0 even)";
   if (2 * (nx + 1) * (ny + 1) > mlmc::kMaxCoarsestDofs) return "level-0 mesh does not halve down to <= 64 DOFs";
   return "";
 }
@@ -665,6 +666,26 @@ mlmc_status mlmc_estimate(mlmc_ctx* h, double e, double theta, int64_t n_star, i
   if (stats)
     for (int l = 0; l <= L; ++l) fill_stats(h, l, &stats[l]);
   return converged ? MLMC_OK : c.fail(MLMC_ERR_NOT_CONVERGED, "max_level reached before the bias test passed");
+}
+
+mlmc_status mlmc_merge_stats(const mlmc_level_stats* a, const mlmc_level_stats* b, mlmc_level_stats* out) {
+  if (!a || !b || !out) return MLMC_ERR_INVALID_ARG;
+  mlmc_level_stats r;
+  std::memset(&r, 0, sizeof(r));
+  r.n = a->n + b->n;
+  r.cost = a->n > 0 ? a->cost : b->cost;
+  const double na = (double)a->n, nb = (double)b->n, n = (double)r.n;
+  for (int k = 0; k < 2; ++k) {
+    if (r.n == 0) break;
+    const double d = b->mean[k] - a->mean[k];
+    r.mean[k] = a->mean[k] + d * (nb / n);
+    r.m2[k] = a->m2[k] + b->m2[k] + d * d * (na * nb / n);
+    r.var[k] = r.m2[k] / n;
+    r.sum_qf[k] = a->sum_qf[k] + b->sum_qf[k];
+    r.sum_qc[k] = a->sum_qc[k] + b->sum_qc[k];
+  }
+  *out = r;
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_kl_coefficients(mlmc_ctx* h, int32_t level, uint64_t first_id, int64_t n, double* xi) {

@@ -1,0 +1,283 @@
+"""GPU parity of whole level pairs, moments, Algorithm 1 and the batch entry points.
+
+Everything goes through the C ABI; every expected value comes from the CPU oracle
+on the same (seed, level, id) inputs. Tolerances: 1e-9 relative per quantity on the
+double-precision path, 1e-6 on the mixed-precision path.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlmc as om
+from workloads import STRIP_FP64_3LEVEL, STRIP_MIXED_5LEVEL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_10271_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def oracle_pairs(w, level, ids, workers=None):
+    import os
+    ids = np.asarray(ids, dtype=np.uint64)
+    workers = workers or min(16, os.cpu_count() or 1, len(ids))
+    if workers <= 1 or len(ids) <= 2:
+        return om.level_pair(w, level, ids)
+    return om.level_pair_parallel(w, level, ids, workers)
+
+
+def rel(a, b):
+    return np.abs(a - b) / np.abs(b)
+
+
+def test_fp64_three_levels_full_counts(B):
+    """The 3-level double-precision strip at its full sample counts (200/100/50)."""
+    w = STRIP_FP64_3LEVEL
+    ctx = B.mlmc_create(B.config_from_workload(w))
+    try:
+        for level, n in enumerate(w["n_per_level"]):
+            qf = np.zeros(2 * n)
+            qc = np.zeros(2 * n)
+            st = np.ones(n, dtype=np.int32)
+            B.mlmc_sample_level(ctx, level, 0, n, qf, qc, st)
+            assert np.all(st == 0)
+            rf, rc = oracle_pairs(w, level, np.arange(n))
+            assert rel(qf.reshape(n, 2), rf).max() < 1e-9
+            if level > 0:
+                assert rel(qc.reshape(n, 2), rc).max() < 1e-9
+            else:
+                assert np.all(qc == 0)
+            # moments of the level against the oracle's exactly rounded sums on the oracle's values
+            s = B.mlmc_level_stats_get(ctx, level)
+            y = rf - rc
+            assert s["n"] == n
+            for k in range(2):
+                n_, mean, var = om.moments(y[:, k])
+                assert s["mean"][k] == pytest.approx(mean, rel=1e-9, abs=1e-9 * abs(rf[:, k]).max())
+                # Y carries 1e-9 relative errors of Q ~ 1e7..1e8: compare var against its scale
+                assert abs(s["var"][k] - var) <= 1e-6 * var + (1e-9 * abs(rf[:, k]).max()) ** 2 * 4
+                assert s["sum_qf"][k] == pytest.approx(math.fsum(rf[:, k]), rel=1e-9)
+    finally:
+        B.mlmc_destroy(ctx)
+
+
+def test_moment_accumulator_against_exact_sums(B):
+    """The device accumulator on the values the GPU itself returned: Welford/Chan with
+    compensated sums against exactly rounded two-pass sums, over two calls."""
+    w = STRIP_FP64_3LEVEL
+    ctx = B.mlmc_create(B.config_from_workload(w))
+    try:
+        n1, n2 = 37, 91
+        q1, c1 = np.zeros(2 * n1), np.zeros(2 * n1)
+        q2, c2 = np.zeros(2 * n2), np.zeros(2 * n2)
+        B.mlmc_sample_level(ctx, 1, 5, n1, q1, c1)
+        B.mlmc_sample_level(ctx, 1, 5 + n1, n2, q2, c2)
+        s = B.mlmc_level_stats_get(ctx, 1)
+        y = np.concatenate([(q1 - c1).reshape(n1, 2), (q2 - c2).reshape(n2, 2)])
+        qf = np.concatenate([q1.reshape(n1, 2), q2.reshape(n2, 2)])
+        assert s["n"] == n1 + n2
+        for k in range(2):
+            _, mean, var = om.moments(y[:, k])
+            assert s["mean"][k] == pytest.approx(mean, rel=1e-13, abs=1e-12)
+            assert s["var"][k] == pytest.approx(var, rel=1e-10)
+            assert s["sum_qf"][k] == pytest.approx(math.fsum(qf[:, k]), rel=1e-15)
+        B.mlmc_reset_stats(ctx)
+        assert B.mlmc_level_stats_get(ctx, 1)["n"] == 0
+    finally:
+        B.mlmc_destroy(ctx)
+
+
+def test_mixed_five_levels_reduced_counts(B):
+    """Every level of the 5-level mixed-precision strip, a few samples each."""
+    w = STRIP_MIXED_5LEVEL
+    ctx = B.mlmc_create(B.config_from_workload(w))
+    try:
+        for level, ids in enumerate([np.arange(0, 9), np.arange(100, 105), np.arange(7, 10), [41], [3]]):
+            ids = np.asarray(ids)
+            n = len(ids)
+            qf = np.zeros(2 * n)
+            qc = np.zeros(2 * n)
+            st = np.ones(n, dtype=np.int32)
+            # non-contiguous ids: one call per contiguous run
+            runs = np.split(ids, np.where(np.diff(ids) != 1)[0] + 1)
+            off = 0
+            for r in runs:
+                B.mlmc_sample_level(ctx, level, int(r[0]), len(r), qf[2 * off:2 * (off + len(r))],
+                                    qc[2 * off:2 * (off + len(r))], st[off:off + len(r)])
+                off += len(r)
+            assert np.all(st == 0)
+            rf, rc = oracle_pairs(w, level, ids)
+            assert rel(qf.reshape(n, 2), rf).max() < 1e-6, level
+            if level > 0:
+                assert rel(qc.reshape(n, 2), rc).max() < 1e-6, level
+    finally:
+        B.mlmc_destroy(ctx)
+
+
+def test_full_size_launch_sampled_outputs(B):
+    """The benchmark's launch (all five levels at N_l = 8192/2048/512/128/32 in one
+    mlmc_sample_levels call); sampled outputs checked one by one against the oracle."""
+    import torch
+    w = STRIP_MIXED_5LEVEL
+    counts = list(w["n_per_level"])
+    total = sum(counts)
+    ctx = B.mlmc_create(B.config_from_workload(w))
+    try:
+        qf = torch.zeros(2 * total, dtype=torch.float64, device="cuda")
+        qc = torch.zeros_like(qf)
+        st = torch.ones(total, dtype=torch.int32, device="cuda")
+        B.mlmc_sample_levels(ctx, list(range(5)), [0] * 5, counts, qf, qc, st)
+        torch.cuda.synchronize()
+        assert int((st != 0).sum()) == 0
+        qf = qf.cpu().numpy().reshape(total, 2)
+        qc = qc.cpu().numpy().reshape(total, 2)
+        offs = np.concatenate([[0], np.cumsum(counts)])
+        picks = {0: [0, 4097, 8191], 1: [5, 2047], 2: [300], 3: [77]}
+        for level, ids in picks.items():
+            rf, rc = oracle_pairs(w, level, ids)
+            got_f = qf[offs[level] + np.array(ids)]
+            got_c = qc[offs[level] + np.array(ids)]
+            assert rel(got_f, rf).max() < 1e-6, level
+            if level > 0:
+                assert rel(got_c, rc).max() < 1e-6, level
+        # every level's moments were folded in once
+        for level, n in enumerate(counts):
+            assert B.mlmc_level_stats_get(ctx, level)["n"] == n
+        # properties at any size: quantities positive and finite, level differences
+        # shrink with the level (variance decay of Y_l, reaction quantity)
+        assert np.all(np.isfinite(qf)) and np.all(qf > 0)
+        v = [np.var(qf[offs[l]:offs[l + 1], 0] - qc[offs[l]:offs[l + 1], 0]) for l in range(1, 5)]
+        assert all(b < a for a, b in zip(v, v[1:]))
+    finally:
+        B.mlmc_destroy(ctx)
+
+
+def test_sample_levels_matches_single_level_calls_and_solve_batch(B):
+    """Same xi on both meshes of a pair; results independent of batch composition."""
+    w = STRIP_MIXED_5LEVEL
+    ctx = B.mlmc_create(B.config_from_workload(w))
+    try:
+        counts = [5, 4, 3]
+        total = sum(counts)
+        qf = np.zeros(2 * total)
+        qc = np.zeros(2 * total)
+        B.mlmc_sample_levels(ctx, [0, 1, 2], [10, 20, 30], counts, qf, qc)
+        off = 0
+        items = []
+        for level, n, first in zip([0, 1, 2], counts, [10, 20, 30]):
+            f1 = np.zeros(2 * n)
+            c1 = np.zeros(2 * n)
+            B.mlmc_sample_level(ctx, level, first, n, f1, c1)
+            np.testing.assert_allclose(f1, qf[2 * off:2 * (off + n)], rtol=1e-8)
+            np.testing.assert_allclose(c1, qc[2 * off:2 * (off + n)], rtol=1e-8)
+            for j in range(n):
+                items.append((level, level, first + j))
+                if level > 0:
+                    items.append((level, level - 1, first + j))
+            off += n
+        qb = np.zeros(2 * len(items))
+        sb = np.ones(len(items), dtype=np.int32)
+        B.mlmc_solve_batch(ctx, items, qb, sb)
+        assert np.all(sb == 0)
+        k = 0
+        off = 0
+        for level, n in zip([0, 1, 2], counts):
+            for j in range(n):
+                np.testing.assert_allclose(qb[2 * k:2 * k + 2], qf[2 * (off + j):2 * (off + j) + 2], rtol=1e-8)
+                k += 1
+                if level > 0:
+                    np.testing.assert_allclose(qb[2 * k:2 * k + 2], qc[2 * (off + j):2 * (off + j) + 2], rtol=1e-8)
+                    k += 1
+            off += n
+    finally:
+        B.mlmc_destroy(ctx)
+
+
+def test_telescoping_on_identical_samples(B):
+    """mean(Q_0) + sum_l mean(Q_l - Q_{l-1}) = mean(Q_L) when every mesh solves the same
+    xi (Eq. MLMC_expectation), with each mesh's values produced by separate solves."""
+    w = STRIP_FP64_3LEVEL
+    ctx = B.mlmc_create(B.config_from_workload(w))
+    try:
+        ids = list(range(12))
+        Q = {}
+        for m in range(3):
+            q = np.zeros(2 * len(ids))
+            B.mlmc_solve_batch(ctx, [(2, m, i) for i in ids], q)
+            Q[m] = q.reshape(-1, 2)
+        tel = Q[0].mean(0) + (Q[1] - Q[0]).mean(0) + (Q[2] - Q[1]).mean(0)
+        np.testing.assert_allclose(tel, Q[2].mean(0), rtol=1e-14)
+        # and the coarse solve inside a level-2 pair equals the mesh-1 solve of the same xi
+        qf, qc = np.zeros(2 * len(ids)), np.zeros(2 * len(ids))
+        B.mlmc_sample_level(ctx, 2, 0, len(ids), qf, qc)
+        np.testing.assert_allclose(qc.reshape(-1, 2), Q[1], rtol=1e-10)
+        np.testing.assert_allclose(qf.reshape(-1, 2), Q[2], rtol=1e-10)
+    finally:
+        B.mlmc_destroy(ctx)
+
+
+def test_algorithm1_against_oracle(B):
+    w = dict(STRIP_FP64_3LEVEL)
+    e, theta, n_star = 1.5e5, 0.5, 12
+    ctx = B.mlmc_create(B.config_from_workload(w))
+    try:
+        status, est, stats, L = B.mlmc_estimate(ctx, e, theta, n_star, 2, qoi=0)
+        ref_est, Y, ref_L, conv = om.algorithm1(w, e, theta, n_star, 2, qoi=0)
+        assert conv and status == B.MLMC_OK
+        assert L == ref_L
+        assert [s["n"] for s in stats] == [len(y) for y in Y]
+        assert est == pytest.approx(ref_est, rel=1e-9)
+        for s, y in zip(stats, Y):
+            assert s["mean"][0] == pytest.approx(np.mean(y), rel=1e-8, abs=1e-6 * abs(ref_est))
+    finally:
+        B.mlmc_destroy(ctx)
+
+
+def test_edge_cases(B):
+    import torch
+    w = STRIP_FP64_3LEVEL
+    ctx = B.mlmc_create(B.config_from_workload(w))
+    try:
+        B.mlmc_sample_level(ctx, 0, 0, 0)                      # empty request is a no-op
+        assert B.mlmc_level_stats_get(ctx, 0)["n"] == 0
+        with pytest.raises(B.MLMCError, match="INVALID_ARG"):
+            B.mlmc_sample_level(ctx, 3, 0, 1, np.zeros(2))      # level out of range
+        with pytest.raises(B.MLMCError, match="INVALID_ARG"):
+            B.mlmc_solve_batch(ctx, [(0, 5, 0)], np.zeros(2))
+        # device and host buffers give the same values; null coarse/status outputs allowed
+        n = 3
+        qh = np.zeros(2 * n)
+        B.mlmc_sample_level(ctx, 1, 1 << 33, n, qh, None, None)
+        qd = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+        B.mlmc_sample_level(ctx, 1, 1 << 33, n, qd)
+        np.testing.assert_allclose(qd.cpu().numpy(), qh, rtol=1e-12)
+        rf, _ = om.level_pair(w, 1, np.arange(1 << 33, (1 << 33) + n, dtype=np.uint64))
+        assert rel(qh.reshape(n, 2), rf).max() < 1e-9
+    finally:
+        B.mlmc_destroy(ctx)
+    bad = B.config_from_workload(w)
+    bad.nx0 = 3
+    with pytest.raises(B.MLMCError, match="INVALID_ARG"):
+        B.mlmc_create(bad)
+
+
+def test_non_converged_samples_are_excluded(B):
+    """An iteration cap too small to converge: status NOT_CONVERGED, moments skip them."""
+    w = STRIP_FP64_3LEVEL
+    ctx = B.mlmc_create(B.config_from_workload(w, max_iter=2, max_outer=1))
+    try:
+        n = 4
+        st = np.zeros(n, dtype=np.int32)
+        B.mlmc_sample_level(ctx, 1, 0, n, np.zeros(2 * n), np.zeros(2 * n), st)
+        assert np.all(st == B.MLMC_ERR_NOT_CONVERGED)
+        assert B.mlmc_level_stats_get(ctx, 1)["n"] == 0
+    finally:
+        B.mlmc_destroy(ctx)
