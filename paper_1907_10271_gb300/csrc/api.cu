@@ -93,6 +93,7 @@ mlmc::Invariants invariants(const mlmc_config& c, bool& ok) {
   U.U3 = (Q11 + Q22 - 2.0 * Q12 - 4.0 * Q66) / 8.0;
   U.U4 = (Q11 + Q22 + 6.0 * Q12 - 4.0 * Q66) / 8.0;
   U.U5 = (Q11 + Q22 - 2.0 * Q12 + 4.0 * Q66) / 8.0;
+  U.round_single();
   return U;
 }
 
@@ -167,8 +168,8 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
       const int64_t nel_f = c.mesh(r.level).n_el(), nel_c = r.level > 0 ? c.mesh(r.level - 1).n_el() : 1;
       alloc(B[k].xi, r.n * nkl);
       alloc(B[k].xi32, r.n * nkl);
-      alloc(reinterpret_cast<T*&>(B[k].theta_f), r.n * nel_f);
-      alloc(reinterpret_cast<T*&>(B[k].theta_c), r.n * nel_c);
+      alloc(reinterpret_cast<T*&>(B[k].theta_f), 2 * r.n * nel_f);
+      alloc(reinterpret_cast<T*&>(B[k].theta_c), 2 * r.n * nel_c);
       alloc(B[k].qf, 2 * r.n);
       alloc(B[k].qc, 2 * r.n);
       alloc(B[k].st_f, r.n);
@@ -210,7 +211,7 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
       const T* basis = c.mixed() ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
       T* th = (T*)(side == 0 ? B[k].theta_f : B[k].theta_c);
       c.timer.begin(mlmc::kProfOther, st);
-      e = mlmc::launch_kl_synthesis<T>(xiT, basis, r.n, (int)c.mesh(m).n_el(), nkl, th, st);
+      e = mlmc::launch_kl_synthesis<T>(xiT, basis, r.n, (int)c.mesh(m).n_el(), nkl, th, true, st);
       c.timer.end(st);
       if (e != cudaSuccess) return c.cuda_fail(e, "kl_synthesis");
       if (side == 0) groups.push_back({m, r.n, th, B[k].qf, B[k].st_f, B[k].it_f});
@@ -251,7 +252,17 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
 mlmc_status sample_levels_impl(mlmc_ctx* h, std::vector<LevelReq> reqs, double* q_fine, double* q_coarse,
                                int32_t* status) {
   Context& c = h->c;
-  const double budget = c.cfg.max_batch > 0 ? 1e300 : 8.0e9;
+  // one lock-stepped solve for as much of the request as half the free device memory
+  // holds (at most 64 GB), unless the caller fixed the batch size
+  double budget = 8.0e9;
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+      budget = std::min(64.0e9, std::max(budget, 0.5 * (double)(free_b + c.solve_arena.cap + c.batch_arena.cap)));
+    else
+      cudaGetLastError();
+  }
+  if (c.cfg.max_batch > 0) budget = 1e300;
   // cut requests larger than the budget (or than max_batch) into pieces
   std::vector<LevelReq> pieces;
   for (const auto& r : reqs) {
@@ -543,7 +554,7 @@ mlmc_status mlmc_solve_batch(mlmc_ctx* h, const mlmc_item* items, int64_t n, dou
   sz.add<int>(1);
   sz.add<int>(n);
   sz.add<uint64_t>(n);
-  sz.add<char>(nel_total * tb);
+  sz.add<char>(2 * nel_total * tb);
   sz.add<double>(2 * n);
   sz.add<int>(n);
   sz.add<int>(n);
@@ -558,7 +569,7 @@ mlmc_status mlmc_solve_batch(mlmc_ctx* h, const mlmc_item* items, int64_t n, dou
   int* fail = c.batch_arena.carve<int>(1);
   int* lv_dev = c.batch_arena.carve<int>(n);
   uint64_t* id_dev = c.batch_arena.carve<uint64_t>(n);
-  char* theta = c.batch_arena.carve<char>(nel_total * tb);
+  char* theta = c.batch_arena.carve<char>(2 * nel_total * tb);
   double* qd = c.batch_arena.carve<double>(2 * n);
   int* sd = c.batch_arena.carve<int>(n);
   int* itd = c.batch_arena.carve<int>(n);
@@ -583,10 +594,11 @@ mlmc_status mlmc_solve_batch(mlmc_ctx* h, const mlmc_item* items, int64_t n, dou
       const int64_t nel = c.mesh(m).n_el();
       T* th = reinterpret_cast<T*>(theta) + eoff;
       const T* B = mixed ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
-      cudaError_t err = mlmc::launch_kl_synthesis<T>(xiT + k * c.cfg.kl_terms, B, nb, (int)nel, c.cfg.kl_terms, th, st);
+      cudaError_t err =
+          mlmc::launch_kl_synthesis<T>(xiT + k * c.cfg.kl_terms, B, nb, (int)nel, c.cfg.kl_terms, th, true, st);
       if (err != cudaSuccess) return c.cuda_fail(err, "kl_synthesis");
       groups.push_back({m, nb, th, qd + 2 * k, sd + k, itd + k});
-      eoff += nb * nel;
+      eoff += 2 * nb * nel;
       k = k1;
     }
     return mlmc::solve_groups<T>(c, groups);
@@ -736,10 +748,11 @@ mlmc_status mlmc_theta(mlmc_ctx* h, int32_t level, int32_t mesh_level, uint64_t 
           cudaSuccess)
     return c.cuda_fail(e, "kl_coefficients");
   if (c.mixed()) {
-    if ((e = mlmc::launch_kl_synthesis<float>(xi32, c.basis32[mesh_level], n, (int)nel, nkl, th32, st)) != cudaSuccess ||
+    if ((e = mlmc::launch_kl_synthesis<float>(xi32, c.basis32[mesh_level], n, (int)nel, nkl, th32, false, st)) !=
+            cudaSuccess ||
         (e = convert(th32, th, n * nel, st)) != cudaSuccess)
       return c.cuda_fail(e, "kl_synthesis");
-  } else if ((e = mlmc::launch_kl_synthesis<double>(xi, c.basis64[mesh_level], n, (int)nel, nkl, th, st)) !=
+  } else if ((e = mlmc::launch_kl_synthesis<double>(xi, c.basis64[mesh_level], n, (int)nel, nkl, th, false, st)) !=
              cudaSuccess) {
     return c.cuda_fail(e, "kl_synthesis");
   }
@@ -760,7 +773,8 @@ mlmc_status mlmc_apply(mlmc_ctx* h, int32_t mesh_level, int64_t n, const double*
   sz.add<double>(ne);
   sz.add<double>(nd);
   sz.add<double>(nd);
-  sz.add<float>(ne);
+  sz.add<double>(2 * ne);
+  sz.add<float>(2 * ne);
   sz.add<float>(nd);
   sz.add<float>(nd);
   cudaError_t e = c.batch_arena.reserve(sz.used + 256);
@@ -769,7 +783,8 @@ mlmc_status mlmc_apply(mlmc_ctx* h, int32_t mesh_level, int64_t n, const double*
   double* th = c.batch_arena.carve<double>(ne);
   double* pd = c.batch_arena.carve<double>(nd);
   double* qd = c.batch_arena.carve<double>(nd);
-  float* th32 = c.batch_arena.carve<float>(ne);
+  double* t2 = c.batch_arena.carve<double>(2 * ne);
+  float* t232 = c.batch_arena.carve<float>(2 * ne);
   float* p32 = c.batch_arena.carve<float>(nd);
   float* q32 = c.batch_arena.carve<float>(nd);
   cudaStream_t st = c.stream;
@@ -777,13 +792,15 @@ mlmc_status mlmc_apply(mlmc_ctx* h, int32_t mesh_level, int64_t n, const double*
     return c.cuda_fail(e, "copy in");
   mlmc_status s;
   if (c.mixed()) {
-    if ((e = convert(th, th32, ne, st)) != cudaSuccess || (e = convert(pd, p32, nd, st)) != cudaSuccess)
+    if ((e = mlmc::launch_theta_to_trig2<float>(th, ne, t232, st)) != cudaSuccess ||
+        (e = convert(pd, p32, nd, st)) != cudaSuccess)
       return c.cuda_fail(e, "convert");
-    s = mlmc::apply_operator<float>(c, mesh_level, n, th32, p32, q32);
+    s = mlmc::apply_operator<float>(c, mesh_level, n, t232, p32, q32);
     if (s != MLMC_OK) return s;
     if ((e = convert(q32, qd, nd, st)) != cudaSuccess) return c.cuda_fail(e, "convert");
   } else {
-    s = mlmc::apply_operator<double>(c, mesh_level, n, th, pd, qd);
+    if ((e = mlmc::launch_theta_to_trig2<double>(th, ne, t2, st)) != cudaSuccess) return c.cuda_fail(e, "convert");
+    s = mlmc::apply_operator<double>(c, mesh_level, n, t2, pd, qd);
     if (s != MLMC_OK) return s;
   }
   if ((e = from_device(q, qd, nd, st)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
@@ -801,7 +818,8 @@ mlmc_status mlmc_solve_theta(mlmc_ctx* h, int32_t mesh_level, int64_t n, const d
   const int64_t ne = n * c.mesh(mesh_level).n_el();
   mlmc::Sizer sz;
   sz.add<double>(ne);
-  sz.add<float>(ne);
+  sz.add<double>(2 * ne);
+  sz.add<float>(2 * ne);
   sz.add<double>(2 * n);
   sz.add<int>(n);
   sz.add<int>(n);
@@ -809,7 +827,8 @@ mlmc_status mlmc_solve_theta(mlmc_ctx* h, int32_t mesh_level, int64_t n, const d
   if (e != cudaSuccess) return c.fail(MLMC_ERR_OOM, "solve buffers");
   c.batch_arena.reset();
   double* th = c.batch_arena.carve<double>(ne);
-  float* th32 = c.batch_arena.carve<float>(ne);
+  double* t2 = c.batch_arena.carve<double>(2 * ne);
+  float* t232 = c.batch_arena.carve<float>(2 * ne);
   double* qd = c.batch_arena.carve<double>(2 * n);
   int* sd = c.batch_arena.carve<int>(n);
   int* itd = c.batch_arena.carve<int>(n);
@@ -817,11 +836,12 @@ mlmc_status mlmc_solve_theta(mlmc_ctx* h, int32_t mesh_level, int64_t n, const d
   if ((e = to_device(th, theta, ne, st)) != cudaSuccess) return c.cuda_fail(e, "copy in");
   mlmc_status s;
   if (c.mixed()) {
-    if ((e = convert(th, th32, ne, st)) != cudaSuccess) return c.cuda_fail(e, "convert");
-    std::vector<mlmc::SolveGroup<float>> g{{mesh_level, n, th32, qd, sd, itd}};
+    if ((e = mlmc::launch_theta_to_trig2<float>(th, ne, t232, st)) != cudaSuccess) return c.cuda_fail(e, "convert");
+    std::vector<mlmc::SolveGroup<float>> g{{mesh_level, n, t232, qd, sd, itd}};
     s = mlmc::solve_groups<float>(c, g);
   } else {
-    std::vector<mlmc::SolveGroup<double>> g{{mesh_level, n, th, qd, sd, itd}};
+    if ((e = mlmc::launch_theta_to_trig2<double>(th, ne, t2, st)) != cudaSuccess) return c.cuda_fail(e, "convert");
+    std::vector<mlmc::SolveGroup<double>> g{{mesh_level, n, t2, qd, sd, itd}};
     s = mlmc::solve_groups<double>(c, g);
   }
   if (s != MLMC_OK) return s;

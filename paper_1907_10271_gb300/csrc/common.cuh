@@ -28,13 +28,23 @@ namespace mlmc {
 
 constexpr int kWarp = 32;
 constexpr int kStripCols = 30;     // output node columns per warp strip (32 lanes, 1 halo each side)
-constexpr int kRowChunk = 16;      // output node rows per warp tile
+constexpr int kRowChunk = 32;      // output node rows per warp tile
+constexpr int kPrefetch32 = 2;     // node rows in flight per warp (FP32 kernels)
+constexpr int kPrefetch64 = 2;     // node rows in flight per warp (FP64 kernels)
 constexpr int kWarpsPerBlock = 4;
 constexpr double kOmega = 0.5;     // Jacobi damping: element bound of lambda_max(D^-1 K) < 3.9 for any angle
 constexpr int kMaxCoarsestDofs = 64;
 
 struct Invariants {
   double U1, U2, U3, U4, U5;
+  float F1, F2, F3, F4, F5;   // the same values rounded once to single precision
+  void round_single() {
+    F1 = (float)U1;
+    F2 = (float)U2;
+    F3 = (float)U3;
+    F4 = (float)U4;
+    F5 = (float)U5;
+  }
 };
 
 template <typename T>
@@ -55,10 +65,17 @@ __device__ __forceinline__ V2<T> v2(T u, T v) {
   return r;
 }
 
+// Single-precision callers read the pre-rounded invariants: a double-to-float
+// conversion per element would run at the (low) FP64 rate.
 template <typename T>
 __device__ __forceinline__ Coef<T> coef_from_trig(const Invariants& U, T c2, T s2, T c4, T s4) {
   Coef<T> c;
-  const T u1 = (T)U.U1, u2 = (T)U.U2, u3 = (T)U.U3, u4 = (T)U.U4, u5 = (T)U.U5;
+  T u1, u2, u3, u4, u5;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    u1 = U.F1; u2 = U.F2; u3 = U.F3; u4 = U.F4; u5 = U.F5;
+  } else {
+    u1 = U.U1; u2 = U.U2; u3 = U.U3; u4 = U.U4; u5 = U.U5;
+  }
   c.c11 = u1 + u2 * c2 + u3 * c4;
   c.c22 = u1 - u2 * c2 + u3 * c4;
   c.c12 = u4 - u3 * c4;
@@ -80,6 +97,12 @@ __device__ __forceinline__ void trig4(T theta, T* c2, T* s2, T* c4, T* s4) {
   *s2 = s;
   *c4 = (T)2 * c * c - (T)1;
   *s4 = (T)2 * s * c;
+}
+
+// From the pair (cos 2t, sin 2t) stored per element of the finest mesh.
+template <typename T>
+__device__ __forceinline__ Coef<T> coef_from_trig2(const Invariants& U, T c2, T s2) {
+  return coef_from_trig(U, c2, s2, (T)2 * c2 * c2 - (T)1, (T)2 * s2 * c2);
 }
 
 template <typename T>

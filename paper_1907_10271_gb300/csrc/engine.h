@@ -16,9 +16,15 @@ cudaError_t launch_kl_coefficients(uint64_t seed, int level, uint64_t first_id, 
                                    const uint64_t* ids, int64_t n, int n_kl, double* xi, float* xi32, int* fail,
                                    cudaStream_t st);
 
+// theta = Xi B^T; with trig2 set, writes (cos 2 theta, sin 2 theta) per element
+// ([nsamp][n_el][2]) instead of theta ([nsamp][n_el]).
 template <typename T>
 cudaError_t launch_kl_synthesis(const T* xi, const T* basis, int64_t nsamp, int n_el, int n_kl,
-                                T* theta, cudaStream_t st);
+                                T* out, bool trig2, cudaStream_t st);
+
+// (cos 2 theta, sin 2 theta) of given angles (double input).
+template <typename T>
+cudaError_t launch_theta_to_trig2(const double* theta, int64_t n, T* trig2, cudaStream_t st);
 
 // ---------------------------------------------------------------- KL basis (host)
 struct KLBasis {
@@ -37,7 +43,7 @@ template <typename T>
 struct SolveGroup {
   int mesh_level;      // MLMC mesh index
   int64_t nsamp;
-  const T* theta;      // [nsamp][n_el] device
+  const T* trig2;      // [nsamp][n_el][2] device: cos 2 theta, sin 2 theta per element
   double* q;           // [nsamp][2] device output
   int* status;         // [nsamp] device output
   int* iters;          // [nsamp] device output (total PCG iterations)
@@ -49,6 +55,6 @@ template <typename T>
 mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups);
 
 template <typename T>
-mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* theta, const T* p, T* q);
+mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* trig2, const T* p, T* q);
 
 }  // namespace mlmc

@@ -69,18 +69,33 @@ __device__ __forceinline__ V2<T> shfl_up2(V2<T> a) {
   return v2<T>(__shfl_up_sync(0xffffffffu, a.u, 1), __shfl_up_sync(0xffffffffu, a.v, 1));
 }
 
+// Per-lane sum of one chunk's row products: compensated in float for the FP32 kernels
+// (at most kRowChunk + 1 terms per lane, no double-precision arithmetic per node),
+// plain double for the FP64 kernels. The warp and cross-warp sums are in double.
+template <typename T>
+struct LaneSum;
+template <>
+struct LaneSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <>
+struct LaneSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
-}
-
-template <typename T>
-__device__ __forceinline__ Coef<T> load_coef(const Invariants& U, const View<T>& V, int64_t ebase, int i, int j) {
-  const int64_t e = ebase + (int64_t)j * V.g.nx + i;
-  if (V.theta) return coef_from_theta<T>(U, V.theta[e]);
-  const T* t = V.trig + 4 * e;
-  return coef_from_trig<T>(U, t[0], t[1], t[2], t[3]);
 }
 
 // Locate the view and tile of this warp.
@@ -99,7 +114,30 @@ __device__ __forceinline__ bool find_tile(const ViewList<T>& L, int gw, int& vi,
   return s < V.nsamp;
 }
 
-template <typename T, typename Op>
+template <typename T>
+struct Vec4T {
+  T x, y, z, w;
+};
+
+__device__ __forceinline__ Vec4T<float> ld4(const float* p) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  return Vec4T<float>{t.x, t.y, t.z, t.w};
+}
+__device__ __forceinline__ Vec4T<double> ld4(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  return Vec4T<double>{a.x, a.y, b.x, b.y};
+}
+
+// Raw element data of one element: the angle (top level) or the averaged trig 4-vector.
+template <typename T>
+struct RawE {
+  T a, b, c, d;
+};
+
+// Walks the warp's strip up its chunk of node rows. Node-row data is prefetched P
+// rows ahead into a register ring (static indices after unrolling), element data P
+// element rows ahead, so each warp keeps P rows of loads in flight.
+template <typename T, int P, typename Op>
 __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V, int strip, int chunk, Op& op) {
   const int lane = threadIdx.x & (kWarp - 1);
   const int nx = V.g.nx, ny = V.g.ny;
@@ -107,55 +145,105 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
   const bool col_in = (i >= 0) && (i <= nx);
   const bool elem = (i >= 0) && (i < nx) && (lane < kWarp - 1);
   const bool out_col = col_in && lane >= 1 && lane <= kStripCols;
+  const int ic = min(max(i, 0), nx);       // in-bounds column for (discarded) loads of outside lanes
+  const int ie = min(max(i, 0), nx - 1);
   const int j0 = chunk * kRowChunk;
   const int j1 = min(j0 + kRowChunk - 1, ny);
   const int er0 = max(j0 - 1, 0);
   const int er1 = min(j1, ny - 1);
   const T rx = (T)V.g.rx, ry = (T)V.g.ry, w = (T)V.g.w;
-  V2<T> pb = col_in ? op.in(i, er0) : zero2<T>();
-  op.shift();
-  V2<T> acc = zero2<T>();
-  for (int er = er0; er <= er1; ++er) {
-    const V2<T> pt = col_in ? op.in(i, er + 1) : zero2<T>();
-    const V2<T> pbr = shfl_down2(pb), ptr = shfl_down2(pt);
-    V2<T> o1 = zero2<T>(), o2 = zero2<T>(), o3 = zero2<T>(), o4 = zero2<T>();
-    if (elem) {
-      const Coef<T> C = op.coef(U, i, er);
-      element_apply<T>(C, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
-    }
-    V2<T> fb = shfl_up2(o2), ft = shfl_up2(o3);
-    if (lane == 0) {
-      fb = zero2<T>();
-      ft = zero2<T>();
-    }
-    acc.u += o1.u + fb.u;
-    acc.v += o1.v + fb.v;
-    if (er >= j0 && out_col) op.out(i, er, acc);
-    acc.u = o4.u + ft.u;
-    acc.v = o4.v + ft.v;
+  typename Op::Raw ring[P];
+  RawE<typename Op::E> ering[P];
+  V2<T> pb;
+  {
+    const typename Op::Raw r0 = op.load(ic, er0);
+    pb = col_in ? op.in(r0, i, er0) : zero2<T>();
     op.shift();
-    pb = pt;
+  }
+#pragma unroll
+  for (int u = 0; u < P; ++u) {
+    if (er0 + 1 + u <= er1 + 1) ring[u] = op.load(ic, er0 + 1 + u);
+    if (er0 + u <= er1) ering[u] = op.loadE(ie, er0 + u);
+  }
+  V2<T> acc = zero2<T>();
+  for (int base = er0; base <= er1; base += P) {
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const int er = base + u;
+      if (er <= er1) {
+        const typename Op::Raw cur = ring[u];
+        const RawE<typename Op::E> ce = ering[u];
+        if (er + 1 + P <= er1 + 1) ring[u] = op.load(ic, er + 1 + P);
+        if (er + P <= er1) ering[u] = op.loadE(ie, er + P);
+        const V2<T> pt = col_in ? op.in(cur, i, er + 1) : zero2<T>();
+        const V2<T> pbr = shfl_down2(pb), ptr = shfl_down2(pt);
+        V2<T> o1 = zero2<T>(), o2 = zero2<T>(), o3 = zero2<T>(), o4 = zero2<T>();
+        if (elem) {
+          const Coef<T> C = op.coef(U, ce);
+          element_apply<T>(C, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
+        }
+        V2<T> fb = shfl_up2(o2), ft = shfl_up2(o3);
+        if (lane == 0) {
+          fb = zero2<T>();
+          ft = zero2<T>();
+        }
+        acc.u += o1.u + fb.u;
+        acc.v += o1.v + fb.v;
+        if (er >= j0 && out_col) op.out(i, er, acc);
+        acc.u = o4.u + ft.u;
+        acc.v = o4.v + ft.v;
+        op.shift();
+        pb = pt;
+      }
+    }
   }
   // the top boundary row (only element row ny - 1 contributes) belongs to the chunk that owns it
   if (er1 + 1 == ny && ny >= j0 && ny <= j1 && out_col) op.out(i, ny, acc);
 }
 
 // ---------------------------------------------------------------- operand handlers
+// Each handler provides: Raw load(i, j) (node data of row j, prefetched), in(raw, i, j)
+// (value K is applied to; keeps what out() needs), out(i, j, K x), shift() (row
+// advance), loadE / coef (element data), live() and finish() (reductions).
 
 template <typename T>
 struct OpBase {
+  using E = T;
+  static constexpr int kP32 = kPrefetch32;   // rows in flight of the FP32 variant
   const View<T>& V;
   int64_t nbase;   // first value of the sample's vectors
   int64_t ebase;   // first element of the sample
-  int nxp;         // nx + 1
-  __device__ OpBase(const View<T>& v, int s)
+  int64_t lane;    // value offset of this lane's node column in row 0
+  int64_t elane;   // element offset of this lane's element column in row 0
+  int rs;          // values per node row
+  __device__ OpBase(const View<T>& v, int s, int ic, int ie)
       : V(v),
         nbase((int64_t)s * 2 * (v.g.nx + 1) * (v.g.ny + 1)),
         ebase((int64_t)s * v.g.nx * v.g.ny),
-        nxp(v.g.nx + 1) {}
-  __device__ __forceinline__ int64_t at(int i, int j) const { return nbase + 2 * ((int64_t)j * nxp + i); }
-  __device__ __forceinline__ Coef<T> coef(const Invariants& U, int i, int j) const {
-    return load_coef<T>(U, V, ebase, i, j);
+        lane((int64_t)s * 2 * (v.g.nx + 1) * (v.g.ny + 1) + 2 * ic),
+        elane((int64_t)s * v.g.nx * v.g.ny + ie),
+        rs(2 * (v.g.nx + 1)) {}
+  // value offset of (own column, row j): every load and store of a lane is in its column
+  __device__ __forceinline__ int64_t at(int, int j) const { return lane + (int64_t)(j * rs); }
+  __device__ __forceinline__ RawE<T> loadE(int, int j) const {
+    const int64_t e = elane + (int64_t)(j * V.g.nx);
+    RawE<T> r;
+    if (V.trig2) {
+      const V2<T> t = ld2(V.trig2 + 2 * e);
+      r.a = t.u;
+      r.b = t.v;
+      r.c = r.d = (T)0;
+    } else {
+      const Vec4T<T> t = ld4(V.trig + 4 * e);
+      r.a = t.x;
+      r.b = t.y;
+      r.c = t.z;
+      r.d = t.w;
+    }
+    return r;
+  }
+  __device__ __forceinline__ Coef<T> coef(const Invariants& U, const RawE<T>& r) const {
+    return V.trig2 ? coef_from_trig2<T>(U, r.a, r.b) : coef_from_trig<T>(U, r.a, r.b, r.c, r.d);
   }
   __device__ __forceinline__ V2<T> mask(int i, V2<T> x) const {
     if (dir_u(i, V.g.nx)) x.u = (T)0;
@@ -166,44 +254,55 @@ struct OpBase {
 
 template <typename T>
 struct OpApply : OpBase<T> {
-  __device__ OpApply(const View<T>& v, int s, const SampleState&) : OpBase<T>(v, s) {}
+  using Raw = V2<T>;
+  __device__ OpApply(const View<T>& v, int s, int ic, int ie, const SampleState&) : OpBase<T>(v, s, ic, ie) {}
   __device__ bool live() const { return true; }
-  __device__ V2<T> in(int i, int j) { return ld2(this->V.a + this->at(i, j)); }
+  __device__ Raw load(int i, int j) const { return ld2(this->V.a + this->at(i, j)); }
+  __device__ V2<T> in(const Raw& r, int, int) { return r; }
   __device__ void out(int i, int j, V2<T> kp) { st2(this->V.o0 + this->at(i, j), kp); }
   __device__ void shift() {}
   __device__ void finish(const SampleState&, int) {}
 };
 
-// a = r (old), b = q, c = p, winvd; o0 = x (updated in place), o1 = r (new), o2 = r1.
+// a = r (old), b = q, c = p, winvd, o0 = x (read and updated); o1 = r (new), o2 = r1.
 template <typename T>
 struct OpPreTop : OpBase<T> {
+  struct Raw {
+    V2<T> r, q, w, x, p;
+  };
+  struct Aux {
+    V2<T> r, x, p;
+  };
   T alpha;
   bool act;
-  V2<T> rt, rb;
-  double rr = 0.0;
-  __device__ OpPreTop(const View<T>& v, int s, const SampleState& S) : OpBase<T>(v, s) {
+  Aux at_, ab_;
+  LaneSum<T> rr;
+  __device__ OpPreTop(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
     act = S.active[v.sbase + s] != 0;
     alpha = (T)S.alpha[v.sbase + s];
   }
   __device__ bool live() const { return act; }
-  __device__ V2<T> in(int i, int j) {
+  __device__ Raw load(int i, int j) const {
     const int64_t k = this->at(i, j);
-    const V2<T> r = ld2(this->V.a + k), q = ld2(this->V.b + k), wd = ld2(this->V.winvd + k);
-    rt = v2<T>(r.u - alpha * q.u, r.v - alpha * q.v);
-    return v2<T>(wd.u * rt.u, wd.v * rt.v);
+    return Raw{ld2(this->V.a + k), ld2(this->V.b + k), ld2(this->V.winvd + k), ld2(this->V.o0 + k),
+               ld2(this->V.c + k)};
+  }
+  __device__ V2<T> in(const Raw& R, int, int) {
+    at_.r = v2<T>(R.r.u - alpha * R.q.u, R.r.v - alpha * R.q.v);
+    at_.x = R.x;
+    at_.p = R.p;
+    return v2<T>(R.w.u * at_.r.u, R.w.v * at_.r.v);
   }
   __device__ void out(int i, int j, V2<T> kx) {
     const int64_t k = this->at(i, j);
-    const V2<T> r1 = this->mask(i, v2<T>(rb.u - kx.u, rb.v - kx.v));
-    st2(this->V.o2 + k, r1);
-    st2(this->V.o1 + k, rb);
-    const V2<T> x = ld2(this->V.o0 + k), p = ld2(this->V.c + k);
-    st2(this->V.o0 + k, v2<T>(x.u + alpha * p.u, x.v + alpha * p.v));
-    rr += (double)rb.u * rb.u + (double)rb.v * rb.v;
+    st2(this->V.o2 + k, this->mask(i, v2<T>(ab_.r.u - kx.u, ab_.r.v - kx.v)));
+    st2(this->V.o1 + k, ab_.r);
+    st2(this->V.o0 + k, v2<T>(ab_.x.u + alpha * ab_.p.u, ab_.x.v + alpha * ab_.p.v));
+    rr.add(ab_.r.u * ab_.r.u + ab_.r.v * ab_.r.v);
   }
-  __device__ void shift() { rb = rt; }
+  __device__ void shift() { ab_ = at_; }
   __device__ void finish(const SampleState& S, int s) {
-    const double t = warp_sum(rr);
+    const double t = warp_sum(rr.value());
     if ((threadIdx.x & 31) == 0) atomicAdd(&S.red_rr[this->V.sbase + s], t);
   }
 };
@@ -211,17 +310,22 @@ struct OpPreTop : OpBase<T> {
 // a = b, winvd; o2 = r1.
 template <typename T>
 struct OpPre : OpBase<T> {
+  struct Raw {
+    V2<T> b, w;
+  };
   bool act;
   V2<T> bt, bb;
-  __device__ OpPre(const View<T>& v, int s, const SampleState& S) : OpBase<T>(v, s) {
+  __device__ OpPre(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
     act = S.active[v.sbase + s] != 0;
   }
   __device__ bool live() const { return act; }
-  __device__ V2<T> in(int i, int j) {
+  __device__ Raw load(int i, int j) const {
     const int64_t k = this->at(i, j);
-    bt = ld2(this->V.a + k);
-    const V2<T> wd = ld2(this->V.winvd + k);
-    return v2<T>(wd.u * bt.u, wd.v * bt.v);
+    return Raw{ld2(this->V.a + k), ld2(this->V.winvd + k)};
+  }
+  __device__ V2<T> in(const Raw& R, int, int) {
+    bt = R.b;
+    return v2<T>(R.w.u * R.b.u, R.w.v * R.b.v);
   }
   __device__ void out(int i, int j, V2<T> kx) {
     st2(this->V.o2 + this->at(i, j), this->mask(i, v2<T>(bb.u - kx.u, bb.v - kx.v)));
@@ -233,25 +337,35 @@ struct OpPre : OpBase<T> {
 // a = b, xc (level below), winvd; o0 = z.  TOP also reduces b . z.
 template <typename T, bool TOP>
 struct OpPost : OpBase<T> {
+  static constexpr int kP32 = 2;   // larger row records (coarse values)
+  struct Raw {
+    V2<T> b, w;
+  };
   bool act;
   int nxc;
   int64_t cbase;
   V2<T> bt, bb, xt, xb, wt, wb;
-  double rz = 0.0;
-  __device__ OpPost(const View<T>& v, int s, const SampleState& S) : OpBase<T>(v, s) {
+  LaneSum<T> rz;
+  __device__ OpPost(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
     act = S.active[v.sbase + s] != 0;
     nxc = v.g.nx / 2;
     cbase = (int64_t)s * 2 * (nxc + 1) * (v.g.ny / 2 + 1);
   }
   __device__ bool live() const { return act; }
   __device__ V2<T> coarse(int I, int J) const { return ld2(this->V.xc + cbase + 2 * ((int64_t)J * (nxc + 1) + I)); }
-  __device__ V2<T> prolong(int i, int j) const {
+  __device__ Raw load(int i, int j) const {
+    const int64_t k = this->at(i, j);
+    return Raw{ld2(this->V.a + k), ld2(this->V.winvd + k)};
+  }
+  // bilinear prolongation of the coarse correction; the coarse vector is a quarter of
+  // the fine one and each value serves up to four neighbouring fine nodes (L1 hits)
+  __device__ V2<T> in(const Raw& R, int i, int j) {
     const int I = i >> 1, J = j >> 1;
     const bool fi = i & 1, fj = j & 1;
-    V2<T> x = coarse(I, J);
+    V2<T> c = coarse(I, J);
     if (fi) {
       const V2<T> r = coarse(I + 1, J);
-      x = v2<T>(x.u + r.u, x.v + r.v);
+      c = v2<T>(c.u + r.u, c.v + r.v);
     }
     if (fj) {
       V2<T> t = coarse(I, J + 1);
@@ -259,23 +373,18 @@ struct OpPost : OpBase<T> {
         const V2<T> tr = coarse(I + 1, J + 1);
         t = v2<T>(t.u + tr.u, t.v + tr.v);
       }
-      x = v2<T>(x.u + t.u, x.v + t.v);
+      c = v2<T>(c.u + t.u, c.v + t.v);
     }
     const T f = (fi && fj) ? (T)0.25 : ((fi || fj) ? (T)0.5 : (T)1);
-    return v2<T>(f * x.u, f * x.v);
-  }
-  __device__ V2<T> in(int i, int j) {
-    const int64_t k = this->at(i, j);
-    bt = ld2(this->V.a + k);
-    wt = ld2(this->V.winvd + k);
-    const V2<T> pc = prolong(i, j);
-    xt = v2<T>(wt.u * bt.u + pc.u, wt.v * bt.v + pc.v);
+    bt = R.b;
+    wt = R.w;
+    xt = v2<T>(R.w.u * R.b.u + f * c.u, R.w.v * R.b.v + f * c.v);
     return xt;
   }
   __device__ void out(int i, int j, V2<T> kx) {
     const V2<T> z = this->mask(i, v2<T>(xb.u + wb.u * (bb.u - kx.u), xb.v + wb.v * (bb.v - kx.v)));
     st2(this->V.o0 + this->at(i, j), z);
-    if (TOP) rz += (double)bb.u * z.u + (double)bb.v * z.v;
+    if (TOP) rz.add(bb.u * z.u + bb.v * z.v);
   }
   __device__ void shift() {
     bb = bt;
@@ -284,7 +393,7 @@ struct OpPost : OpBase<T> {
   }
   __device__ void finish(const SampleState& S, int s) {
     if (TOP) {
-      const double t = warp_sum(rz);
+      const double t = warp_sum(rz.value());
       if ((threadIdx.x & 31) == 0) atomicAdd(&S.red_rz[this->V.sbase + s], t);
     }
   }
@@ -293,19 +402,24 @@ struct OpPost : OpBase<T> {
 // a = z, b = p (old); o0 = p (new), o1 = q.
 template <typename T>
 struct OpPcgP : OpBase<T> {
+  struct Raw {
+    V2<T> z, p;
+  };
   bool act;
   T beta;
   V2<T> pt, pb;
-  double pq = 0.0;
-  __device__ OpPcgP(const View<T>& v, int s, const SampleState& S) : OpBase<T>(v, s) {
+  LaneSum<T> pq;
+  __device__ OpPcgP(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
     act = S.active[v.sbase + s] != 0;
     beta = (T)S.beta[v.sbase + s];
   }
   __device__ bool live() const { return act; }
-  __device__ V2<T> in(int i, int j) {
+  __device__ Raw load(int i, int j) const {
     const int64_t k = this->at(i, j);
-    const V2<T> z = ld2(this->V.a + k), p = ld2(this->V.b + k);
-    pt = v2<T>(z.u + beta * p.u, z.v + beta * p.v);
+    return Raw{ld2(this->V.a + k), ld2(this->V.b + k)};
+  }
+  __device__ V2<T> in(const Raw& R, int, int) {
+    pt = v2<T>(R.z.u + beta * R.p.u, R.z.v + beta * R.p.v);
     return pt;
   }
   __device__ void out(int i, int j, V2<T> kp) {
@@ -313,32 +427,79 @@ struct OpPcgP : OpBase<T> {
     const V2<T> q = this->mask(i, kp);
     st2(this->V.o0 + k, pb);
     st2(this->V.o1 + k, q);
-    pq += (double)pb.u * q.u + (double)pb.v * q.v;
+    pq.add(pb.u * q.u + pb.v * q.v);
   }
   __device__ void shift() { pb = pt; }
   __device__ void finish(const SampleState& S, int s) {
-    const double t = warp_sum(pq);
+    const double t = warp_sum(pq.value());
     if ((threadIdx.x & 31) == 0) atomicAdd(&S.red_pq[this->V.sbase + s], t);
   }
 };
 
-// Refinement residual in double: a = d; ext0 = angles (TI); ext1 = r output (TI).
+// Residual of the lifting d0 (u = -shortening on x = lx, zero elsewhere, generated
+// in registers) in the inner precision: o0 = r = -(K d0) on free DOFs; ||r||^2 into
+// rr64 and the reaction sum of (K d0)_u on x = lx into react. The refinement's first
+// double-precision residual supersedes it, so inner precision suffices here.
+template <typename T>
+struct OpResidInit : OpBase<T> {
+  struct Raw {};
+  bool act;
+  T shortening;
+  double rr = 0.0, react = 0.0;
+  __device__ OpResidInit(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
+    act = S.outer_active[v.sbase + s] != 0;
+    shortening = (T)v.param;
+  }
+  __device__ bool live() const { return act; }
+  __device__ Raw load(int, int) const { return Raw{}; }
+  __device__ V2<T> in(const Raw&, int i, int) { return v2<T>(i == this->V.g.nx ? -shortening : (T)0, (T)0); }
+  __device__ void out(int i, int j, V2<T> kd) {
+    const V2<T> r = this->mask(i, v2<T>(-kd.u, -kd.v));
+    st2(this->V.o0 + this->at(i, j), r);
+    rr += (double)r.u * r.u + (double)r.v * r.v;
+    if (i == this->V.g.nx) react += (double)kd.u;
+  }
+  __device__ void shift() {}
+  __device__ void finish(const SampleState& S, int s) {
+    const double t = warp_sum(rr), u = warp_sum(react);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&S.rr64[this->V.sbase + s], t);
+      atomicAdd(&S.react[this->V.sbase + s], u);
+    }
+  }
+};
+
+// Refinement residual in double: a = d; ext0 = trig2 (TI); ext1 = r output (TI).
+// The rotated stiffness is formed in TI from the TI trig2 pair, as in the inner
+// solve, so both use one operator; its arithmetic is double.
 template <typename TI>
 struct OpResid : OpBase<double> {
+  using E = TI;
+  using Raw = V2<double>;
   bool act;
   const TI* th;
   TI* r;
   double rr = 0.0, react = 0.0;
-  __device__ OpResid(const View<double>& v, int s, const SampleState& S) : OpBase<double>(v, s) {
+  __device__ OpResid(const View<double>& v, int s, int ic, int ie, const SampleState& S) : OpBase<double>(v, s, ic, ie) {
     act = S.outer_active[v.sbase + s] != 0;
     th = static_cast<const TI*>(v.ext0);
     r = static_cast<TI*>(v.ext1);
   }
   __device__ bool live() const { return act; }
-  __device__ Coef<double> coef(const Invariants& U, int i, int j) const {
-    return coef_from_theta<double>(U, (double)th[ebase + (int64_t)j * V.g.nx + i]);
+  __device__ RawE<TI> loadE(int, int j) const {
+    RawE<TI> e;
+    const V2<TI> t = ld2(th + 2 * (elane + (int64_t)(j * V.g.nx)));
+    e.a = t.u;
+    e.b = t.v;
+    e.c = e.d = (TI)0;
+    return e;
   }
-  __device__ V2<double> in(int i, int j) { return ld2(V.a + at(i, j)); }
+  __device__ Coef<double> coef(const Invariants& U, const RawE<TI>& e) const {
+    const Coef<TI> c = coef_from_trig2<TI>(U, e.a, e.b);
+    return Coef<double>{(double)c.c11, (double)c.c12, (double)c.c16, (double)c.c22, (double)c.c26, (double)c.c66};
+  }
+  __device__ Raw load(int i, int j) const { return ld2(V.a + at(i, j)); }
+  __device__ V2<double> in(const Raw& d, int, int) { return d; }
   __device__ void out(int i, int j, V2<double> kd) {
     const V2<double> res = mask(i, v2<double>(-kd.u, -kd.v));
     const int64_t k = at(i, j);
@@ -357,21 +518,22 @@ struct OpResid : OpBase<double> {
   }
 };
 
-template <typename T, typename Op>
+template <typename T, int P, typename Op>
 __global__ void __launch_bounds__(kWarpsPerBlock * kWarp)
     k_strip(const __grid_constant__ ViewList<T> L, SampleState S) {
   const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   int vi, s, strip, chunk;
   if (!find_tile(L, gw, vi, s, strip, chunk)) return;
   const View<T>& V = L.v[vi];
-  Op op(V, s, S);
+  const int col = strip * kStripCols - 1 + (int)(threadIdx.x & 31);
+  Op op(V, s, min(max(col, 0), V.g.nx), min(max(col, 0), V.g.nx - 1), S);
   if (!op.live()) return;
   if (S.units && (threadIdx.x & 31) == 0) {
     const int c0 = max(strip * kStripCols, 0), c1 = min(strip * kStripCols + kStripCols - 1, V.g.nx);
     const int r0 = chunk * kRowChunk, r1 = min(r0 + kRowChunk - 1, V.g.ny);
     atomicAdd(&S.units[L.prof_op], (unsigned long long)((c1 - c0 + 1) * (r1 - r0 + 1)));
   }
-  strip_loop<T>(L.U, V, strip, chunk, op);
+  strip_loop<T, P>(L.U, V, strip, chunk, op);
   op.finish(S, s);
 }
 
@@ -424,7 +586,7 @@ __global__ void k_restrict(const __grid_constant__ ViewList<T> L, SampleState S)
 }
 
 // Coarse element data: o0 = trig (coarse, 4 per element) from the fine level's
-// theta or trig (view geometry = fine level). One thread per coarse element.
+// trig2 or trig (view geometry = fine level). One thread per coarse element.
 template <typename T>
 __global__ void k_trig_average(const __grid_constant__ ViewList<T> L) {
   int vi;
@@ -442,8 +604,11 @@ __global__ void k_trig_average(const __grid_constant__ ViewList<T> L) {
     for (int a = 0; a < 2; ++a) {
       const int64_t fe = (int64_t)s * nx * ny + (int64_t)(2 * J + b) * nx + (2 * I + a);
       T t4[4];
-      if (V.theta) {
-        trig4<T>(V.theta[fe], &t4[0], &t4[1], &t4[2], &t4[3]);
+      if (V.trig2) {
+        t4[0] = V.trig2[2 * fe];
+        t4[1] = V.trig2[2 * fe + 1];
+        t4[2] = (T)2 * t4[0] * t4[0] - (T)1;
+        t4[3] = (T)2 * t4[1] * t4[0];
       } else {
         for (int c = 0; c < 4; ++c) t4[c] = V.trig[4 * fe + c];
       }
@@ -477,8 +642,8 @@ __global__ void k_invdiag(const __grid_constant__ ViewList<T> L) {
     if (ei[k] < 0 || ei[k] >= nx || ej[k] < 0 || ej[k] >= ny) continue;
     Coef<T> C;
     const int64_t e = eb + (int64_t)ej[k] * nx + ei[k];
-    if (V.theta) {
-      C = coef_from_theta<T>(L.U, V.theta[e]);
+    if (V.trig2) {
+      C = coef_from_trig2<T>(L.U, V.trig2[2 * e], V.trig2[2 * e + 1]);
     } else {
       C = coef_from_trig<T>(L.U, V.trig[4 * e], V.trig[4 * e + 1], V.trig[4 * e + 2], V.trig[4 * e + 3]);
     }
@@ -516,8 +681,8 @@ __global__ void __launch_bounds__(256) k_coarsest_setup(const __grid_constant__ 
       for (int ei = 0; ei < nx; ++ei) {
         const int64_t e = (int64_t)s * nx * ny + (int64_t)ej * nx + ei;
         Coef<double> C;
-        if (V.theta) {
-          C = coef_from_theta<double>(L.U, (double)V.theta[e]);
+        if (V.trig2) {
+          C = coef_from_trig2<double>(L.U, (double)V.trig2[2 * e], (double)V.trig2[2 * e + 1]);
         } else {
           C = coef_from_trig<double>(L.U, (double)V.trig[4 * e], (double)V.trig[4 * e + 1],
                                      (double)V.trig[4 * e + 2], (double)V.trig[4 * e + 3]);
@@ -623,7 +788,7 @@ __global__ void k_lift(const __grid_constant__ ViewList<double> L, double shorte
 }
 
 // Fibre-direction compressive stress at centroids in [x0, x1]: a = d (double),
-// ext0 = angles (TI). Max into qoi[2 s + 1] through the ordered bit pattern of
+// ext0 = trig2 (TI). Max into qoi[2 s + 1] through the ordered bit pattern of
 // non-negative doubles. One thread per element.
 template <typename TI>
 __global__ void k_stress(const __grid_constant__ ViewList<double> L, SampleState S, double x0, double x1,
@@ -648,17 +813,67 @@ __global__ void k_stress(const __grid_constant__ ViewList<double> L, SampleState
   const double av = (v2_ - v1) + (v3 - v4), bv = (v4 - v1) + (v3 - v2_);
   const double rx = V.g.rx, ry = V.g.ry;
   const double ex = rx * au, ey = ry * bv, exy = ry * bu + rx * av;
-  const double th = (double)static_cast<const TI*>(V.ext0)[(int64_t)s * per + e];
-  const Coef<double> C = coef_from_theta<double>(L.U, th);
+  const TI* t2 = static_cast<const TI*>(V.ext0) + 2 * ((int64_t)s * per + e);
+  const double c2 = (double)t2[0], s2 = (double)t2[1];
+  const Coef<double> C = coef_from_trig2<double>(L.U, c2, s2);
   const double sx = C.c11 * ex + C.c12 * ey + C.c16 * exy;
   const double sy = C.c12 * ex + C.c22 * ey + C.c26 * exy;
   const double sxy = C.c16 * ex + C.c26 * ey + C.c66 * exy;
-  double sn, cs;
-  sincos(th, &sn, &cs);
-  const double s11 = cs * cs * sx + sn * sn * sy + 2.0 * cs * sn * sxy;
+  // fibre-frame normal stress: cos^2 t sx + sin^2 t sy + 2 sin t cos t sxy
+  const double s11 = 0.5 * (1.0 + c2) * sx + 0.5 * (1.0 - c2) * sy + s2 * sxy;
   const double val = fmax(0.0, -s11);
   atomicMax(reinterpret_cast<unsigned long long*>(&S.qoi[2 * (V.sbase + s) + 1]),
             (unsigned long long)__double_as_longlong(val));
+}
+
+template <typename T>
+__global__ void k_take_residual(const __grid_constant__ ViewList<T> L, SampleState S) {
+  int vi;
+  int64_t loc;
+  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
+  const View<T>& V = L.v[vi];
+  const int64_t per = 2 * (int64_t)(V.g.nx + 1) * (V.g.ny + 1);
+  const int s = (int)(loc / per);
+  if (s >= V.nsamp) return;
+  const int t = V.sbase + s;
+  if (!S.outer_active[t] || S.rpar[t] == 0) return;
+  V.o0[loc] = V.a[loc];
+}
+
+template <typename T>
+__global__ void k_react_delta(const __grid_constant__ ViewList<T> L, SampleState S) {
+  int vi;
+  int64_t loc;
+  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
+  const View<T>& V = L.v[vi];
+  const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
+  const int s = (int)(loc / ny);
+  if (s >= V.nsamp) return;
+  const int t = V.sbase + s;
+  if (!S.outer_active[t]) return;
+  const int j = (int)(loc - (int64_t)s * ny), i = nx - 1;
+  const T* x = V.a + (int64_t)s * 2 * nxp * (ny + 1);
+  auto node = [&](int ii, int jj) { return v2<T>(x[2 * (jj * nxp + ii)], x[2 * (jj * nxp + ii) + 1]); };
+  const int64_t e = (int64_t)s * nx * ny + (int64_t)j * nx + i;
+  const Coef<T> C = V.trig2 ? coef_from_trig2<T>(L.U, V.trig2[2 * e], V.trig2[2 * e + 1])
+                            : coef_from_trig<T>(L.U, V.trig[4 * e], V.trig[4 * e + 1], V.trig[4 * e + 2],
+                                                V.trig[4 * e + 3]);
+  V2<T> o1, o2, o3, o4;
+  element_apply<T>(C, (T)V.g.rx, (T)V.g.ry, (T)V.g.w, node(i, j), node(i + 1, j), node(i + 1, j + 1), node(i, j + 1),
+                   o1, o2, o3, o4);
+  atomicAdd(&S.react[t], (double)o2.u + (double)o3.u);
+}
+
+__global__ void k_inner_end(SampleState S, int total, int recursive) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total || !S.outer_active[t]) return;
+  if (S.active[t]) {   // iteration cap reached
+    S.active[t] = 0;
+    S.status[t] = MLMC_ERR_NOT_CONVERGED;
+    S.outer_active[t] = 0;
+    return;
+  }
+  if (recursive) S.rr64[t] = S.red_rr[t];
 }
 
 // ---------------------------------------------------------------- per-sample scalars
@@ -666,6 +881,7 @@ __global__ void k_stress(const __grid_constant__ ViewList<double> L, SampleState
 __global__ void k_after_post(SampleState S, int total, int iter) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total || !S.active[t]) return;
+  S.rpar[t] = (iter + 1) & 1;   // PreTop of this iteration wrote r' to buffer (iter + 1) & 1
   const double rr = S.red_rr[t];
   if (rr <= S.tol2[t] * S.rr_ref[t]) {
     S.active[t] = 0;
@@ -713,7 +929,6 @@ __global__ void k_outer_check(SampleState S, int total, double rtol, double floo
   const double rr = S.rr64[t];
   S.qoi[2 * t] = -S.react[t];
   S.rr64[t] = 0.0;
-  S.react[t] = 0.0;
   const double target = rtol * rtol * S.rrf[t];
   if (rr <= target || S.status[t] != 0) {
     S.outer_active[t] = 0;
@@ -740,7 +955,8 @@ template <typename T, typename Op>
 cudaError_t launch_strip_op(const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st) {
   if (total_warps <= 0) return cudaSuccess;
   const int blocks = (total_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  k_strip<T, Op><<<blocks, kWarpsPerBlock * kWarp, 0, st>>>(L, S);
+  constexpr int P = sizeof(T) == 4 ? Op::kP32 : kPrefetch64;
+  k_strip<T, P, Op><<<blocks, kWarpsPerBlock * kWarp, 0, st>>>(L, S);
   return cudaGetLastError();
 }
 
@@ -757,6 +973,7 @@ cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int to
     case StripOp::Post: return launch_strip_op<T, OpPost<T, false>>(L, S, total_warps, st);
     case StripOp::PostTop: return launch_strip_op<T, OpPost<T, true>>(L, S, total_warps, st);
     case StripOp::PcgP: return launch_strip_op<T, OpPcgP<T>>(L, S, total_warps, st);
+    case StripOp::ResidInit: return launch_strip_op<T, OpResidInit<T>>(L, S, total_warps, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -822,6 +1039,25 @@ cudaError_t launch_stress(const ViewList<double>& L, SampleState S, double x0, d
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_take_residual(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st) {
+  if (total_threads <= 0) return cudaSuccess;
+  k_take_residual<T><<<blocks_for(total_threads, 256), 256, 0, st>>>(L, S);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_react_delta(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st) {
+  if (total_threads <= 0) return cudaSuccess;
+  k_react_delta<T><<<blocks_for(total_threads, 128), 128, 0, st>>>(L, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inner_end(SampleState S, int total, int recursive, cudaStream_t st) {
+  k_inner_end<<<blocks_for(total, 256), 256, 0, st>>>(S, total, recursive);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_after_post(SampleState S, int total, int iter, cudaStream_t st) {
   k_after_post<<<blocks_for(total, 256), 256, 0, st>>>(S, total, iter);
   return cudaGetLastError();
@@ -851,6 +1087,8 @@ cudaError_t launch_outer_check(SampleState S, int total, double rtol, double flo
   template cudaError_t launch_coarsest_setup<T>(const ViewList<T>&, int, cudaStream_t);                    \
   template cudaError_t launch_coarsest_solve<T>(const ViewList<T>&, SampleState, int, cudaStream_t);       \
   template cudaError_t launch_update_d<T>(const ViewList<T>&, SampleState, int, cudaStream_t);             \
+  template cudaError_t launch_take_residual<T>(const ViewList<T>&, SampleState, int, cudaStream_t);        \
+  template cudaError_t launch_react_delta<T>(const ViewList<T>&, SampleState, int, cudaStream_t);          \
   template cudaError_t launch_resid64<T>(const ViewList<double>&, SampleState, int, cudaStream_t);         \
   template cudaError_t launch_stress<T>(const ViewList<double>&, SampleState, double, double, double, int, \
                                         cudaStream_t);

@@ -8,8 +8,9 @@ constexpr int kMaxViews = 12;
 
 // One multigrid level of one solve group, as seen by a kernel. Pointer meaning
 // depends on the kernel (documented at each launcher). Vectors are
-// [nsamp][ny+1][nx+1][2]; element data [nsamp][ny][nx] (theta) or
-// [nsamp][ny][nx][4] (trig = cos 2t, sin 2t, cos 4t, sin 4t).
+// [nsamp][ny+1][nx+1][2]; element data [nsamp][ny][nx][2] on the finest mesh
+// (trig2 = cos 2t, sin 2t of the element's angle) or [nsamp][ny][nx][4] on coarse
+// meshes (trig = child averages of cos 2t, sin 2t, cos 4t, sin 4t).
 template <typename T>
 struct View {
   Geo g;
@@ -18,7 +19,7 @@ struct View {
   int work_begin;   // first warp (strip kernels) or thread (pointwise kernels) of this view
   int nwork;
   int tiles_x, tiles_y;
-  const T* theta;
+  const T* trig2;
   const T* trig;
   const T* a;
   const T* b;
@@ -30,6 +31,7 @@ struct View {
   T* o2;
   const void* ext0; // kernel-specific (e.g. angle array of another precision, dense inverse)
   void* ext1;
+  double param;     // kernel-specific scalar (e.g. the prescribed end shortening)
 };
 
 // Operation ids of the kernel timer (mlmc_profile_get).
@@ -63,11 +65,12 @@ struct SampleState {
   int* iters;         // PCG iterations (all refinement steps)
   int* status;        // 0 ok, MLMC_ERR_NOT_CONVERGED
   int* count;         // [max_iter] active samples after each iteration
+  int* rpar;          // buffer (0/1) holding the latest inner residual
   unsigned long long* units;   // [kProfOps] nodes processed per operation (null: not counted)
 };
 
 // Strip kernels (q = K p family); see fem.cu for the operand conventions.
-enum class StripOp { Apply, PreTop, Pre, Post, PostTop, PcgP };
+enum class StripOp { Apply, PreTop, Pre, Post, PostTop, PcgP, ResidInit };
 
 template <typename T>
 cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st);
@@ -99,6 +102,21 @@ cudaError_t launch_lift(const ViewList<double>& L, double shortening, int total_
 template <typename TI>
 cudaError_t launch_stress(const ViewList<double>& L, SampleState S, double x0, double x1, double lx,
                           int total_threads, cudaStream_t st);
+
+// Moves each sample's final inner residual into r0 (from r1 where it ended there):
+// views at the top level, a = r1, o0 = r0. One thread per value.
+template <typename T>
+cudaError_t launch_take_residual(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st);
+
+// Reaction increment of the correction: react += sum_j (K x)_u at nodes (nx, j), from
+// the last element column only. Views at the top level, a = x. One thread per element row.
+template <typename T>
+cudaError_t launch_react_delta(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st);
+
+// After an inner solve: samples still running hit the iteration cap (not converged);
+// for the others, when `recursive`, ||r||^2 of the new refinement residual is the
+// PCG's last reduced ||r||^2.
+cudaError_t launch_inner_end(SampleState S, int total, int recursive, cudaStream_t st);
 
 cudaError_t launch_after_post(SampleState S, int total, int iter, cudaStream_t st);
 cudaError_t launch_after_p(SampleState S, int total, cudaStream_t st);

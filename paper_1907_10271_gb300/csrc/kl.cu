@@ -14,10 +14,13 @@ namespace {
 
 constexpr int kTE = 64, kTS = 64, kTK = 16;
 
+__device__ __forceinline__ void sincos_any(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_any(double x, double* s, double* c) { sincos(x, s, c); }
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_kl_synthesis(const T* __restrict__ xi, const T* __restrict__ B,
                                                       int64_t nsamp, int n_el, int n_kl,
-                                                      T* __restrict__ theta) {
+                                                      T* __restrict__ theta, bool trig2) {
   __shared__ T Bs[kTK][kTE + 1];
   __shared__ T Xs[kTK][kTS + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -61,25 +64,52 @@ __global__ void __launch_bounds__(256) k_kl_synthesis(const T* __restrict__ xi, 
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const int e = e0 + tx + 16 * a;
-      if (e < n_el) theta[s * n_el + e] = acc[a][b];
+      if (e >= n_el) continue;
+      if (trig2) {
+        T sn, cs;
+        sincos_any((T)2 * acc[a][b], &sn, &cs);
+        theta[2 * (s * n_el + e)] = cs;
+        theta[2 * (s * n_el + e) + 1] = sn;
+      } else {
+        theta[s * n_el + e] = acc[a][b];
+      }
     }
   }
+}
+
+template <typename T>
+__global__ void k_theta_to_trig2(const double* __restrict__ theta, int64_t n, T* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T sn, cs;
+  sincos_any((T)2 * (T)theta[i], &sn, &cs);
+  out[2 * i] = cs;
+  out[2 * i + 1] = sn;
 }
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_kl_synthesis(const T* xi, const T* basis, int64_t nsamp, int n_el, int n_kl,
-                                T* theta, cudaStream_t st) {
+                                T* out, bool trig2, cudaStream_t st) {
   if (nsamp <= 0) return cudaSuccess;
   dim3 grid((n_el + kTE - 1) / kTE, (unsigned)((nsamp + kTS - 1) / kTS));
-  k_kl_synthesis<T><<<grid, 256, 0, st>>>(xi, basis, nsamp, n_el, n_kl, theta);
+  k_kl_synthesis<T><<<grid, 256, 0, st>>>(xi, basis, nsamp, n_el, n_kl, out, trig2);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_kl_synthesis<float>(const float*, const float*, int64_t, int, int, float*,
+template <typename T>
+cudaError_t launch_theta_to_trig2(const double* theta, int64_t n, T* trig2, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_theta_to_trig2<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(theta, n, trig2);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_kl_synthesis<float>(const float*, const float*, int64_t, int, int, float*, bool,
                                                 cudaStream_t);
 template cudaError_t launch_kl_synthesis<double>(const double*, const double*, int64_t, int, int,
-                                                 double*, cudaStream_t);
+                                                 double*, bool, cudaStream_t);
+template cudaError_t launch_theta_to_trig2<float>(const double*, int64_t, float*, cudaStream_t);
+template cudaError_t launch_theta_to_trig2<double>(const double*, int64_t, double*, cudaStream_t);
 
 }  // namespace mlmc

@@ -26,11 +26,6 @@ std::mutex g_static_mu;
 std::map<int, char*> g_static_addr;   // device ordinal -> device address of g_static_scratch
 std::string g_static_error;
 
-__global__ void k_static_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (float)a[i];
-}
-
 bool device_accessible(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -103,6 +98,7 @@ mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, i
     c.U.U3 = (Q11 + Q22 - 2.0 * Q12 - 4.0 * Q66) / 8.0;
     c.U.U4 = (Q11 + Q22 + 6.0 * Q12 - 4.0 * Q66) / 8.0;
     c.U.U5 = (Q11 + Q22 - 2.0 * Q12 + 4.0 * Q66) / 8.0;
+    c.U.round_single();
   }
   // front of the scratch: staged inputs and outputs; the rest: solver workspace
   const mlmc::LevelLayout m = c.mesh(mesh_level);
@@ -112,7 +108,8 @@ mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, i
   front.cap = kStaticScratchBytes;
   front.borrowed = true;
   double* th64 = front.carve<double>(device_accessible(theta) ? 0 : ne);
-  float* th32 = front.carve<float>(c.mixed() ? ne : 0);
+  float* tr32 = front.carve<float>(c.mixed() ? 2 * ne : 0);
+  double* tr64 = front.carve<double>(c.mixed() ? 0 : 2 * ne);
   double* qd = front.carve<double>(device_accessible(q) ? 0 : 2 * n);
   int* sd = front.carve<int>(status && !device_accessible(status) ? n : 0);
   const size_t front_bytes = (front.used + 255) & ~(size_t)255;
@@ -132,12 +129,14 @@ mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, i
   int* s_dev = status ? (device_accessible(status) ? status : sd) : nullptr;
   mlmc_status s;
   if (c.mixed()) {
-    k_static_d2f<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(th_dev, th32, ne);
-    if ((e = cudaGetLastError()) != cudaSuccess) return static_fail(MLMC_ERR_CUDA, cudaGetErrorString(e));
-    std::vector<mlmc::SolveGroup<float>> g{{mesh_level, n, th32, q_dev, s_dev, nullptr}};
+    if ((e = mlmc::launch_theta_to_trig2<float>(th_dev, ne, tr32, st)) != cudaSuccess)
+      return static_fail(MLMC_ERR_CUDA, cudaGetErrorString(e));
+    std::vector<mlmc::SolveGroup<float>> g{{mesh_level, n, tr32, q_dev, s_dev, nullptr}};
     s = mlmc::solve_groups<float>(c, g);
   } else {
-    std::vector<mlmc::SolveGroup<double>> g{{mesh_level, n, th_dev, q_dev, s_dev, nullptr}};
+    if ((e = mlmc::launch_theta_to_trig2<double>(th_dev, ne, tr64, st)) != cudaSuccess)
+      return static_fail(MLMC_ERR_CUDA, cudaGetErrorString(e));
+    std::vector<mlmc::SolveGroup<double>> g{{mesh_level, n, tr64, q_dev, s_dev, nullptr}};
     s = mlmc::solve_groups<double>(c, g);
   }
   if (s == MLMC_ERR_OOM)

@@ -59,7 +59,7 @@ View<T> base_view(const GroupBuf<T>& g, int k) {
   v.tiles_x = strips_of(v.g.nx);
   v.tiles_y = chunks_of(v.g.ny);
   if (k == 0) {
-    v.theta = g.grp->theta;
+    v.trig2 = g.grp->trig2;
   } else {
     v.trig = g.trig[k];
   }
@@ -198,6 +198,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     alloc.template vec<int>(S.iters, total);
     alloc.template vec<int>(S.status, total);
     alloc.template vec<int>(S.count, (size_t)max_iter + 1);
+    alloc.template vec<int>(S.rpar, total);
     alloc.template vec<int>(outer_count, 1);
   };
   SizeAlloc sz;
@@ -419,7 +420,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       v.tiles_y = chunks_of(v.g.ny);
       v.a = g.d;
       v.o0 = g.d;
-      v.ext0 = g.grp->theta;
+      v.ext0 = g.grp->trig2;
       v.ext1 = g.r[0];
       L.v[L.n++] = v;
     }
@@ -456,8 +457,21 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       return ctx.cuda_fail(e, "init");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return ctx.cuda_fail(e, "init");
   }
-  mlmc_status rs = resid();
-  if (rs != MLMC_OK) return rs;
+  // residual of the lifting in the inner precision (the first double-precision
+  // residual, after the first correction, supersedes it)
+  {
+    ViewList<T> L = empty_list<T>(ctx);
+    for (auto& g : G) {
+      View<T> v = base_view(g, 0);
+      v.o0 = g.r[0];
+      v.param = ctx.cfg.shortening;
+      L.v[L.n++] = v;
+    }
+    const int tw = finalize_warps(L);
+    L.prof_op = kProfOther;
+    MLMC_LAUNCH(kProfOther, "resid_init", launch_strip<T>(StripOp::ResidInit, L, S, tw, st));
+  }
+  mlmc_status rs = MLMC_OK;
   MLMC_LAUNCH(kProfOther, "outer_init", launch_outer_init(S, total, st));
 
   const double floor_tol = inner_double ? 1e-14 : ctx.floor_tol32;
@@ -508,6 +522,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       if (h_count == 0) break;
     }
     max_it_seen = std::max(max_it_seen, it);
+    MLMC_LAUNCH(kProfOther, "inner_end", launch_inner_end(S, total, outer > 0 ? 1 : 0, st));
     // d += x, new residual
     {
       ViewList<T> L = empty_list<T>(ctx);
@@ -522,8 +537,33 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       const int tt = finalize_points(L, per);
       MLMC_LAUNCH(kProfOther, "update_d", launch_update_d<T>(L, S, tt, st));
     }
-    rs = resid();
-    if (rs != MLMC_OK) return rs;
+    if (outer == 0) {
+      // the one double-precision residual: f - K d after the first correction
+      if ((e = cudaMemsetAsync(S.react, 0, sizeof(double) * total, st)) != cudaSuccess)
+        return ctx.cuda_fail(e, "memset");
+      rs = resid();
+      if (rs != MLMC_OK) return rs;
+    } else {
+      // later corrections are small: the inner CG's recursive residual (accurate to
+      // unit roundoff times the correction's size) is the new refinement residual
+      ViewList<T> L = empty_list<T>(ctx), R = empty_list<T>(ctx);
+      std::vector<int64_t> per, rows;
+      for (auto& g : G) {
+        View<T> v = base_view(g, 0);
+        v.a = g.r[1];
+        v.o0 = g.r[0];
+        L.v[L.n++] = v;
+        per.push_back(2 * (int64_t)(g.geo[0].nx + 1) * (g.geo[0].ny + 1));
+        View<T> w = base_view(g, 0);
+        w.a = g.x;
+        R.v[R.n++] = w;
+        rows.push_back(g.geo[0].ny);
+      }
+      const int tt = finalize_points(L, per);
+      MLMC_LAUNCH(kProfOther, "take_residual", launch_take_residual<T>(L, S, tt, st));
+      const int tr = finalize_points(R, rows);
+      MLMC_LAUNCH(kProfOther, "react_delta", launch_react_delta<T>(R, S, tr, st));
+    }
   }
   ctx.last_outer = outer;
   ctx.last_iters = max_it_seen;
@@ -577,7 +617,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
 }
 
 template <typename T>
-mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* theta, const T* p, T* q) {
+mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* trig2, const T* p, T* q) {
   ViewList<T> L = empty_list<T>(ctx);
   const LevelLayout m = ctx.mesh(mesh_level);
   View<T> v;
@@ -586,7 +626,7 @@ mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* the
   v.nsamp = (int)n;
   v.tiles_x = strips_of(m.nx);
   v.tiles_y = chunks_of(m.ny);
-  v.theta = theta;
+  v.trig2 = trig2;
   v.a = p;
   v.o0 = q;
   L.v[L.n++] = v;
