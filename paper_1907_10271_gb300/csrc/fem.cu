@@ -21,8 +21,10 @@
 // Homogeneous Dirichlet rows (u, v on x = 0; u on x = lx) are zero in every vector;
 // w D^-1 is stored with zeros there.
 #include <cfloat>
+#include <type_traits>
 
 #include "../../include/mlmc.h"
+#include "dfloat.cuh"
 #include "fem.cuh"
 
 namespace mlmc {
@@ -56,17 +58,52 @@ __device__ __forceinline__ void st2(T* p, V2<T> v) {
 
 template <typename T>
 __device__ __forceinline__ V2<T> zero2() {
-  return v2<T>((T)0, (T)0);
+  return v2<T>(T{}, T{});
 }
+
+__device__ __forceinline__ float shfl_dn(float a) { return __shfl_down_sync(0xffffffffu, a, 1); }
+__device__ __forceinline__ double shfl_dn(double a) { return __shfl_down_sync(0xffffffffu, a, 1); }
+__device__ __forceinline__ DF shfl_dn(DF a) { return shfl_down_df(a, 1); }
+__device__ __forceinline__ float shfl_upv(float a) { return __shfl_up_sync(0xffffffffu, a, 1); }
+__device__ __forceinline__ double shfl_upv(double a) { return __shfl_up_sync(0xffffffffu, a, 1); }
+__device__ __forceinline__ DF shfl_upv(DF a) { return shfl_up_df(a, 1); }
 
 template <typename T>
 __device__ __forceinline__ V2<T> shfl_down2(V2<T> a) {
-  return v2<T>(__shfl_down_sync(0xffffffffu, a.u, 1), __shfl_down_sync(0xffffffffu, a.v, 1));
+  return v2<T>(shfl_dn(a.u), shfl_dn(a.v));
 }
 
 template <typename T>
 __device__ __forceinline__ V2<T> shfl_up2(V2<T> a) {
-  return v2<T>(__shfl_up_sync(0xffffffffu, a.u, 1), __shfl_up_sync(0xffffffffu, a.v, 1));
+  return v2<T>(shfl_upv(a.u), shfl_upv(a.v));
+}
+
+// K_e applied in float-float to float-float corner values, float stiffness: the same
+// steps as element_apply, with every intermediate kept to about 48 bits.
+__device__ __forceinline__ void element_apply_df(const Coef<float>& C, float rx, float ry, float w, V2<DF> n1,
+                                                 V2<DF> n2, V2<DF> n3, V2<DF> n4, V2<DF>& o1, V2<DF>& o2,
+                                                 V2<DF>& o3, V2<DF>& o4) {
+  const DF du21 = n2.u - n1.u, du34 = n3.u - n4.u, du41 = n4.u - n1.u, du32 = n3.u - n2.u;
+  const DF dv21 = n2.v - n1.v, dv34 = n3.v - n4.v, dv41 = n4.v - n1.v, dv32 = n3.v - n2.v;
+  const DF au = du21 + du34, bu = du41 + du32, gu = du34 - du21;
+  const DF av = dv21 + dv34, bv = dv41 + dv32, gv = dv34 - dv21;
+  const DF ex = au * rx, ey = bv * ry, exy = bu * ry + av * rx;
+  const DF sx = ex * C.c11 + ey * C.c12 + exy * C.c16;
+  const DF sy = ex * C.c12 + ey * C.c22 + exy * C.c26;
+  const DF sxy = ex * C.c16 + ey * C.c26 + exy * C.c66;
+  const DF gxi_y = gv * ry, gxi_g = gu * ry, get_x = gu * rx, get_g = gv * rx;
+  const DF sxi_y = gxi_y * C.c22 + gxi_g * C.c26;
+  const DF sxi_g = gxi_y * C.c26 + gxi_g * C.c66;
+  const DF set_x = get_x * C.c11 + get_g * C.c16;
+  const DF set_g = get_x * C.c16 + get_g * C.c66;
+  const float third = (float)(1.0 / 3.0);
+  const DF A = sx * (w * rx), B = sy * (w * ry), Cx = sxy * (w * ry), Cy = sxy * (w * rx);
+  const DF Hu = (sxi_g * ry + set_x * rx) * (w * third);
+  const DF Hv = (sxi_y * ry + set_g * rx) * (w * third);
+  o1.u = Hu - A - Cx;  o1.v = Hv - B - Cy;
+  o2.u = A - Cx - Hu;  o2.v = Cy - B - Hv;
+  o3.u = A + Cx + Hu;  o3.v = B + Cy + Hv;
+  o4.u = Cx - A - Hu;  o4.v = B - Cy - Hv;
 }
 
 // Per-lane sum of one chunk's row products: compensated in float for the FP32 kernels
@@ -139,6 +176,8 @@ struct RawE {
 // element rows ahead, so each warp keeps P rows of loads in flight.
 template <typename T, int P, typename Op>
 __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V, int strip, int chunk, Op& op) {
+  using Val = typename Op::Val;
+  using Sc = typename Op::Sc;
   const int lane = threadIdx.x & (kWarp - 1);
   const int nx = V.g.nx, ny = V.g.ny;
   const int i = strip * kStripCols - 1 + lane;
@@ -151,13 +190,13 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
   const int j1 = min(j0 + kRowChunk - 1, ny);
   const int er0 = max(j0 - 1, 0);
   const int er1 = min(j1, ny - 1);
-  const T rx = (T)V.g.rx, ry = (T)V.g.ry, w = (T)V.g.w;
+  const Sc rx = (Sc)V.g.rx, ry = (Sc)V.g.ry, w = (Sc)V.g.w;
   typename Op::Raw ring[P];
   RawE<typename Op::E> ering[P];
-  V2<T> pb;
+  V2<Val> pb;
   {
     const typename Op::Raw r0 = op.load(ic, er0);
-    pb = col_in ? op.in(r0, i, er0) : zero2<T>();
+    pb = col_in ? op.in(r0, i, er0) : zero2<Val>();
     op.shift();
   }
 #pragma unroll
@@ -165,7 +204,7 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
     if (er0 + 1 + u <= er1 + 1) ring[u] = op.load(ic, er0 + 1 + u);
     if (er0 + u <= er1) ering[u] = op.loadE(ie, er0 + u);
   }
-  V2<T> acc = zero2<T>();
+  V2<Val> acc = zero2<Val>();
   for (int base = er0; base <= er1; base += P) {
 #pragma unroll
     for (int u = 0; u < P; ++u) {
@@ -175,20 +214,17 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
         const RawE<typename Op::E> ce = ering[u];
         if (er + 1 + P <= er1 + 1) ring[u] = op.load(ic, er + 1 + P);
         if (er + P <= er1) ering[u] = op.loadE(ie, er + P);
-        const V2<T> pt = col_in ? op.in(cur, i, er + 1) : zero2<T>();
-        const V2<T> pbr = shfl_down2(pb), ptr = shfl_down2(pt);
-        V2<T> o1 = zero2<T>(), o2 = zero2<T>(), o3 = zero2<T>(), o4 = zero2<T>();
-        if (elem) {
-          const Coef<T> C = op.coef(U, ce);
-          element_apply<T>(C, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
-        }
-        V2<T> fb = shfl_up2(o2), ft = shfl_up2(o3);
+        const V2<Val> pt = col_in ? op.in(cur, i, er + 1) : zero2<Val>();
+        const V2<Val> pbr = shfl_down2(pb), ptr = shfl_down2(pt);
+        V2<Val> o1 = zero2<Val>(), o2 = zero2<Val>(), o3 = zero2<Val>(), o4 = zero2<Val>();
+        if (elem) op.element(U, ce, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
+        V2<Val> fb = shfl_up2(o2), ft = shfl_up2(o3);
         if (lane == 0) {
-          fb = zero2<T>();
-          ft = zero2<T>();
+          fb = zero2<Val>();
+          ft = zero2<Val>();
         }
-        acc.u += o1.u + fb.u;
-        acc.v += o1.v + fb.v;
+        acc.u = acc.u + (o1.u + fb.u);
+        acc.v = acc.v + (o1.v + fb.v);
         if (er >= j0 && out_col) op.out(i, er, acc);
         acc.u = o4.u + ft.u;
         acc.v = o4.v + ft.v;
@@ -208,7 +244,9 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
 
 template <typename T>
 struct OpBase {
-  using E = T;
+  using E = T;     // element data type
+  using Val = T;   // register type of node values
+  using Sc = T;    // scalar type of stiffness and geometry
   static constexpr int kP32 = kPrefetch32;   // rows in flight of the FP32 variant
   const View<T>& V;
   int64_t nbase;   // first value of the sample's vectors
@@ -249,6 +287,11 @@ struct OpBase {
     if (dir_u(i, V.g.nx)) x.u = (T)0;
     if (dir_v(i)) x.v = (T)0;
     return x;
+  }
+  __device__ __forceinline__ void element(const Invariants& U, const RawE<T>& ce, T rx, T ry, T w, V2<T> n1,
+                                          V2<T> n2, V2<T> n3, V2<T> n4, V2<T>& o1, V2<T>& o2, V2<T>& o3,
+                                          V2<T>& o4) const {
+    element_apply<T>(coef(U, ce), rx, ry, w, n1, n2, n3, n4, o1, o2, o3, o4);
   }
 };
 
@@ -469,18 +512,25 @@ struct OpResidInit : OpBase<T> {
   }
 };
 
-// Refinement residual in double: a = d; ext0 = trig2 (TI); ext1 = r output (TI).
-// The rotated stiffness is formed in TI from the TI trig2 pair, as in the inner
-// solve, so both use one operator; its arithmetic is double.
+// Refinement residual r = -(K d) on free DOFs from the double-precision d:
+// a = d; ext0 = trig2 (TI); ext1 = r output (TI); ||r||^2 into rr64 and the reaction
+// sum of (K d)_u on x = lx into react. The rotated stiffness is formed in TI from the
+// TI trig2 pair, exactly as in the inner solve, so both use one operator. With a
+// single-precision inner solve (TI = float) the arithmetic is float-float (about 48
+// bits, FP32 pipes only); with TI = double it is double.
 template <typename TI>
 struct OpResid : OpBase<double> {
   using E = TI;
-  using Raw = V2<double>;
+  using Val = typename std::conditional<sizeof(TI) == 4, DF, double>::type;
+  using Sc = TI;
+  using Raw = V2<Val>;
   bool act;
   const TI* th;
   TI* r;
-  double rr = 0.0, react = 0.0;
-  __device__ OpResid(const View<double>& v, int s, int ic, int ie, const SampleState& S) : OpBase<double>(v, s, ic, ie) {
+  LaneSum<TI> rr;
+  Val react{};
+  __device__ OpResid(const View<double>& v, int s, int ic, int ie, const SampleState& S)
+      : OpBase<double>(v, s, ic, ie) {
     act = S.outer_active[v.sbase + s] != 0;
     th = static_cast<const TI*>(v.ext0);
     r = static_cast<TI*>(v.ext1);
@@ -494,23 +544,40 @@ struct OpResid : OpBase<double> {
     e.c = e.d = (TI)0;
     return e;
   }
-  __device__ Coef<double> coef(const Invariants& U, const RawE<TI>& e) const {
-    const Coef<TI> c = coef_from_trig2<TI>(U, e.a, e.b);
-    return Coef<double>{(double)c.c11, (double)c.c12, (double)c.c16, (double)c.c22, (double)c.c26, (double)c.c66};
+  __device__ static Val to_val(double x) {
+    if constexpr (sizeof(TI) == 4) return df_from_double(x);
+    else return x;
   }
-  __device__ Raw load(int i, int j) const { return ld2(V.a + at(i, j)); }
-  __device__ V2<double> in(const Raw& d, int, int) { return d; }
-  __device__ void out(int i, int j, V2<double> kd) {
-    const V2<double> res = mask(i, v2<double>(-kd.u, -kd.v));
+  __device__ static TI head(Val x) {
+    if constexpr (sizeof(TI) == 4) return x.hi;
+    else return x;
+  }
+  __device__ Raw load(int i, int j) const {
+    const V2<double> d = ld2(V.a + at(i, j));
+    return v2<Val>(to_val(d.u), to_val(d.v));
+  }
+  __device__ V2<Val> in(const Raw& d, int, int) { return d; }
+  __device__ void element(const Invariants& U, const RawE<TI>& ce, TI rx, TI ry, TI w, V2<Val> n1, V2<Val> n2,
+                          V2<Val> n3, V2<Val> n4, V2<Val>& o1, V2<Val>& o2, V2<Val>& o3, V2<Val>& o4) const {
+    const Coef<TI> C = coef_from_trig2<TI>(U, ce.a, ce.b);
+    if constexpr (sizeof(TI) == 4) element_apply_df(C, rx, ry, w, n1, n2, n3, n4, o1, o2, o3, o4);
+    else element_apply<double>(C, rx, ry, w, n1, n2, n3, n4, o1, o2, o3, o4);
+  }
+  __device__ void out(int i, int j, V2<Val> kd) {
     const int64_t k = at(i, j);
-    r[k] = (TI)res.u;
-    r[k + 1] = (TI)res.v;
-    rr += res.u * res.u + res.v * res.v;
-    if (i == V.g.nx) react += kd.u;
+    const TI ru = dir_u(i, V.g.nx) ? (TI)0 : -head(kd.u);
+    const TI rv = dir_v(i) ? (TI)0 : -head(kd.v);
+    r[k] = ru;
+    r[k + 1] = rv;
+    rr.add(ru * ru + rv * rv);
+    if (i == V.g.nx) react = react + kd.u;
   }
   __device__ void shift() {}
   __device__ void finish(const SampleState& S, int s) {
-    const double t = warp_sum(rr), u = warp_sum(react);
+    double rv;
+    if constexpr (sizeof(TI) == 4) rv = df_to_double(react);
+    else rv = react;
+    const double t = warp_sum(rr.value()), u = warp_sum(rv);
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(&S.rr64[V.sbase + s], t);
       atomicAdd(&S.react[V.sbase + s], u);

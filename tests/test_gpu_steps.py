@@ -123,3 +123,29 @@ def test_homogeneous_block_clamped_vs_oracle(B, theta0):
         assert q[1] == pytest.approx(qs, rel=1e-9)
     finally:
         B.mlmc_destroy(ctx)
+
+
+def test_mixed_refinement_reaches_tight_tolerance(B):
+    """The single-precision inner solve with the float-float refinement residual must
+    reach a relative residual far below single precision (1e-11): only a residual
+    evaluated to about double accuracy allows it."""
+    w = STRIP_MIXED_5LEVEL
+    ctx = make(B, w, rtol=1e-11)
+    try:
+        for mesh in (0, 2):
+            nx, ny = w["nx0"] << mesh, w["ny0"] << mesh
+            n = 2
+            xi = rng.kl_coefficients(w["seed"], 3, np.arange(n), w["kl_terms"])
+            theta = np.ascontiguousarray(kl.theta_field(kl.basis_for_mesh(w, nx, ny), xi))
+            q = np.zeros(2 * n)
+            st = np.ones(n, dtype=np.int32)
+            B.mlmc_solve_theta(ctx, mesh, n, theta, q, st)
+            assert np.all(st == 0)
+            for s in range(n):
+                # the field is rounded to single precision on the GPU: compare on that field
+                th32 = theta[s].astype(np.float32).astype(np.float64)
+                qr, qs, _ = fem.solve_sample(w, nx, ny, th32)
+                assert abs(q[2 * s] / qr - 1) < 1e-6
+                assert abs(q[2 * s + 1] / qs - 1) < 1e-6
+    finally:
+        B.mlmc_destroy(ctx)
