@@ -725,12 +725,15 @@ __global__ void k_invdiag(const __grid_constant__ ViewList<T> L) {
 }
 
 // Dense inverse of the coarsest operator per sample (Dirichlet rows/columns set to
-// the identity), by in-place Gauss-Jordan in double. o0 = inverse [nsamp][n][n] (T).
+// the identity): element columns assembled in parallel (one thread per element
+// column, shared-memory atomics), then in-place Gauss-Jordan in the inner precision
+// (the coarsest solve is part of the preconditioner). o0 = inverse [nsamp][n][n].
+// One 64-thread block per sample.
 template <typename T>
-__global__ void __launch_bounds__(256) k_coarsest_setup(const __grid_constant__ ViewList<T> L) {
-  __shared__ double A[kMaxCoarsestDofs][kMaxCoarsestDofs];
-  __shared__ double pivrow[kMaxCoarsestDofs];
-  __shared__ double pivcol[kMaxCoarsestDofs];
+__global__ void __launch_bounds__(64) k_coarsest_setup(const __grid_constant__ ViewList<T> L) {
+  __shared__ T A[kMaxCoarsestDofs][kMaxCoarsestDofs];
+  __shared__ T pivrow[kMaxCoarsestDofs];
+  __shared__ T pivcol[kMaxCoarsestDofs];
   int vi = 0;
   const int gb = blockIdx.x;
   while (vi < L.n && gb >= L.v[vi].work_begin + L.v[vi].nwork) ++vi;
@@ -740,53 +743,52 @@ __global__ void __launch_bounds__(256) k_coarsest_setup(const __grid_constant__ 
   if (s >= V.nsamp) return;
   const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
   const int n = 2 * (nx + 1) * (ny + 1);
-  for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k / n][k % n] = 0.0;
+  for (int k = threadIdx.x; k < n * n; k += blockDim.x) A[k / n][k % n] = (T)0;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const double rx = V.g.rx, ry = V.g.ry, w = V.g.w;
-    for (int ej = 0; ej < ny; ++ej)
-      for (int ei = 0; ei < nx; ++ei) {
-        const int64_t e = (int64_t)s * nx * ny + (int64_t)ej * nx + ei;
-        Coef<double> C;
-        if (V.trig2) {
-          C = coef_from_trig2<double>(L.U, (double)V.trig2[2 * e], (double)V.trig2[2 * e + 1]);
-        } else {
-          C = coef_from_trig<double>(L.U, (double)V.trig[4 * e], (double)V.trig[4 * e + 1],
-                                     (double)V.trig[4 * e + 2], (double)V.trig[4 * e + 3]);
-        }
-        const int nodes[4] = {ej * nxp + ei, ej * nxp + ei + 1, (ej + 1) * nxp + ei + 1, (ej + 1) * nxp + ei};
-        for (int col = 0; col < 8; ++col) {
-          V2<double> in[4];
-          for (int a = 0; a < 4; ++a) in[a] = v2<double>(0.0, 0.0);
-          if (col & 1) in[col >> 1].v = 1.0; else in[col >> 1].u = 1.0;
-          V2<double> o[4];
-          element_apply<double>(C, rx, ry, w, in[0], in[1], in[2], in[3], o[0], o[1], o[2], o[3]);
-          const int gc = 2 * nodes[col >> 1] + (col & 1);
-          for (int a = 0; a < 4; ++a) {
-            A[2 * nodes[a]][gc] += o[a].u;
-            A[2 * nodes[a] + 1][gc] += o[a].v;
-          }
-        }
-      }
-    // Dirichlet DOFs
-    for (int j = 0; j <= ny; ++j) {
-      const int dofs[3] = {2 * (j * nxp), 2 * (j * nxp) + 1, 2 * (j * nxp + nx)};
-      for (int t = 0; t < 3; ++t) {
-        const int d = dofs[t];
-        for (int m = 0; m < n; ++m) {
-          A[d][m] = 0.0;
-          A[m][d] = 0.0;
-        }
-        A[d][d] = 1.0;
+  const T rx = (T)V.g.rx, ry = (T)V.g.ry, w = (T)V.g.w;
+  for (int job = threadIdx.x; job < nx * ny * 8; job += blockDim.x) {
+    const int el = job >> 3, col = job & 7;
+    const int ej = el / nx, ei = el - ej * nx;
+    const int64_t e = (int64_t)s * nx * ny + el;
+    const Coef<T> C = V.trig2 ? coef_from_trig2<T>(L.U, V.trig2[2 * e], V.trig2[2 * e + 1])
+                              : coef_from_trig<T>(L.U, V.trig[4 * e], V.trig[4 * e + 1], V.trig[4 * e + 2],
+                                                  V.trig[4 * e + 3]);
+    const int nodes[4] = {ej * nxp + ei, ej * nxp + ei + 1, (ej + 1) * nxp + ei + 1, (ej + 1) * nxp + ei};
+    V2<T> in[4];
+    for (int a = 0; a < 4; ++a) in[a] = v2<T>((T)0, (T)0);
+    if (col & 1) in[col >> 1].v = (T)1; else in[col >> 1].u = (T)1;
+    V2<T> o[4];
+    element_apply<T>(C, rx, ry, w, in[0], in[1], in[2], in[3], o[0], o[1], o[2], o[3]);
+    const int gc = 2 * nodes[col >> 1] + (col & 1);
+    for (int a = 0; a < 4; ++a) {
+      atomicAdd(&A[2 * nodes[a]][gc], o[a].u);
+      atomicAdd(&A[2 * nodes[a] + 1][gc], o[a].v);
+    }
+  }
+  __syncthreads();
+  // Dirichlet DOFs: identity rows and columns
+  for (int j = threadIdx.x; j <= ny; j += blockDim.x) {
+    const int dofs[3] = {2 * (j * nxp), 2 * (j * nxp) + 1, 2 * (j * nxp + nx)};
+    for (int q = 0; q < 3; ++q) {
+      const int d = dofs[q];
+      for (int m = 0; m < n; ++m) {
+        A[d][m] = (T)0;
+        A[m][d] = (T)0;
       }
     }
   }
   __syncthreads();
+  for (int j = threadIdx.x; j <= ny; j += blockDim.x) {
+    A[2 * (j * nxp)][2 * (j * nxp)] = (T)1;
+    A[2 * (j * nxp) + 1][2 * (j * nxp) + 1] = (T)1;
+    A[2 * (j * nxp + nx)][2 * (j * nxp + nx)] = (T)1;
+  }
+  __syncthreads();
   // in-place Gauss-Jordan: row k and column k are snapshotted before any update
   for (int k = 0; k < n; ++k) {
-    const double piv = A[k][k];
+    const T piv = A[k][k];
     for (int m = threadIdx.x; m < n; m += blockDim.x) {
-      pivrow[m] = (m == k ? 1.0 : A[k][m]) / piv;
+      pivrow[m] = (m == k ? (T)1 : A[k][m]) / piv;
       pivcol[m] = A[m][k];
     }
     __syncthreads();
@@ -795,13 +797,13 @@ __global__ void __launch_bounds__(256) k_coarsest_setup(const __grid_constant__ 
       if (r == k) {
         A[r][c] = pivrow[c];
       } else {
-        A[r][c] = (c == k ? 0.0 : A[r][c]) - pivcol[r] * pivrow[c];
+        A[r][c] = (c == k ? (T)0 : A[r][c]) - pivcol[r] * pivrow[c];
       }
     }
     __syncthreads();
   }
   T* out = V.o0 + (int64_t)s * n * n;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) out[idx] = (T)A[idx / n][idx % n];
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) out[idx] = A[idx / n][idx % n];
 }
 
 // x = A^-1 b at the coarsest level: a = b, ext0 = inverse (T), o0 = x. One warp per sample.
@@ -855,42 +857,60 @@ __global__ void k_lift(const __grid_constant__ ViewList<double> L, double shorte
 }
 
 // Fibre-direction compressive stress at centroids in [x0, x1]: a = d (double),
-// ext0 = trig2 (TI). Max into qoi[2 s + 1] through the ordered bit pattern of
-// non-negative doubles. One thread per element.
+// ext0 = trig2 (TI). The displacement differences that form the centroid strain are
+// taken in double (they cancel); strain, stress and the fibre-frame projection follow
+// in single precision (relative error ~1e-7). Warp maximum, then one atomicMax per
+// warp on the ordered bit pattern of the non-negative double in qoi[2 s + 1].
+// One thread per element.
 template <typename TI>
 __global__ void k_stress(const __grid_constant__ ViewList<double> L, SampleState S, double x0, double x1,
                          double lx) {
   int vi;
   int64_t loc;
-  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
-  const View<double>& V = L.v[vi];
-  const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
-  const int per = nx * ny;
-  const int s = (int)(loc / per);
-  if (s >= V.nsamp) return;
-  const int e = (int)(loc - (int64_t)s * per);
-  const int j = e / nx, i = e - j * nx;
-  const double cx = (i + 0.5) * (lx / nx);
-  if (cx < x0 || cx > x1) return;
-  const double* d = V.a + (int64_t)s * 2 * nxp * (ny + 1);
-  const int n1 = j * nxp + i, n2 = n1 + 1, n3 = n1 + nxp + 1, n4 = n1 + nxp;
-  const double u1 = d[2 * n1], u2 = d[2 * n2], u3 = d[2 * n3], u4 = d[2 * n4];
-  const double v1 = d[2 * n1 + 1], v2_ = d[2 * n2 + 1], v3 = d[2 * n3 + 1], v4 = d[2 * n4 + 1];
-  const double au = (u2 - u1) + (u3 - u4), bu = (u4 - u1) + (u3 - u2);
-  const double av = (v2_ - v1) + (v3 - v4), bv = (v4 - v1) + (v3 - v2_);
-  const double rx = V.g.rx, ry = V.g.ry;
-  const double ex = rx * au, ey = ry * bv, exy = ry * bu + rx * av;
-  const TI* t2 = static_cast<const TI*>(V.ext0) + 2 * ((int64_t)s * per + e);
-  const double c2 = (double)t2[0], s2 = (double)t2[1];
-  const Coef<double> C = coef_from_trig2<double>(L.U, c2, s2);
-  const double sx = C.c11 * ex + C.c12 * ey + C.c16 * exy;
-  const double sy = C.c12 * ex + C.c22 * ey + C.c26 * exy;
-  const double sxy = C.c16 * ex + C.c26 * ey + C.c66 * exy;
-  // fibre-frame normal stress: cos^2 t sx + sin^2 t sy + 2 sin t cos t sxy
-  const double s11 = 0.5 * (1.0 + c2) * sx + 0.5 * (1.0 - c2) * sy + s2 * sxy;
-  const double val = fmax(0.0, -s11);
-  atomicMax(reinterpret_cast<unsigned long long*>(&S.qoi[2 * (V.sbase + s) + 1]),
-            (unsigned long long)__double_as_longlong(val));
+  const bool have = find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc);
+  double vmax = 0.0;
+  int t = -1;
+  if (have) {
+    const View<double>& V = L.v[vi];
+    const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
+    const int per = nx * ny;
+    const int s = (int)(loc / per);
+    if (s < V.nsamp) {
+      t = V.sbase + s;
+      const int e = (int)(loc - (int64_t)s * per);
+      const int j = e / nx, i = e - j * nx;
+      const double cx = (i + 0.5) * (lx / nx);
+      if (cx >= x0 && cx <= x1) {
+        const double* d = V.a + (int64_t)s * 2 * nxp * (ny + 1);
+        const int n1 = j * nxp + i, n2 = n1 + 1, n3 = n1 + nxp + 1, n4 = n1 + nxp;
+        using R = TI;   // single precision on the mixed path, double on the double path
+        const R au = (R)((d[2 * n2] - d[2 * n1]) + (d[2 * n3] - d[2 * n4]));
+        const R bu = (R)((d[2 * n4] - d[2 * n1]) + (d[2 * n3] - d[2 * n2]));
+        const R av = (R)((d[2 * n2 + 1] - d[2 * n1 + 1]) + (d[2 * n3 + 1] - d[2 * n4 + 1]));
+        const R bv = (R)((d[2 * n4 + 1] - d[2 * n1 + 1]) + (d[2 * n3 + 1] - d[2 * n2 + 1]));
+        const R rx = (R)V.g.rx, ry = (R)V.g.ry;
+        const R ex = rx * au, ey = ry * bv, exy = ry * bu + rx * av;
+        const TI* t2 = static_cast<const TI*>(V.ext0) + 2 * ((int64_t)s * per + e);
+        const R c2 = t2[0], s2 = t2[1];
+        const Coef<R> C = coef_from_trig2<R>(L.U, c2, s2);
+        const R sx = C.c11 * ex + C.c12 * ey + C.c16 * exy;
+        const R sy = C.c12 * ex + C.c22 * ey + C.c26 * exy;
+        const R sxy = C.c16 * ex + C.c26 * ey + C.c66 * exy;
+        // fibre-frame normal stress: cos^2 t sx + sin^2 t sy + 2 sin t cos t sxy
+        const R s11 = (R)0.5 * ((R)1 + c2) * sx + (R)0.5 * ((R)1 - c2) * sy + s2 * sxy;
+        vmax = -s11 > (R)0 ? (double)(-s11) : 0.0;
+      }
+    }
+  }
+  // samples change along the thread index: group the lanes of each sample and reduce
+  // the group's maximum on the high word of the bit pattern (non-negative doubles
+  // order like their patterns); the lanes holding that high word settle the low word
+  // with the 64-bit atomicMax, so one atomic per group in the common case
+  const unsigned same = __match_any_sync(0xffffffffu, t);
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(vmax);
+  const unsigned hmax = __reduce_max_sync(same, (unsigned)(bits >> 32));
+  if (t >= 0 && bits > 0ull && (unsigned)(bits >> 32) == hmax)
+    atomicMax(reinterpret_cast<unsigned long long*>(&S.qoi[2 * t + 1]), bits);
 }
 
 template <typename T>
@@ -1074,7 +1094,7 @@ cudaError_t launch_invdiag(const ViewList<T>& L, int total_threads, cudaStream_t
 template <typename T>
 cudaError_t launch_coarsest_setup(const ViewList<T>& L, int total_blocks, cudaStream_t st) {
   if (total_blocks <= 0) return cudaSuccess;
-  k_coarsest_setup<T><<<total_blocks, 256, 0, st>>>(L);
+  k_coarsest_setup<T><<<total_blocks, 64, 0, st>>>(L);
   return cudaGetLastError();
 }
 

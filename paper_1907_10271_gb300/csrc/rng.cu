@@ -57,10 +57,14 @@ __device__ __forceinline__ double series_ln(double x) {
   }
   const double t = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
   const double t2 = __dmul_rn(t, t);
-  double p = __ddiv_rn(1.0, (double)(2 * kAtanhTerms - 1));
+  // 1 / (2k + 1), correctly rounded (constant-folded at compile time)
+  constexpr double kInvOdd[kAtanhTerms] = {1.0,        1.0 / 3.0,  1.0 / 5.0,  1.0 / 7.0,  1.0 / 9.0,
+                                           1.0 / 11.0, 1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0,
+                                           1.0 / 21.0, 1.0 / 23.0, 1.0 / 25.0, 1.0 / 27.0, 1.0 / 29.0};
+  double p = kInvOdd[kAtanhTerms - 1];
 #pragma unroll
   for (int k = kAtanhTerms - 2; k >= 0; --k) {
-    p = __dadd_rn(__dmul_rn(p, t2), __ddiv_rn(1.0, (double)(2 * k + 1)));
+    p = __dadd_rn(__dmul_rn(p, t2), kInvOdd[k]);
   }
   const double lnm = __dmul_rn(__dmul_rn(2.0, t), p);
   const double de = (double)e;
