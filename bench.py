@@ -33,15 +33,16 @@ METRIC = "level-pair FE solves/s (5-level strip, QoI rtol 1e-8)"
 UNIT = "level-pairs/s"
 
 # Algorithmic bytes per mesh node of each timed operation in the FP32 inner solve
-# (2 DOF per node, float2 vectors 8 B, angle 4 B or averaged trig 16 B per element,
-# one element per node, coarse correction 2 B per fine node).
+# (2 DOF per node: float2 vectors 8 B; per-element data, one element per node:
+# (cos 2t, sin 2t) 8 B on the finest mesh, averaged trig 4-vector 16 B on coarse
+# meshes; the coarse correction read by a prolongation is 2 B per fine node).
 BYTES_PER_NODE = {
-    "pcg_update_presmooth": 8 * 5 + 4 + 8 * 3,    # r q x p w/D + theta ; x r' r1
+    "pcg_update_presmooth": 8 * 5 + 8 + 8 * 3,    # r q x p w/D + trig2 ; x r' r1
     "presmooth": 8 * 2 + 16 + 8,                   # b w/D + trig ; r1
     "postsmooth": 8 * 2 + 16 + 2 + 8,              # b w/D + trig + x_c ; x
-    "postsmooth_top": 8 * 2 + 4 + 2 + 8,           # b w/D + theta + x_c ; z
-    "search_direction": 8 * 2 + 4 + 8 * 2,         # z p + theta ; p' q
-    "refinement_residual": 16 + 4 + 8,             # d (double) + theta ; r (float)
+    "postsmooth_top": 8 * 2 + 8 + 2 + 8,           # b w/D + trig2 + x_c ; z
+    "search_direction": 8 * 2 + 8 + 8 * 2,         # z p + trig2 ; p' q
+    "refinement_residual": 16 + 8 + 8,             # d (double) + trig2 ; r (float)
 }
 
 
@@ -52,6 +53,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-single", dest="fp64_single", action="store_false",
+                    help="skip the plain double-precision single-sample comparison")
     ap.add_argument("--cpu-fraction", type=float, default=1.0 / 32.0,
                     help="fraction of each level's samples the CPU oracle times")
     return ap.parse_args()
@@ -187,6 +190,33 @@ def oracle_throughput(cfg, fraction, cores):
 
 # ---------------------------------------------------------------- GPU arm
 
+def fp64_single_sample(B, cfg, rank):
+    """Level-pairs/s of the plain double-precision GPU form solving one sample per call
+    (same multigrid-PCG, every step in double, no batching), timed on a few samples of
+    each level and weighted by the workload's N_l."""
+    import torch
+    w = dict(cfg)
+    w.update(precision="fp64", rtol=cfg["rtol"])
+    ctx = B.mlmc_create(B.config_from_workload(w), torch.cuda.current_stream().cuda_stream)
+    per_level = [6, 4, 3, 2, 2]
+    t_l = []
+    q = torch.zeros(2, dtype=torch.float64, device="cuda")
+    qc = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for level, m in enumerate(per_level):
+        B.mlmc_sample_level(ctx, level, 1 << 50, 1, q, qc)     # warm the level's workspace
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(m):
+            B.mlmc_sample_level(ctx, level, (1 << 50) + 1 + rank * 1000 + k, 1, q, qc)
+        torch.cuda.synchronize()
+        t_l.append((time.perf_counter() - t0) / m)
+    B.mlmc_destroy(ctx)
+    counts = cfg["n_per_level"]
+    value = sum(counts) / sum(n * t for n, t in zip(counts, t_l))
+    return {"value": round(value, 1), "unit": UNIT, "seconds_per_pair": [round(t, 5) for t in t_l],
+            "sample": f"{per_level} single-sample calls per level, extrapolated to the workload mix"}
+
+
 ID_STRIDE = 1 << 40   # sample ids of rank r start at r * 2^40: disjoint for any realistic run
 
 
@@ -298,6 +328,9 @@ def run_gpu(a):
     clocks = clk.summary()
     B.mlmc_destroy(ctx)
 
+    # ---- comparison point: the plain double-precision form, one sample per call
+    fp64 = fp64_single_sample(B, cfg, rank) if a.fp64_single else None
+
     out = None
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -313,7 +346,10 @@ def run_gpu(a):
                        "d2h_bytes_per_step": total * (2 * 16 + 4),
                        "note": "mlmc_sample_levels with pinned host outputs; per-sample inputs are "
                                "(seed, level, id) counters, fields are synthesised on the device"},
-               "roofline": roofline, "kernels": kernels, "gpu_launches": launches // a.steps,
+               "roofline": roofline, "kernels": kernels,
+               "fp64_single_sample": fp64,
+               "speedup_vs_fp64_single_sample": (round(value / world / fp64["value"], 1) if fp64 else None),
+               "gpu_launches": launches // a.steps,
                "gpu_launches_total": launches, "clocks": clocks}
     if world > 1:
         torch.distributed.barrier()
