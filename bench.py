@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-single", dest="fp64_single", action="store_false",
                     help="skip the plain double-precision single-sample comparison")
+    ap.add_argument("--case", choices=["full", "small"], default="full",
+                    help="small: one untimed call with 1/8 of each level's samples (for profilers)")
     ap.add_argument("--cpu-fraction", type=float, default=1.0 / 32.0,
                     help="fraction of each level's samples the CPU oracle times")
     return ap.parse_args()
@@ -321,6 +323,7 @@ def run_gpu(a):
                 "algorithmic_bytes_per_launch": round(nodes * BYTES_PER_NODE[dom] / nl),
                 "avg_launch_us": round(ms / nl * 1e3, 2), "launches": nl,
                 "share_of_step": round(ms / (t_step * a.steps), 4)}
+    kernel_ms = sum(v[0] for v in prof.values()) / a.steps
     kernels = {k: {"ms_per_step": round(v[0] / a.steps, 3), "launches_per_step": v[1] // a.steps,
                    "GB/s": (round(v[2] * BYTES_PER_NODE[k] / (v[0] / 1e3) / 1e9, 1)
                             if k in BYTES_PER_NODE and v[0] > 0 else None)}
@@ -347,6 +350,7 @@ def run_gpu(a):
                        "note": "mlmc_sample_levels with pinned host outputs; per-sample inputs are "
                                "(seed, level, id) counters, fields are synthesised on the device"},
                "roofline": roofline, "kernels": kernels,
+               "kernel_ms_per_step": round(kernel_ms, 3), "gpu_busy_fraction": round(kernel_ms / worst, 3),
                "fp64_single_sample": fp64,
                "speedup_vs_fp64_single_sample": (round(value / world / fp64["value"], 1) if fp64 else None),
                "gpu_launches": launches // a.steps,
@@ -357,9 +361,31 @@ def run_gpu(a):
     return out
 
 
+def run_small_case():
+    """One call of the workload with 1/8 of each level's samples, after one warm call:
+    a short, bounded command for kernel captures (about 1.3 GB of device memory)."""
+    import torch
+    from paper_1907_10271_gb300 import binding as B
+    cfg = STRIP_MIXED_5LEVEL
+    counts = [n // 8 for n in cfg["n_per_level"]]
+    total = sum(counts)
+    ctx = B.mlmc_create(B.config_from_workload(cfg), torch.cuda.current_stream().cuda_stream)
+    qf = torch.zeros(2 * total, dtype=torch.float64, device="cuda")
+    qc = torch.zeros_like(qf)
+    st = torch.zeros(total, dtype=torch.int32, device="cuda")
+    for k in range(2):
+        B.mlmc_sample_levels(ctx, list(range(cfg["levels"])), [k * 10 ** 6] * cfg["levels"], counts, qf, qc, st)
+    torch.cuda.synchronize()
+    B.mlmc_destroy(ctx)
+    print(json.dumps({"case": "small", "level_pairs": total, "failed": int((st != 0).sum())}))
+
+
 def main():
     a = parse()
     rank, _, world = dist_env()
+    if a.case == "small":
+        run_small_case()
+        return
     if a.impl == "reference":
         if rank != 0:
             return

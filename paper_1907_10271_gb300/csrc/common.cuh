@@ -38,12 +38,24 @@ constexpr int kMaxCoarsestDofs = 64;
 struct Invariants {
   double U1, U2, U3, U4, U5;
   float F1, F2, F3, F4, F5;   // the same values rounded once to single precision
+  double Q1, Q2, Q3, Q4, Q5;  // the values divided by 4 (square-element operator)
+  float G1, G2, G3, G4, G5;   // and rounded to single precision
   void round_single() {
     F1 = (float)U1;
     F2 = (float)U2;
     F3 = (float)U3;
     F4 = (float)U4;
     F5 = (float)U5;
+    Q1 = U1 / 4;
+    Q2 = U2 / 4;
+    Q3 = U3 / 4;
+    Q4 = U4 / 4;
+    Q5 = U5 / 4;
+    G1 = (float)Q1;
+    G2 = (float)Q2;
+    G3 = (float)Q3;
+    G4 = (float)Q4;
+    G5 = (float)Q5;
   }
 };
 
@@ -67,11 +79,15 @@ __device__ __forceinline__ V2<T> v2(T u, T v) {
 
 // Single-precision callers read the pre-rounded invariants: a double-to-float
 // conversion per element would run at the (low) FP64 rate.
-template <typename T>
+template <typename T, bool QUARTER = false>
 __device__ __forceinline__ Coef<T> coef_from_trig(const Invariants& U, T c2, T s2, T c4, T s4) {
   Coef<T> c;
   T u1, u2, u3, u4, u5;
-  if constexpr (sizeof(T) == sizeof(float)) {
+  if constexpr (QUARTER && sizeof(T) == sizeof(float)) {
+    u1 = U.G1; u2 = U.G2; u3 = U.G3; u4 = U.G4; u5 = U.G5;
+  } else if constexpr (QUARTER) {
+    u1 = U.Q1; u2 = U.Q2; u3 = U.Q3; u4 = U.Q4; u5 = U.Q5;
+  } else if constexpr (sizeof(T) == sizeof(float)) {
     u1 = U.F1; u2 = U.F2; u3 = U.F3; u4 = U.F4; u5 = U.F5;
   } else {
     u1 = U.U1; u2 = U.U2; u3 = U.U3; u4 = U.U4; u5 = U.U5;
@@ -100,9 +116,9 @@ __device__ __forceinline__ void trig4(T theta, T* c2, T* s2, T* c4, T* s4) {
 }
 
 // From the pair (cos 2t, sin 2t) stored per element of the finest mesh.
-template <typename T>
+template <typename T, bool QUARTER = false>
 __device__ __forceinline__ Coef<T> coef_from_trig2(const Invariants& U, T c2, T s2) {
-  return coef_from_trig(U, c2, s2, (T)2 * c2 * c2 - (T)1, (T)2 * s2 * c2);
+  return coef_from_trig<T, QUARTER>(U, c2, s2, (T)2 * c2 * c2 - (T)1, (T)2 * s2 * c2);
 }
 
 template <typename T>
@@ -144,6 +160,30 @@ __device__ __forceinline__ void element_apply(const Coef<T>& C, T rx, T ry, T w,
   o4.u = -A + Cx - Hu;  o4.v = B - Cy - Hv;
 }
 
+// Square elements (hx = hy): every geometric factor of element_apply reduces to 1/4 on
+// the centroid part and 1/12 on the hourglass part, and the two shear terms coincide.
+// C4 holds C_bar / 4; the result equals element_apply's exactly in real arithmetic.
+template <typename T>
+__device__ __forceinline__ void element_apply_square(const Coef<T>& C4, V2<T> n1, V2<T> n2, V2<T> n3, V2<T> n4,
+                                                     V2<T>& o1, V2<T>& o2, V2<T>& o3, V2<T>& o4) {
+  const T du21 = n2.u - n1.u, du34 = n3.u - n4.u, du41 = n4.u - n1.u, du32 = n3.u - n2.u;
+  const T dv21 = n2.v - n1.v, dv34 = n3.v - n4.v, dv41 = n4.v - n1.v, dv32 = n3.v - n2.v;
+  const T au = du21 + du34, bu = du41 + du32, gu = du34 - du21;
+  const T av = dv21 + dv34, bv = dv41 + dv32, gv = dv34 - dv21;
+  const T e = bu + av;
+  const T A = C4.c11 * au + C4.c12 * bv + C4.c16 * e;
+  const T B = C4.c12 * au + C4.c22 * bv + C4.c26 * e;
+  const T Cs = C4.c16 * au + C4.c26 * bv + C4.c66 * e;
+  const T third = (T)(1.0 / 3.0);
+  const T p1 = third * (C4.c11 + C4.c66), p2 = third * (C4.c16 + C4.c26), p3 = third * (C4.c22 + C4.c66);
+  const T Hu = p1 * gu + p2 * gv;
+  const T Hv = p2 * gu + p3 * gv;
+  o1.u = -A - Cs + Hu;  o1.v = -B - Cs + Hv;
+  o2.u = A - Cs - Hu;   o2.v = -B + Cs - Hv;
+  o3.u = A + Cs + Hu;   o3.v = B + Cs + Hv;
+  o4.u = -A + Cs - Hu;  o4.v = B - Cs - Hv;
+}
+
 // Diagonal of K_e at local node with xi*eta = sgn (+1 for n1, n3; -1 for n2, n4).
 template <typename T>
 __device__ __forceinline__ V2<T> element_diag(const Coef<T>& C, T rx, T ry, T w, T sgn) {
@@ -158,6 +198,7 @@ __device__ __forceinline__ V2<T> element_diag(const Coef<T>& C, T rx, T ry, T w,
 struct Geo {
   int nx, ny;         // elements
   double rx, ry, w;   // 1/(2hx), 1/(2hy), hx*hy
+  int square;         // hx == hy: the square-element operator applies
   int nodes() const { return (nx + 1) * (ny + 1); }
 };
 

@@ -73,7 +73,7 @@ struct KernelTimer {
   }
   void begin(int op, cudaStream_t st) {
     ++launches;
-    if (!on || op == kProfOther) return;
+    if (!on) return;
     pending_op = op;
     pending_ev = used;
     cudaEventRecord(next(), st);
@@ -133,6 +133,7 @@ struct Context {
     g.rx = 0.5 / hx;
     g.ry = 0.5 / hy;
     g.w = hx * hy;
+    g.square = hx == hy ? 1 : 0;
     return g;
   }
   mlmc_status fail(mlmc_status s, const std::string& m) {

@@ -291,7 +291,13 @@ struct OpBase {
   __device__ __forceinline__ void element(const Invariants& U, const RawE<T>& ce, T rx, T ry, T w, V2<T> n1,
                                           V2<T> n2, V2<T> n3, V2<T> n4, V2<T>& o1, V2<T>& o2, V2<T>& o3,
                                           V2<T>& o4) const {
-    element_apply<T>(coef(U, ce), rx, ry, w, n1, n2, n3, n4, o1, o2, o3, o4);
+    if (V.g.square) {   // uniform over the launch's view
+      const Coef<T> C4 = V.trig2 ? coef_from_trig2<T, true>(U, ce.a, ce.b)
+                                 : coef_from_trig<T, true>(U, ce.a, ce.b, ce.c, ce.d);
+      element_apply_square<T>(C4, n1, n2, n3, n4, o1, o2, o3, o4);
+    } else {
+      element_apply<T>(coef(U, ce), rx, ry, w, n1, n2, n3, n4, o1, o2, o3, o4);
+    }
   }
 };
 

@@ -11,9 +11,9 @@
 // stiffness, and an exact dense solve on the coarsest mesh.
 //
 // All groups (one mesh size each, any number of samples) advance in lock step:
-// multigrid levels are aligned by their distance from each group's coarsest mesh,
-// so one launch per level serves every group that has that level. Every sample
-// keeps its own CG scalars; converged samples drop out of all kernels.
+// multigrid levels are aligned by their depth below each group's finest mesh, so one
+// launch per depth serves every group that has that level. Every sample keeps its
+// own CG scalars; converged samples drop out of all kernels.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -122,7 +122,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   // ---- hierarchy and workspace
   std::vector<GroupBuf<T>> G(groups.size());
   int total = 0;
-  int amax = 0;
+  int dmax = 0;   // deepest coarsest-level index over the groups
   for (size_t gi = 0; gi < groups.size(); ++gi) {
     GroupBuf<T>& g = G[gi];
     g.grp = &groups[gi];
@@ -142,7 +142,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     const Geo& c = g.geo.back();
     if (2 * (c.nx + 1) * (c.ny + 1) > kMaxCoarsestDofs)
       return ctx.fail(MLMC_ERR_INVALID_ARG, "coarsest mesh too large (mesh must halve down to <= 64 DOFs)");
-    amax = std::max(amax, g.nl - 1);
+    dmax = std::max(dmax, g.nl - 1);
   }
   if (total == 0) return MLMC_OK;
   const int max_iter = ctx.cfg.max_iter > 0 ? ctx.cfg.max_iter : 200;
@@ -300,17 +300,19 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     return L;
   };
 
+  // One PCG iteration for every group. Multigrid levels are aligned by depth below
+  // each group's finest mesh, so the finest-level kernels (the largest) are single
+  // launches over all groups; a group's coarse levels join the launches of their depth,
+  // and all coarsest solves share one launch between the down and up sweeps.
   auto run_vcycle_and_pcg = [&](int parity, int iter) -> mlmc_status {
-    cudaError_t err;
-    // down sweep
-    for (int a = amax; a >= 1; --a) {
-      ViewList<T> Ltop = empty_list<T>(ctx), Lmid = empty_list<T>(ctx), Lres = empty_list<T>(ctx);
+    // down sweep: depth d smooths (or, at d = 0, updates PCG and smooths) and restricts
+    for (int d = 0; d < dmax; ++d) {
+      ViewList<T> Lsm = empty_list<T>(ctx), Lres = empty_list<T>(ctx);
       std::vector<int64_t> per_res;
       for (auto& g : G) {
-        const int k = (g.nl - 1) - a;
-        if (k < 0) continue;
-        if (k == 0) {
-          View<T> v = base_view(g, 0);
+        if (d >= g.nl - 1) continue;
+        View<T> v = base_view(g, d);
+        if (d == 0) {
           v.a = g.r[parity];
           v.b = g.q;
           v.c = g.p[parity];
@@ -318,36 +320,34 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
           v.o0 = g.x;
           v.o1 = g.r[parity ^ 1];
           v.o2 = g.r1[0];
-          Ltop.v[Ltop.n++] = v;
         } else {
-          View<T> v = base_view(g, k);
-          v.a = g.b[k];
-          v.winvd = g.winvd[k];
-          v.o2 = g.r1[k];
-          Lmid.v[Lmid.n++] = v;
+          v.a = g.b[d];
+          v.winvd = g.winvd[d];
+          v.o2 = g.r1[d];
         }
-        View<T> r = base_view(g, k);
-        r.a = g.r1[k];
-        r.o0 = g.b[k + 1];
+        Lsm.v[Lsm.n++] = v;
+        View<T> r = base_view(g, d);
+        r.a = g.r1[d];
+        r.o0 = g.b[d + 1];
         Lres.v[Lres.n++] = r;
-        per_res.push_back((int64_t)(g.geo[k].nx / 2 + 1) * (g.geo[k].ny / 2 + 1));
+        per_res.push_back((int64_t)(g.geo[d].nx / 2 + 1) * (g.geo[d].ny / 2 + 1));
       }
-      if (Ltop.n) {
-        const int tw = finalize_warps(Ltop);
-        Ltop.prof_op = kProfPreTop;
-        MLMC_LAUNCH(kProfPreTop, "pre_top", launch_strip<T>(StripOp::PreTop, Ltop, S, tw, st));
-      }
-      if (Lmid.n) {
-        const int tw = finalize_warps(Lmid);
-        Lmid.prof_op = kProfPre;
-        MLMC_LAUNCH(kProfPre, "pre", launch_strip<T>(StripOp::Pre, Lmid, S, tw, st));
+      if (Lsm.n) {
+        const int tw = finalize_warps(Lsm);
+        if (d == 0) {
+          Lsm.prof_op = kProfPreTop;
+          MLMC_LAUNCH(kProfPreTop, "pre_top", launch_strip<T>(StripOp::PreTop, Lsm, S, tw, st));
+        } else {
+          Lsm.prof_op = kProfPre;
+          MLMC_LAUNCH(kProfPre, "pre", launch_strip<T>(StripOp::Pre, Lsm, S, tw, st));
+        }
       }
       if (Lres.n) {
         const int tt = finalize_points(Lres, per_res);
         MLMC_LAUNCH(kProfRestrict, "restrict", launch_restrict<T>(Lres, S, tt, st));
       }
     }
-    // coarsest
+    // every group's coarsest mesh
     {
       ViewList<T> L = empty_list<T>(ctx);
       int acc = 0;
@@ -364,34 +364,31 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       }
       MLMC_LAUNCH(kProfCoarsest, "coarsest", launch_coarsest_solve<T>(L, S, acc, st));
     }
-    // up sweep
-    for (int a = 1; a <= amax; ++a) {
-      ViewList<T> Ltop = empty_list<T>(ctx), Lmid = empty_list<T>(ctx);
+    // up sweep: prolongation and post-smoothing from the deepest level back to the top
+    for (int d = dmax - 1; d >= 0; --d) {
+      ViewList<T> L = empty_list<T>(ctx);
       for (auto& g : G) {
-        const int k = (g.nl - 1) - a;
-        if (k < 0) continue;
-        View<T> v = base_view(g, k);
-        v.xc = g.xl[k + 1];
-        v.winvd = g.winvd[k];
-        if (k == 0) {
+        if (d >= g.nl - 1) continue;
+        View<T> v = base_view(g, d);
+        v.xc = g.xl[d + 1];
+        v.winvd = g.winvd[d];
+        if (d == 0) {
           v.a = g.r[parity ^ 1];
           v.o0 = g.z;
-          Ltop.v[Ltop.n++] = v;
         } else {
-          v.a = g.b[k];
-          v.o0 = g.xl[k];
-          Lmid.v[Lmid.n++] = v;
+          v.a = g.b[d];
+          v.o0 = g.xl[d];
         }
+        L.v[L.n++] = v;
       }
-      if (Lmid.n) {
-        const int tw = finalize_warps(Lmid);
-        Lmid.prof_op = kProfPost;
-        MLMC_LAUNCH(kProfPost, "post", launch_strip<T>(StripOp::Post, Lmid, S, tw, st));
-      }
-      if (Ltop.n) {
-        const int tw = finalize_warps(Ltop);
-        Ltop.prof_op = kProfPostTop;
-        MLMC_LAUNCH(kProfPostTop, "post_top", launch_strip<T>(StripOp::PostTop, Ltop, S, tw, st));
+      if (!L.n) continue;
+      const int tw = finalize_warps(L);
+      if (d == 0) {
+        L.prof_op = kProfPostTop;
+        MLMC_LAUNCH(kProfPostTop, "post_top", launch_strip<T>(StripOp::PostTop, L, S, tw, st));
+      } else {
+        L.prof_op = kProfPost;
+        MLMC_LAUNCH(kProfPost, "post", launch_strip<T>(StripOp::Post, L, S, tw, st));
       }
     }
     MLMC_LAUNCH(kProfOther, "after_post", launch_after_post(S, total, iter, st));
