@@ -29,7 +29,7 @@ namespace mlmc {
 constexpr int kWarp = 32;
 constexpr int kStripCols = 30;     // output node columns per warp strip (32 lanes, 1 halo each side)
 constexpr int kRowChunk = 32;      // output node rows per warp tile
-constexpr int kPrefetch32 = 2;     // node rows in flight per warp (FP32 kernels)
+constexpr int kPrefetch32 = 1;     // node rows in flight per warp (FP32 kernels)
 constexpr int kPrefetch64 = 2;     // node rows in flight per warp (FP64 kernels)
 constexpr int kWarpsPerBlock = 4;
 constexpr double kOmega = 0.5;     // Jacobi damping: element bound of lambda_max(D^-1 K) < 3.9 for any angle

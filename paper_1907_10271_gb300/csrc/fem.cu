@@ -386,7 +386,7 @@ struct OpPre : OpBase<T> {
 // a = b, xc (level below), winvd; o0 = z.  TOP also reduces b . z.
 template <typename T, bool TOP>
 struct OpPost : OpBase<T> {
-  static constexpr int kP32 = 2;   // larger row records (coarse values)
+  static constexpr int kP32 = 1;   // row record plus in-line coarse loads: keep registers low
   struct Raw {
     V2<T> b, w;
   };
