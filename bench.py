@@ -281,6 +281,8 @@ def run_gpu(a):
         barrier()
     launches = B.mlmc_launch_count(ctx)
     prof = {name: B.mlmc_profile_get(ctx, i) for i, name in enumerate(B.PROFILE_OPS)}
+    by_name = {k: {"launches_per_step": v[0] // a.steps, "ms_per_step": round(v[1] / a.steps, 3)}
+               for k, v in sorted(B.mlmc_profile_report(ctx).items(), key=lambda kv: -kv[1][1])}
     B.mlmc_profile_enable(ctx, False)
     t_step = sum(times) / len(times)
 
@@ -351,6 +353,7 @@ def run_gpu(a):
                                "(seed, level, id) counters, fields are synthesised on the device"},
                "roofline": roofline, "kernels": kernels,
                "kernel_ms_per_step": round(kernel_ms, 3), "gpu_busy_fraction": round(kernel_ms / worst, 3),
+               "launches_by_name": by_name,
                "fp64_single_sample": fp64,
                "speedup_vs_fp64_single_sample": (round(value / world / fp64["value"], 1) if fp64 else None),
                "gpu_launches": launches // a.steps,

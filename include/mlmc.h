@@ -244,6 +244,11 @@ mlmc_status mlmc_profile_enable(mlmc_ctx* ctx, int32_t on);
    launches and nodes processed of operation `op` (each output nullable). */
 mlmc_status mlmc_profile_get(mlmc_ctx* ctx, int32_t op, double* ms_total, int64_t* launches, uint64_t* nodes);
 
+/* Per-launch-name totals since the last mlmc_profile_enable, as text lines
+   "name launches total_ms" (all kernels, not only the operations above), written
+   NUL-terminated into buf[cap] (truncated if longer). */
+mlmc_status mlmc_profile_report(mlmc_ctx* ctx, char* buf, int64_t cap);
+
 /* Kernel launches the library issued since the last mlmc_profile_enable. */
 mlmc_status mlmc_launch_count(mlmc_ctx* ctx, int64_t* launches);
 

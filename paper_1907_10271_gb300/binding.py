@@ -87,6 +87,7 @@ def lib():
             "mlmc_profile_get": (I32, [P, I32, P, P, P]),
             "mlmc_launch_count": (I32, [P, P]),
             "mlmc_merge_stats": (I32, [P, P, P]),
+            "mlmc_profile_report": (I32, [P, P, I64]),
             "mlmc_solve_theta_static": (I32, [ctypes.POINTER(mlmc_config), P, I32, I64, P, P, P]),
             "mlmc_static_last_error": (ctypes.c_char_p, []),
         }
@@ -290,3 +291,14 @@ def mlmc_merge_stats(a, b):
     if s != MLMC_OK:
         raise MLMCError(s, "merge")
     return out.as_dict()
+
+
+def mlmc_profile_report(ctx):
+    """{launch name: (launches, total ms)} since the last mlmc_profile_enable."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(ctx, lib().mlmc_profile_report(ctx, ctypes.cast(buf, ctypes.c_void_p), len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms = line.rsplit(" ", 2)
+        out[name] = (int(n), float(ms))
+    return out

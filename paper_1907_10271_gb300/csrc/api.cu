@@ -200,7 +200,7 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
   std::vector<mlmc::SolveGroup<T>> groups;
   for (size_t k = 0; k < reqs.size(); ++k) {
     const LevelReq& r = reqs[k];
-    c.timer.begin(mlmc::kProfOther, st);
+    c.timer.begin(mlmc::kProfOther, st, "kl_coefficients");
     e = mlmc::launch_kl_coefficients(c.cfg.seed, r.level, r.first_id, nullptr, nullptr, r.n, nkl, B[k].xi,
                                      c.mixed() ? B[k].xi32 : nullptr, fail, st);
     c.timer.end(st);
@@ -210,7 +210,7 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
       const int m = r.level - side;
       const T* basis = c.mixed() ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
       T* th = (T*)(side == 0 ? B[k].theta_f : B[k].theta_c);
-      c.timer.begin(mlmc::kProfOther, st);
+      c.timer.begin(mlmc::kProfOther, st, "kl_synthesis");
       e = mlmc::launch_kl_synthesis<T>(xiT, basis, r.n, (int)c.mesh(m).n_el(), nkl, th, true, st);
       c.timer.end(st);
       if (e != cudaSuccess) return c.cuda_fail(e, "kl_synthesis");
@@ -228,14 +228,14 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
   for (size_t k = 0; k < reqs.size(); ++k) {
     const LevelReq& r = reqs[k];
     const int64_t nb = r.n;
-    c.timer.begin(mlmc::kProfOther, st);
+    c.timer.begin(mlmc::kProfOther, st, "combine_status");
     k_combine_status<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(B[k].st_f, r.level > 0 ? B[k].st_c : nullptr,
                                                                   B[k].status, nb);
     c.timer.end(st);
     if ((e = cudaGetLastError()) != cudaSuccess) return c.cuda_fail(e, "status");
     if (r.level == 0 && (e = cudaMemsetAsync(B[k].qc, 0, sizeof(double) * 2 * nb, st)) != cudaSuccess)
       return c.cuda_fail(e, "memset");
-    c.timer.begin(mlmc::kProfOther, st);
+    c.timer.begin(mlmc::kProfOther, st, "moments");
     e = mlmc::launch_moments(B[k].qf, r.level > 0 ? B[k].qc : nullptr, B[k].status, nb, h->acc_dev + r.level, st);
     c.timer.end(st);
     if (e != cudaSuccess) return c.cuda_fail(e, "moments");
@@ -492,6 +492,29 @@ mlmc_status mlmc_profile_get(mlmc_ctx* h, int32_t op, double* ms_total, int64_t*
       return c.cuda_fail(e, "profile");
     *nodes = u[op];
   }
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_profile_report(mlmc_ctx* h, char* buf, int64_t cap) {
+  if (!h || !buf || cap <= 0) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return c.cuda_fail(e, "profile");
+  std::map<std::string, std::pair<int64_t, double>> agg;
+  for (const auto& r : c.timer.recs) {
+    float t = 0.f;
+    if ((e = cudaEventElapsedTime(&t, c.timer.pool[r.ev], c.timer.pool[r.ev + 1])) != cudaSuccess)
+      return c.cuda_fail(e, "profile");
+    auto& a = agg[r.name];
+    a.first += 1;
+    a.second += t;
+  }
+  std::string out;
+  for (const auto& kv : agg)
+    out += kv.first + " " + std::to_string(kv.second.first) + " " + std::to_string(kv.second.second) + "\n";
+  const size_t n = std::min<size_t>(out.size(), (size_t)cap - 1);
+  std::memcpy(buf, out.data(), n);
+  buf[n] = 0;
   return MLMC_OK;
 }
 

@@ -57,11 +57,13 @@ struct KernelTimer {
   struct Rec {
     int op;
     size_t ev;
+    const char* name;
   };
   std::vector<Rec> recs;
   unsigned long long* units_dev = nullptr;   // [kProfOps]
   int pending_op = -1;
   size_t pending_ev = 0;
+  const char* pending_name = "";
 
   cudaEvent_t next() {
     if (used == pool.size()) {
@@ -71,17 +73,18 @@ struct KernelTimer {
     }
     return pool[used++];
   }
-  void begin(int op, cudaStream_t st) {
+  void begin(int op, cudaStream_t st, const char* name = "") {
     ++launches;
     if (!on) return;
     pending_op = op;
     pending_ev = used;
+    pending_name = name;
     cudaEventRecord(next(), st);
   }
   void end(cudaStream_t st) {
     if (pending_op < 0) return;
     cudaEventRecord(next(), st);
-    recs.push_back(Rec{pending_op, pending_ev});
+    recs.push_back(Rec{pending_op, pending_ev, pending_name});
     pending_op = -1;
   }
   void reset() {

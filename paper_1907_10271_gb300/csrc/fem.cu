@@ -383,6 +383,61 @@ struct OpPre : OpBase<T> {
   __device__ void finish(const SampleState&, int) {}
 };
 
+// Coarse-level smoothing with the restriction fused in: b = P^T r1_f (full weighting)
+// is gathered from the finer level's residual (xc), kept for the post-smoothing (o1),
+// then x1 = w D^-1 b, r1 = b - K x1 (o2). winvd of this level.
+template <typename T>
+struct OpPreR : OpBase<T> {
+  struct Raw {
+    V2<T> b, w;
+  };
+  bool act;
+  int nxf, nyf;
+  int64_t fbase;
+  V2<T> bt, bb;
+  __device__ OpPreR(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
+    act = S.active[v.sbase + s] != 0;
+    nxf = 2 * v.g.nx;
+    nyf = 2 * v.g.ny;
+    fbase = (int64_t)s * 2 * (nxf + 1) * (nyf + 1);
+  }
+  __device__ bool live() const { return act; }
+  __device__ Raw load(int i, int j) const {
+    const int64_t k = this->at(i, j);
+    Raw R;
+    R.w = ld2(this->V.winvd + k);
+    T su = (T)0, sv = (T)0;
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int jf = 2 * j + dj;
+      if (jf < 0 || jf > nyf) continue;
+      const T wj = dj == 0 ? (T)1 : (T)0.5;
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const int iff = 2 * i + di;
+        if (iff < 0 || iff > nxf) continue;
+        const T ww = wj * (di == 0 ? (T)1 : (T)0.5);
+        const V2<T> r = ld2(this->V.xc + fbase + 2 * ((int64_t)jf * (nxf + 1) + iff));
+        su += ww * r.u;
+        sv += ww * r.v;
+      }
+    }
+    R.b = this->mask(i, v2<T>(su, sv));
+    return R;
+  }
+  __device__ V2<T> in(const Raw& R, int, int) {
+    bt = R.b;
+    return v2<T>(R.w.u * R.b.u, R.w.v * R.b.v);
+  }
+  __device__ void out(int i, int j, V2<T> kx) {
+    const int64_t k = this->at(i, j);
+    st2(this->V.o1 + k, bb);
+    st2(this->V.o2 + k, this->mask(i, v2<T>(bb.u - kx.u, bb.v - kx.v)));
+  }
+  __device__ void shift() { bb = bt; }
+  __device__ void finish(const SampleState&, int) {}
+};
+
 // a = b, xc (level below), winvd; o0 = z.  TOP also reduces b . z.
 template <typename T, bool TOP>
 struct OpPost : OpBase<T> {
@@ -812,20 +867,49 @@ __global__ void __launch_bounds__(64) k_coarsest_setup(const __grid_constant__ V
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) out[idx] = A[idx / n][idx % n];
 }
 
-// x = A^-1 b at the coarsest level: a = b, ext0 = inverse (T), o0 = x. One warp per sample.
+// x = A^-1 b at the coarsest level: ext0 = inverse (T), o0 = x; b = a, or, when xc is
+// set, b = P^T r1 gathered from the finer level's residual xc. One warp per sample.
 template <typename T>
 __global__ void k_coarsest_solve(const __grid_constant__ ViewList<T> L, SampleState S) {
-  const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  __shared__ T bsh[kWarpsPerBlock][kMaxCoarsestDofs];
+  const int wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * kWarpsPerBlock + wib;
   int vi = 0;
   while (vi < L.n && gw >= L.v[vi].work_begin + L.v[vi].nwork) ++vi;
   if (vi >= L.n) return;
   const View<T>& V = L.v[vi];
   const int s = gw - V.work_begin;
   if (s >= V.nsamp || !S.active[V.sbase + s]) return;
-  const int n = 2 * (V.g.nx + 1) * (V.g.ny + 1);
-  const T* Ai = static_cast<const T*>(V.ext0) + (int64_t)s * n * n;
-  const T* b = V.a + (int64_t)s * n;
+  const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
+  const int n = 2 * (nx + 1) * (ny + 1);
   const int lane = threadIdx.x & 31;
+  T* b = bsh[wib];
+  if (V.xc) {
+    const int nxf = 2 * nx, nyf = 2 * ny;
+    const T* rf = V.xc + (int64_t)s * 2 * (nxf + 1) * (nyf + 1);
+    for (int node = lane; node < n / 2; node += 32) {
+      const int j = node / nxp, i = node - j * nxp;
+      T su = (T)0, sv = (T)0;
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int jf = 2 * j + dj;
+        if (jf < 0 || jf > nyf) continue;
+        const T wj = dj == 0 ? (T)1 : (T)0.5;
+        for (int di = -1; di <= 1; ++di) {
+          const int iff = 2 * i + di;
+          if (iff < 0 || iff > nxf) continue;
+          const T ww = wj * (di == 0 ? (T)1 : (T)0.5);
+          su += ww * rf[2 * (jf * (nxf + 1) + iff)];
+          sv += ww * rf[2 * (jf * (nxf + 1) + iff) + 1];
+        }
+      }
+      b[2 * node] = dir_u(i, nx) ? (T)0 : su;
+      b[2 * node + 1] = dir_v(i) ? (T)0 : sv;
+    }
+  } else {
+    for (int r = lane; r < n; r += 32) b[r] = V.a[(int64_t)s * n + r];
+  }
+  __syncwarp();
+  const T* Ai = static_cast<const T*>(V.ext0) + (int64_t)s * n * n;
   for (int r = lane; r < n; r += 32) {
     T acc = 0;
     for (int c = 0; c < n; ++c) acc += Ai[(int64_t)r * n + c] * b[c];
@@ -1063,6 +1147,7 @@ cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int to
     case StripOp::Apply: return launch_strip_op<T, OpApply<T>>(L, S, total_warps, st);
     case StripOp::PreTop: return launch_strip_op<T, OpPreTop<T>>(L, S, total_warps, st);
     case StripOp::Pre: return launch_strip_op<T, OpPre<T>>(L, S, total_warps, st);
+    case StripOp::PreR: return launch_strip_op<T, OpPreR<T>>(L, S, total_warps, st);
     case StripOp::Post: return launch_strip_op<T, OpPost<T, false>>(L, S, total_warps, st);
     case StripOp::PostTop: return launch_strip_op<T, OpPost<T, true>>(L, S, total_warps, st);
     case StripOp::PcgP: return launch_strip_op<T, OpPcgP<T>>(L, S, total_warps, st);

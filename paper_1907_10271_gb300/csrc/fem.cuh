@@ -70,7 +70,7 @@ struct SampleState {
 };
 
 // Strip kernels (q = K p family); see fem.cu for the operand conventions.
-enum class StripOp { Apply, PreTop, Pre, Post, PostTop, PcgP, ResidInit };
+enum class StripOp { Apply, PreTop, Pre, PreR, Post, PostTop, PcgP, ResidInit };
 
 template <typename T>
 cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st);

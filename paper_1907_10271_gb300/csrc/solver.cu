@@ -27,7 +27,7 @@ namespace mlmc {
 // Launches EXPR (a cudaError_t expression) as timer operation OP, returning on error.
 #define MLMC_LAUNCH(OP, NAME, EXPR)                      \
   do {                                                   \
-    ctx.timer.begin((OP), st);                           \
+    ctx.timer.begin((OP), st, (NAME));                   \
     const cudaError_t launch_err_ = (EXPR);              \
     ctx.timer.end(st);                                   \
     if (launch_err_ != cudaSuccess) return ctx.cuda_fail(launch_err_, (NAME)); \
@@ -305,10 +305,10 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   // launches over all groups; a group's coarse levels join the launches of their depth,
   // and all coarsest solves share one launch between the down and up sweeps.
   auto run_vcycle_and_pcg = [&](int parity, int iter) -> mlmc_status {
-    // down sweep: depth d smooths (or, at d = 0, updates PCG and smooths) and restricts
+    // down sweep: depth d gathers its right-hand side from depth d - 1 (full weighting),
+    // smooths and forms its residual; depth 0 updates the PCG iterate first
     for (int d = 0; d < dmax; ++d) {
-      ViewList<T> Lsm = empty_list<T>(ctx), Lres = empty_list<T>(ctx);
-      std::vector<int64_t> per_res;
+      ViewList<T> Lsm = empty_list<T>(ctx);
       for (auto& g : G) {
         if (d >= g.nl - 1) continue;
         View<T> v = base_view(g, d);
@@ -321,40 +321,31 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
           v.o1 = g.r[parity ^ 1];
           v.o2 = g.r1[0];
         } else {
-          v.a = g.b[d];
+          v.xc = g.r1[d - 1];
+          v.o1 = g.b[d];
           v.winvd = g.winvd[d];
           v.o2 = g.r1[d];
         }
         Lsm.v[Lsm.n++] = v;
-        View<T> r = base_view(g, d);
-        r.a = g.r1[d];
-        r.o0 = g.b[d + 1];
-        Lres.v[Lres.n++] = r;
-        per_res.push_back((int64_t)(g.geo[d].nx / 2 + 1) * (g.geo[d].ny / 2 + 1));
       }
-      if (Lsm.n) {
-        const int tw = finalize_warps(Lsm);
-        if (d == 0) {
-          Lsm.prof_op = kProfPreTop;
-          MLMC_LAUNCH(kProfPreTop, "pre_top", launch_strip<T>(StripOp::PreTop, Lsm, S, tw, st));
-        } else {
-          Lsm.prof_op = kProfPre;
-          MLMC_LAUNCH(kProfPre, "pre", launch_strip<T>(StripOp::Pre, Lsm, S, tw, st));
-        }
-      }
-      if (Lres.n) {
-        const int tt = finalize_points(Lres, per_res);
-        MLMC_LAUNCH(kProfRestrict, "restrict", launch_restrict<T>(Lres, S, tt, st));
+      if (!Lsm.n) continue;
+      const int tw = finalize_warps(Lsm);
+      if (d == 0) {
+        Lsm.prof_op = kProfPreTop;
+        MLMC_LAUNCH(kProfPreTop, "pre_top", launch_strip<T>(StripOp::PreTop, Lsm, S, tw, st));
+      } else {
+        Lsm.prof_op = kProfPre;
+        MLMC_LAUNCH(kProfPre, "pre", launch_strip<T>(StripOp::PreR, Lsm, S, tw, st));
       }
     }
-    // every group's coarsest mesh
+    // every group's coarsest mesh (its right-hand side gathered from the level above)
     {
       ViewList<T> L = empty_list<T>(ctx);
       int acc = 0;
       for (auto& g : G) {
         const int k = g.nl - 1;
         View<T> v = base_view(g, k);
-        v.a = g.b[k];
+        v.xc = g.r1[k - 1];
         v.o0 = g.xl[k];
         v.ext0 = g.ainv;
         v.work_begin = acc;
