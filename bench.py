@@ -14,6 +14,7 @@ rank's time. --impl reference times the CPU oracle on a bounded sample of the sa
 workload instead.
 """
 import argparse
+import math
 import hashlib
 import json
 import os
@@ -38,7 +39,7 @@ UNIT = "level-pairs/s"
 # meshes; the coarse correction read by a prolongation is 2 B per fine node).
 BYTES_PER_NODE = {
     "pcg_update_presmooth": 8 * 5 + 8 + 8 * 3,    # r q x p w/D + trig2 ; x r' r1
-    "presmooth": 8 * 2 + 16 + 8,                   # b w/D + trig ; r1
+    "presmooth": 8 + 4 * 8 + 16 + 8 * 2,          # w/D + finer r1 (4 fine nodes) + trig ; b r1
     "postsmooth": 8 * 2 + 16 + 2 + 8,              # b w/D + trig + x_c ; x
     "postsmooth_top": 8 * 2 + 8 + 2 + 8,           # b w/D + trig2 + x_c ; z
     "search_direction": 8 * 2 + 8 + 8 * 2,         # z p + trig2 ; p' q
@@ -157,24 +158,35 @@ def _oracle_worker(args):
     basis(level)
     if level > 0:
         basis(level - 1)
-    times = []
+    times, qf, qc = [], [], []
     for i in ids:
         t = time.perf_counter()
-        om.level_pair(cfg, level, [int(i)], basis)
+        f, c = om.level_pair(cfg, level, [int(i)], basis)
         times.append(time.perf_counter() - t)
-    return times
+        qf.append(f[0])
+        qc.append(c[0])
+    return times, qf, qc
+
+
+ORACLE_FIRST_ID = 10_000_000
+
+
+def oracle_sample(cfg, fraction):
+    """Per level the number of samples the CPU oracle times (ids from ORACLE_FIRST_ID)."""
+    return [max(1, int(round(n * fraction))) for n in cfg["n_per_level"]]
 
 
 def oracle_throughput(cfg, fraction, cores):
     """Level-pairs/s of the CPU oracle on the workload mix, from a bounded sample:
     per-sample times t_l measured on fraction * N_l samples of each level (at least
-    one), then sum_l N_l / (sum_l N_l t_l / cores)."""
+    one), then sum_l N_l / (sum_l N_l t_l / cores). Also returns the oracle's
+    (Q_fine, Q_coarse) of every sampled id, in id order per level."""
     import multiprocessing as mp
     counts = cfg["n_per_level"]
-    sample = [max(1, int(round(n * fraction))) for n in counts]
+    sample = oracle_sample(cfg, fraction)
     jobs = []
     for l, s in enumerate(sample):
-        ids = np.arange(10_000_000, 10_000_000 + s)
+        ids = np.arange(ORACLE_FIRST_ID, ORACLE_FIRST_ID + s)
         for chunk in np.array_split(ids, min(s, cores)):
             if chunk.size:
                 jobs.append((cfg, l, chunk))
@@ -183,11 +195,33 @@ def oracle_throughput(cfg, fraction, cores):
         res = pool.map(_oracle_worker, jobs)
     wall = time.perf_counter() - t0
     per_level = [[] for _ in counts]
-    for (c, l, _), t in zip(jobs, res):
+    q = [([], []) for _ in counts]
+    for (c, l, _), (t, qf, qc) in zip(jobs, res):
         per_level[l] += t
+        q[l][0].extend(qf)
+        q[l][1].extend(qc)
     t_l = [float(np.mean(x)) for x in per_level]
     seconds = sum(n * t for n, t in zip(counts, t_l)) / cores
-    return sum(counts) / seconds, dict(sample=sample, t_l=t_l, wall=wall, cores=cores)
+    q = [(np.array(f), np.array(c)) for f, c in q]
+    return sum(counts) / seconds, dict(sample=sample, t_l=t_l, wall=wall, cores=cores, q=q)
+
+
+def qoi_parity(gpu_q, oracle_q):
+    """Largest relative difference of each quantity (reaction, stress) between the GPU
+    batch solve and the oracle's sparse direct solve on the same sampled ids."""
+    worst = [0.0, 0.0]
+    pairs = 0
+    for (gf, gc), (of, oc) in zip(gpu_q, oracle_q):
+        pairs += len(of)
+        for g, o in ((gf, of), (gc, oc)):
+            for k in range(2):
+                scale = np.maximum(np.abs(o[:, k]), 1e-300)
+                nz = np.abs(o[:, k]) > 0
+                if nz.any():
+                    worst[k] = max(worst[k], float((np.abs(g[nz, k] - o[nz, k]) / scale[nz]).max()))
+    return {"pairs": pairs, "max_rel_err": {"reaction": worst[0], "stress": worst[1]},
+            "note": "GPU (batched mixed-precision GMG-PCG, rtol 1e-8) vs oracle (SuperLU, FP64) "
+                    "on the cpu_baseline sample's ids, both meshes of each pair"}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -331,6 +365,42 @@ def run_gpu(a):
                             if k in BYTES_PER_NODE and v[0] > 0 else None)}
                for k, v in prof.items() if v[1] > 0}
     clocks = clk.summary()
+
+    # ---- latency: every sample of a step completes with the step (one lock-stepped
+    # batch), so a sample's latency is its step's; plus one level pair alone per call
+    def pct(xs, p):
+        xs = sorted(xs)
+        return round(xs[min(len(xs) - 1, int(math.ceil(p / 100.0 * len(xs))) - 1)], 3)
+
+    q1 = torch.zeros(2, dtype=torch.float64, device="cuda")
+    q2 = torch.zeros_like(q1)
+    single = []
+    for level in levels:
+        B.mlmc_sample_level(ctx, level, 1 << 52, 1, q1, q2)      # warm the level's workspace
+        lat = []
+        for k in range(8):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.mlmc_sample_level(ctx, level, (1 << 52) + 1 + 64 * rank + k, 1, q1, q2)
+            e1.record(stream)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1))
+        single.append({"level": level, "p50": pct(lat, 50), "p99": pct(lat, 99), "calls": len(lat)})
+    latency = {"unit": "ms", "step": {"p50": pct(times, 50), "p99": pct(times, 99), "steps": len(times)},
+               "single_pair": single,
+               "note": "a sample's latency inside a step is the step's (all samples of the batch finish "
+                       "together); single_pair = one level pair per mlmc_sample_level call"}
+
+    # ---- the GPU's QoIs on the ids the CPU oracle samples (compared in main)
+    gpu_q = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        gpu_q = []
+        for level, n in enumerate(oracle_sample(cfg, a.cpu_fraction)):
+            f = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+            c = torch.zeros_like(f)
+            B.mlmc_sample_level(ctx, level, ORACLE_FIRST_ID, n, f, c)
+            gpu_q.append((f.cpu().numpy().reshape(n, 2), c.cpu().numpy().reshape(n, 2)))
     B.mlmc_destroy(ctx)
 
     # ---- comparison point: the plain double-precision form, one sample per call
@@ -357,7 +427,7 @@ def run_gpu(a):
                "fp64_single_sample": fp64,
                "speedup_vs_fp64_single_sample": (round(value / world / fp64["value"], 1) if fp64 else None),
                "gpu_launches": launches // a.steps,
-               "gpu_launches_total": launches, "clocks": clocks}
+               "gpu_launches_total": launches, "clocks": clocks, "latency": latency, "_gpu_q": gpu_q}
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -422,6 +492,9 @@ def main():
                                              "extrapolated to the workload mix" %
                                              (info["sample"], [round(t, 4) for t in info["t_l"]]),
                                    "wall_s": round(info["wall"], 1)}
+            if out.get("_gpu_q") is not None:
+                out["qoi_parity"] = qoi_parity(out["_gpu_q"], info["q"])
+        out.pop("_gpu_q", None)
         print(json.dumps(out))
 
 

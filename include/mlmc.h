@@ -224,15 +224,14 @@ const char* mlmc_static_last_error(void);
 /* Operation ids of the kernel timer. */
 enum {
   MLMC_OP_PCG_UPDATE_PRESMOOTH = 0, /* PCG update + finest-level smoothing + residual */
-  MLMC_OP_PRESMOOTH = 1,            /* coarse-level smoothing + residual */
+  MLMC_OP_PRESMOOTH = 1,            /* coarse-level restriction + smoothing + residual */
   MLMC_OP_POSTSMOOTH = 2,           /* coarse-level prolongation + smoothing */
   MLMC_OP_POSTSMOOTH_TOP = 3,       /* finest-level prolongation + smoothing + r.z */
   MLMC_OP_SEARCH_DIRECTION = 4,     /* p = z + beta p, q = K p, p.q */
   MLMC_OP_REFINEMENT_RESIDUAL = 5,  /* double-precision r = f - K d, reaction */
-  MLMC_OP_RESTRICT = 6,
-  MLMC_OP_COARSEST = 7,
-  MLMC_OP_OTHER = 8,
-  MLMC_OP_COUNT = 9
+  MLMC_OP_COARSEST = 6,
+  MLMC_OP_OTHER = 7,
+  MLMC_OP_COUNT = 8
 };
 
 /* on != 0: from now on record CUDA events around every launch of the operations

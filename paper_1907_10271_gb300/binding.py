@@ -241,7 +241,7 @@ def mlmc_sample_levels(ctx, levels, first_ids, counts, q_fine=None, q_coarse=Non
 
 
 PROFILE_OPS = ["pcg_update_presmooth", "presmooth", "postsmooth", "postsmooth_top", "search_direction",
-               "refinement_residual", "restrict", "coarsest", "other"]
+               "refinement_residual", "coarsest", "other"]
 
 
 def mlmc_profile_enable(ctx, on=True):

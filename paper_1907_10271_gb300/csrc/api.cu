@@ -467,6 +467,8 @@ mlmc_status mlmc_profile_enable(mlmc_ctx* h, int32_t on) {
   return MLMC_OK;
 }
 
+static_assert(mlmc::kProfOps == MLMC_OP_COUNT, "kernel timer operations and MLMC_OP_* ids differ");
+
 mlmc_status mlmc_profile_get(mlmc_ctx* h, int32_t op, double* ms_total, int64_t* launches, uint64_t* nodes) {
   if (!h) return MLMC_ERR_INVALID_ARG;
   Context& c = h->c;

@@ -356,33 +356,6 @@ struct OpPreTop : OpBase<T> {
   }
 };
 
-// a = b, winvd; o2 = r1.
-template <typename T>
-struct OpPre : OpBase<T> {
-  struct Raw {
-    V2<T> b, w;
-  };
-  bool act;
-  V2<T> bt, bb;
-  __device__ OpPre(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
-    act = S.active[v.sbase + s] != 0;
-  }
-  __device__ bool live() const { return act; }
-  __device__ Raw load(int i, int j) const {
-    const int64_t k = this->at(i, j);
-    return Raw{ld2(this->V.a + k), ld2(this->V.winvd + k)};
-  }
-  __device__ V2<T> in(const Raw& R, int, int) {
-    bt = R.b;
-    return v2<T>(R.w.u * R.b.u, R.w.v * R.b.v);
-  }
-  __device__ void out(int i, int j, V2<T> kx) {
-    st2(this->V.o2 + this->at(i, j), this->mask(i, v2<T>(bb.u - kx.u, bb.v - kx.v)));
-  }
-  __device__ void shift() { bb = bt; }
-  __device__ void finish(const SampleState&, int) {}
-};
-
 // Coarse-level smoothing with the restriction fused in: b = P^T r1_f (full weighting)
 // is gathered from the finer level's residual (xc), kept for the post-smoothing (o1),
 // then x1 = w D^-1 b, r1 = b - K x1 (o2). winvd of this level.
@@ -674,43 +647,6 @@ __device__ __forceinline__ bool find_point(const ViewList<T>& L, int64_t gt, int
   if (vi >= L.n) return false;
   local = gt - L.v[vi].work_begin;
   return true;
-}
-
-// Full-weighting restriction b_c = P^T r1: views at the fine level, a = r1 (fine),
-// o0 = b (coarse). One thread per coarse node.
-template <typename T>
-__global__ void k_restrict(const __grid_constant__ ViewList<T> L, SampleState S) {
-  int vi;
-  int64_t loc;
-  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
-  const View<T>& V = L.v[vi];
-  const int nx = V.g.nx, ny = V.g.ny, nxc = nx / 2, nyc = ny / 2;
-  const int per = (nxc + 1) * (nyc + 1);
-  const int s = (int)(loc / per);
-  if (s >= V.nsamp) return;
-  if (!S.active[V.sbase + s]) return;
-  const int node = (int)(loc - (int64_t)s * per);
-  const int J = node / (nxc + 1), I = node - J * (nxc + 1);
-  const int64_t fb = (int64_t)s * 2 * (nx + 1) * (ny + 1);
-  T su = 0, sv = 0;
-#pragma unroll
-  for (int dj = -1; dj <= 1; ++dj) {
-    const int j = 2 * J + dj;
-    if (j < 0 || j > ny) continue;
-    const T wj = dj == 0 ? (T)1 : (T)0.5;
-#pragma unroll
-    for (int di = -1; di <= 1; ++di) {
-      const int i = 2 * I + di;
-      if (i < 0 || i > nx) continue;
-      const T ww = wj * (di == 0 ? (T)1 : (T)0.5);
-      const V2<T> r = ld2(V.a + fb + 2 * ((int64_t)j * (nx + 1) + i));
-      su += ww * r.u;
-      sv += ww * r.v;
-    }
-  }
-  if (dir_u(I, nxc)) su = 0;
-  if (dir_v(I)) sv = 0;
-  st2(V.o0 + (int64_t)s * 2 * per + 2 * node, v2<T>(su, sv));
 }
 
 // Coarse element data: o0 = trig (coarse, 4 per element) from the fine level's
@@ -1146,7 +1082,6 @@ cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int to
   switch (op) {
     case StripOp::Apply: return launch_strip_op<T, OpApply<T>>(L, S, total_warps, st);
     case StripOp::PreTop: return launch_strip_op<T, OpPreTop<T>>(L, S, total_warps, st);
-    case StripOp::Pre: return launch_strip_op<T, OpPre<T>>(L, S, total_warps, st);
     case StripOp::PreR: return launch_strip_op<T, OpPreR<T>>(L, S, total_warps, st);
     case StripOp::Post: return launch_strip_op<T, OpPost<T, false>>(L, S, total_warps, st);
     case StripOp::PostTop: return launch_strip_op<T, OpPost<T, true>>(L, S, total_warps, st);
@@ -1159,13 +1094,6 @@ cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int to
 template <typename TI>
 cudaError_t launch_resid64(const ViewList<double>& L, SampleState S, int total_warps, cudaStream_t st) {
   return launch_strip_op<double, OpResid<TI>>(L, S, total_warps, st);
-}
-
-template <typename T>
-cudaError_t launch_restrict(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st) {
-  if (total_threads <= 0) return cudaSuccess;
-  k_restrict<T><<<blocks_for(total_threads, 256), 256, 0, st>>>(L, S);
-  return cudaGetLastError();
 }
 
 template <typename T>
@@ -1259,7 +1187,6 @@ cudaError_t launch_outer_check(SampleState S, int total, double rtol, double flo
 
 #define MLMC_INST(T)                                                                                        \
   template cudaError_t launch_strip<T>(StripOp, const ViewList<T>&, SampleState, int, cudaStream_t);       \
-  template cudaError_t launch_restrict<T>(const ViewList<T>&, SampleState, int, cudaStream_t);             \
   template cudaError_t launch_trig_average<T>(const ViewList<T>&, int, cudaStream_t);                      \
   template cudaError_t launch_invdiag<T>(const ViewList<T>&, int, cudaStream_t);                           \
   template cudaError_t launch_coarsest_setup<T>(const ViewList<T>&, int, cudaStream_t);                    \

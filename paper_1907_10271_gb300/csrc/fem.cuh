@@ -35,8 +35,8 @@ struct View {
 };
 
 // Operation ids of the kernel timer (mlmc_profile_get).
-enum ProfOp { kProfPreTop = 0, kProfPre, kProfPost, kProfPostTop, kProfPcgP, kProfResid, kProfRestrict,
-              kProfCoarsest, kProfOther, kProfOps };
+enum ProfOp { kProfPreTop = 0, kProfPre, kProfPost, kProfPostTop, kProfPcgP, kProfResid, kProfCoarsest,
+              kProfOther, kProfOps };
 
 template <typename T>
 struct ViewList {
@@ -70,7 +70,7 @@ struct SampleState {
 };
 
 // Strip kernels (q = K p family); see fem.cu for the operand conventions.
-enum class StripOp { Apply, PreTop, Pre, PreR, Post, PostTop, PcgP, ResidInit };
+enum class StripOp { Apply, PreTop, PreR, Post, PostTop, PcgP, ResidInit };
 
 template <typename T>
 cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st);
@@ -78,9 +78,6 @@ cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int to
 // Refinement residual r = -(K d) on free DOFs (double d, T output), ||r||^2 and reaction.
 template <typename TI>
 cudaError_t launch_resid64(const ViewList<double>& L, SampleState S, int total_warps, cudaStream_t st);
-
-template <typename T>
-cudaError_t launch_restrict(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_trig_average(const ViewList<T>& L, int total_threads, cudaStream_t st);
