@@ -37,13 +37,14 @@ UNIT = "level-pairs/s"
 # (2 DOF per node: float2 vectors 8 B; per-element data, one element per node:
 # (cos 2t, sin 2t) 8 B on the finest mesh, averaged trig 4-vector 16 B on coarse
 # meshes; the coarse correction read by a prolongation is 2 B per fine node).
+# The smoother reads 12 B per node (W: u self and v coefficients 8 B, u pair coefficient 4 B).
 BYTES_PER_NODE = {
-    "pcg_update_presmooth": 8 * 5 + 8 + 8 * 3,    # r q x p w/D + trig2 ; x r' r1
-    "presmooth": 8 + 4 * 8 + 16 + 8 * 2,          # w/D + finer r1 (4 fine nodes) + trig ; b r1
-    "postsmooth": 8 * 2 + 16 + 2 + 8,              # b w/D + trig + x_c ; x
-    "postsmooth_top": 8 * 2 + 8 + 2 + 8,           # b w/D + trig2 + x_c ; z
-    "search_direction": 8 * 2 + 8 + 8 * 2,         # z p + trig2 ; p' q
-    "refinement_residual": 16 + 8 + 8,             # d (double) + trig2 ; r (float)
+    "pcg_update_presmooth": 8 * 4 + 12 + 8 + 8 * 3,   # r q x p + W + trig2 ; x r' r1
+    "presmooth": 12 + 4 * 8 + 16 + 8 * 2,            # W + finer r1 (4 fine nodes) + trig ; b r1
+    "postsmooth": 8 + 12 + 16 + 2 + 8,                # b + W + trig + x_c ; x
+    "postsmooth_top": 8 + 12 + 8 + 2 + 8,             # b + W + trig2 + x_c ; z
+    "search_direction": 8 * 2 + 8 + 8 * 2,            # z p + trig2 ; p' q
+    "refinement_residual": 16 + 8 + 8,                # d (double) + trig2 ; r (float)
 }
 
 

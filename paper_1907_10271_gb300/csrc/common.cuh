@@ -28,11 +28,17 @@ namespace mlmc {
 
 constexpr int kWarp = 32;
 constexpr int kStripCols = 30;     // output node columns per warp strip (32 lanes, 1 halo each side)
+constexpr int kSmoothCols = 28;    // strips of the smoothing kernels (2 halo lanes each side, so that
+                                   // every node pair {2m, 2m+1} of the smoother lies in one warp)
 constexpr int kRowChunk = 32;      // output node rows per warp tile
 constexpr int kPrefetch32 = 1;     // node rows in flight per warp (FP32 kernels)
 constexpr int kPrefetch64 = 2;     // node rows in flight per warp (FP64 kernels)
 constexpr int kWarpsPerBlock = 4;
-constexpr double kOmega = 0.5;     // Jacobi damping: element bound of lambda_max(D^-1 K) < 3.9 for any angle
+// Smoother damping. The smoother is block Jacobi whose blocks are the u-DOFs of the
+// node pairs {(2m, j), (2m+1, j)} (the strong fibre-direction coupling) and single
+// v-DOFs; the block graph of the 9-point stencil is 4-colourable, so
+// lambda_max(B^-1 K) <= 4 and w = 1/2 keeps the smoother convergent for any angle field.
+constexpr double kOmega = 0.5;
 constexpr int kMaxCoarsestDofs = 64;
 
 struct Invariants {
@@ -202,8 +208,15 @@ struct Geo {
   int nodes() const { return (nx + 1) * (ny + 1); }
 };
 
-__host__ __device__ __forceinline__ int strips_of(int nx) { return (nx + 1 + kStripCols - 1) / kStripCols; }
+__host__ __device__ __forceinline__ int strips_of(int nx, int cols = kStripCols) { return (nx + 1 + cols - 1) / cols; }
 __host__ __device__ __forceinline__ int chunks_of(int ny) { return (ny + 1 + kRowChunk - 1) / kRowChunk; }
+
+// Kuu coupling of the two nodes of one horizontal element edge (exact, = 2x2 Gauss):
+// w (-4/3 C11 rx^2 + 2/3 C66 ry^2); the C16 terms cancel on such an edge.
+template <typename T>
+__device__ __forceinline__ T element_edge_uu(const Coef<T>& C, T rx, T ry, T w) {
+  return w * ((T)(-4.0 / 3.0) * C.c11 * rx * rx + (T)(2.0 / 3.0) * C.c66 * ry * ry);
+}
 
 // Dirichlet DOFs: u = v = 0 on column 0, u prescribed on column nx.
 __device__ __forceinline__ bool dir_u(int i, int nx) { return i == 0 || i == nx; }

@@ -173,17 +173,21 @@ struct RawE {
 
 // Walks the warp's strip up its chunk of node rows. Node-row data is prefetched P
 // rows ahead into a register ring (static indices after unrolling), element data P
-// element rows ahead, so each warp keeps P rows of loads in flight.
+// element rows ahead, so each warp keeps P rows of loads in flight. Lane l holds node
+// column strip * kCols - kHalo + l; lanes kHalo .. kHalo + kCols - 1 are the outputs.
+// in()/pair() and out() run on every lane (pair() and out() of the smoothing handlers
+// exchange values with lane l ^ 1); out() stores only where is_out.
 template <typename T, int P, typename Op>
 __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V, int strip, int chunk, Op& op) {
   using Val = typename Op::Val;
   using Sc = typename Op::Sc;
+  constexpr int kCols = Op::kCols, kHalo = Op::kHalo;
   const int lane = threadIdx.x & (kWarp - 1);
   const int nx = V.g.nx, ny = V.g.ny;
-  const int i = strip * kStripCols - 1 + lane;
+  const int i = strip * kCols - kHalo + lane;
   const bool col_in = (i >= 0) && (i <= nx);
   const bool elem = (i >= 0) && (i < nx) && (lane < kWarp - 1);
-  const bool out_col = col_in && lane >= 1 && lane <= kStripCols;
+  const bool out_col = col_in && lane >= kHalo && lane < kHalo + kCols;
   const int ic = min(max(i, 0), nx);       // in-bounds column for (discarded) loads of outside lanes
   const int ie = min(max(i, 0), nx - 1);
   const int j0 = chunk * kRowChunk;
@@ -196,7 +200,7 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
   V2<Val> pb;
   {
     const typename Op::Raw r0 = op.load(ic, er0);
-    pb = col_in ? op.in(r0, i, er0) : zero2<Val>();
+    pb = op.pair(col_in ? op.in(r0, i, er0) : zero2<Val>(), col_in);
     op.shift();
   }
 #pragma unroll
@@ -214,7 +218,7 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
         const RawE<typename Op::E> ce = ering[u];
         if (er + 1 + P <= er1 + 1) ring[u] = op.load(ic, er + 1 + P);
         if (er + P <= er1) ering[u] = op.loadE(ie, er + P);
-        const V2<Val> pt = col_in ? op.in(cur, i, er + 1) : zero2<Val>();
+        const V2<Val> pt = op.pair(col_in ? op.in(cur, i, er + 1) : zero2<Val>(), col_in);
         const V2<Val> pbr = shfl_down2(pb), ptr = shfl_down2(pt);
         V2<Val> o1 = zero2<Val>(), o2 = zero2<Val>(), o3 = zero2<Val>(), o4 = zero2<Val>();
         if (elem) op.element(U, ce, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
@@ -225,7 +229,7 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
         }
         acc.u = acc.u + (o1.u + fb.u);
         acc.v = acc.v + (o1.v + fb.v);
-        if (er >= j0 && out_col) op.out(i, er, acc);
+        if (er >= j0) op.out(i, er, acc, out_col);
         acc.u = o4.u + ft.u;
         acc.v = o4.v + ft.v;
         op.shift();
@@ -234,7 +238,7 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
     }
   }
   // the top boundary row (only element row ny - 1 contributes) belongs to the chunk that owns it
-  if (er1 + 1 == ny && ny >= j0 && ny <= j1 && out_col) op.out(i, ny, acc);
+  if (er1 + 1 == ny && ny >= j0 && ny <= j1) op.out(i, ny, acc, out_col);
 }
 
 // ---------------------------------------------------------------- operand handlers
@@ -248,6 +252,8 @@ struct OpBase {
   using Val = T;   // register type of node values
   using Sc = T;    // scalar type of stiffness and geometry
   static constexpr int kP32 = kPrefetch32;   // rows in flight of the FP32 variant
+  static constexpr int kCols = kStripCols;    // output columns per strip
+  static constexpr int kHalo = 1;             // halo lanes on each side
   const View<T>& V;
   int64_t nbase;   // first value of the sample's vectors
   int64_t ebase;   // first element of the sample
@@ -283,6 +289,8 @@ struct OpBase {
   __device__ __forceinline__ Coef<T> coef(const Invariants& U, const RawE<T>& r) const {
     return V.trig2 ? coef_from_trig2<T>(U, r.a, r.b) : coef_from_trig<T>(U, r.a, r.b, r.c, r.d);
   }
+  // value K is applied to, after the smoother's pair exchange (none by default)
+  __device__ __forceinline__ V2<T> pair(V2<T> x, bool) { return x; }
   __device__ __forceinline__ V2<T> mask(int i, V2<T> x) const {
     if (dir_u(i, V.g.nx)) x.u = (T)0;
     if (dir_v(i)) x.v = (T)0;
@@ -308,16 +316,36 @@ struct OpApply : OpBase<T> {
   __device__ bool live() const { return true; }
   __device__ Raw load(int i, int j) const { return ld2(this->V.a + this->at(i, j)); }
   __device__ V2<T> in(const Raw& r, int, int) { return r; }
-  __device__ void out(int i, int j, V2<T> kp) { st2(this->V.o0 + this->at(i, j), kp); }
+  __device__ void out(int i, int j, V2<T> kp, bool is_out) {
+    if (is_out) st2(this->V.o0 + this->at(i, j), kp);
+  }
   __device__ void shift() {}
   __device__ void finish(const SampleState&, int) {}
 };
 
-// a = r (old), b = q, c = p, winvd, o0 = x (read and updated); o1 = r (new), o2 = r1.
+// Smoother of the pre-smoothing from zero, x1 = W b, for the handlers below: u gets
+// its own and its pair partner's term (lane ^ 1, see kOmega), v its own.
+template <typename T>
+struct PairSmooth {
+  T own_u, cross;   // the row being prepared: b.u and this node's partner coefficient
+  __device__ __forceinline__ void set(T bu, T c) {
+    own_u = bu;
+    cross = c;
+  }
+  // every lane calls this (shuffle); lanes outside the mesh send and get nothing
+  __device__ __forceinline__ T partner_term(bool col_in) const {
+    const T other = __shfl_xor_sync(0xffffffffu, col_in ? own_u : (T)0, 1);
+    return col_in ? cross * other : (T)0;
+  }
+};
+
+// a = r (old), b = q, c = p, winvd + wc, o0 = x (read and updated); o1 = r (new), o2 = r1.
 template <typename T>
 struct OpPreTop : OpBase<T> {
+  static constexpr int kCols = kSmoothCols, kHalo = 2;
   struct Raw {
     V2<T> r, q, w, x, p;
+    T c;
   };
   struct Aux {
     V2<T> r, x, p;
@@ -325,6 +353,7 @@ struct OpPreTop : OpBase<T> {
   T alpha;
   bool act;
   Aux at_, ab_;
+  PairSmooth<T> ps;
   LaneSum<T> rr;
   __device__ OpPreTop(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
     act = S.active[v.sbase + s] != 0;
@@ -334,15 +363,21 @@ struct OpPreTop : OpBase<T> {
   __device__ Raw load(int i, int j) const {
     const int64_t k = this->at(i, j);
     return Raw{ld2(this->V.a + k), ld2(this->V.b + k), ld2(this->V.winvd + k), ld2(this->V.o0 + k),
-               ld2(this->V.c + k)};
+               ld2(this->V.c + k), this->V.wc[k >> 1]};
   }
   __device__ V2<T> in(const Raw& R, int, int) {
     at_.r = v2<T>(R.r.u - alpha * R.q.u, R.r.v - alpha * R.q.v);
     at_.x = R.x;
     at_.p = R.p;
+    ps.set(at_.r.u, R.c);
     return v2<T>(R.w.u * at_.r.u, R.w.v * at_.r.v);
   }
-  __device__ void out(int i, int j, V2<T> kx) {
+  __device__ V2<T> pair(V2<T> x1, bool col_in) {
+    x1.u += ps.partner_term(col_in);
+    return x1;
+  }
+  __device__ void out(int i, int j, V2<T> kx, bool is_out) {
+    if (!is_out) return;
     const int64_t k = this->at(i, j);
     st2(this->V.o2 + k, this->mask(i, v2<T>(ab_.r.u - kx.u, ab_.r.v - kx.v)));
     st2(this->V.o1 + k, ab_.r);
@@ -358,16 +393,19 @@ struct OpPreTop : OpBase<T> {
 
 // Coarse-level smoothing with the restriction fused in: b = P^T r1_f (full weighting)
 // is gathered from the finer level's residual (xc), kept for the post-smoothing (o1),
-// then x1 = w D^-1 b, r1 = b - K x1 (o2). winvd of this level.
+// then x1 = W b, r1 = b - K x1 (o2). winvd and wc of this level.
 template <typename T>
 struct OpPreR : OpBase<T> {
+  static constexpr int kCols = kSmoothCols, kHalo = 2;
   struct Raw {
     V2<T> b, w;
+    T c;
   };
   bool act;
   int nxf, nyf;
   int64_t fbase;
   V2<T> bt, bb;
+  PairSmooth<T> ps;
   __device__ OpPreR(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
     act = S.active[v.sbase + s] != 0;
     nxf = 2 * v.g.nx;
@@ -379,6 +417,7 @@ struct OpPreR : OpBase<T> {
     const int64_t k = this->at(i, j);
     Raw R;
     R.w = ld2(this->V.winvd + k);
+    R.c = this->V.wc[k >> 1];
     T su = (T)0, sv = (T)0;
 #pragma unroll
     for (int dj = -1; dj <= 1; ++dj) {
@@ -400,9 +439,15 @@ struct OpPreR : OpBase<T> {
   }
   __device__ V2<T> in(const Raw& R, int, int) {
     bt = R.b;
+    ps.set(R.b.u, R.c);
     return v2<T>(R.w.u * R.b.u, R.w.v * R.b.v);
   }
-  __device__ void out(int i, int j, V2<T> kx) {
+  __device__ V2<T> pair(V2<T> x1, bool col_in) {
+    x1.u += ps.partner_term(col_in);
+    return x1;
+  }
+  __device__ void out(int i, int j, V2<T> kx, bool is_out) {
+    if (!is_out) return;
     const int64_t k = this->at(i, j);
     st2(this->V.o1 + k, bb);
     st2(this->V.o2 + k, this->mask(i, v2<T>(bb.u - kx.u, bb.v - kx.v)));
@@ -411,17 +456,22 @@ struct OpPreR : OpBase<T> {
   __device__ void finish(const SampleState&, int) {}
 };
 
-// a = b, xc (level below), winvd; o0 = z.  TOP also reduces b . z.
+// a = b, xc (level below), winvd + wc; o0 = z = x2 + W (b - K x2) with x2 = W b + P xc.
+// TOP also reduces b . z.
 template <typename T, bool TOP>
 struct OpPost : OpBase<T> {
   static constexpr int kP32 = 1;   // row record plus in-line coarse loads: keep registers low
+  static constexpr int kCols = kSmoothCols, kHalo = 2;
   struct Raw {
     V2<T> b, w;
+    T c;
   };
   bool act;
   int nxc;
   int64_t cbase;
   V2<T> bt, bb, xt, xb, wt, wb;
+  T ct, cb;
+  PairSmooth<T> ps;
   LaneSum<T> rz;
   __device__ OpPost(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
     act = S.active[v.sbase + s] != 0;
@@ -432,7 +482,7 @@ struct OpPost : OpBase<T> {
   __device__ V2<T> coarse(int I, int J) const { return ld2(this->V.xc + cbase + 2 * ((int64_t)J * (nxc + 1) + I)); }
   __device__ Raw load(int i, int j) const {
     const int64_t k = this->at(i, j);
-    return Raw{ld2(this->V.a + k), ld2(this->V.winvd + k)};
+    return Raw{ld2(this->V.a + k), ld2(this->V.winvd + k), this->V.wc[k >> 1]};
   }
   // bilinear prolongation of the coarse correction; the coarse vector is a quarter of
   // the fine one and each value serves up to four neighbouring fine nodes (L1 hits)
@@ -455,11 +505,23 @@ struct OpPost : OpBase<T> {
     const T f = (fi && fj) ? (T)0.25 : ((fi || fj) ? (T)0.5 : (T)1);
     bt = R.b;
     wt = R.w;
+    ct = R.c;
+    ps.set(R.b.u, R.c);
     xt = v2<T>(R.w.u * R.b.u + f * c.u, R.w.v * R.b.v + f * c.v);
     return xt;
   }
-  __device__ void out(int i, int j, V2<T> kx) {
-    const V2<T> z = this->mask(i, v2<T>(xb.u + wb.u * (bb.u - kx.u), xb.v + wb.v * (bb.v - kx.v)));
+  __device__ V2<T> pair(V2<T> x, bool col_in) {
+    const T t = ps.partner_term(col_in);
+    if (!col_in) return x;
+    xt.u += t;
+    return xt;
+  }
+  // every lane forms its residual; output lanes pair with output lanes (kHalo even)
+  __device__ void out(int i, int j, V2<T> kx, bool is_out) {
+    const V2<T> res = v2<T>(bb.u - kx.u, bb.v - kx.v);
+    const T other = __shfl_xor_sync(0xffffffffu, res.u, 1);
+    if (!is_out) return;
+    const V2<T> z = this->mask(i, v2<T>(xb.u + wb.u * res.u + cb * other, xb.v + wb.v * res.v));
     st2(this->V.o0 + this->at(i, j), z);
     if (TOP) rz.add(bb.u * z.u + bb.v * z.v);
   }
@@ -467,6 +529,7 @@ struct OpPost : OpBase<T> {
     bb = bt;
     xb = xt;
     wb = wt;
+    cb = ct;
   }
   __device__ void finish(const SampleState& S, int s) {
     if (TOP) {
@@ -499,7 +562,8 @@ struct OpPcgP : OpBase<T> {
     pt = v2<T>(R.z.u + beta * R.p.u, R.z.v + beta * R.p.v);
     return pt;
   }
-  __device__ void out(int i, int j, V2<T> kp) {
+  __device__ void out(int i, int j, V2<T> kp, bool is_out) {
+    if (!is_out) return;
     const int64_t k = this->at(i, j);
     const V2<T> q = this->mask(i, kp);
     st2(this->V.o0 + k, pb);
@@ -530,7 +594,8 @@ struct OpResidInit : OpBase<T> {
   __device__ bool live() const { return act; }
   __device__ Raw load(int, int) const { return Raw{}; }
   __device__ V2<T> in(const Raw&, int i, int) { return v2<T>(i == this->V.g.nx ? -shortening : (T)0, (T)0); }
-  __device__ void out(int i, int j, V2<T> kd) {
+  __device__ void out(int i, int j, V2<T> kd, bool is_out) {
+    if (!is_out) return;
     const V2<T> r = this->mask(i, v2<T>(-kd.u, -kd.v));
     st2(this->V.o0 + this->at(i, j), r);
     rr += (double)r.u * r.u + (double)r.v * r.v;
@@ -591,13 +656,15 @@ struct OpResid : OpBase<double> {
     return v2<Val>(to_val(d.u), to_val(d.v));
   }
   __device__ V2<Val> in(const Raw& d, int, int) { return d; }
+  __device__ V2<Val> pair(V2<Val> x, bool) { return x; }
   __device__ void element(const Invariants& U, const RawE<TI>& ce, TI rx, TI ry, TI w, V2<Val> n1, V2<Val> n2,
                           V2<Val> n3, V2<Val> n4, V2<Val>& o1, V2<Val>& o2, V2<Val>& o3, V2<Val>& o4) const {
     const Coef<TI> C = coef_from_trig2<TI>(U, ce.a, ce.b);
     if constexpr (sizeof(TI) == 4) element_apply_df(C, rx, ry, w, n1, n2, n3, n4, o1, o2, o3, o4);
     else element_apply<double>(C, rx, ry, w, n1, n2, n3, n4, o1, o2, o3, o4);
   }
-  __device__ void out(int i, int j, V2<Val> kd) {
+  __device__ void out(int i, int j, V2<Val> kd, bool is_out) {
+    if (!is_out) return;
     const int64_t k = at(i, j);
     const TI ru = dir_u(i, V.g.nx) ? (TI)0 : -head(kd.u);
     const TI rv = dir_v(i) ? (TI)0 : -head(kd.v);
@@ -626,11 +693,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * kWarp)
   int vi, s, strip, chunk;
   if (!find_tile(L, gw, vi, s, strip, chunk)) return;
   const View<T>& V = L.v[vi];
-  const int col = strip * kStripCols - 1 + (int)(threadIdx.x & 31);
+  const int col = strip * Op::kCols - Op::kHalo + (int)(threadIdx.x & 31);
   Op op(V, s, min(max(col, 0), V.g.nx), min(max(col, 0), V.g.nx - 1), S);
   if (!op.live()) return;
   if (S.units && (threadIdx.x & 31) == 0) {
-    const int c0 = max(strip * kStripCols, 0), c1 = min(strip * kStripCols + kStripCols - 1, V.g.nx);
+    const int c0 = max(strip * Op::kCols, 0), c1 = min(strip * Op::kCols + Op::kCols - 1, V.g.nx);
     const int r0 = chunk * kRowChunk, r1 = min(r0 + kRowChunk - 1, V.g.ny);
     atomicAdd(&S.units[L.prof_op], (unsigned long long)((c1 - c0 + 1) * (r1 - r0 + 1)));
   }
@@ -682,7 +749,37 @@ __global__ void k_trig_average(const __grid_constant__ ViewList<T> L) {
   for (int c = 0; c < 4; ++c) o[c] = (T)0.25 * acc[c];
 }
 
-// o0 = w / diag(K) (zero on Dirichlet DOFs). One thread per node.
+template <typename T>
+__device__ __forceinline__ Coef<T> element_coef(const ViewList<T>& L, const View<T>& V, int64_t e) {
+  if (V.trig2) return coef_from_trig2<T>(L.U, V.trig2[2 * e], V.trig2[2 * e + 1]);
+  return coef_from_trig<T>(L.U, V.trig[4 * e], V.trig[4 * e + 1], V.trig[4 * e + 2], V.trig[4 * e + 3]);
+}
+
+// Diagonal Kuu, Kvv of node (i, j): sum of the element corner blocks.
+template <typename T>
+__device__ V2<T> node_diag(const ViewList<T>& L, const View<T>& V, int64_t eb, int i, int j) {
+  const int nx = V.g.nx, ny = V.g.ny;
+  const T rx = (T)V.g.rx, ry = (T)V.g.ry, w = (T)V.g.w;
+  // (element column, element row, xi*eta of this node in that element)
+  const int ei[4] = {i - 1, i, i - 1, i};
+  const int ej[4] = {j - 1, j - 1, j, j};
+  const T sg[4] = {(T)1, (T)-1, (T)-1, (T)1};
+  V2<T> d = zero2<T>();
+  for (int k = 0; k < 4; ++k) {
+    if (ei[k] < 0 || ei[k] >= nx || ej[k] < 0 || ej[k] >= ny) continue;
+    const V2<T> c = element_diag<T>(element_coef(L, V, eb + (int64_t)ej[k] * nx + ei[k]), rx, ry, w, sg[k]);
+    d.u += c.u;
+    d.v += c.v;
+  }
+  return d;
+}
+
+// Smoother coefficients of every node (see kOmega): the u-DOFs of the pair
+// {(2m, j), (2m+1, j)} form a 2x2 block [[Kuu_a, k], [k, Kuu_b]] (k from the two
+// elements sharing the pair's edge), v-DOFs are single. o0 = (w Kuu_b / det, w / Kvv)
+// for node a (and symmetrically for b), o1 = -w k / det, det = Kuu_a Kuu_b - k^2. A
+// Dirichlet u-DOF leaves the block: its coefficients are zero and its partner's
+// block is 1x1. One thread per node.
 template <typename T>
 __global__ void k_invdiag(const __grid_constant__ ViewList<T> L) {
   int vi;
@@ -697,28 +794,28 @@ __global__ void k_invdiag(const __grid_constant__ ViewList<T> L) {
   const int j = node / (nx + 1), i = node - j * (nx + 1);
   const T rx = (T)V.g.rx, ry = (T)V.g.ry, w = (T)V.g.w;
   const int64_t eb = (int64_t)s * nx * ny;
-  T du = 0, dv = 0;
-  // (element column, element row, xi*eta of this node in that element)
-  const int ei[4] = {i - 1, i, i - 1, i};
-  const int ej[4] = {j - 1, j - 1, j, j};
-  const T sg[4] = {(T)1, (T)-1, (T)-1, (T)1};
-  for (int k = 0; k < 4; ++k) {
-    if (ei[k] < 0 || ei[k] >= nx || ej[k] < 0 || ej[k] >= ny) continue;
-    Coef<T> C;
-    const int64_t e = eb + (int64_t)ej[k] * nx + ei[k];
-    if (V.trig2) {
-      C = coef_from_trig2<T>(L.U, V.trig2[2 * e], V.trig2[2 * e + 1]);
-    } else {
-      C = coef_from_trig<T>(L.U, V.trig[4 * e], V.trig[4 * e + 1], V.trig[4 * e + 2], V.trig[4 * e + 3]);
-    }
-    const V2<T> d = element_diag<T>(C, rx, ry, w, sg[k]);
-    du += d.u;
-    dv += d.v;
+  const V2<T> d = node_diag(L, V, eb, i, j);
+  const T om = (T)kOmega;
+  T au = om / d.u, c = 0;
+  const int p = i ^ 1;
+  if (p <= nx && !dir_u(p, nx)) {
+    const V2<T> dp = node_diag(L, V, eb, p, j);
+    const int ec = min(i, p);   // element column of the shared edge
+    T k = 0;
+    if (j >= 1) k += element_edge_uu<T>(element_coef(L, V, eb + (int64_t)(j - 1) * nx + ec), rx, ry, w);
+    if (j < ny) k += element_edge_uu<T>(element_coef(L, V, eb + (int64_t)j * nx + ec), rx, ry, w);
+    const T det = d.u * dp.u - k * k;
+    au = om * dp.u / det;
+    c = -om * k / det;
   }
-  V2<T> r = v2<T>((T)kOmega / du, (T)kOmega / dv);
-  if (dir_u(i, nx)) r.u = 0;
+  V2<T> r = v2<T>(au, om / d.v);
+  if (dir_u(i, nx)) {
+    r.u = 0;
+    c = 0;
+  }
   if (dir_v(i)) r.v = 0;
   st2(V.o0 + (int64_t)s * 2 * per + 2 * node, r);
+  V.o1[(int64_t)s * per + node] = c;
 }
 
 // Dense inverse of the coarsest operator per sample (Dirichlet rows/columns set to
@@ -977,6 +1074,38 @@ __global__ void k_react_delta(const __grid_constant__ ViewList<T> L, SampleState
   atomicAdd(&S.react[t], (double)o2.u + (double)o3.u);
 }
 
+// Energy-consistent reaction. With the load entering only through the prescribed end
+// shortening, d^T K d = -d_F . (K d)_F + shortening * R, R = -sum of (K d)_u over x = lx,
+// so at the exact discrete solution R = d^T K d / shortening; for an approximate d
+// that form differs from the nodal sum by -(d_F . r_F) / shortening (r_F = -(K d)_F,
+// the final refinement residual) and its error is quadratic in the solve error
+// (||e||_K^2 / shortening) instead of linear. qoi[2 s] += -(d . r) / shortening for
+// every converged sample: a = r (inner precision, zero on Dirichlet DOFs), ext0 = d.
+// One warp per node row.
+template <typename T>
+__global__ void k_react_energy(const __grid_constant__ ViewList<T> L, SampleState S, double inv_shortening) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  int vi;
+  int64_t loc;
+  if (!find_point(L, gw, vi, loc)) return;
+  const View<T>& V = L.v[vi];
+  const int rows = V.g.ny + 1;
+  const int s = (int)(loc / rows);
+  if (s >= V.nsamp) return;
+  const int t = V.sbase + s;
+  if (S.status[t] != 0) return;
+  const int j = (int)(loc - (int64_t)s * rows);
+  const int nv = 2 * (V.g.nx + 1);
+  const int64_t off = ((int64_t)s * rows + j) * nv;
+  const double* d = static_cast<const double*>(V.ext0) + off;
+  const T* r = V.a + off;
+  double acc = 0.0;
+  for (int k = lane; k < nv; k += 32) acc += d[k] * (double)r[k];
+  acc = warp_sum(acc);
+  if (lane == 0) atomicAdd(&S.qoi[2 * t], -acc * inv_shortening);
+}
+
 __global__ void k_inner_end(SampleState S, int total, int recursive) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total || !S.outer_active[t]) return;
@@ -1077,6 +1206,16 @@ inline int blocks_for(int64_t threads, int bs) { return (int)((threads + bs - 1)
 
 }  // namespace
 
+int strip_cols(StripOp op) {
+  switch (op) {
+    case StripOp::PreTop:
+    case StripOp::PreR:
+    case StripOp::Post:
+    case StripOp::PostTop: return kSmoothCols;
+    default: return kStripCols;
+  }
+}
+
 template <typename T>
 cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st) {
   switch (op) {
@@ -1153,6 +1292,14 @@ cudaError_t launch_take_residual(const ViewList<T>& L, SampleState S, int total_
 }
 
 template <typename T>
+cudaError_t launch_react_energy(const ViewList<T>& L, SampleState S, double shortening, int total_warps,
+                                cudaStream_t st) {
+  if (total_warps <= 0) return cudaSuccess;
+  k_react_energy<T><<<blocks_for((int64_t)total_warps * 32, 128), 128, 0, st>>>(L, S, 1.0 / shortening);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_react_delta(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st) {
   if (total_threads <= 0) return cudaSuccess;
   k_react_delta<T><<<blocks_for(total_threads, 128), 128, 0, st>>>(L, S);
@@ -1194,6 +1341,7 @@ cudaError_t launch_outer_check(SampleState S, int total, double rtol, double flo
   template cudaError_t launch_update_d<T>(const ViewList<T>&, SampleState, int, cudaStream_t);             \
   template cudaError_t launch_take_residual<T>(const ViewList<T>&, SampleState, int, cudaStream_t);        \
   template cudaError_t launch_react_delta<T>(const ViewList<T>&, SampleState, int, cudaStream_t);          \
+  template cudaError_t launch_react_energy<T>(const ViewList<T>&, SampleState, double, int, cudaStream_t);  \
   template cudaError_t launch_resid64<T>(const ViewList<double>&, SampleState, int, cudaStream_t);         \
   template cudaError_t launch_stress<T>(const ViewList<double>&, SampleState, double, double, double, int, \
                                         cudaStream_t);

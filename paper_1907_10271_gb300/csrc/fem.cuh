@@ -24,7 +24,8 @@ struct View {
   const T* a;
   const T* b;
   const T* c;
-  const T* winvd;
+  const T* winvd;   // smoother, per node: (u self coefficient, v coefficient), damping included
+  const T* wc;      // smoother, per node: u coefficient of the pair partner (column i ^ 1)
   const T* xc;      // prolongation source (level below)
   T* o0;
   T* o1;
@@ -72,12 +73,21 @@ struct SampleState {
 // Strip kernels (q = K p family); see fem.cu for the operand conventions.
 enum class StripOp { Apply, PreTop, PreR, Post, PostTop, PcgP, ResidInit };
 
+// Output node columns per warp strip of a strip kernel (sets the views' tiles_x).
+int strip_cols(StripOp op);
+
 template <typename T>
 cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st);
 
 // Refinement residual r = -(K d) on free DOFs (double d, T output), ||r||^2 and reaction.
 template <typename TI>
 cudaError_t launch_resid64(const ViewList<double>& L, SampleState S, int total_warps, cudaStream_t st);
+
+// Energy-consistent reaction correction of converged samples (see fem.cu): a = final
+// refinement residual, ext0 = d (double); one warp per node row.
+template <typename T>
+cudaError_t launch_react_energy(const ViewList<T>& L, SampleState S, double shortening, int total_warps,
+                                cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_trig_average(const ViewList<T>& L, int total_threads, cudaStream_t st);

@@ -44,8 +44,8 @@ struct GroupBuf {
   // top level
   T *x, *r[2], *p[2], *z, *q;
   double* d;
-  // every level k: winvd[k], r1[k]; coarse levels k >= 1: b[k], xl[k], trig[k]
-  std::vector<T*> winvd, r1, b, xl, trig;
+  // every level k: winvd[k], wc[k] (smoother), r1[k]; coarse levels k >= 1: b[k], xl[k], trig[k]
+  std::vector<T*> winvd, wc, r1, b, xl, trig;
   T* ainv;
 };
 
@@ -66,11 +66,13 @@ View<T> base_view(const GroupBuf<T>& g, int k) {
   return v;
 }
 
-// Assigns work offsets for strip kernels (warps) and returns the total.
+// Assigns the strips of operation op and the work offsets of a strip kernel (warps);
+// returns the total.
 template <typename T>
-int finalize_warps(ViewList<T>& L) {
+int finalize_warps(ViewList<T>& L, StripOp op) {
   int acc = 0;
   for (int i = 0; i < L.n; ++i) {
+    L.v[i].tiles_x = strips_of(L.v[i].g.nx, strip_cols(op));
     L.v[i].work_begin = acc;
     L.v[i].nwork = L.v[i].nsamp * L.v[i].tiles_x * L.v[i].tiles_y;
     acc += L.v[i].nwork;
@@ -161,12 +163,14 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       alloc.template vec<T>(g.q, nv(0));
       alloc.template vec<double>(g.d, nv(0));
       g.winvd.assign(g.nl, nullptr);
+      g.wc.assign(g.nl, nullptr);
       g.r1.assign(g.nl, nullptr);
       g.b.assign(g.nl, nullptr);
       g.xl.assign(g.nl, nullptr);
       g.trig.assign(g.nl, nullptr);
       for (int k = 0; k < g.nl; ++k) {
         alloc.template vec<T>(g.winvd[k], nv(k));
+        alloc.template vec<T>(g.wc[k], nv(k) / 2);
         alloc.template vec<T>(g.r1[k], nv(k));
         if (k >= 1) {
           alloc.template vec<T>(g.b[k], nv(k));
@@ -243,6 +247,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       if (k >= g.nl) continue;
       View<T> v = base_view(g, k);
       v.o0 = g.winvd[k];
+      v.o1 = g.wc[k];
       L.v[L.n++] = v;
       per.push_back((int64_t)(g.geo[k].nx + 1) * (g.geo[k].ny + 1));
     }
@@ -276,6 +281,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
           v.b = g.q;
           v.c = g.p[parity];
           v.winvd = g.winvd[0];
+          v.wc = g.wc[0];
           v.o0 = g.x;
           v.o1 = g.r[parity ^ 1];
           v.o2 = g.r1[0];
@@ -284,6 +290,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
           v.a = g.r[parity ^ 1];
           v.xc = g.xl[1];
           v.winvd = g.winvd[0];
+          v.wc = g.wc[0];
           v.o0 = g.z;
           break;
         case StripOp::PcgP:
@@ -317,6 +324,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
           v.b = g.q;
           v.c = g.p[parity];
           v.winvd = g.winvd[0];
+          v.wc = g.wc[0];
           v.o0 = g.x;
           v.o1 = g.r[parity ^ 1];
           v.o2 = g.r1[0];
@@ -324,12 +332,14 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
           v.xc = g.r1[d - 1];
           v.o1 = g.b[d];
           v.winvd = g.winvd[d];
+        v.wc = g.wc[d];
+          v.wc = g.wc[d];
           v.o2 = g.r1[d];
         }
         Lsm.v[Lsm.n++] = v;
       }
       if (!Lsm.n) continue;
-      const int tw = finalize_warps(Lsm);
+      const int tw = finalize_warps(Lsm, d == 0 ? StripOp::PreTop : StripOp::PreR);
       if (d == 0) {
         Lsm.prof_op = kProfPreTop;
         MLMC_LAUNCH(kProfPreTop, "pre_top", launch_strip<T>(StripOp::PreTop, Lsm, S, tw, st));
@@ -363,6 +373,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         View<T> v = base_view(g, d);
         v.xc = g.xl[d + 1];
         v.winvd = g.winvd[d];
+        v.wc = g.wc[d];
         if (d == 0) {
           v.a = g.r[parity ^ 1];
           v.o0 = g.z;
@@ -373,7 +384,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         L.v[L.n++] = v;
       }
       if (!L.n) continue;
-      const int tw = finalize_warps(L);
+      const int tw = finalize_warps(L, d == 0 ? StripOp::PostTop : StripOp::Post);
       if (d == 0) {
         L.prof_op = kProfPostTop;
         MLMC_LAUNCH(kProfPostTop, "post_top", launch_strip<T>(StripOp::PostTop, L, S, tw, st));
@@ -385,7 +396,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     MLMC_LAUNCH(kProfOther, "after_post", launch_after_post(S, total, iter, st));
     {
       ViewList<T> L = top_list(StripOp::PcgP, parity);
-      const int tw = finalize_warps(L);
+      const int tw = finalize_warps(L, StripOp::PcgP);
       L.prof_op = kProfPcgP;
       MLMC_LAUNCH(kProfPcgP, "pcg_p", launch_strip<T>(StripOp::PcgP, L, S, tw, st));
     }
@@ -455,7 +466,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       v.param = ctx.cfg.shortening;
       L.v[L.n++] = v;
     }
-    const int tw = finalize_warps(L);
+    const int tw = finalize_warps(L, StripOp::ResidInit);
     L.prof_op = kProfOther;
     MLMC_LAUNCH(kProfOther, "resid_init", launch_strip<T>(StripOp::ResidInit, L, S, tw, st));
   }
@@ -575,6 +586,20 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       return ctx.cuda_fail(e, "status");
     if (changed && (e = cudaStreamSynchronize(st)) != cudaSuccess) return ctx.cuda_fail(e, "status");
   }
+  // reaction in its energy-consistent form (quadratic in the solve error)
+  {
+    ViewList<T> L = empty_list<T>(ctx);
+    std::vector<int64_t> rows;
+    for (auto& g : G) {
+      View<T> v = base_view(g, 0);
+      v.a = g.r[0];
+      v.ext0 = g.d;
+      L.v[L.n++] = v;
+      rows.push_back(g.geo[0].ny + 1);
+    }
+    const int tw = finalize_points(L, rows);
+    MLMC_LAUNCH(kProfOther, "react_energy", launch_react_energy<T>(L, S, ctx.cfg.shortening, tw, st));
+  }
   // stress quantity from the final d
   {
     ViewList<double> L = d_list();
@@ -618,7 +643,7 @@ mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* tri
   v.a = p;
   v.o0 = q;
   L.v[L.n++] = v;
-  const int tw = finalize_warps(L);
+  const int tw = finalize_warps(L, StripOp::Apply);
   SampleState S;
   std::memset(&S, 0, sizeof(S));
   cudaError_t e = launch_strip<T>(StripOp::Apply, L, S, tw, ctx.stream);
