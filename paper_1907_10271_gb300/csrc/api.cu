@@ -129,6 +129,7 @@ struct LevelReq {
 struct ReqBuffers {
   double* xi;
   float* xi32;
+  float* xi_tc;   // TF32 split of xi: hi [n][kp] then lo [n][kp] (tensor-core synthesis)
   void* theta_f;
   void* theta_c;
   double* qf;
@@ -167,7 +168,8 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
       const LevelReq& r = reqs[k];
       const int64_t nel_f = c.mesh(r.level).n_el(), nel_c = r.level > 0 ? c.mesh(r.level - 1).n_el() : 1;
       alloc(B[k].xi, r.n * nkl);
-      alloc(B[k].xi32, r.n * nkl);
+      alloc(B[k].xi32, c.kl_on_tensor_cores() ? 1 : r.n * nkl);
+      alloc(B[k].xi_tc, c.kl_on_tensor_cores() ? 2 * r.n * c.kl_kpad() : 1);
       alloc(reinterpret_cast<T*&>(B[k].theta_f), 2 * r.n * nel_f);
       alloc(reinterpret_cast<T*&>(B[k].theta_c), 2 * r.n * nel_c);
       alloc(B[k].qf, 2 * r.n);
@@ -183,7 +185,7 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
   {
     auto count = [&](auto*& p, int64_t n) { sz.add<std::remove_reference_t<decltype(*p)>>((size_t)n); };
     plan(count);
-    sz.add<int>(1);
+    sz.add<int>(2);
   }
   cudaError_t e = c.batch_arena.reserve(sz.used + 512);
   if (e != cudaSuccess) {
@@ -194,35 +196,51 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
   {
     auto carve = [&](auto*& p, int64_t n) { p = c.batch_arena.carve<std::remove_reference_t<decltype(*p)>>((size_t)n); };
     plan(carve);
-    fail = c.batch_arena.carve<int>(1);
+    fail = c.batch_arena.carve<int>(2);   // [0] normal generator cap, [1] tensor-core synthesis wait
   }
-  if ((e = cudaMemsetAsync(fail, 0, sizeof(int), st)) != cudaSuccess) return c.cuda_fail(e, "memset");
+  if ((e = cudaMemsetAsync(fail, 0, 2 * sizeof(int), st)) != cudaSuccess) return c.cuda_fail(e, "memset");
   std::vector<mlmc::SolveGroup<T>> groups;
   for (size_t k = 0; k < reqs.size(); ++k) {
     const LevelReq& r = reqs[k];
     c.timer.begin(mlmc::kProfOther, st, "kl_coefficients");
+    const bool tc = c.kl_on_tensor_cores();
     e = mlmc::launch_kl_coefficients(c.cfg.seed, r.level, r.first_id, nullptr, nullptr, r.n, nkl, B[k].xi,
-                                     c.mixed() ? B[k].xi32 : nullptr, fail, st);
+                                     c.mixed() && !tc ? B[k].xi32 : nullptr, fail, st);
     c.timer.end(st);
     if (e != cudaSuccess) return c.cuda_fail(e, "kl_coefficients");
+    mlmc::KlTcOperand xop;
+    if (tc) {
+      const int kp = c.kl_kpad();
+      c.timer.begin(mlmc::kProfOther, st, "kl_split");
+      e = mlmc::launch_tf32_split(B[k].xi, r.n, nkl, kp, B[k].xi_tc, B[k].xi_tc + r.n * kp, st);
+      c.timer.end(st);
+      if (e == cudaSuccess)
+        e = mlmc::make_kl_tc_operand(B[k].xi_tc, B[k].xi_tc + r.n * kp, r.n, kp, mlmc::kKlTcSamples, &xop);
+      if (e != cudaSuccess) return c.cuda_fail(e, "kl_split");
+    }
     const T* xiT = c.mixed() ? (const T*)(const void*)B[k].xi32 : (const T*)(const void*)B[k].xi;
     for (int side = 0; side < (r.level > 0 ? 2 : 1); ++side) {
       const int m = r.level - side;
       const T* basis = c.mixed() ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
       T* th = (T*)(side == 0 ? B[k].theta_f : B[k].theta_c);
       c.timer.begin(mlmc::kProfOther, st, "kl_synthesis");
-      e = mlmc::launch_kl_synthesis<T>(xiT, basis, r.n, (int)c.mesh(m).n_el(), nkl, th, true, st);
+      if (tc)
+        e = mlmc::launch_kl_synthesis_tc(c.basis_tc_op[m], xop, (int)c.mesh(m).n_el(), r.n, (float*)(void*)th, true,
+                                         fail + 1, st);
+      else
+        e = mlmc::launch_kl_synthesis<T>(xiT, basis, r.n, (int)c.mesh(m).n_el(), nkl, th, true, st);
       c.timer.end(st);
       if (e != cudaSuccess) return c.cuda_fail(e, "kl_synthesis");
       if (side == 0) groups.push_back({m, r.n, th, B[k].qf, B[k].st_f, B[k].it_f});
       else groups.push_back({m, r.n, th, B[k].qc, B[k].st_c, B[k].it_c});
     }
   }
-  int h_fail = 0;
-  if ((e = cudaMemcpyAsync(&h_fail, fail, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+  int h_fail[2] = {0, 0};
+  if ((e = cudaMemcpyAsync(h_fail, fail, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return c.cuda_fail(e, "kl_coefficients");
-  if (h_fail) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
+  if (h_fail[0]) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
+  if (h_fail[1]) return c.fail(MLMC_ERR_TIMEOUT, "tensor-core KL synthesis: a wait expired");
   mlmc_status s = mlmc::solve_groups<T>(c, groups);
   if (s != MLMC_OK) return s;
   for (size_t k = 0; k < reqs.size(); ++k) {
@@ -384,6 +402,27 @@ mlmc_status mlmc_create(const mlmc_config* cfg, void* cuda_stream, mlmc_ctx** ou
     cudaMemcpy(d32, B32.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice);
     c.basis64.push_back(d64);
     c.basis32.push_back(d32);
+    if (c.kl_on_tensor_cores()) {
+      const int kp = c.kl_kpad();
+      const int64_t rows = (int64_t)c.bases_host[l].nx * c.bases_host[l].ny;
+      std::vector<float> split(2 * (size_t)rows * kp);
+      mlmc::tf32_split_host(B.data(), rows, c.cfg.kl_terms, kp, split.data(), split.data() + rows * kp);
+      float* dtc = nullptr;
+      mlmc::KlTcOperand op;
+      cudaError_t e = cudaMalloc(&dtc, sizeof(float) * split.size());
+      if (e == cudaSuccess) {
+        c.basis_tc.push_back(dtc);
+        e = cudaMemcpy(dtc, split.data(), sizeof(float) * split.size(), cudaMemcpyHostToDevice);
+      }
+      if (e == cudaSuccess) e = mlmc::make_kl_tc_operand(dtc, dtc + rows * kp, rows, kp, mlmc::kKlTcElements, &op);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = std::string("tensor-core KL basis: ") + cudaGetErrorString(e);
+        mlmc_destroy(h);
+        return e == cudaErrorMemoryAllocation ? MLMC_ERR_OOM : MLMC_ERR_CUDA;
+      }
+      c.basis_tc_op.push_back(op);
+    }
   }
   h->acc_host.assign(c.cfg.levels, mlmc::LevelAcc{});
   std::memset(h->acc_host.data(), 0, sizeof(mlmc::LevelAcc) * c.cfg.levels);
@@ -410,6 +449,7 @@ void mlmc_destroy(mlmc_ctx* h) {
   cudaStreamSynchronize(h->c.stream);
   for (auto p : h->c.basis64) cudaFree(p);
   for (auto p : h->c.basis32) cudaFree(p);
+  for (auto p : h->c.basis_tc) cudaFree(p);
   h->c.solve_arena.release();
   h->c.batch_arena.release();
   h->c.timer.release();
@@ -467,7 +507,7 @@ mlmc_status mlmc_profile_enable(mlmc_ctx* h, int32_t on) {
   return MLMC_OK;
 }
 
-static_assert(mlmc::kProfOps == MLMC_OP_COUNT, "kernel timer operations and MLMC_OP_* ids differ");
+static_assert((int)mlmc::kProfOps == (int)MLMC_OP_COUNT, "kernel timer operations and MLMC_OP_* ids differ");
 
 mlmc_status mlmc_profile_get(mlmc_ctx* h, int32_t op, double* ms_total, int64_t* launches, uint64_t* nodes) {
   if (!h) return MLMC_ERR_INVALID_ARG;
@@ -573,10 +613,13 @@ mlmc_status mlmc_solve_batch(mlmc_ctx* h, const mlmc_item* items, int64_t n, dou
   const size_t tb = mixed ? 4 : 8;
   int64_t nel_total = 0;
   for (int64_t k = 0; k < n; ++k) nel_total += c.mesh(it[order[k]].mesh_level).n_el();
+  const bool tc = c.kl_on_tensor_cores();
+  const int kp = c.kl_kpad();
   mlmc::Sizer sz;
   sz.add<double>(n * c.cfg.kl_terms);
   sz.add<float>(n * c.cfg.kl_terms);
-  sz.add<int>(1);
+  sz.add<float>(tc ? 2 * n * kp : 1);
+  sz.add<int>(2);
   sz.add<int>(n);
   sz.add<uint64_t>(n);
   sz.add<char>(2 * nel_total * tb);
@@ -591,7 +634,8 @@ mlmc_status mlmc_solve_batch(mlmc_ctx* h, const mlmc_item* items, int64_t n, dou
   c.batch_arena.reset();
   double* xi = c.batch_arena.carve<double>(n * c.cfg.kl_terms);
   float* xi32 = c.batch_arena.carve<float>(n * c.cfg.kl_terms);
-  int* fail = c.batch_arena.carve<int>(1);
+  float* xi_tc = c.batch_arena.carve<float>(tc ? 2 * n * kp : 1);
+  int* fail = c.batch_arena.carve<int>(2);
   int* lv_dev = c.batch_arena.carve<int>(n);
   uint64_t* id_dev = c.batch_arena.carve<uint64_t>(n);
   char* theta = c.batch_arena.carve<char>(2 * nel_total * tb);
@@ -601,11 +645,13 @@ mlmc_status mlmc_solve_batch(mlmc_ctx* h, const mlmc_item* items, int64_t n, dou
   cudaStream_t st = c.stream;
   if ((e = cudaMemcpyAsync(lv_dev, lv.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(id_dev, ids.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(fail, 0, sizeof(int), st)) != cudaSuccess)
+      (e = cudaMemsetAsync(fail, 0, 2 * sizeof(int), st)) != cudaSuccess)
     return c.cuda_fail(e, "items");
   if ((e = mlmc::launch_kl_coefficients(c.cfg.seed, 0, 0, lv_dev, id_dev, n, c.cfg.kl_terms, xi,
-                                        mixed ? xi32 : nullptr, fail, st)) != cudaSuccess)
+                                        mixed && !tc ? xi32 : nullptr, fail, st)) != cudaSuccess)
     return c.cuda_fail(e, "kl_coefficients");
+  if (tc && (e = mlmc::launch_tf32_split(xi, n, c.cfg.kl_terms, kp, xi_tc, xi_tc + n * kp, st)) != cudaSuccess)
+    return c.cuda_fail(e, "kl_split");
   auto run = [&](auto tag) -> mlmc_status {
     using T = decltype(tag);
     std::vector<mlmc::SolveGroup<T>> groups;
@@ -619,13 +665,27 @@ mlmc_status mlmc_solve_batch(mlmc_ctx* h, const mlmc_item* items, int64_t n, dou
       const int64_t nel = c.mesh(m).n_el();
       T* th = reinterpret_cast<T*>(theta) + eoff;
       const T* B = mixed ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
-      cudaError_t err =
-          mlmc::launch_kl_synthesis<T>(xiT + k * c.cfg.kl_terms, B, nb, (int)nel, c.cfg.kl_terms, th, true, st);
+      cudaError_t err;
+      if (tc) {
+        mlmc::KlTcOperand xop;
+        err = mlmc::make_kl_tc_operand(xi_tc + k * kp, xi_tc + (n + k) * kp, nb, kp, mlmc::kKlTcSamples, &xop);
+        if (err == cudaSuccess)
+          err = mlmc::launch_kl_synthesis_tc(c.basis_tc_op[m], xop, (int)nel, nb, (float*)(void*)th, true, fail + 1,
+                                             st);
+      } else {
+        err = mlmc::launch_kl_synthesis<T>(xiT + k * c.cfg.kl_terms, B, nb, (int)nel, c.cfg.kl_terms, th, true, st);
+      }
       if (err != cudaSuccess) return c.cuda_fail(err, "kl_synthesis");
       groups.push_back({m, nb, th, qd + 2 * k, sd + k, itd + k});
       eoff += 2 * nb * nel;
       k = k1;
     }
+    int h_err = 0;
+    cudaError_t err;
+    if ((err = cudaMemcpyAsync(&h_err, fail + 1, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (err = cudaStreamSynchronize(st)) != cudaSuccess)
+      return c.cuda_fail(err, "kl_synthesis");
+    if (h_err) return c.fail(MLMC_ERR_TIMEOUT, "tensor-core KL synthesis: a wait expired");
     return mlmc::solve_groups<T>(c, groups);
   };
   mlmc_status s = mixed ? run(float()) : run(double());
@@ -754,9 +814,12 @@ mlmc_status mlmc_theta(mlmc_ctx* h, int32_t level, int32_t mesh_level, uint64_t 
   const int nkl = c.cfg.kl_terms;
   const int64_t nel = c.mesh(mesh_level).n_el();
   mlmc::Sizer sz;
+  const bool tc = c.kl_on_tensor_cores();
+  const int kp = c.kl_kpad();
   sz.add<double>(n * nkl);
   sz.add<float>(n * nkl);
-  sz.add<int>(1);
+  sz.add<float>(tc ? 2 * n * kp : 1);
+  sz.add<int>(2);
   sz.add<double>(n * nel);
   sz.add<float>(n * nel);
   cudaError_t e = c.batch_arena.reserve(sz.used + 256);
@@ -764,15 +827,29 @@ mlmc_status mlmc_theta(mlmc_ctx* h, int32_t level, int32_t mesh_level, uint64_t 
   c.batch_arena.reset();
   double* xi = c.batch_arena.carve<double>(n * nkl);
   float* xi32 = c.batch_arena.carve<float>(n * nkl);
-  int* fail = c.batch_arena.carve<int>(1);
+  float* xi_tc = c.batch_arena.carve<float>(tc ? 2 * n * kp : 1);
+  int* fail = c.batch_arena.carve<int>(2);
   double* th = c.batch_arena.carve<double>(n * nel);
   float* th32 = c.batch_arena.carve<float>(n * nel);
   cudaStream_t st = c.stream;
-  if ((e = cudaMemsetAsync(fail, 0, sizeof(int), st)) != cudaSuccess ||
+  if ((e = cudaMemsetAsync(fail, 0, 2 * sizeof(int), st)) != cudaSuccess ||
       (e = mlmc::launch_kl_coefficients(c.cfg.seed, level, first_id, nullptr, nullptr, n, nkl, xi, xi32, fail, st)) !=
           cudaSuccess)
     return c.cuda_fail(e, "kl_coefficients");
-  if (c.mixed()) {
+  if (tc) {
+    mlmc::KlTcOperand xop;
+    if ((e = mlmc::launch_tf32_split(xi, n, nkl, kp, xi_tc, xi_tc + n * kp, st)) != cudaSuccess ||
+        (e = mlmc::make_kl_tc_operand(xi_tc, xi_tc + n * kp, n, kp, mlmc::kKlTcSamples, &xop)) != cudaSuccess ||
+        (e = mlmc::launch_kl_synthesis_tc(c.basis_tc_op[mesh_level], xop, (int)nel, n, th32, false, fail + 1, st)) !=
+            cudaSuccess ||
+        (e = convert(th32, th, n * nel, st)) != cudaSuccess)
+      return c.cuda_fail(e, "kl_synthesis");
+    int h_err = 0;
+    if ((e = cudaMemcpyAsync(&h_err, fail + 1, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return c.cuda_fail(e, "kl_synthesis");
+    if (h_err) return c.fail(MLMC_ERR_TIMEOUT, "tensor-core KL synthesis: a wait expired");
+  } else if (c.mixed()) {
     if ((e = mlmc::launch_kl_synthesis<float>(xi32, c.basis32[mesh_level], n, (int)nel, nkl, th32, false, st)) !=
             cudaSuccess ||
         (e = convert(th32, th, n * nel, st)) != cudaSuccess)

@@ -5,6 +5,7 @@
 
 #include "engine.h"
 #include "fem.cuh"
+#include "kl_tc.h"
 
 namespace mlmc {
 
@@ -115,6 +116,8 @@ struct Context {
   std::vector<KLBasis> bases_host;
   std::vector<double*> basis64;   // device, per mesh level
   std::vector<float*> basis32;
+  std::vector<float*> basis_tc;          // device, per mesh level: TF32 hi [n_el][kp] then lo
+  std::vector<KlTcOperand> basis_tc_op;  // their TMA descriptors
   Arena solve_arena;              // solver workspace
   Arena batch_arena;              // per-call inputs (xi, theta, outputs)
   std::vector<mlmc_level_stats> stats;
@@ -127,6 +130,9 @@ struct Context {
   int last_iters = 0;             // max PCG iterations of the last solve (diagnostic)
 
   bool mixed() const { return cfg.precision == MLMC_PREC_MIXED; }
+  // KL synthesis of the mixed path on the tensor cores (3xTF32); FP32 CUDA cores past 128 terms
+  bool kl_on_tensor_cores() const { return mixed() && kl_tc_supported(cfg.kl_terms); }
+  int kl_kpad() const { return kl_tc_kpad(cfg.kl_terms); }
   LevelLayout mesh(int l) const { return LevelLayout{cfg.nx0 << l, cfg.ny0 << l}; }
   Geo geo(int nx, int ny) const {
     Geo g;

@@ -76,14 +76,18 @@ __device__ __forceinline__ double uniform_pm1(uint32_t a, uint32_t b) {
   return __dsub_rn(__dmul_rn(__dadd_rn(__dmul_rn(2.0, (double)x), 1.0), 0x1p-52), 1.0);
 }
 
-// One thread per sample: xi[s * n_kl + n] (double), and optionally a float copy.
+// One warp per sample: xi[s * n_kl + n] (double), and optionally a float copy.
 // With item arrays (levels, ids non-null) sample s uses (levels[s], ids[s]);
-// otherwise (level, first_id + s).
+// otherwise (level, first_id + s). Draw d is a function of (key, id, d) alone, so
+// the lanes evaluate draws d = 32 r + lane of round r together; an accepted draw's
+// pair goes to position 2 * (accepted draws before it), found by a ballot prefix, which
+// is the order of the one-draw-at-a-time definition (a then b, b dropped at n_kl).
 __global__ void k_kl_coefficients(uint64_t seed, int level, uint64_t first_id, const int* __restrict__ levels,
                                   const uint64_t* __restrict__ ids, int64_t n, int n_kl, int max_draws,
                                   double* __restrict__ xi, float* __restrict__ xi32, int* __restrict__ fail) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= n) return;   // whole warps
   const uint64_t id = ids ? ids[s] : first_id + (uint64_t)s;
   const int lv = levels ? levels[s] : level;
   const uint32_t key0 = (uint32_t)seed;
@@ -91,26 +95,29 @@ __global__ void k_kl_coefficients(uint64_t seed, int level, uint64_t first_id, c
   double* out = xi + s * n_kl;
   float* out32 = xi32 ? xi32 + s * n_kl : nullptr;
   int got = 0;
-  for (int d = 0; d < max_draws && got < n_kl; ++d) {
+  for (int d0 = 0; d0 < max_draws && got < n_kl; d0 += 32) {
+    const int d = d0 + lane;
     uint32_t c[4] = {(uint32_t)id, (uint32_t)(id >> 32), (uint32_t)d, 0u};
     philox(c, key0, key1);
     const double v1 = uniform_pm1(c[0], c[1]);
     const double v2 = uniform_pm1(c[2], c[3]);
     const double sq = __dadd_rn(__dmul_rn(v1, v1), __dmul_rn(v2, v2));
-    if (sq < 1.0) {
+    const bool accept = sq < 1.0 && d < max_draws;
+    const unsigned mask = __ballot_sync(0xffffffffu, accept);
+    const int pos = got + 2 * __popc(mask & ((1u << lane) - 1u));
+    if (accept && pos < n_kl) {
       const double f = __dsqrt_rn(__ddiv_rn(__dmul_rn(-2.0, series_ln(sq)), sq));
       const double a = __dmul_rn(v1, f), b = __dmul_rn(v2, f);
-      out[got] = a;
-      if (out32) out32[got] = (float)a;
-      ++got;
-      if (got < n_kl) {
-        out[got] = b;
-        if (out32) out32[got] = (float)b;
-        ++got;
+      out[pos] = a;
+      if (out32) out32[pos] = (float)a;
+      if (pos + 1 < n_kl) {
+        out[pos + 1] = b;
+        if (out32) out32[pos + 1] = (float)b;
       }
     }
+    got = min(n_kl, got + 2 * __popc(mask));
   }
-  if (got < n_kl) atomicExch(fail, 1);
+  if (got < n_kl && lane == 0) atomicExch(fail, 1);
 }
 
 }  // namespace
@@ -119,8 +126,8 @@ cudaError_t launch_kl_coefficients(uint64_t seed, int level, uint64_t first_id, 
                                    const uint64_t* ids, int64_t n, int n_kl, double* xi, float* xi32, int* fail,
                                    cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const int threads = 128;
-  const int64_t blocks = (n + threads - 1) / threads;
+  const int threads = 256;   // 8 samples per block
+  const int64_t blocks = (n * 32 + threads - 1) / threads;
   // acceptance probability is pi/4 per draw; this cap is never reached in practice
   const int max_draws = 4 * ((n_kl + 1) / 2) + 256;
   k_kl_coefficients<<<(unsigned)blocks, threads, 0, st>>>(seed, level, first_id, levels, ids, n, n_kl,
