@@ -1,5 +1,6 @@
 // Library context (host side).
 #pragma once
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -143,6 +144,16 @@ struct Context {
     g.ry = 0.5 / hy;
     g.w = hx * hy;
     g.square = hx == hy ? 1 : 0;
+    // centroid x = (i + 1/2) (lx / nx), tested in double exactly as the definition reads
+    g.c0 = nx;
+    g.c1 = -1;
+    for (int i = 0; i < nx; ++i) {
+      const double cx = ((double)i + 0.5) * (cfg.lx / nx);
+      if (cx >= cfg.omega_x0 && cx <= cfg.omega_x1) {
+        g.c0 = std::min(g.c0, i);
+        g.c1 = std::max(g.c1, i);
+      }
+    }
     return g;
   }
   mlmc_status fail(mlmc_status s, const std::string& m) {

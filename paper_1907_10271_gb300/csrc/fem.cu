@@ -136,6 +136,45 @@ __device__ __forceinline__ double warp_sum(double x) {
 }
 
 // Locate the view and tile of this warp.
+// The refinement iterate d. The double path stores it as double; the mixed path as
+// float-float (hi, lo interleaved per DOF, 8 bytes like a double) so that forming,
+// updating and differencing it needs no double-precision arithmetic. TI is the inner
+// precision.
+template <typename TI>
+struct DStore;
+template <>
+struct DStore<double> {
+  using Val = double;
+  __device__ static double get(const double* d, int64_t k) { return d[k]; }
+  __device__ static void put(double* d, int64_t k, double v) { d[k] = v; }
+  __device__ static void add(double* d, int64_t k, double x) { d[k] += x; }
+  // (d_a - d_b) accurate to the double rounding of the difference
+  __device__ static double diff(const double* d, int64_t a, int64_t b) { return d[a] - d[b]; }
+  __device__ static double as_double(const double* d, int64_t k) { return d[k]; }
+};
+template <>
+struct DStore<float> {
+  using Val = DF;
+  __device__ static DF get(const double* d, int64_t k) {
+    const float2 t = reinterpret_cast<const float2*>(d)[k];
+    return DF{t.x, t.y};
+  }
+  __device__ static void put(double* d, int64_t k, DF v) { reinterpret_cast<float2*>(d)[k] = make_float2(v.hi, v.lo); }
+  __device__ static void add(double* d, int64_t k, float x) {
+    const DF a = get(d, k);
+    DF s = two_sum(a.hi, x);
+    s.lo = __fadd_rn(s.lo, a.lo);
+    put(d, k, fast_two_sum(s.hi, s.lo));
+  }
+  // neighbouring values: each part's float difference is exact or rounded relative to
+  // that difference, so the sum carries single-precision relative error of d_a - d_b
+  __device__ static float diff(const double* d, int64_t a, int64_t b) {
+    const float2 x = reinterpret_cast<const float2*>(d)[a], y = reinterpret_cast<const float2*>(d)[b];
+    return __fsub_rn(x.x, y.x) + __fsub_rn(x.y, y.y);
+  }
+  __device__ static double as_double(const double* d, int64_t k) { return df_to_double(get(d, k)); }
+};
+
 template <typename T>
 __device__ __forceinline__ bool find_tile(const ViewList<T>& L, int gw, int& vi, int& s, int& strip, int& chunk) {
   vi = 0;
@@ -577,40 +616,6 @@ struct OpPcgP : OpBase<T> {
   }
 };
 
-// Residual of the lifting d0 (u = -shortening on x = lx, zero elsewhere, generated
-// in registers) in the inner precision: o0 = r = -(K d0) on free DOFs; ||r||^2 into
-// rr64 and the reaction sum of (K d0)_u on x = lx into react. The refinement's first
-// double-precision residual supersedes it, so inner precision suffices here.
-template <typename T>
-struct OpResidInit : OpBase<T> {
-  struct Raw {};
-  bool act;
-  T shortening;
-  double rr = 0.0, react = 0.0;
-  __device__ OpResidInit(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
-    act = S.outer_active[v.sbase + s] != 0;
-    shortening = (T)v.param;
-  }
-  __device__ bool live() const { return act; }
-  __device__ Raw load(int, int) const { return Raw{}; }
-  __device__ V2<T> in(const Raw&, int i, int) { return v2<T>(i == this->V.g.nx ? -shortening : (T)0, (T)0); }
-  __device__ void out(int i, int j, V2<T> kd, bool is_out) {
-    if (!is_out) return;
-    const V2<T> r = this->mask(i, v2<T>(-kd.u, -kd.v));
-    st2(this->V.o0 + this->at(i, j), r);
-    rr += (double)r.u * r.u + (double)r.v * r.v;
-    if (i == this->V.g.nx) react += (double)kd.u;
-  }
-  __device__ void shift() {}
-  __device__ void finish(const SampleState& S, int s) {
-    const double t = warp_sum(rr), u = warp_sum(react);
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&S.rr64[this->V.sbase + s], t);
-      atomicAdd(&S.react[this->V.sbase + s], u);
-    }
-  }
-};
-
 // Refinement residual r = -(K d) on free DOFs from the double-precision d:
 // a = d; ext0 = trig2 (TI); ext1 = r output (TI); ||r||^2 into rr64 and the reaction
 // sum of (K d)_u on x = lx into react. The rotated stiffness is formed in TI from the
@@ -652,8 +657,13 @@ struct OpResid : OpBase<double> {
     else return x;
   }
   __device__ Raw load(int i, int j) const {
-    const V2<double> d = ld2(V.a + at(i, j));
-    return v2<Val>(to_val(d.u), to_val(d.v));
+    if constexpr (sizeof(TI) == 4) {   // float-float iterate: one 16-byte load per node
+      const float4 t = *reinterpret_cast<const float4*>(V.a + at(i, j));
+      return v2<Val>(DF{t.x, t.y}, DF{t.z, t.w});
+    } else {
+      const V2<double> d = ld2(V.a + at(i, j));
+      return v2<Val>(to_val(d.u), to_val(d.v));
+    }
   }
   __device__ V2<Val> in(const Raw& d, int, int) { return d; }
   __device__ V2<Val> pair(V2<Val> x, bool) { return x; }
@@ -755,67 +765,74 @@ __device__ __forceinline__ Coef<T> element_coef(const ViewList<T>& L, const View
   return coef_from_trig<T>(L.U, V.trig[4 * e], V.trig[4 * e + 1], V.trig[4 * e + 2], V.trig[4 * e + 3]);
 }
 
-// Diagonal Kuu, Kvv of node (i, j): sum of the element corner blocks.
-template <typename T>
-__device__ V2<T> node_diag(const ViewList<T>& L, const View<T>& V, int64_t eb, int i, int j) {
-  const int nx = V.g.nx, ny = V.g.ny;
-  const T rx = (T)V.g.rx, ry = (T)V.g.ry, w = (T)V.g.w;
-  // (element column, element row, xi*eta of this node in that element)
-  const int ei[4] = {i - 1, i, i - 1, i};
-  const int ej[4] = {j - 1, j - 1, j, j};
-  const T sg[4] = {(T)1, (T)-1, (T)-1, (T)1};
-  V2<T> d = zero2<T>();
-  for (int k = 0; k < 4; ++k) {
-    if (ei[k] < 0 || ei[k] >= nx || ej[k] < 0 || ej[k] >= ny) continue;
-    const V2<T> c = element_diag<T>(element_coef(L, V, eb + (int64_t)ej[k] * nx + ei[k]), rx, ry, w, sg[k]);
-    d.u += c.u;
-    d.v += c.v;
-  }
-  return d;
-}
-
 // Smoother coefficients of every node (see kOmega): the u-DOFs of the pair
 // {(2m, j), (2m+1, j)} form a 2x2 block [[Kuu_a, k], [k, Kuu_b]] (k from the two
 // elements sharing the pair's edge), v-DOFs are single. o0 = (w Kuu_b / det, w / Kvv)
 // for node a (and symmetrically for b), o1 = -w k / det, det = Kuu_a Kuu_b - k^2. A
 // Dirichlet u-DOF leaves the block: its coefficients are zero and its partner's
-// block is 1x1. One thread per node.
+// block is 1x1. One thread per node pair (the last column pairs with nothing); the
+// six elements around the pair are evaluated once.
 template <typename T>
 __global__ void k_invdiag(const __grid_constant__ ViewList<T> L) {
   int vi;
   int64_t loc;
   if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
   const View<T>& V = L.v[vi];
-  const int nx = V.g.nx, ny = V.g.ny;
-  const int per = (nx + 1) * (ny + 1);
+  const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
+  const int pairs = nx / 2 + 1;   // nx is even on every multigrid level
+  const int per = pairs * (ny + 1);
   const int s = (int)(loc / per);
   if (s >= V.nsamp) return;
-  const int node = (int)(loc - (int64_t)s * per);
-  const int j = node / (nx + 1), i = node - j * (nx + 1);
+  const int r = (int)(loc - (int64_t)s * per);
+  const int j = r / pairs, m = r - j * pairs;
+  const int ia = 2 * m, ib = ia + 1;
   const T rx = (T)V.g.rx, ry = (T)V.g.ry, w = (T)V.g.w;
   const int64_t eb = (int64_t)s * nx * ny;
-  const V2<T> d = node_diag(L, V, eb, i, j);
+  // element corner blocks around the pair: columns ia-1, ia, ia+1; rows j-1, j
+  V2<T> da = zero2<T>(), db = zero2<T>();
+  T k = 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int ei = ia - 1 + c;
+    if (ei < 0 || ei >= nx) continue;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int ej = j - 1 + q;
+      if (ej < 0 || ej >= ny) continue;
+      const Coef<T> C = element_coef(L, V, eb + (int64_t)ej * nx + ei);
+      const T eta = q == 0 ? (T)1 : (T)-1;   // the pair's row is the top (q = 0) or bottom edge
+      if (c <= 1) {   // node a is the element's right (c = 0) or left (c = 1) corner
+        const V2<T> d = element_diag<T>(C, rx, ry, w, (c == 0 ? (T)1 : (T)-1) * eta);
+        da.u += d.u;
+        da.v += d.v;
+      }
+      if (c >= 1) {   // node b is the element's right (c = 1) or left (c = 2) corner
+        const V2<T> d = element_diag<T>(C, rx, ry, w, (c == 1 ? (T)1 : (T)-1) * eta);
+        db.u += d.u;
+        db.v += d.v;
+      }
+      if (c == 1) k += element_edge_uu<T>(C, rx, ry, w);
+    }
+  }
   const T om = (T)kOmega;
-  T au = om / d.u, c = 0;
-  const int p = i ^ 1;
-  if (p <= nx && !dir_u(p, nx)) {
-    const V2<T> dp = node_diag(L, V, eb, p, j);
-    const int ec = min(i, p);   // element column of the shared edge
-    T k = 0;
-    if (j >= 1) k += element_edge_uu<T>(element_coef(L, V, eb + (int64_t)(j - 1) * nx + ec), rx, ry, w);
-    if (j < ny) k += element_edge_uu<T>(element_coef(L, V, eb + (int64_t)j * nx + ec), rx, ry, w);
-    const T det = d.u * dp.u - k * k;
-    au = om * dp.u / det;
-    c = -om * k / det;
+  const bool has_b = ib <= nx;
+  const bool pair = has_b && !dir_u(ia, nx) && !dir_u(ib, nx);
+  const T det = da.u * db.u - k * k;
+  const int64_t nb = (int64_t)s * nxp * (ny + 1) + (int64_t)j * nxp;
+  {
+    V2<T> o = v2<T>(pair ? om * db.u / det : om / da.u, om / da.v);
+    if (dir_u(ia, nx)) o.u = 0;
+    if (dir_v(ia)) o.v = 0;
+    st2(V.o0 + 2 * (nb + ia), o);
+    V.o1[nb + ia] = pair ? -om * k / det : (T)0;
   }
-  V2<T> r = v2<T>(au, om / d.v);
-  if (dir_u(i, nx)) {
-    r.u = 0;
-    c = 0;
+  if (has_b) {
+    V2<T> o = v2<T>(pair ? om * da.u / det : om / db.u, om / db.v);
+    if (dir_u(ib, nx)) o.u = 0;
+    if (dir_v(ib)) o.v = 0;
+    st2(V.o0 + 2 * (nb + ib), o);
+    V.o1[nb + ib] = pair ? -om * k / det : (T)0;
   }
-  if (dir_v(i)) r.v = 0;
-  st2(V.o0 + (int64_t)s * 2 * per + 2 * node, r);
-  V.o1[(int64_t)s * per + node] = c;
 }
 
 // Dense inverse of the coarsest operator per sample (Dirichlet rows/columns set to
@@ -950,7 +967,9 @@ __global__ void k_coarsest_solve(const __grid_constant__ ViewList<T> L, SampleSt
   }
 }
 
-// d += x on refinement-active samples: o0 = d (double, via ext1), a = x (T).
+// d += x on refinement-active samples: ext1 = d (DStore<T>), a = x (T). With o0 set,
+// also moves the inner solve's final residual into o0 from b where it ended there
+// (rpar), making it the next refinement residual.
 template <typename T>
 __global__ void k_update_d(const __grid_constant__ ViewList<T> L, SampleState S) {
   int vi;
@@ -959,95 +978,112 @@ __global__ void k_update_d(const __grid_constant__ ViewList<T> L, SampleState S)
   const View<T>& V = L.v[vi];
   const int64_t per = 2 * (int64_t)(V.g.nx + 1) * (V.g.ny + 1);
   const int s = (int)(loc / per);
-  if (s >= V.nsamp || !S.outer_active[V.sbase + s]) return;
-  double* d = static_cast<double*>(V.ext1);
-  d[loc] += (double)V.a[loc];
+  const int t = V.sbase + s;
+  if (s >= V.nsamp || !S.outer_active[t]) return;
+  DStore<T>::add(static_cast<double*>(V.ext1), loc, V.a[loc]);
+  if (V.o0 && S.rpar[t]) V.o0[loc] = V.b[loc];
 }
 
-// Lifting of the Dirichlet data: d = 0 except u = -shortening on x = lx. o0 = d.
-__global__ void k_lift(const __grid_constant__ ViewList<double> L, double shortening) {
-  int vi;
-  int64_t loc;
-  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
-  const View<double>& V = L.v[vi];
-  const int nxp = V.g.nx + 1;
-  const int64_t per = 2 * (int64_t)nxp * (V.g.ny + 1);
-  const int s = (int)(loc / per);
-  if (s >= V.nsamp) return;
-  const int k = (int)(loc - (int64_t)s * per);
-  const int node = k >> 1, i = node % nxp;
-  V.o0[loc] = ((k & 1) == 0 && i == V.g.nx) ? -shortening : 0.0;
-}
-
-// Fibre-direction compressive stress at centroids in [x0, x1]: a = d (double),
-// ext0 = trig2 (TI). The displacement differences that form the centroid strain are
-// taken in double (they cancel); strain, stress and the fibre-frame projection follow
-// in single precision (relative error ~1e-7). Warp maximum, then one atomicMax per
-// warp on the ordered bit pattern of the non-negative double in qoi[2 s + 1].
-// One thread per element.
-template <typename TI>
-__global__ void k_stress(const __grid_constant__ ViewList<double> L, SampleState S, double x0, double x1,
-                         double lx) {
-  int vi;
-  int64_t loc;
-  const bool have = find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc);
-  double vmax = 0.0;
-  int t = -1;
-  if (have) {
-    const View<double>& V = L.v[vi];
-    const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
-    const int per = nx * ny;
-    const int s = (int)(loc / per);
-    if (s < V.nsamp) {
-      t = V.sbase + s;
-      const int e = (int)(loc - (int64_t)s * per);
-      const int j = e / nx, i = e - j * nx;
-      const double cx = (i + 0.5) * (lx / nx);
-      if (cx >= x0 && cx <= x1) {
-        const double* d = V.a + (int64_t)s * 2 * nxp * (ny + 1);
-        const int n1 = j * nxp + i, n2 = n1 + 1, n3 = n1 + nxp + 1, n4 = n1 + nxp;
-        using R = TI;   // single precision on the mixed path, double on the double path
-        const R au = (R)((d[2 * n2] - d[2 * n1]) + (d[2 * n3] - d[2 * n4]));
-        const R bu = (R)((d[2 * n4] - d[2 * n1]) + (d[2 * n3] - d[2 * n2]));
-        const R av = (R)((d[2 * n2 + 1] - d[2 * n1 + 1]) + (d[2 * n3 + 1] - d[2 * n4 + 1]));
-        const R bv = (R)((d[2 * n4 + 1] - d[2 * n1 + 1]) + (d[2 * n3 + 1] - d[2 * n2 + 1]));
-        const R rx = (R)V.g.rx, ry = (R)V.g.ry;
-        const R ex = rx * au, ey = ry * bv, exy = ry * bu + rx * av;
-        const TI* t2 = static_cast<const TI*>(V.ext0) + 2 * ((int64_t)s * per + e);
-        const R c2 = t2[0], s2 = t2[1];
-        const Coef<R> C = coef_from_trig2<R>(L.U, c2, s2);
-        const R sx = C.c11 * ex + C.c12 * ey + C.c16 * exy;
-        const R sy = C.c12 * ex + C.c22 * ey + C.c26 * exy;
-        const R sxy = C.c16 * ex + C.c26 * ey + C.c66 * exy;
-        // fibre-frame normal stress: cos^2 t sx + sin^2 t sy + 2 sin t cos t sxy
-        const R s11 = (R)0.5 * ((R)1 + c2) * sx + (R)0.5 * ((R)1 - c2) * sy + s2 * sxy;
-        vmax = -s11 > (R)0 ? (double)(-s11) : 0.0;
-      }
-    }
-  }
-  // samples change along the thread index: group the lanes of each sample and reduce
-  // the group's maximum on the high word of the bit pattern (non-negative doubles
-  // order like their patterns); the lanes holding that high word settle the low word
-  // with the 64-bit atomicMax, so one atomic per group in the common case
-  const unsigned same = __match_any_sync(0xffffffffu, t);
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(vmax);
-  const unsigned hmax = __reduce_max_sync(same, (unsigned)(bits >> 32));
-  if (t >= 0 && bits > 0ull && (unsigned)(bits >> 32) == hmax)
-    atomicMax(reinterpret_cast<unsigned long long*>(&S.qoi[2 * t + 1]), bits);
-}
-
+// Lifting d0 (u = -shortening on x = lx, zero elsewhere) and its residual
+// r = -(K d0) on free DOFs, in the inner precision T (the first refinement residual,
+// after the first correction, supersedes it). K d0 is nonzero only on node columns
+// nx - 1 and nx, the nodes of the elements that touch the prescribed column, so the
+// caller clears d and r and this kernel writes d on column nx and r on columns
+// nx - 1 and nx, ||r||^2 into rr64 and the reaction sum of (K d0)_u over x = lx into
+// react. o0 = r (T), ext1 = d (DStore<T>). One thread per (sample, node row, column).
 template <typename T>
-__global__ void k_take_residual(const __grid_constant__ ViewList<T> L, SampleState S) {
+__global__ void k_lift_resid(const __grid_constant__ ViewList<T> L, SampleState S, float sh_hi, float sh_lo,
+                             double shortening) {
   int vi;
   int64_t loc;
   if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
   const View<T>& V = L.v[vi];
-  const int64_t per = 2 * (int64_t)(V.g.nx + 1) * (V.g.ny + 1);
+  const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
+  const int per = 2 * (ny + 1);
   const int s = (int)(loc / per);
   if (s >= V.nsamp) return;
+  const int k = (int)(loc - (int64_t)s * per);
+  const int j = k >> 1, c = k & 1, i = nx - 1 + c;
   const int t = V.sbase + s;
-  if (!S.outer_active[t] || S.rpar[t] == 0) return;
-  V.o0[loc] = V.a[loc];
+  const T dl = (T)(-shortening);
+  const T rx = (T)V.g.rx, ry = (T)V.g.ry, w = (T)V.g.w;
+  V2<T> kd = zero2<T>();
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {   // element rows j - 1 (node on its top edge) and j (bottom edge)
+    const int ej = j - 1 + q;
+    if (ej < 0 || ej >= ny) continue;
+    const int64_t e = (int64_t)s * nx * ny + (int64_t)ej * nx + (nx - 1);
+    const Coef<T> C = coef_from_trig2<T>(L.U, V.trig2[2 * e], V.trig2[2 * e + 1]);
+    V2<T> o1, o2, o3, o4;
+    element_apply<T>(C, rx, ry, w, zero2<T>(), v2<T>(dl, (T)0), v2<T>(dl, (T)0), zero2<T>(), o1, o2, o3, o4);
+    const V2<T> o = c == 0 ? (q == 0 ? o4 : o1) : (q == 0 ? o3 : o2);
+    kd.u += o.u;
+    kd.v += o.v;
+  }
+  V2<T> r = v2<T>(-kd.u, -kd.v);
+  if (dir_u(i, nx)) r.u = 0;
+  if (dir_v(i)) r.v = 0;
+  const int64_t node = (int64_t)s * nxp * (ny + 1) + (int64_t)j * nxp + i;
+  st2(V.o0 + 2 * node, r);
+  atomicAdd(&S.rr64[t], (double)r.u * r.u + (double)r.v * r.v);
+  if (c == 1) {
+    atomicAdd(&S.react[t], (double)kd.u);
+    double* d = static_cast<double*>(V.ext1);
+    if constexpr (sizeof(T) == 4) DStore<float>::put(d, 2 * node, DF{-sh_hi, -sh_lo});
+    else d[2 * node] = -shortening;
+  }
+}
+
+// Fibre-direction compressive stress at centroids in [x0, x1]: a = d (DStore<TI>),
+// ext0 = trig2 (TI). The displacement differences that form the centroid strain are
+// taken from the stored iterate at its own accuracy (they cancel); strain, stress and
+// the fibre-frame projection follow in TI (relative error ~1e-7 on the mixed path).
+// One warp per element row: lanes stride over the row's central columns (Geo c0..c1,
+// found on the host with the definition's double-precision centroid test), and the
+// row maximum goes to qoi[2 s + 1] with one atomicMax on the ordered bit pattern of
+// the non-negative double.
+template <typename TI>
+__global__ void k_stress(const __grid_constant__ ViewList<double> L, SampleState S) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  int vi;
+  int64_t loc;
+  if (!find_point(L, gw, vi, loc)) return;
+  const View<double>& V = L.v[vi];
+  const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
+  const int s = (int)(loc / ny);
+  if (s >= V.nsamp) return;
+  const int j = (int)(loc - (int64_t)s * ny);
+  const int t = V.sbase + s;
+  const int ia = V.g.c0, ib = V.g.c1;
+  using R = TI;   // single precision on the mixed path, double on the double path
+  using D = DStore<TI>;
+  const double* d = V.a + (int64_t)s * 2 * nxp * (ny + 1);
+  const TI* t2 = static_cast<const TI*>(V.ext0) + 2 * ((int64_t)s * nx * ny + (int64_t)j * nx);
+  const R rx = (R)V.g.rx, ry = (R)V.g.ry;
+  R vmax = (R)0;
+  for (int i = ia + lane; i <= ib; i += 32) {
+    const int n1 = j * nxp + i, n2 = n1 + 1, n3 = n1 + nxp + 1, n4 = n1 + nxp;
+    const R au = D::diff(d, 2 * n2, 2 * n1) + D::diff(d, 2 * n3, 2 * n4);
+    const R bu = D::diff(d, 2 * n4, 2 * n1) + D::diff(d, 2 * n3, 2 * n2);
+    const R av = D::diff(d, 2 * n2 + 1, 2 * n1 + 1) + D::diff(d, 2 * n3 + 1, 2 * n4 + 1);
+    const R bv = D::diff(d, 2 * n4 + 1, 2 * n1 + 1) + D::diff(d, 2 * n3 + 1, 2 * n2 + 1);
+    const R ex = rx * au, ey = ry * bv, exy = ry * bu + rx * av;
+    const R c2 = t2[2 * i], s2 = t2[2 * i + 1];
+    const Coef<R> C = coef_from_trig2<R>(L.U, c2, s2);
+    const R sx = C.c11 * ex + C.c12 * ey + C.c16 * exy;
+    const R sy = C.c12 * ex + C.c22 * ey + C.c26 * exy;
+    const R sxy = C.c16 * ex + C.c26 * ey + C.c66 * exy;
+    // fibre-frame normal stress: cos^2 t sx + sin^2 t sy + 2 sin t cos t sxy
+    const R s11 = (R)0.5 * ((R)1 + c2) * sx + (R)0.5 * ((R)1 - c2) * sy + s2 * sxy;
+    vmax = max(vmax, -s11);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vmax = max(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  const double m = (double)vmax;
+  if (lane == 0 && m > 0.0)
+    atomicMax(reinterpret_cast<unsigned long long*>(&S.qoi[2 * t + 1]),
+              (unsigned long long)__double_as_longlong(m));
 }
 
 template <typename T>
@@ -1098,12 +1134,19 @@ __global__ void k_react_energy(const __grid_constant__ ViewList<T> L, SampleStat
   const int j = (int)(loc - (int64_t)s * rows);
   const int nv = 2 * (V.g.nx + 1);
   const int64_t off = ((int64_t)s * rows + j) * nv;
-  const double* d = static_cast<const double*>(V.ext0) + off;
+  const double* d = static_cast<const double*>(V.ext0);
   const T* r = V.a + off;
-  double acc = 0.0;
-  for (int k = lane; k < nv; k += 32) acc += d[k] * (double)r[k];
-  acc = warp_sum(acc);
-  if (lane == 0) atomicAdd(&S.qoi[2 * t], -acc * inv_shortening);
+  LaneSum<T> acc;   // the correction is needed to a few digits only
+  for (int k = lane; k < nv; k += 32) {
+    if constexpr (sizeof(T) == 4) {
+      const DF x = DStore<float>::get(d, off + k);
+      acc.add(x.hi * r[k] + x.lo * r[k]);
+    } else {
+      acc.add(d[off + k] * r[k]);
+    }
+  }
+  const double sum = warp_sum((double)acc.value());
+  if (lane == 0) atomicAdd(&S.qoi[2 * t], -sum * inv_shortening);
 }
 
 __global__ void k_inner_end(SampleState S, int total, int recursive) {
@@ -1225,7 +1268,6 @@ cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int to
     case StripOp::Post: return launch_strip_op<T, OpPost<T, false>>(L, S, total_warps, st);
     case StripOp::PostTop: return launch_strip_op<T, OpPost<T, true>>(L, S, total_warps, st);
     case StripOp::PcgP: return launch_strip_op<T, OpPcgP<T>>(L, S, total_warps, st);
-    case StripOp::ResidInit: return launch_strip_op<T, OpResidInit<T>>(L, S, total_warps, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -1270,24 +1312,19 @@ cudaError_t launch_update_d(const ViewList<T>& L, SampleState S, int total_threa
   return cudaGetLastError();
 }
 
-cudaError_t launch_lift(const ViewList<double>& L, double shortening, int total_threads, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_lift_resid(const ViewList<T>& L, SampleState S, double shortening, int total_threads,
+                              cudaStream_t st) {
   if (total_threads <= 0) return cudaSuccess;
-  k_lift<<<blocks_for(total_threads, 256), 256, 0, st>>>(L, shortening);
+  const float hi = (float)shortening, lo = (float)(shortening - (double)hi);
+  k_lift_resid<T><<<blocks_for(total_threads, 128), 128, 0, st>>>(L, S, hi, lo, shortening);
   return cudaGetLastError();
 }
 
 template <typename TI>
-cudaError_t launch_stress(const ViewList<double>& L, SampleState S, double x0, double x1, double lx,
-                          int total_threads, cudaStream_t st) {
-  if (total_threads <= 0) return cudaSuccess;
-  k_stress<TI><<<blocks_for(total_threads, 256), 256, 0, st>>>(L, S, x0, x1, lx);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_take_residual(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st) {
-  if (total_threads <= 0) return cudaSuccess;
-  k_take_residual<T><<<blocks_for(total_threads, 256), 256, 0, st>>>(L, S);
+cudaError_t launch_stress(const ViewList<double>& L, SampleState S, int total_warps, cudaStream_t st) {
+  if (total_warps <= 0) return cudaSuccess;
+  k_stress<TI><<<blocks_for((int64_t)total_warps * 32, 256), 256, 0, st>>>(L, S);
   return cudaGetLastError();
 }
 
@@ -1339,11 +1376,11 @@ cudaError_t launch_outer_check(SampleState S, int total, double rtol, double flo
   template cudaError_t launch_coarsest_setup<T>(const ViewList<T>&, int, cudaStream_t);                    \
   template cudaError_t launch_coarsest_solve<T>(const ViewList<T>&, SampleState, int, cudaStream_t);       \
   template cudaError_t launch_update_d<T>(const ViewList<T>&, SampleState, int, cudaStream_t);             \
-  template cudaError_t launch_take_residual<T>(const ViewList<T>&, SampleState, int, cudaStream_t);        \
   template cudaError_t launch_react_delta<T>(const ViewList<T>&, SampleState, int, cudaStream_t);          \
   template cudaError_t launch_react_energy<T>(const ViewList<T>&, SampleState, double, int, cudaStream_t);  \
   template cudaError_t launch_resid64<T>(const ViewList<double>&, SampleState, int, cudaStream_t);         \
-  template cudaError_t launch_stress<T>(const ViewList<double>&, SampleState, double, double, double, int, \
+  template cudaError_t launch_lift_resid<T>(const ViewList<T>&, SampleState, double, int, cudaStream_t);  \
+  template cudaError_t launch_stress<T>(const ViewList<double>&, SampleState, int,                         \
                                         cudaStream_t);
 MLMC_INST(float)
 MLMC_INST(double)

@@ -71,7 +71,7 @@ struct SampleState {
 };
 
 // Strip kernels (q = K p family); see fem.cu for the operand conventions.
-enum class StripOp { Apply, PreTop, PreR, Post, PostTop, PcgP, ResidInit };
+enum class StripOp { Apply, PreTop, PreR, Post, PostTop, PcgP };
 
 // Output node columns per warp strip of a strip kernel (sets the views' tiles_x).
 int strip_cols(StripOp op);
@@ -101,19 +101,19 @@ cudaError_t launch_coarsest_setup(const ViewList<T>& L, int total_blocks, cudaSt
 template <typename T>
 cudaError_t launch_coarsest_solve(const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st);
 
+// d += x (a = x, ext1 = d); with o0 set also r0 = r1 where the inner residual ended
+// in r1 (b = r1, o0 = r0). One thread per value.
 template <typename T>
 cudaError_t launch_update_d(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st);
 
-cudaError_t launch_lift(const ViewList<double>& L, double shortening, int total_threads, cudaStream_t st);
+// Lifting d0 and its inner-precision residual on the last two node columns (d and r
+// cleared by the caller): o0 = r, ext1 = d. One thread per (sample, node row, column).
+template <typename T>
+cudaError_t launch_lift_resid(const ViewList<T>& L, SampleState S, double shortening, int total_threads,
+                              cudaStream_t st);
 
 template <typename TI>
-cudaError_t launch_stress(const ViewList<double>& L, SampleState S, double x0, double x1, double lx,
-                          int total_threads, cudaStream_t st);
-
-// Moves each sample's final inner residual into r0 (from r1 where it ended there):
-// views at the top level, a = r1, o0 = r0. One thread per value.
-template <typename T>
-cudaError_t launch_take_residual(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st);
+cudaError_t launch_stress(const ViewList<double>& L, SampleState S, int total_warps, cudaStream_t st);
 
 // Reaction increment of the correction: react += sum_j (K x)_u at nodes (nx, j), from
 // the last element column only. Views at the top level, a = x. One thread per element row.

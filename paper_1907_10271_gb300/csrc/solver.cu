@@ -249,7 +249,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       v.o0 = g.winvd[k];
       v.o1 = g.wc[k];
       L.v[L.n++] = v;
-      per.push_back((int64_t)(g.geo[k].nx + 1) * (g.geo[k].ny + 1));
+      per.push_back((int64_t)(g.geo[k].nx / 2 + 1) * (g.geo[k].ny + 1));   // node pairs
     }
     if (L.n == 0) break;
     const int tt = finalize_points(L, per);
@@ -438,17 +438,6 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     return MLMC_OK;
   };
 
-  // lifting, initial residual ||f||
-  {
-    ViewList<double> L = d_list();
-    int64_t acc = 0;
-    for (int i = 0; i < L.n; ++i) {
-      L.v[i].work_begin = (int)acc;
-      L.v[i].nwork = (int)(L.v[i].nsamp * 2 * (int64_t)(L.v[i].g.nx + 1) * (L.v[i].g.ny + 1));
-      acc += L.v[i].nwork;
-    }
-    MLMC_LAUNCH(kProfOther, "lift", launch_lift(L, ctx.cfg.shortening, (int)acc, st));
-  }
   {
     std::vector<int> ones(total, 1);
     if ((e = cudaMemcpyAsync(S.outer_active, ones.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st)) !=
@@ -456,19 +445,25 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       return ctx.cuda_fail(e, "init");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return ctx.cuda_fail(e, "init");
   }
-  // residual of the lifting in the inner precision (the first double-precision
-  // residual, after the first correction, supersedes it)
+  // lifting d0 and its residual ||f||, in the inner precision (the first refinement
+  // residual, after the first correction, supersedes it): both vectors are zero except
+  // near x = lx
   {
     ViewList<T> L = empty_list<T>(ctx);
+    std::vector<int64_t> per;
     for (auto& g : G) {
+      const size_t nv = (size_t)g.grp->nsamp * 2 * (g.geo[0].nx + 1) * (g.geo[0].ny + 1);
+      if ((e = cudaMemsetAsync(g.d, 0, sizeof(double) * nv, st)) != cudaSuccess ||
+          (e = cudaMemsetAsync(g.r[0], 0, sizeof(T) * nv, st)) != cudaSuccess)
+        return ctx.cuda_fail(e, "memset");
       View<T> v = base_view(g, 0);
       v.o0 = g.r[0];
-      v.param = ctx.cfg.shortening;
+      v.ext1 = g.d;
       L.v[L.n++] = v;
+      per.push_back(2 * (int64_t)(g.geo[0].ny + 1));
     }
-    const int tw = finalize_warps(L, StripOp::ResidInit);
-    L.prof_op = kProfOther;
-    MLMC_LAUNCH(kProfOther, "resid_init", launch_strip<T>(StripOp::ResidInit, L, S, tw, st));
+    const int tt = finalize_points(L, per);
+    MLMC_LAUNCH(kProfOther, "lift_resid", launch_lift_resid<T>(L, S, ctx.cfg.shortening, tt, st));
   }
   mlmc_status rs = MLMC_OK;
   MLMC_LAUNCH(kProfOther, "outer_init", launch_outer_init(S, total, st));
@@ -522,7 +517,9 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     }
     max_it_seen = std::max(max_it_seen, it);
     MLMC_LAUNCH(kProfOther, "inner_end", launch_inner_end(S, total, outer > 0 ? 1 : 0, st));
-    // d += x, new residual
+    // d += x; after the first correction the inner CG's recursive residual (accurate
+    // to unit roundoff times the correction's size) is the new refinement residual,
+    // moved into r0 where it ended in r1
     {
       ViewList<T> L = empty_list<T>(ctx);
       std::vector<int64_t> per;
@@ -530,6 +527,10 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         View<T> v = base_view(g, 0);
         v.a = g.x;
         v.ext1 = g.d;
+        if (outer > 0) {
+          v.b = g.r[1];
+          v.o0 = g.r[0];
+        }
         L.v[L.n++] = v;
         per.push_back(2 * (int64_t)(g.geo[0].nx + 1) * (g.geo[0].ny + 1));
       }
@@ -543,23 +544,14 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       rs = resid();
       if (rs != MLMC_OK) return rs;
     } else {
-      // later corrections are small: the inner CG's recursive residual (accurate to
-      // unit roundoff times the correction's size) is the new refinement residual
-      ViewList<T> L = empty_list<T>(ctx), R = empty_list<T>(ctx);
-      std::vector<int64_t> per, rows;
+      ViewList<T> R = empty_list<T>(ctx);
+      std::vector<int64_t> rows;
       for (auto& g : G) {
-        View<T> v = base_view(g, 0);
-        v.a = g.r[1];
-        v.o0 = g.r[0];
-        L.v[L.n++] = v;
-        per.push_back(2 * (int64_t)(g.geo[0].nx + 1) * (g.geo[0].ny + 1));
         View<T> w = base_view(g, 0);
         w.a = g.x;
         R.v[R.n++] = w;
         rows.push_back(g.geo[0].ny);
       }
-      const int tt = finalize_points(L, per);
-      MLMC_LAUNCH(kProfOther, "take_residual", launch_take_residual<T>(L, S, tt, st));
       const int tr = finalize_points(R, rows);
       MLMC_LAUNCH(kProfOther, "react_delta", launch_react_delta<T>(R, S, tr, st));
     }
@@ -606,10 +598,10 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     int64_t acc = 0;
     for (int i = 0; i < L.n; ++i) {
       L.v[i].work_begin = (int)acc;
-      L.v[i].nwork = (int)(L.v[i].nsamp * (int64_t)L.v[i].g.nx * L.v[i].g.ny);
+      L.v[i].nwork = (int)(L.v[i].nsamp * (int64_t)L.v[i].g.ny);   // one warp per element row
       acc += L.v[i].nwork;
     }
-    MLMC_LAUNCH(kProfOther, "stress", launch_stress<T>(L, S, ctx.cfg.omega_x0, ctx.cfg.omega_x1, ctx.cfg.lx, (int)acc, st));
+    MLMC_LAUNCH(kProfOther, "stress", launch_stress<T>(L, S, (int)acc, st));
   }
   for (auto& g : G) {
     const SolveGroup<T>& sg = *g.grp;
