@@ -215,7 +215,9 @@ struct RawE {
 // element rows ahead, so each warp keeps P rows of loads in flight. Lane l holds node
 // column strip * kCols - kHalo + l; lanes kHalo .. kHalo + kCols - 1 are the outputs.
 // in()/pair() and out() run on every lane (pair() and out() of the smoothing handlers
-// exchange values with lane l ^ 1); out() stores only where is_out.
+// exchange values with lane l ^ 1); out() stores only where is_out. in() and load() may
+// shuffle too: every lane calls them (lanes outside the mesh on clamped columns, their
+// values discarded).
 template <typename T, int P, typename Op>
 __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V, int strip, int chunk, Op& op) {
   using Val = typename Op::Val;
@@ -239,7 +241,8 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
   V2<Val> pb;
   {
     const typename Op::Raw r0 = op.load(ic, er0);
-    pb = op.pair(col_in ? op.in(r0, i, er0) : zero2<Val>(), col_in);
+    const V2<Val> v0 = op.in(r0, i, er0);
+    pb = op.pair(col_in ? v0 : zero2<Val>(), col_in);
     op.shift();
   }
 #pragma unroll
@@ -257,7 +260,8 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
         const RawE<typename Op::E> ce = ering[u];
         if (er + 1 + P <= er1 + 1) ring[u] = op.load(ic, er + 1 + P);
         if (er + P <= er1) ering[u] = op.loadE(ie, er + P);
-        const V2<Val> pt = op.pair(col_in ? op.in(cur, i, er + 1) : zero2<Val>(), col_in);
+        const V2<Val> vt = op.in(cur, i, er + 1);
+        const V2<Val> pt = op.pair(col_in ? vt : zero2<Val>(), col_in);
         const V2<Val> pbr = shfl_down2(pb), ptr = shfl_down2(pt);
         V2<Val> o1 = zero2<Val>(), o2 = zero2<Val>(), o3 = zero2<Val>(), o4 = zero2<Val>();
         if (elem) op.element(U, ce, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
@@ -433,6 +437,10 @@ struct OpPreTop : OpBase<T> {
 // Coarse-level smoothing with the restriction fused in: b = P^T r1_f (full weighting)
 // is gathered from the finer level's residual (xc), kept for the post-smoothing (o1),
 // then x1 = W b, r1 = b - K x1 (o2). winvd and wc of this level.
+// Gather: a lane (coarse column i) loads fine columns 2i and 2i+1 of a fine row and
+// takes 2i-1 from the lane to its left; the row sums of fine rows 2j-1, 2j, 2j+1 make
+// coarse row j, and row 2j+1 is kept for coarse row j+1 (load() runs on ascending
+// rows, on every lane).
 template <typename T>
 struct OpPreR : OpBase<T> {
   static constexpr int kCols = kSmoothCols, kHalo = 2;
@@ -440,10 +448,10 @@ struct OpPreR : OpBase<T> {
     V2<T> b, w;
     T c;
   };
-  bool act;
+  bool act, have_prev = false;
   int nxf, nyf;
   int64_t fbase;
-  V2<T> bt, bb;
+  V2<T> bt, bb, rs_prev;
   PairSmooth<T> ps;
   __device__ OpPreR(const View<T>& v, int s, int ic, int ie, const SampleState& S) : OpBase<T>(v, s, ic, ie) {
     act = S.active[v.sbase + s] != 0;
@@ -452,28 +460,32 @@ struct OpPreR : OpBase<T> {
     fbase = (int64_t)s * 2 * (nxf + 1) * (nyf + 1);
   }
   __device__ bool live() const { return act; }
-  __device__ Raw load(int i, int j) const {
+  // sum over fine columns 2i-1, 2i, 2i+1 of fine row jf, weights 1/2, 1, 1/2
+  __device__ V2<T> row_sum(int ic, int jf) const {
+    V2<T> a = zero2<T>(), b = zero2<T>(), c = zero2<T>();
+    const bool row_in = jf >= 0 && jf <= nyf;
+    const T* row = this->V.xc + fbase + 2 * (int64_t)jf * (nxf + 1);
+    if (row_in) {
+      a = ld2(row + 4 * ic);
+      if (2 * ic + 1 <= nxf) b = ld2(row + 4 * ic + 2);
+    }
+    c.u = __shfl_up_sync(0xffffffffu, b.u, 1);
+    c.v = __shfl_up_sync(0xffffffffu, b.v, 1);
+    if ((threadIdx.x & 31) == 0 && row_in && ic >= 1) c = ld2(row + 4 * ic - 2);
+    if (ic == 0) c = zero2<T>();   // fine column -1 (also lanes left of the mesh, discarded)
+    return v2<T>(a.u + (T)0.5 * (b.u + c.u), a.v + (T)0.5 * (b.v + c.v));
+  }
+  __device__ Raw load(int i, int j) {
     const int64_t k = this->at(i, j);
     Raw R;
     R.w = ld2(this->V.winvd + k);
     R.c = this->V.wc[k >> 1];
-    T su = (T)0, sv = (T)0;
-#pragma unroll
-    for (int dj = -1; dj <= 1; ++dj) {
-      const int jf = 2 * j + dj;
-      if (jf < 0 || jf > nyf) continue;
-      const T wj = dj == 0 ? (T)1 : (T)0.5;
-#pragma unroll
-      for (int di = -1; di <= 1; ++di) {
-        const int iff = 2 * i + di;
-        if (iff < 0 || iff > nxf) continue;
-        const T ww = wj * (di == 0 ? (T)1 : (T)0.5);
-        const V2<T> r = ld2(this->V.xc + fbase + 2 * ((int64_t)jf * (nxf + 1) + iff));
-        su += ww * r.u;
-        sv += ww * r.v;
-      }
-    }
-    R.b = this->mask(i, v2<T>(su, sv));
+    const V2<T> rm = have_prev ? rs_prev : row_sum(i, 2 * j - 1);
+    const V2<T> r0 = row_sum(i, 2 * j);
+    const V2<T> rp = row_sum(i, 2 * j + 1);
+    rs_prev = rp;
+    have_prev = true;
+    R.b = this->mask(i, v2<T>(r0.u + (T)0.5 * (rm.u + rp.u), r0.v + (T)0.5 * (rm.v + rp.v)));
     return R;
   }
   __device__ V2<T> in(const Raw& R, int, int) {
@@ -523,24 +535,20 @@ struct OpPost : OpBase<T> {
     const int64_t k = this->at(i, j);
     return Raw{ld2(this->V.a + k), ld2(this->V.winvd + k), this->V.wc[k >> 1]};
   }
-  // bilinear prolongation of the coarse correction; the coarse vector is a quarter of
-  // the fine one and each value serves up to four neighbouring fine nodes (L1 hits)
+  // bilinear prolongation of the coarse correction: a lane loads coarse column
+  // I = i / 2 (rows J and, on odd rows, J + 1; the row parity is the warp's), and an
+  // odd column adds column I + 1, which is the next lane's own I. Every lane runs this
+  // (shuffle); columns of lanes outside the mesh are clamped and their values unused.
   __device__ V2<T> in(const Raw& R, int i, int j) {
-    const int I = i >> 1, J = j >> 1;
+    const int I = min(max(i, 0), this->V.g.nx) >> 1, J = j >> 1;
     const bool fi = i & 1, fj = j & 1;
     V2<T> c = coarse(I, J);
-    if (fi) {
-      const V2<T> r = coarse(I + 1, J);
-      c = v2<T>(c.u + r.u, c.v + r.v);
-    }
     if (fj) {
-      V2<T> t = coarse(I, J + 1);
-      if (fi) {
-        const V2<T> tr = coarse(I + 1, J + 1);
-        t = v2<T>(t.u + tr.u, t.v + tr.v);
-      }
+      const V2<T> t = coarse(I, J + 1);
       c = v2<T>(c.u + t.u, c.v + t.v);
     }
+    const V2<T> r = shfl_down2(c);
+    if (fi) c = v2<T>(c.u + r.u, c.v + r.v);
     const T f = (fi && fj) ? (T)0.25 : ((fi || fj) ? (T)0.5 : (T)1);
     bt = R.b;
     wt = R.w;
