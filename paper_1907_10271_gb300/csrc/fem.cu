@@ -175,6 +175,39 @@ struct DStore<float> {
   __device__ static double as_double(const double* d, int64_t k) { return df_to_double(get(d, k)); }
 };
 
+// ---------------------------------------------------------------- async row staging
+// The FP32 strip kernels stage node rows (and element rows) in a per-warp ring of
+// shared-memory slots filled by cp.async, several rows ahead of the row being
+// processed, so that each warp keeps several rows of loads in flight without holding
+// them in registers. Slots are field-major over the 32 lanes (lane l reads entry l of
+// each field, entries it copied itself), so a lane waits only for its own copies.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// copy `bytes` (4, 8 or 16) from global to shared; with `valid` false the slot entry
+// is zero-filled and nothing is read
+template <int kBytes>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid = true) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_u32(dst)), "l"(src), "n"(kBytes),
+               "r"(valid ? kBytes : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One element row of a strip: (cos 2t, sin 2t) on the finest mesh, the averaged trig
+// 4-vector on coarse meshes.
+struct ESlot {
+  union {
+    float2 t2[32];
+    float4 t4[32];
+  };
+};
+
 template <typename T>
 __device__ __forceinline__ bool find_tile(const ViewList<T>& L, int gw, int& vi, int& s, int& strip, int& chunk) {
   vi = 0;
@@ -284,6 +317,76 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
   if (er1 + 1 == ny && ny >= j0 && ny <= j1) op.out(i, ny, acc, out_col);
 }
 
+// strip_loop with node and element rows staged through a ring of D shared-memory
+// slots (cp.async); step k holds node row er0 + k and element row er0 + k - 1.
+template <typename T, int D, typename Op>
+__device__ __forceinline__ void strip_loop_async(const Invariants& U, const View<T>& V, int strip, int chunk, Op& op,
+                                                 typename Op::Slot* ring) {
+  using Val = typename Op::Val;
+  using Sc = typename Op::Sc;
+  constexpr int kCols = Op::kCols, kHalo = Op::kHalo;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int nx = V.g.nx, ny = V.g.ny;
+  const int i = strip * kCols - kHalo + lane;
+  const bool col_in = (i >= 0) && (i <= nx);
+  const bool elem = (i >= 0) && (i < nx) && (lane < kWarp - 1);
+  const bool out_col = col_in && lane >= kHalo && lane < kHalo + kCols;
+  const int ic = min(max(i, 0), nx);
+  const int ie = min(max(i, 0), nx - 1);
+  const int j0 = chunk * kRowChunk;
+  const int j1 = min(j0 + kRowChunk - 1, ny);
+  const int er0 = max(j0 - 1, 0);
+  const int er1 = min(j1, ny - 1);
+  const int nsteps = er1 - er0 + 2;   // node rows er0 .. er1 + 1
+  const Sc rx = (Sc)V.g.rx, ry = (Sc)V.g.ry, w = (Sc)V.g.w;
+  auto issue = [&](int k) {
+    if (k < nsteps) {
+      typename Op::Slot& sl = ring[k % D];
+      op.fetch(sl, lane, ic, er0 + k);
+      if (k >= 1) op.fetchE(sl, lane, ie, er0 + k - 1);
+    }
+    cp_async_commit();   // one group per step, empty past the end
+  };
+#pragma unroll
+  for (int k = 0; k < D; ++k) issue(k);
+  cp_async_wait<D - 1>();
+  V2<Val> pb;
+  {
+    const typename Op::Raw r0 = op.read(ring[0], lane, ic, er0);
+    const V2<Val> v0 = op.in(r0, i, er0);
+    pb = op.pair(col_in ? v0 : zero2<Val>(), col_in);
+    op.shift();
+  }
+  V2<Val> acc = zero2<Val>();
+  for (int k = 1; k < nsteps; ++k) {
+    issue(k + D - 1);   // refills the slot of step k - 1, already read
+    cp_async_wait<D - 1>();
+    const int er = er0 + k - 1;
+    const typename Op::Slot& sl = ring[k % D];
+    const typename Op::Raw cur = op.read(sl, lane, ic, er + 1);
+    const RawE<typename Op::E> ce = op.readE(sl, lane);
+    const V2<Val> vt = op.in(cur, i, er + 1);
+    const V2<Val> pt = op.pair(col_in ? vt : zero2<Val>(), col_in);
+    const V2<Val> pbr = shfl_down2(pb), ptr = shfl_down2(pt);
+    V2<Val> o1 = zero2<Val>(), o2 = zero2<Val>(), o3 = zero2<Val>(), o4 = zero2<Val>();
+    if (elem) op.element(U, ce, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
+    V2<Val> fb = shfl_up2(o2), ft = shfl_up2(o3);
+    if (lane == 0) {
+      fb = zero2<Val>();
+      ft = zero2<Val>();
+    }
+    acc.u = acc.u + (o1.u + fb.u);
+    acc.v = acc.v + (o1.v + fb.v);
+    if (er >= j0) op.out(i, er, acc, out_col);
+    acc.u = o4.u + ft.u;
+    acc.v = o4.v + ft.v;
+    op.shift();
+    pb = pt;
+  }
+  cp_async_wait<0>();
+  if (er1 + 1 == ny && ny >= j0 && ny <= j1) op.out(i, ny, acc, out_col);
+}
+
 // ---------------------------------------------------------------- operand handlers
 // Each handler provides: Raw load(i, j) (node data of row j, prefetched), in(raw, i, j)
 // (value K is applied to; keeps what out() needs), out(i, j, K x), shift() (row
@@ -297,6 +400,8 @@ struct OpBase {
   static constexpr int kP32 = kPrefetch32;   // rows in flight of the FP32 variant
   static constexpr int kCols = kStripCols;    // output columns per strip
   static constexpr int kHalo = 1;             // halo lanes on each side
+  static constexpr bool kAsync = false;       // rows staged by strip_loop_async (FP32 only)
+  static constexpr int kDepth = 4;            // slots of the staging ring
   const View<T>& V;
   int64_t nbase;   // first value of the sample's vectors
   int64_t ebase;   // first element of the sample
@@ -322,6 +427,29 @@ struct OpBase {
       r.c = r.d = (T)0;
     } else {
       const Vec4T<T> t = ld4(V.trig + 4 * e);
+      r.a = t.x;
+      r.b = t.y;
+      r.c = t.z;
+      r.d = t.w;
+    }
+    return r;
+  }
+  template <typename Slot>
+  __device__ __forceinline__ void fetchE(Slot& S, int lane, int, int j) const {
+    const int64_t e = elane + (int64_t)(j * V.g.nx);
+    if (V.trig2) cp_async<8>(&S.e.t2[lane], V.trig2 + 2 * e);
+    else cp_async<16>(&S.e.t4[lane], V.trig + 4 * e);
+  }
+  template <typename Slot>
+  __device__ __forceinline__ RawE<T> readE(const Slot& S, int lane) const {
+    RawE<T> r;
+    if (V.trig2) {
+      const float2 t = S.e.t2[lane];
+      r.a = t.x;
+      r.b = t.y;
+      r.c = r.d = (T)0;
+    } else {
+      const float4 t = S.e.t4[lane];
       r.a = t.x;
       r.b = t.y;
       r.c = t.z;
@@ -386,9 +514,16 @@ struct PairSmooth {
 template <typename T>
 struct OpPreTop : OpBase<T> {
   static constexpr int kCols = kSmoothCols, kHalo = 2;
+  static constexpr bool kAsync = sizeof(T) == 4;
+  static constexpr int kDepth = 2;   // 7 streams per row: a deeper ring costs occupancy
   struct Raw {
     V2<T> r, q, w, x, p;
     T c;
+  };
+  struct Slot {
+    V2<T> r[32], q[32], w[32], x[32], p[32];
+    T c[32];
+    ESlot e;
   };
   struct Aux {
     V2<T> r, x, p;
@@ -407,6 +542,18 @@ struct OpPreTop : OpBase<T> {
     const int64_t k = this->at(i, j);
     return Raw{ld2(this->V.a + k), ld2(this->V.b + k), ld2(this->V.winvd + k), ld2(this->V.o0 + k),
                ld2(this->V.c + k), this->V.wc[k >> 1]};
+  }
+  __device__ void fetch(Slot& S, int lane, int i, int j) const {
+    const int64_t k = this->at(i, j);
+    cp_async<8>(&S.r[lane], this->V.a + k);
+    cp_async<8>(&S.q[lane], this->V.b + k);
+    cp_async<8>(&S.w[lane], this->V.winvd + k);
+    cp_async<8>(&S.x[lane], this->V.o0 + k);
+    cp_async<8>(&S.p[lane], this->V.c + k);
+    cp_async<4>(&S.c[lane], this->V.wc + (k >> 1));
+  }
+  __device__ Raw read(const Slot& S, int lane, int, int) const {
+    return Raw{S.r[lane], S.q[lane], S.w[lane], S.x[lane], S.p[lane], S.c[lane]};
   }
   __device__ V2<T> in(const Raw& R, int, int) {
     at_.r = v2<T>(R.r.u - alpha * R.q.u, R.r.v - alpha * R.q.v);
@@ -444,9 +591,19 @@ struct OpPreTop : OpBase<T> {
 template <typename T>
 struct OpPreR : OpBase<T> {
   static constexpr int kCols = kSmoothCols, kHalo = 2;
+  static constexpr bool kAsync = sizeof(T) == 4;
+  static constexpr int kDepth = 3;
   struct Raw {
     V2<T> b, w;
     T c;
+  };
+  // node row j of this level and fine rows 2j, 2j + 1 (columns 2i, 2i + 1; lane 0
+  // also 2i - 1, which the other lanes take from their left neighbour)
+  struct Slot {
+    V2<T> w[32], fa[2][32], fb[2][32];
+    T c[32];
+    V2<T> fc[2];
+    ESlot e;
   };
   bool act, have_prev = false;
   int nxf, nyf;
@@ -474,6 +631,42 @@ struct OpPreR : OpBase<T> {
     if ((threadIdx.x & 31) == 0 && row_in && ic >= 1) c = ld2(row + 4 * ic - 2);
     if (ic == 0) c = zero2<T>();   // fine column -1 (also lanes left of the mesh, discarded)
     return v2<T>(a.u + (T)0.5 * (b.u + c.u), a.v + (T)0.5 * (b.v + c.v));
+  }
+  __device__ void fetch(Slot& S, int lane, int i, int j) const {
+    const int64_t k = this->at(i, j);
+    cp_async<8>(&S.w[lane], this->V.winvd + k);
+    cp_async<4>(&S.c[lane], this->V.wc + (k >> 1));
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int jf = 2 * j + q;
+      const bool row_in = jf <= nyf;
+      const T* row = this->V.xc + fbase + 2 * (int64_t)min(jf, nyf) * (nxf + 1);
+      cp_async<8>(&S.fa[q][lane], row + 4 * i, row_in);
+      cp_async<8>(&S.fb[q][lane], row + 4 * min(i, nxf / 2 - 1) + 2, row_in && 2 * i + 1 <= nxf);
+      if (lane == 0) cp_async<8>(&S.fc[q], row + 4 * max(i, 1) - 2, row_in && i >= 1);
+    }
+  }
+  // fine row sum over columns 2i-1, 2i, 2i+1 from staged values (every lane: shuffle)
+  __device__ V2<T> slot_row_sum(const Slot& S, int lane, int q, int ic) const {
+    const V2<T> a = S.fa[q][lane], b = S.fb[q][lane];
+    V2<T> c;
+    c.u = __shfl_up_sync(0xffffffffu, b.u, 1);
+    c.v = __shfl_up_sync(0xffffffffu, b.v, 1);
+    if (lane == 0) c = S.fc[q];
+    if (ic == 0) c = zero2<T>();
+    return v2<T>(a.u + (T)0.5 * (b.u + c.u), a.v + (T)0.5 * (b.v + c.v));
+  }
+  __device__ Raw read(const Slot& S, int lane, int i, int j) {
+    Raw R;
+    R.w = S.w[lane];
+    R.c = S.c[lane];
+    const V2<T> rm = have_prev ? rs_prev : row_sum(i, 2 * j - 1);
+    const V2<T> r0 = slot_row_sum(S, lane, 0, i);
+    const V2<T> rp = slot_row_sum(S, lane, 1, i);
+    rs_prev = rp;
+    have_prev = true;
+    R.b = this->mask(i, v2<T>(r0.u + (T)0.5 * (rm.u + rp.u), r0.v + (T)0.5 * (rm.v + rp.v)));
+    return R;
   }
   __device__ Raw load(int i, int j) {
     const int64_t k = this->at(i, j);
@@ -513,9 +706,17 @@ template <typename T, bool TOP>
 struct OpPost : OpBase<T> {
   static constexpr int kP32 = 1;   // row record plus in-line coarse loads: keep registers low
   static constexpr int kCols = kSmoothCols, kHalo = 2;
+  static constexpr bool kAsync = sizeof(T) == 4;
+  static constexpr int kDepth = 3;
   struct Raw {
     V2<T> b, w;
     T c;
+    V2<T> c0, c1;   // coarse correction at (I, J) and (I, J + 1) (staged path only)
+  };
+  struct Slot {
+    V2<T> b[32], w[32], c0[32], c1[32];
+    T c[32];
+    ESlot e;
   };
   bool act;
   int nxc;
@@ -533,20 +734,32 @@ struct OpPost : OpBase<T> {
   __device__ V2<T> coarse(int I, int J) const { return ld2(this->V.xc + cbase + 2 * ((int64_t)J * (nxc + 1) + I)); }
   __device__ Raw load(int i, int j) const {
     const int64_t k = this->at(i, j);
-    return Raw{ld2(this->V.a + k), ld2(this->V.winvd + k), this->V.wc[k >> 1]};
+    const int I = i >> 1, J = j >> 1;
+    return Raw{ld2(this->V.a + k), ld2(this->V.winvd + k), this->V.wc[k >> 1], coarse(I, J),
+               (j & 1) ? coarse(I, J + 1) : zero2<T>()};
+  }
+  // i is the lane's clamped column, so the coarse column I = i / 2 is in range
+  __device__ void fetch(Slot& S, int lane, int i, int j) const {
+    const int64_t k = this->at(i, j);
+    const int I = i >> 1, J = j >> 1;
+    cp_async<8>(&S.b[lane], this->V.a + k);
+    cp_async<8>(&S.w[lane], this->V.winvd + k);
+    cp_async<4>(&S.c[lane], this->V.wc + (k >> 1));
+    cp_async<8>(&S.c0[lane], this->V.xc + cbase + 2 * ((int64_t)J * (nxc + 1) + I));
+    const int J1 = (j & 1) ? J + 1 : J;   // even rows need no second coarse row (zero-filled)
+    cp_async<8>(&S.c1[lane], this->V.xc + cbase + 2 * ((int64_t)J1 * (nxc + 1) + I), (j & 1) != 0);
+  }
+  __device__ Raw read(const Slot& S, int lane, int, int) const {
+    return Raw{S.b[lane], S.w[lane], S.c[lane], S.c0[lane], S.c1[lane]};
   }
   // bilinear prolongation of the coarse correction: a lane loads coarse column
   // I = i / 2 (rows J and, on odd rows, J + 1; the row parity is the warp's), and an
   // odd column adds column I + 1, which is the next lane's own I. Every lane runs this
   // (shuffle); columns of lanes outside the mesh are clamped and their values unused.
   __device__ V2<T> in(const Raw& R, int i, int j) {
-    const int I = min(max(i, 0), this->V.g.nx) >> 1, J = j >> 1;
     const bool fi = i & 1, fj = j & 1;
-    V2<T> c = coarse(I, J);
-    if (fj) {
-      const V2<T> t = coarse(I, J + 1);
-      c = v2<T>(c.u + t.u, c.v + t.v);
-    }
+    V2<T> c = R.c0;
+    if (fj) c = v2<T>(c.u + R.c1.u, c.v + R.c1.v);
     const V2<T> r = shfl_down2(c);
     if (fi) c = v2<T>(c.u + r.u, c.v + r.v);
     const T f = (fi && fj) ? (T)0.25 : ((fi || fj) ? (T)0.5 : (T)1);
@@ -589,8 +802,13 @@ struct OpPost : OpBase<T> {
 // a = z, b = p (old); o0 = p (new), o1 = q.
 template <typename T>
 struct OpPcgP : OpBase<T> {
+  static constexpr bool kAsync = sizeof(T) == 4;
   struct Raw {
     V2<T> z, p;
+  };
+  struct Slot {
+    V2<T> z[32], p[32];
+    ESlot e;
   };
   bool act;
   T beta;
@@ -605,6 +823,12 @@ struct OpPcgP : OpBase<T> {
     const int64_t k = this->at(i, j);
     return Raw{ld2(this->V.a + k), ld2(this->V.b + k)};
   }
+  __device__ void fetch(Slot& S, int lane, int i, int j) const {
+    const int64_t k = this->at(i, j);
+    cp_async<8>(&S.z[lane], this->V.a + k);
+    cp_async<8>(&S.p[lane], this->V.b + k);
+  }
+  __device__ Raw read(const Slot& S, int lane, int, int) const { return Raw{S.z[lane], S.p[lane]}; }
   __device__ V2<T> in(const Raw& R, int, int) {
     pt = v2<T>(R.z.u + beta * R.p.u, R.z.v + beta * R.p.v);
     return pt;
@@ -719,7 +943,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * kWarp)
     const int r0 = chunk * kRowChunk, r1 = min(r0 + kRowChunk - 1, V.g.ny);
     atomicAdd(&S.units[L.prof_op], (unsigned long long)((c1 - c0 + 1) * (r1 - r0 + 1)));
   }
-  strip_loop<T, P>(L.U, V, strip, chunk, op);
+  if constexpr (Op::kAsync) {
+    extern __shared__ __align__(16) unsigned char strip_smem[];
+    typename Op::Slot* ring = reinterpret_cast<typename Op::Slot*>(strip_smem) + (threadIdx.x >> 5) * Op::kDepth;
+    strip_loop_async<T, Op::kDepth>(L.U, V, strip, chunk, op, ring);
+  } else {
+    strip_loop<T, P>(L.U, V, strip, chunk, op);
+  }
   op.finish(S, s);
 }
 
@@ -1249,7 +1479,9 @@ cudaError_t launch_strip_op(const ViewList<T>& L, SampleState S, int total_warps
   if (total_warps <= 0) return cudaSuccess;
   const int blocks = (total_warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
   constexpr int P = sizeof(T) == 4 ? Op::kP32 : kPrefetch64;
-  k_strip<T, P, Op><<<blocks, kWarpsPerBlock * kWarp, 0, st>>>(L, S);
+  size_t smem = 0;
+  if constexpr (Op::kAsync) smem = sizeof(typename Op::Slot) * Op::kDepth * kWarpsPerBlock;
+  k_strip<T, P, Op><<<blocks, kWarpsPerBlock * kWarp, smem, st>>>(L, S);
   return cudaGetLastError();
 }
 
