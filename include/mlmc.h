@@ -251,6 +251,96 @@ mlmc_status mlmc_profile_report(mlmc_ctx* ctx, char* buf, int64_t cap);
 /* Kernel launches the library issued since the last mlmc_profile_enable. */
 mlmc_status mlmc_launch_count(mlmc_ctx* ctx, int64_t* launches);
 
+/* ---------------------------------------------------------------- serving
+ *
+ * A request loop on one GPU (continuous batching). Sample requests are queued on
+ * the host as they arrive; `workers` host threads, each with its own context and
+ * CUDA stream, repeatedly take the oldest queued requests that fit their share of
+ * the device-memory budget and solve them as one lock-stepped batch
+ * (mlmc_solve_batch), so requests that arrive while other batches are on the GPU
+ * start in the next free worker and their work overlaps on the device. Field and
+ * solver state of a batch stay on the device until it completes.
+ *
+ * A SELECTIVE request runs the selective refinement of one sample (Sec. 2.4,
+ * Algorithm 2): the failure quantity lambda (quantity 1, the centroid fibre stress)
+ * of sample (level l, id) is solved on meshes j = 0, 1, ... with the same xi; from
+ * j >= 1 the sample stops at the first j with
+ *   |lambda_j - lambda*| >= sr_factor * max(eps_rel |lambda_j|,
+ *                                            |lambda_j - lambda_{j-1}| / (m^alpha - 1))
+ * (Eq. testFailure with the sample bias estimate of Eq. sampleBias, widened by the
+ * solver's error bound), or at j = l. Each further mesh is a new request of the
+ * same loop. The sample's level-l and level-(l-1) values are lambda_J and
+ * lambda_min(J, l-1), J the stopping mesh, and its failure indicators
+ * Q_l = 1(lambda_l > lambda*), Q_{l-1} (0 for l = 0).
+ *
+ * Every result is that of the sample alone: no arithmetic mixes samples, so the
+ * batch a request lands in does not change it beyond floating-point summation
+ * order. Calls on one server are thread-safe. */
+typedef struct mlmc_server mlmc_server;
+
+#define MLMC_SR_MAX_LEVELS 16
+
+typedef enum { MLMC_REQ_SOLVE = 0, MLMC_REQ_SELECTIVE = 1 } mlmc_request_kind;
+
+typedef struct {
+  int32_t kind;         /* mlmc_request_kind */
+  int32_t level;        /* MLMC level l of the sample: its KL stream is (seed, l) */
+  int32_t mesh_level;   /* SOLVE: mesh to solve on; SELECTIVE: unused */
+  uint64_t sample_id;
+  uint64_t tag;         /* the caller's id, returned with the result */
+} mlmc_request;
+
+typedef struct {
+  uint64_t tag;
+  int32_t kind, level, mesh_level;
+  uint64_t sample_id;
+  int32_t status;       /* 0, MLMC_ERR_NOT_CONVERGED, or an error of the batch it ran in */
+  double q[2];          /* SOLVE: (reaction, stress) on mesh_level */
+  int32_t stop_level;   /* SELECTIVE: mesh J where refinement stopped (<= level) */
+  double lambda[MLMC_SR_MAX_LEVELS];   /* SELECTIVE: lambda_j, j = 0 .. stop_level */
+  double lambda_fine, lambda_coarse;   /* SELECTIVE: level-l and level-(l-1) values */
+  int32_t q_fine, q_coarse;            /* SELECTIVE: failure indicators */
+  int32_t solves;       /* meshes solved for this request */
+  double latency_ms;    /* from submission to completion */
+} mlmc_result;
+
+typedef struct {
+  int32_t workers;            /* worker threads (each: one context, one stream) */
+  int64_t max_batch;          /* requests per batch */
+  double hbm_budget_bytes;    /* device memory for all workers' batches (admission) */
+  double threshold;           /* lambda* of SELECTIVE requests (quantity 1) */
+  double sr_factor;           /* solver-error widening of the stopping test (e.g. 2) */
+  double eps_rel;             /* relative error bound of a solved lambda (e.g. 1e-6) */
+} mlmc_server_config;
+
+/* Starts the workers. cfg describes the problem (as for mlmc_create). */
+mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config* scfg, mlmc_server** out);
+
+/* Queues n requests (copied); returns at once. A request whose single-sample
+   footprint exceeds a worker's share of the budget completes with
+   MLMC_ERR_OOM. */
+mlmc_status mlmc_server_submit(mlmc_server* srv, const mlmc_request* reqs, int64_t n);
+
+/* Moves up to `max` completed results into out (oldest first); *count receives
+   how many. Never blocks. */
+mlmc_status mlmc_server_poll(mlmc_server* srv, mlmc_result* out, int64_t max, int64_t* count);
+
+/* Waits until every submitted request has completed, at most timeout_ms
+   (MLMC_ERR_TIMEOUT after that; the requests keep running). */
+mlmc_status mlmc_server_drain(mlmc_server* srv, double timeout_ms);
+
+/* Counters since creation: batches run, meshes solved, peak bytes admitted at
+   once over all workers (each output nullable). */
+mlmc_status mlmc_server_counters(mlmc_server* srv, int64_t* batches, int64_t* solves, double* peak_bytes);
+
+/* Stops the workers after their current batch and frees everything; requests
+   still queued are dropped. */
+void mlmc_server_destroy(mlmc_server* srv);
+
+/* Message of the last failure of a server call or batch (creation errors: srv
+   NULL). */
+const char* mlmc_server_last_error(const mlmc_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

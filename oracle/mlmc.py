@@ -157,3 +157,78 @@ def algorithm1(cfg, e, theta, n_star, max_level, qoi=0, alpha=1.0, gamma=1.0, m=
             converged = True
     estimate = math.fsum(moments(y)[1] for y in Y)
     return estimate, Y, L, converged
+
+
+# ---------------------------------------------------------------- selective refinement
+#
+# Sec. 2.4 (Algorithm 2). For one sample (level l, id) the failure quantity lambda
+# (quantity 1, the centroid fibre stress) is computed on meshes j = 0, 1, ... from the
+# sample's own xi. From j >= 1 (reading: the printed "j > 1" contradicts the rare-event
+# table, where most samples stop after level 1) the sample bias estimate of
+# Eq. sampleBias, |lambda_j - lambda_{j-1}| / (m^alpha - 1), decides: once
+# |lambda_j - lambda*| is at least that estimate (Eq. testFailure), widened by a solver
+# error bound (reading of "within 2 solver-error bounds": factor sr_factor on
+# max(eps_rel |lambda_j|, bias)), every finer level has the same failure indicator and
+# refinement stops at J = j; otherwise it continues, up to J = l. The sample's level-l
+# value is lambda_J and its level-(l-1) value lambda_min(J, l-1); the failure
+# indicator is 1(lambda > lambda*) (reading of the garbled 1(lambda_l - lambda*)).
+
+def sr_stops(lam, j, level, threshold, m, alpha, sr_factor, eps_rel):
+    """Stopping test of Algorithm 2 after lambda_j (lam holds lambda_0 .. lambda_j)."""
+    if j >= level:
+        return True
+    if j < 1:
+        return False
+    bias = abs(lam[j] - lam[j - 1]) / (m ** alpha - 1.0)
+    return abs(lam[j] - threshold) >= sr_factor * max(eps_rel * abs(lam[j]), bias)
+
+
+def selective_refinement(cfg, level, sample_id, threshold, m=4.0, alpha=1.0, sr_factor=2.0, eps_rel=1e-6,
+                         basis=None, solve=None):
+    """Algorithm 2 for one sample: (J, [lambda_0 .. lambda_J], lambda_l, lambda_{l-1}, Q_l, Q_{l-1}).
+
+    `solve(mesh) -> lambda` defaults to the FE solve of this module on the sample's xi.
+    """
+    if solve is None:
+        basis = basis or Basis(cfg)
+        xi = rng.kl_coefficients(cfg["seed"], level, [sample_id], cfg["kl_terms"])[0]
+
+        def solve(mesh):
+            return solve_on_mesh(cfg, basis, mesh, xi)[1]
+
+    lam = []
+    j = 0
+    while True:
+        lam.append(float(solve(j)))
+        if sr_stops(lam, j, level, threshold, m, alpha, sr_factor, eps_rel):
+            break
+        j += 1
+    lam_fine = lam[j]
+    lam_coarse = lam[min(j, level - 1)] if level >= 1 else 0.0
+    q_fine = 1 if lam_fine > threshold else 0
+    q_coarse = (1 if lam_coarse > threshold else 0) if level >= 1 else 0
+    return j, lam, lam_fine, lam_coarse, q_fine, q_coarse
+
+
+def biased_probability(x, n, k=1):
+    """Eq. biased_estimator: (x + k) / (N + k) for x events in N samples (reading: k = 1)."""
+    return (x + k) / (n + k)
+
+
+def trinomial_moments(y, k=1):
+    """Mean and variance of a level difference Y in {-1, 0, 1} from the biased estimates
+    of p_{+1} and p_{-1}: E[Y] = p_{+1} - p_{-1}, V[Y] = p_{+1} + p_{-1} - (p_{+1} - p_{-1})^2
+    (the trinomial moments; the printed forms are garbled)."""
+    y = np.asarray(y)
+    n = y.size
+    pp = biased_probability(int(np.sum(y == 1)), n, k)
+    pm = biased_probability(int(np.sum(y == -1)), n, k)
+    return pp - pm, pp + pm - (pp - pm) ** 2
+
+
+def upper_quantile(values, fraction):
+    """The order statistic ceil(N (1 - fraction)) (1-based) of the sorted values: the
+    threshold exceeded by about `fraction` of them (reading for the 1/150 quantile)."""
+    v = np.sort(np.asarray(values, dtype=np.float64))
+    k = int(math.ceil(v.size * (1.0 - fraction)))
+    return float(v[min(max(k, 1), v.size) - 1])

@@ -58,6 +58,36 @@ class mlmc_level_stats(ctypes.Structure):
                     sum_qf=list(self.sum_qf), sum_qc=list(self.sum_qc), cost=self.cost)
 
 
+SR_MAX_LEVELS = 16
+REQ_SOLVE, REQ_SELECTIVE = 0, 1
+
+
+class mlmc_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("mesh_level", ctypes.c_int32),
+                ("sample_id", ctypes.c_uint64), ("tag", ctypes.c_uint64)]
+
+
+class mlmc_result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("kind", ctypes.c_int32), ("level", ctypes.c_int32),
+                ("mesh_level", ctypes.c_int32), ("sample_id", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("q", ctypes.c_double * 2), ("stop_level", ctypes.c_int32),
+                ("lambda_", ctypes.c_double * SR_MAX_LEVELS), ("lambda_fine", ctypes.c_double),
+                ("lambda_coarse", ctypes.c_double), ("q_fine", ctypes.c_int32), ("q_coarse", ctypes.c_int32),
+                ("solves", ctypes.c_int32), ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(tag=self.tag, kind=self.kind, level=self.level, mesh_level=self.mesh_level,
+                    sample_id=self.sample_id, status=self.status, q=list(self.q), stop_level=self.stop_level,
+                    lambdas=list(self.lambda_[:self.stop_level + 1]), lambda_fine=self.lambda_fine,
+                    lambda_coarse=self.lambda_coarse, q_fine=self.q_fine, q_coarse=self.q_coarse,
+                    solves=self.solves, latency_ms=self.latency_ms)
+
+
+class mlmc_server_config(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int64), ("hbm_budget_bytes", ctypes.c_double),
+                ("threshold", ctypes.c_double), ("sr_factor", ctypes.c_double), ("eps_rel", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -90,6 +120,14 @@ def lib():
             "mlmc_profile_report": (I32, [P, P, I64]),
             "mlmc_solve_theta_static": (I32, [ctypes.POINTER(mlmc_config), P, I32, I64, P, P, P]),
             "mlmc_static_last_error": (ctypes.c_char_p, []),
+            "mlmc_server_create": (I32, [ctypes.POINTER(mlmc_config), ctypes.POINTER(mlmc_server_config),
+                                         ctypes.POINTER(P)]),
+            "mlmc_server_submit": (I32, [P, P, I64]),
+            "mlmc_server_poll": (I32, [P, P, I64, P]),
+            "mlmc_server_drain": (I32, [P, D]),
+            "mlmc_server_counters": (I32, [P, P, P, P]),
+            "mlmc_server_destroy": (None, [P]),
+            "mlmc_server_last_error": (ctypes.c_char_p, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -302,3 +340,54 @@ def mlmc_profile_report(ctx):
         name, n, ms = line.rsplit(" ", 2)
         out[name] = (int(n), float(ms))
     return out
+
+
+# ---------------------------------------------------------------- serving
+
+def mlmc_server_create(cfg, workers=2, max_batch=4096, hbm_budget_bytes=8e9, threshold=0.0, sr_factor=2.0,
+                       eps_rel=1e-6):
+    L = lib()
+    sc = mlmc_server_config(workers, max_batch, float(hbm_budget_bytes), float(threshold), float(sr_factor),
+                            float(eps_rel))
+    srv = ctypes.c_void_p()
+    st = L.mlmc_server_create(ctypes.byref(cfg), ctypes.byref(sc), ctypes.byref(srv))
+    if st != 0:
+        raise MLMCError(st, L.mlmc_server_last_error(None).decode())
+    return srv
+
+
+def mlmc_server_submit(srv, requests):
+    """requests: iterable of (kind, level, mesh_level, sample_id, tag)."""
+    reqs = list(requests)
+    arr = (mlmc_request * max(1, len(reqs)))(*[mlmc_request(*r) for r in reqs])
+    st = lib().mlmc_server_submit(srv, ctypes.cast(arr, ctypes.c_void_p), len(reqs))
+    if st != 0:
+        raise MLMCError(st, lib().mlmc_server_last_error(srv).decode())
+
+
+def mlmc_server_poll(srv, max_results=4096):
+    buf = (mlmc_result * max_results)()
+    n = ctypes.c_int64()
+    st = lib().mlmc_server_poll(srv, ctypes.cast(buf, ctypes.c_void_p), max_results, ctypes.byref(n))
+    if st != 0:
+        raise MLMCError(st, lib().mlmc_server_last_error(srv).decode())
+    return [buf[k].as_dict() for k in range(n.value)]
+
+
+def mlmc_server_drain(srv, timeout_ms=600000.0):
+    """True when every submitted request completed within the timeout."""
+    return lib().mlmc_server_drain(srv, float(timeout_ms)) == 0
+
+
+def mlmc_server_counters(srv):
+    b, s, pk = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    lib().mlmc_server_counters(srv, ctypes.byref(b), ctypes.byref(s), ctypes.byref(pk))
+    return {"batches": b.value, "solves": s.value, "peak_bytes": pk.value}
+
+
+def mlmc_server_last_error(srv):
+    return lib().mlmc_server_last_error(srv).decode()
+
+
+def mlmc_server_destroy(srv):
+    lib().mlmc_server_destroy(srv)

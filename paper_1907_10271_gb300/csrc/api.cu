@@ -346,6 +346,28 @@ void fill_stats(const mlmc_ctx* h, int l, mlmc_level_stats* out) {
 
 }  // namespace
 
+namespace mlmc {
+
+mlmc_status reserve_workspace(mlmc_ctx* h, size_t solve_bytes, size_t batch_bytes) {
+  Context& c = h->c;
+  cudaError_t e = c.solve_arena.reserve(solve_bytes);
+  if (e == cudaSuccess) e = c.batch_arena.reserve(batch_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return c.fail(MLMC_ERR_OOM, "workspace reservation failed");
+  }
+  return MLMC_OK;
+}
+
+double solve_bytes_per_sample(const mlmc_config& cfg, int mesh) {
+  const double tb = cfg.precision == MLMC_PREC_MIXED ? 4.0 : 8.0;
+  const double nx = (double)((int64_t)cfg.nx0 << mesh), ny = (double)((int64_t)cfg.ny0 << mesh);
+  const double dofs = 2.0 * (nx + 1.0) * (ny + 1.0);
+  return dofs * (14.0 * tb + 16.0) * 1.4 + 2.0 * nx * ny * tb + 96.0 * cfg.kl_terms + 512.0;
+}
+
+}  // namespace mlmc
+
 extern "C" {
 
 mlmc_status mlmc_create(const mlmc_config* cfg, void* cuda_stream, mlmc_ctx** out) {

@@ -57,4 +57,12 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups);
 template <typename T>
 mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* trig2, const T* p, T* q);
 
+// Grows a context's solver and batch workspaces to at least the given sizes now, so
+// that later calls within them allocate nothing (cudaFree synchronises the device).
+mlmc_status reserve_workspace(mlmc_ctx* h, size_t solve_bytes, size_t batch_bytes);
+
+// Device bytes one solve on `mesh` needs in a batch (solver workspace, field and
+// outputs), with margin.
+double solve_bytes_per_sample(const mlmc_config& cfg, int mesh);
+
 }  // namespace mlmc

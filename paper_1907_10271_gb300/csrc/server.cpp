@@ -1,0 +1,301 @@
+// Request loop with continuous batching on one GPU, and the selective refinement of
+// Sec. 2.4 (Algorithm 2) as a request kind.
+//
+// Host side only: a FIFO of pending requests (escalations of selective-refinement
+// samples go to its front), `workers` threads each owning an mlmc context on its own
+// non-blocking CUDA stream. A free worker takes the oldest pending requests whose
+// footprint fits its share of the device-memory budget (at most max_batch), runs them
+// as one mlmc_solve_batch, and feeds the results back: SOLVE requests complete,
+// SELECTIVE requests either stop (the stopping test of Eq. testFailure with the
+// sample bias estimate of Eq. sampleBias) or re-enter the queue on the next mesh.
+// Workspaces are reserved to the share up front, so serving allocates nothing.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "engine.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Pending {
+  mlmc_request req;
+  Clock::time_point t0;
+  int mesh = 0;   // SELECTIVE: next mesh to solve
+  int solves = 0;
+  double lambda[MLMC_SR_MAX_LEVELS] = {0};
+};
+
+}  // namespace
+
+struct mlmc_server {
+  mlmc_config cfg;
+  mlmc_server_config scfg;
+  std::vector<mlmc_ctx*> ctx;
+  std::vector<cudaStream_t> streams;
+  std::vector<std::thread> threads;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Pending> queue;
+  std::deque<mlmc_result> done;
+  int64_t outstanding = 0;
+  bool stop = false;
+  int64_t batches = 0, solves = 0;
+  double in_flight = 0.0, peak = 0.0, share = 0.0;
+  int device = 0;
+  char err[512] = {0};   // last failure message (stable storage for mlmc_server_last_error)
+
+  void record_error(const std::string& m) {
+    std::lock_guard<std::mutex> g(mu);
+    std::strncpy(err, m.c_str(), sizeof(err) - 1);
+  }
+
+  // called with mu held
+  void complete(const Pending& p, int32_t status, const double* q, int stop_level) {
+    mlmc_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.tag = p.req.tag;
+    r.kind = p.req.kind;
+    r.level = p.req.level;
+    r.mesh_level = p.req.mesh_level;
+    r.sample_id = p.req.sample_id;
+    r.status = status;
+    r.solves = p.solves;
+    if (q) {
+      r.q[0] = q[0];
+      r.q[1] = q[1];
+    }
+    if (p.req.kind == MLMC_REQ_SELECTIVE && status == 0) {
+      r.stop_level = stop_level;
+      for (int j = 0; j <= stop_level; ++j) r.lambda[j] = p.lambda[j];
+      const int l = p.req.level;
+      r.lambda_fine = p.lambda[stop_level];
+      r.q_fine = r.lambda_fine > scfg.threshold ? 1 : 0;
+      if (l >= 1) {
+        r.lambda_coarse = p.lambda[std::min(stop_level, l - 1)];
+        r.q_coarse = r.lambda_coarse > scfg.threshold ? 1 : 0;
+      }
+    }
+    r.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - p.t0).count();
+    done.push_back(r);
+    --outstanding;
+  }
+
+  // Stopping test of a selective-refinement sample after its solve on mesh j.
+  bool sr_stops(const Pending& p, int j) const {
+    if (j >= p.req.level) return true;
+    if (j < 1) return false;   // no bias estimate before two meshes
+    const double lj = p.lambda[j], lp = p.lambda[j - 1];
+    const double bias = std::fabs(lj - lp) / (std::pow(cfg.mlmc_m, cfg.mlmc_alpha) - 1.0);
+    const double bound = scfg.sr_factor * std::max(scfg.eps_rel * std::fabs(lj), bias);
+    return std::fabs(lj - scfg.threshold) >= bound;
+  }
+
+  int mesh_of(const Pending& p) const { return p.req.kind == MLMC_REQ_SOLVE ? p.req.mesh_level : p.mesh; }
+
+  void worker(int w) {
+    cudaSetDevice(device);
+    std::vector<Pending> batch;
+    std::vector<mlmc_item> items;
+    std::vector<double> q;
+    std::vector<int32_t> st;
+    for (;;) {
+      double bytes = 0.0;
+      batch.clear();
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+        if (stop) return;
+        while (!queue.empty() && (int64_t)batch.size() < scfg.max_batch) {
+          const double b = mlmc::solve_bytes_per_sample(cfg, mesh_of(queue.front()));
+          if (batch.empty() && b > share) {   // can never fit
+            Pending p = queue.front();
+            queue.pop_front();
+            complete(p, MLMC_ERR_OOM, nullptr, 0);
+            cv_done.notify_all();
+            continue;
+          }
+          if (bytes + b > share) break;
+          bytes += b;
+          batch.push_back(queue.front());
+          queue.pop_front();
+        }
+        if (batch.empty()) continue;
+        in_flight += bytes;
+        peak = std::max(peak, in_flight);
+      }
+      items.resize(batch.size());
+      for (size_t k = 0; k < batch.size(); ++k) {
+        items[k].level = batch[k].req.level;
+        items[k].mesh_level = mesh_of(batch[k]);
+        items[k].sample_id = batch[k].req.sample_id;
+      }
+      q.assign(2 * batch.size(), 0.0);
+      st.assign(batch.size(), 0);
+      const mlmc_status s = mlmc_solve_batch(ctx[w], items.data(), (int64_t)items.size(), q.data(), st.data());
+      if (s != MLMC_OK) record_error(mlmc_last_error(ctx[w]));
+      {
+        std::lock_guard<std::mutex> g(mu);
+        in_flight -= bytes;
+        ++batches;
+        solves += (int64_t)batch.size();
+        std::vector<Pending> again;
+        for (size_t k = 0; k < batch.size(); ++k) {
+          Pending& p = batch[k];
+          ++p.solves;
+          const int32_t status = s != MLMC_OK ? (int32_t)s : st[k];
+          if (status != 0 || p.req.kind == MLMC_REQ_SOLVE) {
+            complete(p, status, &q[2 * k], 0);
+            continue;
+          }
+          const int j = p.mesh;
+          p.lambda[j] = q[2 * k + 1];
+          if (sr_stops(p, j)) {
+            complete(p, 0, &q[2 * k], j);
+          } else {
+            p.mesh = j + 1;
+            again.push_back(p);
+          }
+        }
+        // escalations go first, in their original order
+        for (auto it = again.rbegin(); it != again.rend(); ++it) queue.push_front(*it);
+        if (!again.empty()) cv_work.notify_all();
+        cv_done.notify_all();
+      }
+    }
+  }
+};
+
+namespace {
+std::string g_server_error;
+}
+
+extern "C" {
+
+mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config* scfg, mlmc_server** out) {
+  if (!cfg || !scfg || !out) return MLMC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (scfg->workers < 1 || scfg->workers > 64 || scfg->max_batch < 1 || !(scfg->hbm_budget_bytes > 0) ||
+      !(scfg->sr_factor >= 1.0) || !(scfg->eps_rel >= 0.0) || cfg->levels > MLMC_SR_MAX_LEVELS) {
+    g_server_error = "bad server configuration";
+    return MLMC_ERR_INVALID_ARG;
+  }
+  if (!(cfg->mlmc_m > 1.0) || !(cfg->mlmc_alpha > 0.0)) {
+    g_server_error = "selective refinement needs mlmc_m > 1 and mlmc_alpha > 0";
+    return MLMC_ERR_INVALID_ARG;
+  }
+  mlmc_server* s = new mlmc_server();
+  s->cfg = *cfg;
+  s->scfg = *scfg;
+  s->share = scfg->hbm_budget_bytes / scfg->workers;
+  cudaGetDevice(&s->device);
+  for (int w = 0; w < scfg->workers; ++w) {
+    cudaStream_t st = nullptr;
+    mlmc_ctx* c = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      g_server_error = "stream creation failed";
+      mlmc_server_destroy(s);
+      return MLMC_ERR_CUDA;
+    }
+    s->streams.push_back(st);
+    mlmc_status e = mlmc_create(cfg, st, &c);
+    if (e != MLMC_OK) {
+      g_server_error = std::string("worker context: ") + mlmc_last_error(nullptr);
+      mlmc_server_destroy(s);
+      return e;
+    }
+    s->ctx.push_back(c);
+    // the share, split like the footprint estimate: solver workspace and batch buffers
+    e = mlmc::reserve_workspace(c, (size_t)(0.85 * s->share), (size_t)(0.15 * s->share));
+    if (e != MLMC_OK) {
+      g_server_error = std::string("worker workspace: ") + mlmc_last_error(c);
+      mlmc_server_destroy(s);
+      return e;
+    }
+  }
+  for (int w = 0; w < scfg->workers; ++w) s->threads.emplace_back([s, w] { s->worker(w); });
+  *out = s;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_server_submit(mlmc_server* s, const mlmc_request* reqs, int64_t n) {
+  if (!s || n < 0 || (n > 0 && !reqs)) return MLMC_ERR_INVALID_ARG;
+  for (int64_t k = 0; k < n; ++k) {
+    const mlmc_request& r = reqs[k];
+    const bool ok = r.level >= 0 && r.level < s->cfg.levels &&
+                    (r.kind == MLMC_REQ_SELECTIVE ||
+                     (r.kind == MLMC_REQ_SOLVE && r.mesh_level >= 0 && r.mesh_level < s->cfg.levels));
+    if (!ok) {
+      s->record_error("request with an invalid kind, level or mesh");
+      return MLMC_ERR_INVALID_ARG;
+    }
+  }
+  const Clock::time_point t0 = Clock::now();
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    for (int64_t k = 0; k < n; ++k) {
+      Pending p;
+      p.req = reqs[k];
+      p.t0 = t0;
+      s->queue.push_back(p);
+    }
+    s->outstanding += n;
+  }
+  s->cv_work.notify_all();
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_server_poll(mlmc_server* s, mlmc_result* out, int64_t max, int64_t* count) {
+  if (!s || !count || max < 0 || (max > 0 && !out)) return MLMC_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  int64_t k = 0;
+  while (k < max && !s->done.empty()) {
+    out[k++] = s->done.front();
+    s->done.pop_front();
+  }
+  *count = k;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_server_drain(mlmc_server* s, double timeout_ms) {
+  if (!s) return MLMC_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const bool ok = s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(std::max(0.0, timeout_ms)),
+                                      [&] { return s->outstanding == 0; });
+  return ok ? MLMC_OK : MLMC_ERR_TIMEOUT;
+}
+
+mlmc_status mlmc_server_counters(mlmc_server* s, int64_t* batches, int64_t* solves, double* peak_bytes) {
+  if (!s) return MLMC_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  if (batches) *batches = s->batches;
+  if (solves) *solves = s->solves;
+  if (peak_bytes) *peak_bytes = s->peak;
+  return MLMC_OK;
+}
+
+void mlmc_server_destroy(mlmc_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->threads) t.join();
+  for (auto* c : s->ctx) mlmc_destroy(c);
+  for (auto st : s->streams) cudaStreamDestroy(st);
+  delete s;
+}
+
+const char* mlmc_server_last_error(const mlmc_server* s) { return s ? s->err : g_server_error.c_str(); }
+
+}  // extern "C"

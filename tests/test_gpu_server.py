@@ -1,0 +1,159 @@
+"""The request loop (continuous batching) and selective refinement, through the C ABI.
+
+- a request's result is the same alone and in a mix of concurrent traffic (the stated
+  1e-6 per quantity; nothing mixes samples, so the difference is summation order);
+- served solves equal mlmc_solve_batch and the oracle;
+- selective refinement follows the oracle's Algorithm 2 (same stopping meshes, same
+  lambdas, same indicators);
+- admission: a request that cannot fit a worker's share of the budget completes with
+  MLMC_ERR_OOM, and the bytes admitted at once never exceed the budget.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import mlmc as om
+from workloads import STRIP_FP64_3LEVEL, STRIP_MIXED_5LEVEL
+
+pytestmark = pytest.mark.gpu
+
+SOLVE, SEL = 0, 1
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1907_10271_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def collect(B, srv, n, timeout_s=600):
+    assert B.mlmc_server_drain(srv, timeout_s * 1e3), B.mlmc_server_last_error(srv)
+    out = []
+    while len(out) < n:
+        got = B.mlmc_server_poll(srv, 4096)
+        assert got, "drained server returned fewer results than submitted"
+        out += got
+    return {r["tag"]: r for r in out}
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def test_result_is_the_same_alone_and_in_the_mix(B):
+    w = STRIP_MIXED_5LEVEL
+    cfg = B.config_from_workload(w)
+    cases = [(l, m, 1000 + 17 * k + l) for l in range(3) for m in sorted({l, max(l - 1, 0)}) for k in range(4)]
+    probe = [(SOLVE, l, m, sid, tag) for tag, (l, m, sid) in enumerate(cases)]
+    # alone: one worker, one request at a time
+    srv = B.mlmc_server_create(cfg, workers=1, max_batch=64, hbm_budget_bytes=2e9)
+    alone = {}
+    try:
+        for r in probe:
+            B.mlmc_server_submit(srv, [r])
+            alone.update(collect(B, srv, 1))
+    finally:
+        B.mlmc_server_destroy(srv)
+    # in the mix: three workers, the probes interleaved with other traffic that keeps
+    # arriving while earlier batches run
+    g = np.random.default_rng(3)
+    noise = [(SOLVE, int(l), int(l), 50000 + k, 10 ** 6 + k) for k, l in enumerate(g.integers(0, 3, 150))]
+    traffic = probe + noise
+    order = g.permutation(len(traffic))
+    srv = B.mlmc_server_create(cfg, workers=3, max_batch=24, hbm_budget_bytes=3e9)
+    try:
+        for chunk in np.array_split(order, 6):
+            B.mlmc_server_submit(srv, [traffic[i] for i in chunk])
+            time.sleep(0.02)
+        mix = collect(B, srv, len(traffic))
+        counters = B.mlmc_server_counters(srv)
+    finally:
+        B.mlmc_server_destroy(srv)
+    assert counters["batches"] > 6 and counters["solves"] == len(traffic)
+    for r in probe:
+        a, m = alone[r[4]], mix[r[4]]
+        assert a["status"] == 0 and m["status"] == 0
+        for k in range(2):
+            assert rel(m["q"][k], a["q"][k]) < 1e-6, (r, a["q"], m["q"])
+    # and both equal a plain batch solve of the same items
+    ctx = B.mlmc_create(cfg)
+    try:
+        q = np.zeros(2 * len(probe))
+        B.mlmc_solve_batch(ctx, [(r[1], r[2], r[3]) for r in probe], q)
+    finally:
+        B.mlmc_destroy(ctx)
+    for k, r in enumerate(probe):
+        for c in range(2):
+            assert rel(alone[r[4]]["q"][c], q[2 * k + c]) < 1e-6
+
+
+def test_served_solves_match_the_oracle(B):
+    w = STRIP_FP64_3LEVEL
+    srv = B.mlmc_server_create(B.config_from_workload(w), workers=2, max_batch=8, hbm_budget_bytes=1e9)
+    cases = [(l, m, 7 + k) for l in range(3) for m in sorted({l, max(l - 1, 0)}) for k in range(3)]
+    reqs = [(SOLVE, l, m, sid, tag) for tag, (l, m, sid) in enumerate(cases)]
+    try:
+        B.mlmc_server_submit(srv, reqs)
+        res = collect(B, srv, len(reqs))
+    finally:
+        B.mlmc_server_destroy(srv)
+    basis = om.Basis(w)
+    for kind, l, m, sid, tag in reqs:
+        xi = om.rng.kl_coefficients(w["seed"], l, [sid], w["kl_terms"])[0]
+        ref = om.solve_on_mesh(w, basis, m, xi)
+        for c in range(2):
+            assert rel(res[tag]["q"][c], ref[c]) < 1e-9
+
+
+def test_selective_refinement_matches_the_oracle(B):
+    w = STRIP_FP64_3LEVEL
+    basis = om.Basis(w)
+    # threshold: an upper quantile of the level-1 stress from a seeded pilot on the
+    # oracle, so that samples on both sides and near it occur
+    pilot = [om.level_pair(w, 1, [k], basis)[0][0, 1] for k in range(40)]
+    thr = om.upper_quantile(pilot, 0.3)
+    srv = B.mlmc_server_create(B.config_from_workload(w), workers=2, max_batch=16, hbm_budget_bytes=1e9,
+                               threshold=thr, sr_factor=2.0, eps_rel=1e-6)
+    reqs = [(SEL, l, 0, sid, 1000 * l + sid) for l in range(3) for sid in range(12)]
+    try:
+        B.mlmc_server_submit(srv, reqs)
+        res = collect(B, srv, len(reqs))
+    finally:
+        B.mlmc_server_destroy(srv)
+    m, alpha = w.get("mlmc_m", 4.0), w.get("mlmc_alpha", 1.0)
+    decided_early = 0
+    for _, l, _, sid, tag in reqs:
+        r = res[tag]
+        assert r["status"] == 0
+        J, lam, lf, lc, qf, qc = om.selective_refinement(w, l, sid, thr, m=m, alpha=alpha, sr_factor=2.0,
+                                                          eps_rel=1e-6, basis=basis)
+        assert r["stop_level"] == J and r["solves"] == J + 1
+        assert all(rel(a, b) < 1e-9 for a, b in zip(r["lambdas"], lam))
+        assert (r["q_fine"], r["q_coarse"]) == (qf, qc)
+        assert rel(r["lambda_fine"], lf) < 1e-9
+        decided_early += J < l
+        assert r["latency_ms"] > 0
+    assert decided_early > 0
+
+
+def test_admission_by_memory_budget(B):
+    w = STRIP_MIXED_5LEVEL
+    cfg = B.config_from_workload(w)
+    # a share (budget / workers) that holds level-2 meshes but not a 1024 x 256 solve
+    srv = B.mlmc_server_create(cfg, workers=2, max_batch=1000, hbm_budget_bytes=2 * 20e6)
+    reqs = [(SOLVE, 2, 2, k, k) for k in range(40)] + [(SOLVE, 4, 4, 0, 999)]
+    try:
+        B.mlmc_server_submit(srv, reqs)
+        res = collect(B, srv, len(reqs))
+        counters = B.mlmc_server_counters(srv)
+    finally:
+        B.mlmc_server_destroy(srv)
+    assert res[999]["status"] == 2          # MLMC_ERR_OOM: larger than a worker's share
+    assert all(res[k]["status"] == 0 for k in range(40))
+    assert 0 < counters["peak_bytes"] <= 2 * 20e6
+    assert counters["batches"] >= 4     # a 256 x 64 solve needs ~3.5 MB: the share splits the load
