@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-single", dest="fp64_single", action="store_false",
                     help="skip the plain double-precision single-sample comparison")
+    ap.add_argument("--no-serving", dest="serving", action="store_false",
+                    help="skip the request-loop (selective refinement) measurement")
     ap.add_argument("--case", choices=["full", "small"], default="full",
                     help="small: one untimed call with 1/8 of each level's samples (for profilers)")
     ap.add_argument("--cpu-fraction", type=float, default=1.0 / 32.0,
@@ -452,6 +454,104 @@ def run_gpu(a):
     return out
 
 
+# ---------------------------------------------------------------- serving (selective refinement)
+
+def run_serving(B, cfg_w, seconds=3.0, load=0.5):
+    """The request loop on the selective-refinement workload: failure of the 5-level
+    strip when the centroid fibre stress exceeds the 1/150 upper quantile of a seeded
+    pilot (seed 1, 4096 level-2 samples); SELECTIVE requests of levels 0..4 in the
+    proportions of the MLMC level counts. Capacity from a saturating burst, then
+    Poisson arrivals at `load` of it for `seconds`: completed requests/s (each one
+    level sample Y_l = Q_l - Q_{l-1}), latency p50/p99, solves per request, and the
+    estimate sum_l mean(Y_l) of the failure probability."""
+    import torch
+    counts = cfg_w["n_per_level"]
+    levels = list(range(cfg_w["levels"]))
+    # threshold from the pilot
+    pilot_cfg = B.config_from_workload(cfg_w, seed=1)
+    ctx = B.mlmc_create(pilot_cfg, torch.cuda.current_stream().cuda_stream)
+    n_pilot = 4096
+    qf = torch.zeros(2 * n_pilot, dtype=torch.float64, device="cuda")
+    qc = torch.zeros_like(qf)
+    B.mlmc_sample_level(ctx, 2, 0, n_pilot, qf, qc)
+    torch.cuda.synchronize()
+    B.mlmc_destroy(ctx)
+    stress = np.sort(qf.view(n_pilot, 2)[:, 1].cpu().numpy())
+    threshold = float(stress[int(math.ceil(n_pilot * (1.0 - 1.0 / 150.0))) - 1])
+    srv = B.mlmc_server_create(B.config_from_workload(cfg_w), workers=4, max_batch=4096, hbm_budget_bytes=100e9,
+                               threshold=threshold, sr_factor=2.0, eps_rel=1e-6)
+    g = np.random.default_rng(2)
+    p_level = np.array(counts, dtype=float) / sum(counts)
+    next_id = [0] * len(levels)
+    tag = [0]
+
+    def make(n):
+        out = []
+        for l in g.choice(levels, size=n, p=p_level):
+            out.append((1, int(l), 0, next_id[l], tag[0]))
+            next_id[l] += 1
+            tag[0] += 1
+        return out
+
+    def drain_all():
+        res = []
+        while True:
+            got = B.mlmc_server_poll(srv, 65536)
+            if not got:
+                break
+            res += got
+        return res
+
+    try:
+        # capacity: a burst of requests at once
+        burst = make(8192)
+        t0 = time.perf_counter()
+        B.mlmc_server_submit(srv, burst)
+        B.mlmc_server_drain(srv, 600e3)
+        cap = len(burst) / (time.perf_counter() - t0)
+        results = drain_all()
+        # Poisson arrivals at `load` of capacity
+        rate = load * cap
+        n = int(rate * seconds)
+        arrivals = np.cumsum(g.exponential(1.0 / rate, size=n))
+        reqs = make(n)
+        t0 = time.perf_counter()
+        k = 0
+        while k < n:
+            now = time.perf_counter() - t0
+            j = int(np.searchsorted(arrivals, now, side="right"))
+            if j > k:
+                B.mlmc_server_submit(srv, reqs[k:j])
+                k = j
+            else:
+                time.sleep(min(0.001, max(0.0, arrivals[k] - now)))
+        B.mlmc_server_drain(srv, 600e3)
+        wall = time.perf_counter() - t0
+        stream = [r for r in drain_all() if r["tag"] >= len(burst)]
+        counters = B.mlmc_server_counters(srv)
+    finally:
+        B.mlmc_server_destroy(srv)
+    lat = np.array([r["latency_ms"] for r in stream])
+    ok = [r for r in results + stream if r["status"] == 0]
+    est_ml, _, _ = B.mlmc_failure_estimate(ok, threshold, k=1, two_level=False)
+    est_2l, _, _ = B.mlmc_failure_estimate(ok, threshold, k=1, two_level=True)
+    return {"workload": "selective refinement, P(stress > 1/150 upper quantile of a seed-1 pilot), levels 0-4 "
+                        "in MLMC proportions, 4 workers, 100 GB budget",
+            "threshold_pa": threshold,
+            "capacity_requests_per_s": round(cap, 1),
+            "offered_requests_per_s": round(rate, 1),
+            "value": round(len(stream) / wall, 1), "unit": "level-samples/s (Poisson arrivals at %.0f%% of capacity)"
+            % (100 * load),
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                           "p99": round(float(np.percentile(lat, 99)), 3)},
+            "solves_per_request": round(sum(r["solves"] for r in ok) / max(1, len(ok)), 3),
+            "stopped_early": round(sum(r["stop_level"] < r["level"] for r in ok) / max(1, len(ok)), 4),
+            "failure_probability": {"multilevel": est_ml, "two_level": est_2l,
+                                    "estimator": "biased (x + k)/(N + k), k = 1, trinomial moments"},
+            "failed_requests": len(results) + len(stream) - len(ok),
+            "batches": counters["batches"], "peak_admitted_gb": round(counters["peak_bytes"] / 1e9, 2)}
+
+
 def run_small_case():
     """One call of the workload with 1/8 of each level's samples, after one warm call:
     a short, bounded command for kernel captures (about 1.3 GB of device memory)."""
@@ -501,6 +601,9 @@ def main():
                                   "d2h_bytes_per_step": 0}}))
         return
     out = run_gpu(a)
+    if rank == 0 and out is not None and world == 1 and a.serving:
+        from paper_1907_10271_gb300 import binding as B
+        out["serving"] = run_serving(B, STRIP_MIXED_5LEVEL)
     if rank == 0 and out is not None:
         if world == 1 and not a.no_cpu_baseline:
             cores = os.cpu_count() or 1

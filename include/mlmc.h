@@ -313,6 +313,24 @@ typedef struct {
   double eps_rel;             /* relative error bound of a solved lambda (e.g. 1e-6) */
 } mlmc_server_config;
 
+/* Failure-probability estimate from completed SELECTIVE results (host arithmetic
+   only; Sec. 2.4). Per term, with x_{+1}, x_{-1} the counts of Y = +1 and Y = -1
+   among N results, the biased estimates p~ = (x + k) / (N + k) (Eq.
+   biased_estimator) give E[Y] = p~_{+1} - p~_{-1} and
+   V[Y] = p~_{+1} + p~_{-1} - (p~_{+1} - p~_{-1})^2; level-0 terms are binomial
+   (p~_{-1} = 0).
+   two_level == 0: the multilevel sum over the levels present,
+     sum_l E[Y_l], Y_l = Q_l - Q_{l-1} (Y_0 = Q_0);
+   two_level != 0: E[Q] ~ E[Q_0] + E[Y_{L,0}] with Q_0 from the level-0 results and
+     Y_{L,0} = Q_L - 1(lambda_0 > threshold) from the results of the highest level L
+     present (lambda_0 the sample's mesh-0 value, solved first by every SELECTIVE
+     request).
+   Results with a nonzero status are skipped. mean[] and var[] (nullable, length
+   MLMC_SR_MAX_LEVELS) receive each term's E and V (indexed by level; in the
+   two-level form index 0 holds Q_0 and index L holds Y_{L,0}). */
+mlmc_status mlmc_failure_estimate(const mlmc_result* results, int64_t n, double threshold, int32_t k,
+                                  int32_t two_level, double* estimate, double* mean, double* var);
+
 /* Starts the workers. cfg describes the problem (as for mlmc_create). */
 mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config* scfg, mlmc_server** out);
 

@@ -232,3 +232,33 @@ def upper_quantile(values, fraction):
     v = np.sort(np.asarray(values, dtype=np.float64))
     k = int(math.ceil(v.size * (1.0 - fraction)))
     return float(v[min(max(k, 1), v.size) - 1])
+
+
+def failure_estimate(levels, q_fine, q_coarse, q_mesh0, k=1, two_level=False):
+    """Failure probability from selective-refinement samples (Sec. 2.4): per level l the
+    indicators Q_l (q_fine), Q_{l-1} (q_coarse) and 1(lambda_0 > lambda*) (q_mesh0).
+
+    Multilevel form: sum over levels of E[Y_l], Y_l = Q_l - Q_{l-1}, Y_0 = Q_0.
+    Two-level form (the paper's E[Q] ~ Q_0 + Y_{L,0}): the level-0 samples' Q_0 plus
+    the top level's Y_{L,0} = Q_L - Q_0 of the same sample. Each term's mean and
+    variance come from the biased estimates (x + k)/(N + k) of P(Y = +1) and
+    P(Y = -1) (trinomial moments; a level-0 term has no -1 outcome).
+    Returns (estimate, {term level: (mean, var)})."""
+    levels = np.asarray(levels)
+    top = int(levels.max())
+    terms = {}
+    for l in sorted(set(levels.tolist())):
+        idx = levels == l
+        if l == 0:
+            y = np.asarray(q_fine)[idx]
+        elif not two_level:
+            y = np.asarray(q_fine)[idx] - np.asarray(q_coarse)[idx]
+        elif l == top:
+            y = np.asarray(q_fine)[idx] - np.asarray(q_mesh0)[idx]
+        else:
+            continue
+        n = y.size
+        pp = biased_probability(int(np.sum(y == 1)), n, k)
+        pm = 0.0 if l == 0 else biased_probability(int(np.sum(y == -1)), n, k)
+        terms[l] = (pp - pm, pp + pm - (pp - pm) ** 2)
+    return math.fsum(m for m, _ in terms.values()), terms

@@ -128,6 +128,7 @@ def lib():
             "mlmc_server_counters": (I32, [P, P, P, P]),
             "mlmc_server_destroy": (None, [P]),
             "mlmc_server_last_error": (ctypes.c_char_p, [P]),
+            "mlmc_failure_estimate": (I32, [P, I64, D, I32, I32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -391,3 +392,24 @@ def mlmc_server_last_error(srv):
 
 def mlmc_server_destroy(srv):
     lib().mlmc_server_destroy(srv)
+
+
+def mlmc_failure_estimate(results, threshold, k=1, two_level=False):
+    """(estimate, mean[16], var[16]) from result dicts of mlmc_server_poll."""
+    arr = (mlmc_result * max(1, len(results)))()
+    for i, r in enumerate(results):
+        a = arr[i]
+        a.tag, a.kind, a.level, a.mesh_level, a.sample_id = r["tag"], r["kind"], r["level"], r["mesh_level"], r["sample_id"]
+        a.status, a.stop_level = r["status"], r["stop_level"]
+        for j, v in enumerate(r["lambdas"]):
+            a.lambda_[j] = v
+        a.lambda_fine, a.lambda_coarse, a.q_fine, a.q_coarse = r["lambda_fine"], r["lambda_coarse"], r["q_fine"], r["q_coarse"]
+    est = ctypes.c_double()
+    mean = (ctypes.c_double * SR_MAX_LEVELS)()
+    var = (ctypes.c_double * SR_MAX_LEVELS)()
+    st = lib().mlmc_failure_estimate(ctypes.cast(arr, ctypes.c_void_p), len(results), float(threshold), int(k),
+                                     1 if two_level else 0, ctypes.byref(est), ctypes.cast(mean, ctypes.c_void_p),
+                                     ctypes.cast(var, ctypes.c_void_p))
+    if st != 0:
+        raise MLMCError(st, "mlmc_failure_estimate")
+    return est.value, list(mean), list(var)

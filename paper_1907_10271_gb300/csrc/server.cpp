@@ -296,6 +296,47 @@ void mlmc_server_destroy(mlmc_server* s) {
   delete s;
 }
 
+mlmc_status mlmc_failure_estimate(const mlmc_result* res, int64_t n, double threshold, int32_t k,
+                                  int32_t two_level, double* estimate, double* mean, double* var) {
+  if (n < 0 || (n > 0 && !res) || k < 0 || !estimate) return MLMC_ERR_INVALID_ARG;
+  int64_t cnt[MLMC_SR_MAX_LEVELS] = {0}, plus[MLMC_SR_MAX_LEVELS] = {0}, minus[MLMC_SR_MAX_LEVELS] = {0};
+  int top = -1;
+  for (int64_t i = 0; i < n; ++i)
+    if (res[i].status == 0 && res[i].kind == MLMC_REQ_SELECTIVE) top = std::max(top, (int)res[i].level);
+  for (int64_t i = 0; i < n; ++i) {
+    const mlmc_result& r = res[i];
+    if (r.status != 0 || r.kind != MLMC_REQ_SELECTIVE || r.level < 0 || r.level >= MLMC_SR_MAX_LEVELS) continue;
+    int y;
+    if (r.level == 0) {
+      y = r.q_fine;
+    } else if (!two_level) {
+      y = r.q_fine - r.q_coarse;
+    } else if (r.level == top) {
+      y = r.q_fine - (r.lambda[0] > threshold ? 1 : 0);
+    } else {
+      continue;   // intermediate levels take no part in the two-level form
+    }
+    ++cnt[r.level];
+    plus[r.level] += y == 1;
+    minus[r.level] += y == -1;
+  }
+  double est = 0.0;
+  for (int l = 0; l < MLMC_SR_MAX_LEVELS; ++l) {
+    double e = 0.0, v = 0.0;
+    if (cnt[l] > 0) {
+      const double pp = (double)(plus[l] + k) / (double)(cnt[l] + k);
+      const double pm = l == 0 ? 0.0 : (double)(minus[l] + k) / (double)(cnt[l] + k);
+      e = pp - pm;
+      v = pp + pm - e * e;
+      est += e;
+    }
+    if (mean) mean[l] = e;
+    if (var) var[l] = v;
+  }
+  *estimate = est;
+  return MLMC_OK;
+}
+
 const char* mlmc_server_last_error(const mlmc_server* s) { return s ? s->err : g_server_error.c_str(); }
 
 }  // extern "C"

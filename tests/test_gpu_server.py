@@ -157,3 +157,25 @@ def test_admission_by_memory_budget(B):
     assert all(res[k]["status"] == 0 for k in range(40))
     assert 0 < counters["peak_bytes"] <= 2 * 20e6
     assert counters["batches"] >= 4     # a 256 x 64 solve needs ~3.5 MB: the share splits the load
+
+
+@pytest.mark.parametrize("k", [0, 1, 3])
+@pytest.mark.parametrize("two_level", [False, True])
+def test_failure_estimate_matches_the_oracle(B, k, two_level):
+    # host arithmetic of the library on synthetic selective-refinement results
+    g = np.random.default_rng(7 + k)
+    n, thr = 2500, 1.0
+    lv = g.integers(0, 4, n)
+    lam0 = g.normal(0.0, 1.0, n) + 0.5
+    qm0 = (lam0 > thr).astype(int)
+    qf = np.where(g.random(n) < 0.1, 1 - qm0, qm0)
+    qc = np.where(lv == 0, 0, np.where(g.random(n) < 0.05, 1 - qf, qf))
+    res = [dict(tag=i, kind=SEL, level=int(lv[i]), mesh_level=0, sample_id=i, status=0, stop_level=0,
+                lambdas=[float(lam0[i])], lambda_fine=0.0, lambda_coarse=0.0, q_fine=int(qf[i]), q_coarse=int(qc[i]))
+           for i in range(n)]
+    est, mean, var = B.mlmc_failure_estimate(res, thr, k=k, two_level=two_level)
+    ref, terms = om.failure_estimate(lv, qf, qc, qm0, k=k, two_level=two_level)
+    assert est == pytest.approx(ref, rel=1e-13, abs=1e-15)
+    for l, (m, v) in terms.items():
+        assert mean[l] == pytest.approx(m, rel=1e-13, abs=1e-15)
+        assert var[l] == pytest.approx(v, rel=1e-13, abs=1e-15)

@@ -90,3 +90,26 @@ def test_upper_quantile_order_statistic():
     q = om.upper_quantile(v, 1.0 / 150.0)
     assert q == math.ceil(4096 * (1 - 1 / 150))
     assert np.sum(v > q) == 4096 - math.ceil(4096 * (1 - 1 / 150))
+
+
+def synthetic_results(seed=5, n=3000, levels=4, p=0.05):
+    g = np.random.default_rng(seed)
+    lv = g.integers(0, levels, n)
+    qm0 = (g.random(n) < p).astype(int)
+    qf = np.where(g.random(n) < 0.1, 1 - qm0, qm0)
+    qc = np.where(g.random(n) < 0.05, 1 - qf, qf)
+    qc[lv == 0] = 0
+    return lv, qf, qc, qm0
+
+
+def test_failure_estimate_plain_means_at_k0():
+    lv, qf, qc, qm0 = synthetic_results()
+    est, terms = om.failure_estimate(lv, qf, qc, qm0, k=0)
+    plain = sum(float(np.mean(np.where(lv[lv == l] == 0, qf[lv == l], qf[lv == l] - qc[lv == l])))
+                for l in range(4))
+    assert est == pytest.approx(plain, abs=1e-15)
+    est2, terms2 = om.failure_estimate(lv, qf, qc, qm0, k=0, two_level=True)
+    top = lv.max()
+    assert est2 == pytest.approx(float(np.mean(qf[lv == 0])) + float(np.mean(qf[lv == top] - qm0[lv == top])),
+                                 abs=1e-15)
+    assert sorted(terms2) == [0, top]
