@@ -277,7 +277,10 @@ def run_gpu(a):
     counts = list(cfg["n_per_level"])
     levels = list(range(cfg["levels"]))
     total = sum(counts)
-    stream = torch.cuda.current_stream()
+    # a stream of its own (the legacy default stream cannot hold the library's
+    # captured CUDA graphs); every event below is recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx = B.mlmc_create(B.config_from_workload(cfg), stream.cuda_stream)
     qf = torch.empty(2 * total, dtype=torch.float64, device="cuda")
     qc = torch.empty_like(qf)

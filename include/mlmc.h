@@ -23,7 +23,9 @@
  * Memory. Every array argument is caller-owned and may be host memory or device
  * memory of the context's GPU (the library checks with cudaPointerGetAttributes
  * and copies as needed). Device work is issued on the stream given to
- * mlmc_create; calls return after that stream has finished the call's work.
+ * mlmc_create; calls return after that stream has finished the call's work. On a
+ * stream other than the legacy default stream the multigrid-PCG iterations are
+ * captured once per solve into a CUDA graph and replayed (fewer launch gaps).
  * The context owns its device workspace, the KL bases and the mesh hierarchy.
  *
  * Errors. Every call returns an mlmc_status; none aborts. On failure

@@ -359,6 +359,8 @@ mlmc_status reserve_workspace(mlmc_ctx* h, size_t solve_bytes, size_t batch_byte
   return MLMC_OK;
 }
 
+void set_graph_replay(mlmc_ctx* h, bool on) { h->c.graphs = on; }
+
 double solve_bytes_per_sample(const mlmc_config& cfg, int mesh) {
   const double tb = cfg.precision == MLMC_PREC_MIXED ? 4.0 : 8.0;
   const double nx = (double)((int64_t)cfg.nx0 << mesh), ny = (double)((int64_t)cfg.ny0 << mesh);

@@ -127,6 +127,7 @@ struct Context {
   KernelTimer timer;
   double floor_tol32 = 3e-6;      // tightest inner relative tolerance of the FP32 solve
   int check_every = 4;            // PCG iterations between host convergence checks
+  bool graphs = true;             // replay PCG batches from a CUDA graph captured per solve
   int last_outer = 0;             // refinement steps of the last solve (diagnostic)
   int last_iters = 0;             // max PCG iterations of the last solve (diagnostic)
 

@@ -61,6 +61,11 @@ mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* tri
 // that later calls within them allocate nothing (cudaFree synchronises the device).
 mlmc_status reserve_workspace(mlmc_ctx* h, size_t solve_bytes, size_t batch_bytes);
 
+// Whether solves of this context replay their PCG batches from captured CUDA graphs
+// (on by default). A capture and instantiation per solve pays off over a few replays
+// of a fixed batch; a request loop whose every batch differs turns it off.
+void set_graph_replay(mlmc_ctx* h, bool on);
+
 // Device bytes one solve on `mesh` needs in a batch (solver workspace, field and
 // outputs), with margin.
 double solve_bytes_per_sample(const mlmc_config& cfg, int mesh);

@@ -1401,10 +1401,13 @@ __global__ void k_inner_end(SampleState S, int total, int recursive) {
 
 // ---------------------------------------------------------------- per-sample scalars
 
-__global__ void k_after_post(SampleState S, int total, int iter) {
+// slot: the iteration's position in its batch (batches start at even iterations, so
+// slot and iteration have the same parity); count[slot] receives the samples still
+// active after it.
+__global__ void k_after_post(SampleState S, int total, int slot) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total || !S.active[t]) return;
-  S.rpar[t] = (iter + 1) & 1;   // PreTop of this iteration wrote r' to buffer (iter + 1) & 1
+  S.rpar[t] = (slot + 1) & 1;   // PreTop of this iteration wrote r' to buffer (iteration + 1) & 1
   const double rr = S.red_rr[t];
   if (rr <= S.tol2[t] * S.rr_ref[t]) {
     S.active[t] = 0;
@@ -1421,7 +1424,7 @@ __global__ void k_after_post(SampleState S, int total, int iter) {
   S.rz_old[t] = rz;
   S.red_pq[t] = 0.0;
   S.iters[t] += 1;
-  atomicAdd(&S.count[iter], 1);
+  atomicAdd(&S.count[slot], 1);
 }
 
 __global__ void k_after_p(SampleState S, int total) {
@@ -1588,8 +1591,8 @@ cudaError_t launch_inner_end(SampleState S, int total, int recursive, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_after_post(SampleState S, int total, int iter, cudaStream_t st) {
-  k_after_post<<<blocks_for(total, 256), 256, 0, st>>>(S, total, iter);
+cudaError_t launch_after_post(SampleState S, int total, int slot, cudaStream_t st) {
+  k_after_post<<<blocks_for(total, 256), 256, 0, st>>>(S, total, slot);
   return cudaGetLastError();
 }
 

@@ -65,7 +65,7 @@ struct SampleState {
   int* outer_active;  // refinement running
   int* iters;         // PCG iterations (all refinement steps)
   int* status;        // 0 ok, MLMC_ERR_NOT_CONVERGED
-  int* count;         // [max_iter] active samples after each iteration
+  int* count;         // [batch] active samples after each iteration of the current batch
   int* rpar;          // buffer (0/1) holding the latest inner residual
   unsigned long long* units;   // [kProfOps] nodes processed per operation (null: not counted)
 };
@@ -125,7 +125,7 @@ cudaError_t launch_react_delta(const ViewList<T>& L, SampleState S, int total_th
 // PCG's last reduced ||r||^2.
 cudaError_t launch_inner_end(SampleState S, int total, int recursive, cudaStream_t st);
 
-cudaError_t launch_after_post(SampleState S, int total, int iter, cudaStream_t st);
+cudaError_t launch_after_post(SampleState S, int total, int slot, cudaStream_t st);
 cudaError_t launch_after_p(SampleState S, int total, cudaStream_t st);
 cudaError_t launch_outer_init(SampleState S, int total, cudaStream_t st);
 cudaError_t launch_outer_check(SampleState S, int total, double rtol, double floor_tol, int* outer_count,

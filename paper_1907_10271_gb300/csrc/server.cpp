@@ -214,6 +214,7 @@ mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config*
       return e;
     }
     s->ctx.push_back(c);
+    mlmc::set_graph_replay(c, false);   // every batch differs: no graph to reuse
     // the share, split like the footprint estimate: solver workspace and batch buffers
     e = mlmc::reserve_workspace(c, (size_t)(0.85 * s->share), (size_t)(0.15 * s->share));
     if (e != MLMC_OK) {

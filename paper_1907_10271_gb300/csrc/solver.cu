@@ -201,7 +201,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     alloc.template vec<int>(S.outer_active, total);
     alloc.template vec<int>(S.iters, total);
     alloc.template vec<int>(S.status, total);
-    alloc.template vec<int>(S.count, (size_t)max_iter + 1);
+    alloc.template vec<int>(S.count, (size_t)std::max(ctx.check_every, 1));
     alloc.template vec<int>(S.rpar, total);
     alloc.template vec<int>(outer_count, 1);
   };
@@ -311,7 +311,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   // each group's finest mesh, so the finest-level kernels (the largest) are single
   // launches over all groups; a group's coarse levels join the launches of their depth,
   // and all coarsest solves share one launch between the down and up sweeps.
-  auto run_vcycle_and_pcg = [&](int parity, int iter) -> mlmc_status {
+  auto run_vcycle_and_pcg = [&](int parity, int slot) -> mlmc_status {
     // down sweep: depth d gathers its right-hand side from depth d - 1 (full weighting),
     // smooths and forms its residual; depth 0 updates the PCG iterate first
     for (int d = 0; d < dmax; ++d) {
@@ -393,7 +393,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         MLMC_LAUNCH(kProfPost, "post", launch_strip<T>(StripOp::Post, L, S, tw, st));
       }
     }
-    MLMC_LAUNCH(kProfOther, "after_post", launch_after_post(S, total, iter, st));
+    MLMC_LAUNCH(kProfOther, "after_post", launch_after_post(S, total, slot, st));
     {
       ViewList<T> L = top_list(StripOp::PcgP, parity);
       const int tw = finalize_warps(L, StripOp::PcgP);
@@ -468,6 +468,48 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   mlmc_status rs = MLMC_OK;
   MLMC_LAUNCH(kProfOther, "outer_init", launch_outer_init(S, total, st));
 
+  // PCG iterations run in batches of check_every (even) between host convergence
+  // checks. A full batch is captured once per solve into a CUDA graph and replayed: its
+  // launches depend on the iteration only through the parity of the residual buffers
+  // and the slot of the active-sample counter, both fixed within a batch that starts
+  // at an even iteration. The kernel timer, which records events around each launch,
+  // runs the same launches directly, and so does the legacy default stream, which
+  // cannot be captured.
+  cudaGraphExec_t batch_graph = nullptr;
+  struct GraphGuard {
+    cudaGraphExec_t* g;
+    ~GraphGuard() {
+      if (*g) cudaGraphExecDestroy(*g);
+    }
+  } graph_guard{&batch_graph};
+  int64_t graph_launches = 0;
+  const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+  const bool graphs = ctx.graphs && capturable && !ctx.timer.on && ctx.check_every % 2 == 0;
+  auto capture_batch = [&]() -> mlmc_status {
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return ctx.cuda_fail(ce, "graph capture");
+    const int64_t l0 = ctx.timer.launches;
+    mlmc_status cs = MLMC_OK;
+    ce = cudaMemsetAsync(S.count, 0, sizeof(int) * ctx.check_every, st);
+    for (int b = 0; b < ctx.check_every && cs == MLMC_OK && ce == cudaSuccess; ++b) cs = run_vcycle_and_pcg(b & 1, b);
+    const cudaError_t ee = cudaStreamEndCapture(st, &g);
+    if (cs != MLMC_OK || ce != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return cs != MLMC_OK ? cs : ctx.cuda_fail(ce != cudaSuccess ? ce : ee, "graph capture");
+    }
+    graph_launches = ctx.timer.launches - l0;
+    ctx.timer.launches = l0;   // counted again at every replay
+    ce = cudaGraphInstantiate(&batch_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      batch_graph = nullptr;
+      return ctx.cuda_fail(ce, "graph instantiate");
+    }
+    return MLMC_OK;
+  };
+
   const double floor_tol = inner_double ? 1e-14 : ctx.floor_tol32;
   int outer = 0, max_it_seen = 0;
   for (;; ++outer) {
@@ -500,16 +542,27 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
           (e = cudaMemsetAsync(g.q, 0, bytes, st)) != cudaSuccess)
         return ctx.cuda_fail(e, "memset");
     }
-    if ((e = cudaMemsetAsync(S.count, 0, sizeof(int) * (max_iter + 1), st)) != cudaSuccess) return ctx.cuda_fail(e, "memset");
     int it = 0;
     while (it < max_iter) {
       const int batch = std::min(ctx.check_every, max_iter - it);
-      for (int b = 0; b < batch; ++b, ++it) {
-        mlmc_status s2 = run_vcycle_and_pcg(it & 1, it);
-        if (s2 != MLMC_OK) return s2;
+      if (graphs && batch == ctx.check_every) {
+        if (!batch_graph) {
+          const mlmc_status cs = capture_batch();
+          if (cs != MLMC_OK) return cs;
+        }
+        if ((e = cudaGraphLaunch(batch_graph, st)) != cudaSuccess) return ctx.cuda_fail(e, "graph launch");
+        ctx.timer.launches += graph_launches;
+        it += batch;
+      } else {
+        if ((e = cudaMemsetAsync(S.count, 0, sizeof(int) * batch, st)) != cudaSuccess)
+          return ctx.cuda_fail(e, "memset");
+        for (int b = 0; b < batch; ++b, ++it) {
+          mlmc_status s2 = run_vcycle_and_pcg(it & 1, b);
+          if (s2 != MLMC_OK) return s2;
+        }
       }
       int h_count = 0;
-      if ((e = cudaMemcpyAsync(&h_count, S.count + (it - 1), sizeof(int), cudaMemcpyDeviceToHost, st)) !=
+      if ((e = cudaMemcpyAsync(&h_count, S.count + (batch - 1), sizeof(int), cudaMemcpyDeviceToHost, st)) !=
               cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return ctx.cuda_fail(e, "pcg_count");

@@ -281,3 +281,26 @@ def test_non_converged_samples_are_excluded(B):
         assert B.mlmc_level_stats_get(ctx, 1)["n"] == 0
     finally:
         B.mlmc_destroy(ctx)
+
+
+def test_graph_replay_equals_direct_launches(B):
+    """PCG batches replayed from a captured CUDA graph give the results of the same
+    launches issued directly (the kernel timer forces direct launches); only the
+    order in which warps add their partial dot products may differ."""
+    import torch
+    w = STRIP_MIXED_5LEVEL
+    side = torch.cuda.Stream()   # capturable (the legacy default stream is not)
+    ctx = B.mlmc_create(B.config_from_workload(w), side.cuda_stream)
+    try:
+        out = []
+        for timer in (False, True):
+            B.mlmc_profile_enable(ctx, timer)
+            qf = np.zeros(2 * 40)
+            qc = np.zeros(2 * 40)
+            B.mlmc_sample_levels(ctx, [1, 2], [300, 300], [32, 8], qf, qc)
+            out.append((qf.copy(), qc.copy()))
+        B.mlmc_profile_enable(ctx, False)
+        np.testing.assert_allclose(out[0][0], out[1][0], rtol=1e-12)
+        np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-12)
+    finally:
+        B.mlmc_destroy(ctx)
