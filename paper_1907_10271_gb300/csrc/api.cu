@@ -130,8 +130,7 @@ struct ReqBuffers {
   double* xi;
   float* xi32;
   float* xi_tc;   // TF32 split of xi: hi [n][kp] then lo [n][kp] (tensor-core synthesis)
-  void* theta_f;
-  void* theta_c;
+  void* theta_f;   // the field of the phase being solved (sized for the finest mesh)
   double* qf;
   double* qc;
   int* st_f;
@@ -148,36 +147,47 @@ double bytes_per_sample(const Context& c, int level) {
   return (dofs(level) + dofs(level - 1)) * (14.0 * tb + 16.0) * 1.4 + 64.0 * c.cfg.kl_terms + 256.0;
 }
 
-// One lock-stepped solve of every level pair in `reqs`: xi per level, theta on the
-// fine and coarse meshes from the same xi, all fine and coarse groups solved together,
-// then the per-level moments and the outputs.
+// Every level pair in `reqs`, solved by nested iteration along each sample's mesh
+// chain: phase j solves, in one lock-stepped multigrid-PCG, every sample whose level
+// is at least j on mesh j (its field synthesised on mesh j from its own xi), starting
+// from its phase j-1 solution prolongated to mesh j (phase 0 from the lifting). The
+// sample's level-l pair takes Q_l from phase l and Q_{l-1} from phase l-1; the
+// phases below l-1 only provide starting iterates, at a small fraction of the
+// cost. Each solve still reaches ||f - K d|| <= rtol ||f|| on its own mesh. Then the
+// per-level moments and the outputs.
 template <typename T>
 mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, double* q_fine, double* q_coarse,
                                int32_t* status) {
   Context& c = h->c;
   cudaStream_t st = c.stream;
   const int nkl = c.cfg.kl_terms;
-  int64_t total = 0;
+  const bool tc = c.kl_on_tensor_cores();
   mlmc::Sizer sz;
-  for (const auto& r : reqs) {
-    total += r.n;
-  }
+  int top = 0;
+  for (const auto& r : reqs) top = std::max(top, r.level);
   std::vector<ReqBuffers> B(reqs.size());
+  std::vector<double*> dA(reqs.size()), dB(reqs.size());   // iterates of alternate phases
+  std::vector<double*> qs(reqs.size());                    // QoI of phases below l - 1 (unused)
+  std::vector<int*> ss(reqs.size()), is(reqs.size());
   auto plan = [&](auto& alloc) {
     for (size_t k = 0; k < reqs.size(); ++k) {
       const LevelReq& r = reqs[k];
-      const int64_t nel_f = c.mesh(r.level).n_el(), nel_c = r.level > 0 ? c.mesh(r.level - 1).n_el() : 1;
+      const int64_t nel = c.mesh(r.level).n_el(), dofs = 2 * c.mesh(r.level).n_nodes();
       alloc(B[k].xi, r.n * nkl);
-      alloc(B[k].xi32, c.kl_on_tensor_cores() ? 1 : r.n * nkl);
-      alloc(B[k].xi_tc, c.kl_on_tensor_cores() ? 2 * r.n * c.kl_kpad() : 1);
-      alloc(reinterpret_cast<T*&>(B[k].theta_f), 2 * r.n * nel_f);
-      alloc(reinterpret_cast<T*&>(B[k].theta_c), 2 * r.n * nel_c);
+      alloc(B[k].xi32, c.mixed() && !tc ? r.n * nkl : 1);
+      alloc(B[k].xi_tc, tc ? 2 * r.n * c.kl_kpad() : 1);
+      alloc(reinterpret_cast<T*&>(B[k].theta_f), 2 * r.n * nel);
+      alloc(dA[k], r.level > 0 ? r.n * dofs : 1);
+      alloc(dB[k], r.level > 1 ? r.n * dofs : 1);
       alloc(B[k].qf, 2 * r.n);
       alloc(B[k].qc, 2 * r.n);
+      alloc(qs[k], 2 * r.n);
       alloc(B[k].st_f, r.n);
       alloc(B[k].st_c, r.n);
+      alloc(ss[k], r.n);
       alloc(B[k].it_f, r.n);
       alloc(B[k].it_c, r.n);
+      alloc(is[k], r.n);
       alloc(B[k].status, r.n);
     }
   };
@@ -199,50 +209,60 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
     fail = c.batch_arena.carve<int>(2);   // [0] normal generator cap, [1] tensor-core synthesis wait
   }
   if ((e = cudaMemsetAsync(fail, 0, 2 * sizeof(int), st)) != cudaSuccess) return c.cuda_fail(e, "memset");
-  std::vector<mlmc::SolveGroup<T>> groups;
+  // KL coefficients once per request, shared by all of its meshes
+  std::vector<mlmc::KlTcOperand> xop(reqs.size());
   for (size_t k = 0; k < reqs.size(); ++k) {
     const LevelReq& r = reqs[k];
     c.timer.begin(mlmc::kProfOther, st, "kl_coefficients");
-    const bool tc = c.kl_on_tensor_cores();
     e = mlmc::launch_kl_coefficients(c.cfg.seed, r.level, r.first_id, nullptr, nullptr, r.n, nkl, B[k].xi,
                                      c.mixed() && !tc ? B[k].xi32 : nullptr, fail, st);
     c.timer.end(st);
     if (e != cudaSuccess) return c.cuda_fail(e, "kl_coefficients");
-    mlmc::KlTcOperand xop;
     if (tc) {
       const int kp = c.kl_kpad();
       c.timer.begin(mlmc::kProfOther, st, "kl_split");
       e = mlmc::launch_tf32_split(B[k].xi, r.n, nkl, kp, B[k].xi_tc, B[k].xi_tc + r.n * kp, st);
       c.timer.end(st);
       if (e == cudaSuccess)
-        e = mlmc::make_kl_tc_operand(B[k].xi_tc, B[k].xi_tc + r.n * kp, r.n, kp, mlmc::kKlTcSamples, &xop);
+        e = mlmc::make_kl_tc_operand(B[k].xi_tc, B[k].xi_tc + r.n * kp, r.n, kp, mlmc::kKlTcSamples, &xop[k]);
       if (e != cudaSuccess) return c.cuda_fail(e, "kl_split");
     }
-    const T* xiT = c.mixed() ? (const T*)(const void*)B[k].xi32 : (const T*)(const void*)B[k].xi;
-    for (int side = 0; side < (r.level > 0 ? 2 : 1); ++side) {
-      const int m = r.level - side;
-      const T* basis = c.mixed() ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
-      T* th = (T*)(side == 0 ? B[k].theta_f : B[k].theta_c);
+  }
+  for (int j = 0; j <= top; ++j) {
+    std::vector<mlmc::SolveGroup<T>> groups;
+    for (size_t k = 0; k < reqs.size(); ++k) {
+      const LevelReq& r = reqs[k];
+      if (r.level < j) continue;
+      T* th = (T*)B[k].theta_f;
       c.timer.begin(mlmc::kProfOther, st, "kl_synthesis");
-      if (tc)
-        e = mlmc::launch_kl_synthesis_tc(c.basis_tc_op[m], xop, (int)c.mesh(m).n_el(), r.n, (float*)(void*)th, true,
-                                         fail + 1, st);
-      else
-        e = mlmc::launch_kl_synthesis<T>(xiT, basis, r.n, (int)c.mesh(m).n_el(), nkl, th, true, st);
+      if (tc) {
+        e = mlmc::launch_kl_synthesis_tc(c.basis_tc_op[j], xop[k], (int)c.mesh(j).n_el(), r.n, (float*)(void*)th,
+                                         true, fail + 1, st);
+      } else {
+        const T* xiT = c.mixed() ? (const T*)(const void*)B[k].xi32 : (const T*)(const void*)B[k].xi;
+        const T* basis = c.mixed() ? (const T*)(const void*)c.basis32[j] : (const T*)(const void*)c.basis64[j];
+        e = mlmc::launch_kl_synthesis<T>(xiT, basis, r.n, (int)c.mesh(j).n_el(), nkl, th, true, st);
+      }
       c.timer.end(st);
       if (e != cudaSuccess) return c.cuda_fail(e, "kl_synthesis");
-      if (side == 0) groups.push_back({m, r.n, th, B[k].qf, B[k].st_f, B[k].it_f});
-      else groups.push_back({m, r.n, th, B[k].qc, B[k].st_c, B[k].it_c});
+      mlmc::SolveGroup<T> g{j, r.n, th, qs[k], ss[k], is[k]};
+      if (j == r.level) g = mlmc::SolveGroup<T>{j, r.n, th, B[k].qf, B[k].st_f, B[k].it_f};
+      if (j + 1 == r.level) g = mlmc::SolveGroup<T>{j, r.n, th, B[k].qc, B[k].st_c, B[k].it_c};
+      double* prev = (j & 1) ? dA[k] : dB[k];   // written by phase j - 1
+      double* cur = (j & 1) ? dB[k] : dA[k];
+      g.d_guess = j > 0 ? prev : nullptr;
+      g.d_out = j < r.level ? cur : nullptr;
+      groups.push_back(g);
     }
+    int h_fail[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(h_fail, fail, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return c.cuda_fail(e, "kl_coefficients");
+    if (h_fail[0]) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
+    if (h_fail[1]) return c.fail(MLMC_ERR_TIMEOUT, "tensor-core KL synthesis: a wait expired");
+    mlmc_status s = mlmc::solve_groups<T>(c, groups);
+    if (s != MLMC_OK) return s;
   }
-  int h_fail[2] = {0, 0};
-  if ((e = cudaMemcpyAsync(h_fail, fail, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(st)) != cudaSuccess)
-    return c.cuda_fail(e, "kl_coefficients");
-  if (h_fail[0]) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
-  if (h_fail[1]) return c.fail(MLMC_ERR_TIMEOUT, "tensor-core KL synthesis: a wait expired");
-  mlmc_status s = mlmc::solve_groups<T>(c, groups);
-  if (s != MLMC_OK) return s;
   for (size_t k = 0; k < reqs.size(); ++k) {
     const LevelReq& r = reqs[k];
     const int64_t nb = r.n;

@@ -47,6 +47,11 @@ struct SolveGroup {
   double* q;           // [nsamp][2] device output
   int* status;         // [nsamp] device output
   int* iters;          // [nsamp] device output (total PCG iterations)
+  // nested iteration (optional): the same samples' final iterates on mesh
+  // mesh_level - 1, prolongated as the initial iterate, and where to copy this
+  // solve's final iterates (both in the refinement iterate's storage layout)
+  const double* d_guess = nullptr;
+  double* d_out = nullptr;
 };
 
 // Solves every group to cfg.rtol (fp64 path: T = double throughout; mixed path:

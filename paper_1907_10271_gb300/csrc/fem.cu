@@ -1272,6 +1272,46 @@ __global__ void k_lift_resid(const __grid_constant__ ViewList<T> L, SampleState 
   }
 }
 
+// Initial iterate from the same sample's solution on the next coarser mesh (nested
+// iteration): bilinear prolongation of the coarse iterate, Dirichlet values included
+// (both meshes prescribe the same end values, which the prolongation reproduces).
+// ext0 = coarse d, ext1 = fine d (both DStore<TI>); view geometry = the fine mesh.
+// One thread per fine node.
+template <typename TI>
+__global__ void k_prolong_d(const __grid_constant__ ViewList<TI> L) {
+  int vi;
+  int64_t loc;
+  if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
+  const View<TI>& V = L.v[vi];
+  const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
+  const int per = nxp * (ny + 1);
+  const int s = (int)(loc / per);
+  if (s >= V.nsamp) return;
+  const int node = (int)(loc - (int64_t)s * per);
+  const int j = node / nxp, i = node - j * nxp;
+  const int nxc = nx / 2, nyc = ny / 2, I = i >> 1, J = j >> 1;
+  const bool fi = i & 1, fj = j & 1;
+  const double* dc = static_cast<const double*>(V.ext0);
+  double* df = static_cast<double*>(V.ext1);
+  const int64_t cb = (int64_t)s * 2 * (nxc + 1) * (nyc + 1);
+  auto at = [&](int II, int JJ, int comp) { return cb + 2 * ((int64_t)JJ * (nxc + 1) + II) + comp; };
+  const int64_t fo = (int64_t)s * 2 * per + 2 * (int64_t)node;
+  using D = DStore<TI>;
+#pragma unroll
+  for (int comp = 0; comp < 2; ++comp) {
+    typename D::Val v = D::get(dc, at(I, J, comp));
+    if (fi) v = v + D::get(dc, at(I + 1, J, comp));
+    if (fj) {
+      typename D::Val t = D::get(dc, at(I, J + 1, comp));
+      if (fi) t = t + D::get(dc, at(I + 1, J + 1, comp));
+      v = v + t;
+    }
+    const TI f = (fi && fj) ? (TI)0.25 : ((fi || fj) ? (TI)0.5 : (TI)1);   // powers of two: exact
+    if constexpr (sizeof(TI) == 4) D::put(df, fo + comp, DF{v.hi * f, v.lo * f});
+    else D::put(df, fo + comp, v * f);
+  }
+}
+
 // Fibre-direction compressive stress at centroids in [x0, x1]: a = d (DStore<TI>),
 // ext0 = trig2 (TI). The displacement differences that form the centroid strain are
 // taken from the stored iterate at its own accuracy (they cancel); strain, stress and
@@ -1565,6 +1605,13 @@ cudaError_t launch_lift_resid(const ViewList<T>& L, SampleState S, double shorte
 }
 
 template <typename TI>
+cudaError_t launch_prolong_d(const ViewList<TI>& L, int total_threads, cudaStream_t st) {
+  if (total_threads <= 0) return cudaSuccess;
+  k_prolong_d<TI><<<blocks_for(total_threads, 256), 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+template <typename TI>
 cudaError_t launch_stress(const ViewList<double>& L, SampleState S, int total_warps, cudaStream_t st) {
   if (total_warps <= 0) return cudaSuccess;
   k_stress<TI><<<blocks_for((int64_t)total_warps * 32, 256), 256, 0, st>>>(L, S);
@@ -1623,6 +1670,7 @@ cudaError_t launch_outer_check(SampleState S, int total, double rtol, double flo
   template cudaError_t launch_react_energy<T>(const ViewList<T>&, SampleState, double, int, cudaStream_t);  \
   template cudaError_t launch_resid64<T>(const ViewList<double>&, SampleState, int, cudaStream_t);         \
   template cudaError_t launch_lift_resid<T>(const ViewList<T>&, SampleState, double, int, cudaStream_t);  \
+  template cudaError_t launch_prolong_d<T>(const ViewList<T>&, int, cudaStream_t);                        \
   template cudaError_t launch_stress<T>(const ViewList<double>&, SampleState, int,                         \
                                         cudaStream_t);
 MLMC_INST(float)

@@ -112,6 +112,11 @@ template <typename T>
 cudaError_t launch_lift_resid(const ViewList<T>& L, SampleState S, double shortening, int total_threads,
                               cudaStream_t st);
 
+// Nested iteration: fine d (ext1) from the coarser mesh's d (ext0) by bilinear
+// prolongation; views at the fine mesh. One thread per fine node.
+template <typename TI>
+cudaError_t launch_prolong_d(const ViewList<TI>& L, int total_threads, cudaStream_t st);
+
 template <typename TI>
 cudaError_t launch_stress(const ViewList<double>& L, SampleState S, int total_warps, cudaStream_t st);
 

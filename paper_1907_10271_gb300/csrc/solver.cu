@@ -468,6 +468,34 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   mlmc_status rs = MLMC_OK;
   MLMC_LAUNCH(kProfOther, "outer_init", launch_outer_init(S, total, st));
 
+  // nested iteration: start from the same samples' solutions on the next coarser mesh
+  // (the lifting above still defines ||f||); their residual is formed exactly, and the
+  // corrections that follow are small, so every later residual is the inner CG's
+  // recursive one
+  const bool guessed = G.front().grp->d_guess != nullptr;
+  for (auto& g : G)
+    if ((g.grp->d_guess != nullptr) != guessed)
+      return ctx.fail(MLMC_ERR_INVALID_ARG, "initial iterates given for some groups of a solve only");
+  bool exact_next = !guessed;   // the next refinement residual is formed from d
+  if (guessed) {
+    ViewList<T> L = empty_list<T>(ctx);
+    std::vector<int64_t> per;
+    for (auto& g : G) {
+      View<T> v = base_view(g, 0);
+      v.ext0 = g.grp->d_guess;
+      v.ext1 = g.d;
+      L.v[L.n++] = v;
+      per.push_back((int64_t)(g.geo[0].nx + 1) * (g.geo[0].ny + 1));
+    }
+    const int tt = finalize_points(L, per);
+    MLMC_LAUNCH(kProfOther, "prolong_d", launch_prolong_d<T>(L, tt, st));
+    if ((e = cudaMemsetAsync(S.rr64, 0, sizeof(double) * total, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(S.react, 0, sizeof(double) * total, st)) != cudaSuccess)
+      return ctx.cuda_fail(e, "memset");
+    rs = resid();
+    if (rs != MLMC_OK) return rs;
+  }
+
   // PCG iterations run in batches of check_every (even) between host convergence
   // checks. A full batch is captured once per solve into a CUDA graph and replayed: its
   // launches depend on the iteration only through the parity of the residual buffers
@@ -569,7 +597,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       if (h_count == 0) break;
     }
     max_it_seen = std::max(max_it_seen, it);
-    MLMC_LAUNCH(kProfOther, "inner_end", launch_inner_end(S, total, outer > 0 ? 1 : 0, st));
+    MLMC_LAUNCH(kProfOther, "inner_end", launch_inner_end(S, total, exact_next ? 0 : 1, st));
     // d += x; after the first correction the inner CG's recursive residual (accurate
     // to unit roundoff times the correction's size) is the new refinement residual,
     // moved into r0 where it ended in r1
@@ -580,7 +608,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         View<T> v = base_view(g, 0);
         v.a = g.x;
         v.ext1 = g.d;
-        if (outer > 0) {
+        if (!exact_next) {   // this correction's recursive residual becomes the refinement residual
           v.b = g.r[1];
           v.o0 = g.r[0];
         }
@@ -590,12 +618,13 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       const int tt = finalize_points(L, per);
       MLMC_LAUNCH(kProfOther, "update_d", launch_update_d<T>(L, S, tt, st));
     }
-    if (outer == 0) {
+    if (exact_next) {
       // the one double-precision residual: f - K d after the first correction
       if ((e = cudaMemsetAsync(S.react, 0, sizeof(double) * total, st)) != cudaSuccess)
         return ctx.cuda_fail(e, "memset");
       rs = resid();
       if (rs != MLMC_OK) return rs;
+      exact_next = false;
     } else {
       ViewList<T> R = empty_list<T>(ctx);
       std::vector<int64_t> rows;
@@ -658,6 +687,10 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   }
   for (auto& g : G) {
     const SolveGroup<T>& sg = *g.grp;
+    if (sg.d_out &&
+        (e = cudaMemcpyAsync(sg.d_out, g.d, sizeof(double) * sg.nsamp * 2 * (g.geo[0].nx + 1) * (g.geo[0].ny + 1),
+                             cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return ctx.cuda_fail(e, "copy d");
     if ((e = cudaMemcpyAsync(sg.q, S.qoi + 2 * (size_t)g.sbase, sizeof(double) * 2 * sg.nsamp,
                              cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
       return ctx.cuda_fail(e, "copy q");

@@ -161,7 +161,13 @@ def test_full_size_launch_sampled_outputs(B):
 
 
 def test_sample_levels_matches_single_level_calls_and_solve_batch(B):
-    """Same xi on both meshes of a pair; results independent of batch composition."""
+    """Same xi on both meshes of a pair; results independent of batch composition.
+
+    mlmc_sample_level(s) solve each sample's meshes by nested iteration (each mesh
+    starts from the next coarser one's solution), mlmc_solve_batch from the lifting:
+    both end at ||f - K d|| <= 1e-8 ||f||, from different starting iterates, so they
+    agree to the solver's accuracy on the quantities (the stated 1e-6), while calls
+    running the same procedure agree to rounding."""
     w = STRIP_MIXED_5LEVEL
     ctx = B.mlmc_create(B.config_from_workload(w))
     try:
@@ -191,10 +197,10 @@ def test_sample_levels_matches_single_level_calls_and_solve_batch(B):
         off = 0
         for level, n in zip([0, 1, 2], counts):
             for j in range(n):
-                np.testing.assert_allclose(qb[2 * k:2 * k + 2], qf[2 * (off + j):2 * (off + j) + 2], rtol=1e-8)
+                np.testing.assert_allclose(qb[2 * k:2 * k + 2], qf[2 * (off + j):2 * (off + j) + 2], rtol=1e-6)
                 k += 1
                 if level > 0:
-                    np.testing.assert_allclose(qb[2 * k:2 * k + 2], qc[2 * (off + j):2 * (off + j) + 2], rtol=1e-8)
+                    np.testing.assert_allclose(qb[2 * k:2 * k + 2], qc[2 * (off + j):2 * (off + j) + 2], rtol=1e-6)
                     k += 1
             off += n
     finally:
@@ -216,10 +222,11 @@ def test_telescoping_on_identical_samples(B):
         tel = Q[0].mean(0) + (Q[1] - Q[0]).mean(0) + (Q[2] - Q[1]).mean(0)
         np.testing.assert_allclose(tel, Q[2].mean(0), rtol=1e-14)
         # and the coarse solve inside a level-2 pair equals the mesh-1 solve of the same xi
+        # (nested iteration vs a solve from the lifting: equal to the double path's 1e-9)
         qf, qc = np.zeros(2 * len(ids)), np.zeros(2 * len(ids))
         B.mlmc_sample_level(ctx, 2, 0, len(ids), qf, qc)
-        np.testing.assert_allclose(qc.reshape(-1, 2), Q[1], rtol=1e-10)
-        np.testing.assert_allclose(qf.reshape(-1, 2), Q[2], rtol=1e-10)
+        np.testing.assert_allclose(qc.reshape(-1, 2), Q[1], rtol=1e-9)
+        np.testing.assert_allclose(qf.reshape(-1, 2), Q[2], rtol=1e-9)
     finally:
         B.mlmc_destroy(ctx)
 
