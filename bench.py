@@ -556,12 +556,13 @@ def run_serving(B, cfg_w, seconds=3.0, load=0.5):
 
 
 def run_small_case():
-    """One call of the workload with 1/8 of each level's samples, after one warm call:
-    a short, bounded command for kernel captures (about 1.3 GB of device memory)."""
+    """One call of the workload with 1/4 of each level's samples, after one warm call:
+    a short, bounded command for kernel captures (about 3 M nodes per nested-iteration
+    phase, above the L2 size in bytes; under 3 GB of device memory)."""
     import torch
     from paper_1907_10271_gb300 import binding as B
     cfg = STRIP_MIXED_5LEVEL
-    counts = [n // 8 for n in cfg["n_per_level"]]
+    counts = [n // 4 for n in cfg["n_per_level"]]
     total = sum(counts)
     ctx = B.mlmc_create(B.config_from_workload(cfg), torch.cuda.current_stream().cuda_stream)
     qf = torch.zeros(2 * total, dtype=torch.float64, device="cuda")

@@ -125,6 +125,16 @@ const char* mlmc_last_error(const mlmc_ctx* ctx);
 mlmc_status mlmc_sample_level(mlmc_ctx* ctx, int32_t level, uint64_t first_id, int64_t n,
                               double* q_fine, double* q_coarse, int32_t* status);
 
+/* Level-pair calls (mlmc_sample_level(s), mlmc_estimate) whose samples' finest
+   meshes hold at least min_nodes nodes in total solve by nested iteration along
+   each sample's mesh chain: mesh j starts from the sample's mesh j-1 solution,
+   prolongated (Sec. 2.3: the meshes of a level pair are nested). Smaller calls,
+   whose per-mesh launches would not fill the GPU, solve the fine and coarse mesh
+   of every pair in one lock-stepped batch from the lifting. Both reach the same
+   residual tolerance rtol. Default 4,194,304; 0 = always nested.
+   Errors: MLMC_ERR_INVALID_ARG for min_nodes < 0. */
+mlmc_status mlmc_set_nested_threshold(mlmc_ctx* ctx, int64_t min_nodes);
+
 /* Several level pairs in one call: request k asks for counts[k] samples of level
    levels[k] with ids first_ids[k] ..; levels, first_ids and counts are HOST arrays
    of n_req entries, each level at most once per call is solved in one lock-stepped

@@ -113,6 +113,7 @@ def lib():
             "mlmc_apply": (I32, [P, I32, I64, P, P, P]),
             "mlmc_solve_theta": (I32, [P, I32, I64, P, P, P, P]),
             "mlmc_sample_levels": (I32, [P, I32, P, P, P, P, P, P]),
+            "mlmc_set_nested_threshold": (I32, [P, I64]),
             "mlmc_profile_enable": (I32, [P, I32]),
             "mlmc_profile_get": (I32, [P, I32, P, P, P]),
             "mlmc_launch_count": (I32, [P, P]),
@@ -281,6 +282,10 @@ def mlmc_sample_levels(ctx, levels, first_ids, counts, q_fine=None, q_coarse=Non
 
 PROFILE_OPS = ["pcg_update_presmooth", "presmooth", "postsmooth", "postsmooth_top", "search_direction",
                "refinement_residual", "coarsest", "other"]
+
+
+def mlmc_set_nested_threshold(ctx, min_nodes):
+    return _check(ctx, lib().mlmc_set_nested_threshold(ctx, int(min_nodes)))
 
 
 def mlmc_profile_enable(ctx, on=True):

@@ -130,7 +130,8 @@ struct ReqBuffers {
   double* xi;
   float* xi32;
   float* xi_tc;   // TF32 split of xi: hi [n][kp] then lo [n][kp] (tensor-core synthesis)
-  void* theta_f;   // the field of the phase being solved (sized for the finest mesh)
+  void* theta_f;   // the field on the finest mesh (nested: of the phase being solved)
+  void* theta_c;   // the field on the coarse mesh (single lock-stepped solve only)
   double* qf;
   double* qc;
   int* st_f;
@@ -147,14 +148,17 @@ double bytes_per_sample(const Context& c, int level) {
   return (dofs(level) + dofs(level - 1)) * (14.0 * tb + 16.0) * 1.4 + 64.0 * c.cfg.kl_terms + 256.0;
 }
 
-// Every level pair in `reqs`, solved by nested iteration along each sample's mesh
-// chain: phase j solves, in one lock-stepped multigrid-PCG, every sample whose level
-// is at least j on mesh j (its field synthesised on mesh j from its own xi), starting
-// from its phase j-1 solution prolongated to mesh j (phase 0 from the lifting). The
-// sample's level-l pair takes Q_l from phase l and Q_{l-1} from phase l-1; the
-// phases below l-1 only provide starting iterates, at a small fraction of the
-// cost. Each solve still reaches ||f - K d|| <= rtol ||f|| on its own mesh. Then the
-// per-level moments and the outputs.
+// Every level pair in `reqs`. Large calls are solved by nested iteration along each
+// sample's mesh chain: phase j solves, in one lock-stepped multigrid-PCG, every sample
+// whose level is at least j on mesh j (its field synthesised on mesh j from its own
+// xi), starting from its phase j-1 solution prolongated to mesh j (phase 0 from the
+// lifting). The sample's level-l pair takes Q_l from phase l and Q_{l-1} from phase
+// l-1; the phases below l-1 only provide starting iterates, at a small fraction of
+// the cost. Small calls solve the fine and coarse meshes of every pair together in
+// one lock-stepped solve from the lifting (below Context::nested_min_nodes finest-mesh
+// nodes the launches of a phase are too small to fill the GPU, and the sequence of
+// phases costs more latency than their fewer iterations save). Either way each solve reaches
+// ||f - K d|| <= rtol ||f|| on its own mesh. Then the per-level moments and outputs.
 template <typename T>
 mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, double* q_fine, double* q_coarse,
                                int32_t* status) {
@@ -164,7 +168,12 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
   const bool tc = c.kl_on_tensor_cores();
   mlmc::Sizer sz;
   int top = 0;
-  for (const auto& r : reqs) top = std::max(top, r.level);
+  int64_t fine_nodes = 0;
+  for (const auto& r : reqs) {
+    top = std::max(top, r.level);
+    fine_nodes += r.n * c.mesh(r.level).n_nodes();
+  }
+  const bool nested = fine_nodes >= c.nested_min_nodes;
   std::vector<ReqBuffers> B(reqs.size());
   std::vector<double*> dA(reqs.size()), dB(reqs.size());   // iterates of alternate phases
   std::vector<double*> qs(reqs.size());                    // QoI of phases below l - 1 (unused)
@@ -177,8 +186,9 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
       alloc(B[k].xi32, c.mixed() && !tc ? r.n * nkl : 1);
       alloc(B[k].xi_tc, tc ? 2 * r.n * c.kl_kpad() : 1);
       alloc(reinterpret_cast<T*&>(B[k].theta_f), 2 * r.n * nel);
-      alloc(dA[k], r.level > 0 ? r.n * dofs : 1);
-      alloc(dB[k], r.level > 1 ? r.n * dofs : 1);
+      alloc(reinterpret_cast<T*&>(B[k].theta_c), !nested && r.level > 0 ? 2 * r.n * c.mesh(r.level - 1).n_el() : 1);
+      alloc(dA[k], nested && r.level > 0 ? r.n * dofs : 1);
+      alloc(dB[k], nested && r.level > 1 ? r.n * dofs : 1);
       alloc(B[k].qf, 2 * r.n);
       alloc(B[k].qc, 2 * r.n);
       alloc(qs[k], 2 * r.n);
@@ -228,23 +238,53 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
       if (e != cudaSuccess) return c.cuda_fail(e, "kl_split");
     }
   }
-  for (int j = 0; j <= top; ++j) {
+  auto synthesize = [&](size_t k, int m, T* th) -> cudaError_t {
+    const LevelReq& r = reqs[k];
+    c.timer.begin(mlmc::kProfOther, st, "kl_synthesis");
+    cudaError_t err;
+    if (tc) {
+      err = mlmc::launch_kl_synthesis_tc(c.basis_tc_op[m], xop[k], (int)c.mesh(m).n_el(), r.n, (float*)(void*)th, true,
+                                         fail + 1, st);
+    } else {
+      const T* xiT = c.mixed() ? (const T*)(const void*)B[k].xi32 : (const T*)(const void*)B[k].xi;
+      const T* basis = c.mixed() ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
+      err = mlmc::launch_kl_synthesis<T>(xiT, basis, r.n, (int)c.mesh(m).n_el(), nkl, th, true, st);
+    }
+    c.timer.end(st);
+    return err;
+  };
+  auto check_fail = [&]() -> mlmc_status {
+    int h_fail[2] = {0, 0};
+    cudaError_t err;
+    if ((err = cudaMemcpyAsync(h_fail, fail, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (err = cudaStreamSynchronize(st)) != cudaSuccess)
+      return c.cuda_fail(err, "kl_coefficients");
+    if (h_fail[0]) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
+    if (h_fail[1]) return c.fail(MLMC_ERR_TIMEOUT, "tensor-core KL synthesis: a wait expired");
+    return MLMC_OK;
+  };
+  if (!nested) {
+    std::vector<mlmc::SolveGroup<T>> groups;
+    for (size_t k = 0; k < reqs.size(); ++k) {
+      const LevelReq& r = reqs[k];
+      if ((e = synthesize(k, r.level, (T*)B[k].theta_f)) != cudaSuccess) return c.cuda_fail(e, "kl_synthesis");
+      groups.push_back({r.level, r.n, (T*)B[k].theta_f, B[k].qf, B[k].st_f, B[k].it_f});
+      if (r.level > 0) {
+        if ((e = synthesize(k, r.level - 1, (T*)B[k].theta_c)) != cudaSuccess) return c.cuda_fail(e, "kl_synthesis");
+        groups.push_back({r.level - 1, r.n, (T*)B[k].theta_c, B[k].qc, B[k].st_c, B[k].it_c});
+      }
+    }
+    mlmc_status s = check_fail();
+    if (s == MLMC_OK) s = mlmc::solve_groups<T>(c, groups);
+    if (s != MLMC_OK) return s;
+  }
+  for (int j = 0; nested && j <= top; ++j) {
     std::vector<mlmc::SolveGroup<T>> groups;
     for (size_t k = 0; k < reqs.size(); ++k) {
       const LevelReq& r = reqs[k];
       if (r.level < j) continue;
       T* th = (T*)B[k].theta_f;
-      c.timer.begin(mlmc::kProfOther, st, "kl_synthesis");
-      if (tc) {
-        e = mlmc::launch_kl_synthesis_tc(c.basis_tc_op[j], xop[k], (int)c.mesh(j).n_el(), r.n, (float*)(void*)th,
-                                         true, fail + 1, st);
-      } else {
-        const T* xiT = c.mixed() ? (const T*)(const void*)B[k].xi32 : (const T*)(const void*)B[k].xi;
-        const T* basis = c.mixed() ? (const T*)(const void*)c.basis32[j] : (const T*)(const void*)c.basis64[j];
-        e = mlmc::launch_kl_synthesis<T>(xiT, basis, r.n, (int)c.mesh(j).n_el(), nkl, th, true, st);
-      }
-      c.timer.end(st);
-      if (e != cudaSuccess) return c.cuda_fail(e, "kl_synthesis");
+      if ((e = synthesize(k, j, th)) != cudaSuccess) return c.cuda_fail(e, "kl_synthesis");
       mlmc::SolveGroup<T> g{j, r.n, th, qs[k], ss[k], is[k]};
       if (j == r.level) g = mlmc::SolveGroup<T>{j, r.n, th, B[k].qf, B[k].st_f, B[k].it_f};
       if (j + 1 == r.level) g = mlmc::SolveGroup<T>{j, r.n, th, B[k].qc, B[k].st_c, B[k].it_c};
@@ -254,13 +294,8 @@ mlmc_status run_level_requests(mlmc_ctx* h, const std::vector<LevelReq>& reqs, d
       g.d_out = j < r.level ? cur : nullptr;
       groups.push_back(g);
     }
-    int h_fail[2] = {0, 0};
-    if ((e = cudaMemcpyAsync(h_fail, fail, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-      return c.cuda_fail(e, "kl_coefficients");
-    if (h_fail[0]) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
-    if (h_fail[1]) return c.fail(MLMC_ERR_TIMEOUT, "tensor-core KL synthesis: a wait expired");
-    mlmc_status s = mlmc::solve_groups<T>(c, groups);
+    mlmc_status s = check_fail();
+    if (s == MLMC_OK) s = mlmc::solve_groups<T>(c, groups);
     if (s != MLMC_OK) return s;
   }
   for (size_t k = 0; k < reqs.size(); ++k) {
@@ -533,6 +568,13 @@ mlmc_status mlmc_sample_levels(mlmc_ctx* h, int32_t n_req, const int32_t* levels
   mlmc_status s = sample_levels_impl(h, reqs, q_fine, q_coarse, status);
   if (s != MLMC_OK) return s;
   return sync_stats(h);
+}
+
+mlmc_status mlmc_set_nested_threshold(mlmc_ctx* h, int64_t min_nodes) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  if (min_nodes < 0) return h->c.fail(MLMC_ERR_INVALID_ARG, "nested threshold must be >= 0");
+  h->c.nested_min_nodes = min_nodes;
+  return MLMC_OK;
 }
 
 mlmc_status mlmc_profile_enable(mlmc_ctx* h, int32_t on) {

@@ -128,6 +128,7 @@ struct Context {
   double floor_tol32 = 3e-6;      // tightest inner relative tolerance of the FP32 solve
   int check_every = 4;            // PCG iterations between host convergence checks
   bool graphs = true;             // replay PCG batches from a CUDA graph captured per solve
+  int64_t nested_min_nodes = int64_t(1) << 22;   // finest-mesh nodes per call for nested iteration
   int last_outer = 0;             // refinement steps of the last solve (diagnostic)
   int last_iters = 0;             // max PCG iterations of the last solve (diagnostic)
 

@@ -160,17 +160,20 @@ def test_full_size_launch_sampled_outputs(B):
         B.mlmc_destroy(ctx)
 
 
-def test_sample_levels_matches_single_level_calls_and_solve_batch(B):
+@pytest.mark.parametrize("nested_min_nodes", [0, 1 << 40])
+def test_sample_levels_matches_single_level_calls_and_solve_batch(B, nested_min_nodes):
     """Same xi on both meshes of a pair; results independent of batch composition.
 
-    mlmc_sample_level(s) solve each sample's meshes by nested iteration (each mesh
-    starts from the next coarser one's solution), mlmc_solve_batch from the lifting:
-    both end at ||f - K d|| <= 1e-8 ||f||, from different starting iterates, so they
+    With threshold 0 mlmc_sample_level(s) solve each sample's meshes by nested
+    iteration (each mesh starts from the next coarser one's solution), with a huge
+    one in one lock-stepped batch from the lifting like mlmc_solve_batch: all end at
+    ||f - K d|| <= 1e-8 ||f||, possibly from different starting iterates, so they
     agree to the solver's accuracy on the quantities (the stated 1e-6), while calls
     running the same procedure agree to rounding."""
     w = STRIP_MIXED_5LEVEL
     ctx = B.mlmc_create(B.config_from_workload(w))
     try:
+        B.mlmc_set_nested_threshold(ctx, nested_min_nodes)
         counts = [5, 4, 3]
         total = sum(counts)
         qf = np.zeros(2 * total)
@@ -207,12 +210,14 @@ def test_sample_levels_matches_single_level_calls_and_solve_batch(B):
         B.mlmc_destroy(ctx)
 
 
-def test_telescoping_on_identical_samples(B):
+@pytest.mark.parametrize("nested_min_nodes", [0, 1 << 40])
+def test_telescoping_on_identical_samples(B, nested_min_nodes):
     """mean(Q_0) + sum_l mean(Q_l - Q_{l-1}) = mean(Q_L) when every mesh solves the same
     xi (Eq. MLMC_expectation), with each mesh's values produced by separate solves."""
     w = STRIP_FP64_3LEVEL
     ctx = B.mlmc_create(B.config_from_workload(w))
     try:
+        B.mlmc_set_nested_threshold(ctx, nested_min_nodes)
         ids = list(range(12))
         Q = {}
         for m in range(3):
@@ -222,7 +227,8 @@ def test_telescoping_on_identical_samples(B):
         tel = Q[0].mean(0) + (Q[1] - Q[0]).mean(0) + (Q[2] - Q[1]).mean(0)
         np.testing.assert_allclose(tel, Q[2].mean(0), rtol=1e-14)
         # and the coarse solve inside a level-2 pair equals the mesh-1 solve of the same xi
-        # (nested iteration vs a solve from the lifting: equal to the double path's 1e-9)
+        # (nested iteration or a lock-stepped pair vs single-mesh solves from the
+        # lifting: equal to the double path's 1e-9)
         qf, qc = np.zeros(2 * len(ids)), np.zeros(2 * len(ids))
         B.mlmc_sample_level(ctx, 2, 0, len(ids), qf, qc)
         np.testing.assert_allclose(qc.reshape(-1, 2), Q[1], rtol=1e-9)
