@@ -210,7 +210,7 @@ struct Geo {
 };
 
 __host__ __device__ __forceinline__ int strips_of(int nx, int cols = kStripCols) { return (nx + 1 + cols - 1) / cols; }
-__host__ __device__ __forceinline__ int chunks_of(int ny) { return (ny + 1 + kRowChunk - 1) / kRowChunk; }
+__host__ __device__ __forceinline__ int chunks_of(int ny, int rows = kRowChunk) { return (ny + 1 + rows - 1) / rows; }
 
 // Kuu coupling of the two nodes of one horizontal element edge (exact, = 2x2 Gauss):
 // w (-4/3 C11 rx^2 + 2/3 C66 ry^2); the C16 terms cancel on such an edge.

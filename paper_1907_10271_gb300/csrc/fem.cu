@@ -1,13 +1,16 @@
 // Matrix-free Q1 plane-strain operator (Eq. matrixinplane) and the multigrid-PCG
 // kernels built on it.
 //
-// Warp-strip scheme. A warp owns 32 consecutive node columns of one sample (one halo
-// column each side, 30 output columns) and walks up a chunk of node rows. Lane L
-// computes the element to the upper right of its node from its own column values
-// and its right neighbour's (warp shuffle down); the element's contributions to the
-// right-hand nodes go back by a shuffle up, and the contributions to the upper nodes
-// stay in registers for the next row. No shared memory, every vector read once per
-// row with 256-byte coalesced accesses (FP32), each element evaluated once per warp.
+// Warp-strip scheme. A warp owns 32 consecutive node columns of one sample (halo
+// columns on each side: one for the operator alone, two for the smoothing kernels,
+// whose pair-block smoother couples columns 2m and 2m + 1) and walks up a chunk of
+// node rows. Lane L computes the element to the upper right of its node from its own
+// column values and its right neighbour's (warp shuffle down); the element's
+// contributions to the right-hand nodes go back by a shuffle up, and the
+// contributions to the upper nodes stay in registers for the next row. Every vector
+// is read once per row with 256-byte coalesced accesses (FP32: staged through a
+// per-warp ring of shared-memory slots filled by cp.async), and each element is
+// evaluated once per warp.
 //
 // The kernels fuse each V-cycle / PCG step with the operator it needs:
 //   Apply    q = K p (all rows; testing)
@@ -243,6 +246,45 @@ struct RawE {
   T a, b, c, d;
 };
 
+// Per-row element pass shared by the strip loops. Element row er (between node rows
+// er and er + 1) of lane l has corners n1 = (l, er), n2 = (l + 1, er), n3 = (l + 1,
+// er + 1), n4 = (l, er + 1); its contributions o1..o4 go to those nodes. Node (l, er)
+// therefore sums o1 of row er, o4 of row er - 1, and the left lane's o2 of row er and
+// o3 of row er - 1: those two are added before the one shuffle up that brings them.
+// The right neighbour's bottom values are its top values of the previous row, so one
+// shuffle down per row suffices as well.
+template <typename Val>
+struct RowCarry {
+  V2<Val> pb, pbr;   // bottom node values of the next element row: own and right lane's
+  V2<Val> o3p, o4p;  // previous element row's contributions to its top nodes
+  __device__ __forceinline__ explicit RowCarry(V2<Val> p0)
+      : pb(p0), pbr(shfl_down2(p0)), o3p(zero2<Val>()), o4p(zero2<Val>()) {}
+  // pt: top node values of element row er; returns K x at node (lane, er)
+  template <typename Op, typename RE, typename Sc>
+  __device__ __forceinline__ V2<Val> step(const Op& op, const Invariants& U, const RE& ce, Sc rx, Sc ry, Sc w,
+                                          bool elem, V2<Val> pt) {
+    const int lane = threadIdx.x & (kWarp - 1);
+    const V2<Val> ptr = shfl_down2(pt);
+    V2<Val> o1 = zero2<Val>(), o2 = zero2<Val>(), o3 = zero2<Val>(), o4 = zero2<Val>();
+    if (elem) op.element(U, ce, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
+    V2<Val> f = shfl_up2(v2<Val>(o2.u + o3p.u, o2.v + o3p.v));
+    if (lane == 0) f = zero2<Val>();
+    const V2<Val> kx = v2<Val>((o1.u + o4p.u) + f.u, (o1.v + o4p.v) + f.v);
+    o3p = o3;
+    o4p = o4;
+    pb = pt;
+    pbr = ptr;
+    return kx;
+  }
+  // K x at the top node row of the last element row
+  __device__ __forceinline__ V2<Val> top() const {
+    const int lane = threadIdx.x & (kWarp - 1);
+    V2<Val> f = shfl_up2(o3p);
+    if (lane == 0) f = zero2<Val>();
+    return v2<Val>(o4p.u + f.u, o4p.v + f.v);
+  }
+};
+
 // Walks the warp's strip up its chunk of node rows. Node-row data is prefetched P
 // rows ahead into a register ring (static indices after unrolling), element data P
 // element rows ahead, so each warp keeps P rows of loads in flight. Lane l holds node
@@ -264,8 +306,9 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
   const bool out_col = col_in && lane >= kHalo && lane < kHalo + kCols;
   const int ic = min(max(i, 0), nx);       // in-bounds column for (discarded) loads of outside lanes
   const int ie = min(max(i, 0), nx - 1);
-  const int j0 = chunk * kRowChunk;
-  const int j1 = min(j0 + kRowChunk - 1, ny);
+  const int rows = V.rows > 0 ? V.rows : kRowChunk;
+  const int j0 = chunk * rows;
+  const int j1 = min(j0 + rows - 1, ny);
   const int er0 = max(j0 - 1, 0);
   const int er1 = min(j1, ny - 1);
   const Sc rx = (Sc)V.g.rx, ry = (Sc)V.g.ry, w = (Sc)V.g.w;
@@ -283,7 +326,7 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
     if (er0 + 1 + u <= er1 + 1) ring[u] = op.load(ic, er0 + 1 + u);
     if (er0 + u <= er1) ering[u] = op.loadE(ie, er0 + u);
   }
-  V2<Val> acc = zero2<Val>();
+  RowCarry<Val> rc(pb);
   for (int base = er0; base <= er1; base += P) {
 #pragma unroll
     for (int u = 0; u < P; ++u) {
@@ -295,26 +338,14 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
         if (er + P <= er1) ering[u] = op.loadE(ie, er + P);
         const V2<Val> vt = op.in(cur, i, er + 1);
         const V2<Val> pt = op.pair(col_in ? vt : zero2<Val>(), col_in);
-        const V2<Val> pbr = shfl_down2(pb), ptr = shfl_down2(pt);
-        V2<Val> o1 = zero2<Val>(), o2 = zero2<Val>(), o3 = zero2<Val>(), o4 = zero2<Val>();
-        if (elem) op.element(U, ce, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
-        V2<Val> fb = shfl_up2(o2), ft = shfl_up2(o3);
-        if (lane == 0) {
-          fb = zero2<Val>();
-          ft = zero2<Val>();
-        }
-        acc.u = acc.u + (o1.u + fb.u);
-        acc.v = acc.v + (o1.v + fb.v);
-        if (er >= j0) op.out(i, er, acc, out_col);
-        acc.u = o4.u + ft.u;
-        acc.v = o4.v + ft.v;
+        const V2<Val> kx = rc.step(op, U, ce, rx, ry, w, elem, pt);
+        if (er >= j0) op.out(i, er, kx, out_col);
         op.shift();
-        pb = pt;
       }
     }
   }
   // the top boundary row (only element row ny - 1 contributes) belongs to the chunk that owns it
-  if (er1 + 1 == ny && ny >= j0 && ny <= j1) op.out(i, ny, acc, out_col);
+  if (er1 + 1 == ny && ny >= j0 && ny <= j1) op.out(i, ny, rc.top(), out_col);
 }
 
 // strip_loop with node and element rows staged through a ring of D shared-memory
@@ -333,22 +364,24 @@ __device__ __forceinline__ void strip_loop_async(const Invariants& U, const View
   const bool out_col = col_in && lane >= kHalo && lane < kHalo + kCols;
   const int ic = min(max(i, 0), nx);
   const int ie = min(max(i, 0), nx - 1);
-  const int j0 = chunk * kRowChunk;
-  const int j1 = min(j0 + kRowChunk - 1, ny);
+  const int rows = V.rows > 0 ? V.rows : kRowChunk;
+  const int j0 = chunk * rows;
+  const int j1 = min(j0 + rows - 1, ny);
   const int er0 = max(j0 - 1, 0);
   const int er1 = min(j1, ny - 1);
   const int nsteps = er1 - er0 + 2;   // node rows er0 .. er1 + 1
   const Sc rx = (Sc)V.g.rx, ry = (Sc)V.g.ry, w = (Sc)V.g.w;
-  auto issue = [&](int k) {
+  // step k into slot k % D (passed in: the loop keeps the slot indices as counters)
+  auto issue = [&](int k, int slot) {
     if (k < nsteps) {
-      typename Op::Slot& sl = ring[k % D];
+      typename Op::Slot& sl = ring[slot];
       op.fetch(sl, lane, ic, er0 + k);
       if (k >= 1) op.fetchE(sl, lane, ie, er0 + k - 1);
     }
     cp_async_commit();   // one group per step, empty past the end
   };
 #pragma unroll
-  for (int k = 0; k < D; ++k) issue(k);
+  for (int k = 0; k < D; ++k) issue(k, k);
   cp_async_wait<D - 1>();
   V2<Val> pb;
   {
@@ -357,34 +390,25 @@ __device__ __forceinline__ void strip_loop_async(const Invariants& U, const View
     pb = op.pair(col_in ? v0 : zero2<Val>(), col_in);
     op.shift();
   }
-  V2<Val> acc = zero2<Val>();
+  RowCarry<Val> rc(pb);
+  int refill = 0, slot = 1 % D;   // slots of steps k - 1 and k
   for (int k = 1; k < nsteps; ++k) {
-    issue(k + D - 1);   // refills the slot of step k - 1, already read
+    issue(k + D - 1, refill);   // refills the slot of step k - 1, already read
     cp_async_wait<D - 1>();
     const int er = er0 + k - 1;
-    const typename Op::Slot& sl = ring[k % D];
+    const typename Op::Slot& sl = ring[slot];
     const typename Op::Raw cur = op.read(sl, lane, ic, er + 1);
     const RawE<typename Op::E> ce = op.readE(sl, lane);
     const V2<Val> vt = op.in(cur, i, er + 1);
     const V2<Val> pt = op.pair(col_in ? vt : zero2<Val>(), col_in);
-    const V2<Val> pbr = shfl_down2(pb), ptr = shfl_down2(pt);
-    V2<Val> o1 = zero2<Val>(), o2 = zero2<Val>(), o3 = zero2<Val>(), o4 = zero2<Val>();
-    if (elem) op.element(U, ce, rx, ry, w, pb, pbr, ptr, pt, o1, o2, o3, o4);
-    V2<Val> fb = shfl_up2(o2), ft = shfl_up2(o3);
-    if (lane == 0) {
-      fb = zero2<Val>();
-      ft = zero2<Val>();
-    }
-    acc.u = acc.u + (o1.u + fb.u);
-    acc.v = acc.v + (o1.v + fb.v);
-    if (er >= j0) op.out(i, er, acc, out_col);
-    acc.u = o4.u + ft.u;
-    acc.v = o4.v + ft.v;
+    const V2<Val> kx = rc.step(op, U, ce, rx, ry, w, elem, pt);
+    if (er >= j0) op.out(i, er, kx, out_col);
     op.shift();
-    pb = pt;
+    refill = slot;
+    slot = slot + 1 == D ? 0 : slot + 1;
   }
   cp_async_wait<0>();
-  if (er1 + 1 == ny && ny >= j0 && ny <= j1) op.out(i, ny, acc, out_col);
+  if (er1 + 1 == ny && ny >= j0 && ny <= j1) op.out(i, ny, rc.top(), out_col);
 }
 
 // ---------------------------------------------------------------- operand handlers
@@ -402,6 +426,7 @@ struct OpBase {
   static constexpr int kHalo = 1;             // halo lanes on each side
   static constexpr bool kAsync = false;       // rows staged by strip_loop_async (FP32 only)
   static constexpr int kDepth = 4;            // slots of the staging ring
+  static constexpr int kMinBlocks = 7;        // FP32: resident 128-thread blocks per SM (<= 72 registers)
   const View<T>& V;
   int64_t nbase;   // first value of the sample's vectors
   int64_t ebase;   // first element of the sample
@@ -593,6 +618,7 @@ struct OpPreR : OpBase<T> {
   static constexpr int kCols = kSmoothCols, kHalo = 2;
   static constexpr bool kAsync = sizeof(T) == 4;
   static constexpr int kDepth = 3;
+  static constexpr int kMinBlocks = 6;   // capped at 7 blocks it spills in the loop
   struct Raw {
     V2<T> b, w;
     T c;
@@ -929,7 +955,7 @@ struct OpResid : OpBase<double> {
 };
 
 template <typename T, int P, typename Op>
-__global__ void __launch_bounds__(kWarpsPerBlock * kWarp)
+__global__ void __launch_bounds__(kWarpsPerBlock * kWarp, sizeof(T) == 4 ? Op::kMinBlocks : 0)
     k_strip(const __grid_constant__ ViewList<T> L, SampleState S) {
   const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   int vi, s, strip, chunk;
@@ -940,7 +966,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * kWarp)
   if (!op.live()) return;
   if (S.units && (threadIdx.x & 31) == 0) {
     const int c0 = max(strip * Op::kCols, 0), c1 = min(strip * Op::kCols + Op::kCols - 1, V.g.nx);
-    const int r0 = chunk * kRowChunk, r1 = min(r0 + kRowChunk - 1, V.g.ny);
+    const int rows = V.rows > 0 ? V.rows : kRowChunk;
+    const int r0 = chunk * rows, r1 = min(r0 + rows - 1, V.g.ny);
     atomicAdd(&S.units[L.prof_op], (unsigned long long)((c1 - c0 + 1) * (r1 - r0 + 1)));
   }
   if constexpr (Op::kAsync) {

@@ -19,6 +19,7 @@ struct View {
   int work_begin;   // first warp (strip kernels) or thread (pointwise kernels) of this view
   int nwork;
   int tiles_x, tiles_y;
+  int rows;         // node rows per warp tile of a strip kernel (0: kRowChunk)
   const T* trig2;
   const T* trig;
   const T* a;

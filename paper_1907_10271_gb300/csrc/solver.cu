@@ -66,17 +66,34 @@ View<T> base_view(const GroupBuf<T>& g, int k) {
   return v;
 }
 
-// Assigns the strips of operation op and the work offsets of a strip kernel (warps);
-// returns the total.
+// Assigns the strips of operation op, the row chunks and the work offsets of a strip
+// kernel (warps); returns the total. A warp walks its rows one after another, so a
+// launch of fewer warps than about one and a half waves (152 SMs x 28 resident warps)
+// is bound by that walk: its views are cut into 2 or 4 times as many row chunks of
+// equal height (at least kMinRows rows each), which shortens every warp's walk at the
+// cost of one extra element row per chunk.
 template <typename T>
 int finalize_warps(ViewList<T>& L, StripOp op) {
-  int acc = 0;
-  for (int i = 0; i < L.n; ++i) {
-    L.v[i].tiles_x = strips_of(L.v[i].g.nx, strip_cols(op));
-    L.v[i].work_begin = acc;
-    L.v[i].nwork = L.v[i].nsamp * L.v[i].tiles_x * L.v[i].tiles_y;
-    acc += L.v[i].nwork;
-  }
+  constexpr int kTargetWarps = 152 * 28 * 3 / 2;
+  constexpr int kMinRows = 6;
+  auto layout = [&](int split) {
+    int acc = 0;
+    for (int i = 0; i < L.n; ++i) {
+      View<T>& v = L.v[i];
+      const int nodes_y = v.g.ny + 1;
+      const int base = chunks_of(v.g.ny);
+      const int nch = std::max(base, std::min(base * split, nodes_y / kMinRows));
+      v.rows = (nodes_y + nch - 1) / nch;
+      v.tiles_x = strips_of(v.g.nx, strip_cols(op));
+      v.tiles_y = chunks_of(v.g.ny, v.rows);
+      v.work_begin = acc;
+      v.nwork = v.nsamp * v.tiles_x * v.tiles_y;
+      acc += v.nwork;
+    }
+    return acc;
+  };
+  int split = 1, acc = layout(1);
+  while (acc < kTargetWarps && split < 4) acc = layout(split *= 2);
   return acc;
 }
 
@@ -332,7 +349,6 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
           v.xc = g.r1[d - 1];
           v.o1 = g.b[d];
           v.winvd = g.winvd[d];
-        v.wc = g.wc[d];
           v.wc = g.wc[d];
           v.o2 = g.r1[d];
         }
