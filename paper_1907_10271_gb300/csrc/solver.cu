@@ -67,21 +67,23 @@ View<T> base_view(const GroupBuf<T>& g, int k) {
 }
 
 // Assigns the strips of operation op, the row chunks and the work offsets of a strip
-// kernel (warps); returns the total. A warp walks its rows one after another, so a
-// launch of fewer warps than about one and a half waves (152 SMs x 28 resident warps)
-// is bound by that walk: its views are cut into 2 or 4 times as many row chunks of
-// equal height (at least kMinRows rows each), which shortens every warp's walk at the
-// cost of one extra element row per chunk.
+// kernel (warps); returns the total. A mesh's node rows are cut into chunks of equal
+// height, at most kMaxRows (each chunk costs one extra element row and a pipeline
+// fill). A warp walks its rows one after another, so a launch of fewer warps than
+// about one and a half waves (152 SMs x 28 resident warps) is bound by that walk: its
+// views are cut into 2, 4 or 8 times as many chunks (at least kMinRows rows each),
+// which shortens every warp's walk.
 template <typename T>
 int finalize_warps(ViewList<T>& L, StripOp op) {
   constexpr int kTargetWarps = 152 * 28 * 3 / 2;
   constexpr int kMinRows = 6;
+  constexpr int kMaxRows = 64;
   auto layout = [&](int split) {
     int acc = 0;
     for (int i = 0; i < L.n; ++i) {
       View<T>& v = L.v[i];
       const int nodes_y = v.g.ny + 1;
-      const int base = chunks_of(v.g.ny);
+      const int base = chunks_of(v.g.ny, kMaxRows);
       const int nch = std::max(base, std::min(base * split, nodes_y / kMinRows));
       v.rows = (nodes_y + nch - 1) / nch;
       v.tiles_x = strips_of(v.g.nx, strip_cols(op));
@@ -93,7 +95,7 @@ int finalize_warps(ViewList<T>& L, StripOp op) {
     return acc;
   };
   int split = 1, acc = layout(1);
-  while (acc < kTargetWarps && split < 4) acc = layout(split *= 2);
+  while (acc < kTargetWarps && split < 8) acc = layout(split *= 2);
   return acc;
 }
 
