@@ -418,3 +418,129 @@ def mlmc_failure_estimate(results, threshold, k=1, two_level=False):
     if st != 0:
         raise MLMCError(st, "mlmc_failure_estimate")
     return est.value, list(mean), list(var)
+
+
+# ---------------------------------------------------------------- 3D Hex8 block (mlmc3d.h)
+
+class mlmc3d_config(ctypes.Structure):
+    _fields_ = [
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+        ("nx0", ctypes.c_int32), ("ny0", ctypes.c_int32), ("nz0", ctypes.c_int32), ("levels", ctypes.c_int32),
+        ("E11", ctypes.c_double), ("E22", ctypes.c_double), ("E33", ctypes.c_double),
+        ("G12", ctypes.c_double), ("G13", ctypes.c_double), ("G23", ctypes.c_double),
+        ("nu12", ctypes.c_double), ("nu13", ctypes.c_double), ("nu23", ctypes.c_double),
+        ("kl_terms", ctypes.c_int32), ("kl_std", ctypes.c_double), ("kl_corr", ctypes.c_double),
+        ("kl_quad", ctypes.c_int32),
+        ("shortening", ctypes.c_double), ("omega_x0", ctypes.c_double), ("omega_x1", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("rtol", ctypes.c_double),
+        ("max_iter", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+    ]
+
+
+_SIG3 = None
+
+
+def lib3():
+    """The library with the 3D entry points' signatures set."""
+    global _SIG3
+    L = lib()
+    if _SIG3 is None:
+        P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        sig = {
+            "mlmc3d_create": (I32, [ctypes.POINTER(mlmc3d_config), P, ctypes.POINTER(P)]),
+            "mlmc3d_destroy": (None, [P]),
+            "mlmc3d_last_error": (ctypes.c_char_p, [P]),
+            "mlmc3d_sample_level": (I32, [P, I32, U64, I64, P, P, P]),
+            "mlmc3d_solve_batch": (I32, [P, P, I64, P, P]),
+            "mlmc3d_level_stats_get": (I32, [P, I32, P]),
+            "mlmc3d_reset_stats": (I32, [P]),
+            "mlmc3d_theta": (I32, [P, I32, I32, U64, I64, P]),
+            "mlmc3d_apply": (I32, [P, I32, I64, P, P, P]),
+            "mlmc3d_apply_bench": (I32, [P, I32, I64, I32, P, P, P]),
+            "mlmc3d_last_iters": (I32, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _SIG3 = True
+    return L
+
+
+def config3_from_workload(w, **overrides):
+    """mlmc3d_config from a 3D workload dict (see workloads.py); keyword overrides win."""
+    w = dict(w)
+    w.update(overrides)
+    c = mlmc3d_config()
+    for f in ("lx", "ly", "lz", "E11", "E22", "E33", "G12", "G13", "G23", "nu12", "nu13", "nu23", "kl_corr",
+              "shortening", "omega_x0", "omega_x1", "rtol"):
+        setattr(c, f, float(w[f]))
+    c.nx0, c.ny0, c.nz0, c.levels = int(w["nx0"]), int(w["ny0"]), int(w["nz0"]), int(w["levels"])
+    c.kl_terms, c.kl_quad = int(w["kl_terms"]), int(w["kl_quad"])
+    c.kl_std = float(np.deg2rad(w["kl_std_deg"]))
+    c.seed = int(w["seed"])
+    c.max_iter = int(w.get("max_iter", 0))
+    c.max_outer = int(w.get("max_outer", 0))
+    return c
+
+
+def _check3(ctx, status):
+    if status != MLMC_OK:
+        raise MLMCError(status, lib3().mlmc3d_last_error(ctx).decode(errors="replace"))
+    return status
+
+
+def mlmc3d_create(cfg, stream=None):
+    h = ctypes.c_void_p()
+    st = current_stream() if stream is None else stream
+    s = lib3().mlmc3d_create(ctypes.byref(cfg), ctypes.c_void_p(st), ctypes.byref(h))
+    if s != MLMC_OK:
+        raise MLMCError(s, lib3().mlmc3d_last_error(None).decode(errors="replace"))
+    return h
+
+
+def mlmc3d_destroy(ctx):
+    lib3().mlmc3d_destroy(ctx)
+
+
+def mlmc3d_sample_level(ctx, level, first_id, n, q_fine=None, q_coarse=None, status=None):
+    return _check3(ctx, lib3().mlmc3d_sample_level(ctx, level, first_id, n, _ptr(q_fine, np.float64),
+                                                    _ptr(q_coarse, np.float64), _ptr(status, np.int32)))
+
+
+def mlmc3d_solve_batch(ctx, items, q=None, status=None):
+    arr = (mlmc_item * len(items))(*[mlmc_item(int(l), int(m), int(s)) for (l, m, s) in items])
+    return _check3(ctx, lib3().mlmc3d_solve_batch(ctx, ctypes.cast(arr, ctypes.c_void_p), len(items),
+                                                   _ptr(q, np.float64), _ptr(status, np.int32)))
+
+
+def mlmc3d_level_stats(ctx, level):
+    out = mlmc_level_stats()
+    _check3(ctx, lib3().mlmc3d_level_stats_get(ctx, level, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def mlmc3d_reset_stats(ctx):
+    return _check3(ctx, lib3().mlmc3d_reset_stats(ctx))
+
+
+def mlmc3d_theta(ctx, mesh_level, level, first_id, n, theta):
+    return _check3(ctx, lib3().mlmc3d_theta(ctx, mesh_level, level, first_id, n, _ptr(theta, np.float64)))
+
+
+def mlmc3d_apply(ctx, mesh_level, n, theta, x, y):
+    return _check3(ctx, lib3().mlmc3d_apply(ctx, mesh_level, n, _ptr(theta, np.float64), _ptr(x, np.float32),
+                                             _ptr(y, np.float32)))
+
+
+def mlmc3d_apply_bench(ctx, mesh_level, n, reps):
+    ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check3(ctx, lib3().mlmc3d_apply_bench(ctx, mesh_level, n, reps, ctypes.byref(ms), ctypes.byref(by),
+                                            ctypes.byref(fl)))
+    return ms.value, by.value, fl.value
+
+
+def mlmc3d_last_iters(ctx):
+    it = ctypes.c_int32()
+    _check3(ctx, lib3().mlmc3d_last_iters(ctx, ctypes.byref(it)))
+    return it.value

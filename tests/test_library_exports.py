@@ -15,14 +15,15 @@ def declared_functions():
         if f.endswith(".h"):
             text = open(os.path.join(ROOT, "include", f)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names += re.findall(r"\b(mlmc_[a-z0-9_]+)\s*\(", text)
+            names += re.findall(r"\b(mlmc(?:3d)?_[a-z0-9_]+)\s*\(", text)
     return sorted(set(names))
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("mlmc_create", "mlmc_destroy", "mlmc_sample_level", "mlmc_solve_batch",
-                     "mlmc_estimate", "mlmc_last_error"):
+                     "mlmc_estimate", "mlmc_last_error", "mlmc3d_create", "mlmc3d_sample_level",
+                     "mlmc3d_solve_batch"):
         assert required in names
 
 
@@ -49,3 +50,12 @@ def test_config_marshalling():
     assert (c.nx0, c.ny0, c.levels, c.kl_terms) == (64, 16, 5, 100)
     assert c.precision == binding.MLMC_PREC_MIXED
     assert abs(c.kl_std - 2.0 * 3.141592653589793 / 180.0) < 1e-15
+
+
+def test_config3_marshalling():
+    from paper_1907_10271_gb300 import binding
+    from workloads import HEX8_MIXED_4LEVEL
+    c = binding.config3_from_workload(HEX8_MIXED_4LEVEL)
+    assert (c.nx0, c.ny0, c.nz0, c.levels, c.kl_terms) == (32, 8, 4, 4, 200)
+    assert (c.G23, c.nu23, c.lz) == (3.5e9, 0.45, 0.125)
+    assert abs(c.kl_std - 3.0 * 3.141592653589793 / 180.0) < 1e-15

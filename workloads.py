@@ -46,7 +46,32 @@ STRIP_MIXED_5LEVEL.update(
     rtol=1e-8,
 )
 
-WORKLOADS = {w["name"]: w for w in (STRIP_FP64_3LEVEL, STRIP_MIXED_5LEVEL)}
+# 3D fibre-waviness block: the strip problem generalised to trilinear Hex8 elements on
+# [0, lx] x [0, ly] x [0, lz], cube elements halved per level (m = 8 DOF growth),
+# orthotropic ply constants (fibre axis 1) rotated about y by an out-of-plane
+# waviness angle theta(x, z) (constant through y), clamped at x = 0 and shortened at
+# x = lx.
+HEX8_MIXED_4LEVEL = dict(
+    name="block-hex8-mixed-4level",
+    lx=1.0, ly=0.25, lz=0.125,
+    nx0=32, ny0=8, nz0=4,       # level-0 mesh; level l has (nx0, ny0, nz0) * 2^l cube elements
+    levels=4,
+    E11=135e9, E22=9.5e9, E33=9.5e9,
+    G12=5e9, G13=5e9, G23=3.5e9,
+    nu12=0.3, nu13=0.3, nu23=0.45,
+    kl_terms=200,               # N_KL of the 2D field theta(x, z)
+    kl_std_deg=3.0,
+    kl_corr=0.2,
+    kl_quad=128,
+    shortening=1e-3,
+    omega_x0=0.25, omega_x1=0.75,
+    seed=0,
+    n_per_level=(2048, 512, 128, 32),
+    precision="mixed",
+    rtol=1e-8,
+)
+
+WORKLOADS = {w["name"]: w for w in (STRIP_FP64_3LEVEL, STRIP_MIXED_5LEVEL, HEX8_MIXED_4LEVEL)}
 
 
 def mesh_dims(cfg, level):
@@ -57,3 +82,13 @@ def mesh_dims(cfg, level):
 def n_dofs(cfg, level):
     nx, ny = mesh_dims(cfg, level)
     return 2 * (nx + 1) * (ny + 1)
+
+
+def mesh_dims3(cfg, level):
+    """(nx, ny, nz) element counts of mesh `level` of a 3D workload."""
+    return cfg["nx0"] << level, cfg["ny0"] << level, cfg["nz0"] << level
+
+
+def n_dofs3(cfg, level):
+    nx, ny, nz = mesh_dims3(cfg, level)
+    return 3 * (nx + 1) * (ny + 1) * (nz + 1)
