@@ -59,8 +59,11 @@ def parse():
                     help="skip the plain double-precision single-sample comparison")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the request-loop (selective refinement) measurement")
-    ap.add_argument("--case", choices=["full", "small"], default="full",
-                    help="small: one untimed call with 1/8 of each level's samples (for profilers)")
+    ap.add_argument("--case", choices=["full", "small", "hex3d"], default="full",
+                    help="small: one untimed call with 1/4 of each level's samples; hex3d: one untimed "
+                         "step of the 3D Hex8 block (both for profilers)")
+    ap.add_argument("--no-hex3d", dest="hex3d", action="store_false",
+                    help="skip the 3D Hex8 block measurement")
     ap.add_argument("--cpu-fraction", type=float, default=1.0 / 32.0,
                     help="fraction of each level's samples the CPU oracle times")
     return ap.parse_args()
@@ -575,11 +578,120 @@ def run_small_case():
     print(json.dumps({"case": "small", "level_pairs": total, "failed": int((st != 0).sum())}))
 
 
+# FP32 CUDA-core peak of one GB300 from its unit counts and clock: 152 SMs x 128 FP32
+# lanes x 2 flops per FMA x 2.07 GHz (the 3D element operator is plain FP32 arithmetic).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def run_hex3d(B, steps=2, warmup=1, parity=True):
+    """The 3D Hex8 block (block-hex8-mixed-4level): one MLMC step is every level's
+    samples (2048/512/128/32), one mlmc3d_sample_level call per level with host
+    outputs, timed with the device synchronised on both sides (inputs, about 3 GB of
+    solver state per level, are far larger than L2). The operator alone is timed by
+    mlmc3d_apply_bench on the 256x64x32 mesh. Parity: four level-0 solves and one
+    level-1 pair against the oracle's direct solves, whose times are the CPU baseline
+    (levels 2 and 3 are not timed on the CPU: a single SuperLU solve there takes more
+    than ten minutes)."""
+    import torch
+    from workloads import HEX8_MIXED_4LEVEL as W
+    counts = list(W["n_per_level"])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = B.mlmc3d_create(B.config3_from_workload(W), stream.cuda_stream)
+        try:
+            bufs = [(np.zeros(2 * n), np.zeros(2 * n), np.zeros(n, dtype=np.int32)) for n in counts]
+            iters = []
+
+            def step(k):
+                iters.clear()
+                for lev, n in enumerate(counts):
+                    qf, qc, st = bufs[lev]
+                    B.mlmc3d_sample_level(ctx, lev, k * 10 ** 6, n, qf, qc, st)
+                    iters.append(B.mlmc3d_last_iters(ctx))
+
+            for k in range(warmup):
+                step(k)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(steps):
+                step(warmup + k)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) / steps * 1e3
+            failed = sum(int((b[2] != 0).sum()) for b in bufs)
+            op_ms, op_bytes, op_flops = B.mlmc3d_apply_bench(ctx, 3, counts[3], 5)
+            hbm, kind = peaks()
+            tflops = op_flops / op_ms / 1e9
+            out = {
+                "workload": W["name"], "meshes": "32x8x4..256x64x32 Hex8, 3 DOF/node",
+                "samples_per_level": counts, "kl_terms": W["kl_terms"], "rtol": W["rtol"],
+                "metric": "level-pairs/s", "value": round(sum(counts) / ms * 1e3, 1), "ms_per_step": round(ms, 2),
+                "steps": steps, "warmup": warmup, "samples_failed": failed, "pcg_iterations_per_level": list(iters),
+                "note": "host outputs (mlmc3d_sample_level), one call per level; FP32 PCG with a double-precision "
+                        "refinement residual",
+                "roofline": {"kernel": "hex8_apply (FP32, 256x64x32, 32 samples)", "bound": "alu",
+                             "achieved": round(tflops, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                             "frac": round(tflops / FP32_PEAK_TFLOPS, 4),
+                             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                             "flops_per_element": 976, "launch_ms": round(op_ms, 4),
+                             "hbm": {"achieved_gbs": round(op_bytes / op_ms / 1e6, 1), "peak_gbs": hbm,
+                                     "frac": round(op_bytes / op_ms / 1e6 / hbm, 4), "peak_kind": kind}},
+            }
+            if parity:
+                from oracle import hex as H
+                from oracle import kl, rng
+                ids = [10 ** 7 + k for k in range(4)]
+                items = [(0, 0, i) for i in ids] + [(1, 1, ids[0]), (1, 0, ids[0])]
+                q = np.zeros(2 * len(items))
+                B.mlmc3d_solve_batch(ctx, items, q)
+                errs, times = [0.0, 0.0], {0: [], 1: []}
+                for k, (lev, m, sid) in enumerate(items):
+                    nx, ny, nz = W["nx0"] << m, W["ny0"] << m, W["nz0"] << m
+                    cx, cz = H.column_centroids(W, nx, nz)
+                    Bm, _, _ = kl.kl_basis(W["lx"], W["lz"], W["kl_corr"], np.deg2rad(W["kl_std_deg"]), W["kl_quad"],
+                                           W["kl_terms"], cx, cz)
+                    xi = rng.kl_coefficients(W["seed"], lev, [sid], W["kl_terms"])[0]
+                    t1 = time.perf_counter()
+                    r, sv, _ = H.solve_sample(W, nx, ny, nz, Bm @ xi)
+                    times[m].append(time.perf_counter() - t1)
+                    for c, ref in enumerate((r, sv)):
+                        errs[c] = max(errs[c], abs(q[2 * k + c] - ref) / abs(ref))
+                out["qoi_parity"] = {"pairs": "4 level-0 solves, 1 level-1 pair", "max_rel_err":
+                                     {"reaction": errs[0], "stress": errs[1]},
+                                     "note": "GPU vs oracle (FP64 Hex8, SuperLU) on the same xi"}
+                out["cpu_baseline"] = {"kind": "oracle", "cores": 1,
+                                       "seconds_per_solve": {"mesh0": round(float(np.mean(times[0])), 3),
+                                                             "mesh1": round(float(np.mean(times[1])), 3)},
+                                       "sample": "the parity solves above; meshes 2 and 3 not timed (over ten "
+                                                 "minutes per SuperLU solve)"}
+        finally:
+            B.mlmc3d_destroy(ctx)
+    return out
+
+
+def run_hex3d_case():
+    """One step of the 3D Hex8 block (every level's samples), untimed: for profilers."""
+    import torch
+    from paper_1907_10271_gb300 import binding as B
+    from workloads import HEX8_MIXED_4LEVEL as W
+    ctx = B.mlmc3d_create(B.config3_from_workload(W), torch.cuda.current_stream().cuda_stream)
+    failed = 0
+    for lev, n in enumerate(W["n_per_level"]):
+        qf, qc, st = np.zeros(2 * n), np.zeros(2 * n), np.zeros(n, dtype=np.int32)
+        B.mlmc3d_sample_level(ctx, lev, 0, n, qf, qc, st)
+        failed += int((st != 0).sum())
+    torch.cuda.synchronize()
+    B.mlmc3d_destroy(ctx)
+    print(json.dumps({"case": "hex3d", "level_pairs": sum(W["n_per_level"]), "failed": failed}))
+
+
 def main():
     a = parse()
     rank, _, world = dist_env()
     if a.case == "small":
         run_small_case()
+        return
+    if a.case == "hex3d":
+        run_hex3d_case()
         return
     if a.impl == "reference":
         if rank != 0:
@@ -608,6 +720,9 @@ def main():
     if rank == 0 and out is not None and world == 1 and a.serving:
         from paper_1907_10271_gb300 import binding as B
         out["serving"] = run_serving(B, STRIP_MIXED_5LEVEL)
+    if rank == 0 and out is not None and world == 1 and a.hex3d:
+        from paper_1907_10271_gb300 import binding as B
+        out["hex3d"] = run_hex3d(B, parity=not a.no_cpu_baseline)
     if rank == 0 and out is not None:
         if world == 1 and not a.no_cpu_baseline:
             cores = os.cpu_count() or 1
