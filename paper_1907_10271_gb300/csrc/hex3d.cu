@@ -16,17 +16,17 @@
 // refinement residual.
 #include <cfloat>
 
+#include "dfloat.cuh"
 #include "hex3d.cuh"
 
 namespace mlmc3 {
+
+using mlmc::DF;
 
 namespace {
 
 __constant__ Harmonics g_harm;
 
-struct alignas(32) D4 {   // one node of a double vector (u, v, w, unused)
-  double x, y, z, w;
-};
 
 template <typename T>
 struct V3 {
@@ -40,9 +40,17 @@ template <typename T>
 __device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) {
   return V3<T>{a.x - b.x, a.y - b.y, a.z - b.z};
 }
-template <typename T>
-__device__ __forceinline__ V3<T> operator*(T s, V3<T> a) {
+template <typename T, typename S>
+__device__ __forceinline__ V3<T> operator*(S s, V3<T> a) {
   return V3<T>{s * a.x, s * a.y, s * a.z};
+}
+template <typename T>
+__device__ __forceinline__ T zero_of() {
+  return T{};
+}
+template <typename T>
+__device__ __forceinline__ V3<T> zero3() {
+  return V3<T>{zero_of<T>(), zero_of<T>(), zero_of<T>()};
 }
 
 // The 13 monoclinic entries at one angle, from (c2, s2, c4, s4).
@@ -91,9 +99,9 @@ struct GW {
 };
 
 // out[g1][g2] = sum_{a1, a2} w(a1, g1) w(a2, g2) in[a1][a2] (and its transpose: the same)
-template <typename T>
+template <typename T, typename S>
 __device__ __forceinline__ void interp2(const V3<T> in[2][2], V3<T> out[2][2]) {
-  const T wp = GW<T>::wp, wm = GW<T>::wm;
+  const S wp = GW<S>::wp, wm = GW<S>::wm;
   V3<T> t[2][2];
 #pragma unroll
   for (int g = 0; g < 2; ++g)
@@ -105,32 +113,33 @@ __device__ __forceinline__ void interp2(const V3<T> in[2][2], V3<T> out[2][2]) {
     for (int g2 = 0; g2 < 2; ++g2) out[g1][g2] = wp * t[g1][g2] + wm * t[g1][1 - g2];
 }
 
-// f = K_e u for the cube element of side h; u, f indexed [ax][ay][az].
-template <typename T>
-__device__ __forceinline__ void element_apply(const Cm<T>& C, T h, const V3<T> u[2][2][2], V3<T> f[2][2][2]) {
+// f = K_e u for the cube element of side h; u, f indexed [ax][ay][az]. T is the value
+// type (float, float-float or double), S the scalar type of the stiffness and weights.
+template <typename T, typename S>
+__device__ __forceinline__ void element_apply(const Cm<S>& C, S h, const V3<T> u[2][2][2], V3<T> f[2][2][2]) {
   V3<T> D[2][2], Gx[2][2], Gy[2][2], Gz[2][2];
-  const T ih = (T)1 / h;
+  const S ih = (S)1 / h;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b) D[a][b] = ih * (u[1][a][b] - u[0][a][b]);   // x edges, [ay][az]
-  interp2(D, Gx);                                                            // Gx[gy][gz]
+  interp2<T, S>(D, Gx);                                                      // Gx[gy][gz]
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b) D[a][b] = ih * (u[a][1][b] - u[a][0][b]);   // y edges, [ax][az]
-  interp2(D, Gy);                                                            // Gy[gx][gz]
+  interp2<T, S>(D, Gy);                                                      // Gy[gx][gz]
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b) D[a][b] = ih * (u[a][b][1] - u[a][b][0]);   // z edges, [ax][ay]
-  interp2(D, Gz);                                                            // Gz[gx][gy]
+  interp2<T, S>(D, Gz);                                                      // Gz[gx][gy]
   // stresses at the 8 points, summed into the fluxes of each derivative direction
   V3<T> Sx[2][2], Sy[2][2], Sz[2][2];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) Sx[a][b] = Sy[a][b] = Sz[a][b] = V3<T>{0, 0, 0};
+    for (int b = 0; b < 2; ++b) Sx[a][b] = Sy[a][b] = Sz[a][b] = zero3<T>();
 #pragma unroll
   for (int gx = 0; gx < 2; ++gx)
 #pragma unroll
@@ -151,15 +160,15 @@ __device__ __forceinline__ void element_apply(const Cm<T>& C, T h, const V3<T> u
         Sz[gx][gy] = Sz[gx][gy] + V3<T>{s5, s4, s3};
       }
   // transposed passes; Gauss weights 1, det J = (h / 2)^3, dN/dx = sign / h: (h / 2)^3 / h
-  const T wj = h * h / (T)8;
+  const S wj = h * h / (S)8;
   V3<T> A[2][2];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) f[a][b][c] = V3<T>{0, 0, 0};
-  interp2(Sx, A);
+      for (int c = 0; c < 2; ++c) f[a][b][c] = zero3<T>();
+  interp2<T, S>(Sx, A);
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -167,7 +176,7 @@ __device__ __forceinline__ void element_apply(const Cm<T>& C, T h, const V3<T> u
       f[1][a][b] = f[1][a][b] + wj * A[a][b];
       f[0][a][b] = f[0][a][b] - wj * A[a][b];
     }
-  interp2(Sy, A);
+  interp2<T, S>(Sy, A);
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -175,7 +184,7 @@ __device__ __forceinline__ void element_apply(const Cm<T>& C, T h, const V3<T> u
       f[a][1][b] = f[a][1][b] + wj * A[a][b];
       f[a][0][b] = f[a][0][b] - wj * A[a][b];
     }
-  interp2(Sz, A);
+  interp2<T, S>(Sz, A);
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -291,53 +300,89 @@ __global__ void k_dinv(Grid3 g, const float4* __restrict__ trig4, float4* __rest
 
 // ---------------------------------------------------------------- operator
 
-template <typename T>
-__device__ __forceinline__ V3<T> load_node(const float4* x, int64_t n) {
+// Node storage: the FP32 vectors hold one float4 (u, v, w, 0) per node; the refinement
+// iterate d holds float-float pairs, 8 floats per node (u.hi, u.lo, v.hi, v.lo, w.hi,
+// w.lo, 0, 0), so that updating and applying K to it needs no double arithmetic.
+__device__ __forceinline__ V3<float> load_v(const float4* x, int64_t n) {
   const float4 a = x[n];
-  return V3<T>{(T)a.x, (T)a.y, (T)a.z};
+  return V3<float>{a.x, a.y, a.z};
 }
-template <typename T>
-__device__ __forceinline__ V3<T> load_node(const double* x, int64_t n) {
-  const double2 a = reinterpret_cast<const double2*>(x)[2 * n];
-  const double b = x[4 * n + 2];
-  return V3<T>{(T)a.x, (T)a.y, (T)b};
+__device__ __forceinline__ V3<DF> load_v(const float* d, int64_t n) {
+  const float4 a = reinterpret_cast<const float4*>(d)[2 * n], b = reinterpret_cast<const float4*>(d)[2 * n + 1];
+  return V3<DF>{DF{a.x, a.y}, DF{a.z, a.w}, DF{b.x, b.y}};
+}
+__device__ __forceinline__ V3<double> load_d(const float* d, int64_t n) {
+  const V3<DF> v = load_v(d, n);
+  return V3<double>{(double)v.x.hi + (double)v.x.lo, (double)v.y.hi + (double)v.y.lo,
+                    (double)v.z.hi + (double)v.z.lo};
 }
 __device__ __forceinline__ void add_node(float4* y, int64_t n, V3<float> f) {
   atomicAdd(y + n, make_float4(f.x, f.y, f.z, 0.f));
 }
-__device__ __forceinline__ void add_node(double* y, int64_t n, V3<double> f) {
-  atomicAdd(y + 4 * n, f.x);
-  atomicAdd(y + 4 * n + 1, f.y);
-  atomicAdd(y + 4 * n + 2, f.z);
+// float-float contributions are summed in double (the nodes' totals cancel to a small
+// residual; each contribution keeps about 48 bits)
+__device__ __forceinline__ void add_node(double* y, int64_t n, V3<DF> f) {
+  atomicAdd(y + 4 * n, (double)f.x.hi + (double)f.x.lo);
+  atomicAdd(y + 4 * n + 1, (double)f.y.hi + (double)f.y.lo);
+  atomicAdd(y + 4 * n + 2, (double)f.z.hi + (double)f.z.lo);
 }
 
-// one thread per element; y (zeroed by the caller) += K x over all DOFs
-template <typename T, typename X, typename Y>
+__device__ __forceinline__ float dot_part(V3<float> a, V3<float> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float dot_part(V3<DF> a, V3<DF> b) { return 0.f; }
+
+// One thread per element; y (zeroed by the caller) += K x over all DOFs. T: value type
+// (float, or float-float for the refinement residual: the same FP32 stiffness, every
+// intermediate kept to about 48 bits). With `boundary` only the last element column
+// (i = nx - 1), which alone reaches the nodes on x = lx. With `energy` set, also
+// energy[s] += x . K x as the sum of the element energies x_e . K_e x_e (the PCG's
+// p . q when x vanishes on the prescribed DOFs).
+template <typename T, bool ENERGY, typename X, typename Y>
 __global__ void __launch_bounds__(128) k_apply(Grid3 g, const float4* __restrict__ trig4, const X* __restrict__ x,
-                                               Y* __restrict__ y, const int* __restrict__ active) {
+                                               Y* __restrict__ y, const int* __restrict__ active, int boundary,
+                                               double* __restrict__ energy) {
   const int s = blockIdx.y;
-  if (active && !active[s]) return;
+  if (active && !active[s]) return;   // uniform over the block
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= g.elems()) return;
-  const int i = (int)(e % g.nx);
-  const int64_t r = e / g.nx;
-  const int j = (int)(r % g.ny), k = (int)(r / g.ny);
-  const Cm<T> C = coef<T>(trig4[(int64_t)s * g.cols() + (int64_t)k * g.nx + i]);
-  const int64_t base = (int64_t)s * g.nodes();
-  V3<T> u[2][2][2], f[2][2][2];
+  int i = 0, j = 0, k = 0;
+  bool valid;
+  if (boundary) {
+    valid = e < (int64_t)g.ny * g.nz;
+    i = g.nx - 1;
+    j = (int)(e % g.ny);
+    k = (int)(e / g.ny);
+  } else {
+    valid = e < g.elems();
+    i = (int)(e % g.nx);
+    const int64_t r = e / g.nx;
+    j = (int)(r % g.ny);
+    k = (int)(r / g.ny);
+  }
+  float en = 0.f;
+  if (valid) {
+    const Cm<float> C = coef<float>(trig4[(int64_t)s * g.cols() + (int64_t)k * g.nx + i]);
+    const int64_t base = (int64_t)s * g.nodes();
+    V3<T> u[2][2][2], f[2][2][2];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < 2; ++b)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) u[a][b][c] = load_node<T>(x, base + node_of(g, i + a, j + b, k + c));
-  element_apply<T>(C, (T)g.h, u, f);
+        for (int c = 0; c < 2; ++c) u[a][b][c] = load_v(x, base + node_of(g, i + a, j + b, k + c));
+    element_apply<T, float>(C, g.h, u, f);
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < 2; ++b)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) add_node(y, base + node_of(g, i + a, j + b, k + c), f[a][b][c]);
+        for (int c = 0; c < 2; ++c) {
+          add_node(y, base + node_of(g, i + a, j + b, k + c), f[a][b][c]);
+          if (ENERGY) en += dot_part(u[a][b][c], f[a][b][c]);
+        }
+  }
+  if (ENERGY) {   // every thread of the block reaches the reduction
+    const double t = block_sum((double)en);
+    if (threadIdx.x == 0) atomicAdd(&energy[s], t);
+  }
 }
 
 // ---------------------------------------------------------------- coarsest mesh
@@ -371,7 +416,7 @@ __global__ void __launch_bounds__(256) k_coarsest_setup(Grid3 g, const float4* _
       if (qc == 1) uq.y = 1.f;
       if (qc == 2) uq.z = 1.f;
     }
-    element_apply<float>(C, g.h, u, f);
+    element_apply<float, float>(C, g.h, u, f);
     const int col = 3 * (int)node_of(g, i + (qa & 1), j + ((qa >> 1) & 1), k + (qa >> 2)) + qc;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -642,15 +687,18 @@ __global__ void k_check(State3 S, int n, int it, int max_iter, int slot) {
 
 // ---------------------------------------------------------------- refinement and outputs
 
-__global__ void k_lift(Grid3 g, double shortening, double* __restrict__ d, float4* __restrict__ xl) {
+// d = the lifting (u = -shortening on x = lx, as the float-float pair (hi, lo)); xl its FP32 copy
+__global__ void k_lift(Grid3 g, float u_hi, float u_lo, float* __restrict__ d, float4* __restrict__ xl) {
   const int s = blockIdx.y;
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (n >= g.nodes()) return;
   const int i = (int)(n % (g.nx + 1));
   const int64_t q = (int64_t)s * g.nodes() + n;
-  const double u = (i == g.nx) ? -shortening : 0.0;
-  reinterpret_cast<D4*>(d)[q] = D4{u, 0.0, 0.0, 0.0};
-  xl[q] = make_float4((float)u, 0.f, 0.f, 0.f);
+  const bool end = i == g.nx;
+  float4* d4 = reinterpret_cast<float4*>(d);
+  d4[2 * q] = make_float4(end ? u_hi : 0.f, end ? u_lo : 0.f, 0.f, 0.f);
+  d4[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  xl[q] = make_float4(end ? u_hi : 0.f, 0.f, 0.f, 0.f);
 }
 
 // r = -(K x_lift) on free DOFs; ||r||^2 = ||f||^2
@@ -673,51 +721,71 @@ __global__ void k_lift_resid(Grid3 g, State3 S, const float4* __restrict__ t, fl
   }
 }
 
-__global__ void k_update_d(Grid3 g, State3 S, const float4* __restrict__ x, double* __restrict__ d) {
+// float-float d += float x (TwoSum of the heads, the tail added, renormalised)
+__device__ __forceinline__ DF df_add(DF a, float x) {
+  DF t = mlmc::two_sum(a.hi, x);
+  t.lo = __fadd_rn(t.lo, a.lo);
+  return mlmc::fast_two_sum(t.hi, t.lo);
+}
+
+__global__ void k_update_d(Grid3 g, State3 S, const float4* __restrict__ x, float* __restrict__ d) {
   const int s = blockIdx.y;
   if (!S.outer_active[s]) return;
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (n >= g.nodes()) return;
   const int64_t q = (int64_t)s * g.nodes() + n;
   const float4 xx = x[q];
-  D4 dd = reinterpret_cast<D4*>(d)[q];
-  dd.x += xx.x;
-  dd.y += xx.y;
-  dd.z += xx.z;
-  reinterpret_cast<D4*>(d)[q] = dd;
+  V3<DF> v = load_v(d, q);
+  v.x = df_add(v.x, xx.x);
+  v.y = df_add(v.y, xx.y);
+  v.z = df_add(v.z, xx.z);
+  float4* d4 = reinterpret_cast<float4*>(d);
+  d4[2 * q] = make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo);
+  d4[2 * q + 1] = make_float4(v.z.hi, v.z.lo, 0.f, 0.f);
 }
 
-// kd = K d (double): r = -(K d) on free DOFs (float), ||r||^2 (double); on the final
-// pass also the reaction -sum over x = lx of (K d)_u and d_F . r_F
-__global__ void k_resid64(Grid3 g, State3 S, const double* __restrict__ kd, const double* __restrict__ d,
-                          float4* __restrict__ r, int final_pass) {
+// kd = K d (double sums of float-float contributions): r = -(K d) on free DOFs
+// (float), ||r||^2 (double)
+__global__ void k_resid_exact(Grid3 g, State3 S, const double* __restrict__ kd, float4* __restrict__ r) {
   const int s = blockIdx.y;
-  if (!final_pass && !S.outer_active[s]) return;
+  if (!S.outer_active[s]) return;
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double rr = 0.0, re = 0.0, dr = 0.0;
+  double rr = 0.0;
   if (n < g.nodes()) {
     const int i = (int)(n % (g.nx + 1));
     const int64_t q = (int64_t)s * g.nodes() + n;
-    const D4 k4 = reinterpret_cast<const D4*>(kd)[q];
-    double rx = -k4.x, ry = -k4.y, rzv = -k4.z;
-    if (i == g.nx) re = -k4.x;
+    const double* k4 = kd + 4 * q;
+    double rx = -k4[0], ry = -k4[1], rzv = -k4[2];
     if (i == 0) rx = ry = rzv = 0.0;
     if (i == g.nx) rx = 0.0;
-    r[q] = make_float4((float)rx, (float)ry, (float)rzv, 0.f);
-    rr = rx * rx + ry * ry + rzv * rzv;
-    if (final_pass) {
-      const D4 dd = reinterpret_cast<const D4*>(d)[q];
-      dr = dd.x * rx + dd.y * ry + dd.z * rzv;
-    }
+    const float4 rf = make_float4((float)rx, (float)ry, (float)rzv, 0.f);
+    r[q] = rf;
+    rr = (double)rf.x * rf.x + (double)rf.y * rf.y + (double)rf.z * rf.z;
   }
   const double a = block_sum(rr);
   if (threadIdx.x == 0) atomicAdd(&S.rr[s], a);
-  if (final_pass) {
-    const double b = block_sum(re);
-    if (threadIdx.x == 0) atomicAdd(&S.react[s], b);
-    const double c = block_sum(dr);
-    if (threadIdx.x == 0) atomicAdd(&S.dr[s], c);
+}
+
+// final pass: the reaction -sum over x = lx of (K d)_u (kd from the last element column
+// only, complete on those nodes) and d_F . r_F with the latest residual r (zero on the
+// prescribed DOFs)
+__global__ void k_final(Grid3 g, State3 S, const double* __restrict__ kd, const float* __restrict__ d,
+                        const float4* __restrict__ r) {
+  const int s = blockIdx.y;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double re = 0.0, dr = 0.0;
+  if (n < g.nodes()) {
+    const int i = (int)(n % (g.nx + 1));
+    const int64_t q = (int64_t)s * g.nodes() + n;
+    if (i == g.nx) re = -kd[4 * q];
+    const float4 rr = r[q];
+    const V3<double> dd = load_d(d, q);
+    dr = dd.x * rr.x + dd.y * rr.y + dd.z * rr.z;
   }
+  const double a = block_sum(re);
+  if (threadIdx.x == 0) atomicAdd(&S.react[s], a);
+  const double b = block_sum(dr);
+  if (threadIdx.x == 0) atomicAdd(&S.dr[s], b);
 }
 
 // per sample: start an inner solve with tolerance max(floor, 0.5 rtol ||f|| / ||r||)
@@ -746,7 +814,7 @@ __global__ void k_outer_check(State3 S, int n, double rtol, int* outer_count) {
 
 // max over elements with centroid x in [x0, x1] of max(0, -a1 . sigma a1) at the
 // centroid, a1 = (cos t, 0, -sin t) the rotated fibre direction
-__global__ void k_stress(Grid3 g, State3 S, const float4* __restrict__ trig4, const double* __restrict__ d,
+__global__ void k_stress(Grid3 g, State3 S, const float4* __restrict__ trig4, const float* __restrict__ d,
                          double x0, double x1) {
   const int s = blockIdx.y;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -764,12 +832,12 @@ __global__ void k_stress(Grid3 g, State3 S, const float4* __restrict__ trig4, co
       V3<double> gx{0, 0, 0}, gy{0, 0, 0}, gz{0, 0, 0};
       for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) {
-          gx = gx + (load_node<double>(d, base + node_of(g, i + 1, j + a, k + b)) -
-                     load_node<double>(d, base + node_of(g, i, j + a, k + b)));
-          gy = gy + (load_node<double>(d, base + node_of(g, i + a, j + 1, k + b)) -
-                     load_node<double>(d, base + node_of(g, i + a, j, k + b)));
-          gz = gz + (load_node<double>(d, base + node_of(g, i + a, j + b, k + 1)) -
-                     load_node<double>(d, base + node_of(g, i + a, j + b, k)));
+          gx = gx + (load_d(d, base + node_of(g, i + 1, j + a, k + b)) -
+                     load_d(d, base + node_of(g, i, j + a, k + b)));
+          gy = gy + (load_d(d, base + node_of(g, i + a, j + 1, k + b)) -
+                     load_d(d, base + node_of(g, i + a, j, k + b)));
+          gz = gz + (load_d(d, base + node_of(g, i + a, j + b, k + 1)) -
+                     load_d(d, base + node_of(g, i + a, j + b, k)));
         }
       const double f = 0.25 / (double)g.h;
       gx = f * gx;
@@ -836,15 +904,19 @@ cudaError_t launch_dinv(const Grid3& g, const float* trig4, float4* dinv, cudaSt
   return cudaGetLastError();
 }
 cudaError_t launch_apply(const Grid3& g, const float* trig4, const float4* x, float4* y, const int* active,
-                         cudaStream_t st) {
-  k_apply<float><<<dim3(blocks(g.elems(), 128), g.nsamp), 128, 0, st>>>(g, reinterpret_cast<const float4*>(trig4),
-                                                                         x, y, active);
+                         cudaStream_t st, double* energy) {
+  const dim3 grid(blocks(g.elems(), 128), g.nsamp);
+  if (energy)
+    k_apply<float, true><<<grid, 128, 0, st>>>(g, reinterpret_cast<const float4*>(trig4), x, y, active, 0, energy);
+  else
+    k_apply<float, false><<<grid, 128, 0, st>>>(g, reinterpret_cast<const float4*>(trig4), x, y, active, 0, nullptr);
   return cudaGetLastError();
 }
-cudaError_t launch_apply64(const Grid3& g, const float* trig4, const double* d, double* y, const int* active,
-                           cudaStream_t st) {
-  k_apply<double><<<dim3(blocks(g.elems(), 128), g.nsamp), 128, 0, st>>>(g, reinterpret_cast<const float4*>(trig4),
-                                                                          d, y, active);
+cudaError_t launch_apply_df(const Grid3& g, const float* trig4, const float* d, double* y, const int* active,
+                            bool boundary, cudaStream_t st) {
+  const int64_t n = boundary ? (int64_t)g.ny * g.nz : g.elems();
+  k_apply<DF, false><<<dim3(blocks(n, 128), g.nsamp), 128, 0, st>>>(g, reinterpret_cast<const float4*>(trig4), d, y, active,
+                                                             boundary ? 1 : 0, nullptr);
   return cudaGetLastError();
 }
 cudaError_t launch_coarsest_setup(const Grid3& g, const float* trig4, float* ainv, cudaStream_t st) {
@@ -906,21 +978,26 @@ cudaError_t launch_check(const State3& S, int n, int it, int max_iter, int slot,
   k_check<<<blocks(n, 128), 128, 0, st>>>(S, n, it, max_iter, slot);
   return cudaGetLastError();
 }
-cudaError_t launch_lift(const Grid3& g, double shortening, double* d, float4* xl, cudaStream_t st) {
-  k_lift<<<dim3(blocks(g.nodes(), 256), g.nsamp), 256, 0, st>>>(g, shortening, d, xl);
+cudaError_t launch_lift(const Grid3& g, double shortening, float* d, float4* xl, cudaStream_t st) {
+  const float hi = (float)(-shortening), lo = (float)(-shortening - (double)hi);
+  k_lift<<<dim3(blocks(g.nodes(), 256), g.nsamp), 256, 0, st>>>(g, hi, lo, d, xl);
   return cudaGetLastError();
 }
 cudaError_t launch_lift_resid(const Grid3& g, const State3& S, const float4* t, float4* r, cudaStream_t st) {
   k_lift_resid<<<dim3(blocks(g.nodes(), 256), g.nsamp), 256, 0, st>>>(g, S, t, r);
   return cudaGetLastError();
 }
-cudaError_t launch_update_d(const Grid3& g, const State3& S, const float4* x, double* d, cudaStream_t st) {
+cudaError_t launch_update_d(const Grid3& g, const State3& S, const float4* x, float* d, cudaStream_t st) {
   k_update_d<<<dim3(blocks(g.nodes(), 256), g.nsamp), 256, 0, st>>>(g, S, x, d);
   return cudaGetLastError();
 }
-cudaError_t launch_resid64(const Grid3& g, const State3& S, const double* kd, const double* d, float4* r,
-                           double /*shortening*/, bool final_pass, cudaStream_t st) {
-  k_resid64<<<dim3(blocks(g.nodes(), 256), g.nsamp), 256, 0, st>>>(g, S, kd, d, r, final_pass ? 1 : 0);
+cudaError_t launch_resid_exact(const Grid3& g, const State3& S, const double* kd, float4* r, cudaStream_t st) {
+  k_resid_exact<<<dim3(blocks(g.nodes(), 256), g.nsamp), 256, 0, st>>>(g, S, kd, r);
+  return cudaGetLastError();
+}
+cudaError_t launch_final(const Grid3& g, const State3& S, const double* kd, const float* d, const float4* r,
+                         cudaStream_t st) {
+  k_final<<<dim3(blocks(g.nodes(), 256), g.nsamp), 256, 0, st>>>(g, S, kd, d, r);
   return cudaGetLastError();
 }
 cudaError_t launch_inner_begin(const State3& S, int n, double rtol, double floor_tol, int, cudaStream_t st) {
@@ -931,7 +1008,7 @@ cudaError_t launch_outer_check(const State3& S, int n, double rtol, int* outer_c
   k_outer_check<<<blocks(n, 128), 128, 0, st>>>(S, n, rtol, outer_count);
   return cudaGetLastError();
 }
-cudaError_t launch_stress(const Grid3& g, const State3& S, const float* trig4, const double* d, double x0, double x1,
+cudaError_t launch_stress(const Grid3& g, const State3& S, const float* trig4, const float* d, double x0, double x1,
                           cudaStream_t st) {
   k_stress<<<dim3(blocks(g.elems(), 128), g.nsamp), 128, 0, st>>>(g, S, reinterpret_cast<const float4*>(trig4), d,
                                                                    x0, x1);

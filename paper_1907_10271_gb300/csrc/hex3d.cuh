@@ -50,12 +50,15 @@ cudaError_t launch_expand_trig(const float* trig2, int64_t n_cols_total, float* 
 cudaError_t launch_average_trig(const Grid3& fine, const float* tf, float* tc, cudaStream_t st);
 // Dinv = omega / diag(K) per DOF, zero on prescribed DOFs
 cudaError_t launch_dinv(const Grid3& g, const float* trig4, float4* dinv, cudaStream_t st);
-// y += K x (FP32, every DOF, unmasked); only samples with active[s] (null: all)
+// y += K x (FP32, every DOF, unmasked); only samples with active[s] (null: all); with
+// energy set also energy[s] += x . K x (summed over elements)
 cudaError_t launch_apply(const Grid3& g, const float* trig4, const float4* x, float4* y, const int* active,
-                         cudaStream_t st);
-// y += K d in double ([sample][node][4] doubles)
-cudaError_t launch_apply64(const Grid3& g, const float* trig4, const double* d, double* y, const int* active,
-                           cudaStream_t st);
+                         cudaStream_t st, double* energy = nullptr);
+// y += K d for the float-float iterate d ([sample][node][8] floats: u, v, w as (hi, lo)),
+// float-float element arithmetic summed into y in double ([sample][node][4] doubles);
+// with boundary only the last element column (the x = lx nodes' complete sums)
+cudaError_t launch_apply_df(const Grid3& g, const float* trig4, const float* d, double* y, const int* active,
+                            bool boundary, cudaStream_t st);
 cudaError_t launch_coarsest_setup(const Grid3& g, const float* trig4, float* ainv, cudaStream_t st);
 cudaError_t launch_coarsest_solve(const Grid3& g, const float* ainv, const float4* b, float4* x, const int* active,
                                   cudaStream_t st);
@@ -79,14 +82,17 @@ cudaError_t launch_update_xr(const Grid3& g, const State3& S, const float4* p, c
                              cudaStream_t st);
 cudaError_t launch_check(const State3& S, int n, int it, int max_iter, int slot, cudaStream_t st);
 // refinement
-cudaError_t launch_lift(const Grid3& g, double shortening, double* d, float4* xl, cudaStream_t st);
+cudaError_t launch_lift(const Grid3& g, double shortening, float* d, float4* xl, cudaStream_t st);
 cudaError_t launch_lift_resid(const Grid3& g, const State3& S, const float4* t, float4* r, cudaStream_t st);
-cudaError_t launch_update_d(const Grid3& g, const State3& S, const float4* x, double* d, cudaStream_t st);
-cudaError_t launch_resid64(const Grid3& g, const State3& S, const double* kd, const double* d, float4* r,
-                           double shortening, bool final_pass, cudaStream_t st);
+cudaError_t launch_update_d(const Grid3& g, const State3& S, const float4* x, float* d, cudaStream_t st);
+// r = -(K d) on free DOFs from kd, ||r||^2
+cudaError_t launch_resid_exact(const Grid3& g, const State3& S, const double* kd, float4* r, cudaStream_t st);
+// reaction from the boundary column's kd, d_F . r_F from the latest residual
+cudaError_t launch_final(const Grid3& g, const State3& S, const double* kd, const float* d, const float4* r,
+                         cudaStream_t st);
 cudaError_t launch_inner_begin(const State3& S, int n, double rtol, double floor_tol, int outer, cudaStream_t st);
 cudaError_t launch_outer_check(const State3& S, int n, double rtol, int* outer_count, cudaStream_t st);
-cudaError_t launch_stress(const Grid3& g, const State3& S, const float* trig4, const double* d, double x0, double x1,
+cudaError_t launch_stress(const Grid3& g, const State3& S, const float* trig4, const float* d, double x0, double x1,
                           cudaStream_t st);
 cudaError_t launch_qoi(const State3& S, int n, double shortening, double* q, int* status, cudaStream_t st);
 cudaError_t launch_zero4(float4* v, int64_t n, cudaStream_t st);

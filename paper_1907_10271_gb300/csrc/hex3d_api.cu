@@ -6,10 +6,12 @@
 // every coarser multigrid mesh averages its children's 4-vectors (rediscretisation
 // with the averaged rotated stiffness). The FP32 PCG, preconditioned by one V(1,1)
 // cycle, runs on all samples in lock step with per-sample scalars and convergence
-// flags. Refinement: the lifting residual (FP32) starts the first inner solve; after
-// its correction the residual f - K d is formed in double; later corrections take
-// the inner CG's recursive residual. A final double-precision K d gives the
-// energy-consistent reaction R - (d_F . r_F) / shortening and the centroid stresses.
+// flags. Refinement: the iterate d is float-float; the lifting residual (FP32) starts
+// the first inner solve; after its correction the residual f - K d is formed with
+// float-float element arithmetic summed in double; later corrections take the inner
+// CG's recursive residual. The final pass forms K d on the x = lx nodes only (the last
+// element column) for the energy-consistent reaction R - (d_F . r_F) / shortening, and
+// the centroid stresses.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -231,7 +233,8 @@ struct Bufs {
   std::vector<float*> trig;              // per MG level [n][cols][4]
   std::vector<float4*> dinv, b, x, t;    // per MG level (b unused at 0: r)
   float4 *r, *p, *q, *xs, *xl;           // top: residual, search direction, K p, PCG iterate, lifting
-  double *d, *kd;
+  float* d;                              // refinement iterate, float-float, 8 floats per node
+  double* kd;                            // K d, 4 doubles per node
   float* ainv;
   State3 S;
   int* outer_count;
@@ -259,7 +262,7 @@ void plan(A& a, const std::vector<Grid3>& G, int n, Bufs& B) {
   B.q = a.template take<float4>(nv);
   B.xs = a.template take<float4>(nv);
   B.xl = a.template take<float4>(nv);
-  B.d = a.template take<double>(4 * nv);
+  B.d = a.template take<float>(8 * nv);
   B.kd = a.template take<double>(4 * nv);
   const size_t nc = 3 * (size_t)G.back().nodes();
   B.ainv = a.template take<float>((size_t)n * nc * nc);
@@ -345,8 +348,7 @@ mlmc_status solve3(mlmc3d_ctx& c, int m, int n, const float* trig2, double* q, i
         if (vs != MLMC_OK) return vs;
         CK(mlmc3::launch_beta(S, n, it == 0 ? 1 : 0, st), "beta");
         CK(mlmc3::launch_update_p(G[0], S, B.x[0], B.p, B.q, st), "update_p");
-        CK(mlmc3::launch_apply(G[0], B.trig[0], B.p, B.q, S.active, st), "apply");
-        CK(mlmc3::launch_dot_pq(G[0], S, B.p, B.q, st), "dot_pq");
+        CK(mlmc3::launch_apply(G[0], B.trig[0], B.p, B.q, S.active, st, S.pq), "apply");   // q = K p, p . q
         CK(mlmc3::launch_alpha(S, n, st), "alpha");
         CK(mlmc3::launch_update_xr(G[0], S, B.p, B.q, B.xs, B.r, st), "update_xr");
         CK(mlmc3::launch_check(S, n, it, c.max_iter, b, st), "check");
@@ -358,19 +360,19 @@ mlmc_status solve3(mlmc3d_ctx& c, int m, int n, const float* trig2, double* q, i
     }
     max_it_seen = std::max(max_it_seen, it);
     CK(mlmc3::launch_update_d(G[0], S, B.xs, B.d, st), "update_d");
-    if (outer == 0) {   // the double-precision residual after the first correction
+    if (outer == 0) {   // the exact (float-float) residual after the first correction
       CK(cudaMemsetAsync(B.kd, 0, sizeof(double) * 4 * nv0, st), "memset");
       CK(cudaMemsetAsync(S.rr, 0, sizeof(double) * n, st), "memset");
-      CK(mlmc3::launch_apply64(G[0], B.trig[0], B.d, B.kd, S.outer_active, st), "apply64");
-      CK(mlmc3::launch_resid64(G[0], S, B.kd, B.d, B.r, c.cfg.shortening, false, st), "resid64");
+      CK(mlmc3::launch_apply_df(G[0], B.trig[0], B.d, B.kd, S.outer_active, false, st), "apply_df");
+      CK(mlmc3::launch_resid_exact(G[0], S, B.kd, B.r, st), "resid_exact");
     }
   }
   c.last_iters = max_it_seen;
-  // final double-precision pass: reaction, d . r, stresses
+  // final pass: K d on the x = lx nodes (last element column) for the reaction, d . r
+  // with the latest residual, stresses
   CK(cudaMemsetAsync(B.kd, 0, sizeof(double) * 4 * nv0, st), "memset");
-  CK(cudaMemsetAsync(S.rr, 0, sizeof(double) * n, st), "memset");
-  CK(mlmc3::launch_apply64(G[0], B.trig[0], B.d, B.kd, nullptr, st), "apply64");
-  CK(mlmc3::launch_resid64(G[0], S, B.kd, B.d, B.r, c.cfg.shortening, true, st), "resid64");
+  CK(mlmc3::launch_apply_df(G[0], B.trig[0], B.d, B.kd, nullptr, true, st), "apply_df");
+  CK(mlmc3::launch_final(G[0], S, B.kd, B.d, B.r, st), "final");
   CK(mlmc3::launch_stress(G[0], S, B.trig[0], B.d, c.cfg.omega_x0, c.cfg.omega_x1, st), "stress");
   CK(mlmc3::launch_qoi(S, n, c.cfg.shortening, q, status, st), "qoi");
   CK(cudaStreamSynchronize(st), "solve");
