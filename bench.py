@@ -64,6 +64,8 @@ def parse():
                          "step of the 3D Hex8 block (both for profilers)")
     ap.add_argument("--no-hex3d", dest="hex3d", action="store_false",
                     help="skip the 3D Hex8 block measurement")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the library's default launch shapes instead of running mlmc_autotune first")
     ap.add_argument("--cpu-fraction", type=float, default=1.0 / 32.0,
                     help="fraction of each level's samples the CPU oracle times")
     return ap.parse_args()
@@ -296,6 +298,9 @@ def run_gpu(a):
     def step(k, q1, q2, s):
         B.mlmc_sample_levels(ctx, levels, first_ids(k), counts, q1, q2, s)
 
+    # launch shapes and the nested-iteration switch picked by the library's autotuner on
+    # this workload, before (and outside) the warm-up and timed steps
+    tuning = B.mlmc_autotune(ctx, levels, counts, reps=1) if a.autotune else B.mlmc_get_tuning(ctx)
     for k in range(a.warmup):
         step(k, qf, qc, st)
     torch.cuda.synchronize()
@@ -440,7 +445,9 @@ def run_gpu(a):
                "config": {"workload": cfg["name"], "meshes": "64x16..1024x256 Q1, 2 DOF/node",
                           "samples_per_level": counts, "kl_terms": cfg["kl_terms"], "rtol": cfg["rtol"],
                           "parallelism": f"dp{world} (disjoint sample ids)",
-                          "l2": "flushed (256 MB write) between timed steps"},
+                          "l2": "flushed (256 MB write) between timed steps",
+                          "tuning": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuning.items()},
+                          "tuning_source": "mlmc_autotune (untimed)" if a.autotune else "defaults"},
                "level_pairs_per_step": total, "samples_failed": bad,
                "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                        "d2h_bytes_per_step": total * (2 * 16 + 4),

@@ -135,6 +135,29 @@ mlmc_status mlmc_sample_level(mlmc_ctx* ctx, int32_t level, uint64_t first_id, i
    Errors: MLMC_ERR_INVALID_ARG for min_nodes < 0. */
 mlmc_status mlmc_set_nested_threshold(mlmc_ctx* ctx, int64_t min_nodes);
 
+/* Launch shapes of the strip kernels and the nested-iteration switch (see
+   mlmc_autotune). */
+typedef struct {
+  int32_t max_rows;           /* node rows per warp tile, at most (1 .. 64) */
+  int32_t min_rows;           /* rows per tile when small launches split (1 .. max_rows) */
+  double target_waves;        /* launches below this many resident waves split their tiles */
+  int64_t nested_min_nodes;   /* as mlmc_set_nested_threshold */
+  double step_ms;             /* (autotune output) time of the tuned workload with these values */
+} mlmc_tuning;
+
+/* Times the level-pair workload {levels[k], counts[k]} (host arrays of n_req entries,
+   as for mlmc_sample_levels, on sample ids far from any the caller uses) under
+   candidate launch shapes and nested-iteration settings, by coordinate descent
+   (nested iteration on / off, target_waves 0.75 / 1.5 / 3, max_rows 32 / 64, min_rows
+   4 / 6 / 8; one warm-up and `reps` timed calls each, the median kept), and keeps
+   the fastest on the context. The level moments are left as they were. out
+   (nullable) receives the chosen values. Errors as mlmc_sample_levels. */
+mlmc_status mlmc_autotune(mlmc_ctx* ctx, int32_t n_req, const int32_t* levels, const int64_t* counts, int32_t reps,
+                          mlmc_tuning* out);
+mlmc_status mlmc_get_tuning(mlmc_ctx* ctx, mlmc_tuning* out);
+/* Errors: MLMC_ERR_INVALID_ARG for values out of range. */
+mlmc_status mlmc_set_tuning(mlmc_ctx* ctx, const mlmc_tuning* t);
+
 /* Several level pairs in one call: request k asks for counts[k] samples of level
    levels[k] with ids first_ids[k] ..; levels, first_ids and counts are HOST arrays
    of n_req entries, each level at most once per call is solved in one lock-stepped

@@ -114,6 +114,9 @@ def lib():
             "mlmc_solve_theta": (I32, [P, I32, I64, P, P, P, P]),
             "mlmc_sample_levels": (I32, [P, I32, P, P, P, P, P, P]),
             "mlmc_set_nested_threshold": (I32, [P, I64]),
+            "mlmc_autotune": (I32, [P, I32, P, P, I32, P]),
+            "mlmc_get_tuning": (I32, [P, P]),
+            "mlmc_set_tuning": (I32, [P, P]),
             "mlmc_profile_enable": (I32, [P, I32]),
             "mlmc_profile_get": (I32, [P, I32, P, P, P]),
             "mlmc_launch_count": (I32, [P, P]),
@@ -282,6 +285,34 @@ def mlmc_sample_levels(ctx, levels, first_ids, counts, q_fine=None, q_coarse=Non
 
 PROFILE_OPS = ["pcg_update_presmooth", "presmooth", "postsmooth", "postsmooth_top", "search_direction",
                "refinement_residual", "coarsest", "other"]
+
+
+class mlmc_tuning(ctypes.Structure):
+    _fields_ = [("max_rows", ctypes.c_int32), ("min_rows", ctypes.c_int32), ("target_waves", ctypes.c_double),
+                ("nested_min_nodes", ctypes.c_int64), ("step_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(max_rows=self.max_rows, min_rows=self.min_rows, target_waves=self.target_waves,
+                    nested_min_nodes=self.nested_min_nodes, step_ms=self.step_ms)
+
+
+def mlmc_autotune(ctx, levels, counts, reps=2):
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    ct = np.ascontiguousarray(counts, dtype=np.int64)
+    out = mlmc_tuning()
+    _check(ctx, lib().mlmc_autotune(ctx, len(lv), _ptr(lv, np.int32), _ptr(ct, np.int64), reps, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def mlmc_get_tuning(ctx):
+    out = mlmc_tuning()
+    _check(ctx, lib().mlmc_get_tuning(ctx, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def mlmc_set_tuning(ctx, max_rows, min_rows, target_waves, nested_min_nodes):
+    t = mlmc_tuning(max_rows, min_rows, target_waves, nested_min_nodes, 0.0)
+    return _check(ctx, lib().mlmc_set_tuning(ctx, ctypes.byref(t)))
 
 
 def mlmc_set_nested_threshold(ctx, min_nodes):

@@ -577,6 +577,124 @@ mlmc_status mlmc_set_nested_threshold(mlmc_ctx* h, int64_t min_nodes) {
   return MLMC_OK;
 }
 
+mlmc_status mlmc_get_tuning(mlmc_ctx* h, mlmc_tuning* out) {
+  if (!h || !out) return MLMC_ERR_INVALID_ARG;
+  const Context& c = h->c;
+  out->max_rows = c.max_rows;
+  out->min_rows = c.min_rows;
+  out->target_waves = c.target_waves;
+  out->nested_min_nodes = c.nested_min_nodes;
+  out->step_ms = 0.0;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_set_tuning(mlmc_ctx* h, const mlmc_tuning* t) {
+  if (!h || !t) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (t->max_rows < 1 || t->max_rows > 64 || t->min_rows < 1 || t->min_rows > t->max_rows ||
+      !(t->target_waves >= 0.0 && t->target_waves <= 64.0) || t->nested_min_nodes < 0)
+    return c.fail(MLMC_ERR_INVALID_ARG, "tuning value out of range");
+  c.max_rows = t->max_rows;
+  c.min_rows = t->min_rows;
+  c.target_waves = t->target_waves;
+  c.nested_min_nodes = t->nested_min_nodes;
+  return MLMC_OK;
+}
+
+mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, const int64_t* counts, int32_t reps,
+                          mlmc_tuning* out) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (n_req <= 0 || !levels || !counts || reps < 1 || reps > 64) return c.fail(MLMC_ERR_INVALID_ARG, "bad tuning request");
+  std::vector<LevelReq> reqs;
+  int64_t total = 0;
+  for (int k = 0; k < n_req; ++k) {
+    if (levels[k] < 0 || levels[k] >= c.cfg.levels) return c.fail(MLMC_ERR_INVALID_ARG, "level out of range");
+    if (counts[k] < 0) return c.fail(MLMC_ERR_INVALID_ARG, "negative sample count");
+    // sample ids from 2^62 up: the tuning solves draw fields no caller's ids reach
+    if (counts[k] > 0) reqs.push_back(LevelReq{levels[k], (uint64_t)1 << 62, counts[k], total});
+    total += counts[k];
+  }
+  if (reqs.empty()) return c.fail(MLMC_ERR_INVALID_ARG, "empty tuning request");
+  // the tuning solves fold into the moments: keep the caller's and put them back
+  std::vector<mlmc::LevelAcc> saved(c.cfg.levels);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(saved.data(), h->acc_dev, sizeof(mlmc::LevelAcc) * c.cfg.levels, cudaMemcpyDeviceToHost,
+                           c.stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c.stream)) != cudaSuccess)
+    return c.cuda_fail(e, "autotune");
+  std::vector<double> qf(2 * total), qc(2 * total);
+  std::vector<int32_t> st(total);
+  cudaEvent_t e0, e1;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
+    return c.cuda_fail(e, "autotune");
+  struct Cand {
+    int64_t nested;
+    double waves;
+    int max_rows, min_rows;
+  };
+  Cand best{c.nested_min_nodes, c.target_waves, c.max_rows, c.min_rows};
+  double best_ms = 1e300;
+  mlmc_status s = MLMC_OK;
+  auto measure = [&](const Cand& k, double& ms) -> mlmc_status {
+    c.nested_min_nodes = k.nested;
+    c.target_waves = k.waves;
+    c.max_rows = k.max_rows;
+    c.min_rows = k.min_rows;
+    std::vector<double> t;
+    for (int r = 0; r <= reps; ++r) {
+      cudaEventRecord(e0, c.stream);
+      mlmc_status ss = sample_levels_impl(h, reqs, qf.data(), qc.data(), st.data());
+      if (ss != MLMC_OK) return ss;
+      cudaEventRecord(e1, c.stream);
+      cudaEventSynchronize(e1);
+      float v = 0.f;
+      cudaEventElapsedTime(&v, e0, e1);
+      if (r > 0) t.push_back(v);   // the first call warms up
+    }
+    std::sort(t.begin(), t.end());
+    ms = t[t.size() / 2];
+    return MLMC_OK;
+  };
+  auto consider = [&](Cand k) -> mlmc_status {
+    double ms = 0;
+    mlmc_status ss = measure(k, ms);
+    if (ss == MLMC_OK && ms < best_ms) {
+      best_ms = ms;
+      best = k;
+    }
+    return ss;
+  };
+  // coordinate descent from the current values
+  const int64_t nested_vals[2] = {0, (int64_t)1 << 62};
+  const double wave_vals[3] = {0.75, 1.5, 3.0};
+  const int max_vals[2] = {32, 64}, min_vals[3] = {4, 6, 8};
+  for (int64_t v : nested_vals)
+    if (s == MLMC_OK) s = consider(Cand{v, best.waves, best.max_rows, best.min_rows});
+  for (double v : wave_vals)
+    if (s == MLMC_OK) s = consider(Cand{best.nested, v, best.max_rows, best.min_rows});
+  for (int v : max_vals)
+    if (s == MLMC_OK) s = consider(Cand{best.nested, best.waves, v, std::min(best.min_rows, v)});
+  for (int v : min_vals)
+    if (s == MLMC_OK) s = consider(Cand{best.nested, best.waves, best.max_rows, std::min(v, best.max_rows)});
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c.nested_min_nodes = best.nested;
+  c.target_waves = best.waves;
+  c.max_rows = best.max_rows;
+  c.min_rows = best.min_rows;
+  if ((e = cudaMemcpyAsync(h->acc_dev, saved.data(), sizeof(mlmc::LevelAcc) * c.cfg.levels, cudaMemcpyHostToDevice,
+                           c.stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c.stream)) != cudaSuccess)
+    return c.cuda_fail(e, "autotune");
+  if (s != MLMC_OK) return s;
+  if (out) {
+    mlmc_get_tuning(h, out);
+    out->step_ms = best_ms;
+  }
+  return MLMC_OK;
+}
+
 mlmc_status mlmc_profile_enable(mlmc_ctx* h, int32_t on) {
   if (!h) return MLMC_ERR_INVALID_ARG;
   Context& c = h->c;

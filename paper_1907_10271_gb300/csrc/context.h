@@ -129,6 +129,12 @@ struct Context {
   int check_every = 4;            // PCG iterations between host convergence checks
   bool graphs = true;             // replay PCG batches from a CUDA graph captured per solve
   int64_t nested_min_nodes = int64_t(1) << 22;   // finest-mesh nodes per call for nested iteration
+  // launch shapes of the strip kernels (mlmc_autotune): row chunks of at most max_rows
+  // rows; launches of fewer warps than target_waves resident waves split their chunks
+  // (up to 8 ways, at least min_rows rows each)
+  int max_rows = 64;
+  int min_rows = 6;
+  double target_waves = 1.5;
   int last_outer = 0;             // refinement steps of the last solve (diagnostic)
   int last_iters = 0;             // max PCG iterations of the last solve (diagnostic)
 

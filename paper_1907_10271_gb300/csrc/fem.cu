@@ -110,7 +110,7 @@ __device__ __forceinline__ void element_apply_df(const Coef<float>& C, float rx,
 }
 
 // Per-lane sum of one chunk's row products: compensated in float for the FP32 kernels
-// (at most kRowChunk + 1 terms per lane, no double-precision arithmetic per node),
+// (at most 2 * 64 + 1 terms per lane, no double-precision arithmetic per node),
 // plain double for the FP64 kernels. The warp and cross-warp sums are in double.
 template <typename T>
 struct LaneSum;

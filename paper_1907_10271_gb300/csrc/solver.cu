@@ -68,23 +68,23 @@ View<T> base_view(const GroupBuf<T>& g, int k) {
 
 // Assigns the strips of operation op, the row chunks and the work offsets of a strip
 // kernel (warps); returns the total. A mesh's node rows are cut into chunks of equal
-// height, at most kMaxRows (each chunk costs one extra element row and a pipeline
+// height, at most ctx.max_rows (each chunk costs one extra element row and a pipeline
 // fill). A warp walks its rows one after another, so a launch of fewer warps than
-// about one and a half waves (152 SMs x 28 resident warps) is bound by that walk: its
-// views are cut into 2, 4 or 8 times as many chunks (at least kMinRows rows each),
-// which shortens every warp's walk.
+// ctx.target_waves waves (152 SMs x 28 resident warps each) is bound by that walk: its
+// views are cut into 2, 4 or 8 times as many chunks (at least ctx.min_rows rows each),
+// which shortens every warp's walk. mlmc_autotune picks the three parameters.
 template <typename T>
-int finalize_warps(ViewList<T>& L, StripOp op) {
-  constexpr int kTargetWarps = 152 * 28 * 3 / 2;
-  constexpr int kMinRows = 6;
-  constexpr int kMaxRows = 64;
+int finalize_warps(const Context& ctx, ViewList<T>& L, StripOp op) {
+  const int target_warps = (int)(152 * 28 * ctx.target_waves);
+  const int min_rows = std::max(1, ctx.min_rows);
+  const int max_rows = std::min(64, std::max(min_rows, ctx.max_rows));
   auto layout = [&](int split) {
     int acc = 0;
     for (int i = 0; i < L.n; ++i) {
       View<T>& v = L.v[i];
       const int nodes_y = v.g.ny + 1;
-      const int base = chunks_of(v.g.ny, kMaxRows);
-      const int nch = std::max(base, std::min(base * split, nodes_y / kMinRows));
+      const int base = chunks_of(v.g.ny, max_rows);
+      const int nch = std::max(base, std::min(base * split, nodes_y / min_rows));
       v.rows = (nodes_y + nch - 1) / nch;
       v.tiles_x = strips_of(v.g.nx, strip_cols(op));
       v.tiles_y = chunks_of(v.g.ny, v.rows);
@@ -95,7 +95,7 @@ int finalize_warps(ViewList<T>& L, StripOp op) {
     return acc;
   };
   int split = 1, acc = layout(1);
-  while (acc < kTargetWarps && split < 8) acc = layout(split *= 2);
+  while (acc < target_warps && split < 8) acc = layout(split *= 2);
   return acc;
 }
 
@@ -357,7 +357,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         Lsm.v[Lsm.n++] = v;
       }
       if (!Lsm.n) continue;
-      const int tw = finalize_warps(Lsm, d == 0 ? StripOp::PreTop : StripOp::PreR);
+      const int tw = finalize_warps(ctx, Lsm, d == 0 ? StripOp::PreTop : StripOp::PreR);
       if (d == 0) {
         Lsm.prof_op = kProfPreTop;
         MLMC_LAUNCH(kProfPreTop, "pre_top", launch_strip<T>(StripOp::PreTop, Lsm, S, tw, st));
@@ -402,7 +402,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         L.v[L.n++] = v;
       }
       if (!L.n) continue;
-      const int tw = finalize_warps(L, d == 0 ? StripOp::PostTop : StripOp::Post);
+      const int tw = finalize_warps(ctx, L, d == 0 ? StripOp::PostTop : StripOp::Post);
       if (d == 0) {
         L.prof_op = kProfPostTop;
         MLMC_LAUNCH(kProfPostTop, "post_top", launch_strip<T>(StripOp::PostTop, L, S, tw, st));
@@ -414,7 +414,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     MLMC_LAUNCH(kProfOther, "after_post", launch_after_post(S, total, slot, st));
     {
       ViewList<T> L = top_list(StripOp::PcgP, parity);
-      const int tw = finalize_warps(L, StripOp::PcgP);
+      const int tw = finalize_warps(ctx, L, StripOp::PcgP);
       L.prof_op = kProfPcgP;
       MLMC_LAUNCH(kProfPcgP, "pcg_p", launch_strip<T>(StripOp::PcgP, L, S, tw, st));
     }
@@ -739,7 +739,7 @@ mlmc_status apply_operator(Context& ctx, int mesh_level, int64_t n, const T* tri
   v.a = p;
   v.o0 = q;
   L.v[L.n++] = v;
-  const int tw = finalize_warps(L, StripOp::Apply);
+  const int tw = finalize_warps(ctx, L, StripOp::Apply);
   SampleState S;
   std::memset(&S, 0, sizeof(S));
   cudaError_t e = launch_strip<T>(StripOp::Apply, L, S, tw, ctx.stream);

@@ -317,3 +317,28 @@ def test_graph_replay_equals_direct_launches(B):
         np.testing.assert_allclose(out[0][1], out[1][1], rtol=1e-12)
     finally:
         B.mlmc_destroy(ctx)
+
+
+def test_autotune_keeps_results_and_moments(B):
+    """mlmc_autotune leaves the level moments as they were, returns values inside the
+    candidate set, and solves after tuning agree with solves before it (the stated
+    1e-6: tuning changes launch shapes and possibly nested iteration, not the method)."""
+    w = STRIP_MIXED_5LEVEL
+    ctx = B.mlmc_create(B.config_from_workload(w))
+    try:
+        qa = np.zeros(2 * 6)
+        B.mlmc_sample_level(ctx, 2, 5, 6, qa, np.zeros(12))
+        before = B.mlmc_level_stats_get(ctx, 2)
+        t = B.mlmc_autotune(ctx, [0, 1, 2], [64, 16, 6], reps=1)
+        assert t["max_rows"] in (32, 64) and t["min_rows"] in (4, 6, 8)
+        assert t["target_waves"] in (0.75, 1.5, 3.0) and t["nested_min_nodes"] in (0, 1 << 62)
+        assert t["step_ms"] > 0
+        assert B.mlmc_level_stats_get(ctx, 2) == before
+        assert B.mlmc_get_tuning(ctx)["max_rows"] == t["max_rows"]
+        qb = np.zeros(2 * 6)
+        B.mlmc_solve_batch(ctx, [(2, 2, 5 + k) for k in range(6)], qb)
+        np.testing.assert_allclose(qb, qa, rtol=1e-6)
+        with pytest.raises(B.MLMCError):
+            B.mlmc_set_tuning(ctx, 65, 4, 1.5, 0)
+    finally:
+        B.mlmc_destroy(ctx)
