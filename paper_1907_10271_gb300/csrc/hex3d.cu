@@ -431,13 +431,16 @@ __global__ void __launch_bounds__(256) k_coarsest_setup(Grid3 g, const float4* _
         }
   }
   __syncthreads();
-  // prescribed DOFs -> identity
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int r = t / n, c = t % n;
-    const int ir = (r / 3) % (g.nx + 1), ic = (c / 3) % (g.nx + 1);
-    const bool pr = ir == 0 || (ir == g.nx && r % 3 == 0);
-    const bool pc = ic == 0 || (ic == g.nx && c % 3 == 0);
-    if (pr || pc) A[t] = (r == c) ? 1.f : 0.f;
+  // prescribed DOFs -> identity (warps take rows, lanes columns: no division per entry)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  auto prescribed = [&](int dof) {
+    const int i = (dof / 3) % (g.nx + 1);
+    return i == 0 || (i == g.nx && dof % 3 == 0);
+  };
+  for (int r = warp; r < n; r += nw) {
+    const bool pr = prescribed(r);
+    for (int c = lane; c < n; c += 32)
+      if (pr || prescribed(c)) A[r * n + c] = (r == c) ? 1.f : 0.f;
   }
   __syncthreads();
   // Gauss-Jordan inversion in place
@@ -446,12 +449,11 @@ __global__ void __launch_bounds__(256) k_coarsest_setup(Grid3 g, const float4* _
     __syncthreads();
     for (int c = threadIdx.x; c < n; c += blockDim.x) A[p * n + c] = (c == p) ? piv : A[p * n + c] * piv;
     __syncthreads();
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-      const int r = t / n, c = t % n;
+    for (int r = warp; r < n; r += nw) {
       if (r == p) continue;
       const float m = A[r * n + p];
-      if (c == p) continue;
-      A[t] -= m * A[p * n + c];
+      for (int c = lane; c < n; c += 32)
+        if (c != p) A[r * n + c] -= m * A[p * n + c];
     }
     __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x)
