@@ -473,7 +473,8 @@ def run_serving(B, cfg_w, seconds=3.0, load=0.5):
     """The request loop on the selective-refinement workload: failure of the 5-level
     strip when the centroid fibre stress exceeds the 1/150 upper quantile of a seeded
     pilot (seed 1, 4096 level-2 samples); SELECTIVE requests of levels 0..4 in the
-    proportions of the MLMC level counts. Capacity from a saturating burst, then
+    proportions of the MLMC level counts. Capacity from saturating bursts (median of three
+    after a warm-up burst), then
     Poisson arrivals at `load` of it for `seconds`: completed requests/s (each one
     level sample Y_l = Q_l - Q_{l-1}), latency p50/p99, solves per request, and the
     estimate sum_l mean(Y_l) of the failure probability."""
@@ -516,13 +517,20 @@ def run_serving(B, cfg_w, seconds=3.0, load=0.5):
         return res
 
     try:
-        # capacity: a burst of requests at once
-        burst = make(8192)
-        t0 = time.perf_counter()
-        B.mlmc_server_submit(srv, burst)
-        B.mlmc_server_drain(srv, 600e3)
-        cap = len(burst) / (time.perf_counter() - t0)
-        results = drain_all()
+        # capacity: bursts of requests submitted at once; one untimed warm-up burst, then
+        # the median of three (a single ~40 ms burst is sensitive to the host's load)
+        results = []
+        caps = []
+        for b in range(4):
+            burst = make(8192)
+            t0 = time.perf_counter()
+            B.mlmc_server_submit(srv, burst)
+            B.mlmc_server_drain(srv, 600e3)
+            if b > 0:
+                caps.append(len(burst) / (time.perf_counter() - t0))
+            results += drain_all()
+        cap = float(np.median(caps))
+        n_burst = tag[0]
         # Poisson arrivals at `load` of capacity
         rate = load * cap
         n = int(rate * seconds)
@@ -540,7 +548,7 @@ def run_serving(B, cfg_w, seconds=3.0, load=0.5):
                 time.sleep(min(0.001, max(0.0, arrivals[k] - now)))
         B.mlmc_server_drain(srv, 600e3)
         wall = time.perf_counter() - t0
-        stream = [r for r in drain_all() if r["tag"] >= len(burst)]
+        stream = [r for r in drain_all() if r["tag"] >= n_burst]
         counters = B.mlmc_server_counters(srv)
     finally:
         B.mlmc_server_destroy(srv)
@@ -552,6 +560,7 @@ def run_serving(B, cfg_w, seconds=3.0, load=0.5):
                         "in MLMC proportions, 4 workers, 100 GB budget",
             "threshold_pa": threshold,
             "capacity_requests_per_s": round(cap, 1),
+            "capacity_bursts_per_s": [round(c, 1) for c in caps],
             "offered_requests_per_s": round(rate, 1),
             "value": round(len(stream) / wall, 1), "unit": "level-samples/s (Poisson arrivals at %.0f%% of capacity)"
             % (100 * load),

@@ -158,3 +158,27 @@ def test_full_size_level3(B):
 def test_invalid_config(B):
     with pytest.raises(B.MLMCError, match="cubes"):
         B.mlmc3d_create(B.config3_from_workload(W, ly=0.3))
+
+
+def test_edge_arguments(B):
+    ctx = B.mlmc3d_create(B.config3_from_workload(SMALL))
+    try:
+        B.mlmc3d_sample_level(ctx, 1, 0, 0)                 # n = 0: no-op
+        assert B.mlmc3d_level_stats(ctx, 1)["n"] == 0
+        with pytest.raises(B.MLMCError, match="level"):
+            B.mlmc3d_sample_level(ctx, 2, 0, 1, np.zeros(2), np.zeros(2))
+        with pytest.raises(B.MLMCError, match="level"):
+            B.mlmc3d_solve_batch(ctx, [(0, 5, 0)], np.zeros(2))
+        # device outputs (torch) and a level-0 pair (coarse quantities zero)
+        import torch
+        qf = torch.zeros(4, dtype=torch.float64, device="cuda")
+        qc = torch.ones(4, dtype=torch.float64, device="cuda")
+        st = torch.ones(2, dtype=torch.int32, device="cuda")
+        B.mlmc3d_sample_level(ctx, 0, 3, 2, qf, qc, st)
+        torch.cuda.synchronize()
+        assert int(st.abs().sum()) == 0 and float(qc.abs().sum()) == 0.0 and float(qf.min()) > 0
+        assert B.mlmc3d_level_stats(ctx, 0)["n"] == 2
+        B.mlmc3d_reset_stats(ctx)
+        assert B.mlmc3d_level_stats(ctx, 0)["n"] == 0
+    finally:
+        B.mlmc3d_destroy(ctx)

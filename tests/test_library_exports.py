@@ -59,3 +59,14 @@ def test_config3_marshalling():
     assert (c.nx0, c.ny0, c.nz0, c.levels, c.kl_terms) == (32, 8, 4, 4, 200)
     assert (c.G23, c.nu23, c.lz) == (3.5e9, 0.45, 0.125)
     assert abs(c.kl_std - 3.0 * 3.141592653589793 / 180.0) < 1e-15
+
+
+@pytest.mark.parametrize("override,msg", [(dict(ly=0.3), "cubes"), (dict(levels=0), "levels"),
+                                          (dict(kl_terms=0), "kl_terms"), (dict(rtol=0.0), "rtol"),
+                                          (dict(nx0=4, ny0=1, nz0=1, lx=1.0, ly=0.25, lz=0.25), "mesh too small")])
+def test_create3_rejects_invalid_configs_without_a_gpu(override, msg):
+    # validation runs before any CUDA call, so it answers on a machine without a GPU
+    from paper_1907_10271_gb300 import binding
+    from workloads import HEX8_MIXED_4LEVEL
+    with pytest.raises(binding.MLMCError, match=msg):
+        binding.mlmc3d_create(binding.config3_from_workload(HEX8_MIXED_4LEVEL, **override), stream=0)
