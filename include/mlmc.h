@@ -142,14 +142,17 @@ typedef struct {
   int32_t min_rows;           /* rows per tile when small launches split (1 .. max_rows) */
   double target_waves;        /* launches below this many resident waves split their tiles */
   int64_t nested_min_nodes;   /* as mlmc_set_nested_threshold */
+  int32_t fused_bottom;       /* 1: the two smallest non-coarsest multigrid meshes and the coarsest
+                                 solve of each hierarchy run as one launch (mixed precision) */
   double step_ms;             /* (autotune output) time of the tuned workload with these values */
 } mlmc_tuning;
 
 /* Times the level-pair workload {levels[k], counts[k]} (host arrays of n_req entries,
    as for mlmc_sample_levels, on sample ids far from any the caller uses) under
    candidate launch shapes and nested-iteration settings, by coordinate descent
-   (nested iteration on / off, target_waves 0.75 / 1.5 / 3, max_rows 32 / 64, min_rows
-   4 / 6 / 8; one warm-up and `reps` timed calls each, the median kept), and keeps
+   (nested iteration on / off, fused multigrid bottom on / off, target_waves 0.75 /
+   1.5 / 3, max_rows 32 / 64, min_rows 4 / 6 / 8; one warm-up and `reps` timed calls
+   each, the median kept), and keeps
    the fastest on the context. The level moments are left as they were. out
    (nullable) receives the chosen values. Errors as mlmc_sample_levels. */
 mlmc_status mlmc_autotune(mlmc_ctx* ctx, int32_t n_req, const int32_t* levels, const int64_t* counts, int32_t reps,

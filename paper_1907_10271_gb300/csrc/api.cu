@@ -584,6 +584,7 @@ mlmc_status mlmc_get_tuning(mlmc_ctx* h, mlmc_tuning* out) {
   out->min_rows = c.min_rows;
   out->target_waves = c.target_waves;
   out->nested_min_nodes = c.nested_min_nodes;
+  out->fused_bottom = c.fused_bottom ? 1 : 0;
   out->step_ms = 0.0;
   return MLMC_OK;
 }
@@ -592,8 +593,10 @@ mlmc_status mlmc_set_tuning(mlmc_ctx* h, const mlmc_tuning* t) {
   if (!h || !t) return MLMC_ERR_INVALID_ARG;
   Context& c = h->c;
   if (t->max_rows < 1 || t->max_rows > 64 || t->min_rows < 1 || t->min_rows > t->max_rows ||
-      !(t->target_waves >= 0.0 && t->target_waves <= 64.0) || t->nested_min_nodes < 0)
+      !(t->target_waves >= 0.0 && t->target_waves <= 64.0) || t->nested_min_nodes < 0 ||
+      (t->fused_bottom != 0 && t->fused_bottom != 1))
     return c.fail(MLMC_ERR_INVALID_ARG, "tuning value out of range");
+  c.fused_bottom = t->fused_bottom != 0;
   c.max_rows = t->max_rows;
   c.min_rows = t->min_rows;
   c.target_waves = t->target_waves;
@@ -632,8 +635,9 @@ mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, con
     int64_t nested;
     double waves;
     int max_rows, min_rows;
+    bool fused;
   };
-  Cand best{c.nested_min_nodes, c.target_waves, c.max_rows, c.min_rows};
+  Cand best{c.nested_min_nodes, c.target_waves, c.max_rows, c.min_rows, c.fused_bottom};
   double best_ms = 1e300;
   mlmc_status s = MLMC_OK;
   auto measure = [&](const Cand& k, double& ms) -> mlmc_status {
@@ -641,6 +645,7 @@ mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, con
     c.target_waves = k.waves;
     c.max_rows = k.max_rows;
     c.min_rows = k.min_rows;
+    c.fused_bottom = k.fused;
     std::vector<double> t;
     for (int r = 0; r <= reps; ++r) {
       cudaEventRecord(e0, c.stream);
@@ -670,19 +675,22 @@ mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, con
   const double wave_vals[3] = {0.75, 1.5, 3.0};
   const int max_vals[2] = {32, 64}, min_vals[3] = {4, 6, 8};
   for (int64_t v : nested_vals)
-    if (s == MLMC_OK) s = consider(Cand{v, best.waves, best.max_rows, best.min_rows});
+    if (s == MLMC_OK) s = consider(Cand{v, best.waves, best.max_rows, best.min_rows, best.fused});
+  for (bool v : {true, false})
+    if (s == MLMC_OK) s = consider(Cand{best.nested, best.waves, best.max_rows, best.min_rows, v});
   for (double v : wave_vals)
-    if (s == MLMC_OK) s = consider(Cand{best.nested, v, best.max_rows, best.min_rows});
+    if (s == MLMC_OK) s = consider(Cand{best.nested, v, best.max_rows, best.min_rows, best.fused});
   for (int v : max_vals)
-    if (s == MLMC_OK) s = consider(Cand{best.nested, best.waves, v, std::min(best.min_rows, v)});
+    if (s == MLMC_OK) s = consider(Cand{best.nested, best.waves, v, std::min(best.min_rows, v), best.fused});
   for (int v : min_vals)
-    if (s == MLMC_OK) s = consider(Cand{best.nested, best.waves, best.max_rows, std::min(v, best.max_rows)});
+    if (s == MLMC_OK) s = consider(Cand{best.nested, best.waves, best.max_rows, std::min(v, best.max_rows), best.fused});
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c.nested_min_nodes = best.nested;
   c.target_waves = best.waves;
   c.max_rows = best.max_rows;
   c.min_rows = best.min_rows;
+  c.fused_bottom = best.fused;
   if ((e = cudaMemcpyAsync(h->acc_dev, saved.data(), sizeof(mlmc::LevelAcc) * c.cfg.levels, cudaMemcpyHostToDevice,
                            c.stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(c.stream)) != cudaSuccess)

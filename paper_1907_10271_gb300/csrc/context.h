@@ -135,6 +135,9 @@ struct Context {
   int max_rows = 64;
   int min_rows = 6;
   double target_waves = 1.5;
+  // run the two smallest non-coarsest multigrid meshes and the coarsest solve of each
+  // hierarchy in one launch (FP32 path, small enough bottoms)
+  bool fused_bottom = true;
   int last_outer = 0;             // refinement steps of the last solve (diagnostic)
   int last_iters = 0;             // max PCG iterations of the last solve (diagnostic)
 

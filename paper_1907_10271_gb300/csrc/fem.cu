@@ -1232,6 +1232,207 @@ __global__ void k_coarsest_solve(const __grid_constant__ ViewList<T> L, SampleSt
   }
 }
 
+// ---------------------------------------------------------------- multigrid bottom (FP32)
+// Small-mesh pieces of k_bottom; one warp per sample, vectors in shared memory as
+// [node][2] with node = j (nx + 1) + i. Each piece ends with a warp barrier.
+
+// b = mask(R f): full weighting of the fine vector f (nodes of the 2nx x 2ny mesh)
+__device__ __forceinline__ void bot_restrict(const Geo& g, const float* f, float* b, int lane) {
+  const int nxp = g.nx + 1, nxf = 2 * g.nx, nyf = 2 * g.ny;
+  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {
+    const int j = node / nxp, i = node - j * nxp;
+    float su = 0.f, sv = 0.f;
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int jf = 2 * j + dj;
+      if (jf < 0 || jf > nyf) continue;
+      const float wj = dj == 0 ? 1.f : 0.5f;
+      for (int di = -1; di <= 1; ++di) {
+        const int iff = 2 * i + di;
+        if (iff < 0 || iff > nxf) continue;
+        const float ww = wj * (di == 0 ? 1.f : 0.5f);
+        su += ww * f[2 * (jf * (nxf + 1) + iff)];
+        sv += ww * f[2 * (jf * (nxf + 1) + iff) + 1];
+      }
+    }
+    b[2 * node] = dir_u(i, g.nx) ? 0.f : su;
+    b[2 * node + 1] = dir_v(i) ? 0.f : sv;
+  }
+  __syncwarp();
+}
+
+// y = W v (pair-block smoother: u takes its pair partner's term, column i ^ 1), plus add
+__device__ __forceinline__ void bot_smooth(const Geo& g, const float* winv, const float* wc, const float* v,
+                                           const float* add, float* y, int lane) {
+  const int nxp = g.nx + 1;
+  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {
+    const int j = node / nxp, i = node - j * nxp;
+    const int ip = i ^ 1;
+    const float other = ip <= g.nx ? v[2 * (j * nxp + ip)] : 0.f;
+    const float2 w = reinterpret_cast<const float2*>(winv)[node];
+    float u = w.x * v[2 * node] + wc[node] * other, vv = w.y * v[2 * node + 1];
+    if (add) {
+      u += add[2 * node];
+      vv += add[2 * node + 1];
+    }
+    y[2 * node] = u;
+    y[2 * node + 1] = vv;
+  }
+  __syncwarp();
+}
+
+// t = K x (t zeroed here); element (i, j) has corners (i, j) (i+1, j) (i+1, j+1) (i, j+1)
+__device__ __forceinline__ void bot_apply(const Invariants& U, const Geo& g, const float* trig, const float* x,
+                                          float* t, int lane) {
+  const int nxp = g.nx + 1;
+  for (int r = lane; r < 2 * nxp * (g.ny + 1); r += 32) t[r] = 0.f;
+  __syncwarp();
+  const float rx = (float)g.rx, ry = (float)g.ry, w = (float)g.w;
+  for (int e = lane; e < g.nx * g.ny; e += 32) {
+    const int j = e / g.nx, i = e - j * g.nx;
+    const float4 tr = reinterpret_cast<const float4*>(trig)[e];
+    const int k1 = j * nxp + i, k2 = k1 + 1, k3 = k1 + nxp + 1, k4 = k1 + nxp;
+    const V2<float> n1 = v2<float>(x[2 * k1], x[2 * k1 + 1]), n2 = v2<float>(x[2 * k2], x[2 * k2 + 1]);
+    const V2<float> n3 = v2<float>(x[2 * k3], x[2 * k3 + 1]), n4 = v2<float>(x[2 * k4], x[2 * k4 + 1]);
+    V2<float> o1, o2, o3, o4;
+    if (g.square) {
+      const Coef<float> C4 = coef_from_trig<float, true>(U, tr.x, tr.y, tr.z, tr.w);
+      element_apply_square<float>(C4, n1, n2, n3, n4, o1, o2, o3, o4);
+    } else {
+      element_apply<float>(coef_from_trig<float>(U, tr.x, tr.y, tr.z, tr.w), rx, ry, w, n1, n2, n3, n4, o1, o2, o3,
+                           o4);
+    }
+    atomicAdd(&t[2 * k1], o1.u);
+    atomicAdd(&t[2 * k1 + 1], o1.v);
+    atomicAdd(&t[2 * k2], o2.u);
+    atomicAdd(&t[2 * k2 + 1], o2.v);
+    atomicAdd(&t[2 * k3], o3.u);
+    atomicAdd(&t[2 * k3 + 1], o3.v);
+    atomicAdd(&t[2 * k4], o4.u);
+    atomicAdd(&t[2 * k4 + 1], o4.v);
+  }
+  __syncwarp();
+}
+
+// r = mask(b - t)
+__device__ __forceinline__ void bot_resid(const Geo& g, const float* b, const float* t, float* r, int lane) {
+  const int nxp = g.nx + 1;
+  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {
+    const int i = node % nxp;
+    r[2 * node] = dir_u(i, g.nx) ? 0.f : b[2 * node] - t[2 * node];
+    r[2 * node + 1] = dir_v(i) ? 0.f : b[2 * node + 1] - t[2 * node + 1];
+  }
+  __syncwarp();
+}
+
+// p = P xc (bilinear prolongation of the coarse vector)
+__device__ __forceinline__ void bot_prolong(const Geo& g, const float* xc, float* p, int lane) {
+  const int nxp = g.nx + 1, nxc = g.nx / 2;
+  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {
+    const int j = node / nxp, i = node - j * nxp;
+    const int I = i >> 1, J = j >> 1;
+    float cu = xc[2 * (J * (nxc + 1) + I)], cv = xc[2 * (J * (nxc + 1) + I) + 1];
+    if (j & 1) {
+      cu += xc[2 * ((J + 1) * (nxc + 1) + I)];
+      cv += xc[2 * ((J + 1) * (nxc + 1) + I) + 1];
+    }
+    if (i & 1) {
+      cu += xc[2 * (J * (nxc + 1) + I + 1)];
+      cv += xc[2 * (J * (nxc + 1) + I + 1) + 1];
+      if (j & 1) {
+        cu += xc[2 * ((J + 1) * (nxc + 1) + I + 1)];
+        cv += xc[2 * ((J + 1) * (nxc + 1) + I + 1) + 1];
+      }
+    }
+    const float f = ((i & 1) && (j & 1)) ? 0.25f : (((i & 1) || (j & 1)) ? 0.5f : 1.f);
+    p[2 * node] = f * cu;
+    p[2 * node + 1] = f * cv;
+  }
+  __syncwarp();
+}
+
+// post-smoothing of level g: x2 = W b + P xc, z = mask(x2 + W (b - K x2)) into out
+__device__ __forceinline__ void bot_post(const Invariants& U, const Geo& g, const float* winv, const float* wc,
+                                         const float* trig, const float* b, const float* xc, float* x2, float* t,
+                                         float* out, int lane) {
+  bot_prolong(g, xc, t, lane);                 // t = P xc
+  bot_smooth(g, winv, wc, b, t, x2, lane);     // x2 = W b + P xc
+  bot_apply(U, g, trig, x2, t, lane);          // t = K x2
+  const int nxp = g.nx + 1;
+  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {   // t = b - K x2 (unmasked: W is zero there)
+    t[2 * node] = b[2 * node] - t[2 * node];
+    t[2 * node + 1] = b[2 * node + 1] - t[2 * node + 1];
+  }
+  __syncwarp();
+  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {
+    const int j = node / nxp, i = node - j * nxp;
+    const int ip = i ^ 1;
+    const float other = ip <= g.nx ? t[2 * (j * nxp + ip)] : 0.f;
+    const float2 w = reinterpret_cast<const float2*>(winv)[node];
+    float zu = x2[2 * node] + w.x * t[2 * node] + wc[node] * other;
+    float zv = x2[2 * node + 1] + w.y * t[2 * node + 1];
+    if (dir_u(i, g.nx)) zu = 0.f;
+    if (dir_v(i)) zv = 0.f;
+    out[2 * node] = zu;
+    out[2 * node + 1] = zv;
+  }
+  __syncwarp();
+}
+
+constexpr int kBotFloats = 2 * kBotNodes * 3 + 2 * kBotNodesB * 3 + 2 * kMaxCoarsestDofs;
+
+__global__ void __launch_bounds__(kWarpsPerBlock * kWarp) k_bottom(const __grid_constant__ BottomList L, SampleState S) {
+  __shared__ __align__(16) float sm[kWarpsPerBlock][kBotFloats];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarpsPerBlock + wib;
+  int vi = 0;
+  while (vi < L.n && gw >= L.v[vi].work_begin + L.v[vi].nsamp) ++vi;
+  if (vi >= L.n) return;
+  const BottomView& V = L.v[vi];
+  const int s = gw - V.work_begin;
+  if (s < 0 || !S.active[V.sbase + s]) return;   // the whole warp
+  const Geo& ga = V.ga;
+  const Geo& gb = V.gb;
+  const Geo& gc = V.gc;
+  const int na = (ga.nx + 1) * (ga.ny + 1), nb = (gb.nx + 1) * (gb.ny + 1), nc = 2 * (gc.nx + 1) * (gc.ny + 1);
+  const int nf = (2 * ga.nx + 1) * (2 * ga.ny + 1);
+  float* bA = sm[wib];
+  float* xA = bA + 2 * kBotNodes;
+  float* tA = xA + 2 * kBotNodes;
+  float* bB = tA + 2 * kBotNodes;
+  float* xB = bB + 2 * kBotNodesB;
+  float* tB = xB + 2 * kBotNodesB;
+  float* bC = tB + 2 * kBotNodesB;
+  const float* winvA = V.winv_a + (int64_t)s * 2 * na;
+  const float* wcA = V.wc_a + (int64_t)s * na;
+  const float* trA = V.trig_a + (int64_t)s * 4 * ga.nx * ga.ny;
+  const float* winvB = V.winv_b + (int64_t)s * 2 * nb;
+  const float* wcB = V.wc_b + (int64_t)s * nb;
+  const float* trB = V.trig_b + (int64_t)s * 4 * gb.nx * gb.ny;
+  // down: level A from the residual of the level above, then level B
+  bot_restrict(ga, V.rin + (int64_t)s * 2 * nf, bA, lane);
+  bot_smooth(ga, winvA, wcA, bA, nullptr, xA, lane);
+  bot_apply(L.U, ga, trA, xA, tA, lane);
+  bot_resid(ga, bA, tA, tA, lane);             // tA = r_A
+  bot_restrict(gb, tA, bB, lane);
+  bot_smooth(gb, winvB, wcB, bB, nullptr, xB, lane);
+  bot_apply(L.U, gb, trB, xB, tB, lane);
+  bot_resid(gb, bB, tB, tB, lane);             // tB = r_B
+  // coarsest: x_C = A^-1 R r_B (into tA's space, free now: level C has <= 64 values)
+  bot_restrict(gc, tB, bC, lane);
+  float* xC = tA;
+  const float* Ai = V.ainv + (int64_t)s * nc * nc;
+  for (int r = lane; r < nc; r += 32) {
+    float acc = 0.f;
+    for (int c = 0; c < nc; ++c) acc += Ai[(int64_t)r * nc + c] * bC[c];
+    xC[r] = acc;
+  }
+  __syncwarp();
+  // up: level B (its post-smoothed x into xB), then level A straight to the output
+  bot_post(L.U, gb, winvB, wcB, trB, bB, xC, xB, tB, xB, lane);   // scratch x2 = out = xB, t = tB
+  float* outA = V.xout + (int64_t)s * 2 * na;
+  bot_post(L.U, ga, winvA, wcA, trA, bA, xB, xA, tA, outA, lane);   // scratch x2 = xA, t = tA
+}
+
 // d += x on refinement-active samples: ext1 = d (DStore<T>), a = x (T). With o0 set,
 // also moves the inner solve's final residual into o0 from b where it ended there
 // (rpar), making it the next refinement residual.
@@ -1612,6 +1813,18 @@ template <typename T>
 cudaError_t launch_coarsest_solve(const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st) {
   if (total_warps <= 0) return cudaSuccess;
   k_coarsest_solve<T><<<blocks_for(total_warps, kWarpsPerBlock), kWarpsPerBlock * kWarp, 0, st>>>(L, S);
+  return cudaGetLastError();
+}
+
+bool bottom_fits(const Geo& ga, const Geo& gb, const Geo& gc) {
+  return (ga.nx + 1) * (ga.ny + 1) <= kBotNodes && (gb.nx + 1) * (gb.ny + 1) <= kBotNodesB &&
+         2 * (gc.nx + 1) * (gc.ny + 1) <= kMaxCoarsestDofs && ga.nx == 2 * gb.nx && ga.ny == 2 * gb.ny &&
+         gb.nx == 2 * gc.nx && gb.ny == 2 * gc.ny;
+}
+
+cudaError_t launch_bottom(const BottomList& L, SampleState S, int total_warps, cudaStream_t st) {
+  if (total_warps <= 0) return cudaSuccess;
+  k_bottom<<<blocks_for(total_warps, kWarpsPerBlock), kWarpsPerBlock * kWarp, 0, st>>>(L, S);
   return cudaGetLastError();
 }
 

@@ -102,6 +102,31 @@ cudaError_t launch_coarsest_setup(const ViewList<T>& L, int total_blocks, cudaSt
 template <typename T>
 cudaError_t launch_coarsest_solve(const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st);
 
+// The bottom of a group's multigrid hierarchy in one launch (FP32): levels A = nl-3
+// and B = nl-2 and the coarsest C = nl-1 of every sample, one warp per sample in
+// shared memory. Does what PreR (A, B), the coarsest solve and Post (B, A) do, in
+// the same order and arithmetic: b_A = R r_in, x_A = W b_A, r_A = b_A - K x_A,
+// b_B = R r_A, ..., x_C = A^-1 R r_B, x_B = W b_B + P x_C, x_B += W (b_B - K x_B),
+// x_A likewise; writes x_A (what Post at level nl-4 prolongates).
+constexpr int kBotNodes = 96;   // nodes of level A at most
+constexpr int kBotNodesB = 32;  // of level B
+struct BottomView {
+  Geo ga, gb, gc;
+  int nsamp, sbase, work_begin;
+  const float *rin;                        // level nl-4 residual [s][nodes][2]
+  const float *winv_a, *wc_a, *trig_a;     // level A smoother and coarse element data
+  const float *winv_b, *wc_b, *trig_b;
+  const float* ainv;                       // coarsest inverses [s][n][n]
+  float* xout;                             // x_A [s][nodes][2]
+};
+struct BottomList {
+  int n;
+  Invariants U;
+  BottomView v[kMaxViews];
+};
+bool bottom_fits(const Geo& ga, const Geo& gb, const Geo& gc);
+cudaError_t launch_bottom(const BottomList& L, SampleState S, int total_warps, cudaStream_t st);
+
 // d += x (a = x, ext1 = d); with o0 set also r0 = r1 where the inner residual ended
 // in r1 (b = r1, o0 = r0). One thread per value.
 template <typename T>

@@ -15,6 +15,7 @@
 // launch per depth serves every group that has that level. Every sample keeps its
 // own CG scalars; converged samples drop out of all kernels.
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 #include <cmath>
@@ -166,6 +167,13 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     dmax = std::max(dmax, g.nl - 1);
   }
   if (total == 0) return MLMC_OK;
+  // the multigrid bottom of every group in one launch (FP32, hierarchies of 4 levels or
+  // more whose three smallest meshes fit a warp's shared memory): the sweeps then stop
+  // three levels above each group's coarsest
+  bool fused = std::is_same<T, float>::value && ctx.fused_bottom;
+  for (auto& g : G)
+    fused = fused && g.nl >= 4 && bottom_fits(g.geo[g.nl - 3], g.geo[g.nl - 2], g.geo[g.nl - 1]);
+  const int bottom_depth = fused ? 3 : 1;
   const int max_iter = ctx.cfg.max_iter > 0 ? ctx.cfg.max_iter : 200;
   const int max_outer = ctx.cfg.max_outer > 0 ? ctx.cfg.max_outer : 8;
 
@@ -336,7 +344,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     for (int d = 0; d < dmax; ++d) {
       ViewList<T> Lsm = empty_list<T>(ctx);
       for (auto& g : G) {
-        if (d >= g.nl - 1) continue;
+        if (d >= g.nl - bottom_depth) continue;
         View<T> v = base_view(g, d);
         if (d == 0) {
           v.a = g.r[parity];
@@ -366,8 +374,37 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         MLMC_LAUNCH(kProfPre, "pre", launch_strip<T>(StripOp::PreR, Lsm, S, tw, st));
       }
     }
-    // every group's coarsest mesh (its right-hand side gathered from the level above)
-    {
+    // every group's bottom: levels nl-3, nl-2 and the coarsest in one launch, or the
+    // coarsest mesh alone (its right-hand side gathered from the level above)
+    if (fused) {
+      BottomList L;
+      std::memset(&L, 0, sizeof(L));
+      L.U = ctx.U;
+      int acc = 0;
+      for (auto& g : G) {
+        const int a = g.nl - 3;
+        BottomView v;
+        std::memset(&v, 0, sizeof(v));
+        v.ga = g.geo[a];
+        v.gb = g.geo[a + 1];
+        v.gc = g.geo[a + 2];
+        v.nsamp = (int)g.grp->nsamp;
+        v.sbase = g.sbase;
+        v.work_begin = acc;
+        v.rin = reinterpret_cast<const float*>(g.r1[a - 1]);
+        v.winv_a = reinterpret_cast<const float*>(g.winvd[a]);
+        v.wc_a = reinterpret_cast<const float*>(g.wc[a]);
+        v.trig_a = reinterpret_cast<const float*>(g.trig[a]);
+        v.winv_b = reinterpret_cast<const float*>(g.winvd[a + 1]);
+        v.wc_b = reinterpret_cast<const float*>(g.wc[a + 1]);
+        v.trig_b = reinterpret_cast<const float*>(g.trig[a + 1]);
+        v.ainv = reinterpret_cast<const float*>(g.ainv);
+        v.xout = reinterpret_cast<float*>(g.xl[a]);
+        acc += v.nsamp;
+        L.v[L.n++] = v;
+      }
+      MLMC_LAUNCH(kProfCoarsest, "bottom", launch_bottom(L, S, acc, st));
+    } else {
       ViewList<T> L = empty_list<T>(ctx);
       int acc = 0;
       for (auto& g : G) {
@@ -387,7 +424,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     for (int d = dmax - 1; d >= 0; --d) {
       ViewList<T> L = empty_list<T>(ctx);
       for (auto& g : G) {
-        if (d >= g.nl - 1) continue;
+        if (d >= g.nl - bottom_depth) continue;
         View<T> v = base_view(g, d);
         v.xc = g.xl[d + 1];
         v.winvd = g.winvd[d];

@@ -332,6 +332,7 @@ def test_autotune_keeps_results_and_moments(B):
         t = B.mlmc_autotune(ctx, [0, 1, 2], [64, 16, 6], reps=1)
         assert t["max_rows"] in (32, 64) and t["min_rows"] in (4, 6, 8)
         assert t["target_waves"] in (0.75, 1.5, 3.0) and t["nested_min_nodes"] in (0, 1 << 62)
+        assert t["fused_bottom"] in (0, 1)
         assert t["step_ms"] > 0
         assert B.mlmc_level_stats_get(ctx, 2) == before
         assert B.mlmc_get_tuning(ctx)["max_rows"] == t["max_rows"]
@@ -342,3 +343,26 @@ def test_autotune_keeps_results_and_moments(B):
             B.mlmc_set_tuning(ctx, 65, 4, 1.5, 0)
     finally:
         B.mlmc_destroy(ctx)
+
+
+@pytest.mark.parametrize("nested_min_nodes", [0, 1 << 40])
+def test_fused_bottom_matches_separate_launches(B, nested_min_nodes):
+    """The multigrid bottom in one launch (levels nl-3, nl-2 and the coarsest per
+    sample in a warp) does the same operations as the separate PreR / coarsest / Post
+    launches: the solves agree to rounding, checked at the stated 1e-6, and take the
+    same PCG iterations."""
+    w = STRIP_MIXED_5LEVEL
+    out = {}
+    for fused in (1, 0):
+        ctx = B.mlmc_create(B.config_from_workload(w))
+        try:
+            B.mlmc_set_tuning(ctx, 64, 6, 1.5, nested_min_nodes, fused)
+            qf, qc = np.zeros(2 * 20), np.zeros(2 * 20)
+            st = np.ones(20, dtype=np.int32)
+            B.mlmc_sample_levels(ctx, [0, 1, 2, 3], [0, 0, 0, 0], [8, 6, 4, 2], qf, qc, st)
+            assert np.all(st == 0)
+            out[fused] = (qf, qc)
+        finally:
+            B.mlmc_destroy(ctx)
+    np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-6)
+    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-6, atol=0)
