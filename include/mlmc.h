@@ -152,7 +152,8 @@ typedef struct {
    candidate launch shapes and nested-iteration settings, by coordinate descent
    (nested iteration on / off, fused multigrid bottom on / off, target_waves 0.75 /
    1.5 / 3, max_rows 32 / 64, min_rows 4 / 6 / 8; one warm-up and `reps` timed calls
-   each, the median kept), and keeps
+   each, the median kept; the current values are timed first and a candidate replaces
+   them only when more than 1 % faster), and keeps
    the fastest on the context. The level moments are left as they were. out
    (nullable) receives the chosen values. Errors as mlmc_sample_levels. */
 mlmc_status mlmc_autotune(mlmc_ctx* ctx, int32_t n_req, const int32_t* levels, const int64_t* counts, int32_t reps,

@@ -661,19 +661,22 @@ mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, con
     ms = t[t.size() / 2];
     return MLMC_OK;
   };
+  // a candidate replaces the best only when it is faster by more than 1 %: ties (such
+  // as thresholds on either side of the workload's size) keep the current value
   auto consider = [&](Cand k) -> mlmc_status {
     double ms = 0;
     mlmc_status ss = measure(k, ms);
-    if (ss == MLMC_OK && ms < best_ms) {
+    if (ss == MLMC_OK && ms < 0.99 * best_ms) {
       best_ms = ms;
       best = k;
     }
     return ss;
   };
-  // coordinate descent from the current values
+  // coordinate descent from the current values, timed first
   const int64_t nested_vals[2] = {0, (int64_t)1 << 62};
   const double wave_vals[3] = {0.75, 1.5, 3.0};
   const int max_vals[2] = {32, 64}, min_vals[3] = {4, 6, 8};
+  s = consider(best);
   for (int64_t v : nested_vals)
     if (s == MLMC_OK) s = consider(Cand{v, best.waves, best.max_rows, best.min_rows, best.fused});
   for (bool v : {true, false})
