@@ -267,20 +267,33 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     const int tt = finalize_points(L, per);
     MLMC_LAUNCH(kProfOther, "trig_average", launch_trig_average<T>(L, tt, st));
   }
-  for (int k = 0; k < 64; ++k) {
+  // smoothers of every level of every group: independent, so up to kMaxViews
+  // (group, level) views share a launch
+  {
     ViewList<T> L = empty_list<T>(ctx);
     std::vector<int64_t> per;
-    for (auto& g : G) {
-      if (k >= g.nl) continue;
-      View<T> v = base_view(g, k);
-      v.o0 = g.winvd[k];
-      v.o1 = g.wc[k];
-      L.v[L.n++] = v;
-      per.push_back((int64_t)(g.geo[k].nx / 2 + 1) * (g.geo[k].ny + 1));   // node pairs
-    }
-    if (L.n == 0) break;
-    const int tt = finalize_points(L, per);
-    MLMC_LAUNCH(kProfOther, "invdiag", launch_invdiag<T>(L, tt, st));
+    auto flush = [&]() -> mlmc_status {
+      if (L.n == 0) return MLMC_OK;
+      const int tt = finalize_points(L, per);
+      MLMC_LAUNCH(kProfOther, "invdiag", launch_invdiag<T>(L, tt, st));
+      L = empty_list<T>(ctx);
+      per.clear();
+      return MLMC_OK;
+    };
+    for (auto& g : G)
+      for (int k = 0; k < g.nl; ++k) {
+        if (L.n == kMaxViews) {
+          const mlmc_status fs = flush();
+          if (fs != MLMC_OK) return fs;
+        }
+        View<T> v = base_view(g, k);
+        v.o0 = g.winvd[k];
+        v.o1 = g.wc[k];
+        L.v[L.n++] = v;
+        per.push_back((int64_t)(g.geo[k].nx / 2 + 1) * (g.geo[k].ny + 1));   // node pairs
+      }
+    const mlmc_status fs = flush();
+    if (fs != MLMC_OK) return fs;
   }
   {
     ViewList<T> L = empty_list<T>(ctx);
