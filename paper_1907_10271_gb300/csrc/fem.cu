@@ -411,6 +411,59 @@ __device__ __forceinline__ void strip_loop_async(const Invariants& U, const View
   if (er1 + 1 == ny && ny >= j0 && ny <= j1) op.out(i, ny, rc.top(), out_col);
 }
 
+// ---------------------------------------------------------------- per-sample scalars
+// The PCG's scalar steps run in the launch that completes their reduction: each live
+// warp of a sample adds its partial sum and then counts itself in (lane 0); the warp
+// whose count completes the sample's tiles sees every partial (fence before the count,
+// fence after it, L2 reads) and takes the step. Nothing waits on another warp.
+
+// True for the sample's last arriving warp, which also rearms the counter.
+__device__ __forceinline__ bool last_tile(unsigned* arrive, int t, int tiles) {
+  __threadfence();
+  if (atomicAdd(&arrive[t], 1u) + 1u != (unsigned)tiles) return false;
+  __threadfence();
+  arrive[t] = 0u;
+  return true;
+}
+
+// After b . z is complete (post-smoothing at the top level): convergence on the
+// iteration's ||r||^2, then the conjugate-gradient beta = rz / rz_old. count[slot]
+// receives the samples still active; batches start at even iterations, so slot and
+// iteration have the same parity.
+__device__ void after_post(const SampleState& S, int t) {
+  S.rpar[t] = (S.slot + 1) & 1;   // PreTop of this iteration wrote r' to buffer (iteration + 1) & 1
+  const double rr = __ldcg(&S.red_rr[t]);
+  if (rr <= S.tol2[t] * S.rr_ref[t]) {
+    S.active[t] = 0;
+    return;
+  }
+  const double rz = __ldcg(&S.red_rz[t]);
+  if (!(rz > 0.0) || !isfinite(rz)) {   // preconditioned residual lost positivity
+    S.active[t] = 0;
+    S.status[t] = MLMC_ERR_NOT_CONVERGED;
+    return;
+  }
+  const double old = S.rz_old[t];
+  S.beta[t] = old > 0.0 ? rz / old : 0.0;
+  S.rz_old[t] = rz;
+  S.red_pq[t] = 0.0;
+  S.iters[t] += 1;
+  atomicAdd(&S.count[S.slot], 1);
+}
+
+// After p . q is complete: alpha = rz / pq, and the next iteration's sums start at 0.
+__device__ void after_p(const SampleState& S, int t) {
+  const double pq = __ldcg(&S.red_pq[t]);
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    S.active[t] = 0;
+    S.status[t] = MLMC_ERR_NOT_CONVERGED;
+    return;
+  }
+  S.alpha[t] = S.rz_old[t] / pq;
+  S.red_rr[t] = 0.0;
+  S.red_rz[t] = 0.0;
+}
+
 // ---------------------------------------------------------------- operand handlers
 // Each handler provides: Raw load(i, j) (node data of row j, prefetched), in(raw, i, j)
 // (value K is applied to; keeps what out() needs), out(i, j, K x), shift() (row
@@ -820,7 +873,11 @@ struct OpPost : OpBase<T> {
   __device__ void finish(const SampleState& S, int s) {
     if (TOP) {
       const double t = warp_sum(rz.value());
-      if ((threadIdx.x & 31) == 0) atomicAdd(&S.red_rz[this->V.sbase + s], t);
+      if ((threadIdx.x & 31) == 0) {
+        const int g = this->V.sbase + s;
+        atomicAdd(&S.red_rz[g], t);
+        if (last_tile(S.arrive, g, this->V.tiles_x * this->V.tiles_y)) after_post(S, g);
+      }
     }
   }
 };
@@ -870,7 +927,11 @@ struct OpPcgP : OpBase<T> {
   __device__ void shift() { pb = pt; }
   __device__ void finish(const SampleState& S, int s) {
     const double t = warp_sum(pq.value());
-    if ((threadIdx.x & 31) == 0) atomicAdd(&S.red_pq[this->V.sbase + s], t);
+    if ((threadIdx.x & 31) == 0) {
+      const int g = this->V.sbase + s;
+      atomicAdd(&S.red_pq[g], t);
+      if (last_tile(S.arrive, g, this->V.tiles_x * this->V.tiles_y)) after_p(S, g);
+    }
   }
 };
 
@@ -1667,48 +1728,6 @@ __global__ void k_inner_end(SampleState S, int total, int recursive) {
   if (recursive) S.rr64[t] = S.red_rr[t];
 }
 
-// ---------------------------------------------------------------- per-sample scalars
-
-// slot: the iteration's position in its batch (batches start at even iterations, so
-// slot and iteration have the same parity); count[slot] receives the samples still
-// active after it.
-__global__ void k_after_post(SampleState S, int total, int slot) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total || !S.active[t]) return;
-  S.rpar[t] = (slot + 1) & 1;   // PreTop of this iteration wrote r' to buffer (iteration + 1) & 1
-  const double rr = S.red_rr[t];
-  if (rr <= S.tol2[t] * S.rr_ref[t]) {
-    S.active[t] = 0;
-    return;
-  }
-  const double rz = S.red_rz[t];
-  if (!(rz > 0.0) || !isfinite(rz)) {   // preconditioned residual lost positivity
-    S.active[t] = 0;
-    S.status[t] = MLMC_ERR_NOT_CONVERGED;
-    return;
-  }
-  const double old = S.rz_old[t];
-  S.beta[t] = old > 0.0 ? rz / old : 0.0;
-  S.rz_old[t] = rz;
-  S.red_pq[t] = 0.0;
-  S.iters[t] += 1;
-  atomicAdd(&S.count[slot], 1);
-}
-
-__global__ void k_after_p(SampleState S, int total) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total || !S.active[t]) return;
-  const double pq = S.red_pq[t];
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    S.active[t] = 0;
-    S.status[t] = MLMC_ERR_NOT_CONVERGED;
-    return;
-  }
-  S.alpha[t] = S.rz_old[t] / pq;
-  S.red_rr[t] = 0.0;
-  S.red_rz[t] = 0.0;
-}
-
 __global__ void k_outer_init(SampleState S, int total) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
@@ -1875,16 +1894,6 @@ cudaError_t launch_react_delta(const ViewList<T>& L, SampleState S, int total_th
 
 cudaError_t launch_inner_end(SampleState S, int total, int recursive, cudaStream_t st) {
   k_inner_end<<<blocks_for(total, 256), 256, 0, st>>>(S, total, recursive);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_after_post(SampleState S, int total, int slot, cudaStream_t st) {
-  k_after_post<<<blocks_for(total, 256), 256, 0, st>>>(S, total, slot);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_after_p(SampleState S, int total, cudaStream_t st) {
-  k_after_p<<<blocks_for(total, 256), 256, 0, st>>>(S, total);
   return cudaGetLastError();
 }
 

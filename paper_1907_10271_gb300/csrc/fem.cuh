@@ -68,7 +68,10 @@ struct SampleState {
   int* status;        // 0 ok, MLMC_ERR_NOT_CONVERGED
   int* count;         // [batch] active samples after each iteration of the current batch
   int* rpar;          // buffer (0/1) holding the latest inner residual
+  unsigned* arrive;   // warps of the running launch that added their share of a sample's
+                      // reduction; zero between launches (see last_tile in fem.cu)
   unsigned long long* units;   // [kProfOps] nodes processed per operation (null: not counted)
+  int slot;           // the PCG iteration's position in its batch (post-smoothing launch)
 };
 
 // Strip kernels (q = K p family); see fem.cu for the operand conventions.
@@ -156,8 +159,6 @@ cudaError_t launch_react_delta(const ViewList<T>& L, SampleState S, int total_th
 // PCG's last reduced ||r||^2.
 cudaError_t launch_inner_end(SampleState S, int total, int recursive, cudaStream_t st);
 
-cudaError_t launch_after_post(SampleState S, int total, int slot, cudaStream_t st);
-cudaError_t launch_after_p(SampleState S, int total, cudaStream_t st);
 cudaError_t launch_outer_init(SampleState S, int total, cudaStream_t st);
 cudaError_t launch_outer_check(SampleState S, int total, double rtol, double floor_tol, int* outer_count,
                                cudaStream_t st);

@@ -230,6 +230,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     alloc.template vec<int>(S.status, total);
     alloc.template vec<int>(S.count, (size_t)std::max(ctx.check_every, 1));
     alloc.template vec<int>(S.rpar, total);
+    alloc.template vec<unsigned>(S.arrive, total);
     alloc.template vec<int>(outer_count, 1);
   };
   SizeAlloc sz;
@@ -245,6 +246,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   plan(ca);
   plan_state(ca);
   S.units = ctx.timer.on ? ctx.timer.units_dev : nullptr;
+  S.slot = 0;
   {
     char* state_begin = reinterpret_cast<char*>(S.alpha);
     char* state_end = reinterpret_cast<char*>(outer_count + 1);
@@ -453,22 +455,22 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       }
       if (!L.n) continue;
       const int tw = finalize_warps(ctx, L, d == 0 ? StripOp::PostTop : StripOp::Post);
-      if (d == 0) {
+      if (d == 0) {   // its last warp per sample also takes the convergence test and beta
         L.prof_op = kProfPostTop;
-        MLMC_LAUNCH(kProfPostTop, "post_top", launch_strip<T>(StripOp::PostTop, L, S, tw, st));
+        SampleState Ss = S;
+        Ss.slot = slot;
+        MLMC_LAUNCH(kProfPostTop, "post_top", launch_strip<T>(StripOp::PostTop, L, Ss, tw, st));
       } else {
         L.prof_op = kProfPost;
         MLMC_LAUNCH(kProfPost, "post", launch_strip<T>(StripOp::Post, L, S, tw, st));
       }
     }
-    MLMC_LAUNCH(kProfOther, "after_post", launch_after_post(S, total, slot, st));
-    {
+    {   // its last warp per sample also forms alpha
       ViewList<T> L = top_list(StripOp::PcgP, parity);
       const int tw = finalize_warps(ctx, L, StripOp::PcgP);
       L.prof_op = kProfPcgP;
       MLMC_LAUNCH(kProfPcgP, "pcg_p", launch_strip<T>(StripOp::PcgP, L, S, tw, st));
     }
-    MLMC_LAUNCH(kProfOther, "after_p", launch_after_p(S, total, st));
     return MLMC_OK;
   };
 
