@@ -71,7 +71,30 @@ HEX8_MIXED_4LEVEL = dict(
     rtol=1e-8,
 )
 
-WORKLOADS = {w["name"]: w for w in (STRIP_FP64_3LEVEL, STRIP_MIXED_5LEVEL, HEX8_MIXED_4LEVEL)}
+# Wing-skin panel buckling with uncertain ply angles (Sec. 4.1): a simply supported
+# Reissner-Mindlin plate [0, lx] x [0, ly] (mm) of 8 IM7-8552 plies, 0.8 mm each, in the
+# paper's stacking sequence, each ply angle perturbed by an independent N(0, 3 deg^2);
+# unit compressive line load along x; square Q4 elements (24 x 8 on level 0), halved per
+# level. p_star is the paper's failure threshold on the critical load (Sec. 4.2).
+PANEL_RM_4LEVEL = dict(
+    name="panel-rm-q4-4level",
+    lx=636.0, ly=212.0,
+    nx0=24, ny0=8,
+    levels=4,
+    E11=130000.0, E22=9250.0, G12=5130.0, nu12=0.36,   # MPa
+    G13=5130.0, k_shear=5.0 / 6.0,
+    plies_deg=(45.0, -45.0, -45.0, 45.0, -45.0, 45.0, 45.0, -45.0),
+    t_ply=0.8,                  # mm
+    ply_std_deg=3.0,
+    bc="hard",                  # w = 0 and the tangential rotation held on the boundary
+    p_star=272.47,              # kN
+    seed=0,
+    n_per_level=(4096, 1024, 256, 64),
+    tol=5e-5,                   # LOBPCG preconditioned-residual tolerance
+    max_iter=120,
+)
+
+WORKLOADS = {w["name"]: w for w in (STRIP_FP64_3LEVEL, STRIP_MIXED_5LEVEL, HEX8_MIXED_4LEVEL, PANEL_RM_4LEVEL)}
 
 
 def mesh_dims(cfg, level):
@@ -92,3 +115,14 @@ def mesh_dims3(cfg, level):
 def n_dofs3(cfg, level):
     nx, ny, nz = mesh_dims3(cfg, level)
     return 3 * (nx + 1) * (ny + 1) * (nz + 1)
+
+
+def mesh_dims_panel(cfg, level):
+    """(nx, ny) element counts of panel mesh `level`."""
+    return cfg["nx0"] << level, cfg["ny0"] << level
+
+
+def n_dofs_panel(cfg, level):
+    """3 (nx + 1) (ny + 1): DOFs of panel mesh `level` (w, theta_x, theta_y per node)."""
+    nx, ny = mesh_dims_panel(cfg, level)
+    return 3 * (nx + 1) * (ny + 1)
