@@ -60,11 +60,13 @@ def parse():
                     help="skip the plain double-precision single-sample comparison")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the request-loop (selective refinement) measurement")
-    ap.add_argument("--case", choices=["full", "small", "hex3d"], default="full",
-                    help="small: one untimed call with 1/4 of each level's samples; hex3d: one untimed "
-                         "step of the 3D Hex8 block (both for profilers)")
+    ap.add_argument("--case", choices=["full", "small", "hex3d", "panel"], default="full",
+                    help="small: one untimed call with 1/4 of each level's samples; hex3d / panel: one "
+                         "untimed step of the 3D Hex8 block / the buckling panel (all for profilers)")
     ap.add_argument("--no-hex3d", dest="hex3d", action="store_false",
                     help="skip the 3D Hex8 block measurement")
+    ap.add_argument("--no-panel", dest="panel", action="store_false",
+                    help="skip the panel-buckling measurement")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default launch shapes instead of running mlmc_autotune first")
     ap.add_argument("--cpu-fraction", type=float, default=1.0 / 32.0,
@@ -687,6 +689,91 @@ def run_hex3d(B, steps=2, warmup=1, parity=True):
     return out
 
 
+def run_panel(B, steps=2, warmup=1, parity=True):
+    """The buckling panel (panel-rm-q4-4level): one MLMC step is every level's samples
+    (4096/1024/256/64 level pairs on 24x8 ... 192x64 Q4 meshes), one mlmcp_sample_level
+    call per level with host outputs, timed with the device synchronised on both sides.
+    Parity: four level-0 pairs and two level-1 pairs against the oracle's sparse
+    eigen-solves, whose times are the CPU baseline (one core)."""
+    import torch
+    from workloads import PANEL_RM_4LEVEL as W
+    counts = list(W["n_per_level"])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = B.mlmcp_create(B.configp_from_workload(W), stream.cuda_stream)
+        try:
+            bufs = [(np.zeros(2 * n), np.zeros(2 * n), np.zeros(n, dtype=np.int32)) for n in counts]
+            iters = []
+
+            def step(k):
+                iters.clear()
+                for lev, n in enumerate(counts):
+                    qf, qc, st = bufs[lev]
+                    B.mlmcp_sample_level(ctx, lev, k * 10 ** 6, n, qf, qc, st)
+                    iters.append(B.mlmcp_last_iters(ctx))
+
+            for k in range(warmup):
+                step(k)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(steps):
+                step(warmup + k)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) / steps * 1e3
+            failed = sum(int((b[2] != 0).sum()) for b in bufs)
+            fails = [float(b[0][1::2].mean()) for b in bufs]
+            out = {
+                "workload": W["name"], "meshes": "24x8..192x64 Q4 (w, theta_x, theta_y), 636 x 212 mm",
+                "samples_per_level": counts, "plies": len(W["plies_deg"]), "ply_std_deg": W["ply_std_deg"],
+                "metric": "level-pairs/s", "value": round(sum(counts) / ms * 1e3, 1), "ms_per_step": round(ms, 2),
+                "steps": steps, "warmup": warmup, "samples_failed": failed,
+                "lobpcg_iterations_per_level": list(iters),
+                "fine_failure_fraction_per_level": [round(f, 4) for f in fails],
+                "note": "host outputs (mlmcp_sample_level), one call per level; block LOBPCG (2 vectors) in FP32 "
+                        "preconditioned by a V(2,2) multigrid cycle, FP64 Gram matrices and final Rayleigh quotient",
+            }
+            if parity:
+                from oracle import plate as P
+                ids = [10 ** 7 + k for k in range(4)]
+                items = [(0, 0, i) for i in ids] + [(1, 1, i) for i in ids[:2]] + [(1, 0, i) for i in ids[:2]]
+                q = np.zeros(2 * len(items))
+                B.mlmcp_solve_batch(ctx, items, q)
+                err, ind_ok, times = 0.0, True, {0: [], 1: []}
+                for k, (lev, m, sid) in enumerate(items):
+                    phi = P.sample_perturbations(W, lev, [sid])[0]
+                    t1 = time.perf_counter()
+                    ref = P.solve_mesh(W, m, phi)
+                    times[m].append(time.perf_counter() - t1)
+                    err = max(err, abs(q[2 * k] / ref[0] - 1.0))
+                    ind_ok = ind_ok and (q[2 * k + 1] == ref[1] or abs(ref[0] / W["p_star"] - 1) < 1e-6)
+                out["qoi_parity"] = {"solves": len(items), "max_rel_err_load": err, "indicator_agrees": ind_ok,
+                                     "note": "GPU vs oracle (FP64 CLT + Q4, sparse eigen-solve) on the same "
+                                             "perturbations"}
+                out["cpu_baseline"] = {"kind": "oracle", "cores": 1,
+                                       "seconds_per_solve": {f"mesh{m}": round(float(np.mean(t)), 4)
+                                                             for m, t in times.items()},
+                                       "sample": "the parity solves above"}
+            return out
+        finally:
+            B.mlmcp_destroy(ctx)
+
+
+def run_panel_case():
+    """One step of the buckling panel (every level's samples), untimed: for profilers."""
+    import torch
+    from paper_1907_10271_gb300 import binding as B
+    from workloads import PANEL_RM_4LEVEL as W
+    ctx = B.mlmcp_create(B.configp_from_workload(W), torch.cuda.current_stream().cuda_stream)
+    failed = 0
+    for lev, n in enumerate(W["n_per_level"]):
+        qf, qc, st = np.zeros(2 * n), np.zeros(2 * n), np.zeros(n, dtype=np.int32)
+        B.mlmcp_sample_level(ctx, lev, 0, n, qf, qc, st)
+        failed += int((st != 0).sum())
+    torch.cuda.synchronize()
+    B.mlmcp_destroy(ctx)
+    print(json.dumps({"case": "panel", "level_pairs": sum(W["n_per_level"]), "failed": failed}))
+
+
 def run_hex3d_case():
     """One step of the 3D Hex8 block (every level's samples), untimed: for profilers."""
     import torch
@@ -711,6 +798,9 @@ def main():
         return
     if a.case == "hex3d":
         run_hex3d_case()
+        return
+    if a.case == "panel":
+        run_panel_case()
         return
     if a.impl == "reference":
         if rank != 0:
@@ -742,6 +832,9 @@ def main():
     if rank == 0 and out is not None and world == 1 and a.hex3d:
         from paper_1907_10271_gb300 import binding as B
         out["hex3d"] = run_hex3d(B, parity=not a.no_cpu_baseline)
+    if rank == 0 and out is not None and world == 1 and a.panel:
+        from paper_1907_10271_gb300 import binding as B
+        out["panel"] = run_panel(B, parity=not a.no_cpu_baseline)
     if rank == 0 and out is not None:
         if world == 1 and not a.no_cpu_baseline:
             cores = os.cpu_count() or 1

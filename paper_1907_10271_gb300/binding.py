@@ -575,3 +575,127 @@ def mlmc3d_last_iters(ctx):
     it = ctypes.c_int32()
     _check3(ctx, lib3().mlmc3d_last_iters(ctx, ctypes.byref(it)))
     return it.value
+
+
+# ---------------------------------------------------------------- panel buckling (mlmc_panel.h)
+
+MLMCP_MAX_PLIES = 32
+
+
+class mlmcp_config(ctypes.Structure):
+    _fields_ = [
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+        ("nx0", ctypes.c_int32), ("ny0", ctypes.c_int32), ("levels", ctypes.c_int32),
+        ("E11", ctypes.c_double), ("E22", ctypes.c_double), ("G12", ctypes.c_double), ("nu12", ctypes.c_double),
+        ("G13", ctypes.c_double), ("k_shear", ctypes.c_double),
+        ("n_plies", ctypes.c_int32), ("plies_deg", ctypes.c_double * MLMCP_MAX_PLIES),
+        ("t_ply", ctypes.c_double), ("ply_std_deg", ctypes.c_double),
+        ("hard_support", ctypes.c_int32), ("p_star", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+    ]
+
+
+_SIGP = None
+
+
+def libp():
+    """The library with the panel entry points' signatures set."""
+    global _SIGP
+    L = lib()
+    if _SIGP is None:
+        P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        sig = {
+            "mlmcp_create": (I32, [ctypes.POINTER(mlmcp_config), P, ctypes.POINTER(P)]),
+            "mlmcp_destroy": (None, [P]),
+            "mlmcp_last_error": (ctypes.c_char_p, [P]),
+            "mlmcp_sample_level": (I32, [P, I32, U64, I64, P, P, P]),
+            "mlmcp_solve_batch": (I32, [P, P, I64, P, P]),
+            "mlmcp_level_stats_get": (I32, [P, I32, P]),
+            "mlmcp_reset_stats": (I32, [P]),
+            "mlmcp_laminate": (I32, [P, I32, U64, I64, P, P]),
+            "mlmcp_apply": (I32, [P, I32, I32, U64, I64, P, P, P]),
+            "mlmcp_last_iters": (I32, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _SIGP = True
+    return L
+
+
+def configp_from_workload(w, **overrides):
+    """mlmcp_config from a panel workload dict (see workloads.py); keyword overrides win."""
+    w = dict(w)
+    w.update(overrides)
+    c = mlmcp_config()
+    for f in ("lx", "ly", "E11", "E22", "G12", "nu12", "G13", "k_shear", "t_ply", "ply_std_deg", "p_star"):
+        setattr(c, f, float(w[f]))
+    c.nx0, c.ny0, c.levels = int(w["nx0"]), int(w["ny0"]), int(w["levels"])
+    plies = list(w["plies_deg"])
+    if not 1 <= len(plies) <= MLMCP_MAX_PLIES:
+        raise ValueError("1 to 32 plies")
+    c.n_plies = len(plies)
+    for k, a in enumerate(plies):
+        c.plies_deg[k] = float(a)
+    c.hard_support = 1 if w.get("bc", "hard") == "hard" else 0
+    c.seed = int(w["seed"])
+    c.tol = float(w.get("tol", 0.0))
+    c.max_iter = int(w.get("max_iter", 0))
+    return c
+
+
+def _checkp(ctx, status):
+    if status != MLMC_OK:
+        raise MLMCError(status, libp().mlmcp_last_error(ctx).decode(errors="replace"))
+    return status
+
+
+def mlmcp_create(cfg, stream=None):
+    h = ctypes.c_void_p()
+    st = current_stream() if stream is None else stream
+    s = libp().mlmcp_create(ctypes.byref(cfg), ctypes.c_void_p(st), ctypes.byref(h))
+    if s != MLMC_OK:
+        raise MLMCError(s, libp().mlmcp_last_error(None).decode(errors="replace"))
+    return h
+
+
+def mlmcp_destroy(ctx):
+    libp().mlmcp_destroy(ctx)
+
+
+def mlmcp_sample_level(ctx, level, first_id, n, q_fine=None, q_coarse=None, status=None):
+    return _checkp(ctx, libp().mlmcp_sample_level(ctx, level, first_id, n, _ptr(q_fine, np.float64),
+                                                   _ptr(q_coarse, np.float64), _ptr(status, np.int32)))
+
+
+def mlmcp_solve_batch(ctx, items, q=None, status=None):
+    arr = (mlmc_item * len(items))(*[mlmc_item(int(l), int(m), int(s)) for (l, m, s) in items])
+    return _checkp(ctx, libp().mlmcp_solve_batch(ctx, ctypes.cast(arr, ctypes.c_void_p), len(items),
+                                                  _ptr(q, np.float64), _ptr(status, np.int32)))
+
+
+def mlmcp_level_stats(ctx, level):
+    out = mlmc_level_stats()
+    _checkp(ctx, libp().mlmcp_level_stats_get(ctx, level, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def mlmcp_reset_stats(ctx):
+    return _checkp(ctx, libp().mlmcp_reset_stats(ctx))
+
+
+def mlmcp_laminate(ctx, level, first_id, n, dstar, kgt=None):
+    return _checkp(ctx, libp().mlmcp_laminate(ctx, level, first_id, n, _ptr(dstar, np.float64),
+                                               _ptr(kgt, np.float64)))
+
+
+def mlmcp_apply(ctx, mesh_level, level, first_id, n, x, y, g=None):
+    return _checkp(ctx, libp().mlmcp_apply(ctx, mesh_level, level, first_id, n, _ptr(x, np.float32),
+                                            _ptr(y, np.float32), _ptr(g, np.float32)))
+
+
+def mlmcp_last_iters(ctx):
+    it = ctypes.c_int32()
+    _checkp(ctx, libp().mlmcp_last_iters(ctx, ctypes.byref(it)))
+    return it.value

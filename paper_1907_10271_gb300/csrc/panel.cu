@@ -1,0 +1,766 @@
+// Panel-buckling kernels: laminate (Eq. CLTABD), Reissner-Mindlin Q4 operators
+// (Eq. MomentWeakForm), the multigrid V-cycle on K, and the LOBPCG steps for the
+// largest mu of G d = mu K d (Eq. matrixeig, lambda = 1 / mu).
+//
+// Every sample's plate has constant coefficients (its laminate is uniform over the
+// panel), so one 12 x 12 element matrix per sample and mesh describes K entirely; the
+// node-centric kernels keep it in shared memory and each node forms its own three rows
+// from the (up to) four elements around it. The geometric form with the 1-point rule
+// is sample-independent: G_e = hy / (4 hx) s s^T on the w-DOFs, s = (-1, 1, 1, -1).
+#include "panel.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+#include "../../include/mlmc.h"
+
+namespace mlmcp {
+namespace {
+
+constexpr int kThreads = 128;
+
+// corner a of an element at offset (ox, oy) from its lower-left node
+__device__ __forceinline__ int corner_of(int ox, int oy) { return oy == 0 ? ox : 3 - ox; }
+__device__ __forceinline__ int corner_x(int a) { return (a == 1 || a == 2) ? 1 : 0; }
+__device__ __forceinline__ int corner_y(int a) { return a >= 2 ? 1 : 0; }
+
+// which DOFs of node (i, j) are free (w held on the boundary; with hard support the
+// tangential rotation too)
+struct Free {
+  bool w, tx, ty;
+};
+__device__ __forceinline__ Free free_of(const PGrid& g, int i, int j) {
+  const bool bx = i == 0 || i == g.nx, by = j == 0 || j == g.ny;
+  return Free{!(bx || by), !(g.hard && by), !(g.hard && bx)};
+}
+__device__ __forceinline__ float4 masked(const Free& f, float4 v) {
+  return make_float4(f.w ? v.x : 0.f, f.tx ? v.y : 0.f, f.ty ? v.z : 0.f, 0.f);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_laminate(Laminate lam, const double* __restrict__ xi, int n, double* __restrict__ dstar,
+                           double* __restrict__ kgt) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  // lamina stiffness (plane stress)
+  const double nu21 = lam.nu12 * lam.E22 / lam.E11;
+  const double den = 1.0 - lam.nu12 * nu21;
+  const double q11 = lam.E11 / den, q22 = lam.E22 / den, q12 = lam.nu12 * lam.E22 / den, q66 = lam.G12;
+  double A[6] = {0, 0, 0, 0, 0, 0}, B[6] = {0, 0, 0, 0, 0, 0}, D[6] = {0, 0, 0, 0, 0, 0};   // 11 12 16 22 26 66
+  const double t = lam.t_ply * lam.n_plies;
+  for (int k = 0; k < lam.n_plies; ++k) {
+    const double th = lam.psi[k] + lam.std_rad * xi[(size_t)s * lam.n_plies + k];
+    const double c = cos(th), sn = sin(th);
+    const double c2 = c * c, s2 = sn * sn, cs = c * sn;
+    // transformed reduced stiffness, angle from the x axis to the fibre
+    const double Qb[6] = {
+        q11 * c2 * c2 + 2.0 * (q12 + 2.0 * q66) * s2 * c2 + q22 * s2 * s2,
+        (q11 + q22 - 4.0 * q66) * s2 * c2 + q12 * (s2 * s2 + c2 * c2),
+        (q11 - q12 - 2.0 * q66) * cs * c2 + (q12 - q22 + 2.0 * q66) * cs * s2,
+        q11 * s2 * s2 + 2.0 * (q12 + 2.0 * q66) * s2 * c2 + q22 * c2 * c2,
+        (q11 - q12 - 2.0 * q66) * cs * s2 + (q12 - q22 + 2.0 * q66) * cs * c2,
+        (q11 + q22 - 2.0 * q12 - 2.0 * q66) * s2 * c2 + q66 * (s2 * s2 + c2 * c2)};
+    const double z0 = -0.5 * t + k * lam.t_ply, z1 = z0 + lam.t_ply;
+    for (int m = 0; m < 6; ++m) {
+      A[m] += Qb[m] * (z1 - z0);
+      B[m] += 0.5 * Qb[m] * (z1 * z1 - z0 * z0);
+      D[m] += Qb[m] * (z1 * z1 * z1 - z0 * z0 * z0) / 3.0;
+    }
+  }
+  // D* = D - B A^-1 B with symmetric 3x3 matrices stored as (11 12 16 22 26 66)
+  const double a11 = A[0], a12 = A[1], a13 = A[2], a22 = A[3], a23 = A[4], a33 = A[5];
+  const double c11 = a22 * a33 - a23 * a23, c12 = a13 * a23 - a12 * a33, c13 = a12 * a23 - a13 * a22;
+  const double c22 = a11 * a33 - a13 * a13, c23 = a12 * a13 - a11 * a23, c33 = a11 * a22 - a12 * a12;
+  const double det = a11 * c11 + a12 * c12 + a13 * c13;
+  const double Ai[3][3] = {{c11 / det, c12 / det, c13 / det}, {c12 / det, c22 / det, c23 / det},
+                           {c13 / det, c23 / det, c33 / det}};
+  const double Bm[3][3] = {{B[0], B[1], B[2]}, {B[1], B[3], B[4]}, {B[2], B[4], B[5]}};
+  double T[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) T[r][c] = Ai[r][0] * Bm[0][c] + Ai[r][1] * Bm[1][c] + Ai[r][2] * Bm[2][c];
+  const int rr[6] = {0, 0, 0, 1, 1, 2}, cc[6] = {0, 1, 2, 1, 2, 2};
+  for (int m = 0; m < 6; ++m) {
+    const int r = rr[m], c = cc[m];
+    dstar[(size_t)s * 6 + m] = D[m] - (Bm[r][0] * T[0][c] + Bm[r][1] * T[1][c] + Bm[r][2] * T[2][c]);
+  }
+  kgt[s] = lam.k_shear * lam.G13 * t;
+}
+
+// bending column (kappa_x, kappa_y, kappa_xy) and shear column (gamma_x, gamma_y) of
+// local DOF q = 3 a + comp at (xi, eta)
+__device__ void b_columns(int q, double xi, double eta, double hx, double hy, double bb[3], double bs[2]) {
+  const int a = q / 3, comp = q - 3 * a;
+  const double sx = corner_x(a) ? 1.0 : -1.0, sy = corner_y(a) ? 1.0 : -1.0;
+  const double N = 0.25 * (1.0 + sx * xi) * (1.0 + sy * eta);
+  const double dx = 0.25 * sx * (1.0 + sy * eta) * 2.0 / hx;
+  const double dy = 0.25 * sy * (1.0 + sx * xi) * 2.0 / hy;
+  bb[0] = bb[1] = bb[2] = 0.0;
+  bs[0] = bs[1] = 0.0;
+  if (comp == 0) {
+    bs[0] = dx;
+    bs[1] = dy;
+  } else if (comp == 1) {
+    bb[0] = dx;
+    bb[2] = dy;
+    bs[0] = -N;
+  } else {
+    bb[1] = dy;
+    bb[2] = dx;
+    bs[1] = -N;
+  }
+}
+
+__global__ void k_element(const double* __restrict__ dstar, const double* __restrict__ kgt, int n, double hx,
+                          double hy, float* __restrict__ k32, double* __restrict__ k64) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * 144) return;
+  const int s = (int)(t / 144), e = (int)(t - (int64_t)s * 144);
+  const int p = e / 12, q = e - 12 * p;
+  const double* d = dstar + (size_t)s * 6;
+  const double D[3][3] = {{d[0], d[1], d[2]}, {d[1], d[3], d[4]}, {d[2], d[4], d[5]}};
+  const double det = 0.25 * hx * hy, g = 0.577350269189625764509148780502;
+  double v = 0.0;
+  double bp[3], bq[3], sp[2], sq[2];
+  for (int gy = 0; gy < 2; ++gy)
+    for (int gx = 0; gx < 2; ++gx) {
+      const double xi = gx ? g : -g, eta = gy ? g : -g;
+      b_columns(p, xi, eta, hx, hy, bp, sp);
+      b_columns(q, xi, eta, hx, hy, bq, sq);
+      double m = 0.0;
+      for (int r = 0; r < 3; ++r) m += bp[r] * (D[r][0] * bq[0] + D[r][1] * bq[1] + D[r][2] * bq[2]);
+      v += det * m;
+    }
+  b_columns(p, 0.0, 0.0, hx, hy, bp, sp);
+  b_columns(q, 0.0, 0.0, hx, hy, bq, sq);
+  v += kgt[s] * 4.0 * det * (sp[0] * sq[0] + sp[1] * sq[1]);
+  if (k32) k32[t] = (float)v;
+  if (k64) k64[t] = v;
+}
+
+// K x (rows of node (i, j)) with the element matrix K in shared memory; the G x w-row
+// in *gw; optionally the node's 3x3 diagonal block of K in diag (11 12 13 22 23 33)
+template <bool DIAG>
+__device__ __forceinline__ float4 node_kx(const PGrid& g, const float* K, const float4* xe, int i, int j, bool bc,
+                                          float* gw, float* diag) {
+  const int np = g.nx + 1;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, gsum_all = 0.f;
+  for (int oy = 0; oy < 2; ++oy)
+    for (int ox = 0; ox < 2; ++ox) {
+      const int ei = i - ox, ej = j - oy;   // element whose corner (ox, oy) is this node
+      if (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) continue;
+      const int a = corner_of(ox, oy);
+      const float* Ka = K + 36 * a;   // rows 3a .. 3a+2
+      float gs = 0.f;
+      if (xe) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int ni = ei + corner_x(c), nj = ej + corner_y(c);
+          float4 v = xe[nj * np + ni];
+          if (bc) v = masked(free_of(g, ni, nj), v);
+          const float* r = Ka + 3 * c;
+          a0 += r[0] * v.x + r[1] * v.y + r[2] * v.z;
+          a1 += r[12] * v.x + r[13] * v.y + r[14] * v.z;
+          a2 += r[24] * v.x + r[25] * v.y + r[26] * v.z;
+          gs += corner_x(c) ? v.x : -v.x;
+        }
+      }
+      gsum_all += corner_x(a) ? gs : -gs;
+      if (DIAG) {
+        const float* r = Ka + 3 * a;
+        diag[0] += r[0];
+        diag[1] += r[1];
+        diag[2] += r[2];
+        diag[3] += r[13];
+        diag[4] += r[14];
+        diag[5] += r[26];
+      }
+    }
+  if (gw) *gw = gsum_all * (g.hy / (4.f * g.hx));
+  return make_float4(a0, a1, a2, 0.f);
+}
+
+__global__ void __launch_bounds__(kThreads) k_apply(PGrid g, const float* __restrict__ ke, const float4* __restrict__ x,
+                                                    const float4* __restrict__ b, float4* __restrict__ out,
+                                                    float4* __restrict__ gout, const int* __restrict__ active, int bc) {
+  const int e = blockIdx.y, s = e >> g.cshift;
+  if (active && !active[s]) return;
+  __shared__ float K[144];
+  for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke[(size_t)s * 144 + k];
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = g.nodes();
+  if (t >= nn) return;
+  const int i = t % (g.nx + 1), j = t / (g.nx + 1);
+  const size_t o = (size_t)e * nn;
+  float gw = 0.f;
+  float4 y = node_kx<false>(g, K, x + o, i, j, bc != 0, gout ? &gw : nullptr, nullptr);
+  if (b) {
+    const float4 bb = b[o + t];
+    y = make_float4(bb.x - y.x, bb.y - y.y, bb.z - y.z, 0.f);
+  }
+  const Free f = free_of(g, i, j);
+  if (bc) y = masked(f, y);
+  out[o + t] = y;
+  if (gout) gout[o + t] = make_float4((bc && !f.w) ? 0.f : gw, 0.f, 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(kThreads) k_smooth(PGrid g, const float* __restrict__ ke, const float4* __restrict__ b,
+                                                     const float4* __restrict__ x, float4* __restrict__ out,
+                                                     const int* __restrict__ active) {
+  const int e = blockIdx.y, s = e >> g.cshift;
+  if (active && !active[s]) return;
+  __shared__ float K[144];
+  for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke[(size_t)s * 144 + k];
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = g.nodes();
+  if (t >= nn) return;
+  const int i = t % (g.nx + 1), j = t / (g.nx + 1);
+  const size_t o = (size_t)e * nn;
+  float d[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const float4 kx = node_kx<true>(g, K, x ? x + o : nullptr, i, j, true, nullptr, d);
+  const Free f = free_of(g, i, j);
+  const float4 bb = b[o + t];
+  float r0 = f.w ? bb.x - kx.x : 0.f, r1 = f.tx ? bb.y - kx.y : 0.f, r2 = f.ty ? bb.z - kx.z : 0.f;
+  // restrict the block to the free DOFs (identity rows for the held ones)
+  if (!f.w) {
+    d[0] = 1.f;
+    d[1] = d[2] = 0.f;
+  }
+  if (!f.tx) {
+    d[3] = 1.f;
+    d[1] = d[4] = 0.f;
+  }
+  if (!f.ty) {
+    d[5] = 1.f;
+    d[2] = d[4] = 0.f;
+  }
+  // inverse of the symmetric block by cofactors
+  const float c00 = d[3] * d[5] - d[4] * d[4], c01 = d[2] * d[4] - d[1] * d[5], c02 = d[1] * d[4] - d[2] * d[3];
+  const float c11 = d[0] * d[5] - d[2] * d[2], c12 = d[1] * d[2] - d[0] * d[4], c22 = d[0] * d[3] - d[1] * d[1];
+  const float inv = kOmegaP / (d[0] * c00 + d[1] * c01 + d[2] * c02);
+  const float u0 = inv * (c00 * r0 + c01 * r1 + c02 * r2);
+  const float u1 = inv * (c01 * r0 + c11 * r1 + c12 * r2);
+  const float u2 = inv * (c02 * r0 + c12 * r1 + c22 * r2);
+  float4 xo = x ? x[o + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+  out[o + t] = masked(f, make_float4(xo.x + u0, xo.y + u1, xo.z + u2, 0.f));
+}
+
+__global__ void __launch_bounds__(kThreads) k_restrict(PGrid gf, PGrid gc, const float4* __restrict__ rf,
+                                                       float4* __restrict__ bc, const int* __restrict__ active) {
+  const int e = blockIdx.y, s = e >> gc.cshift;
+  if (active && !active[s]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nc = gc.nodes(), nf = gf.nodes();
+  if (t >= nc) return;
+  const int I = t % (gc.nx + 1), J = t / (gc.nx + 1);
+  const float4* r = rf + (size_t)e * nf;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  for (int dj = -1; dj <= 1; ++dj) {
+    const int fj = 2 * J + dj;
+    if (fj < 0 || fj > gf.ny) continue;
+    for (int di = -1; di <= 1; ++di) {
+      const int fi = 2 * I + di;
+      if (fi < 0 || fi > gf.nx) continue;
+      const float w = (di ? 0.5f : 1.f) * (dj ? 0.5f : 1.f);
+      const float4 v = r[fj * (gf.nx + 1) + fi];
+      a0 += w * v.x;
+      a1 += w * v.y;
+      a2 += w * v.z;
+    }
+  }
+  bc[(size_t)e * nc + t] = masked(free_of(gc, I, J), make_float4(a0, a1, a2, 0.f));
+}
+
+__global__ void __launch_bounds__(kThreads) k_prolong(PGrid gf, PGrid gc, const float4* __restrict__ xc,
+                                                      float4* __restrict__ xf, const int* __restrict__ active) {
+  const int e = blockIdx.y, s = e >> gf.cshift;
+  if (active && !active[s]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nf = gf.nodes(), nc = gc.nodes();
+  if (t >= nf) return;
+  const int i = t % (gf.nx + 1), j = t / (gf.nx + 1);
+  const float4* c = xc + (size_t)e * nc;
+  const int I0 = i >> 1, J0 = j >> 1, I1 = (i & 1) ? I0 + 1 : I0, J1 = (j & 1) ? J0 + 1 : J0;
+  const int cp = gc.nx + 1;
+  const float4 v00 = c[J0 * cp + I0], v10 = c[J0 * cp + I1], v01 = c[J1 * cp + I0], v11 = c[J1 * cp + I1];
+  const float4 xo = xf[(size_t)e * nf + t];
+  const float4 p = make_float4(0.25f * (v00.x + v10.x + v01.x + v11.x), 0.25f * (v00.y + v10.y + v01.y + v11.y),
+                               0.25f * (v00.z + v10.z + v01.z + v11.z), 0.f);
+  xf[(size_t)e * nf + t] = masked(free_of(gf, i, j), make_float4(xo.x + p.x, xo.y + p.y, xo.z + p.z, 0.f));
+}
+
+// one block per sample: assemble K on the free DOFs in shared memory, invert in place
+// (Gauss-Jordan without pivoting: K is symmetric positive definite there)
+__global__ void k_coarse_setup(PGrid g, const float* __restrict__ ke, const int* __restrict__ freedofs, int nf,
+                               float* __restrict__ ainv) {
+  extern __shared__ float smem[];
+  float* A = smem;                  // nf * nf
+  float* col = A + nf * nf;         // nf
+  int* map = reinterpret_cast<int*>(col + nf);   // nodes * 4
+  __shared__ float K[144];
+  __shared__ float pinv;
+  const int s = blockIdx.x;
+  const int nn = g.nodes();
+  for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke[(size_t)s * 144 + k];
+  for (int k = threadIdx.x; k < nf * nf; k += blockDim.x) A[k] = 0.f;
+  for (int k = threadIdx.x; k < 4 * nn; k += blockDim.x) map[k] = -1;
+  __syncthreads();
+  for (int k = threadIdx.x; k < nf; k += blockDim.x) map[freedofs[k]] = k;
+  __syncthreads();
+  const int ne = g.nx * g.ny;
+  for (int k = threadIdx.x; k < ne * 144; k += blockDim.x) {
+    const int el = k / 144, pq = k - 144 * el, p = pq / 12, q = pq - 12 * p;
+    const int ei = el % g.nx, ej = el / g.nx;
+    const int ap = p / 3, aq = q / 3;
+    const int np_ = (ej + corner_y(ap)) * (g.nx + 1) + ei + corner_x(ap);
+    const int nq = (ej + corner_y(aq)) * (g.nx + 1) + ei + corner_x(aq);
+    const int fp = map[4 * np_ + p - 3 * ap], fq = map[4 * nq + q - 3 * aq];
+    if (fp >= 0 && fq >= 0) atomicAdd(&A[fp * nf + fq], K[pq]);
+  }
+  for (int k = 0; k < nf; ++k) {
+    __syncthreads();
+    if (threadIdx.x == 0) pinv = 1.f / A[k * nf + k];
+    for (int r = threadIdx.x; r < nf; r += blockDim.x) col[r] = A[r * nf + k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < nf; c += blockDim.x) A[k * nf + c] = (c == k ? 1.f : A[k * nf + c]) * pinv;
+    __syncthreads();
+    for (int rc = threadIdx.x; rc < nf * nf; rc += blockDim.x) {
+      const int r = rc / nf, c = rc - r * nf;
+      if (r == k) continue;
+      A[rc] = (c == k ? 0.f : A[rc]) - col[r] * A[k * nf + c];
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nf * nf; k += blockDim.x) ainv[(size_t)s * nf * nf + k] = A[k];
+}
+
+__global__ void k_coarse_solve(PGrid g, const float* __restrict__ ainv, const int* __restrict__ freedofs, int nf,
+                               const float4* __restrict__ b, float4* __restrict__ x, const int* __restrict__ active) {
+  const int e = blockIdx.x, s = e >> g.cshift;
+  if (active && !active[s]) return;
+  __shared__ float bl[kMaxCoarseFree];
+  const int nn = g.nodes();
+  const float* bf = reinterpret_cast<const float*>(b + (size_t)e * nn);
+  float* xf = reinterpret_cast<float*>(x + (size_t)e * nn);
+  for (int k = threadIdx.x; k < nf; k += blockDim.x) bl[k] = bf[freedofs[k]];
+  for (int k = threadIdx.x; k < 4 * nn; k += blockDim.x) xf[k] = 0.f;
+  __syncthreads();
+  const float* A = ainv + (size_t)s * nf * nf;
+  for (int r = threadIdx.x; r < nf; r += blockDim.x) {
+    float acc = 0.f;
+    for (int c = 0; c < nf; ++c) acc += A[r * nf + c] * bl[c];
+    xf[freedofs[r]] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- LOBPCG
+
+__device__ __forceinline__ float hash_unit(uint32_t v) {
+  v ^= v >> 16;
+  v *= 0x7feb352dU;
+  v ^= v >> 15;
+  v *= 0x846ca68bU;
+  v ^= v >> 16;
+  return (float)(v >> 8) * (2.f / 16777216.f) - 1.f;
+}
+
+__global__ void k_init_start(PGrid g, float4* __restrict__ z) {
+  const int e = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = g.nodes();
+  if (t >= nn) return;
+  const int i = t % (g.nx + 1), j = t / (g.nx + 1);
+  const int c = e & ((1 << g.cshift) - 1);
+  const float w = hash_unit((uint32_t)t * 2654435761U + (uint32_t)c * 40503U + 17U);
+  z[(size_t)e * nn + t] = masked(free_of(g, i, j), make_float4(w, 0.f, 0.f, 0.f));
+}
+
+__global__ void __launch_bounds__(kThreads) k_residual(PGrid g, Eig E, const float4* __restrict__ kx,
+                                                       const float4* __restrict__ gx, float4* __restrict__ r) {
+  const int e = blockIdx.y, s = e >> g.cshift, c = e & ((1 << g.cshift) - 1);
+  if (!E.active[s]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = g.nodes();
+  if (t >= nn) return;
+  const size_t o = (size_t)e * nn + t;
+  const float mu = (float)E.mu[s * kCols + c];
+  const float4 k = kx[o], q = gx[o];
+  r[o] = make_float4(q.x - mu * k.x, q.y - mu * k.y, q.z - mu * k.z, 0.f);
+}
+
+// v: X, W, P, KX, KW, KP, GX, GW, GP, each [n][kCols][nodes]; one block row per sample
+__global__ void __launch_bounds__(kThreads) k_gram(PGrid g, Eig E, const __grid_constant__ Vecs V) {
+  const float4* const* vp = V.v;
+  const int s = blockIdx.y;
+  if (!E.active[s]) return;
+  const int nn = g.nodes();
+  double acc[2 * kGram];
+#pragma unroll
+  for (int k = 0; k < 2 * kGram; ++k) acc[k] = 0.0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += gridDim.x * blockDim.x) {
+    float4 S[kSub], KS[kSub];
+    float GS[kSub];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) {
+        const size_t o = ((size_t)s * kCols + c) * nn + t;
+        S[b * kCols + c] = vp[b][o];
+        KS[b * kCols + c] = vp[3 + b][o];
+        GS[b * kCols + c] = vp[6 + b][o].x;
+      }
+    int m = 0;
+#pragma unroll
+    for (int p = 0; p < kSub; ++p)
+#pragma unroll
+      for (int q = p; q < kSub; ++q, ++m) {
+        acc[m] += (double)(S[p].x * KS[q].x + S[p].y * KS[q].y + S[p].z * KS[q].z);
+        acc[kGram + m] += (double)(S[p].x * GS[q]);
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < 2 * kGram; ++k) {
+    const double v = warp_sum_d(acc[k]);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&E.gram[(size_t)s * 2 * kGram + k], v);
+  }
+}
+
+// symmetric eigen-decomposition by cyclic Jacobi rotations (n <= kSub)
+__device__ void jacobi_eig(double A[kSub][kSub], double V[kSub][kSub], int n) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      diag += A[i][i] * A[i][i];
+      for (int j = i + 1; j < n; ++j) off += A[i][j] * A[i][j];
+    }
+    if (off <= 1e-30 * diag || off == 0.0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (A[p][q] == 0.0) continue;
+        const double th = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+        const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(tt * tt + 1.0), sn = tt * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - sn * akq;
+          A[k][q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - sn * aqk;
+          A[q][k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - sn * vkq;
+          V[k][q] = sn * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+__global__ void k_rayleigh_ritz(Eig E, int n, double tol2, int max_iter, int first) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n || !E.active[s]) return;
+  double* gr = E.gram + (size_t)s * 2 * kGram;
+  double Km[kSub][kSub], Gm[kSub][kSub];
+  int m = 0;
+  for (int p = 0; p < kSub; ++p)
+    for (int q = p; q < kSub; ++q, ++m) {
+      Km[p][q] = Km[q][p] = gr[m];
+      Gm[p][q] = Gm[q][p] = gr[kGram + m];
+    }
+  for (int k = 0; k < 2 * kGram; ++k) gr[k] = 0.0;
+  double* cf = E.coef + (size_t)s * kSub * kCols;
+  if (!first) {
+    // preconditioned residual of the first column in the K norm (w = T r, r = G x - mu K x):
+    // w^T K w <= tol^2 mu^2 x^T K x; the eigenvalue error is about tol^2
+    const double mu0 = E.mu[s * kCols];
+    if (Km[2][2] <= tol2 * mu0 * mu0 * Km[0][0]) {   // converged: keep X
+      E.active[s] = 0;
+      return;
+    }
+    if (E.iters[s] >= max_iter) {   // cap: keep X, flag through iters
+      E.iters[s] = max_iter + 1;
+      E.active[s] = 0;
+      return;
+    }
+    E.iters[s] += 1;
+  }
+  // scale to unit K-diagonal, then Cholesky with dropping of dependent directions
+  double dsc[kSub];
+  for (int k = 0; k < kSub; ++k) dsc[k] = Km[k][k] > 0.0 ? 1.0 / sqrt(Km[k][k]) : 0.0;
+  int idx[kSub];
+  double L[kSub][kSub];
+  int nk = 0;
+  for (int k = 0; k < kSub; ++k) {
+    if (dsc[k] == 0.0) continue;
+    double l[kSub];
+    double d = Km[k][k] * dsc[k] * dsc[k];
+    for (int p = 0; p < nk; ++p) {
+      double v = Km[idx[p]][k] * dsc[idx[p]] * dsc[k];
+      for (int q = 0; q < p; ++q) v -= L[p][q] * l[q];
+      l[p] = v / L[p][p];
+      d -= l[p] * l[p];
+    }
+    if (!(d > 1e-6)) continue;
+    for (int p = 0; p < nk; ++p) L[nk][p] = l[p];
+    L[nk][nk] = sqrt(d);
+    idx[nk++] = k;
+  }
+  if (nk == 0) {   // no usable direction (the iterate vanished): stop as not converged
+    E.iters[s] = max_iter + 1;
+    E.active[s] = 0;
+    return;
+  }
+  // A = L^-1 Gs L^-T on the kept directions
+  double M[kSub][kSub], A[kSub][kSub], V[kSub][kSub];
+  for (int c = 0; c < nk; ++c)
+    for (int r = 0; r < nk; ++r) {   // M = L^-1 Gs, column c
+      double v = Gm[idx[r]][idx[c]] * dsc[idx[r]] * dsc[idx[c]];
+      for (int q = 0; q < r; ++q) v -= L[r][q] * M[q][c];
+      M[r][c] = v / L[r][r];
+    }
+  for (int c = 0; c < nk; ++c)
+    for (int r = 0; r < nk; ++r) {   // A = L^-1 M^T, column c
+      double v = M[c][r];
+      for (int q = 0; q < r; ++q) v -= L[r][q] * A[q][c];
+      A[r][c] = v / L[r][r];
+    }
+  for (int r = 0; r < nk; ++r)
+    for (int c = r + 1; c < nk; ++c) A[r][c] = A[c][r] = 0.5 * (A[r][c] + A[c][r]);
+  jacobi_eig(A, V, nk);
+  // the kCols largest eigenvalues, in descending order
+  int order[kSub];
+  for (int k = 0; k < nk; ++k) order[k] = k;
+  for (int a = 0; a < nk; ++a)
+    for (int b = a + 1; b < nk; ++b)
+      if (A[order[b]][order[b]] > A[order[a]][order[a]]) {
+        const int t = order[a];
+        order[a] = order[b];
+        order[b] = t;
+      }
+  for (int k = 0; k < kSub * kCols; ++k) cf[k] = 0.0;
+  for (int c = 0; c < kCols && c < nk; ++c) {
+    const int o = order[c];
+    E.mu[s * kCols + c] = A[o][o];
+    double y[kSub];   // back substitution L^T y = v
+    for (int r = nk - 1; r >= 0; --r) {
+      double v = V[r][o];
+      for (int q = r + 1; q < nk; ++q) v -= L[q][r] * y[q];
+      y[r] = v / L[r][r];
+    }
+    for (int r = 0; r < nk; ++r) cf[idx[r] * kCols + c] = y[r] * dsc[idx[r]];
+  }
+  atomicAdd(E.count, 1);
+}
+
+__global__ void __launch_bounds__(kThreads) k_update(PGrid g, Eig E, const __grid_constant__ Vecs V) {
+  float4* const* vp = V.v;
+  const int s = blockIdx.y;
+  if (!E.active[s]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = g.nodes();
+  if (t >= nn) return;
+  const double* c = E.coef + (size_t)s * kSub * kCols;
+  for (int set = 0; set < 3; ++set) {   // (X, W, P), (KX, KW, KP), (GX, GW, GP)
+    float4 v[kSub];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int k = 0; k < kCols; ++k) v[b * kCols + k] = vp[3 * set + b][((size_t)s * kCols + k) * nn + t];
+#pragma unroll
+    for (int k = 0; k < kCols; ++k) {
+      float x0 = 0.f, x1 = 0.f, x2 = 0.f, p0 = 0.f, p1 = 0.f, p2 = 0.f;
+#pragma unroll
+      for (int q = 0; q < kSub; ++q) {
+        const float w = (float)c[q * kCols + k];
+        x0 += w * v[q].x;
+        x1 += w * v[q].y;
+        x2 += w * v[q].z;
+        if (q >= kCols) {
+          p0 += w * v[q].x;
+          p1 += w * v[q].y;
+          p2 += w * v[q].z;
+        }
+      }
+      const size_t o = ((size_t)s * kCols + k) * nn + t;
+      vp[3 * set][o] = make_float4(x0, x1, x2, 0.f);
+      vp[3 * set + 2][o] = make_float4(p0, p1, p2, 0.f);
+    }
+  }
+}
+
+// x^T K x and x^T G x of column 0 in double, element by element
+__global__ void __launch_bounds__(kThreads) k_energy(PGrid g, const double* __restrict__ ke64,
+                                                     const float4* __restrict__ x, Eig E) {
+  const int s = blockIdx.y;
+  const int ne = g.nx * g.ny, nn = g.nodes();
+  const double* K = ke64 + (size_t)s * 144;
+  const float4* xs = x + (size_t)s * kCols * nn;   // column 0
+  const double gsc = (double)g.hy / (4.0 * (double)g.hx);
+  double ek = 0.0, eg = 0.0;
+  for (int el = blockIdx.x * blockDim.x + threadIdx.x; el < ne; el += gridDim.x * blockDim.x) {
+    const int ei = el % g.nx, ej = el / g.nx;
+    double u[12];
+    for (int a = 0; a < 4; ++a) {
+      const float4 v = xs[(ej + corner_y(a)) * (g.nx + 1) + ei + corner_x(a)];
+      u[3 * a] = v.x;
+      u[3 * a + 1] = v.y;
+      u[3 * a + 2] = v.z;
+    }
+    for (int p = 0; p < 12; ++p) {
+      double r = 0.0;
+      for (int q = 0; q < 12; ++q) r += K[p * 12 + q] * u[q];
+      ek += u[p] * r;
+    }
+    const double gs = -u[0] + u[3] + u[6] - u[9];
+    eg += gsc * gs * gs;
+  }
+  ek = warp_sum_d(ek);
+  eg = warp_sum_d(eg);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&E.energy[2 * s], ek);
+    atomicAdd(&E.energy[2 * s + 1], eg);
+  }
+}
+
+__global__ void k_panel_qoi(Eig E, int n, double ly, double p_star, int max_iter, double* __restrict__ q,
+                            int* __restrict__ status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const double ek = E.energy[2 * s], eg = E.energy[2 * s + 1];
+  const double lam = ek / eg;
+  const bool ok = eg > 0.0 && isfinite(lam) && lam > 0.0 && E.iters[s] <= max_iter;
+  const double P = lam * ly * 1e-3;
+  q[2 * s] = P;
+  q[2 * s + 1] = P < p_star ? 1.0 : 0.0;
+  status[s] = ok ? 0 : (int)MLMC_ERR_NOT_CONVERGED;
+}
+
+inline dim3 grid_nodes(const PGrid& g, int rows) {
+  return dim3((unsigned)((g.nodes() + kThreads - 1) / kThreads), (unsigned)rows);
+}
+
+}  // namespace
+
+cudaError_t launch_laminate(const Laminate& lam, const double* xi, int n, double* dstar, double* kgt,
+                            cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_laminate<<<(n + 127) / 128, 128, 0, st>>>(lam, xi, n, dstar, kgt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_element_matrices(const double* dstar, const double* kgt, int n, double hx, double hy, float* k32,
+                                    double* k64, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t total = (int64_t)n * 144;
+  k_element<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(dstar, kgt, n, hx, hy, k32, k64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const PGrid& g, const float* ke, const float4* x, const float4* b, float4* out,
+                         float4* gout, const int* active, bool bc, cudaStream_t st) {
+  if (g.nb <= 0) return cudaSuccess;
+  k_apply<<<grid_nodes(g, g.nb), kThreads, 0, st>>>(g, ke, x, b, out, gout, active, bc ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_smooth(const PGrid& g, const float* ke, const float4* b, const float4* x, float4* out,
+                          const int* active, cudaStream_t st) {
+  if (g.nb <= 0) return cudaSuccess;
+  k_smooth<<<grid_nodes(g, g.nb), kThreads, 0, st>>>(g, ke, b, x, out, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const PGrid& fine, const PGrid& coarse, const float4* rf, float4* bc, const int* active,
+                            cudaStream_t st) {
+  if (coarse.nb <= 0) return cudaSuccess;
+  k_restrict<<<grid_nodes(coarse, coarse.nb), kThreads, 0, st>>>(fine, coarse, rf, bc, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(const PGrid& fine, const PGrid& coarse, const float4* xc, float4* xf, const int* active,
+                           cudaStream_t st) {
+  if (fine.nb <= 0) return cudaSuccess;
+  k_prolong<<<grid_nodes(fine, fine.nb), kThreads, 0, st>>>(fine, coarse, xc, xf, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_setup(const PGrid& g, const float* ke, int n_samples, const int* freedofs, int nf,
+                                float* ainv, cudaStream_t st) {
+  if (n_samples <= 0) return cudaSuccess;
+  if (nf <= 0 || nf > kMaxCoarseFree) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float) * ((size_t)nf * nf + nf) + sizeof(int) * 4 * (size_t)g.nodes();
+  cudaError_t e = cudaFuncSetAttribute(k_coarse_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_coarse_setup<<<n_samples, 256, smem, st>>>(g, ke, freedofs, nf, ainv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve(const PGrid& g, const float* ainv, const int* freedofs, int nf, const float4* b,
+                                float4* x, const int* active, cudaStream_t st) {
+  if (g.nb <= 0) return cudaSuccess;
+  if (nf <= 0 || nf > kMaxCoarseFree) return cudaErrorInvalidValue;
+  k_coarse_solve<<<g.nb, kThreads, 0, st>>>(g, ainv, freedofs, nf, b, x, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_start(const PGrid& g, float4* z, cudaStream_t st) {
+  if (g.nb <= 0) return cudaSuccess;
+  k_init_start<<<grid_nodes(g, g.nb), kThreads, 0, st>>>(g, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const PGrid& g, const Eig& E, const float4* kx, const float4* gx, float4* r,
+                            cudaStream_t st) {
+  if (g.nb <= 0) return cudaSuccess;
+  k_residual<<<grid_nodes(g, g.nb), kThreads, 0, st>>>(g, E, kx, gx, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram(const PGrid& g, const Eig& E, const Vecs& v, cudaStream_t st) {
+  const int n = g.nb >> g.cshift;
+  if (n <= 0) return cudaSuccess;
+  const unsigned bx = (unsigned)std::min((g.nodes() + kThreads * 4 - 1) / (kThreads * 4), 64);
+  k_gram<<<dim3(bx, (unsigned)n), kThreads, 0, st>>>(g, E, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rayleigh_ritz(const Eig& E, int n, double tol, int max_iter, bool first, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_rayleigh_ritz<<<(n + 63) / 64, 64, 0, st>>>(E, n, tol * tol, max_iter, first ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const PGrid& g, const Eig& E, const Vecs& v, cudaStream_t st) {
+  const int n = g.nb >> g.cshift;
+  if (n <= 0) return cudaSuccess;
+  k_update<<<grid_nodes(g, n), kThreads, 0, st>>>(g, E, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const PGrid& g, const double* ke64, const float4* x, const Eig& E, cudaStream_t st) {
+  const int n = g.nb >> g.cshift;
+  if (n <= 0) return cudaSuccess;
+  const unsigned bx = (unsigned)std::min((g.nx * g.ny + kThreads - 1) / kThreads, 32);
+  k_energy<<<dim3(bx, (unsigned)n), kThreads, 0, st>>>(g, ke64, x, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_panel_qoi(const Eig& E, int n, double ly, double p_star, int max_iter, double* q, int* status,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_panel_qoi<<<(n + 127) / 128, 128, 0, st>>>(E, n, ly, p_star, max_iter, q, status);
+  return cudaGetLastError();
+}
+
+}  // namespace mlmcp

@@ -1,0 +1,91 @@
+// Internal interfaces of the panel-buckling engine (Reissner-Mindlin Q4 plates).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace mlmcp {
+
+constexpr int kMaxPlies = 32;
+constexpr int kMaxCoarseFree = 192;   // free DOFs of the coarsest mesh (dense inverse in shared memory)
+constexpr int kCols = 2;              // LOBPCG block size
+constexpr int kSub = 3 * kCols;       // Rayleigh-Ritz subspace [X, W, P]
+constexpr int kGram = kSub * (kSub + 1) / 2;
+constexpr float kOmegaP = 0.5f;       // block-Jacobi damping of the smoother
+
+// Laminate constants, identical for every sample: ply stiffness, stacking, thickness.
+struct Laminate {
+  double E11, E22, G12, nu12, G13, k_shear, t_ply, std_rad;
+  int n_plies;
+  double psi[kMaxPlies];   // pristine angles, radians, bottom ply first
+};
+
+// One mesh of one solve: nb vectors ("batch entries") on nx x ny square elements; a
+// vector entry b belongs to sample b >> cshift. Vectors are [entry][node][4] floats
+// (w, theta_x, theta_y, 0), node = j (nx + 1) + i.
+struct PGrid {
+  int nx, ny, nb, cshift, hard;
+  float hx, hy;
+  __host__ __device__ int nodes() const { return (nx + 1) * (ny + 1); }
+};
+
+// Per-sample laminate of a solve: dstar [n][6] (11, 12, 16, 22, 26, 66), kgt [n].
+cudaError_t launch_laminate(const Laminate& lam, const double* xi, int n, double* dstar, double* kgt,
+                            cudaStream_t st);
+// Element matrices [n][144] (row-major, local DOF 3 a + c, corners (i, j), (i+1, j),
+// (i+1, j+1), (i, j+1)) of every sample on elements hx x hy; k32 and k64 nullable.
+cudaError_t launch_element_matrices(const double* dstar, const double* kgt, int n, double hx, double hy, float* k32,
+                                    double* k64, cudaStream_t st);
+
+// out = K x (or b - K x with b set) and optionally gout = G x, for entries whose
+// sample is active (null: all). bc: zero the constrained DOFs of inputs and outputs.
+cudaError_t launch_apply(const PGrid& g, const float* ke, const float4* x, const float4* b, float4* out,
+                         float4* gout, const int* active, bool bc, cudaStream_t st);
+// out = x + w D^-1 (b - K x) (x null: out = w D^-1 b), D the nodal 3x3 diagonal blocks
+cudaError_t launch_smooth(const PGrid& g, const float* ke, const float4* b, const float4* x, float4* out,
+                          const int* active, cudaStream_t st);
+// bc = P^T rf (full weighting), xf += P xc (bilinear)
+cudaError_t launch_restrict(const PGrid& fine, const PGrid& coarse, const float4* rf, float4* bc, const int* active,
+                            cudaStream_t st);
+cudaError_t launch_prolong(const PGrid& fine, const PGrid& coarse, const float4* xc, float4* xf, const int* active,
+                           cudaStream_t st);
+// Coarsest mesh: per-sample dense inverse of K on the free DOFs (free[k] = 4 node + c)
+cudaError_t launch_coarse_setup(const PGrid& g, const float* ke, int n_samples, const int* free, int nf, float* ainv,
+                                cudaStream_t st);
+cudaError_t launch_coarse_solve(const PGrid& g, const float* ainv, const int* free, int nf, const float4* b,
+                                float4* x, const int* active, cudaStream_t st);
+
+// LOBPCG state of a solve (per sample unless noted).
+struct Eig {
+  double* gram;     // [n][2][kGram]: K and G Gram matrices of [X0 X1 W0 W1 P0 P1]
+  double* coef;     // [n][kSub][kCols]: Ritz coefficients
+  double* mu;       // [n][kCols]
+  double* energy;   // [n][2]: x^T K x, x^T G x of the final vector (double)
+  int* active;      // [n]
+  int* iters;       // [n]
+  int* count;       // [1] samples still active after the latest Rayleigh-Ritz
+};
+
+// X (both columns) from a fixed pseudo-random w field: X = G Z (to be preconditioned)
+cudaError_t launch_init_start(const PGrid& g, float4* z, cudaStream_t st);
+// R = G X - mu K X per column
+cudaError_t launch_residual(const PGrid& g, const Eig& E, const float4* kx, const float4* gx, float4* r,
+                            cudaStream_t st);
+// The Rayleigh-Ritz vector sets: v[0..2] = X, W, P; v[3..5] = K X, K W, K P;
+// v[6..8] = G X, G W, G P, each [n][kCols][nodes].
+struct Vecs {
+  float4* v[9];
+};
+cudaError_t launch_gram(const PGrid& g, const Eig& E, const Vecs& v, cudaStream_t st);
+// Rayleigh-Ritz per sample; convergence test on the preconditioned residual W of the
+// current iterate (its K norm against mu times X's); bumps count
+cudaError_t launch_rayleigh_ritz(const Eig& E, int n, double tol, int max_iter, bool first, cudaStream_t st);
+// X, P (and K X, K P, G X, G P) from the Ritz coefficients
+cudaError_t launch_update(const PGrid& g, const Eig& E, const Vecs& v, cudaStream_t st);
+// energies of column 0 in double with the double element matrices
+cudaError_t launch_energy(const PGrid& g, const double* ke64, const float4* x, const Eig& E, cudaStream_t st);
+// q[n][2] = (P [kN], P < p_star); status from the iteration cap and the energies
+cudaError_t launch_panel_qoi(const Eig& E, int n, double ly, double p_star, int max_iter, double* q, int* status,
+                             cudaStream_t st);
+
+}  // namespace mlmcp

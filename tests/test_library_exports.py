@@ -15,7 +15,7 @@ def declared_functions():
         if f.endswith(".h"):
             text = open(os.path.join(ROOT, "include", f)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names += re.findall(r"\b(mlmc(?:3d)?_[a-z0-9_]+)\s*\(", text)
+            names += re.findall(r"\b(mlmc(?:3d|p)?_[a-z0-9_]+)\s*\(", text)
     return sorted(set(names))
 
 
@@ -23,7 +23,7 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("mlmc_create", "mlmc_destroy", "mlmc_sample_level", "mlmc_solve_batch",
                      "mlmc_estimate", "mlmc_last_error", "mlmc3d_create", "mlmc3d_sample_level",
-                     "mlmc3d_solve_batch"):
+                     "mlmc3d_solve_batch", "mlmcp_create", "mlmcp_sample_level", "mlmcp_solve_batch"):
         assert required in names
 
 
@@ -70,3 +70,24 @@ def test_create3_rejects_invalid_configs_without_a_gpu(override, msg):
     from workloads import HEX8_MIXED_4LEVEL
     with pytest.raises(binding.MLMCError, match=msg):
         binding.mlmc3d_create(binding.config3_from_workload(HEX8_MIXED_4LEVEL, **override), stream=0)
+
+
+def test_configp_marshalling():
+    from paper_1907_10271_gb300 import binding
+    from workloads import PANEL_RM_4LEVEL
+    c = binding.configp_from_workload(PANEL_RM_4LEVEL)
+    assert (c.nx0, c.ny0, c.levels, c.n_plies, c.hard_support) == (24, 8, 4, 8, 1)
+    assert list(c.plies_deg[:8]) == [45.0, -45.0, -45.0, 45.0, -45.0, 45.0, 45.0, -45.0]
+    assert (c.t_ply, c.ply_std_deg, c.p_star, c.lx, c.ly) == (0.8, 3.0, 272.47, 636.0, 212.0)
+    assert binding.configp_from_workload(PANEL_RM_4LEVEL, bc="soft").hard_support == 0
+
+
+@pytest.mark.parametrize("override,msg", [(dict(levels=0), "levels"), (dict(t_ply=0.0), "thickness"),
+                                          (dict(nx0=25), "coarsest"), (dict(tol=-1.0), "tolerances"),
+                                          (dict(G13=0.0), "moduli")])
+def test_createp_rejects_invalid_configs_without_a_gpu(override, msg):
+    # validation runs before any CUDA call, so it answers on a machine without a GPU
+    from paper_1907_10271_gb300 import binding
+    from workloads import PANEL_RM_4LEVEL
+    with pytest.raises(binding.MLMCError, match=msg):
+        binding.mlmcp_create(binding.configp_from_workload(PANEL_RM_4LEVEL, **override), stream=0)
