@@ -746,7 +746,7 @@ def run_panel(B, steps=2, warmup=1, parity=True):
                     times[m].append(time.perf_counter() - t1)
                     err = max(err, abs(q[2 * k] / ref[0] - 1.0))
                     ind_ok = ind_ok and (q[2 * k + 1] == ref[1] or abs(ref[0] / W["p_star"] - 1) < 1e-6)
-                out["qoi_parity"] = {"solves": len(items), "max_rel_err_load": err, "indicator_agrees": ind_ok,
+                out["qoi_parity"] = {"solves": len(items), "max_rel_err_load": float(err), "indicator_agrees": bool(ind_ok),
                                      "note": "GPU vs oracle (FP64 CLT + Q4, sparse eigen-solve) on the same "
                                              "perturbations"}
                 out["cpu_baseline"] = {"kind": "oracle", "cores": 1,

@@ -64,7 +64,8 @@ typedef struct {
   double p_star;               /* failure threshold of quantity 1, kN */
   uint64_t seed;
   double tol;                  /* LOBPCG stop: (w^T K w)^1/2 <= tol mu (x^T K x)^1/2 with w the
-                                  preconditioned residual of the first vector (0: 5e-5) */
+                                  preconditioned residual of the first vector (0: 1e-4;
+                                  the load error is about tol^2) */
   int32_t max_iter;            /* LOBPCG iterations (0: 120) */
 } mlmcp_config;
 

@@ -80,7 +80,7 @@ struct mlmcp_ctx {
   mlmc::LevelAcc* acc_dev = nullptr;
   std::vector<mlmc::LevelAcc> acc_host;
   int last_iters = 0;
-  double tol = 5e-5;
+  double tol = 1e-4;
   int max_iter = 120;
 
   mlmc_status fail(mlmc_status s, const std::string& m) {
@@ -316,7 +316,7 @@ mlmc_status mlmcp_create(const mlmcp_config* cfg, void* cuda_stream, mlmcp_ctx**
   auto c = new mlmcp_ctx;
   c->cfg = k;
   c->st = static_cast<cudaStream_t>(cuda_stream);
-  c->tol = k.tol > 0 ? k.tol : 5e-5;
+  c->tol = k.tol > 0 ? k.tol : 1e-4;
   c->max_iter = k.max_iter > 0 ? k.max_iter : 120;
   c->lam.E11 = k.E11;
   c->lam.E22 = k.E22;
