@@ -394,15 +394,17 @@ __global__ void __launch_bounds__(kThreads) k_residual(PGrid g, Eig E, const flo
   r[o] = make_float4(q.x - mu * k.x, q.y - mu * k.y, q.z - mu * k.z, 0.f);
 }
 
-// v: X, W, P, KX, KW, KP, GX, GW, GP, each [n][kCols][nodes]; one block row per sample
+// v: X, W, P, KX, KW, KP, GX, GW, GP, each [n][kCols][nodes]; one block row per sample.
+// A thread sums the products of its few nodes in single precision; warps and the block
+// add in double, and each block adds its 42 sums to the sample's Gram matrices.
 __global__ void __launch_bounds__(kThreads) k_gram(PGrid g, Eig E, const __grid_constant__ Vecs V) {
   const float4* const* vp = V.v;
   const int s = blockIdx.y;
   if (!E.active[s]) return;
   const int nn = g.nodes();
-  double acc[2 * kGram];
+  float acc[2 * kGram];
 #pragma unroll
-  for (int k = 0; k < 2 * kGram; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 2 * kGram; ++k) acc[k] = 0.f;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += gridDim.x * blockDim.x) {
     float4 S[kSub], KS[kSub];
     float GS[kSub];
@@ -420,71 +422,84 @@ __global__ void __launch_bounds__(kThreads) k_gram(PGrid g, Eig E, const __grid_
     for (int p = 0; p < kSub; ++p)
 #pragma unroll
       for (int q = p; q < kSub; ++q, ++m) {
-        acc[m] += (double)(S[p].x * KS[q].x + S[p].y * KS[q].y + S[p].z * KS[q].z);
-        acc[kGram + m] += (double)(S[p].x * GS[q]);
+        acc[m] += S[p].x * KS[q].x + S[p].y * KS[q].y + S[p].z * KS[q].z;
+        acc[kGram + m] += S[p].x * GS[q];
       }
   }
+  __shared__ double red[kThreads / 32][2 * kGram];
+  const int warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 2 * kGram; ++k) {
-    const double v = warp_sum_d(acc[k]);
-    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&E.gram[(size_t)s * 2 * kGram + k], v);
+    const double v = warp_sum_d((double)acc[k]);
+    if ((threadIdx.x & 31) == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * kGram; k += blockDim.x) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) v += red[w][k];
+    if (v != 0.0) atomicAdd(&E.gram[(size_t)s * 2 * kGram + k], v);
   }
 }
 
-// symmetric eigen-decomposition by cyclic Jacobi rotations (n <= kSub)
-__device__ void jacobi_eig(double A[kSub][kSub], double V[kSub][kSub], int n) {
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) V[i][j] = i == j ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0, diag = 0.0;
-    for (int i = 0; i < n; ++i) {
-      diag += A[i][i] * A[i][i];
-      for (int j = i + 1; j < n; ++j) off += A[i][j] * A[i][j];
-    }
-    if (off <= 1e-30 * diag || off == 0.0) break;
-    for (int p = 0; p < n; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        if (A[p][q] == 0.0) continue;
-        const double th = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
-        const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double c = 1.0 / sqrt(tt * tt + 1.0), sn = tt * c;
-        for (int k = 0; k < n; ++k) {
-          const double akp = A[k][p], akq = A[k][q];
-          A[k][p] = c * akp - sn * akq;
-          A[k][q] = sn * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double apk = A[p][k], aqk = A[q][k];
-          A[p][k] = c * apk - sn * aqk;
-          A[q][k] = sn * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = V[k][p], vkq = V[k][q];
-          V[k][p] = c * vkp - sn * vkq;
-          V[k][q] = sn * vkp + c * vkq;
-        }
-      }
+// One Jacobi rotation of the symmetric kSub x kSub matrix A (both triangles kept)
+// zeroing A[p][q], accumulated into V. p, q are compile-time after unrolling, so A and V
+// stay in registers.
+__device__ __forceinline__ void jacobi_rotate(double (&A)[kSub][kSub], double (&V)[kSub][kSub], int p, int q) {
+  const double apq = A[p][q];
+  if (apq == 0.0) return;
+  const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
+  const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+  const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+#pragma unroll
+  for (int k = 0; k < kSub; ++k) {
+    if (k == p || k == q) continue;
+    const double akp = A[k][p], akq = A[k][q];
+    A[k][p] = A[p][k] = c * akp - sn * akq;
+    A[k][q] = A[q][k] = sn * akp + c * akq;
+  }
+  A[p][p] -= t * apq;
+  A[q][q] += t * apq;
+  A[p][q] = A[q][p] = 0.0;
+#pragma unroll
+  for (int k = 0; k < kSub; ++k) {
+    const double vkp = V[k][p], vkq = V[k][q];
+    V[k][p] = c * vkp - sn * vkq;
+    V[k][q] = sn * vkp + c * vkq;
   }
 }
 
-__global__ void k_rayleigh_ritz(Eig E, int n, double tol2, int max_iter, int first) {
+// Per-sample Rayleigh-Ritz on S = [X0 X1 W0 W1 P0 P1]: the K and G Gram matrices are
+// scaled to unit K-diagonal, K is factored by Cholesky with dependent directions
+// dropped (a dropped direction gets an identity row and eigenvalue -1, below every
+// Ritz value mu > 0), A = L^-1 G L^-T is diagonalised by cyclic Jacobi, and the two
+// largest eigenpairs give the coefficients C = D L^-T V. All loops have compile-time
+// bounds so that the small matrices live in registers.
+__global__ void __launch_bounds__(32) k_rayleigh_ritz(Eig E, int n, double tol2, int max_iter, int first) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || !E.active[s]) return;
   double* gr = E.gram + (size_t)s * 2 * kGram;
-  double Km[kSub][kSub], Gm[kSub][kSub];
-  int m = 0;
-  for (int p = 0; p < kSub; ++p)
-    for (int q = p; q < kSub; ++q, ++m) {
-      Km[p][q] = Km[q][p] = gr[m];
-      Gm[p][q] = Gm[q][p] = gr[kGram + m];
-    }
+  double A[kSub][kSub], L[kSub][kSub];   // A first holds the scaled G, L the scaled K
+  double dsc[kSub];
+  bool keep[kSub];
+  {
+    int m = 0;
+#pragma unroll
+    for (int p = 0; p < kSub; ++p)
+#pragma unroll
+      for (int q = p; q < kSub; ++q, ++m) {
+        L[p][q] = L[q][p] = gr[m];
+        A[p][q] = A[q][p] = gr[kGram + m];
+      }
+  }
+#pragma unroll
   for (int k = 0; k < 2 * kGram; ++k) gr[k] = 0.0;
-  double* cf = E.coef + (size_t)s * kSub * kCols;
   if (!first) {
     // preconditioned residual of the first column in the K norm (w = T r, r = G x - mu K x):
     // w^T K w <= tol^2 mu^2 x^T K x; the eigenvalue error is about tol^2
     const double mu0 = E.mu[s * kCols];
-    if (Km[2][2] <= tol2 * mu0 * mu0 * Km[0][0]) {   // converged: keep X
+    E.eta2[s] = L[2][2] / (mu0 * mu0 * L[0][0]);
+    if (L[2][2] <= tol2 * mu0 * mu0 * L[0][0]) {   // converged: keep X
       E.active[s] = 0;
       return;
     }
@@ -495,71 +510,130 @@ __global__ void k_rayleigh_ritz(Eig E, int n, double tol2, int max_iter, int fir
     }
     E.iters[s] += 1;
   }
-  // scale to unit K-diagonal, then Cholesky with dropping of dependent directions
-  double dsc[kSub];
-  for (int k = 0; k < kSub; ++k) dsc[k] = Km[k][k] > 0.0 ? 1.0 / sqrt(Km[k][k]) : 0.0;
-  int idx[kSub];
-  double L[kSub][kSub];
-  int nk = 0;
+#pragma unroll
   for (int k = 0; k < kSub; ++k) {
-    if (dsc[k] == 0.0) continue;
-    double l[kSub];
-    double d = Km[k][k] * dsc[k] * dsc[k];
-    for (int p = 0; p < nk; ++p) {
-      double v = Km[idx[p]][k] * dsc[idx[p]] * dsc[k];
-      for (int q = 0; q < p; ++q) v -= L[p][q] * l[q];
-      l[p] = v / L[p][p];
-      d -= l[p] * l[p];
-    }
-    if (!(d > 1e-6)) continue;
-    for (int p = 0; p < nk; ++p) L[nk][p] = l[p];
-    L[nk][nk] = sqrt(d);
-    idx[nk++] = k;
+    dsc[k] = L[k][k] > 0.0 ? 1.0 / sqrt(L[k][k]) : 0.0;
+    keep[k] = dsc[k] > 0.0;
   }
+#pragma unroll
+  for (int p = 0; p < kSub; ++p)
+#pragma unroll
+    for (int q = 0; q < kSub; ++q) {
+      L[p][q] *= dsc[p] * dsc[q];
+      A[p][q] *= dsc[p] * dsc[q];
+    }
+  // Cholesky of the scaled K in place (lower triangle), dropping dependent directions
+#pragma unroll
+  for (int k = 0; k < kSub; ++k) {
+#pragma unroll
+    for (int p = 0; p < k; ++p) {
+      double v = L[k][p];
+#pragma unroll
+      for (int q = 0; q < p; ++q) v -= L[k][q] * L[p][q];
+      L[k][p] = keep[p] ? v / L[p][p] : 0.0;
+    }
+    double d = L[k][k];
+#pragma unroll
+    for (int q = 0; q < k; ++q) d -= L[k][q] * L[k][q];
+    if (keep[k] && d > 1e-6) {
+      L[k][k] = sqrt(d);
+    } else {
+      keep[k] = false;
+#pragma unroll
+      for (int q = 0; q < k; ++q) L[k][q] = 0.0;
+      L[k][k] = 1.0;
+    }
+  }
+  int nk = 0;
+#pragma unroll
+  for (int k = 0; k < kSub; ++k) nk += keep[k] ? 1 : 0;
   if (nk == 0) {   // no usable direction (the iterate vanished): stop as not converged
     E.iters[s] = max_iter + 1;
     E.active[s] = 0;
     return;
   }
-  // A = L^-1 Gs L^-T on the kept directions
-  double M[kSub][kSub], A[kSub][kSub], V[kSub][kSub];
-  for (int c = 0; c < nk; ++c)
-    for (int r = 0; r < nk; ++r) {   // M = L^-1 Gs, column c
-      double v = Gm[idx[r]][idx[c]] * dsc[idx[r]] * dsc[idx[c]];
-      for (int q = 0; q < r; ++q) v -= L[r][q] * M[q][c];
-      M[r][c] = v / L[r][r];
-    }
-  for (int c = 0; c < nk; ++c)
-    for (int r = 0; r < nk; ++r) {   // A = L^-1 M^T, column c
-      double v = M[c][r];
+  // A <- L^-1 A (forward substitution per column) on the kept directions
+#pragma unroll
+  for (int p = 0; p < kSub; ++p)
+#pragma unroll
+    for (int q = 0; q < kSub; ++q)
+      if (!keep[p] || !keep[q]) A[p][q] = 0.0;
+#pragma unroll
+  for (int c = 0; c < kSub; ++c)
+#pragma unroll
+    for (int r = 0; r < kSub; ++r) {
+      double v = A[r][c];
+#pragma unroll
       for (int q = 0; q < r; ++q) v -= L[r][q] * A[q][c];
       A[r][c] = v / L[r][r];
     }
-  for (int r = 0; r < nk; ++r)
-    for (int c = r + 1; c < nk; ++c) A[r][c] = A[c][r] = 0.5 * (A[r][c] + A[c][r]);
-  jacobi_eig(A, V, nk);
-  // the kCols largest eigenvalues, in descending order
-  int order[kSub];
-  for (int k = 0; k < nk; ++k) order[k] = k;
-  for (int a = 0; a < nk; ++a)
-    for (int b = a + 1; b < nk; ++b)
-      if (A[order[b]][order[b]] > A[order[a]][order[a]]) {
-        const int t = order[a];
-        order[a] = order[b];
-        order[b] = t;
-      }
-  for (int k = 0; k < kSub * kCols; ++k) cf[k] = 0.0;
-  for (int c = 0; c < kCols && c < nk; ++c) {
-    const int o = order[c];
-    E.mu[s * kCols + c] = A[o][o];
-    double y[kSub];   // back substitution L^T y = v
-    for (int r = nk - 1; r >= 0; --r) {
-      double v = V[r][o];
-      for (int q = r + 1; q < nk; ++q) v -= L[q][r] * y[q];
+  // T = L^-1 A^T = L^-1 G L^-T, symmetrised; dropped directions get eigenvalue -1
+  double T[kSub][kSub], V[kSub][kSub];
+#pragma unroll
+  for (int c = 0; c < kSub; ++c)
+#pragma unroll
+    for (int r = 0; r < kSub; ++r) {
+      double v = A[c][r];
+#pragma unroll
+      for (int q = 0; q < r; ++q) v -= L[r][q] * T[q][c];
+      T[r][c] = v / L[r][r];
+    }
+#pragma unroll
+  for (int r = 0; r < kSub; ++r) {
+#pragma unroll
+    for (int c = r + 1; c < kSub; ++c) T[r][c] = T[c][r] = 0.5 * (T[r][c] + T[c][r]);
+    if (!keep[r]) T[r][r] = -1.0;
+#pragma unroll
+    for (int c = 0; c < kSub; ++c) V[r][c] = r == c ? 1.0 : 0.0;
+  }
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    double off = 0.0, diag = 0.0;
+#pragma unroll
+    for (int p = 0; p < kSub; ++p) {
+      diag += T[p][p] * T[p][p];
+#pragma unroll
+      for (int q = p + 1; q < kSub; ++q) off += T[p][q] * T[p][q];
+    }
+    if (off <= 1e-30 * diag) break;
+#pragma unroll
+    for (int p = 0; p < kSub; ++p)
+#pragma unroll
+      for (int q = p + 1; q < kSub; ++q) jacobi_rotate(T, V, p, q);
+  }
+  // the two largest eigenvalues (runtime indices only compared, never used to index)
+  double best0 = -1e300, best1 = -1e300;
+  int o0 = 0, o1 = 0;
+#pragma unroll
+  for (int k = 0; k < kSub; ++k)
+    if (T[k][k] > best0) {
+      best0 = T[k][k];
+      o0 = k;
+    }
+#pragma unroll
+  for (int k = 0; k < kSub; ++k)
+    if (k != o0 && T[k][k] > best1) {
+      best1 = T[k][k];
+      o1 = k;
+    }
+  double* cf = E.coef + (size_t)s * kSub * kCols;
+#pragma unroll
+  for (int c = 0; c < kCols; ++c) {
+    const int o = c == 0 ? o0 : o1;
+    double y[kSub];
+#pragma unroll
+    for (int r = kSub - 1; r >= 0; --r) {   // back substitution L^T y = v
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < kSub; ++j) v = j == o ? V[r][j] : v;
+#pragma unroll
+      for (int q = r + 1; q < kSub; ++q) v -= L[q][r] * y[q];
       y[r] = v / L[r][r];
     }
-    for (int r = 0; r < nk; ++r) cf[idx[r] * kCols + c] = y[r] * dsc[idx[r]];
+#pragma unroll
+    for (int r = 0; r < kSub; ++r) cf[r * kCols + c] = keep[r] ? y[r] * dsc[r] : 0.0;
   }
+  E.mu[s * kCols] = best0;
+  E.mu[s * kCols + 1] = best1;
   atomicAdd(E.count, 1);
 }
 
@@ -571,7 +645,8 @@ __global__ void __launch_bounds__(kThreads) k_update(PGrid g, Eig E, const __gri
   const int nn = g.nodes();
   if (t >= nn) return;
   const double* c = E.coef + (size_t)s * kSub * kCols;
-  for (int set = 0; set < 3; ++set) {   // (X, W, P), (KX, KW, KP), (GX, GW, GP)
+  {
+    const int set = 0;   // X and P; K X, K P, G X, G P are recomputed from them
     float4 v[kSub];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
@@ -737,7 +812,7 @@ cudaError_t launch_gram(const PGrid& g, const Eig& E, const Vecs& v, cudaStream_
 
 cudaError_t launch_rayleigh_ritz(const Eig& E, int n, double tol, int max_iter, bool first, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_rayleigh_ritz<<<(n + 63) / 64, 64, 0, st>>>(E, n, tol * tol, max_iter, first ? 1 : 0);
+  k_rayleigh_ritz<<<(n + 31) / 32, 32, 0, st>>>(E, n, tol * tol, max_iter, first ? 1 : 0);
   return cudaGetLastError();
 }
 

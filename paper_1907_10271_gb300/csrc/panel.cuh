@@ -61,6 +61,7 @@ struct Eig {
   double* coef;     // [n][kSub][kCols]: Ritz coefficients
   double* mu;       // [n][kCols]
   double* energy;   // [n][2]: x^T K x, x^T G x of the final vector (double)
+  double* eta2;     // [n]: (w^T K w) / (mu^2 x^T K x) of the first column at the latest test
   int* active;      // [n]
   int* iters;       // [n]
   int* count;       // [1] samples still active after the latest Rayleigh-Ritz
@@ -80,7 +81,8 @@ cudaError_t launch_gram(const PGrid& g, const Eig& E, const Vecs& v, cudaStream_
 // Rayleigh-Ritz per sample; convergence test on the preconditioned residual W of the
 // current iterate (its K norm against mu times X's); bumps count
 cudaError_t launch_rayleigh_ritz(const Eig& E, int n, double tol, int max_iter, bool first, cudaStream_t st);
-// X, P (and K X, K P, G X, G P) from the Ritz coefficients
+// X and P from the Ritz coefficients (their K and G images are recomputed by the caller:
+// carried along as combinations they drift in single precision)
 cudaError_t launch_update(const PGrid& g, const Eig& E, const Vecs& v, cudaStream_t st);
 // energies of column 0 in double with the double element matrices
 cudaError_t launch_energy(const PGrid& g, const double* ke64, const float4* x, const Eig& E, cudaStream_t st);

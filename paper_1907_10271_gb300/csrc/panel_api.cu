@@ -12,6 +12,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -197,6 +199,7 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
   E.coef = sc.take<double>((size_t)n * mlmcp::kSub * mlmcp::kCols);
   E.mu = sc.take<double>((size_t)n * mlmcp::kCols);
   E.energy = sc.take<double>((size_t)n * 2);
+  E.eta2 = sc.take<double>(n);
   E.active = sc.take<int>(n);
   E.iters = sc.take<int>(n);
   E.count = sc.take<int>(1);
@@ -212,7 +215,8 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
     CK(cudaStreamSynchronize(st), "copy");
   }
   const int* act = E.active;
-  float4 *X = V.v[0], *W = V.v[1], *KX = V.v[3], *KW = V.v[4], *GX = V.v[6], *GW = V.v[7];
+  float4 *X = V.v[0], *W = V.v[1], *P = V.v[2], *KX = V.v[3], *KW = V.v[4], *KP = V.v[5], *GX = V.v[6],
+         *GW = V.v[7], *GP = V.v[8];
 
   // one V(2,2) cycle: out = T b0 (level-0 batch entries)
   auto vcycle = [&](const float4* b0, float4* out) -> cudaError_t {
@@ -250,14 +254,33 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
 
   int it = 0;
   const int check_every = 4;
+  // diagnostic: MLMC_TRACE=<k> prints sample k's Ritz values and convergence measure
+  // after every iteration of this solve (synchronising each time)
+  const char* trace_env = std::getenv("MLMC_TRACE");
+  const int trace = trace_env ? std::atoi(trace_env) : -1;
   for (; it <= c.max_iter; ++it) {
     CK(cudaMemsetAsync(E.count, 0, sizeof(int), st), "memset");
+    // K and G images of the new X and P, recomputed (not updated by the Ritz
+    // coefficients, whose single-precision drift raises the residual floor)
+    CK(mlmcp::launch_apply(G[0], ke[0], X, nullptr, KX, GX, act, true, st), "apply");
+    CK(mlmcp::launch_apply(G[0], ke[0], P, nullptr, KP, GP, act, true, st), "apply");
     CK(mlmcp::launch_residual(G[0], E, KX, GX, R, st), "residual");
     CK(vcycle(R, W), "v-cycle");
     CK(mlmcp::launch_apply(G[0], ke[0], W, nullptr, KW, GW, act, true, st), "apply");
     CK(mlmcp::launch_gram(G[0], E, V, st), "gram");
     CK(mlmcp::launch_rayleigh_ritz(E, n, c.tol, c.max_iter, false, st), "rayleigh-ritz");
     CK(mlmcp::launch_update(G[0], E, V, st), "update");
+    if (trace >= 0 && trace < n) {
+      double h_mu[2], h_eta2;
+      int h_act, h_it;
+      CK(cudaMemcpyAsync(h_mu, E.mu + 2 * trace, sizeof(double) * 2, cudaMemcpyDeviceToHost, st), "trace");
+      CK(cudaMemcpyAsync(&h_eta2, E.eta2 + trace, sizeof(double), cudaMemcpyDeviceToHost, st), "trace");
+      CK(cudaMemcpyAsync(&h_act, E.active + trace, sizeof(int), cudaMemcpyDeviceToHost, st), "trace");
+      CK(cudaMemcpyAsync(&h_it, E.iters + trace, sizeof(int), cudaMemcpyDeviceToHost, st), "trace");
+      CK(cudaStreamSynchronize(st), "trace");
+      std::fprintf(stderr, "panel trace mesh %d sample %d it %d active %d mu %.12e %.12e eta2 %.3e\n", m, trace,
+                   h_it, h_act, h_mu[0], h_mu[1], h_eta2);
+    }
     if ((it + 1) % check_every == 0 || it == c.max_iter) {
       int h_count = 0;
       CK(cudaMemcpyAsync(&h_count, E.count, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
