@@ -330,10 +330,14 @@ __global__ void k_coarse_setup(PGrid g, const float* __restrict__ ke, const int*
     __syncthreads();
     for (int c = threadIdx.x; c < nf; c += blockDim.x) A[k * nf + c] = (c == k ? 1.f : A[k * nf + c]) * pinv;
     __syncthreads();
-    for (int rc = threadIdx.x; rc < nf * nf; rc += blockDim.x) {
-      const int r = rc / nf, c = rc - r * nf;
+    // a warp per row, lanes along the row (conflict-free, no index division)
+    const int nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const float* Ak = A + k * nf;
+    for (int r = threadIdx.x >> 5; r < nf; r += nw) {
       if (r == k) continue;
-      A[rc] = (c == k ? 0.f : A[rc]) - col[r] * A[k * nf + c];
+      const float f = col[r];
+      float* Ar = A + r * nf;
+      for (int c = lane; c < nf; c += 32) Ar[c] = (c == k ? 0.f : Ar[c]) - f * Ak[c];
     }
   }
   __syncthreads();
@@ -445,25 +449,27 @@ __global__ void __launch_bounds__(kThreads) k_gram(PGrid g, Eig E, const __grid_
 // One Jacobi rotation of the symmetric kSub x kSub matrix A (both triangles kept)
 // zeroing A[p][q], accumulated into V. p, q are compile-time after unrolling, so A and V
 // stay in registers.
-__device__ __forceinline__ void jacobi_rotate(double (&A)[kSub][kSub], double (&V)[kSub][kSub], int p, int q) {
-  const double apq = A[p][q];
-  if (apq == 0.0) return;
-  const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
-  const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-  const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+template <typename R>
+__device__ __forceinline__ void jacobi_rotate(R (&A)[kSub][kSub], R (&V)[kSub][kSub], int p, int q) {
+  const R apq = A[p][q];
+  if (apq == R(0)) return;
+  const R th = (A[q][q] - A[p][p]) / (R(2) * apq);
+  // |th| beyond 1e18: the rotation is the identity to working precision (avoids th^2 overflow)
+  const R t = fabs(th) > R(1e18) ? R(0) : (th >= R(0) ? R(1) : R(-1)) / (fabs(th) + sqrt(th * th + R(1)));
+  const R c = R(1) / sqrt(t * t + R(1)), sn = t * c;
 #pragma unroll
   for (int k = 0; k < kSub; ++k) {
     if (k == p || k == q) continue;
-    const double akp = A[k][p], akq = A[k][q];
+    const R akp = A[k][p], akq = A[k][q];
     A[k][p] = A[p][k] = c * akp - sn * akq;
     A[k][q] = A[q][k] = sn * akp + c * akq;
   }
   A[p][p] -= t * apq;
   A[q][q] += t * apq;
-  A[p][q] = A[q][p] = 0.0;
+  A[p][q] = A[q][p] = R(0);
 #pragma unroll
   for (int k = 0; k < kSub; ++k) {
-    const double vkp = V[k][p], vkq = V[k][q];
+    const R vkp = V[k][p], vkq = V[k][q];
     V[k][p] = c * vkp - sn * vkq;
     V[k][q] = sn * vkp + c * vkq;
   }
@@ -567,8 +573,8 @@ __global__ void __launch_bounds__(32) k_rayleigh_ritz(Eig E, int n, double tol2,
       for (int q = 0; q < r; ++q) v -= L[r][q] * A[q][c];
       A[r][c] = v / L[r][r];
     }
-  // T = L^-1 A^T = L^-1 G L^-T, symmetrised; dropped directions get eigenvalue -1
-  double T[kSub][kSub], V[kSub][kSub];
+  // T = L^-1 A^T = L^-1 G L^-T, symmetrised
+  double T[kSub][kSub];
 #pragma unroll
   for (int c = 0; c < kSub; ++c)
 #pragma unroll
@@ -578,43 +584,58 @@ __global__ void __launch_bounds__(32) k_rayleigh_ritz(Eig E, int n, double tol2,
       for (int q = 0; q < r; ++q) v -= L[r][q] * T[q][c];
       T[r][c] = v / L[r][r];
     }
+  // Jacobi in single precision on T scaled to a unit largest kept diagonal (dropped
+  // directions get eigenvalue -1); the double-precision work stays in the Gram scaling,
+  // the Cholesky factor and the back substitution. Eigenvalues come out within about
+  // 1e-6 of the largest, far inside the stopping tolerance.
+  double sc = 0.0;
 #pragma unroll
-  for (int r = 0; r < kSub; ++r) {
+  for (int r = 0; r < kSub; ++r)
+    if (keep[r]) sc = fmax(sc, fabs(T[r][r]));
+  if (!(sc > 0.0)) sc = 1.0;
+  const double isc = 1.0 / sc;
+  float Tf[kSub][kSub], Vf[kSub][kSub];
 #pragma unroll
-    for (int c = r + 1; c < kSub; ++c) T[r][c] = T[c][r] = 0.5 * (T[r][c] + T[c][r]);
-    if (!keep[r]) T[r][r] = -1.0;
+  for (int r = 0; r < kSub; ++r)
 #pragma unroll
-    for (int c = 0; c < kSub; ++c) V[r][c] = r == c ? 1.0 : 0.0;
-  }
-  for (int sweep = 0; sweep < 12; ++sweep) {
-    double off = 0.0, diag = 0.0;
+    for (int c = 0; c < kSub; ++c) {
+      Tf[r][c] = (keep[r] && keep[c]) ? (float)(0.5 * (T[r][c] + T[c][r]) * isc) : 0.f;
+      Vf[r][c] = r == c ? 1.f : 0.f;
+    }
+#pragma unroll
+  for (int r = 0; r < kSub; ++r)
+    if (!keep[r]) Tf[r][r] = -1.f;
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    float off = 0.f, diag = 0.f;
 #pragma unroll
     for (int p = 0; p < kSub; ++p) {
-      diag += T[p][p] * T[p][p];
+      diag += Tf[p][p] * Tf[p][p];
 #pragma unroll
-      for (int q = p + 1; q < kSub; ++q) off += T[p][q] * T[p][q];
+      for (int q = p + 1; q < kSub; ++q) off += Tf[p][q] * Tf[p][q];
     }
-    if (off <= 1e-30 * diag) break;
+    if (off <= 1e-13f * diag) break;
 #pragma unroll
     for (int p = 0; p < kSub; ++p)
 #pragma unroll
-      for (int q = p + 1; q < kSub; ++q) jacobi_rotate(T, V, p, q);
+      for (int q = p + 1; q < kSub; ++q) jacobi_rotate(Tf, Vf, p, q);
   }
   // the two largest eigenvalues (runtime indices only compared, never used to index)
   double best0 = -1e300, best1 = -1e300;
   int o0 = 0, o1 = 0;
 #pragma unroll
   for (int k = 0; k < kSub; ++k)
-    if (T[k][k] > best0) {
-      best0 = T[k][k];
+    if (Tf[k][k] > best0) {
+      best0 = Tf[k][k];
       o0 = k;
     }
 #pragma unroll
   for (int k = 0; k < kSub; ++k)
-    if (k != o0 && T[k][k] > best1) {
-      best1 = T[k][k];
+    if (k != o0 && Tf[k][k] > best1) {
+      best1 = Tf[k][k];
       o1 = k;
     }
+  best0 *= sc;
+  best1 *= sc;
   double* cf = E.coef + (size_t)s * kSub * kCols;
 #pragma unroll
   for (int c = 0; c < kCols; ++c) {
@@ -624,7 +645,7 @@ __global__ void __launch_bounds__(32) k_rayleigh_ritz(Eig E, int n, double tol2,
     for (int r = kSub - 1; r >= 0; --r) {   // back substitution L^T y = v
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < kSub; ++j) v = j == o ? V[r][j] : v;
+      for (int j = 0; j < kSub; ++j) v = j == o ? (double)Vf[r][j] : v;
 #pragma unroll
       for (int q = r + 1; q < kSub; ++q) v -= L[q][r] * y[q];
       y[r] = v / L[r][r];
