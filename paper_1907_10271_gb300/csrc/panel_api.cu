@@ -159,6 +159,24 @@ mlmc_status draw_xi(mlmcp_ctx& c, int level, uint64_t first_id, const int* level
 // (device)
 mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int* status) {
   if (n <= 0) return MLMC_OK;
+  {
+    // a solve holds about 15 vectors of 2 n (nodes) float4: chunk it so that one vector
+    // stays within 1 GB and the 2 n batch entries within a grid's y extent
+    const int64_t nodes = (int64_t)((c.cfg.nx0 << m) + 1) * ((c.cfg.ny0 << m) + 1);
+    const int per = (int)std::max<int64_t>(
+        1, std::min<int64_t>(16384, ((int64_t)1 << 30) / (2 * nodes * (int64_t)sizeof(float4))));
+    if (n > per) {
+      int its = 0;
+      for (int off = 0; off < n; off += per) {
+        const int k = std::min(per, n - off);
+        const mlmc_status s = solve_p(c, m, k, xi + (size_t)off * c.cfg.n_plies, q + 2 * (size_t)off, status + off);
+        if (s != MLMC_OK) return s;
+        its = std::max(its, c.last_iters);
+      }
+      c.last_iters = its;
+      return MLMC_OK;
+    }
+  }
   cudaStream_t st = c.st;
   const std::vector<Mesh>& H = c.hier[m];
   const int L = (int)H.size();

@@ -10,7 +10,8 @@
 - the pristine panel (no perturbation) reproduces the oracle and lies within 0.5 % of
   the load printed in Sec. 4.2; soft support matches the oracle as well;
 - the per-level moments equal numpy's on the returned quantities; solve_batch returns
-  the same quantities as sample_level; n = 0 is a no-op and bad levels are refused.
+  the same quantities as sample_level; n = 0 is a no-op and bad levels are refused;
+- a batch larger than one solve holds is split, and its samples equal their solves alone.
 """
 import numpy as np
 import pytest
@@ -153,3 +154,17 @@ def test_moments_and_batch_agree(B):
             B.mlmcp_sample_level(h, W["levels"], 0, 1, qf, qc, st)
     finally:
         B.mlmcp_destroy(h)
+
+
+def test_large_batch_is_chunked(B, ctx):
+    # 16385 level-0 samples exceed one solve's batch (16384): the last sample is solved
+    # in a chunk of its own and must equal its solve alone
+    n = 16385
+    qf = np.zeros(2 * n)
+    st = np.zeros(n, dtype=np.int32)
+    B.mlmcp_sample_level(ctx, 0, 500, n, qf, None, st)
+    assert np.all(st == 0)
+    q = np.zeros(2 * 2)
+    B.mlmcp_solve_batch(ctx, [(0, 0, 500), (0, 0, 500 + n - 1)], q)
+    assert abs(q[0] / qf[0] - 1.0) < RTOL and abs(q[2] / qf[2 * (n - 1)] - 1.0) < RTOL
+    assert 0.0 < qf[0::2].min() and qf[0::2].max() < 400.0
