@@ -15,7 +15,8 @@
   refinement (one-sided convergence, Sec. 4.2);
 - symmetries: mirroring every ply angle, or reversing the stacking order, leaves the
   critical load unchanged; the dense and sparse eigensolvers agree;
-- perturbations: the first n_plies normals of each sample's stream scaled by 3 degrees.
+- perturbations: the first n_plies normals of each sample's stream scaled by 3 degrees;
+- the soft support never gives a higher load than the hard one (a larger admissible space).
 """
 import os
 
@@ -164,3 +165,15 @@ def test_perturbations_and_level_pair():
         p = P.sample_perturbations(W, 1, [sid])[0]
         assert np.allclose(qf[k], P.solve_mesh(W, 1, p)) and np.allclose(qc[k], P.solve_mesh(W, 0, p))
     assert qf[:, 1].tolist() == [1.0 if v < W["p_star"] else 0.0 for v in qf[:, 0]]
+
+
+def test_soft_support_never_stiffer_than_hard():
+    # the soft support frees the tangential rotation, so its admissible space contains the
+    # hard one's and the smallest Rayleigh quotient can only fall
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        phi = np.radians(3.0) * rng.standard_normal(8)
+        for nx, ny in ((24, 8), (48, 16)):
+            soft = P.solve_sample(W, nx, ny, phi, bc="soft")
+            hard = P.solve_sample(W, nx, ny, phi, bc="hard")
+            assert soft < hard
