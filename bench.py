@@ -181,31 +181,35 @@ def _oracle_worker(args):
     return times, qf, qc
 
 
-ORACLE_FIRST_ID = 10_000_000
-
-
 def oracle_sample(cfg, fraction):
-    """Per level the number of samples the CPU oracle times (ids from ORACLE_FIRST_ID)."""
+    """Per level the number of samples the CPU oracle times (at least one)."""
     return [max(1, int(round(n * fraction))) for n in cfg["n_per_level"]]
 
 
-def oracle_throughput(cfg, fraction, cores):
+def spread_picks(n, s):
+    """s indices spread evenly over range(n), first and last included."""
+    return np.unique(np.round(np.linspace(0, n - 1, s)).astype(np.int64))
+
+
+def oracle_throughput(cfg, ids_per_level, cores, t_fixed=None):
     """Level-pairs/s of the CPU oracle on the workload mix, from a bounded sample:
-    per-sample times t_l measured on fraction * N_l samples of each level (at least
-    one), then sum_l N_l / (sum_l N_l t_l / cores). Also returns the oracle's
-    (Q_fine, Q_coarse) of every sampled id, in id order per level."""
+    per-sample times t_l measured on the given ids of each level (levels with no ids
+    take t_fixed[l], measured earlier), then sum_l N_l / (sum_l N_l t_l / cores).
+    Also returns the oracle's (Q_fine, Q_coarse) of every sampled id, in the given
+    order per level, and the wall time of the sample."""
     import multiprocessing as mp
     counts = cfg["n_per_level"]
-    sample = oracle_sample(cfg, fraction)
     jobs = []
-    for l, s in enumerate(sample):
-        ids = np.arange(ORACLE_FIRST_ID, ORACLE_FIRST_ID + s)
-        for chunk in np.array_split(ids, min(s, cores)):
+    for l, ids in enumerate(ids_per_level):
+        ids = np.asarray(ids, dtype=np.uint64)
+        for chunk in np.array_split(ids, min(len(ids), cores)) if len(ids) else []:
             if chunk.size:
                 jobs.append((cfg, l, chunk))
+    # largest meshes first, so that the longest solves start at once
+    jobs.sort(key=lambda j: -j[1])
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(min(cores, len(jobs))) as pool:
-        res = pool.map(_oracle_worker, jobs)
+        res = pool.map(_oracle_worker, jobs, chunksize=1)
     wall = time.perf_counter() - t0
     per_level = [[] for _ in counts]
     q = [([], []) for _ in counts]
@@ -213,10 +217,11 @@ def oracle_throughput(cfg, fraction, cores):
         per_level[l] += t
         q[l][0].extend(qf)
         q[l][1].extend(qc)
-    t_l = [float(np.mean(x)) for x in per_level]
+    t_l = [float(np.mean(x)) if x else t_fixed[l] for l, x in enumerate(per_level)]
     seconds = sum(n * t for n, t in zip(counts, t_l)) / cores
     q = [(np.array(f), np.array(c)) for f, c in q]
-    return sum(counts) / seconds, dict(sample=sample, t_l=t_l, wall=wall, cores=cores, q=q)
+    return sum(counts) / seconds, dict(t_l=t_l, wall=wall, cores=cores, q=q,
+                                       sample=[len(x) for x in ids_per_level])
 
 
 def qoi_parity(gpu_q, oracle_q):
@@ -233,8 +238,9 @@ def qoi_parity(gpu_q, oracle_q):
                 if nz.any():
                     worst[k] = max(worst[k], float((np.abs(g[nz, k] - o[nz, k]) / scale[nz]).max()))
     return {"pairs": pairs, "max_rel_err": {"reaction": worst[0], "stress": worst[1]},
-            "note": "GPU (batched mixed-precision GMG-PCG, rtol 1e-8) vs oracle (SuperLU, FP64) "
-                    "on the cpu_baseline sample's ids, both meshes of each pair"}
+            "note": "outputs of the last timed step's mlmc_sample_levels call (nested iteration, all five "
+                    "levels in one call) vs the oracle (SuperLU, FP64) on ids spread over each level of that "
+                    "step, both meshes of each pair"}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -334,6 +340,9 @@ def run_gpu(a):
         barrier()
     launches = B.mlmc_launch_count(ctx) - launches0
     t_step = sum(times) / len(times)
+    # outputs of the last timed step (copied after the timed region), for the parity check
+    last_step = a.warmup + a.steps - 1
+    timed_q = (qf.cpu().numpy().reshape(total, 2), qc.cpu().numpy().reshape(total, 2))
 
     # ---- the same steps again with the library's kernel timer on (CUDA events around
     # every launch on the library's stream): per-operation times, nodes and the roofline
@@ -427,15 +436,17 @@ def run_gpu(a):
                "note": "a sample's latency inside a step is the step's (all samples of the batch finish "
                        "together); single_pair = one level pair per mlmc_sample_level call"}
 
-    # ---- the GPU's QoIs on the ids the CPU oracle samples (compared in main)
+    # ---- the timed call's own QoIs on ids spread over every level of the last timed
+    # step (compared with the oracle in main)
     gpu_q = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        gpu_q = []
+        gpu_q = {"ids": [], "q": []}
+        offs = np.concatenate([[0], np.cumsum(counts)])
+        firsts = first_ids(last_step)
         for level, n in enumerate(oracle_sample(cfg, a.cpu_fraction)):
-            f = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
-            c = torch.zeros_like(f)
-            B.mlmc_sample_level(ctx, level, ORACLE_FIRST_ID, n, f, c)
-            gpu_q.append((f.cpu().numpy().reshape(n, 2), c.cpu().numpy().reshape(n, 2)))
+            picks = spread_picks(counts[level], n)
+            gpu_q["ids"].append(firsts[level] + picks)
+            gpu_q["q"].append((timed_q[0][offs[level] + picks], timed_q[1][offs[level] + picks]))
     B.mlmc_destroy(ctx)
 
     # ---- comparison point: the plain double-precision form, one sample per call
@@ -454,10 +465,14 @@ def run_gpu(a):
                           "tuning": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tuning.items()},
                           "tuning_source": "mlmc_autotune (untimed)" if a.autotune else "defaults"},
                "level_pairs_per_step": total, "samples_failed": bad,
-               "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+               "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
+                       "h2d_bytes_per_step": len(levels) * (4 + 8 + 8),
                        "d2h_bytes_per_step": total * (2 * 16 + 4),
-                       "note": "mlmc_sample_levels with pinned host outputs; per-sample inputs are "
-                               "(seed, level, id) counters, fields are synthesised on the device"},
+                       "note": "mlmc_sample_levels with pinned host outputs (Q_fine, Q_coarse, status per "
+                               "pair); the step's inputs are its request arrays (level int32, first id "
+                               "uint64, count int64 per level), which reach the device as kernel "
+                               "arguments: per-sample inputs are (seed, level, id) counters and the "
+                               "fields are synthesised on the device"},
                "roofline": roofline, "kernels": kernels,
                "kernel_ms_per_step": round(kernel_ms, 3),
                "gpu_busy_fraction": round(kernel_ms / (sum(prof_times) / len(prof_times)), 3),
@@ -599,9 +614,25 @@ def run_small_case():
     print(json.dumps({"case": "small", "level_pairs": total, "failed": int((st != 0).sum())}))
 
 
-# FP32 CUDA-core peak of one GB300 from its unit counts and clock: 152 SMs x 128 FP32
-# lanes x 2 flops per FMA x 2.07 GHz (the 3D element operator is plain FP32 arithmetic).
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+def fp32_peak_tflops():
+    """FP32 CUDA-core peak from the device's SM count (read at run time), 128 FP32 lanes
+    per SM, 2 flops per FMA and the maximum SM clock (MEASURED_PEAKS.json, else
+    nvidia-smi, else 2.07 GHz): the 3D element operator is plain FP32 arithmetic."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = json.load(f).get("sm_max_mhz")
+    if not mhz:
+        try:
+            mhz = float(subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                                        "-i", str(torch.cuda.current_device())], capture_output=True, text=True,
+                                       timeout=10).stdout.split()[0])
+        except Exception:
+            mhz = 2070.0
+    return sms * 128 * 2 * float(mhz) * 1e6 / 1e12, sms, float(mhz)
 
 
 def run_hex3d(B, steps=2, warmup=1, parity=True):
@@ -641,6 +672,7 @@ def run_hex3d(B, steps=2, warmup=1, parity=True):
             failed = sum(int((b[2] != 0).sum()) for b in bufs)
             op_ms, op_bytes, op_flops = B.mlmc3d_apply_bench(ctx, 3, counts[3], 5)
             hbm, kind = peaks()
+            fp32_peak, sms, mhz = fp32_peak_tflops()
             tflops = op_flops / op_ms / 1e9
             out = {
                 "workload": W["name"], "meshes": "32x8x4..256x64x32 Hex8, 3 DOF/node",
@@ -650,9 +682,9 @@ def run_hex3d(B, steps=2, warmup=1, parity=True):
                 "note": "host outputs (mlmc3d_sample_level), one call per level; FP32 PCG with a double-precision "
                         "refinement residual",
                 "roofline": {"kernel": "hex8_apply (FP32, 256x64x32, 32 samples)", "bound": "alu",
-                             "achieved": round(tflops, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                             "frac": round(tflops / FP32_PEAK_TFLOPS, 4),
-                             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                             "achieved": round(tflops, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                             "frac": round(tflops / fp32_peak, 4),
+                             "peak_kind": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sms, mhz),
                              "flops_per_element": 976, "launch_ms": round(op_ms, 4),
                              "hbm": {"achieved_gbs": round(op_bytes / op_ms / 1e6, 1), "peak_gbs": hbm,
                                      "frac": round(op_bytes / op_ms / 1e6 / hbm, 4), "peak_kind": kind}},
@@ -790,6 +822,49 @@ def run_hex3d_case():
     print(json.dumps({"case": "hex3d", "level_pairs": sum(W["n_per_level"]), "failed": failed}))
 
 
+# per-step sample of the reference arm: levels 0-3 (a few seconds of wall time on the
+# host's cores); level 4 (one sample, tens of seconds) is timed once before the steps
+REF_STEP_SAMPLE = [16, 4, 1, 1, 0]
+
+
+def run_reference(a, world):
+    """The CPU oracle as it stands, timed on the host's cores: one untimed calibration
+    of every level (one level-4 sample among them), W warm-up and K timed steps, each
+    a bounded sample of levels 0-3 whose per-sample times, with the calibration's
+    level-4 time, are extrapolated to the workload mix. ms_per_step is the wall time
+    of one timed sample step; the mix it stands for is in `extrapolated`."""
+    cfg = STRIP_MIXED_5LEVEL
+    counts = list(cfg["n_per_level"])
+    cores = os.cpu_count() or 1
+    base = 10_000_000
+    calib = [np.arange(base, base + n) for n in [16, 4, 1, 1, 1]]
+    _, info0 = oracle_throughput(cfg, calib, cores)
+    vals, walls, t_ls = [], [], []
+    for k in range(a.warmup + a.steps):
+        ids = [base + (1 + k) * 1000 + np.arange(n) for n in REF_STEP_SAMPLE]
+        v, info = oracle_throughput(cfg, ids, cores, t_fixed=info0["t_l"])
+        if k >= a.warmup:
+            vals.append(v)
+            walls.append(info["wall"])
+            t_ls.append(info["t_l"])
+    value = sum(vals) / len(vals)
+    t_l = [float(np.mean([t[l] for t in t_ls])) for l in range(len(counts))]
+    sample = ("each step: %s samples of levels 0-4 (of %s), per-sample times %s s; level 4 from one untimed "
+              "calibration sample (%.1f s); extrapolated to the workload mix over %d cores" %
+              (REF_STEP_SAMPLE, counts, [round(t, 4) for t in t_l], info0["t_l"][4], cores))
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+                      "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
+                      "ms_per_step": round(1e3 * sum(walls) / len(walls), 1),
+                      "extrapolated": {"ms_per_full_step": round(sum(counts) / value * 1e3, 1),
+                                       "note": "time the oracle would take for one whole step of the workload "
+                                               "at the measured per-sample rates"},
+                      "config": {"workload": cfg["name"]}, "dtype": "f64",
+                      "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": round(value, 3),
+                                       "unit": UNIT},
+                      "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}))
+
+
 def main():
     a = parse()
     rank, _, world = dist_env()
@@ -805,25 +880,7 @@ def main():
     if a.impl == "reference":
         if rank != 0:
             return
-        cores = os.cpu_count() or 1
-        vals = []
-        info = None
-        for k in range(a.warmup + a.steps):
-            v, info = oracle_throughput(STRIP_MIXED_5LEVEL, a.cpu_fraction, cores)
-            if k >= a.warmup:
-                vals.append(v)
-        value = sum(vals) / len(vals)
-        sample = ("per level %s samples of %s (ids from 1e7), per-sample times %s s extrapolated to the "
-                  "workload mix over %d cores" % (info["sample"], list(STRIP_MIXED_5LEVEL["n_per_level"]),
-                                                 [round(t, 4) for t in info["t_l"]], cores))
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
-                          "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
-                          "ms_per_step": round(sum(STRIP_MIXED_5LEVEL["n_per_level"]) / value * 1e3, 1),
-                          "config": {"workload": STRIP_MIXED_5LEVEL["name"]}, "dtype": "f64",
-                          "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": round(value, 3),
-                                           "unit": UNIT},
-                          "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
-                                  "d2h_bytes_per_step": 0}}))
+        run_reference(a, world)
         return
     out = run_gpu(a)
     if rank == 0 and out is not None and world == 1 and a.serving:
@@ -836,16 +893,16 @@ def main():
         from paper_1907_10271_gb300 import binding as B
         out["panel"] = run_panel(B, parity=not a.no_cpu_baseline)
     if rank == 0 and out is not None:
-        if world == 1 and not a.no_cpu_baseline:
+        if world == 1 and not a.no_cpu_baseline and out.get("_gpu_q") is not None:
             cores = os.cpu_count() or 1
-            v, info = oracle_throughput(STRIP_MIXED_5LEVEL, a.cpu_fraction, cores)
+            gq = out["_gpu_q"]
+            v, info = oracle_throughput(STRIP_MIXED_5LEVEL, gq["ids"], cores)
             out["cpu_baseline"] = {"value": round(v, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
-                                   "sample": "per level %s samples (1/32 of each level), per-sample times %s s, "
-                                             "extrapolated to the workload mix" %
-                                             (info["sample"], [round(t, 4) for t in info["t_l"]]),
+                                   "sample": "per level %s samples (1/32 of each level, ids spread over the last "
+                                             "timed step's), per-sample times %s s, extrapolated to the "
+                                             "workload mix" % (info["sample"], [round(t, 4) for t in info["t_l"]]),
                                    "wall_s": round(info["wall"], 1)}
-            if out.get("_gpu_q") is not None:
-                out["qoi_parity"] = qoi_parity(out["_gpu_q"], info["q"])
+            out["qoi_parity"] = qoi_parity(gq["q"], info["q"])
         out.pop("_gpu_q", None)
         print(json.dumps(out))
 

@@ -200,6 +200,40 @@ def solve(K, ddofs, dvals):
     return d
 
 
+def apply(nx, ny, nz, h, C_col, x):
+    """K x without assembling K: the sum over elements of the element matrix applied
+    to the element's DOFs, scattered back (the definition of assembly, element by
+    element column; column (i, k) -> k nx + i, all elements of a column alike)."""
+    dofs = element_dofs(nx, ny, nz).reshape(nz, ny, nx, 24)
+    contrib = np.empty((nz, ny, nx, 24))
+    for k in range(nz):
+        for i in range(nx):
+            Ke = element_matrix(C_col[k * nx + i], h)
+            contrib[k, :, i, :] = x[dofs[k, :, i, :]] @ Ke.T   # the column's ny elements
+    return np.bincount(dofs.ravel(), weights=contrib.ravel(), minlength=3 * (nx + 1) * (ny + 1) * (nz + 1))
+
+
+def solve_cg(K, ddofs, dvals, rtol=1e-12, maxiter=50000):
+    """The same discrete solution as solve(), by conjugate gradients with the diagonal
+    as preconditioner, to a relative residual of rtol on the free DOFs (for meshes on
+    which the direct factorisation's fill-in is too large). Raises if CG stops short."""
+    n = K.shape[0]
+    free = np.setdiff1d(np.arange(n), ddofs)
+    d = np.zeros(n)
+    d[ddofs] = dvals
+    Kff = K[free][:, free].tocsr()
+    rhs = -(K[free][:, ddofs] @ dvals)
+    dg = Kff.diagonal()
+    M = spla.LinearOperator(Kff.shape, matvec=lambda v: v / dg)
+    x, info = spla.cg(Kff, rhs, rtol=rtol, atol=0.0, maxiter=maxiter, M=M)
+    if info != 0:
+        raise RuntimeError(f"CG did not reach rtol {rtol} (info {info})")
+    if np.linalg.norm(rhs - Kff @ x) > 10 * rtol * np.linalg.norm(rhs):
+        raise RuntimeError("CG residual above its tolerance")
+    d[free] = x
+    return d
+
+
 def reaction(K, d, nx, ny, nz):
     Kd = K @ d
     idx = [3 * node_index(nx, j, k, nx, ny) for k in range(nz + 1) for j in range(ny + 1)]
@@ -226,14 +260,15 @@ def max_fibre_compression(cfg, d, C_col, theta_col, nx, ny, nz, h):
     return best
 
 
-def solve_sample(cfg, nx, ny, nz, theta_col, bc="clamped"):
-    """(reaction, stress, d) of one sample on the nx x ny x nz mesh."""
+def solve_sample(cfg, nx, ny, nz, theta_col, bc="clamped", solver="direct"):
+    """(reaction, stress, d) of one sample on the nx x ny x nz mesh; solver "direct"
+    (sparse LU) or "cg" (solve_cg to a relative residual of 1e-12)."""
     h = cfg["lx"] / nx
     C = material_stiffness(cfg)
     C_col = np.array([rotate(C, t) for t in theta_col])
     K = assemble(nx, ny, nz, h, C_col)
     dd, dv = dirichlet(nx, ny, nz, cfg["shortening"], bc)
-    d = solve(K, dd, dv)
+    d = solve(K, dd, dv) if solver == "direct" else solve_cg(K, dd, dv)
     return reaction(K, d, nx, ny, nz), max_fibre_compression(cfg, d, C_col, theta_col, nx, ny, nz, h), d
 
 

@@ -72,53 +72,6 @@ __global__ void k_combine_status(const int* a, const int* b, int* out, int64_t n
   if (i < n) out[i] = a[i] != 0 ? a[i] : (b ? b[i] : 0);
 }
 
-mlmc::Invariants invariants(const mlmc_config& c, bool& ok) {
-  // plane-strain fibre-frame stiffness: (1,2) block of the inverse 3D normal compliance
-  double S[3][3] = {{1.0 / c.E11, -c.nu12 / c.E11, -c.nu13 / c.E11},
-                    {-c.nu12 / c.E11, 1.0 / c.E22, -c.nu23 / c.E22},
-                    {-c.nu13 / c.E11, -c.nu23 / c.E22, 1.0 / c.E33}};
-  // inverse by cofactors
-  const double det = S[0][0] * (S[1][1] * S[2][2] - S[1][2] * S[2][1]) -
-                     S[0][1] * (S[1][0] * S[2][2] - S[1][2] * S[2][0]) +
-                     S[0][2] * (S[1][0] * S[2][1] - S[1][1] * S[2][0]);
-  ok = std::isfinite(det) && det > 0.0;
-  const double Q11 = (S[1][1] * S[2][2] - S[1][2] * S[2][1]) / det;
-  const double Q12 = -(S[0][1] * S[2][2] - S[0][2] * S[2][1]) / det;
-  const double Q22 = (S[0][0] * S[2][2] - S[0][2] * S[2][0]) / det;
-  const double Q66 = c.G12;
-  ok = ok && Q11 > 0 && Q22 > 0 && Q66 > 0 && Q11 * Q22 > Q12 * Q12;
-  mlmc::Invariants U;
-  U.U1 = (3.0 * Q11 + 3.0 * Q22 + 2.0 * Q12 + 4.0 * Q66) / 8.0;
-  U.U2 = (Q11 - Q22) / 2.0;
-  U.U3 = (Q11 + Q22 - 2.0 * Q12 - 4.0 * Q66) / 8.0;
-  U.U4 = (Q11 + Q22 + 6.0 * Q12 - 4.0 * Q66) / 8.0;
-  U.U5 = (Q11 + Q22 - 2.0 * Q12 + 4.0 * Q66) / 8.0;
-  U.round_single();
-  return U;
-}
-
-std::string validate(const mlmc_config& c) {
-  if (!(c.lx > 0 && c.ly > 0)) return "lx, ly must be positive";
-  if (c.nx0 < 2 || c.ny0 < 2) return "nx0, ny0 must be >= 2";
-  if (c.levels < 1 || c.levels > 12) return "levels must be in [1, 12]";
-  if ((int64_t)(c.nx0 << (c.levels - 1)) > (1 << 16) || (int64_t)(c.ny0 << (c.levels - 1)) > (1 << 16))
-    return "finest mesh too large";
-  if (c.kl_terms < 1 || c.kl_terms > 512) return "kl_terms must be in [1, 512]";
-  if (!(c.kl_std >= 0) || !(c.kl_corr > 0)) return "kl_std >= 0 and kl_corr > 0 required";
-  if (!(c.rtol > 0 && c.rtol < 1)) return "rtol must be in (0, 1)";
-  if (c.precision != MLMC_PREC_FP64 && c.precision != MLMC_PREC_MIXED) return "unknown precision";
-  if (!(c.E11 > 0 && c.E22 > 0 && c.E33 > 0 && c.G12 > 0)) return "moduli must be positive";
-  // the multigrid hierarchy halves the level-0 mesh down to <= 64 DOFs
-  int nx = c.nx0, ny = c.ny0;
-  while (nx % 2 == 0 && ny % 2 == 0 && ny >= 2) {
-    nx /= 2;
-    ny /= 2;
-  }
-  if (nx == c.nx0) return "level-0 mesh must halve at least once (nx0, ny0 even)";
-  if (2 * (nx + 1) * (ny + 1) > mlmc::kMaxCoarsestDofs) return "level-0 mesh does not halve down to <= 64 DOFs";
-  return "";
-}
-
 struct LevelReq {
   int level;
   uint64_t first_id;
@@ -403,6 +356,53 @@ void fill_stats(const mlmc_ctx* h, int l, mlmc_level_stats* out) {
 
 namespace mlmc {
 
+Invariants invariants(const mlmc_config& c, bool& ok) {
+  // plane-strain fibre-frame stiffness: (1,2) block of the inverse 3D normal compliance
+  double S[3][3] = {{1.0 / c.E11, -c.nu12 / c.E11, -c.nu13 / c.E11},
+                    {-c.nu12 / c.E11, 1.0 / c.E22, -c.nu23 / c.E22},
+                    {-c.nu13 / c.E11, -c.nu23 / c.E22, 1.0 / c.E33}};
+  // inverse by cofactors
+  const double det = S[0][0] * (S[1][1] * S[2][2] - S[1][2] * S[2][1]) -
+                     S[0][1] * (S[1][0] * S[2][2] - S[1][2] * S[2][0]) +
+                     S[0][2] * (S[1][0] * S[2][1] - S[1][1] * S[2][0]);
+  ok = std::isfinite(det) && det > 0.0;
+  const double Q11 = (S[1][1] * S[2][2] - S[1][2] * S[2][1]) / det;
+  const double Q12 = -(S[0][1] * S[2][2] - S[0][2] * S[2][1]) / det;
+  const double Q22 = (S[0][0] * S[2][2] - S[0][2] * S[2][0]) / det;
+  const double Q66 = c.G12;
+  ok = ok && Q11 > 0 && Q22 > 0 && Q66 > 0 && Q11 * Q22 > Q12 * Q12;
+  Invariants U;
+  U.U1 = (3.0 * Q11 + 3.0 * Q22 + 2.0 * Q12 + 4.0 * Q66) / 8.0;
+  U.U2 = (Q11 - Q22) / 2.0;
+  U.U3 = (Q11 + Q22 - 2.0 * Q12 - 4.0 * Q66) / 8.0;
+  U.U4 = (Q11 + Q22 + 6.0 * Q12 - 4.0 * Q66) / 8.0;
+  U.U5 = (Q11 + Q22 - 2.0 * Q12 + 4.0 * Q66) / 8.0;
+  U.round_single();
+  return U;
+}
+
+std::string validate(const mlmc_config& c) {
+  if (!(c.lx > 0 && c.ly > 0)) return "lx, ly must be positive";
+  if (c.nx0 < 2 || c.ny0 < 2) return "nx0, ny0 must be >= 2";
+  if (c.levels < 1 || c.levels > 12) return "levels must be in [1, 12]";
+  if ((int64_t)(c.nx0 << (c.levels - 1)) > (1 << 16) || (int64_t)(c.ny0 << (c.levels - 1)) > (1 << 16))
+    return "finest mesh too large";
+  if (c.kl_terms < 1 || c.kl_terms > 512) return "kl_terms must be in [1, 512]";
+  if (!(c.kl_std >= 0) || !(c.kl_corr > 0)) return "kl_std >= 0 and kl_corr > 0 required";
+  if (!(c.rtol > 0 && c.rtol < 1)) return "rtol must be in (0, 1)";
+  if (c.precision != MLMC_PREC_FP64 && c.precision != MLMC_PREC_MIXED) return "unknown precision";
+  if (!(c.E11 > 0 && c.E22 > 0 && c.E33 > 0 && c.G12 > 0)) return "moduli must be positive";
+  // the multigrid hierarchy halves the level-0 mesh down to <= 64 DOFs
+  int nx = c.nx0, ny = c.ny0;
+  while (nx % 2 == 0 && ny % 2 == 0 && ny >= 2) {
+    nx /= 2;
+    ny /= 2;
+  }
+  if (nx == c.nx0) return "level-0 mesh must halve at least once (nx0, ny0 even)";
+  if (2 * (nx + 1) * (ny + 1) > kMaxCoarsestDofs) return "level-0 mesh does not halve down to <= 64 DOFs";
+  return "";
+}
+
 mlmc_status reserve_workspace(mlmc_ctx* h, size_t solve_bytes, size_t batch_bytes) {
   Context& c = h->c;
   cudaError_t e = c.solve_arena.reserve(solve_bytes);
@@ -433,13 +433,13 @@ mlmc_status mlmc_create(const mlmc_config* cfg, void* cuda_stream, mlmc_ctx** ou
     return MLMC_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  std::string v = validate(*cfg);
+  std::string v = mlmc::validate(*cfg);
   if (!v.empty()) {
     g_create_error = v;
     return MLMC_ERR_INVALID_ARG;
   }
   bool ok = true;
-  mlmc::Invariants U = invariants(*cfg, ok);
+  mlmc::Invariants U = mlmc::invariants(*cfg, ok);
   if (!ok) {
     g_create_error = "material constants do not give a positive definite plane-strain stiffness";
     return MLMC_ERR_INVALID_ARG;

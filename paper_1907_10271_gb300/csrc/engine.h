@@ -71,6 +71,13 @@ mlmc_status reserve_workspace(mlmc_ctx* h, size_t solve_bytes, size_t batch_byte
 // of a fixed batch; a request loop whose every batch differs turns it off.
 void set_graph_replay(mlmc_ctx* h, bool on);
 
+// Checks a strip configuration: the reason it is rejected, or "" when it is valid.
+std::string validate(const mlmc_config& cfg);
+
+// Tsai-Pagano invariants of the plane-strain fibre-frame stiffness of cfg's ply; ok is
+// false when the constants do not give a positive definite stiffness.
+Invariants invariants(const mlmc_config& cfg, bool& ok);
+
 // Device bytes one solve on `mesh` needs in a batch (solver workspace, field and
 // outputs), with margin.
 double solve_bytes_per_sample(const mlmc_config& cfg, int mesh);

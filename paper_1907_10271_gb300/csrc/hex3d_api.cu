@@ -183,7 +183,7 @@ struct mlmc3d_ctx {
   std::vector<float*> basis32;   // per mesh [cols][n_kl]
   mlmc::LevelAcc* acc_dev = nullptr;
   std::vector<mlmc::LevelAcc> acc_host;
-  Arena ws, io;
+  Arena ws, io, kl;   // solver workspace, per-call buffers, KL coefficients (all grow-only)
   int last_iters = 0;
   int max_iter = 200, max_outer = 8;
 
@@ -384,21 +384,25 @@ mlmc_status synthesize(mlmc3d_ctx& c, int m, int level, uint64_t first_id, const
                        const uint64_t* ids_dev, int n, float* out, bool trig2) {
   const int nkl = c.cfg.kl_terms;
   const Grid3 g = c.mesh(m, n);
-  double* xi;
-  float* xi32;
-  int* fail;
-  CK(cudaMallocAsync(&xi, sizeof(double) * n * nkl, c.st), "alloc");
-  CK(cudaMallocAsync(&xi32, sizeof(float) * n * nkl, c.st), "alloc");
-  CK(cudaMallocAsync(&fail, sizeof(int) * 2, c.st), "alloc");
+  double* xi = nullptr;
+  float* xi32 = nullptr;
+  int* fail = nullptr;
+  auto carve = [&](auto& a) {
+    xi = a.template take<double>((size_t)n * nkl);
+    xi32 = a.template take<float>((size_t)n * nkl);
+    fail = a.template take<int>(2);
+  };
+  Sizer3 sz;
+  carve(sz);
+  CK(c.kl.reserve(sz.used + 256), "KL buffers");
+  c.kl.used = 0;
+  carve(c.kl);
   CK(cudaMemsetAsync(fail, 0, sizeof(int) * 2, c.st), "memset");
   CK(mlmc::launch_kl_coefficients(c.cfg.seed, level, first_id, levels_dev, ids_dev, n, nkl, xi, xi32, fail, c.st),
      "kl_coefficients");
   CK(mlmc::launch_kl_synthesis<float>(xi32, c.basis32[m], n, (int)g.cols(), nkl, out, trig2, c.st), "kl_synthesis");
   int h_fail = 0;
   CK(cudaMemcpyAsync(&h_fail, fail, sizeof(int), cudaMemcpyDeviceToHost, c.st), "kl");
-  CK(cudaFreeAsync(xi, c.st), "free");
-  CK(cudaFreeAsync(xi32, c.st), "free");
-  CK(cudaFreeAsync(fail, c.st), "free");
   CK(cudaStreamSynchronize(c.st), "kl");
   if (h_fail) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
   return MLMC_OK;
@@ -512,24 +516,30 @@ mlmc_status mlmc3d_sample_level(mlmc3d_ctx* h, int32_t level, uint64_t first_id,
   if (n < 0 || n > (1 << 24)) return c.fail(MLMC_ERR_INVALID_ARG, "bad sample count");
   if (n == 0) return MLMC_OK;
   const int ni = (int)n;
-  float* t2f;
+  float* t2f = nullptr;
   float* t2c = nullptr;
-  double *qf, *qc;
-  int *sf, *sc;
+  double *qf = nullptr, *qc = nullptr;
+  int *sf = nullptr, *sc = nullptr;
   const Grid3 gf = c.mesh(level, ni);
-  CK(cudaMallocAsync(&t2f, sizeof(float) * 2 * gf.cols() * n, c.st), "alloc");
-  CK(cudaMallocAsync(&qf, sizeof(double) * 2 * n, c.st), "alloc");
-  CK(cudaMallocAsync(&qc, sizeof(double) * 2 * n, c.st), "alloc");
-  CK(cudaMallocAsync(&sf, sizeof(int) * n, c.st), "alloc");
-  CK(cudaMallocAsync(&sc, sizeof(int) * n, c.st), "alloc");
+  auto carve = [&](auto& a) {
+    t2f = a.template take<float>(2 * gf.cols() * n);
+    if (level > 0) t2c = a.template take<float>(2 * c.mesh(level - 1, ni).cols() * n);
+    qf = a.template take<double>(2 * n);
+    qc = a.template take<double>(2 * n);
+    sf = a.template take<int>(n);
+    sc = a.template take<int>(n);
+  };
+  Sizer3 sz;
+  carve(sz);
+  CK(c.io.reserve(sz.used + 256), "call buffers");
+  c.io.used = 0;
+  carve(c.io);
   CK(cudaMemsetAsync(qc, 0, sizeof(double) * 2 * n, c.st), "memset");
   CK(cudaMemsetAsync(sc, 0, sizeof(int) * n, c.st), "memset");
   mlmc_status s = synthesize(c, level, level, first_id, nullptr, nullptr, ni, t2f, true);
   if (s == MLMC_OK) s = solve3(c, level, ni, t2f, qf, sf);
   int it_f = c.last_iters;
   if (s == MLMC_OK && level > 0) {
-    const Grid3 gc = c.mesh(level - 1, ni);
-    CK(cudaMallocAsync(&t2c, sizeof(float) * 2 * gc.cols() * n, c.st), "alloc");
     s = synthesize(c, level - 1, level, first_id, nullptr, nullptr, ni, t2c, true);
     if (s == MLMC_OK) s = solve3(c, level - 1, ni, t2c, qc, sc);
     c.last_iters = std::max(it_f, c.last_iters);
@@ -541,12 +551,6 @@ mlmc_status mlmc3d_sample_level(mlmc3d_ctx* h, int32_t level, uint64_t first_id,
     if (s == MLMC_OK) s = copy_out(c, q_coarse, qc, 2 * (size_t)n);
     if (s == MLMC_OK) s = copy_out(c, status, sf, (size_t)n);
   }
-  cudaFreeAsync(t2f, c.st);
-  if (t2c) cudaFreeAsync(t2c, c.st);
-  cudaFreeAsync(qf, c.st);
-  cudaFreeAsync(qc, c.st);
-  cudaFreeAsync(sf, c.st);
-  cudaFreeAsync(sc, c.st);
   cudaStreamSynchronize(c.st);
   return s;
 }
@@ -579,16 +583,23 @@ mlmc_status mlmc3d_solve_batch(mlmc3d_ctx* h, const mlmc_item* items, int64_t n,
     if (idx.empty()) continue;
     const int ng = (int)idx.size();
     const Grid3 g = c.mesh(m, ng);
-    int* lv_d;
-    uint64_t* ids_d;
-    float* t2;
-    double* qd;
-    int* sd;
-    CK(cudaMallocAsync(&lv_d, sizeof(int) * ng, c.st), "alloc");
-    CK(cudaMallocAsync(&ids_d, sizeof(uint64_t) * ng, c.st), "alloc");
-    CK(cudaMallocAsync(&t2, sizeof(float) * 2 * g.cols() * ng, c.st), "alloc");
-    CK(cudaMallocAsync(&qd, sizeof(double) * 2 * ng, c.st), "alloc");
-    CK(cudaMallocAsync(&sd, sizeof(int) * ng, c.st), "alloc");
+    int* lv_d = nullptr;
+    uint64_t* ids_d = nullptr;
+    float* t2 = nullptr;
+    double* qd = nullptr;
+    int* sd = nullptr;
+    auto carve = [&](auto& a) {
+      lv_d = a.template take<int>(ng);
+      ids_d = a.template take<uint64_t>(ng);
+      t2 = a.template take<float>(2 * g.cols() * ng);
+      qd = a.template take<double>(2 * ng);
+      sd = a.template take<int>(ng);
+    };
+    Sizer3 sz;
+    carve(sz);
+    CK(c.io.reserve(sz.used + 256), "call buffers");
+    c.io.used = 0;
+    carve(c.io);
     CK(cudaMemcpyAsync(lv_d, lv.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, c.st), "copy");
     CK(cudaMemcpyAsync(ids_d, ids.data(), sizeof(uint64_t) * ng, cudaMemcpyHostToDevice, c.st), "copy");
     mlmc_status s = synthesize(c, m, 0, 0, lv_d, ids_d, ng, t2, true);
@@ -599,11 +610,6 @@ mlmc_status mlmc3d_solve_batch(mlmc3d_ctx* h, const mlmc_item* items, int64_t n,
       CK(cudaMemcpyAsync(qh.data(), qd, sizeof(double) * 2 * ng, cudaMemcpyDeviceToHost, c.st), "copy");
       CK(cudaMemcpyAsync(sh.data(), sd, sizeof(int) * ng, cudaMemcpyDeviceToHost, c.st), "copy");
     }
-    cudaFreeAsync(lv_d, c.st);
-    cudaFreeAsync(ids_d, c.st);
-    cudaFreeAsync(t2, c.st);
-    cudaFreeAsync(qd, c.st);
-    cudaFreeAsync(sd, c.st);
     CK(cudaStreamSynchronize(c.st), "solve_batch");
     if (s != MLMC_OK) return s;
     for (int k = 0; k < ng; ++k) {
@@ -662,14 +668,14 @@ mlmc_status mlmc3d_theta(mlmc3d_ctx* h, int32_t mesh_level, int32_t level, uint6
     return c.fail(MLMC_ERR_INVALID_ARG, "level out of range");
   if (n <= 0) return MLMC_OK;
   const Grid3 g = c.mesh(mesh_level, (int)n);
-  float* t;
-  CK(cudaMallocAsync(&t, sizeof(float) * g.cols() * n, c.st), "alloc");
+  CK(c.io.reserve(sizeof(float) * g.cols() * n + 256), "call buffers");
+  c.io.used = 0;
+  float* t = c.io.take<float>(g.cols() * n);
   mlmc_status s = synthesize(c, mesh_level, level, first_id, nullptr, nullptr, (int)n, t, false);
   std::vector<float> th(g.cols() * n);
   if (s == MLMC_OK) {
     CK(cudaMemcpyAsync(th.data(), t, sizeof(float) * th.size(), cudaMemcpyDeviceToHost, c.st), "copy");
   }
-  cudaFreeAsync(t, c.st);
   CK(cudaStreamSynchronize(c.st), "theta");
   if (s != MLMC_OK) return s;
   std::vector<double> out(th.begin(), th.end());

@@ -22,9 +22,9 @@ constexpr size_t kStaticScratchBytes = size_t(32) << 20;   // 32 MiB
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_static_mu;
-std::map<int, char*> g_static_addr;   // device ordinal -> device address of g_static_scratch
-std::string g_static_error;
+std::mutex g_static_mu;                // guards g_static_addr
+std::map<int, char*> g_static_addr;    // device ordinal -> device address of g_static_scratch
+thread_local std::string g_static_error;   // last failure on the calling thread
 
 bool device_accessible(const void* p) {
   cudaPointerAttributes a;
@@ -36,7 +36,6 @@ bool device_accessible(const void* p) {
 }
 
 mlmc_status static_fail(mlmc_status s, const std::string& m) {
-  std::lock_guard<std::mutex> g(g_static_mu);
   g_static_error = m;
   return s;
 }
@@ -45,6 +44,7 @@ mlmc_status static_fail(mlmc_status s, const std::string& m) {
 
 extern "C" {
 
+// The message stays valid until the calling thread's next call of mlmc_solve_theta_static.
 const char* mlmc_static_last_error(void) { return g_static_error.c_str(); }
 
 mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, int32_t mesh_level, int64_t n,
@@ -52,9 +52,19 @@ mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, i
   if (!cfg) return static_fail(MLMC_ERR_INVALID_ARG, "null config");
   if (mesh_level < 0 || mesh_level >= cfg->levels || n < 0 || (n > 0 && (!theta || !q)))
     return static_fail(MLMC_ERR_INVALID_ARG, "bad arguments");
+  // the same checks mlmc_create applies to a configuration, except on the KL fields,
+  // which this entry point does not read
+  mlmc_config vc = *cfg;
+  vc.kl_terms = 1;
+  vc.kl_std = 0.0;
+  vc.kl_corr = 1.0;
+  const std::string why = mlmc::validate(vc);
+  if (!why.empty()) return static_fail(MLMC_ERR_INVALID_ARG, why);
+  bool ok = true;
+  const mlmc::Invariants U = mlmc::invariants(*cfg, ok);
+  if (!ok)
+    return static_fail(MLMC_ERR_INVALID_ARG, "material constants do not give a positive definite plane-strain stiffness");
   if (n == 0) return MLMC_OK;
-  if (cfg->precision != MLMC_PREC_FP64 && cfg->precision != MLMC_PREC_MIXED)
-    return static_fail(MLMC_ERR_INVALID_ARG, "unknown precision");
   // device address of the scratch array, looked up once per device with that device current
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -80,26 +90,10 @@ mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, i
   c.cfg = *cfg;
   c.stream = static_cast<cudaStream_t>(cuda_stream);
   c.device = dev;
-  {
-    const mlmc_config& k = *cfg;
-    const double S[3][3] = {{1.0 / k.E11, -k.nu12 / k.E11, -k.nu13 / k.E11},
-                            {-k.nu12 / k.E11, 1.0 / k.E22, -k.nu23 / k.E22},
-                            {-k.nu13 / k.E11, -k.nu23 / k.E22, 1.0 / k.E33}};
-    const double det = S[0][0] * (S[1][1] * S[2][2] - S[1][2] * S[2][1]) -
-                       S[0][1] * (S[1][0] * S[2][2] - S[1][2] * S[2][0]) +
-                       S[0][2] * (S[1][0] * S[2][1] - S[1][1] * S[2][0]);
-    if (!(std::isfinite(det) && det > 0.0)) return static_fail(MLMC_ERR_INVALID_ARG, "bad material constants");
-    const double Q11 = (S[1][1] * S[2][2] - S[1][2] * S[2][1]) / det;
-    const double Q12 = -(S[0][1] * S[2][2] - S[0][2] * S[2][1]) / det;
-    const double Q22 = (S[0][0] * S[2][2] - S[0][2] * S[2][0]) / det;
-    const double Q66 = k.G12;
-    c.U.U1 = (3.0 * Q11 + 3.0 * Q22 + 2.0 * Q12 + 4.0 * Q66) / 8.0;
-    c.U.U2 = (Q11 - Q22) / 2.0;
-    c.U.U3 = (Q11 + Q22 - 2.0 * Q12 - 4.0 * Q66) / 8.0;
-    c.U.U4 = (Q11 + Q22 + 6.0 * Q12 - 4.0 * Q66) / 8.0;
-    c.U.U5 = (Q11 + Q22 - 2.0 * Q12 + 4.0 * Q66) / 8.0;
-    c.U.round_single();
-  }
+  c.U = U;
+  // no CUDA graphs: capturing and instantiating one allocates, and a caller's stream
+  // that is itself being captured cannot begin a second capture
+  c.graphs = false;
   // front of the scratch: staged inputs and outputs; the rest: solver workspace
   const mlmc::LevelLayout m = c.mesh(mesh_level);
   const int64_t ne = n * m.n_el();
@@ -119,10 +113,17 @@ mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, i
   c.solve_arena.cap = kStaticScratchBytes - front_bytes;
   c.solve_arena.borrowed = true;
   cudaStream_t st = c.stream;
+  // after work is queued, a failing call waits for it, so that the next serialised
+  // call cannot find kernels of this one still writing the scratch array
+  auto fail_queued = [&](mlmc_status s, const std::string& m) {
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    return static_fail(s, m);
+  };
   const double* th_dev = theta;
   if (!device_accessible(theta)) {
     if ((e = cudaMemcpyAsync(th64, theta, sizeof(double) * ne, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-      return static_fail(MLMC_ERR_CUDA, std::string("copy in: ") + cudaGetErrorString(e));
+      return fail_queued(MLMC_ERR_CUDA, std::string("copy in: ") + cudaGetErrorString(e));
     th_dev = th64;
   }
   double* q_dev = device_accessible(q) ? q : qd;
@@ -130,27 +131,27 @@ mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, i
   mlmc_status s;
   if (c.mixed()) {
     if ((e = mlmc::launch_theta_to_trig2<float>(th_dev, ne, tr32, st)) != cudaSuccess)
-      return static_fail(MLMC_ERR_CUDA, cudaGetErrorString(e));
+      return fail_queued(MLMC_ERR_CUDA, cudaGetErrorString(e));
     std::vector<mlmc::SolveGroup<float>> g{{mesh_level, n, tr32, q_dev, s_dev, nullptr}};
     s = mlmc::solve_groups<float>(c, g);
   } else {
     if ((e = mlmc::launch_theta_to_trig2<double>(th_dev, ne, tr64, st)) != cudaSuccess)
-      return static_fail(MLMC_ERR_CUDA, cudaGetErrorString(e));
+      return fail_queued(MLMC_ERR_CUDA, cudaGetErrorString(e));
     std::vector<mlmc::SolveGroup<double>> g{{mesh_level, n, tr64, q_dev, s_dev, nullptr}};
     s = mlmc::solve_groups<double>(c, g);
   }
   if (s == MLMC_ERR_OOM)
-    return static_fail(MLMC_ERR_INVALID_ARG, "n = " + std::to_string(n) + " samples on a " + std::to_string(m.nx) +
+    return fail_queued(MLMC_ERR_INVALID_ARG, "n = " + std::to_string(n) + " samples on a " + std::to_string(m.nx) +
                                                  " x " + std::to_string(m.ny) +
                                                  " mesh need more than the 32 MiB static scratch");
-  if (s != MLMC_OK) return static_fail(s, c.err);
+  if (s != MLMC_OK) return fail_queued(s, c.err);
   if (q_dev != q && (e = cudaMemcpyAsync(q, q_dev, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-    return static_fail(MLMC_ERR_CUDA, std::string("copy out: ") + cudaGetErrorString(e));
+    return fail_queued(MLMC_ERR_CUDA, std::string("copy out: ") + cudaGetErrorString(e));
   if (s_dev && s_dev != status &&
       (e = cudaMemcpyAsync(status, s_dev, sizeof(int) * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-    return static_fail(MLMC_ERR_CUDA, std::string("copy out: ") + cudaGetErrorString(e));
+    return fail_queued(MLMC_ERR_CUDA, std::string("copy out: ") + cudaGetErrorString(e));
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
-    return static_fail(MLMC_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(e));
+    return fail_queued(MLMC_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(e));
   return MLMC_OK;
 }
 

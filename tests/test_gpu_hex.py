@@ -4,8 +4,11 @@
   synthesis bound;
 - the FP32 operator equals the oracle's assembled K applied to the same vector
   (1e-5 of max |K x|: sums of up to 24 terms in single precision);
+- the operator on the benchmark's 128x32x16 and 256x64x32 meshes equals the oracle's
+  element-by-element K x;
 - solves on the 16x4x2 / 32x8x4 meshes and on the benchmark's level-0 and level-1
-  meshes match the oracle's direct solves within the stated 1e-6 per quantity;
+  meshes match the oracle's direct solves, and on its 128x32x16 mesh the oracle's
+  conjugate-gradient solve, within the stated 1e-6 per quantity;
 - level pairs use the same xi on both meshes (the coarse solve of a pair equals the
   plain solve of that sample on the coarse mesh), and the moments equal numpy's;
 - the full-size level-3 mesh (256x64x32, 1.65M DOFs per sample) converges, and its
@@ -68,7 +71,7 @@ def test_theta_matches_oracle(B, w, m, level, first, n):
         B.mlmc3d_destroy(ctx)
 
 
-@pytest.mark.parametrize("w,m", [(SMALL, 0), (W, 0)])
+@pytest.mark.parametrize("w,m", [(SMALL, 0), (W, 0), (W, 2), (W, 3)])
 def test_operator_matches_oracle(B, w, m):
     ctx = B.mlmc3d_create(B.config3_from_workload(w))
     try:
@@ -83,8 +86,9 @@ def test_operator_matches_oracle(B, w, m):
         B.mlmc3d_apply(ctx, m, n, np.ascontiguousarray(theta), x, y)
         C = H.material_stiffness(w)
         for s in range(n):
-            K = H.assemble(nx, ny, nz, w["lx"] / nx, np.array([H.rotate(C, t) for t in theta[s]]))
-            ref = (K @ x[s, :, :3].astype(np.float64).ravel()).reshape(nn, 3)
+            # the oracle's element-by-element K x (no global matrix on the large meshes)
+            Cc = np.array([H.rotate(C, t) for t in theta[s]])
+            ref = H.apply(nx, ny, nz, w["lx"] / nx, Cc, x[s, :, :3].astype(np.float64).ravel()).reshape(nn, 3)
             assert np.abs(y[s, :, :3] - ref).max() <= 1e-5 * np.abs(ref).max()
             assert np.all(y[s, :, 3] == 0)
     finally:
@@ -109,6 +113,29 @@ def test_solves_match_oracle(B, w, items):
             xi = rng.kl_coefficients(w["seed"], level, [sid], w["kl_terms"])[0]
             ref = oracle_q(w, m, basis[m] @ xi)
             np.testing.assert_allclose(q[2 * k:2 * k + 2], ref, rtol=1e-6)
+    finally:
+        B.mlmc3d_destroy(ctx)
+
+
+def test_solves_on_the_128x32x16_mesh_match_oracle(B):
+    """Mesh 2 of the benchmark (217k DOFs per sample), the fine mesh of a level-2 pair
+    and the coarse mesh of a level-3 pair, against the oracle's conjugate-gradient solve
+    to a relative residual of 1e-12 (its factorisation's fill-in is too large there;
+    the quantities it gives have settled to about 1e-11 at that residual)."""
+    w = W
+    items = [(2, 2, 5), (3, 2, 9)]
+    ctx = B.mlmc3d_create(B.config3_from_workload(w))
+    try:
+        q = np.zeros(2 * len(items))
+        st = np.ones(len(items), dtype=np.int32)
+        B.mlmc3d_solve_batch(ctx, items, q, st)
+        assert np.all(st == 0)
+        Bm = oracle_basis(w, 2)
+        nx, ny, nz = dims(w, 2)
+        for k, (level, m, sid) in enumerate(items):
+            xi = rng.kl_coefficients(w["seed"], level, [sid], w["kl_terms"])[0]
+            r, s, _ = H.solve_sample(w, nx, ny, nz, Bm @ xi, solver="cg")
+            np.testing.assert_allclose(q[2 * k:2 * k + 2], [r, s], rtol=1e-6)
     finally:
         B.mlmc3d_destroy(ctx)
 

@@ -124,7 +124,9 @@ def test_mixed_five_levels_reduced_counts(B):
 
 def test_full_size_launch_sampled_outputs(B):
     """The benchmark's launch (all five levels at N_l = 8192/2048/512/128/32 in one
-    mlmc_sample_levels call); sampled outputs checked one by one against the oracle."""
+    mlmc_sample_levels call, which the library solves by nested iteration along each
+    sample's mesh chain); sampled outputs of every level, the 1024 x 256 / 512 x 128
+    pairs included, checked one by one against the oracle."""
     import torch
     w = STRIP_MIXED_5LEVEL
     counts = list(w["n_per_level"])
@@ -140,7 +142,9 @@ def test_full_size_launch_sampled_outputs(B):
         qf = qf.cpu().numpy().reshape(total, 2)
         qc = qc.cpu().numpy().reshape(total, 2)
         offs = np.concatenate([[0], np.cumsum(counts)])
-        picks = {0: [0, 4097, 8191], 1: [5, 2047], 2: [300], 3: [77]}
+        assert B.mlmc_get_tuning(ctx)["nested_min_nodes"] <= sum(
+            n * ((w["nx0"] << l) + 1) * ((w["ny0"] << l) + 1) for l, n in enumerate(counts))
+        picks = {0: [0, 4097, 8191], 1: [5, 2047], 2: [300], 3: [77], 4: [0, 31]}
         for level, ids in picks.items():
             rf, rc = oracle_pairs(w, level, ids)
             got_f = qf[offs[level] + np.array(ids)]

@@ -155,3 +155,88 @@ def test_telescoping_on_identical_xi():
     np.testing.assert_allclose(tel, Q[2].mean(0), rtol=1e-13)
     # and refinement changes the reaction by a shrinking amount
     assert abs(Q[2][0, 0] - Q[1][0, 0]) < abs(Q[1][0, 0] - Q[0][0, 0])
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.06, -0.2, 0.7])
+def test_fibre_stress_of_the_homogeneous_block(theta):
+    """Under the roller conditions the stress is uniaxial, sigma_xx = -shortening /
+    (lx S'_11), so the fibre-direction stress a1 . sigma a1 is sigma_xx cos^2 theta
+    in every element (the 3D counterpart of the strip's c^2 sigma_xx pin)."""
+    nx, ny, nz = 8, 2, 2
+    cfg = dict(W)
+    _, s, _ = H.solve_sample(cfg, nx, ny, nz, np.full(nx * nz, theta), bc="roller")
+    Sr = np.linalg.inv(H.rotate(H.material_stiffness(cfg), theta))
+    sxx = -cfg["shortening"] / (cfg["lx"] * Sr[0, 0])
+    assert s == pytest.approx(max(0.0, -sxx * np.cos(theta) ** 2), rel=1e-10)
+
+
+def test_fibre_stress_of_a_general_uniform_strain():
+    """All six strain components at once, so that a misplaced shear slot or a wrong
+    centroid strain shows: for a linear displacement field u = G x the centroid strain
+    is sym(G) exactly, and the fibre stress equals the first material-frame stress
+    component (C eps')_1, eps' = R^T eps R, computed without the rotated stiffness."""
+    nx, ny, nz = 8, 2, 2
+    cfg = dict(W)
+    h = cfg["lx"] / nx
+    g = np.random.default_rng(7)
+    G = g.normal(size=(3, 3)) * 1e-3
+    G[0, 0] = -2e-3                     # compressive along x
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    X = np.stack([i.ravel() * h, j.ravel() * h, k.ravel() * h], axis=1)   # node n = (k (ny+1) + j)(nx+1) + i
+    d = (X @ G.T).ravel()
+    theta = g.normal(scale=0.4, size=nx * nz)
+    C = H.material_stiffness(cfg)
+    C_col = np.array([H.rotate(C, t) for t in theta])
+    eps = 0.5 * (G + G.T)
+    expected = 0.0
+    for col in range(nx * nz):
+        xc = (col % nx + 0.5) * h
+        if not (cfg["omega_x0"] <= xc <= cfg["omega_x1"]):
+            continue
+        R = H.rotation_y(theta[col])
+        E = R.T @ eps @ R
+        e_mat = np.array([E[0, 0], E[1, 1], E[2, 2], 2 * E[1, 2], 2 * E[0, 2], 2 * E[0, 1]])
+        expected = max(expected, -(C @ e_mat)[0])
+    got = H.max_fibre_compression(cfg, d, C_col, theta, nx, ny, nz, h)
+    assert expected > 0
+    assert got == pytest.approx(expected, rel=1e-10)
+
+
+def test_fibre_stress_is_taken_at_the_centroid():
+    """u = (a x y, 0, 0) is trilinear, so the element strain is exact: e_xx = a y. At
+    theta = 0 the fibre stress is C_11 a y_c at the element centroid (y_c = (j + 1/2) h);
+    with a < 0 the maximum compression sits in the top element row."""
+    nx, ny, nz = 8, 2, 2
+    cfg = dict(W)
+    h = cfg["lx"] / nx
+    a = -1e-2
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    x, y = i.ravel() * h, j.ravel() * h
+    d = np.zeros(3 * x.size)
+    d[0::3] = a * x * y
+    C = H.material_stiffness(cfg)
+    theta = np.zeros(nx * nz)
+    got = H.max_fibre_compression(cfg, d, np.array([C] * (nx * nz)), theta, nx, ny, nz, h)
+    assert got == pytest.approx(-C[0, 0] * a * (ny - 0.5) * h, rel=1e-12)
+
+
+def test_matrix_free_apply_equals_assembled_matrix():
+    nx, ny, nz = 6, 2, 3
+    h = W["lx"] / nx
+    g = np.random.default_rng(11)
+    C = H.material_stiffness(W)
+    Cc = np.array([H.rotate(C, t) for t in g.normal(scale=0.2, size=nx * nz)])
+    K = H.assemble(nx, ny, nz, h, Cc)
+    x = g.normal(size=K.shape[0])
+    np.testing.assert_allclose(H.apply(nx, ny, nz, h, Cc, x), K @ x, rtol=1e-12, atol=1e-12 * np.abs(K @ x).max())
+
+
+def test_cg_solve_equals_direct_solve():
+    nx, ny, nz = 8, 2, 2
+    g = np.random.default_rng(12)
+    theta = g.normal(scale=0.05, size=nx * nz)
+    r1, s1, d1 = H.solve_sample(W, nx, ny, nz, theta)
+    r2, s2, d2 = H.solve_sample(W, nx, ny, nz, theta, solver="cg")
+    assert r2 == pytest.approx(r1, rel=1e-10)
+    assert s2 == pytest.approx(s1, rel=1e-8)
+    assert np.abs(d2 - d1).max() <= 1e-8 * np.abs(d1).max()

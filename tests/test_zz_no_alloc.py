@@ -72,3 +72,42 @@ def test_static_rejects_requests_beyond_its_scratch(B):
     q = np.zeros(2 * n)
     with pytest.raises(B.MLMCError, match="static scratch"):
         B.mlmc_solve_theta_static(cfg, 4, n, theta, q)
+
+
+def test_static_on_a_side_stream_matches_regular_entry_point(B):
+    """On a caller's own (non-default) stream the call still runs directly, with no
+    graph capture: the results match the regular entry point's, twice in a row."""
+    import torch
+    w, mesh, tol = STRIP_MIXED_5LEVEL, 1, 1e-6
+    cfg = B.config_from_workload(w)
+    ctx = B.mlmc_create(cfg)
+    side = torch.cuda.Stream()
+    try:
+        for call, (n, first) in enumerate([(5, 7), (3, 300)]):
+            theta = fields(w, mesh, n, first)
+            ref = np.zeros(2 * n)
+            ref_st = np.zeros(n, dtype=np.int32)
+            B.mlmc_solve_theta(ctx, mesh, n, theta, ref, ref_st)
+            with torch.cuda.stream(side):
+                th_d = torch.from_numpy(theta).cuda()
+                q_d = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+                st_d = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+                B.mlmc_solve_theta_static(cfg, mesh, n, th_d, q_d, st_d, stream=side.cuda_stream)
+            side.synchronize()
+            assert np.all(st_d.cpu().numpy() == 0) and np.all(ref_st == 0), call
+            np.testing.assert_allclose(q_d.cpu().numpy(), ref, rtol=tol, atol=0)
+    finally:
+        B.mlmc_destroy(ctx)
+
+
+@pytest.mark.parametrize("field,value,match", [("levels", 0, "levels"), ("nx0", 1, "nx0"), ("rtol", 1.5, "rtol"),
+                                               ("E22", -1.0, "moduli"), ("nu23", 1.5, "positive definite")])
+def test_static_rejects_the_configs_the_context_rejects(B, field, value, match):
+    cfg = B.config_from_workload(STRIP_MIXED_5LEVEL)
+    setattr(cfg, field, value)
+    theta = np.zeros(64 * 16)
+    q = np.zeros(2)
+    with pytest.raises(B.MLMCError, match=match):
+        B.mlmc_solve_theta_static(cfg, 0, 1, theta, q)
+    with pytest.raises(B.MLMCError, match=match):
+        B.mlmc_create(cfg)
