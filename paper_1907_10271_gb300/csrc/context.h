@@ -138,6 +138,8 @@ struct Context {
   // run the two smallest non-coarsest multigrid meshes and the coarsest solve of each
   // hierarchy in one launch (FP32 path, small enough bottoms)
   bool fused_bottom = true;
+  // strip kernels tile the samples of a view side by side (see View::packed)
+  bool pack_samples = true;
   int last_outer = 0;             // refinement steps of the last solve (diagnostic)
   int last_iters = 0;             // max PCG iterations of the last solve (diagnostic)
 

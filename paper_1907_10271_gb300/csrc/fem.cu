@@ -226,6 +226,40 @@ __device__ __forceinline__ bool find_tile(const ViewList<T>& L, int gw, int& vi,
   return s < V.nsamp;
 }
 
+// This lane's node column of a strip kernel: column i of sample s (s clamped into the
+// view, so that loads stay in bounds), whether it is a real node of a real sample
+// (valid), whether that sample is still iterating (live) and whether the lane writes
+// an output there (out: valid, live and one of the strip's output lanes).
+struct LaneCol {
+  int s, i;
+  bool valid, live, out;
+};
+
+// Strips of a strip kernel that hold output columns of sample s.
+template <typename T>
+__device__ __forceinline__ int tiles_of_sample(const View<T>& V, int s, int cols) {
+  if (!V.packed) return V.tiles_x * V.tiles_y;
+  const int a = s * V.vw;
+  return ((a + V.g.nx) / cols - a / cols + 1) * V.tiles_y;
+}
+
+// Sums v over the output lanes of each sample whose columns this warp writes (one, or
+// two on a packed view: lanes hold ascending virtual columns, so the first and last
+// output lanes name them) and calls f(sample, total) on lane 0 for each.
+template <typename F>
+__device__ __forceinline__ void per_sample(const LaneCol& lc, double v, F&& f) {
+  const unsigned m = __ballot_sync(0xffffffffu, lc.out);
+  if (m == 0u) return;
+  const int sa = __shfl_sync(0xffffffffu, lc.s, __ffs(m) - 1);
+  const int sb = __shfl_sync(0xffffffffu, lc.s, 31 - __clz(m));
+  const double ta = warp_sum(lc.out && lc.s == sa ? v : 0.0);
+  const double tb = sb != sa ? warp_sum(lc.out && lc.s == sb ? v : 0.0) : 0.0;
+  if ((threadIdx.x & 31) == 0) {
+    f(sa, ta);
+    if (sb != sa) f(sb, tb);
+  }
+}
+
 template <typename T>
 struct Vec4T {
   T x, y, z, w;
@@ -287,23 +321,27 @@ struct RowCarry {
 
 // Walks the warp's strip up its chunk of node rows. Node-row data is prefetched P
 // rows ahead into a register ring (static indices after unrolling), element data P
-// element rows ahead, so each warp keeps P rows of loads in flight. Lane l holds node
-// column strip * kCols - kHalo + l; lanes kHalo .. kHalo + kCols - 1 are the outputs.
+// element rows ahead, so each warp keeps P rows of loads in flight. Lane l holds
+// virtual column strip * kCols - kHalo + l (lc: its sample and node column); lanes
+// kHalo .. kHalo + kCols - 1 are the outputs. Neighbouring samples of a packed view
+// never couple: the element flag is false on a sample's last column and on its
+// padding column, so no element spans two samples and the shuffles across the seam
+// carry zero contributions.
 // in()/pair() and out() run on every lane (pair() and out() of the smoothing handlers
 // exchange values with lane l ^ 1); out() stores only where is_out. in() and load() may
 // shuffle too: every lane calls them (lanes outside the mesh on clamped columns, their
 // values discarded).
 template <typename T, int P, typename Op>
-__device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V, int strip, int chunk, Op& op) {
+__device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V, const LaneCol& lc, int chunk,
+                                           Op& op) {
   using Val = typename Op::Val;
   using Sc = typename Op::Sc;
-  constexpr int kCols = Op::kCols, kHalo = Op::kHalo;
   const int lane = threadIdx.x & (kWarp - 1);
   const int nx = V.g.nx, ny = V.g.ny;
-  const int i = strip * kCols - kHalo + lane;
-  const bool col_in = (i >= 0) && (i <= nx);
-  const bool elem = (i >= 0) && (i < nx) && (lane < kWarp - 1);
-  const bool out_col = col_in && lane >= kHalo && lane < kHalo + kCols;
+  const int i = lc.i;
+  const bool col_in = lc.valid;
+  const bool elem = lc.valid && (i < nx) && (lane < kWarp - 1);
+  const bool out_col = lc.out;
   const int ic = min(max(i, 0), nx);       // in-bounds column for (discarded) loads of outside lanes
   const int ie = min(max(i, 0), nx - 1);
   const int rows = V.rows > 0 ? V.rows : kRowChunk;
@@ -351,17 +389,16 @@ __device__ __forceinline__ void strip_loop(const Invariants& U, const View<T>& V
 // strip_loop with node and element rows staged through a ring of D shared-memory
 // slots (cp.async); step k holds node row er0 + k and element row er0 + k - 1.
 template <typename T, int D, typename Op>
-__device__ __forceinline__ void strip_loop_async(const Invariants& U, const View<T>& V, int strip, int chunk, Op& op,
-                                                 typename Op::Slot* ring) {
+__device__ __forceinline__ void strip_loop_async(const Invariants& U, const View<T>& V, const LaneCol& lc, int chunk,
+                                                 Op& op, typename Op::Slot* ring) {
   using Val = typename Op::Val;
   using Sc = typename Op::Sc;
-  constexpr int kCols = Op::kCols, kHalo = Op::kHalo;
   const int lane = threadIdx.x & (kWarp - 1);
   const int nx = V.g.nx, ny = V.g.ny;
-  const int i = strip * kCols - kHalo + lane;
-  const bool col_in = (i >= 0) && (i <= nx);
-  const bool elem = (i >= 0) && (i < nx) && (lane < kWarp - 1);
-  const bool out_col = col_in && lane >= kHalo && lane < kHalo + kCols;
+  const int i = lc.i;
+  const bool col_in = lc.valid;
+  const bool elem = lc.valid && (i < nx) && (lane < kWarp - 1);
+  const bool out_col = lc.out;
   const int ic = min(max(i, 0), nx);
   const int ie = min(max(i, 0), nx - 1);
   const int rows = V.rows > 0 ? V.rows : kRowChunk;
@@ -569,7 +606,7 @@ struct OpApply : OpBase<T> {
     if (is_out) st2(this->V.o0 + this->at(i, j), kp);
   }
   __device__ void shift() {}
-  __device__ void finish(const SampleState&, int) {}
+  __device__ void finish(const SampleState&, const LaneCol&) {}
 };
 
 // Smoother of the pre-smoothing from zero, x1 = W b, for the handlers below: u gets
@@ -653,9 +690,8 @@ struct OpPreTop : OpBase<T> {
     rr.add(ab_.r.u * ab_.r.u + ab_.r.v * ab_.r.v);
   }
   __device__ void shift() { ab_ = at_; }
-  __device__ void finish(const SampleState& S, int s) {
-    const double t = warp_sum(rr.value());
-    if ((threadIdx.x & 31) == 0) atomicAdd(&S.red_rr[this->V.sbase + s], t);
+  __device__ void finish(const SampleState& S, const LaneCol& lc) {
+    per_sample(lc, rr.value(), [&](int s, double t) { atomicAdd(&S.red_rr[this->V.sbase + s], t); });
   }
 };
 
@@ -776,7 +812,7 @@ struct OpPreR : OpBase<T> {
     st2(this->V.o2 + k, this->mask(i, v2<T>(bb.u - kx.u, bb.v - kx.v)));
   }
   __device__ void shift() { bb = bt; }
-  __device__ void finish(const SampleState&, int) {}
+  __device__ void finish(const SampleState&, const LaneCol&) {}
 };
 
 // a = b, xc (level below), winvd + wc; o0 = z = x2 + W (b - K x2) with x2 = W b + P xc.
@@ -870,14 +906,13 @@ struct OpPost : OpBase<T> {
     wb = wt;
     cb = ct;
   }
-  __device__ void finish(const SampleState& S, int s) {
+  __device__ void finish(const SampleState& S, const LaneCol& lc) {
     if (TOP) {
-      const double t = warp_sum(rz.value());
-      if ((threadIdx.x & 31) == 0) {
+      per_sample(lc, rz.value(), [&](int s, double t) {
         const int g = this->V.sbase + s;
         atomicAdd(&S.red_rz[g], t);
-        if (last_tile(S.arrive, g, this->V.tiles_x * this->V.tiles_y)) after_post(S, g);
-      }
+        if (last_tile(S.arrive, g, tiles_of_sample(this->V, s, kCols))) after_post(S, g);
+      });
     }
   }
 };
@@ -925,13 +960,12 @@ struct OpPcgP : OpBase<T> {
     pq.add(pb.u * q.u + pb.v * q.v);
   }
   __device__ void shift() { pb = pt; }
-  __device__ void finish(const SampleState& S, int s) {
-    const double t = warp_sum(pq.value());
-    if ((threadIdx.x & 31) == 0) {
+  __device__ void finish(const SampleState& S, const LaneCol& lc) {
+    per_sample(lc, pq.value(), [&](int s, double t) {
       const int g = this->V.sbase + s;
       atomicAdd(&S.red_pq[g], t);
-      if (last_tile(S.arrive, g, this->V.tiles_x * this->V.tiles_y)) after_p(S, g);
-    }
+      if (last_tile(S.arrive, g, tiles_of_sample(this->V, s, OpBase<T>::kCols))) after_p(S, g);
+    });
   }
 };
 
@@ -1003,15 +1037,12 @@ struct OpResid : OpBase<double> {
     if (i == V.g.nx) react = react + kd.u;
   }
   __device__ void shift() {}
-  __device__ void finish(const SampleState& S, int s) {
+  __device__ void finish(const SampleState& S, const LaneCol& lc) {
     double rv;
     if constexpr (sizeof(TI) == 4) rv = df_to_double(react);
     else rv = react;
-    const double t = warp_sum(rr.value()), u = warp_sum(rv);
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&S.rr64[V.sbase + s], t);
-      atomicAdd(&S.react[V.sbase + s], u);
-    }
+    per_sample(lc, rr.value(), [&](int s, double t) { atomicAdd(&S.rr64[V.sbase + s], t); });
+    per_sample(lc, rv, [&](int s, double t) { atomicAdd(&S.react[V.sbase + s], t); });
   }
 };
 
@@ -1022,23 +1053,39 @@ __global__ void __launch_bounds__(kWarpsPerBlock * kWarp, sizeof(T) == 4 ? Op::k
   int vi, s, strip, chunk;
   if (!find_tile(L, gw, vi, s, strip, chunk)) return;
   const View<T>& V = L.v[vi];
-  const int col = strip * Op::kCols - Op::kHalo + (int)(threadIdx.x & 31);
-  Op op(V, s, min(max(col, 0), V.g.nx), min(max(col, 0), V.g.nx - 1), S);
-  if (!op.live()) return;
-  if (S.units && (threadIdx.x & 31) == 0) {
-    const int c0 = max(strip * Op::kCols, 0), c1 = min(strip * Op::kCols + Op::kCols - 1, V.g.nx);
-    const int rows = V.rows > 0 ? V.rows : kRowChunk;
-    const int r0 = chunk * rows, r1 = min(r0 + rows - 1, V.g.ny);
-    atomicAdd(&S.units[L.prof_op], (unsigned long long)((c1 - c0 + 1) * (r1 - r0 + 1)));
+  const int lane = (int)(threadIdx.x & 31);
+  const int vcol = strip * Op::kCols - Op::kHalo + lane;
+  LaneCol lc;
+  if (V.packed) {   // virtual column -> (sample, column); the padding column nx + 1 is not valid
+    const int q = vcol >= 0 ? vcol / V.vw : 0;
+    lc.i = vcol >= 0 ? vcol - q * V.vw : vcol;
+    lc.valid = vcol >= 0 && q < V.nsamp && lc.i <= V.g.nx;
+    lc.s = min(q, V.nsamp - 1);
+  } else {
+    lc.s = s;
+    lc.i = vcol;
+    lc.valid = vcol >= 0 && vcol <= V.g.nx;
+  }
+  Op op(V, lc.s, min(max(lc.i, 0), V.g.nx), min(max(lc.i, 0), V.g.nx - 1), S);
+  lc.live = op.live();
+  if (!__any_sync(0xffffffffu, lc.valid && lc.live)) return;
+  lc.out = lc.valid && lc.live && lane >= Op::kHalo && lane < Op::kHalo + Op::kCols;
+  if (S.units) {
+    const unsigned m = __ballot_sync(0xffffffffu, lc.out);
+    if (lane == 0 && m) {
+      const int rows = V.rows > 0 ? V.rows : kRowChunk;
+      const int r0 = chunk * rows, r1 = min(r0 + rows - 1, V.g.ny);
+      atomicAdd(&S.units[L.prof_op], (unsigned long long)(__popc(m) * (r1 - r0 + 1)));
+    }
   }
   if constexpr (Op::kAsync) {
     extern __shared__ __align__(16) unsigned char strip_smem[];
     typename Op::Slot* ring = reinterpret_cast<typename Op::Slot*>(strip_smem) + (threadIdx.x >> 5) * Op::kDepth;
-    strip_loop_async<T, Op::kDepth>(L.U, V, strip, chunk, op, ring);
+    strip_loop_async<T, Op::kDepth>(L.U, V, lc, chunk, op, ring);
   } else {
-    strip_loop<T, P>(L.U, V, strip, chunk, op);
+    strip_loop<T, P>(L.U, V, lc, chunk, op);
   }
-  op.finish(S, s);
+  op.finish(S, lc);
 }
 
 // ---------------------------------------------------------------- pointwise kernels

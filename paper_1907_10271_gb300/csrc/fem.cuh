@@ -20,6 +20,13 @@ struct View {
   int nwork;
   int tiles_x, tiles_y;
   int rows;         // node rows per warp tile of a strip kernel (0: kRowChunk)
+  // strip kernels, packed views: the samples lie side by side along one virtual row of
+  // nsamp * vw node columns (vw = nx + 2: the nx + 1 real columns and one padding
+  // column, so that every sample starts on an even column), and warp strips tile that
+  // row, so a narrow mesh does not leave most of a sample's last strip idle;
+  // tiles_x then counts the strips of the whole virtual row
+  int packed;
+  int vw;
   const T* trig2;
   const T* trig;
   const T* a;

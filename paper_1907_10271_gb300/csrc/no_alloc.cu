@@ -50,8 +50,6 @@ const char* mlmc_static_last_error(void) { return g_static_error.c_str(); }
 mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, int32_t mesh_level, int64_t n,
                                     const double* theta, double* q, int32_t* status) {
   if (!cfg) return static_fail(MLMC_ERR_INVALID_ARG, "null config");
-  if (mesh_level < 0 || mesh_level >= cfg->levels || n < 0 || (n > 0 && (!theta || !q)))
-    return static_fail(MLMC_ERR_INVALID_ARG, "bad arguments");
   // the same checks mlmc_create applies to a configuration, except on the KL fields,
   // which this entry point does not read
   mlmc_config vc = *cfg;
@@ -64,6 +62,8 @@ mlmc_status mlmc_solve_theta_static(const mlmc_config* cfg, void* cuda_stream, i
   const mlmc::Invariants U = mlmc::invariants(*cfg, ok);
   if (!ok)
     return static_fail(MLMC_ERR_INVALID_ARG, "material constants do not give a positive definite plane-strain stiffness");
+  if (mesh_level < 0 || mesh_level >= cfg->levels) return static_fail(MLMC_ERR_INVALID_ARG, "mesh level out of range");
+  if (n < 0 || (n > 0 && (!theta || !q))) return static_fail(MLMC_ERR_INVALID_ARG, "bad arguments");
   if (n == 0) return MLMC_OK;
   // device address of the scratch array, looked up once per device with that device current
   int dev = 0;

@@ -87,10 +87,20 @@ int finalize_warps(const Context& ctx, ViewList<T>& L, StripOp op) {
       const int base = chunks_of(v.g.ny, max_rows);
       const int nch = std::max(base, std::min(base * split, nodes_y / min_rows));
       v.rows = (nodes_y + nch - 1) / nch;
-      v.tiles_x = strips_of(v.g.nx, strip_cols(op));
       v.tiles_y = chunks_of(v.g.ny, v.rows);
+      // samples side by side when a sample's width fills at least one strip (then a
+      // warp's outputs span at most two samples)
+      const int cols = strip_cols(op);
+      v.vw = v.g.nx + 2;
+      v.packed = ctx.pack_samples && v.vw >= cols ? 1 : 0;
+      if (v.packed) {
+        v.tiles_x = (int)(((int64_t)v.nsamp * v.vw + cols - 1) / cols);
+        v.nwork = v.tiles_x * v.tiles_y;
+      } else {
+        v.tiles_x = strips_of(v.g.nx, cols);
+        v.nwork = v.nsamp * v.tiles_x * v.tiles_y;
+      }
       v.work_begin = acc;
-      v.nwork = v.nsamp * v.tiles_x * v.tiles_y;
       acc += v.nwork;
     }
     return acc;
