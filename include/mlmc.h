@@ -142,15 +142,22 @@ typedef struct {
   int32_t min_rows;           /* rows per tile when small launches split (1 .. max_rows) */
   double target_waves;        /* launches below this many resident waves split their tiles */
   int64_t nested_min_nodes;   /* as mlmc_set_nested_threshold */
-  int32_t fused_bottom;       /* 1: the two smallest non-coarsest multigrid meshes and the coarsest
-                                 solve of each hierarchy run as one launch (mixed precision) */
+  int32_t fused_bottom;       /* multigrid bottom of the mixed-precision path: 2 = the three
+                                 smallest non-coarsest meshes and the coarsest solve of each
+                                 hierarchy in one launch (a thread block per sample, hierarchies
+                                 of five levels or more); 1 = the two smallest and the coarsest
+                                 in one launch (a warp per sample); 0 = a launch per level */
   double step_ms;             /* (autotune output) time of the tuned workload with these values */
+  int32_t pack_samples;       /* 1: the strip kernels tile the samples of a mesh side by side
+                                 (a warp strip may hold the end of one sample and the start of
+                                 the next), so narrow meshes fill their warps; 0: every warp
+                                 strip holds columns of one sample */
 } mlmc_tuning;
 
 /* Times the level-pair workload {levels[k], counts[k]} (host arrays of n_req entries,
    as for mlmc_sample_levels, on sample ids far from any the caller uses) under
    candidate launch shapes and nested-iteration settings, by coordinate descent
-   (nested iteration on / off, fused multigrid bottom on / off, target_waves 0.75 /
+   (nested iteration on / off, fused multigrid bottom 2 / 1 / 0, target_waves 0.75 /
    1.5 / 3, max_rows 32 / 64, min_rows 4 / 6 / 8; one warm-up and `reps` timed calls
    each, the median kept; the current values are timed first and a candidate replaces
    them only when more than 1 % faster), and keeps

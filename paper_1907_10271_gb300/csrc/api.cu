@@ -584,7 +584,8 @@ mlmc_status mlmc_get_tuning(mlmc_ctx* h, mlmc_tuning* out) {
   out->min_rows = c.min_rows;
   out->target_waves = c.target_waves;
   out->nested_min_nodes = c.nested_min_nodes;
-  out->fused_bottom = c.fused_bottom ? 1 : 0;
+  out->fused_bottom = c.fused_bottom;
+  out->pack_samples = c.pack_samples ? 1 : 0;
   out->step_ms = 0.0;
   return MLMC_OK;
 }
@@ -594,9 +595,10 @@ mlmc_status mlmc_set_tuning(mlmc_ctx* h, const mlmc_tuning* t) {
   Context& c = h->c;
   if (t->max_rows < 1 || t->max_rows > 64 || t->min_rows < 1 || t->min_rows > t->max_rows ||
       !(t->target_waves >= 0.0 && t->target_waves <= 64.0) || t->nested_min_nodes < 0 ||
-      (t->fused_bottom != 0 && t->fused_bottom != 1))
+      t->fused_bottom < 0 || t->fused_bottom > 2 || (t->pack_samples != 0 && t->pack_samples != 1))
     return c.fail(MLMC_ERR_INVALID_ARG, "tuning value out of range");
-  c.fused_bottom = t->fused_bottom != 0;
+  c.fused_bottom = t->fused_bottom;
+  c.pack_samples = t->pack_samples != 0;
   c.max_rows = t->max_rows;
   c.min_rows = t->min_rows;
   c.target_waves = t->target_waves;
@@ -635,7 +637,7 @@ mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, con
     int64_t nested;
     double waves;
     int max_rows, min_rows;
-    bool fused;
+    int fused;
   };
   Cand best{c.nested_min_nodes, c.target_waves, c.max_rows, c.min_rows, c.fused_bottom};
   double best_ms = 1e300;
@@ -679,7 +681,7 @@ mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, con
   s = consider(best);
   for (int64_t v : nested_vals)
     if (s == MLMC_OK) s = consider(Cand{v, best.waves, best.max_rows, best.min_rows, best.fused});
-  for (bool v : {true, false})
+  for (int v : {1, 2, 0})
     if (s == MLMC_OK) s = consider(Cand{best.nested, best.waves, best.max_rows, best.min_rows, v});
   for (double v : wave_vals)
     if (s == MLMC_OK) s = consider(Cand{best.nested, v, best.max_rows, best.min_rows, best.fused});

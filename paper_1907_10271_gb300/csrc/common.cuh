@@ -206,7 +206,7 @@ struct Geo {
   double rx, ry, w;   // 1/(2hx), 1/(2hy), hx*hy
   int square;         // hx == hy: the square-element operator applies
   int c0, c1;         // element columns whose centroid x lies in the stress region (c1 < c0: none)
-  int nodes() const { return (nx + 1) * (ny + 1); }
+  __host__ __device__ int nodes() const { return (nx + 1) * (ny + 1); }
 };
 
 __host__ __device__ __forceinline__ int strips_of(int nx, int cols = kStripCols) { return (nx + 1 + cols - 1) / cols; }

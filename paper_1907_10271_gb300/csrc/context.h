@@ -135,9 +135,11 @@ struct Context {
   int max_rows = 64;
   int min_rows = 6;
   double target_waves = 1.5;
-  // run the two smallest non-coarsest multigrid meshes and the coarsest solve of each
-  // hierarchy in one launch (FP32 path, small enough bottoms)
-  bool fused_bottom = true;
+  // multigrid bottom (FP32 path, small enough bottoms): 2 = the three smallest
+  // non-coarsest meshes and the coarsest solve of each hierarchy in one launch, one
+  // thread block per sample; 1 = the two smallest and the coarsest, one warp per
+  // sample; 0 = a launch per level
+  int fused_bottom = 1;
   // strip kernels tile the samples of a view side by side (see View::packed)
   bool pack_samples = true;
   int last_outer = 0;             // refinement steps of the last solve (diagnostic)

@@ -1341,13 +1341,24 @@ __global__ void k_coarsest_solve(const __grid_constant__ ViewList<T> L, SampleSt
 }
 
 // ---------------------------------------------------------------- multigrid bottom (FP32)
-// Small-mesh pieces of k_bottom; one warp per sample, vectors in shared memory as
-// [node][2] with node = j (nx + 1) + i. Each piece ends with a warp barrier.
+// Small-mesh pieces of k_bottom (one warp per sample) and k_bottom_deep (one thread
+// block per sample); vectors in shared memory as [node][2] with node = j (nx + 1) + i.
+// The threads of group G share the work of each piece, which ends with G's barrier.
+struct WarpGroup {
+  int t;
+  static constexpr int n = 32;
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+struct BlockGroup {
+  int t, n;
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
 
 // b = mask(R f): full weighting of the fine vector f (nodes of the 2nx x 2ny mesh)
-__device__ __forceinline__ void bot_restrict(const Geo& g, const float* f, float* b, int lane) {
+template <typename Grp>
+__device__ __forceinline__ void bot_restrict(const Geo& g, const float* f, float* b, const Grp& G) {
   const int nxp = g.nx + 1, nxf = 2 * g.nx, nyf = 2 * g.ny;
-  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {
+  for (int node = G.t; node < nxp * (g.ny + 1); node += G.n) {
     const int j = node / nxp, i = node - j * nxp;
     float su = 0.f, sv = 0.f;
     for (int dj = -1; dj <= 1; ++dj) {
@@ -1365,14 +1376,15 @@ __device__ __forceinline__ void bot_restrict(const Geo& g, const float* f, float
     b[2 * node] = dir_u(i, g.nx) ? 0.f : su;
     b[2 * node + 1] = dir_v(i) ? 0.f : sv;
   }
-  __syncwarp();
+  G.sync();
 }
 
 // y = W v (pair-block smoother: u takes its pair partner's term, column i ^ 1), plus add
+template <typename Grp>
 __device__ __forceinline__ void bot_smooth(const Geo& g, const float* winv, const float* wc, const float* v,
-                                           const float* add, float* y, int lane) {
+                                           const float* add, float* y, const Grp& G) {
   const int nxp = g.nx + 1;
-  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {
+  for (int node = G.t; node < nxp * (g.ny + 1); node += G.n) {
     const int j = node / nxp, i = node - j * nxp;
     const int ip = i ^ 1;
     const float other = ip <= g.nx ? v[2 * (j * nxp + ip)] : 0.f;
@@ -1385,17 +1397,18 @@ __device__ __forceinline__ void bot_smooth(const Geo& g, const float* winv, cons
     y[2 * node] = u;
     y[2 * node + 1] = vv;
   }
-  __syncwarp();
+  G.sync();
 }
 
 // t = K x (t zeroed here); element (i, j) has corners (i, j) (i+1, j) (i+1, j+1) (i, j+1)
+template <typename Grp>
 __device__ __forceinline__ void bot_apply(const Invariants& U, const Geo& g, const float* trig, const float* x,
-                                          float* t, int lane) {
+                                          float* t, const Grp& G) {
   const int nxp = g.nx + 1;
-  for (int r = lane; r < 2 * nxp * (g.ny + 1); r += 32) t[r] = 0.f;
-  __syncwarp();
+  for (int r = G.t; r < 2 * nxp * (g.ny + 1); r += G.n) t[r] = 0.f;
+  G.sync();
   const float rx = (float)g.rx, ry = (float)g.ry, w = (float)g.w;
-  for (int e = lane; e < g.nx * g.ny; e += 32) {
+  for (int e = G.t; e < g.nx * g.ny; e += G.n) {
     const int j = e / g.nx, i = e - j * g.nx;
     const float4 tr = reinterpret_cast<const float4*>(trig)[e];
     const int k1 = j * nxp + i, k2 = k1 + 1, k3 = k1 + nxp + 1, k4 = k1 + nxp;
@@ -1418,24 +1431,26 @@ __device__ __forceinline__ void bot_apply(const Invariants& U, const Geo& g, con
     atomicAdd(&t[2 * k4], o4.u);
     atomicAdd(&t[2 * k4 + 1], o4.v);
   }
-  __syncwarp();
+  G.sync();
 }
 
 // r = mask(b - t)
-__device__ __forceinline__ void bot_resid(const Geo& g, const float* b, const float* t, float* r, int lane) {
+template <typename Grp>
+__device__ __forceinline__ void bot_resid(const Geo& g, const float* b, const float* t, float* r, const Grp& G) {
   const int nxp = g.nx + 1;
-  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {
+  for (int node = G.t; node < nxp * (g.ny + 1); node += G.n) {
     const int i = node % nxp;
     r[2 * node] = dir_u(i, g.nx) ? 0.f : b[2 * node] - t[2 * node];
     r[2 * node + 1] = dir_v(i) ? 0.f : b[2 * node + 1] - t[2 * node + 1];
   }
-  __syncwarp();
+  G.sync();
 }
 
 // p = P xc (bilinear prolongation of the coarse vector)
-__device__ __forceinline__ void bot_prolong(const Geo& g, const float* xc, float* p, int lane) {
+template <typename Grp>
+__device__ __forceinline__ void bot_prolong(const Geo& g, const float* xc, float* p, const Grp& G) {
   const int nxp = g.nx + 1, nxc = g.nx / 2;
-  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {
+  for (int node = G.t; node < nxp * (g.ny + 1); node += G.n) {
     const int j = node / nxp, i = node - j * nxp;
     const int I = i >> 1, J = j >> 1;
     float cu = xc[2 * (J * (nxc + 1) + I)], cv = xc[2 * (J * (nxc + 1) + I) + 1];
@@ -1455,23 +1470,24 @@ __device__ __forceinline__ void bot_prolong(const Geo& g, const float* xc, float
     p[2 * node] = f * cu;
     p[2 * node + 1] = f * cv;
   }
-  __syncwarp();
+  G.sync();
 }
 
 // post-smoothing of level g: x2 = W b + P xc, z = mask(x2 + W (b - K x2)) into out
+template <typename Grp>
 __device__ __forceinline__ void bot_post(const Invariants& U, const Geo& g, const float* winv, const float* wc,
                                          const float* trig, const float* b, const float* xc, float* x2, float* t,
-                                         float* out, int lane) {
-  bot_prolong(g, xc, t, lane);                 // t = P xc
-  bot_smooth(g, winv, wc, b, t, x2, lane);     // x2 = W b + P xc
-  bot_apply(U, g, trig, x2, t, lane);          // t = K x2
+                                         float* out, const Grp& G) {
+  bot_prolong(g, xc, t, G);                 // t = P xc
+  bot_smooth(g, winv, wc, b, t, x2, G);     // x2 = W b + P xc
+  bot_apply(U, g, trig, x2, t, G);          // t = K x2
   const int nxp = g.nx + 1;
-  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {   // t = b - K x2 (unmasked: W is zero there)
+  for (int node = G.t; node < nxp * (g.ny + 1); node += G.n) {   // t = b - K x2 (unmasked: W is zero there)
     t[2 * node] = b[2 * node] - t[2 * node];
     t[2 * node + 1] = b[2 * node + 1] - t[2 * node + 1];
   }
-  __syncwarp();
-  for (int node = lane; node < nxp * (g.ny + 1); node += 32) {
+  G.sync();
+  for (int node = G.t; node < nxp * (g.ny + 1); node += G.n) {
     const int j = node / nxp, i = node - j * nxp;
     const int ip = i ^ 1;
     const float other = ip <= g.nx ? t[2 * (j * nxp + ip)] : 0.f;
@@ -1483,7 +1499,7 @@ __device__ __forceinline__ void bot_post(const Invariants& U, const Geo& g, cons
     out[2 * node] = zu;
     out[2 * node + 1] = zv;
   }
-  __syncwarp();
+  G.sync();
 }
 
 constexpr int kBotFloats = 2 * kBotNodes * 3 + 2 * kBotNodesB * 3 + 2 * kMaxCoarsestDofs;
@@ -1491,6 +1507,7 @@ constexpr int kBotFloats = 2 * kBotNodes * 3 + 2 * kBotNodesB * 3 + 2 * kMaxCoar
 __global__ void __launch_bounds__(kWarpsPerBlock * kWarp) k_bottom(const __grid_constant__ BottomList L, SampleState S) {
   __shared__ __align__(16) float sm[kWarpsPerBlock][kBotFloats];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const WarpGroup G{lane};
   const int gw = blockIdx.x * kWarpsPerBlock + wib;
   int vi = 0;
   while (vi < L.n && gw >= L.v[vi].work_begin + L.v[vi].nsamp) ++vi;
@@ -1517,16 +1534,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * kWarp) k_bottom(const __grid_
   const float* wcB = V.wc_b + (int64_t)s * nb;
   const float* trB = V.trig_b + (int64_t)s * 4 * gb.nx * gb.ny;
   // down: level A from the residual of the level above, then level B
-  bot_restrict(ga, V.rin + (int64_t)s * 2 * nf, bA, lane);
-  bot_smooth(ga, winvA, wcA, bA, nullptr, xA, lane);
-  bot_apply(L.U, ga, trA, xA, tA, lane);
-  bot_resid(ga, bA, tA, tA, lane);             // tA = r_A
-  bot_restrict(gb, tA, bB, lane);
-  bot_smooth(gb, winvB, wcB, bB, nullptr, xB, lane);
-  bot_apply(L.U, gb, trB, xB, tB, lane);
-  bot_resid(gb, bB, tB, tB, lane);             // tB = r_B
+  bot_restrict(ga, V.rin + (int64_t)s * 2 * nf, bA, G);
+  bot_smooth(ga, winvA, wcA, bA, nullptr, xA, G);
+  bot_apply(L.U, ga, trA, xA, tA, G);
+  bot_resid(ga, bA, tA, tA, G);             // tA = r_A
+  bot_restrict(gb, tA, bB, G);
+  bot_smooth(gb, winvB, wcB, bB, nullptr, xB, G);
+  bot_apply(L.U, gb, trB, xB, tB, G);
+  bot_resid(gb, bB, tB, tB, G);             // tB = r_B
   // coarsest: x_C = A^-1 R r_B (into tA's space, free now: level C has <= 64 values)
-  bot_restrict(gc, tB, bC, lane);
+  bot_restrict(gc, tB, bC, G);
   float* xC = tA;
   const float* Ai = V.ainv + (int64_t)s * nc * nc;
   for (int r = lane; r < nc; r += 32) {
@@ -1536,9 +1553,86 @@ __global__ void __launch_bounds__(kWarpsPerBlock * kWarp) k_bottom(const __grid_
   }
   __syncwarp();
   // up: level B (its post-smoothed x into xB), then level A straight to the output
-  bot_post(L.U, gb, winvB, wcB, trB, bB, xC, xB, tB, xB, lane);   // scratch x2 = out = xB, t = tB
+  bot_post(L.U, gb, winvB, wcB, trB, bB, xC, xB, tB, xB, G);   // scratch x2 = out = xB, t = tB
   float* outA = V.xout + (int64_t)s * 2 * na;
-  bot_post(L.U, ga, winvA, wcA, trA, bA, xB, xA, tA, outA, lane);   // scratch x2 = xA, t = tA
+  bot_post(L.U, ga, winvA, wcA, trA, bA, xB, xA, tA, outA, G);   // scratch x2 = xA, t = tA
+}
+
+
+// The deepest levels of every group in one launch, one thread block per sample: the
+// smoothed levels A_0 .. A_{nb-1} (finest first) and the coarsest C, with each
+// smoothed level's smoother and element data copied into shared memory once at the
+// start (cp.async), so that the V-cycle's many dependent steps on these small meshes
+// wait on shared memory only. Same operations and order as PreR on A_0 .. A_{nb-1},
+// the coarsest solve and Post back up: b_0 = R r_in, x_k = W b_k, r_k = b_k - K x_k,
+// b_{k+1} = R r_k, ..., x_C = A^-1 R r_{nb-1}; then for k = nb-1 .. 0:
+// x2 = W b_k + P x_{k+1}, x_k = x2 + W (b_k - K x2); writes x_0 (what Post or PostTop
+// on the level above prolongates).
+__global__ void __launch_bounds__(kDeepThreads) k_bottom_deep(const __grid_constant__ DeepList L, SampleState S) {
+  extern __shared__ __align__(16) float dsm[];
+  int vi = 0;
+  const int gb = blockIdx.x;
+  while (vi < L.n && gb >= L.v[vi].work_begin + L.v[vi].nsamp) ++vi;
+  if (vi >= L.n) return;
+  const DeepView& V = L.v[vi];
+  const int s = gb - V.work_begin;
+  if (s < 0 || !S.active[V.sbase + s]) return;   // the whole block
+  const BlockGroup G{(int)threadIdx.x, (int)blockDim.x};
+  const int nb = V.nb;
+  float *b[kDeepMax], *x[kDeepMax], *t[kDeepMax], *w[kDeepMax], *c[kDeepMax], *tr[kDeepMax];
+  float* p = dsm;
+  auto take = [&](int count) {   // 16-byte aligned carving (float4 element data, float2 smoother)
+    float* q = p;
+    p += (count + 3) & ~3;
+    return q;
+  };
+  for (int k = 0; k < nb; ++k) {
+    const int n = V.g[k].nodes(), ne = V.g[k].nx * V.g[k].ny;
+    b[k] = take(2 * n);
+    x[k] = take(2 * n);
+    t[k] = take(2 * n);
+    w[k] = take(2 * n);
+    c[k] = take(n);
+    tr[k] = take(4 * ne);
+    const float* ws = V.winv[k] + (int64_t)s * 2 * n;
+    const float* cs = V.wc[k] + (int64_t)s * n;
+    const float* ts = V.trig[k] + (int64_t)s * 4 * ne;
+    for (int q = G.t; q < 2 * n; q += G.n) cp_async<4>(w[k] + q, ws + q);
+    for (int q = G.t; q < n; q += G.n) cp_async<4>(c[k] + q, cs + q);
+    for (int q = G.t; q < 4 * ne; q += G.n) cp_async<4>(tr[k] + q, ts + q);
+  }
+  const int nc = 2 * V.gc.nodes();
+  float* bC = take(nc);
+  float* xC = take(nc);
+  cp_async_commit();
+  // down; the first restriction reads the residual of the level above from global memory
+  {
+    const Geo& g0 = V.g[0];
+    const int nf = (2 * g0.nx + 1) * (2 * g0.ny + 1);
+    bot_restrict(g0, V.rin + (int64_t)s * 2 * nf, b[0], G);
+  }
+  cp_async_wait<0>();
+  G.sync();
+  for (int k = 0; k < nb; ++k) {
+    if (k > 0) bot_restrict(V.g[k], t[k - 1], b[k], G);
+    bot_smooth(V.g[k], w[k], c[k], b[k], nullptr, x[k], G);
+    bot_apply(L.U, V.g[k], tr[k], x[k], t[k], G);
+    bot_resid(V.g[k], b[k], t[k], t[k], G);      // t_k = r_k
+  }
+  bot_restrict(V.gc, t[nb - 1], bC, G);
+  const float* Ai = V.ainv + (int64_t)s * nc * nc;
+  for (int r = G.t; r < nc; r += G.n) {
+    float acc = 0.f;
+    for (int q = 0; q < nc; ++q) acc += Ai[(int64_t)r * nc + q] * bC[q];
+    xC[r] = acc;
+  }
+  G.sync();
+  // up: each level's post-smoothed x in place, level 0 straight to the output
+  for (int k = nb - 1; k >= 0; --k) {
+    const float* xc = k == nb - 1 ? xC : x[k + 1];
+    float* out = k == 0 ? V.xout + (int64_t)s * 2 * V.g[0].nodes() : x[k];
+    bot_post(L.U, V.g[k], w[k], c[k], tr[k], b[k], xc, x[k], t[k], out, G);
+  }
 }
 
 // d += x on refinement-active samples: ext1 = d (DStore<T>), a = x (T). With o0 set,
@@ -1891,6 +1985,31 @@ bool bottom_fits(const Geo& ga, const Geo& gb, const Geo& gc) {
 cudaError_t launch_bottom(const BottomList& L, SampleState S, int total_warps, cudaStream_t st) {
   if (total_warps <= 0) return cudaSuccess;
   k_bottom<<<blocks_for(total_warps, kWarpsPerBlock), kWarpsPerBlock * kWarp, 0, st>>>(L, S);
+  return cudaGetLastError();
+}
+
+int deep_floats(const Geo* g, int nb, const Geo& gc) {
+  auto up4 = [](int c) { return (c + 3) & ~3; };
+  int f = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int n = g[k].nodes(), ne = g[k].nx * g[k].ny;
+    f += 4 * up4(2 * n) + up4(n) + up4(4 * ne);
+  }
+  return f + 2 * up4(2 * gc.nodes());
+}
+
+bool deep_fits(const Geo* g, int nb, const Geo& gc) {
+  if (nb < 1 || nb > kDeepMax || 2 * gc.nodes() > kMaxCoarsestDofs) return false;
+  for (int k = 0; k < nb; ++k) {
+    const Geo& nxt = k + 1 < nb ? g[k + 1] : gc;
+    if (g[k].nx != 2 * nxt.nx || g[k].ny != 2 * nxt.ny) return false;
+  }
+  return deep_floats(g, nb, gc) <= kDeepFloats;
+}
+
+cudaError_t launch_bottom_deep(const DeepList& L, SampleState S, int total_blocks, int floats, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
+  k_bottom_deep<<<total_blocks, kDeepThreads, sizeof(float) * (size_t)floats, st>>>(L, S);
   return cudaGetLastError();
 }
 

@@ -137,6 +137,34 @@ struct BottomList {
 bool bottom_fits(const Geo& ga, const Geo& gb, const Geo& gc);
 cudaError_t launch_bottom(const BottomList& L, SampleState S, int total_warps, cudaStream_t st);
 
+// The deepest levels of a group's hierarchy with one thread block per sample (FP32):
+// nb smoothed levels (finest first, each twice the next) and the coarsest, with every
+// smoothed level's smoother and element data staged in shared memory; same operations
+// as PreR on those levels, the coarsest solve and Post back up; writes the finest
+// bottom level's correction (what Post or PostTop on the level above prolongates).
+constexpr int kDeepMax = 4;          // smoothed levels at most
+constexpr int kDeepThreads = 128;
+constexpr int kDeepFloats = 12288;   // shared memory per block at most (48 KB)
+struct DeepView {
+  Geo g[kDeepMax];
+  Geo gc;
+  int nb, nsamp, sbase, work_begin;
+  const float* rin;                  // residual of the level above g[0] [s][nodes][2]
+  const float* winv[kDeepMax];
+  const float* wc[kDeepMax];
+  const float* trig[kDeepMax];
+  const float* ainv;                 // coarsest inverses [s][n][n]
+  float* xout;                       // correction on g[0] [s][nodes][2]
+};
+struct DeepList {
+  int n;
+  Invariants U;
+  DeepView v[kMaxViews];
+};
+int deep_floats(const Geo* g, int nb, const Geo& gc);   // shared floats one block needs
+bool deep_fits(const Geo* g, int nb, const Geo& gc);
+cudaError_t launch_bottom_deep(const DeepList& L, SampleState S, int total_blocks, int floats, cudaStream_t st);
+
 // d += x (a = x, ext1 = d); with o0 set also r0 = r1 where the inner residual ended
 // in r1 (b = r1, o0 = r0). One thread per value.
 template <typename T>

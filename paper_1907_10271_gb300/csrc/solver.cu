@@ -180,10 +180,16 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   // the multigrid bottom of every group in one launch (FP32, hierarchies of 4 levels or
   // more whose three smallest meshes fit a warp's shared memory): the sweeps then stop
   // three levels above each group's coarsest
-  bool fused = std::is_same<T, float>::value && ctx.fused_bottom;
+  // or, one block per sample, the three smoothed levels above each group's coarsest and
+  // the coarsest solve (hierarchies of 5 levels or more, small enough bottoms)
+  const int bottom_mode = std::is_same<T, float>::value ? ctx.fused_bottom : 0;
+  bool deep = bottom_mode == 2;
+  for (auto& g : G)
+    deep = deep && g.nl >= 5 && deep_fits(&g.geo[g.nl - 4], 3, g.geo[g.nl - 1]);
+  bool fused = !deep && bottom_mode >= 1;
   for (auto& g : G)
     fused = fused && g.nl >= 4 && bottom_fits(g.geo[g.nl - 3], g.geo[g.nl - 2], g.geo[g.nl - 1]);
-  const int bottom_depth = fused ? 3 : 1;
+  const int bottom_depth = deep ? 4 : fused ? 3 : 1;
   const int max_iter = ctx.cfg.max_iter > 0 ? ctx.cfg.max_iter : 200;
   const int max_outer = ctx.cfg.max_outer > 0 ? ctx.cfg.max_outer : 8;
 
@@ -399,9 +405,39 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         MLMC_LAUNCH(kProfPre, "pre", launch_strip<T>(StripOp::PreR, Lsm, S, tw, st));
       }
     }
-    // every group's bottom: levels nl-3, nl-2 and the coarsest in one launch, or the
-    // coarsest mesh alone (its right-hand side gathered from the level above)
-    if (fused) {
+    // every group's bottom: levels nl-4 .. nl-2 and the coarsest in one launch (a block
+    // per sample), levels nl-3, nl-2 and the coarsest in one launch (a warp per
+    // sample), or the coarsest mesh alone (its right-hand side gathered from the level
+    // above)
+    if (deep) {
+      DeepList L;
+      std::memset(&L, 0, sizeof(L));
+      L.U = ctx.U;
+      int acc = 0, floats = 0;
+      for (auto& g : G) {
+        const int a = g.nl - 4;
+        DeepView v;
+        std::memset(&v, 0, sizeof(v));
+        v.nb = 3;
+        for (int k = 0; k < 3; ++k) {
+          v.g[k] = g.geo[a + k];
+          v.winv[k] = reinterpret_cast<const float*>(g.winvd[a + k]);
+          v.wc[k] = reinterpret_cast<const float*>(g.wc[a + k]);
+          v.trig[k] = reinterpret_cast<const float*>(g.trig[a + k]);
+        }
+        v.gc = g.geo[g.nl - 1];
+        v.nsamp = (int)g.grp->nsamp;
+        v.sbase = g.sbase;
+        v.work_begin = acc;
+        v.rin = reinterpret_cast<const float*>(g.r1[a - 1]);
+        v.ainv = reinterpret_cast<const float*>(g.ainv);
+        v.xout = reinterpret_cast<float*>(g.xl[a]);
+        acc += v.nsamp;
+        floats = std::max(floats, deep_floats(v.g, v.nb, v.gc));
+        L.v[L.n++] = v;
+      }
+      MLMC_LAUNCH(kProfCoarsest, "bottom_deep", launch_bottom_deep(L, S, acc, floats, st));
+    } else if (fused) {
       BottomList L;
       std::memset(&L, 0, sizeof(L));
       L.U = ctx.U;

@@ -336,7 +336,7 @@ def test_autotune_keeps_results_and_moments(B):
         t = B.mlmc_autotune(ctx, [0, 1, 2], [64, 16, 6], reps=1)
         assert t["max_rows"] in (32, 64) and t["min_rows"] in (4, 6, 8)
         assert t["target_waves"] in (0.75, 1.5, 3.0) and t["nested_min_nodes"] in (0, 1 << 22, 1 << 62)
-        assert t["fused_bottom"] in (0, 1)
+        assert t["fused_bottom"] in (0, 1, 2) and t["pack_samples"] in (0, 1)
         assert t["step_ms"] > 0
         assert B.mlmc_level_stats_get(ctx, 2) == before
         assert B.mlmc_get_tuning(ctx)["max_rows"] == t["max_rows"]
@@ -351,13 +351,13 @@ def test_autotune_keeps_results_and_moments(B):
 
 @pytest.mark.parametrize("nested_min_nodes", [0, 1 << 40])
 def test_fused_bottom_matches_separate_launches(B, nested_min_nodes):
-    """The multigrid bottom in one launch (levels nl-3, nl-2 and the coarsest per
-    sample in a warp) does the same operations as the separate PreR / coarsest / Post
-    launches: the solves agree to rounding, checked at the stated 1e-6, and take the
-    same PCG iterations."""
+    """The multigrid bottom in one launch (levels nl-4 .. nl-2 and the coarsest per
+    sample in a thread block, or nl-3, nl-2 and the coarsest per sample in a warp) does
+    the same operations as the separate PreR / coarsest / Post launches: the solves
+    agree to rounding, checked at the stated 1e-6."""
     w = STRIP_MIXED_5LEVEL
     out = {}
-    for fused in (1, 0):
+    for fused in (2, 1, 0):
         ctx = B.mlmc_create(B.config_from_workload(w))
         try:
             B.mlmc_set_tuning(ctx, 64, 6, 1.5, nested_min_nodes, fused)
@@ -366,6 +366,32 @@ def test_fused_bottom_matches_separate_launches(B, nested_min_nodes):
             B.mlmc_sample_levels(ctx, [0, 1, 2, 3], [0, 0, 0, 0], [8, 6, 4, 2], qf, qc, st)
             assert np.all(st == 0)
             out[fused] = (qf, qc)
+        finally:
+            B.mlmc_destroy(ctx)
+    for fused in (2, 1):
+        np.testing.assert_allclose(out[fused][0], out[0][0], rtol=1e-6)
+        np.testing.assert_allclose(out[fused][1], out[0][1], rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("nested_min_nodes", [0, 1 << 40])
+def test_packed_strips_match_one_sample_per_strip(B, nested_min_nodes):
+    """Strip kernels that tile the samples of a mesh side by side (a warp may hold the
+    end of one sample and the start of the next) give the solves of one sample per
+    strip: samples do not couple across the seam, and per-sample sums and the CG
+    steps taken by each sample's last warp stay per sample. 13 samples of every level
+    (an odd count, so that some warp strips straddle two samples on every mesh)."""
+    w = STRIP_MIXED_5LEVEL
+    out = {}
+    for pack in (1, 0):
+        ctx = B.mlmc_create(B.config_from_workload(w))
+        try:
+            B.mlmc_set_tuning(ctx, 64, 6, 1.5, nested_min_nodes, 2, pack)
+            n = 13
+            qf, qc = np.zeros(2 * 5 * n), np.zeros(2 * 5 * n)
+            st = np.ones(5 * n, dtype=np.int32)
+            B.mlmc_sample_levels(ctx, [0, 1, 2, 3, 4], [7] * 5, [n] * 5, qf, qc, st)
+            assert np.all(st == 0)
+            out[pack] = (qf, qc)
         finally:
             B.mlmc_destroy(ctx)
     np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-6)
