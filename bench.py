@@ -493,7 +493,7 @@ def run_serving(B, cfg_w, seconds=3.0, load=0.5):
     """The request loop on the selective-refinement workload: failure of the 5-level
     strip when the centroid fibre stress exceeds the 1/150 upper quantile of a seeded
     pilot (seed 1, 4096 level-2 samples); SELECTIVE requests of levels 0..4 in the
-    proportions of the MLMC level counts. Capacity from saturating bursts (median of three
+    proportions of the MLMC level counts. Capacity from saturating bursts (median of seven
     after a warm-up burst), then
     Poisson arrivals at `load` of it for `seconds`: completed requests/s (each one
     level sample Y_l = Q_l - Q_{l-1}), latency p50/p99, solves per request, and the
@@ -538,10 +538,11 @@ def run_serving(B, cfg_w, seconds=3.0, load=0.5):
 
     try:
         # capacity: bursts of requests submitted at once; one untimed warm-up burst, then
-        # the median of three (a single ~40 ms burst is sensitive to the host's load)
+        # the median of seven (a single ~30 ms burst is sensitive to the host's load:
+        # bursts of one run range over a factor of two)
         results = []
         caps = []
-        for b in range(4):
+        for b in range(8):
             burst = make(8192)
             t0 = time.perf_counter()
             B.mlmc_server_submit(srv, burst)
@@ -574,6 +575,24 @@ def run_serving(B, cfg_w, seconds=3.0, load=0.5):
         B.mlmc_server_destroy(srv)
     lat = np.array([r["latency_ms"] for r in stream])
     ok = [r for r in results + stream if r["status"] == 0]
+
+    def iteration_stats(rs):
+        first = [r["pcg_iterations"][0] for r in rs if r["pcg_iterations"]]
+        esc = [i for r in rs for i in r["pcg_iterations"][1:]]
+        return {"first_solve": round(float(np.mean(first)), 2) if first else None,
+                "escalation": round(float(np.mean(esc)), 2) if esc else None, "escalations": len(esc)}
+
+    # the same first burst of requests with every solve from the lifting: PCG iterations
+    # per escalation without the carried iterates
+    srv0 = B.mlmc_server_create(B.config_from_workload(cfg_w), workers=4, max_batch=4096, hbm_budget_bytes=100e9,
+                                threshold=threshold, sr_factor=2.0, eps_rel=1e-6, carry_iterates=False)
+    try:
+        first_burst = sorted([r for r in results if r["tag"] < 8192], key=lambda r: r["tag"])
+        B.mlmc_server_submit(srv0, [(1, r["level"], 0, r["sample_id"], r["tag"]) for r in first_burst])
+        B.mlmc_server_drain(srv0, 600e3)
+        no_carry = [r for r in drain_all_of(B, srv0) if r["status"] == 0]
+    finally:
+        B.mlmc_server_destroy(srv0)
     est_ml, _, _ = B.mlmc_failure_estimate(ok, threshold, k=1, two_level=False)
     est_2l, _, _ = B.mlmc_failure_estimate(ok, threshold, k=1, two_level=True)
     return {"workload": "selective refinement, P(stress > 1/150 upper quantile of a seed-1 pilot), levels 0-4 "
@@ -590,8 +609,23 @@ def run_serving(B, cfg_w, seconds=3.0, load=0.5):
             "stopped_early": round(sum(r["stop_level"] < r["level"] for r in ok) / max(1, len(ok)), 4),
             "failure_probability": {"multilevel": est_ml, "two_level": est_2l,
                                     "estimator": "biased (x + k)/(N + k), k = 1, trinomial moments"},
+            "pcg_iterations_per_solve": {"carried_iterates": iteration_stats(ok),
+                                         "from_lifting_first_burst": iteration_stats(no_carry),
+                                         "carried_first_burst": iteration_stats(
+                                             [r for r in ok if r["tag"] < 8192]),
+                                         "note": "escalation = a selective sample's solve on mesh j >= 1; with "
+                                                 "carried iterates it starts from its own mesh j-1 solution"},
             "failed_requests": len(results) + len(stream) - len(ok),
             "batches": counters["batches"], "peak_admitted_gb": round(counters["peak_bytes"] / 1e9, 2)}
+
+
+def drain_all_of(B, srv):
+    res = []
+    while True:
+        got = B.mlmc_server_poll(srv, 65536)
+        if not got:
+            return res
+        res += got
 
 
 def run_small_case():

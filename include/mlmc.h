@@ -319,6 +319,11 @@ mlmc_status mlmc_launch_count(mlmc_ctx* ctx, int64_t* launches);
  * lambda_min(J, l-1), J the stopping mesh, and its failure indicators
  * Q_l = 1(lambda_l > lambda*), Q_{l-1} (0 for l = 0).
  *
+ * With carry_iterates, a SELECTIVE sample's solve on mesh j + 1 starts from its own
+ * mesh-j solution (kept on the device between its solves), so each escalation needs
+ * fewer PCG iterations; every solve still ends at ||f - K d|| <= rtol ||f|| on its
+ * mesh.
+ *
  * Every result is that of the sample alone: no arithmetic mixes samples, so the
  * batch a request lands in does not change it beyond floating-point summation
  * order. Calls on one server are thread-safe. */
@@ -348,6 +353,7 @@ typedef struct {
   int32_t q_fine, q_coarse;            /* SELECTIVE: failure indicators */
   int32_t solves;       /* meshes solved for this request */
   double latency_ms;    /* from submission to completion */
+  int32_t pcg_iterations[MLMC_SR_MAX_LEVELS];   /* PCG iterations of each solve, in order */
 } mlmc_result;
 
 typedef struct {
@@ -357,6 +363,11 @@ typedef struct {
   double threshold;           /* lambda* of SELECTIVE requests (quantity 1) */
   double sr_factor;           /* solver-error widening of the stopping test (e.g. 2) */
   double eps_rel;             /* relative error bound of a solved lambda (e.g. 1e-6) */
+  int32_t carry_iterates;     /* 1: a SELECTIVE sample keeps its solution on the device between
+                                 its solves and starts each further mesh from it (bilinear
+                                 prolongation, as nested iteration), in a pool of iterate slots
+                                 of 1/8 of the budget (a sample that finds no free slot starts
+                                 from the lifting); 0: every solve starts from the lifting */
 } mlmc_server_config;
 
 /* Failure-probability estimate from completed SELECTIVE results (host arithmetic

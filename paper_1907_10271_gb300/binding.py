@@ -73,19 +73,22 @@ class mlmc_result(ctypes.Structure):
                 ("q", ctypes.c_double * 2), ("stop_level", ctypes.c_int32),
                 ("lambda_", ctypes.c_double * SR_MAX_LEVELS), ("lambda_fine", ctypes.c_double),
                 ("lambda_coarse", ctypes.c_double), ("q_fine", ctypes.c_int32), ("q_coarse", ctypes.c_int32),
-                ("solves", ctypes.c_int32), ("latency_ms", ctypes.c_double)]
+                ("solves", ctypes.c_int32), ("latency_ms", ctypes.c_double),
+                ("pcg_iterations", ctypes.c_int32 * SR_MAX_LEVELS)]
 
     def as_dict(self):
         return dict(tag=self.tag, kind=self.kind, level=self.level, mesh_level=self.mesh_level,
                     sample_id=self.sample_id, status=self.status, q=list(self.q), stop_level=self.stop_level,
                     lambdas=list(self.lambda_[:self.stop_level + 1]), lambda_fine=self.lambda_fine,
                     lambda_coarse=self.lambda_coarse, q_fine=self.q_fine, q_coarse=self.q_coarse,
-                    solves=self.solves, latency_ms=self.latency_ms)
+                    solves=self.solves, latency_ms=self.latency_ms,
+                    pcg_iterations=list(self.pcg_iterations[:min(self.solves, SR_MAX_LEVELS)]))
 
 
 class mlmc_server_config(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int64), ("hbm_budget_bytes", ctypes.c_double),
-                ("threshold", ctypes.c_double), ("sr_factor", ctypes.c_double), ("eps_rel", ctypes.c_double)]
+                ("threshold", ctypes.c_double), ("sr_factor", ctypes.c_double), ("eps_rel", ctypes.c_double),
+                ("carry_iterates", ctypes.c_int32)]
 
 
 _lib = None
@@ -384,10 +387,10 @@ def mlmc_profile_report(ctx):
 # ---------------------------------------------------------------- serving
 
 def mlmc_server_create(cfg, workers=2, max_batch=4096, hbm_budget_bytes=8e9, threshold=0.0, sr_factor=2.0,
-                       eps_rel=1e-6):
+                       eps_rel=1e-6, carry_iterates=True):
     L = lib()
     sc = mlmc_server_config(workers, max_batch, float(hbm_budget_bytes), float(threshold), float(sr_factor),
-                            float(eps_rel))
+                            float(eps_rel), 1 if carry_iterates else 0)
     srv = ctypes.c_void_p()
     st = L.mlmc_server_create(ctypes.byref(cfg), ctypes.byref(sc), ctypes.byref(srv))
     if st != 0:

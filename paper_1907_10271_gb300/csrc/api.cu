@@ -67,6 +67,19 @@ cudaError_t convert(const float* a, double* b, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// dst[i][0 .. per) = src[i][0 .. per) for the items of a pointer table (null: skipped);
+// one thread per value, item-major.
+__global__ void k_copy_iterates(const double* const* src, int64_t src_stride, double* const* dst,
+                                int64_t dst_stride, const double* src_base, double* dst_base, int64_t per, int n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * n) return;
+  const int i = (int)(t / per);
+  const int64_t j = t - (int64_t)i * per;
+  const double* s = src ? src[i] : src_base + (int64_t)i * src_stride;
+  double* d = dst ? dst[i] : dst_base + (int64_t)i * dst_stride;
+  if (s && d) d[j] = s[j];
+}
+
 __global__ void k_combine_status(const int* a, const int* b, int* out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a[i] != 0 ? a[i] : (b ? b[i] : 0);
@@ -416,11 +429,232 @@ mlmc_status reserve_workspace(mlmc_ctx* h, size_t solve_bytes, size_t batch_byte
 
 void set_graph_replay(mlmc_ctx* h, bool on) { h->c.graphs = on; }
 
+int64_t iterate_values(const mlmc_config& cfg, int m) {
+  return 2 * (((int64_t)cfg.nx0 << m) + 1) * (((int64_t)cfg.ny0 << m) + 1);
+}
+
+mlmc_status solve_batch_carry(mlmc_ctx* h, const mlmc_item* items, int64_t n, double* q, int32_t* status,
+                              const double* const* guess, double* const* out, int32_t* iters) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  Context& c = h->c;
+  if (n < 0 || (n > 0 && !items)) return c.fail(MLMC_ERR_INVALID_ARG, "bad item array");
+  if (n == 0) return MLMC_OK;
+  std::vector<mlmc_item> it(n);
+  if (is_device_ptr(items)) {
+    cudaMemcpy(it.data(), items, sizeof(mlmc_item) * n, cudaMemcpyDeviceToHost);
+  } else {
+    std::memcpy(it.data(), items, sizeof(mlmc_item) * n);
+  }
+  for (int64_t k = 0; k < n; ++k) {
+    const auto& x = it[k];
+    if (x.level < 0 || x.level >= c.cfg.levels || x.mesh_level < 0 || x.mesh_level >= c.cfg.levels)
+      return c.fail(MLMC_ERR_INVALID_ARG, "item level out of range");
+    if (guess && guess[k] && x.mesh_level == 0)
+      return c.fail(MLMC_ERR_INVALID_ARG, "an initial iterate for a mesh-0 item (no coarser mesh)");
+  }
+  auto has_guess = [&](int64_t k) { return guess && guess[k] ? 1 : 0; };
+  // groups: items of one mesh, those with initial iterates apart, stable order
+  std::vector<int64_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    if (it[a].mesh_level != it[b].mesh_level) return it[a].mesh_level < it[b].mesh_level;
+    return has_guess(a) < has_guess(b);
+  });
+  struct Run {
+    int64_t k0, k1;
+    int mesh;
+    bool guessed, outs;
+  };
+  std::vector<Run> runs;
+  for (int64_t k = 0; k < n;) {
+    const int m = it[order[k]].mesh_level, gflag = has_guess(order[k]);
+    int64_t k1 = k;
+    bool outs = false;
+    while (k1 < n && it[order[k1]].mesh_level == m && has_guess(order[k1]) == gflag) {
+      outs = outs || (out && out[order[k1]]);
+      ++k1;
+    }
+    runs.push_back(Run{k, k1, m, gflag != 0, outs});
+    k = k1;
+  }
+  std::vector<int> lv(n);
+  std::vector<uint64_t> ids(n);
+  for (int64_t k = 0; k < n; ++k) {
+    lv[k] = it[order[k]].level;
+    ids[k] = it[order[k]].sample_id;
+  }
+  const bool mixed = c.mixed();
+  const size_t tb = mixed ? 4 : 8;
+  int64_t nel_total = 0, carry_values = 0;
+  for (int64_t k = 0; k < n; ++k) nel_total += c.mesh(it[order[k]].mesh_level).n_el();
+  for (const Run& r : runs) {
+    if (r.guessed) carry_values += (r.k1 - r.k0) * iterate_values(c.cfg, r.mesh - 1);
+    if (r.outs) carry_values += (r.k1 - r.k0) * iterate_values(c.cfg, r.mesh);
+  }
+  const bool tc = c.kl_on_tensor_cores();
+  const int kp = c.kl_kpad();
+  mlmc::Sizer sz;
+  sz.add<double>(n * c.cfg.kl_terms);
+  sz.add<float>(n * c.cfg.kl_terms);
+  sz.add<float>(tc ? 2 * n * kp : 1);
+  sz.add<int>(2);
+  sz.add<int>(n);
+  sz.add<uint64_t>(n);
+  sz.add<char>(2 * nel_total * tb);
+  sz.add<double>(2 * n);
+  sz.add<int>(n);
+  sz.add<int>(n);
+  sz.add<double>(carry_values);
+  sz.add<const double*>(2 * n);
+  cudaError_t e = c.batch_arena.reserve(sz.used + 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return c.fail(MLMC_ERR_OOM, "batch buffers");
+  }
+  c.batch_arena.reset();
+  double* xi = c.batch_arena.carve<double>(n * c.cfg.kl_terms);
+  float* xi32 = c.batch_arena.carve<float>(n * c.cfg.kl_terms);
+  float* xi_tc = c.batch_arena.carve<float>(tc ? 2 * n * kp : 1);
+  int* fail = c.batch_arena.carve<int>(2);
+  int* lv_dev = c.batch_arena.carve<int>(n);
+  uint64_t* id_dev = c.batch_arena.carve<uint64_t>(n);
+  char* theta = c.batch_arena.carve<char>(2 * nel_total * tb);
+  double* qd = c.batch_arena.carve<double>(2 * n);
+  int* sd = c.batch_arena.carve<int>(n);
+  int* itd = c.batch_arena.carve<int>(n);
+  double* carry = c.batch_arena.carve<double>(carry_values);
+  const double** ptr_dev = c.batch_arena.carve<const double*>(2 * n);   // [guess (sorted) | out (sorted)]
+  cudaStream_t st = c.stream;
+  if ((e = cudaMemcpyAsync(lv_dev, lv.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(id_dev, ids.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(fail, 0, 2 * sizeof(int), st)) != cudaSuccess)
+    return c.cuda_fail(e, "items");
+  // initial iterates into one buffer per guessed group (a copy kernel over a pointer table)
+  std::vector<double*> run_guess(runs.size(), nullptr), run_out(runs.size(), nullptr);
+  if (carry_values > 0) {
+    std::vector<const double*> ptrs(2 * n, nullptr);
+    for (int64_t k = 0; k < n; ++k) {
+      ptrs[k] = guess ? guess[order[k]] : nullptr;
+      ptrs[n + k] = out ? out[order[k]] : nullptr;
+    }
+    if ((e = cudaMemcpyAsync(ptr_dev, ptrs.data(), sizeof(const double*) * 2 * n, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return c.cuda_fail(e, "iterate table");
+    double* p = carry;
+    for (size_t r = 0; r < runs.size(); ++r) {
+      const Run& R = runs[r];
+      const int nb = (int)(R.k1 - R.k0);
+      if (R.guessed) {
+        const int64_t per = iterate_values(c.cfg, R.mesh - 1);
+        run_guess[r] = p;
+        c.timer.begin(mlmc::kProfOther, st, "carry_in");
+        k_copy_iterates<<<(unsigned)((per * nb + 255) / 256), 256, 0, st>>>(ptr_dev + R.k0, 0, nullptr, per, nullptr,
+                                                                          p, per, nb);
+        c.timer.end(st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return c.cuda_fail(e, "carry_in");
+        p += per * nb;
+      }
+      if (R.outs) {
+        run_out[r] = p;
+        p += iterate_values(c.cfg, R.mesh) * nb;
+      }
+    }
+  }
+  if ((e = mlmc::launch_kl_coefficients(c.cfg.seed, 0, 0, lv_dev, id_dev, n, c.cfg.kl_terms, xi,
+                                        mixed && !tc ? xi32 : nullptr, fail, st)) != cudaSuccess)
+    return c.cuda_fail(e, "kl_coefficients");
+  if (tc && (e = mlmc::launch_tf32_split(xi, n, c.cfg.kl_terms, kp, xi_tc, xi_tc + n * kp, st)) != cudaSuccess)
+    return c.cuda_fail(e, "kl_split");
+  auto run = [&](auto tag) -> mlmc_status {
+    using T = decltype(tag);
+    std::vector<mlmc::SolveGroup<T>> groups;
+    const T* xiT = mixed ? (const T*)(const void*)xi32 : (const T*)(const void*)xi;
+    int64_t eoff = 0;
+    for (size_t r = 0; r < runs.size(); ++r) {
+      const Run& R = runs[r];
+      const int m = R.mesh;
+      const int64_t k = R.k0, nb = R.k1 - R.k0;
+      const int64_t nel = c.mesh(m).n_el();
+      T* th = reinterpret_cast<T*>(theta) + eoff;
+      const T* B = mixed ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
+      cudaError_t err;
+      if (tc) {
+        mlmc::KlTcOperand xop;
+        err = mlmc::make_kl_tc_operand(xi_tc + k * kp, xi_tc + (n + k) * kp, nb, kp, mlmc::kKlTcSamples, &xop);
+        if (err == cudaSuccess)
+          err = mlmc::launch_kl_synthesis_tc(c.basis_tc_op[m], xop, (int)nel, nb, (float*)(void*)th, true, fail + 1,
+                                             st);
+      } else {
+        err = mlmc::launch_kl_synthesis<T>(xiT + k * c.cfg.kl_terms, B, nb, (int)nel, c.cfg.kl_terms, th, true, st);
+      }
+      if (err != cudaSuccess) return c.cuda_fail(err, "kl_synthesis");
+      mlmc::SolveGroup<T> g{m, nb, th, qd + 2 * k, sd + k, itd + k};
+      g.d_guess = run_guess[r];
+      g.d_out = run_out[r];
+      groups.push_back(g);
+      eoff += 2 * nb * nel;
+    }
+    int h_err = 0;
+    cudaError_t err;
+    if ((err = cudaMemcpyAsync(&h_err, fail + 1, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (err = cudaStreamSynchronize(st)) != cudaSuccess)
+      return c.cuda_fail(err, "kl_synthesis");
+    if (h_err) return c.fail(MLMC_ERR_TIMEOUT, "tensor-core KL synthesis: a wait expired");
+    // at most kMaxViews groups per lock-stepped solve
+    for (size_t g0 = 0; g0 < groups.size(); g0 += kMaxViews) {
+      std::vector<mlmc::SolveGroup<T>> part(groups.begin() + g0,
+                                            groups.begin() + std::min(groups.size(), g0 + (size_t)kMaxViews));
+      const mlmc_status ps = mlmc::solve_groups<T>(c, part);
+      if (ps != MLMC_OK) return ps;
+    }
+    return MLMC_OK;
+  };
+  mlmc_status s = mixed ? run(float()) : run(double());
+  if (s != MLMC_OK) return s;
+  // final iterates to the items' own storage
+  for (size_t r = 0; r < runs.size(); ++r) {
+    const Run& R = runs[r];
+    if (!R.outs) continue;
+    const int64_t per = iterate_values(c.cfg, R.mesh);
+    const int nb = (int)(R.k1 - R.k0);
+    c.timer.begin(mlmc::kProfOther, st, "carry_out");
+    k_copy_iterates<<<(unsigned)((per * nb + 255) / 256), 256, 0, st>>>(nullptr, per, const_cast<double* const*>(
+                                                                             ptr_dev + n + R.k0), 0, run_out[r],
+                                                                       nullptr, per, nb);
+    c.timer.end(st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return c.cuda_fail(e, "carry_out");
+  }
+  // scatter back to item order
+  std::vector<double> qh(2 * n), qo(2 * n);
+  std::vector<int> sh(n), so(n), ih(n);
+  if ((e = cudaMemcpyAsync(qh.data(), qd, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(sh.data(), sd, sizeof(int) * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(ih.data(), itd, sizeof(int) * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return c.cuda_fail(e, "copy out");
+  for (int64_t k = 0; k < n; ++k) {
+    qo[2 * order[k]] = qh[2 * k];
+    qo[2 * order[k] + 1] = qh[2 * k + 1];
+    so[order[k]] = sh[k];
+    if (iters) iters[order[k]] = ih[k];
+  }
+  if (q) {
+    if (is_device_ptr(q)) e = cudaMemcpy(q, qo.data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice);
+    else std::memcpy(q, qo.data(), sizeof(double) * 2 * n);
+  }
+  if (status) {
+    if (is_device_ptr(status)) e = cudaMemcpy(status, so.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+    else std::memcpy(status, so.data(), sizeof(int) * n);
+  }
+  return e == cudaSuccess ? MLMC_OK : c.cuda_fail(e, "copy out");
+}
+
 double solve_bytes_per_sample(const mlmc_config& cfg, int mesh) {
   const double tb = cfg.precision == MLMC_PREC_MIXED ? 4.0 : 8.0;
   const double nx = (double)((int64_t)cfg.nx0 << mesh), ny = (double)((int64_t)cfg.ny0 << mesh);
   const double dofs = 2.0 * (nx + 1.0) * (ny + 1.0);
-  return dofs * (14.0 * tb + 16.0) * 1.4 + 2.0 * nx * ny * tb + 96.0 * cfg.kl_terms + 512.0;
+  // plus the carried iterates of a served escalation (its previous mesh's and its own)
+  return dofs * (14.0 * tb + 16.0) * 1.4 + 2.0 * nx * ny * tb + 96.0 * cfg.kl_terms + 512.0 + 1.25 * 8.0 * dofs + 16.0;
 }
 
 }  // namespace mlmc
@@ -803,131 +1037,7 @@ mlmc_status mlmc_reset_stats(mlmc_ctx* h) {
 }
 
 mlmc_status mlmc_solve_batch(mlmc_ctx* h, const mlmc_item* items, int64_t n, double* q, int32_t* status) {
-  if (!h) return MLMC_ERR_INVALID_ARG;
-  Context& c = h->c;
-  if (n < 0 || (n > 0 && !items)) return c.fail(MLMC_ERR_INVALID_ARG, "bad item array");
-  if (n == 0) return MLMC_OK;
-  std::vector<mlmc_item> it(n);
-  if (is_device_ptr(items)) {
-    cudaMemcpy(it.data(), items, sizeof(mlmc_item) * n, cudaMemcpyDeviceToHost);
-  } else {
-    std::memcpy(it.data(), items, sizeof(mlmc_item) * n);
-  }
-  for (const auto& x : it)
-    if (x.level < 0 || x.level >= c.cfg.levels || x.mesh_level < 0 || x.mesh_level >= c.cfg.levels)
-      return c.fail(MLMC_ERR_INVALID_ARG, "item level out of range");
-  // group by mesh, stable order
-  std::vector<int64_t> order(n);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return it[a].mesh_level < it[b].mesh_level; });
-  std::vector<int> lv(n);
-  std::vector<uint64_t> ids(n);
-  for (int64_t k = 0; k < n; ++k) {
-    lv[k] = it[order[k]].level;
-    ids[k] = it[order[k]].sample_id;
-  }
-  const bool mixed = c.mixed();
-  const size_t tb = mixed ? 4 : 8;
-  int64_t nel_total = 0;
-  for (int64_t k = 0; k < n; ++k) nel_total += c.mesh(it[order[k]].mesh_level).n_el();
-  const bool tc = c.kl_on_tensor_cores();
-  const int kp = c.kl_kpad();
-  mlmc::Sizer sz;
-  sz.add<double>(n * c.cfg.kl_terms);
-  sz.add<float>(n * c.cfg.kl_terms);
-  sz.add<float>(tc ? 2 * n * kp : 1);
-  sz.add<int>(2);
-  sz.add<int>(n);
-  sz.add<uint64_t>(n);
-  sz.add<char>(2 * nel_total * tb);
-  sz.add<double>(2 * n);
-  sz.add<int>(n);
-  sz.add<int>(n);
-  cudaError_t e = c.batch_arena.reserve(sz.used + 256);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return c.fail(MLMC_ERR_OOM, "batch buffers");
-  }
-  c.batch_arena.reset();
-  double* xi = c.batch_arena.carve<double>(n * c.cfg.kl_terms);
-  float* xi32 = c.batch_arena.carve<float>(n * c.cfg.kl_terms);
-  float* xi_tc = c.batch_arena.carve<float>(tc ? 2 * n * kp : 1);
-  int* fail = c.batch_arena.carve<int>(2);
-  int* lv_dev = c.batch_arena.carve<int>(n);
-  uint64_t* id_dev = c.batch_arena.carve<uint64_t>(n);
-  char* theta = c.batch_arena.carve<char>(2 * nel_total * tb);
-  double* qd = c.batch_arena.carve<double>(2 * n);
-  int* sd = c.batch_arena.carve<int>(n);
-  int* itd = c.batch_arena.carve<int>(n);
-  cudaStream_t st = c.stream;
-  if ((e = cudaMemcpyAsync(lv_dev, lv.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(id_dev, ids.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(fail, 0, 2 * sizeof(int), st)) != cudaSuccess)
-    return c.cuda_fail(e, "items");
-  if ((e = mlmc::launch_kl_coefficients(c.cfg.seed, 0, 0, lv_dev, id_dev, n, c.cfg.kl_terms, xi,
-                                        mixed && !tc ? xi32 : nullptr, fail, st)) != cudaSuccess)
-    return c.cuda_fail(e, "kl_coefficients");
-  if (tc && (e = mlmc::launch_tf32_split(xi, n, c.cfg.kl_terms, kp, xi_tc, xi_tc + n * kp, st)) != cudaSuccess)
-    return c.cuda_fail(e, "kl_split");
-  auto run = [&](auto tag) -> mlmc_status {
-    using T = decltype(tag);
-    std::vector<mlmc::SolveGroup<T>> groups;
-    const T* xiT = mixed ? (const T*)(const void*)xi32 : (const T*)(const void*)xi;
-    int64_t k = 0, eoff = 0;
-    while (k < n) {
-      const int m = it[order[k]].mesh_level;
-      int64_t k1 = k;
-      while (k1 < n && it[order[k1]].mesh_level == m) ++k1;
-      const int64_t nb = k1 - k;
-      const int64_t nel = c.mesh(m).n_el();
-      T* th = reinterpret_cast<T*>(theta) + eoff;
-      const T* B = mixed ? (const T*)(const void*)c.basis32[m] : (const T*)(const void*)c.basis64[m];
-      cudaError_t err;
-      if (tc) {
-        mlmc::KlTcOperand xop;
-        err = mlmc::make_kl_tc_operand(xi_tc + k * kp, xi_tc + (n + k) * kp, nb, kp, mlmc::kKlTcSamples, &xop);
-        if (err == cudaSuccess)
-          err = mlmc::launch_kl_synthesis_tc(c.basis_tc_op[m], xop, (int)nel, nb, (float*)(void*)th, true, fail + 1,
-                                             st);
-      } else {
-        err = mlmc::launch_kl_synthesis<T>(xiT + k * c.cfg.kl_terms, B, nb, (int)nel, c.cfg.kl_terms, th, true, st);
-      }
-      if (err != cudaSuccess) return c.cuda_fail(err, "kl_synthesis");
-      groups.push_back({m, nb, th, qd + 2 * k, sd + k, itd + k});
-      eoff += 2 * nb * nel;
-      k = k1;
-    }
-    int h_err = 0;
-    cudaError_t err;
-    if ((err = cudaMemcpyAsync(&h_err, fail + 1, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (err = cudaStreamSynchronize(st)) != cudaSuccess)
-      return c.cuda_fail(err, "kl_synthesis");
-    if (h_err) return c.fail(MLMC_ERR_TIMEOUT, "tensor-core KL synthesis: a wait expired");
-    return mlmc::solve_groups<T>(c, groups);
-  };
-  mlmc_status s = mixed ? run(float()) : run(double());
-  if (s != MLMC_OK) return s;
-  // scatter back to item order
-  std::vector<double> qh(2 * n), qo(2 * n);
-  std::vector<int> sh(n), so(n);
-  if ((e = cudaMemcpyAsync(qh.data(), qd, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(sh.data(), sd, sizeof(int) * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(st)) != cudaSuccess)
-    return c.cuda_fail(e, "copy out");
-  for (int64_t k = 0; k < n; ++k) {
-    qo[2 * order[k]] = qh[2 * k];
-    qo[2 * order[k] + 1] = qh[2 * k + 1];
-    so[order[k]] = sh[k];
-  }
-  if (q) {
-    if (is_device_ptr(q)) e = cudaMemcpy(q, qo.data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice);
-    else std::memcpy(q, qo.data(), sizeof(double) * 2 * n);
-  }
-  if (status) {
-    if (is_device_ptr(status)) e = cudaMemcpy(status, so.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
-    else std::memcpy(status, so.data(), sizeof(int) * n);
-  }
-  return e == cudaSuccess ? MLMC_OK : c.cuda_fail(e, "copy out");
+  return mlmc::solve_batch_carry(h, items, n, q, status, nullptr, nullptr, nullptr);
 }
 
 mlmc_status mlmc_estimate(mlmc_ctx* h, double e, double theta, int64_t n_star, int32_t max_level, int32_t qoi,

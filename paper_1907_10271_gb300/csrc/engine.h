@@ -71,6 +71,17 @@ mlmc_status reserve_workspace(mlmc_ctx* h, size_t solve_bytes, size_t batch_byte
 // of a fixed batch; a request loop whose every batch differs turns it off.
 void set_graph_replay(mlmc_ctx* h, bool on);
 
+// mlmc_solve_batch with per-item starting iterates: guess[k] (device: item k's final
+// iterate on mesh mesh_level - 1, in the refinement iterate's storage layout, 2 values
+// per node; null: the item starts from the lifting) and out[k] (device: where item k's
+// final iterate on its mesh is stored, or null). guess and out may be null as a whole.
+// iters (host, nullable): each item's PCG iterations.
+mlmc_status solve_batch_carry(mlmc_ctx* h, const mlmc_item* items, int64_t n, double* q, int32_t* status,
+                              const double* const* guess, double* const* out, int32_t* iters);
+
+// Values of a refinement iterate on mesh m (2 per node; 8 bytes each).
+int64_t iterate_values(const mlmc_config& cfg, int m);
+
 // Checks a strip configuration: the reason it is rejected, or "" when it is valid.
 std::string validate(const mlmc_config& cfg);
 

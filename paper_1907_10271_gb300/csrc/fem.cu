@@ -1857,7 +1857,7 @@ __global__ void k_react_energy(const __grid_constant__ ViewList<T> L, SampleStat
   if (lane == 0) atomicAdd(&S.qoi[2 * t], -sum * inv_shortening);
 }
 
-__global__ void k_inner_end(SampleState S, int total, int recursive) {
+__global__ void k_inner_end(SampleState S, int total) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total || !S.outer_active[t]) return;
   if (S.active[t]) {   // iteration cap reached
@@ -1866,7 +1866,7 @@ __global__ void k_inner_end(SampleState S, int total, int recursive) {
     S.outer_active[t] = 0;
     return;
   }
-  if (recursive) S.rr64[t] = S.red_rr[t];
+  if (!S.exact[t]) S.rr64[t] = S.red_rr[t];
 }
 
 __global__ void k_outer_init(SampleState S, int total) {
@@ -2058,8 +2058,8 @@ cudaError_t launch_react_delta(const ViewList<T>& L, SampleState S, int total_th
   return cudaGetLastError();
 }
 
-cudaError_t launch_inner_end(SampleState S, int total, int recursive, cudaStream_t st) {
-  k_inner_end<<<blocks_for(total, 256), 256, 0, st>>>(S, total, recursive);
+cudaError_t launch_inner_end(SampleState S, int total, cudaStream_t st) {
+  k_inner_end<<<blocks_for(total, 256), 256, 0, st>>>(S, total);
   return cudaGetLastError();
 }
 

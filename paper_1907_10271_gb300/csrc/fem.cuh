@@ -75,6 +75,7 @@ struct SampleState {
   int* status;        // 0 ok, MLMC_ERR_NOT_CONVERGED
   int* count;         // [batch] active samples after each iteration of the current batch
   int* rpar;          // buffer (0/1) holding the latest inner residual
+  int* exact;         // 1: the next refinement residual is formed from d (not the inner CG's)
   unsigned* arrive;   // warps of the running launch that added their share of a sample's
                       // reduction; zero between launches (see last_tile in fem.cu)
   unsigned long long* units;   // [kProfOps] nodes processed per operation (null: not counted)
@@ -190,9 +191,9 @@ template <typename T>
 cudaError_t launch_react_delta(const ViewList<T>& L, SampleState S, int total_threads, cudaStream_t st);
 
 // After an inner solve: samples still running hit the iteration cap (not converged);
-// for the others, when `recursive`, ||r||^2 of the new refinement residual is the
-// PCG's last reduced ||r||^2.
-cudaError_t launch_inner_end(SampleState S, int total, int recursive, cudaStream_t st);
+// for the others whose next refinement residual is not formed exactly (S.exact),
+// ||r||^2 of the new refinement residual is the PCG's last reduced ||r||^2.
+cudaError_t launch_inner_end(SampleState S, int total, cudaStream_t st);
 
 cudaError_t launch_outer_init(SampleState S, int total, cudaStream_t st);
 cudaError_t launch_outer_check(SampleState S, int total, double rtol, double floor_tol, int* outer_count,

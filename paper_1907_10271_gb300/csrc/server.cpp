@@ -8,7 +8,10 @@
 // as one mlmc_solve_batch, and feeds the results back: SOLVE requests complete,
 // SELECTIVE requests either stop (the stopping test of Eq. testFailure with the
 // sample bias estimate of Eq. sampleBias) or re-enter the queue on the next mesh.
-// Workspaces are reserved to the share up front, so serving allocates nothing.
+// Workspaces are reserved to the share up front, so serving allocates nothing. With
+// carry_iterates, a SELECTIVE sample that may escalate takes a slot of a per-mesh
+// pool (allocated at creation) for its final iterate on the mesh it is solving; its
+// next mesh starts from that iterate (nested iteration) and gives the slot back.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -32,6 +35,32 @@ struct Pending {
   int mesh = 0;   // SELECTIVE: next mesh to solve
   int solves = 0;
   double lambda[MLMC_SR_MAX_LEVELS] = {0};
+  int iters[MLMC_SR_MAX_LEVELS] = {0};
+  int carry = -1;   // pool slot on mesh - 1 holding the previous solve's iterate (or -1)
+  int out = -1;     // pool slot on mesh receiving this solve's iterate (or -1)
+};
+
+// Fixed-size slots of device memory, one class per mesh, each one refinement iterate.
+struct IteratePool {
+  std::vector<double*> base;             // per mesh
+  std::vector<int64_t> values;           // per mesh: doubles per slot
+  std::vector<std::vector<int>> free;    // per mesh
+  bool empty() const { return base.empty(); }
+  double* at(int m, int slot) const { return base[m] + (int64_t)slot * values[m]; }
+  int take(int m) {
+    if (m >= (int)free.size() || free[m].empty()) return -1;
+    const int k = free[m].back();
+    free[m].pop_back();
+    return k;
+  }
+  void give(int m, int slot) {
+    if (slot >= 0) free[m].push_back(slot);
+  }
+  void release() {
+    for (double* p : base)
+      if (p) cudaFree(p);
+    base.clear();
+  }
 };
 
 }  // namespace
@@ -51,6 +80,7 @@ struct mlmc_server {
   int64_t batches = 0, solves = 0;
   double in_flight = 0.0, peak = 0.0, share = 0.0;
   int device = 0;
+  IteratePool pool;      // carried iterates (guarded by mu)
   char err[512] = {0};   // last failure message (stable storage for mlmc_server_last_error)
 
   void record_error(const std::string& m) {
@@ -69,6 +99,7 @@ struct mlmc_server {
     r.sample_id = p.req.sample_id;
     r.status = status;
     r.solves = p.solves;
+    for (int j = 0; j < std::min(p.solves, MLMC_SR_MAX_LEVELS); ++j) r.pcg_iterations[j] = p.iters[j];
     if (q) {
       r.q[0] = q[0];
       r.q[1] = q[1];
@@ -106,7 +137,9 @@ struct mlmc_server {
     std::vector<Pending> batch;
     std::vector<mlmc_item> items;
     std::vector<double> q;
-    std::vector<int32_t> st;
+    std::vector<int32_t> st, its;
+    std::vector<const double*> guess;
+    std::vector<double*> outp;
     for (;;) {
       double bytes = 0.0;
       batch.clear();
@@ -119,6 +152,7 @@ struct mlmc_server {
           if (batch.empty() && b > share) {   // can never fit
             Pending p = queue.front();
             queue.pop_front();
+            if (p.carry >= 0) pool.give(p.mesh - 1, p.carry);
             complete(p, MLMC_ERR_OOM, nullptr, 0);
             cv_done.notify_all();
             continue;
@@ -127,20 +161,30 @@ struct mlmc_server {
           bytes += b;
           batch.push_back(queue.front());
           queue.pop_front();
+          // a sample that may escalate keeps this solve's iterate, if a slot is free
+          Pending& p = batch.back();
+          if (!pool.empty() && p.req.kind == MLMC_REQ_SELECTIVE && p.mesh < p.req.level) p.out = pool.take(p.mesh);
         }
         if (batch.empty()) continue;
         in_flight += bytes;
         peak = std::max(peak, in_flight);
       }
       items.resize(batch.size());
+      guess.assign(batch.size(), nullptr);
+      outp.assign(batch.size(), nullptr);
       for (size_t k = 0; k < batch.size(); ++k) {
-        items[k].level = batch[k].req.level;
-        items[k].mesh_level = mesh_of(batch[k]);
-        items[k].sample_id = batch[k].req.sample_id;
+        const Pending& p = batch[k];
+        items[k].level = p.req.level;
+        items[k].mesh_level = mesh_of(p);
+        items[k].sample_id = p.req.sample_id;
+        if (p.carry >= 0) guess[k] = pool.at(p.mesh - 1, p.carry);
+        if (p.out >= 0) outp[k] = pool.at(p.mesh, p.out);
       }
       q.assign(2 * batch.size(), 0.0);
       st.assign(batch.size(), 0);
-      const mlmc_status s = mlmc_solve_batch(ctx[w], items.data(), (int64_t)items.size(), q.data(), st.data());
+      its.assign(batch.size(), 0);
+      const mlmc_status s = mlmc::solve_batch_carry(ctx[w], items.data(), (int64_t)items.size(), q.data(), st.data(),
+                                                    guess.data(), outp.data(), its.data());
       if (s != MLMC_OK) record_error(mlmc_last_error(ctx[w]));
       {
         std::lock_guard<std::mutex> g(mu);
@@ -150,17 +194,27 @@ struct mlmc_server {
         std::vector<Pending> again;
         for (size_t k = 0; k < batch.size(); ++k) {
           Pending& p = batch[k];
+          if (p.solves < MLMC_SR_MAX_LEVELS) p.iters[p.solves] = its[k];
           ++p.solves;
           const int32_t status = s != MLMC_OK ? (int32_t)s : st[k];
+          // the previous mesh's iterate has been read; this solve's is kept only for an escalation
+          if (p.carry >= 0) pool.give(p.mesh - 1, p.carry);
+          p.carry = -1;
           if (status != 0 || p.req.kind == MLMC_REQ_SOLVE) {
+            if (p.out >= 0) pool.give(p.mesh, p.out);
+            p.out = -1;
             complete(p, status, &q[2 * k], 0);
             continue;
           }
           const int j = p.mesh;
           p.lambda[j] = q[2 * k + 1];
           if (sr_stops(p, j)) {
+            if (p.out >= 0) pool.give(j, p.out);
+            p.out = -1;
             complete(p, 0, &q[2 * k], j);
           } else {
+            p.carry = p.out;
+            p.out = -1;
             p.mesh = j + 1;
             again.push_back(p);
           }
@@ -192,11 +246,39 @@ mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config*
     g_server_error = "selective refinement needs mlmc_m > 1 and mlmc_alpha > 0";
     return MLMC_ERR_INVALID_ARG;
   }
+  if (scfg->carry_iterates != 0 && scfg->carry_iterates != 1) {
+    g_server_error = "carry_iterates must be 0 or 1";
+    return MLMC_ERR_INVALID_ARG;
+  }
   mlmc_server* s = new mlmc_server();
   s->cfg = *cfg;
   s->scfg = *scfg;
-  s->share = scfg->hbm_budget_bytes / scfg->workers;
   cudaGetDevice(&s->device);
+  // carried iterates: 1/8 of the budget, split evenly over the meshes a sample can
+  // escalate from (0 .. levels - 2), at most four slots per request a batch holds
+  double pool_bytes = 0.0;
+  if (scfg->carry_iterates && cfg->levels > 1) {
+    const int meshes = cfg->levels - 1;
+    const double per_mesh = scfg->hbm_budget_bytes / 8.0 / meshes;
+    for (int m = 0; m < meshes; ++m) {
+      const int64_t vals = mlmc::iterate_values(*cfg, m);
+      const int64_t slots = std::min<int64_t>((int64_t)(per_mesh / (8.0 * vals)), 4 * scfg->max_batch * scfg->workers);
+      double* base = nullptr;
+      if (slots > 0 && cudaMalloc(&base, sizeof(double) * vals * slots) != cudaSuccess) {
+        cudaGetLastError();
+        s->pool.release();
+        delete s;
+        g_server_error = "iterate pool allocation failed";
+        return MLMC_ERR_OOM;
+      }
+      s->pool.base.push_back(base);
+      s->pool.values.push_back(vals);
+      s->pool.free.emplace_back();
+      for (int64_t k = slots - 1; k >= 0; --k) s->pool.free.back().push_back((int)k);
+      pool_bytes += 8.0 * vals * slots;
+    }
+  }
+  s->share = (scfg->hbm_budget_bytes - pool_bytes) / scfg->workers;
   for (int w = 0; w < scfg->workers; ++w) {
     cudaStream_t st = nullptr;
     mlmc_ctx* c = nullptr;
@@ -294,6 +376,7 @@ void mlmc_server_destroy(mlmc_server* s) {
   for (auto& t : s->threads) t.join();
   for (auto* c : s->ctx) mlmc_destroy(c);
   for (auto st : s->streams) cudaStreamDestroy(st);
+  s->pool.release();
   delete s;
 }
 

@@ -246,6 +246,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     alloc.template vec<int>(S.status, total);
     alloc.template vec<int>(S.count, (size_t)std::max(ctx.check_every, 1));
     alloc.template vec<int>(S.rpar, total);
+    alloc.template vec<int>(S.exact, total);
     alloc.template vec<unsigned>(S.arrive, total);
     alloc.template vec<int>(outer_count, 1);
   };
@@ -521,11 +522,19 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   };
 
   // double-precision views for lifting, residual and stress
-  auto d_list = [&]() {
+  // groups whose next refinement residual is formed exactly from d: those that start
+  // from the lifting, after their first correction; those with initial iterates (nested
+  // iteration) at the start. Each group keeps its own sequence, so a sample's solve does
+  // not depend on the other groups of its batch.
+  std::vector<char> exact(G.size());
+  for (size_t gi = 0; gi < G.size(); ++gi) exact[gi] = G[gi].grp->d_guess == nullptr;
+  auto d_list = [&](int want_exact = -1) {
     ViewList<double> L;
     std::memset(&L, 0, sizeof(L));
     L.U = ctx.U;
-    for (auto& g : G) {
+    for (size_t gi = 0; gi < G.size(); ++gi) {
+      if (want_exact >= 0 && exact[gi] != want_exact) continue;
+      auto& g = G[gi];
       View<double> v;
       std::memset(&v, 0, sizeof(v));
       v.g = g.geo[0];
@@ -541,8 +550,9 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     }
     return L;
   };
-  auto resid = [&]() -> mlmc_status {
-    ViewList<double> L = d_list();
+  auto resid = [&]() -> mlmc_status {   // the groups marked exact
+    ViewList<double> L = d_list(1);
+    if (L.n == 0) return MLMC_OK;
     int acc = 0;
     for (int i = 0; i < L.n; ++i) {
       L.v[i].work_begin = acc;
@@ -588,28 +598,42 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   // (the lifting above still defines ||f||); their residual is formed exactly, and the
   // corrections that follow are small, so every later residual is the inner CG's
   // recursive one
-  const bool guessed = G.front().grp->d_guess != nullptr;
-  for (auto& g : G)
-    if ((g.grp->d_guess != nullptr) != guessed)
-      return ctx.fail(MLMC_ERR_INVALID_ARG, "initial iterates given for some groups of a solve only");
-  bool exact_next = !guessed;   // the next refinement residual is formed from d
-  if (guessed) {
+  // nested iteration: groups with initial iterates start from the same samples'
+  // solutions on the next coarser mesh (the lifting above still defines ||f||); their
+  // residual is formed exactly, and the corrections that follow are small, so every
+  // later residual is the inner CG's recursive one
+  {
     ViewList<T> L = empty_list<T>(ctx);
     std::vector<int64_t> per;
-    for (auto& g : G) {
+    for (size_t gi = 0; gi < G.size(); ++gi) {
+      auto& g = G[gi];
+      if (!g.grp->d_guess) continue;
       View<T> v = base_view(g, 0);
       v.ext0 = g.grp->d_guess;
       v.ext1 = g.d;
       L.v[L.n++] = v;
       per.push_back((int64_t)(g.geo[0].nx + 1) * (g.geo[0].ny + 1));
+      if ((e = cudaMemsetAsync(S.rr64 + g.sbase, 0, sizeof(double) * g.grp->nsamp, st)) != cudaSuccess ||
+          (e = cudaMemsetAsync(S.react + g.sbase, 0, sizeof(double) * g.grp->nsamp, st)) != cudaSuccess)
+        return ctx.cuda_fail(e, "memset");
     }
-    const int tt = finalize_points(L, per);
-    MLMC_LAUNCH(kProfOther, "prolong_d", launch_prolong_d<T>(L, tt, st));
-    if ((e = cudaMemsetAsync(S.rr64, 0, sizeof(double) * total, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(S.react, 0, sizeof(double) * total, st)) != cudaSuccess)
-      return ctx.cuda_fail(e, "memset");
-    rs = resid();
-    if (rs != MLMC_OK) return rs;
+    if (L.n > 0) {
+      const int tt = finalize_points(L, per);
+      MLMC_LAUNCH(kProfOther, "prolong_d", launch_prolong_d<T>(L, tt, st));
+      for (size_t gi = 0; gi < G.size(); ++gi) exact[gi] = G[gi].grp->d_guess != nullptr;
+      rs = resid();
+      if (rs != MLMC_OK) return rs;
+    }
+    // from here on: exact marks the groups whose residual after the next correction is
+    // formed from d (those that started from the lifting)
+    std::vector<int> ex(total, 0);
+    for (size_t gi = 0; gi < G.size(); ++gi) {
+      exact[gi] = G[gi].grp->d_guess == nullptr;
+      for (int64_t k = 0; k < G[gi].grp->nsamp; ++k) ex[G[gi].sbase + k] = exact[gi];
+    }
+    // (from pageable memory: the call returns once ex has been staged)
+    if ((e = cudaMemcpyAsync(S.exact, ex.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return ctx.cuda_fail(e, "init");
   }
 
   // PCG iterations run in batches of check_every (even) between host convergence
@@ -713,18 +737,19 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       if (h_count == 0) break;
     }
     max_it_seen = std::max(max_it_seen, it);
-    MLMC_LAUNCH(kProfOther, "inner_end", launch_inner_end(S, total, exact_next ? 0 : 1, st));
+    MLMC_LAUNCH(kProfOther, "inner_end", launch_inner_end(S, total, st));
     // d += x; after the first correction the inner CG's recursive residual (accurate
     // to unit roundoff times the correction's size) is the new refinement residual,
     // moved into r0 where it ended in r1
     {
       ViewList<T> L = empty_list<T>(ctx);
       std::vector<int64_t> per;
-      for (auto& g : G) {
+      for (size_t gi = 0; gi < G.size(); ++gi) {
+        auto& g = G[gi];
         View<T> v = base_view(g, 0);
         v.a = g.x;
         v.ext1 = g.d;
-        if (!exact_next) {   // this correction's recursive residual becomes the refinement residual
+        if (!exact[gi]) {   // this correction's recursive residual becomes the refinement residual
           v.b = g.r[1];
           v.o0 = g.r[0];
         }
@@ -734,24 +759,38 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       const int tt = finalize_points(L, per);
       MLMC_LAUNCH(kProfOther, "update_d", launch_update_d<T>(L, S, tt, st));
     }
-    if (exact_next) {
-      // the one double-precision residual: f - K d after the first correction
-      if ((e = cudaMemsetAsync(S.react, 0, sizeof(double) * total, st)) != cudaSuccess)
-        return ctx.cuda_fail(e, "memset");
+    // the groups marked exact: the one double-precision residual f - K d after their
+    // first correction; the others: the reaction increment of the correction
+    bool any_exact = false, any_rec = false;
+    for (size_t gi = 0; gi < G.size(); ++gi) {
+      if (exact[gi]) {
+        any_exact = true;
+        if ((e = cudaMemsetAsync(S.react + G[gi].sbase, 0, sizeof(double) * G[gi].grp->nsamp, st)) != cudaSuccess)
+          return ctx.cuda_fail(e, "memset");
+      } else {
+        any_rec = true;
+      }
+    }
+    if (any_exact) {
       rs = resid();
       if (rs != MLMC_OK) return rs;
-      exact_next = false;
-    } else {
+    }
+    if (any_rec) {
       ViewList<T> R = empty_list<T>(ctx);
       std::vector<int64_t> rows;
-      for (auto& g : G) {
-        View<T> w = base_view(g, 0);
-        w.a = g.x;
+      for (size_t gi = 0; gi < G.size(); ++gi) {
+        if (exact[gi]) continue;
+        View<T> w = base_view(G[gi], 0);
+        w.a = G[gi].x;
         R.v[R.n++] = w;
-        rows.push_back(g.geo[0].ny);
+        rows.push_back(G[gi].geo[0].ny);
       }
       const int tr = finalize_points(R, rows);
       MLMC_LAUNCH(kProfOther, "react_delta", launch_react_delta<T>(R, S, tr, st));
+    }
+    if (any_exact) {
+      std::fill(exact.begin(), exact.end(), 0);
+      if ((e = cudaMemsetAsync(S.exact, 0, sizeof(int) * total, st)) != cudaSuccess) return ctx.cuda_fail(e, "memset");
     }
   }
   ctx.last_outer = outer;

@@ -179,3 +179,70 @@ def test_failure_estimate_matches_the_oracle(B, k, two_level):
     for l, (m, v) in terms.items():
         assert mean[l] == pytest.approx(m, rel=1e-13, abs=1e-15)
         assert var[l] == pytest.approx(v, rel=1e-13, abs=1e-15)
+
+
+def _selective(B, w, thr, reqs, carry, workers, max_batch, chunks=1):
+    srv = B.mlmc_server_create(B.config_from_workload(w), workers=workers, max_batch=max_batch,
+                               hbm_budget_bytes=4e9, threshold=thr, sr_factor=2.0, eps_rel=1e-6,
+                               carry_iterates=carry)
+    try:
+        for chunk in np.array_split(np.arange(len(reqs)), chunks):
+            B.mlmc_server_submit(srv, [reqs[i] for i in chunk])
+            if chunks > 1:
+                time.sleep(0.02)
+        return collect(B, srv, len(reqs))
+    finally:
+        B.mlmc_server_destroy(srv)
+
+
+def test_carried_iterates_keep_results_and_save_iterations(B):
+    """Selective refinement on the 5-level mixed strip with each sample's solution kept
+    on the device between its solves (its next mesh starts from it) against every solve
+    from the lifting: the same stopping meshes and lambdas (the stated 1e-6) and fewer
+    PCG iterations per escalation solve."""
+    w = STRIP_MIXED_5LEVEL
+    ctx = B.mlmc_create(B.config_from_workload(w))
+    try:
+        n = 256
+        qf, qc = np.zeros(2 * n), np.zeros(2 * n)
+        B.mlmc_sample_level(ctx, 1, 0, n, qf, qc)
+    finally:
+        B.mlmc_destroy(ctx)
+    thr = float(np.quantile(qf.reshape(n, 2)[:, 1], 0.6))
+    reqs = [(SEL, l, 0, 300 + sid, 100 * l + sid) for l in range(1, 5) for sid in range(10)]
+    on = _selective(B, w, thr, reqs, True, workers=2, max_batch=16)
+    off = _selective(B, w, thr, reqs, False, workers=2, max_batch=16)
+    esc_on, esc_off = [], []
+    for r in reqs:
+        a, b = on[r[4]], off[r[4]]
+        assert a["status"] == 0 and b["status"] == 0
+        assert a["stop_level"] == b["stop_level"] and a["solves"] == b["solves"]
+        assert all(rel(x, y) < 1e-6 for x, y in zip(a["lambdas"], b["lambdas"]))
+        assert a["pcg_iterations"][0] == b["pcg_iterations"][0]      # mesh 0: no coarser start either way
+        esc_on += a["pcg_iterations"][1:]
+        esc_off += b["pcg_iterations"][1:]
+    assert len(esc_on) >= 20
+    assert np.mean(esc_on) < 0.9 * np.mean(esc_off), (np.mean(esc_on), np.mean(esc_off))
+
+
+def test_selective_result_is_the_same_alone_and_in_the_mix(B):
+    """With carried iterates, a selective sample's escalations share batches with other
+    requests (some starting from carried iterates, some from the lifting); each group of
+    a batch keeps its own refinement sequence, so the lambdas equal the sample's alone."""
+    w = STRIP_MIXED_5LEVEL
+    thr = 1.3e8
+    probe = [(SEL, l, 0, 700 + sid, 10 * l + sid) for l in range(1, 4) for sid in range(4)]
+    alone = {}
+    for r in probe:
+        alone.update(_selective(B, w, thr, [r], True, workers=1, max_batch=8))
+    g = np.random.default_rng(11)
+    noise = [(SEL if k % 2 else SOLVE, int(l), int(l), 80000 + k, 10 ** 6 + k)
+             for k, l in enumerate(g.integers(0, 4, 60))]
+    traffic = probe + noise
+    order = g.permutation(len(traffic))
+    mix = _selective(B, w, thr, [traffic[i] for i in order], True, workers=3, max_batch=12, chunks=5)
+    for r in probe:
+        a, m = alone[r[4]], mix[r[4]]
+        assert a["status"] == 0 and m["status"] == 0
+        assert a["stop_level"] == m["stop_level"]
+        assert all(rel(x, y) < 1e-6 for x, y in zip(a["lambdas"], m["lambdas"]))
