@@ -755,14 +755,33 @@ def run_hex3d(B, steps=2, warmup=1, parity=True):
     return out
 
 
-def run_panel(B, steps=2, warmup=1, parity=True):
-    """The buckling panel (panel-rm-q4-4level): one MLMC step is every level's samples
-    (4096/1024/256/64 level pairs on 24x8 ... 192x64 Q4 meshes), one mlmcp_sample_level
-    call per level with host outputs, timed with the device synchronised on both sides.
-    Parity: four level-0 pairs and two level-1 pairs against the oracle's sparse
-    eigen-solves, whose times are the CPU baseline (one core)."""
+def panel_pilot_threshold(B, W, n=4096, level=2):
+    """The 1/150 lower quantile (kN) of the critical load of a seeded pilot: seed 1, n
+    samples of `level` (order statistic ceil(n / 150))."""
     import torch
-    from workloads import PANEL_RM_4LEVEL as W
+    ctx = B.mlmcp_create(B.configp_from_workload(W, seed=1), torch.cuda.current_stream().cuda_stream)
+    try:
+        qf, qc = np.zeros(2 * n), np.zeros(2 * n)
+        B.mlmcp_sample_level(ctx, level, 0, n, qf, qc)
+    finally:
+        B.mlmcp_destroy(ctx)
+    P = np.sort(qf[0::2])
+    return float(P[int(math.ceil(n / 150.0)) - 1])
+
+
+def run_panel(B, steps=2, warmup=1, parity=True, W=None, pilot=False):
+    """A buckling panel workload (by default panel-rm-q4-4level, the paper's panel): one
+    MLMC step is every level's samples (4096/1024/256/64 level pairs), one
+    mlmcp_sample_level call per level with host outputs, timed with the device
+    synchronised on both sides. With pilot, the failure threshold is first set to the
+    1/150 lower quantile of a seeded pilot. Parity: four level-0 pairs and two level-1
+    pairs against the oracle's sparse eigen-solves, whose times are the CPU baseline
+    (one core)."""
+    import torch
+    if W is None:
+        from workloads import PANEL_RM_4LEVEL as W
+    if pilot:
+        W = dict(W, p_star=panel_pilot_threshold(B, W))
     counts = list(W["n_per_level"])
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -788,15 +807,25 @@ def run_panel(B, steps=2, warmup=1, parity=True):
             ms = (time.perf_counter() - t0) / steps * 1e3
             failed = sum(int((b[2] != 0).sum()) for b in bufs)
             fails = [float(b[0][1::2].mean()) for b in bufs]
+            nx0, ny0 = W["nx0"], W["ny0"]
             out = {
-                "workload": W["name"], "meshes": "24x8..192x64 Q4 (w, theta_x, theta_y), 636 x 212 mm",
+                "workload": W["name"],
+                "meshes": "%dx%d..%dx%d Q4 (w, theta_x, theta_y), %g x %g mm, t = %g mm" % (
+                    nx0, ny0, nx0 << (W["levels"] - 1), ny0 << (W["levels"] - 1), W["lx"], W["ly"],
+                    W["t_ply"] * len(W["plies_deg"])),
+                "smoother": W.get("smoother", "nodal"), "p_star_kn": W["p_star"],
+                "p_star_source": "1/150 lower quantile of a seed-1 pilot (4096 level-2 samples)" if pilot
+                else "workload value",
                 "samples_per_level": counts, "plies": len(W["plies_deg"]), "ply_std_deg": W["ply_std_deg"],
                 "metric": "level-pairs/s", "value": round(sum(counts) / ms * 1e3, 1), "ms_per_step": round(ms, 2),
                 "steps": steps, "warmup": warmup, "samples_failed": failed,
                 "lobpcg_iterations_per_level": list(iters),
                 "fine_failure_fraction_per_level": [round(f, 4) for f in fails],
                 "note": "host outputs (mlmcp_sample_level), one call per level; block LOBPCG (2 vectors) in FP32 "
-                        "preconditioned by a V(2,2) multigrid cycle, FP64 Gram matrices and final Rayleigh quotient",
+                        "preconditioned by " + ("a V(1,1) multigrid cycle with the 3x3-node patch smoother (nine "
+                                                "colours)" if W.get("smoother") == "patch" else
+                                                "a V(2,2) multigrid cycle with the nodal block-Jacobi smoother") +
+                        ", FP64 Gram matrices and final Rayleigh quotient",
             }
             if parity:
                 from oracle import plate as P
@@ -925,7 +954,9 @@ def main():
         out["hex3d"] = run_hex3d(B, parity=not a.no_cpu_baseline)
     if rank == 0 and out is not None and world == 1 and a.panel:
         from paper_1907_10271_gb300 import binding as B
+        from workloads import PANEL_C5_4LEVEL
         out["panel"] = run_panel(B, parity=not a.no_cpu_baseline)
+        out["panel_thin"] = run_panel(B, parity=not a.no_cpu_baseline, W=PANEL_C5_4LEVEL, pilot=True)
     if rank == 0 and out is not None:
         if world == 1 and not a.no_cpu_baseline and out.get("_gpu_q") is not None:
             cores = os.cpu_count() or 1

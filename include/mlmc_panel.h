@@ -67,6 +67,12 @@ typedef struct {
                                   preconditioned residual of the first vector (0: 1e-4;
                                   the load error is about tol^2) */
   int32_t max_iter;            /* LOBPCG iterations (0: 120) */
+  int32_t smoother;            /* multigrid smoother: 0 = damped nodal 3x3 block Jacobi, V(2,2);
+                                  1 = multiplicative Schwarz on 3x3-node patches in nine
+                                  colours, V(1,1), for thin plates (b / t in the hundreds),
+                                  where the nodal smoother does not resolve the nearly held
+                                  transverse shear; meshes of the hierarchy must then have at
+                                  least 4 elements per side */
 } mlmcp_config;
 
 /* Validates cfg and builds the mesh hierarchies. The multigrid coarsens each mesh by

@@ -597,6 +597,7 @@ class mlmcp_config(ctypes.Structure):
         ("t_ply", ctypes.c_double), ("ply_std_deg", ctypes.c_double),
         ("hard_support", ctypes.c_int32), ("p_star", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+        ("smoother", ctypes.c_int32),
     ]
 
 
@@ -647,6 +648,7 @@ def configp_from_workload(w, **overrides):
     c.seed = int(w["seed"])
     c.tol = float(w.get("tol", 0.0))
     c.max_iter = int(w.get("max_iter", 0))
+    c.smoother = {"nodal": 0, "patch": 1}[w.get("smoother", "nodal")]
     return c
 
 

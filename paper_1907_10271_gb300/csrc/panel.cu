@@ -209,6 +209,60 @@ __global__ void __launch_bounds__(kThreads) k_apply(PGrid g, const float* __rest
   if (gout) gout[o + t] = make_float4((bc && !f.w) ? 0.f : gw, 0.f, 0.f, 0.f);
 }
 
+// K x with the double element matrix and double sums (the vector itself single): for
+// thin plates, whose transverse shear strain grad w - theta is a small difference of
+// large terms, a single-precision sum keeps only a few digits of it. G x in single
+// precision (no cancellation). Rounded to single at the end.
+__global__ void __launch_bounds__(kThreads) k_apply64(PGrid g, const double* __restrict__ ke64,
+                                                      const float4* __restrict__ x, float4* __restrict__ out,
+                                                      float4* __restrict__ gout, float4* __restrict__ rout,
+                                                      const double* __restrict__ mu, const int* __restrict__ active) {
+  const int e = blockIdx.y, s = e >> g.cshift;
+  if (active && !active[s]) return;
+  __shared__ double K[144];
+  for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke64[(size_t)s * 144 + k];
+  __syncthreads();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nn = g.nodes();
+  if (t >= nn) return;
+  const int i = t % (g.nx + 1), j = t / (g.nx + 1), np = g.nx + 1;
+  const float4* xe = x + (size_t)e * nn;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, gsum = 0.0;
+  for (int oy = 0; oy < 2; ++oy)
+    for (int ox = 0; ox < 2; ++ox) {
+      const int ei = i - ox, ej = j - oy;
+      if (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) continue;
+      const int a = corner_of(ox, oy);
+      const double* Ka = K + 36 * a;
+      double gs = 0.0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ni = ei + corner_x(c), nj = ej + corner_y(c);
+        const Free fc = free_of(g, ni, nj);
+        const float4 v = xe[nj * np + ni];
+        // w in two parts (high in x, low in w; the low part is zero for vectors kept in
+        // one float)
+        const double vw = fc.w ? (double)v.x + (double)v.w : 0.0;
+        const double vx = fc.tx ? (double)v.y : 0.0, vy = fc.ty ? (double)v.z : 0.0;
+        const double* r = Ka + 3 * c;
+        a0 += r[0] * vw + r[1] * vx + r[2] * vy;
+        a1 += r[12] * vw + r[13] * vx + r[14] * vy;
+        a2 += r[24] * vw + r[25] * vx + r[26] * vy;
+        gs += corner_x(c) ? vw : -vw;
+      }
+      gsum += corner_x(a) ? gs : -gs;
+    }
+  const Free f = free_of(g, i, j);
+  const double gw = f.w ? gsum * ((double)g.hy / (4.0 * (double)g.hx)) : 0.0;
+  const size_t o = (size_t)e * nn + t;
+  out[o] = masked(f, make_float4((float)a0, (float)a1, (float)a2, 0.f));
+  if (gout) gout[o] = make_float4((float)gw, 0.f, 0.f, 0.f);
+  if (rout) {   // R = G x - mu K x of the entry's column, in double
+    const double m = mu[(size_t)s * kCols + (e & ((1 << g.cshift) - 1))];
+    rout[o] = masked(f, make_float4((float)(gw - m * a0), (float)(-m * a1), (float)(-m * a2), 0.f));
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_smooth(PGrid g, const float* __restrict__ ke, const float4* __restrict__ b,
                                                      const float4* __restrict__ x, float4* __restrict__ out,
                                                      const int* __restrict__ active) {
@@ -293,6 +347,132 @@ __global__ void __launch_bounds__(kThreads) k_prolong(PGrid gf, PGrid gc, const 
   const float4 p = make_float4(0.25f * (v00.x + v10.x + v01.x + v11.x), 0.25f * (v00.y + v10.y + v01.y + v11.y),
                                0.25f * (v00.z + v10.z + v01.z + v11.z), 0.f);
   xf[(size_t)e * nf + t] = masked(free_of(gf, i, j), make_float4(xo.x + p.x, xo.y + p.y, xo.z + p.z, 0.f));
+}
+
+// ---------------------------------------------------------------- patch smoother
+// boundary case of a patch centre c on an axis of n elements: -1, 0, 1 -> 0, 1, 2;
+// interior -> 3; n - 1, n, n + 1 -> 4, 5, 6 (n >= 4: the cases are distinct)
+__device__ __forceinline__ int patch_case(int c, int n) {
+  if (c <= 1) return c + 1;
+  if (c >= n - 1) return c - n + 5;
+  return 3;
+}
+__device__ __forceinline__ int patch_centre(int t, int n) { return t <= 2 ? t - 1 : (t == 3 ? 2 : n - 5 + t); }
+__device__ __forceinline__ bool free_comp(const Free& f, int c) { return c == 0 ? f.w : (c == 1 ? f.tx : f.ty); }
+
+// one block per (case, sample): A_p from the element matrix, scaled to a unit diagonal,
+// inverted by Gauss-Jordan in single precision (symmetric positive definite: no
+// pivoting; scaled, the patches' condition numbers stay near 1e3 to 1e4), unscaled
+__global__ void __launch_bounds__(kThreads) k_patch_setup(PGrid g, const float* __restrict__ ke,
+                                                          float* __restrict__ pinv) {
+  const int type = blockIdx.x, s = blockIdx.y;
+  __shared__ float K[144];
+  __shared__ float A[kPatchDofs][kPatchDofs + 1];
+  __shared__ float dsc[kPatchDofs], fcol[kPatchDofs];
+  for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke[(size_t)s * 144 + k];
+  __syncthreads();
+  const int ci = patch_centre(type % 7, g.nx), cj = patch_centre(type / 7, g.ny);
+  auto slot_dof = [&](int p, int& i, int& j, int& c) -> bool {
+    const int a = p / 3;
+    c = p - 3 * a;
+    i = ci + a % 3 - 1;
+    j = cj + a / 3 - 1;
+    return i >= 0 && i <= g.nx && j >= 0 && j <= g.ny && free_comp(free_of(g, i, j), c);
+  };
+  for (int idx = threadIdx.x; idx < kPatchDofs * kPatchDofs; idx += blockDim.x) {
+    const int p = idx / kPatchDofs, q = idx - kPatchDofs * p;
+    int ia, ja, ca, ib, jb, cb;
+    const bool fa = slot_dof(p, ia, ja, ca), fb = slot_dof(q, ib, jb, cb);
+    float v = p == q ? 1.f : 0.f;
+    if (fa && fb) {
+      v = 0.f;
+      // elements with both nodes as corners (lower-left node (ei, ej))
+      for (int ej = max(ja, jb) - 1; ej <= min(ja, jb); ++ej)
+        for (int ei = max(ia, ib) - 1; ei <= min(ia, ib); ++ei) {
+          if (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) continue;
+          const int la = corner_of(ia - ei, ja - ej), lb = corner_of(ib - ei, jb - ej);
+          v += K[(3 * la + ca) * 12 + 3 * lb + cb];
+        }
+    }
+    A[p][q] = v;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < kPatchDofs; p += blockDim.x) dsc[p] = rsqrtf(A[p][p]);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < kPatchDofs * kPatchDofs; idx += blockDim.x) {
+    const int p = idx / kPatchDofs, q = idx - kPatchDofs * p;
+    A[p][q] *= dsc[p] * dsc[q];
+  }
+  __syncthreads();
+  for (int k = 0; k < kPatchDofs; ++k) {
+    const float piv = 1.f / A[k][k];
+    __syncthreads();
+    for (int q = threadIdx.x; q < kPatchDofs; q += blockDim.x) A[k][q] = (q == k ? 1.f : A[k][q]) * piv;
+    for (int r = threadIdx.x; r < kPatchDofs; r += blockDim.x) fcol[r] = r == k ? 0.f : A[r][k];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kPatchDofs * kPatchDofs; idx += blockDim.x) {
+      const int r = idx / kPatchDofs, q = idx - kPatchDofs * r;
+      if (r != k) A[r][q] = (q == k ? 0.f : A[r][q]) - fcol[r] * A[k][q];
+    }
+    __syncthreads();
+  }
+  float* out = pinv + ((size_t)s * kPatchTypes + type) * kPatchDofs * kPatchDofs;
+  for (int idx = threadIdx.x; idx < kPatchDofs * kPatchDofs; idx += blockDim.x) {
+    const int p = idx / kPatchDofs, q = idx - kPatchDofs * p;
+    out[idx] = A[p][q] * dsc[p] * dsc[q];
+  }
+}
+
+// one warp per patch of colour (sx, sy): the residual at the patch's 9 nodes (lanes
+// 0..8, from `in`), the correction A_p^-1 r at its 27 slots (lanes 0..26; A_p^-1 is
+// symmetric, so lane l reads column l, coalesced), out = in + correction on the patch
+__global__ void __launch_bounds__(kThreads) k_patch_color(PGrid g, const float* __restrict__ ke,
+                                                          const float* __restrict__ pinv, const float4* __restrict__ b,
+                                                          const float4* __restrict__ xin, float4* __restrict__ xout,
+                                                          int sx, int sy, const int* __restrict__ active) {
+  const int e = blockIdx.y, s = e >> g.cshift;
+  if (active && !active[s]) return;
+  __shared__ float K[144];
+  __shared__ float rs[kThreads / 32][32], ds[kThreads / 32][32];
+  for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke[(size_t)s * 144 + k];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int fx = sx == 2 ? -1 : sx, fy = sy == 2 ? -1 : sy;   // first centres of the colour
+  const int px_n = (g.nx + 1 - fx) / 3 + 1, py_n = (g.ny + 1 - fy) / 3 + 1;
+  const int pid = blockIdx.x * (kThreads / 32) + warp;
+  if (pid >= px_n * py_n) return;   // the whole warp
+  const int ci = fx + 3 * (pid % px_n), cj = fy + 3 * (pid / px_n);
+  const int type = patch_case(ci, g.nx) + 7 * patch_case(cj, g.ny);
+  const int np = g.nx + 1;
+  const size_t o = (size_t)e * g.nodes();
+  const int li = ci + lane % 3 - 1, lj = cj + (lane / 3) % 3 - 1;   // node of lanes 0..8
+  const bool node_in = lane < 9 && li >= 0 && li <= g.nx && lj >= 0 && lj <= g.ny;
+  float4 xo = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (node_in) {
+    const float4 kx = xin ? node_kx<false>(g, K, xin + o, li, lj, true, nullptr, nullptr) : xo;
+    const float4 bb = b[o + lj * np + li];
+    const Free f = free_of(g, li, lj);
+    if (xin) xo = xin[o + lj * np + li];
+    rs[warp][3 * lane] = f.w ? bb.x - kx.x : 0.f;
+    rs[warp][3 * lane + 1] = f.tx ? bb.y - kx.y : 0.f;
+    rs[warp][3 * lane + 2] = f.ty ? bb.z - kx.z : 0.f;
+  } else if (lane < 9) {
+    rs[warp][3 * lane] = rs[warp][3 * lane + 1] = rs[warp][3 * lane + 2] = 0.f;
+  }
+  __syncwarp();
+  if (lane < kPatchDofs) {
+    const float* M = pinv + ((size_t)s * kPatchTypes + type) * kPatchDofs * kPatchDofs;
+    float d = 0.f;
+#pragma unroll 9
+    for (int q = 0; q < kPatchDofs; ++q) d += M[q * kPatchDofs + lane] * rs[warp][q];
+    ds[warp][lane] = d;
+  }
+  __syncwarp();
+  if (node_in) {
+    const Free f = free_of(g, li, lj);
+    xout[o + lj * np + li] = masked(f, make_float4(xo.x + ds[warp][3 * lane], xo.y + ds[warp][3 * lane + 1],
+                                                  xo.z + ds[warp][3 * lane + 2], 0.f));
+  }
 }
 
 // one block per sample: assemble K on the free DOFs in shared memory, invert in place
@@ -658,7 +838,11 @@ __global__ void __launch_bounds__(32) k_rayleigh_ritz(Eig E, int n, double tol2,
   atomicAdd(E.count, 1);
 }
 
-__global__ void __launch_bounds__(kThreads) k_update(PGrid g, Eig E, const __grid_constant__ Vecs V) {
+// X = S C and P = [W P] C (their K and G images are recomputed by the caller). With
+// two_part (thin plates): the combination in double and the new X's w kept in two
+// floats (high in x, low in w), so that its rounding error, whose transverse shear
+// energy dominates on coarse meshes of a thin plate, stays below the tolerance.
+__global__ void __launch_bounds__(kThreads) k_update(PGrid g, Eig E, const __grid_constant__ Vecs V, int two_part) {
   float4* const* vp = V.v;
   const int s = blockIdx.y;
   if (!E.active[s]) return;
@@ -675,22 +859,42 @@ __global__ void __launch_bounds__(kThreads) k_update(PGrid g, Eig E, const __gri
       for (int k = 0; k < kCols; ++k) v[b * kCols + k] = vp[3 * set + b][((size_t)s * kCols + k) * nn + t];
 #pragma unroll
     for (int k = 0; k < kCols; ++k) {
-      float x0 = 0.f, x1 = 0.f, x2 = 0.f, p0 = 0.f, p1 = 0.f, p2 = 0.f;
-#pragma unroll
-      for (int q = 0; q < kSub; ++q) {
-        const float w = (float)c[q * kCols + k];
-        x0 += w * v[q].x;
-        x1 += w * v[q].y;
-        x2 += w * v[q].z;
-        if (q >= kCols) {
-          p0 += w * v[q].x;
-          p1 += w * v[q].y;
-          p2 += w * v[q].z;
-        }
-      }
       const size_t o = ((size_t)s * kCols + k) * nn + t;
-      vp[3 * set][o] = make_float4(x0, x1, x2, 0.f);
-      vp[3 * set + 2][o] = make_float4(p0, p1, p2, 0.f);
+      if (two_part) {
+        double x0 = 0.0, x1 = 0.0, x2 = 0.0, p0 = 0.0, p1 = 0.0, p2 = 0.0;
+#pragma unroll
+        for (int q = 0; q < kSub; ++q) {
+          const double w = c[q * kCols + k];
+          const double vw = (double)v[q].x + (q < kCols ? (double)v[q].w : 0.0);
+          x0 += w * vw;
+          x1 += w * (double)v[q].y;
+          x2 += w * (double)v[q].z;
+          if (q >= kCols) {
+            p0 += w * vw;
+            p1 += w * (double)v[q].y;
+            p2 += w * (double)v[q].z;
+          }
+        }
+        const float hi = (float)x0;
+        vp[3 * set][o] = make_float4(hi, (float)x1, (float)x2, (float)(x0 - (double)hi));
+        vp[3 * set + 2][o] = make_float4((float)p0, (float)p1, (float)p2, 0.f);
+      } else {
+        float x0 = 0.f, x1 = 0.f, x2 = 0.f, p0 = 0.f, p1 = 0.f, p2 = 0.f;
+#pragma unroll
+        for (int q = 0; q < kSub; ++q) {
+          const float w = (float)c[q * kCols + k];
+          x0 += w * v[q].x;
+          x1 += w * v[q].y;
+          x2 += w * v[q].z;
+          if (q >= kCols) {
+            p0 += w * v[q].x;
+            p1 += w * v[q].y;
+            p2 += w * v[q].z;
+          }
+        }
+        vp[3 * set][o] = make_float4(x0, x1, x2, 0.f);
+        vp[3 * set + 2][o] = make_float4(p0, p1, p2, 0.f);
+      }
     }
   }
 }
@@ -709,7 +913,7 @@ __global__ void __launch_bounds__(kThreads) k_energy(PGrid g, const double* __re
     double u[12];
     for (int a = 0; a < 4; ++a) {
       const float4 v = xs[(ej + corner_y(a)) * (g.nx + 1) + ei + corner_x(a)];
-      u[3 * a] = v.x;
+      u[3 * a] = (double)v.x + (double)v.w;   // w in two parts (low part zero unless kept)
       u[3 * a + 1] = v.y;
       u[3 * a + 2] = v.z;
     }
@@ -770,6 +974,13 @@ cudaError_t launch_apply(const PGrid& g, const float* ke, const float4* x, const
   return cudaGetLastError();
 }
 
+cudaError_t launch_apply64(const PGrid& g, const double* ke64, const float4* x, float4* out, float4* gout,
+                           float4* rout, const double* mu, const int* active, cudaStream_t st) {
+  k_apply64<<<dim3((g.nodes() + kThreads - 1) / kThreads, g.nb), kThreads, 0, st>>>(g, ke64, x, out, gout, rout, mu,
+                                                                                    active);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_smooth(const PGrid& g, const float* ke, const float4* b, const float4* x, float4* out,
                           const int* active, cudaStream_t st) {
   if (g.nb <= 0) return cudaSuccess;
@@ -810,6 +1021,23 @@ cudaError_t launch_coarse_solve(const PGrid& g, const float* ainv, const int* fr
   return cudaGetLastError();
 }
 
+cudaError_t launch_patch_setup(const PGrid& g, const float* ke, int n_samples, float* pinv, cudaStream_t st) {
+  if (n_samples <= 0) return cudaSuccess;
+  if (g.nx < 4 || g.ny < 4) return cudaErrorInvalidValue;
+  k_patch_setup<<<dim3(kPatchTypes, n_samples), kThreads, 0, st>>>(g, ke, pinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_patch_color(const PGrid& g, const float* ke, const float* pinv, const float4* b, const float4* in,
+                               float4* out, int sx, int sy, const int* active, cudaStream_t st) {
+  const int fx = sx == 2 ? -1 : sx, fy = sy == 2 ? -1 : sy;
+  const int patches = ((g.nx + 1 - fx) / 3 + 1) * ((g.ny + 1 - fy) / 3 + 1);
+  const int warps = kThreads / 32;
+  k_patch_color<<<dim3((patches + warps - 1) / warps, g.nb), kThreads, 0, st>>>(g, ke, pinv, b, in, out, sx, sy,
+                                                                               active);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_start(const PGrid& g, float4* z, cudaStream_t st) {
   if (g.nb <= 0) return cudaSuccess;
   k_init_start<<<grid_nodes(g, g.nb), kThreads, 0, st>>>(g, z);
@@ -837,10 +1065,10 @@ cudaError_t launch_rayleigh_ritz(const Eig& E, int n, double tol, int max_iter, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_update(const PGrid& g, const Eig& E, const Vecs& v, cudaStream_t st) {
+cudaError_t launch_update(const PGrid& g, const Eig& E, const Vecs& v, bool two_part, cudaStream_t st) {
   const int n = g.nb >> g.cshift;
   if (n <= 0) return cudaSuccess;
-  k_update<<<grid_nodes(g, n), kThreads, 0, st>>>(g, E, v);
+  k_update<<<grid_nodes(g, n), kThreads, 0, st>>>(g, E, v, two_part ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -41,6 +41,12 @@ cudaError_t launch_element_matrices(const double* dstar, const double* kgt, int 
 // sample is active (null: all). bc: zero the constrained DOFs of inputs and outputs.
 cudaError_t launch_apply(const PGrid& g, const float* ke, const float4* x, const float4* b, float4* out,
                          float4* gout, const int* active, bool bc, cudaStream_t st);
+// out = K x with the double element matrices ke64 and double sums, gout = G x, and
+// (rout set) rout = G x - mu K x with mu[sample][column] of each entry, also in double;
+// the input's w in two parts (x.x + x.w); the constrained DOFs of inputs and outputs
+// zeroed (the images and residuals of the LOBPCG vectors of thin plates)
+cudaError_t launch_apply64(const PGrid& g, const double* ke64, const float4* x, float4* out, float4* gout,
+                           float4* rout, const double* mu, const int* active, cudaStream_t st);
 // out = x + w D^-1 (b - K x) (x null: out = w D^-1 b), D the nodal 3x3 diagonal blocks
 cudaError_t launch_smooth(const PGrid& g, const float* ke, const float4* b, const float4* x, float4* out,
                           const int* active, cudaStream_t st);
@@ -49,6 +55,22 @@ cudaError_t launch_restrict(const PGrid& fine, const PGrid& coarse, const float4
                             cudaStream_t st);
 cudaError_t launch_prolong(const PGrid& fine, const PGrid& coarse, const float4* xc, float4* xf, const int* active,
                            cudaStream_t st);
+// Patch smoother (thin plates): multiplicative Schwarz over 3 x 3-node patches in nine
+// colours. Colour (sx, sy) tiles the mesh with the patches centred on the nodes
+// (sx + 3 k, sy + 3 l), k, l integers (centres from -1 to n + 1, patches cut at the
+// boundary), so one colour step is block Jacobi on that tiling:
+//   out = in + sum_p R_p^T A_p^-1 R_p (b - K in),   A_p = R_p K R_p^T,
+// with R_p the free DOFs of patch p. K is uniform inside the mesh, so A_p depends only
+// on how the mesh boundary cuts the patch: 7 cases per axis (centre -1, 0, 1, interior,
+// n - 1, n, n + 1), 49 inverses per sample and mesh, each [27][27] with identity rows
+// for the slots outside the mesh or held. kPatchTypes * kPatchDofs^2 floats per sample.
+constexpr int kPatchTypes = 49;
+constexpr int kPatchDofs = 27;
+cudaError_t launch_patch_setup(const PGrid& g, const float* ke, int n_samples, float* pinv, cudaStream_t st);
+// one colour step (in null: zero); in and out are different buffers
+cudaError_t launch_patch_color(const PGrid& g, const float* ke, const float* pinv, const float4* b, const float4* in,
+                               float4* out, int sx, int sy, const int* active, cudaStream_t st);
+
 // Coarsest mesh: per-sample dense inverse of K on the free DOFs (free[k] = 4 node + c)
 cudaError_t launch_coarse_setup(const PGrid& g, const float* ke, int n_samples, const int* free, int nf, float* ainv,
                                 cudaStream_t st);
@@ -82,8 +104,9 @@ cudaError_t launch_gram(const PGrid& g, const Eig& E, const Vecs& v, cudaStream_
 // current iterate (its K norm against mu times X's); bumps count
 cudaError_t launch_rayleigh_ritz(const Eig& E, int n, double tol, int max_iter, bool first, cudaStream_t st);
 // X and P from the Ritz coefficients (their K and G images are recomputed by the caller:
-// carried along as combinations they drift in single precision)
-cudaError_t launch_update(const PGrid& g, const Eig& E, const Vecs& v, cudaStream_t st);
+// carried along as combinations they drift in single precision). two_part: combined in
+// double, X's w kept as high (x) plus low (w) float (thin plates)
+cudaError_t launch_update(const PGrid& g, const Eig& E, const Vecs& v, bool two_part, cudaStream_t st);
 // energies of column 0 in double with the double element matrices
 cudaError_t launch_energy(const PGrid& g, const double* ke64, const float4* x, const Eig& E, cudaStream_t st);
 // q[n][2] = (P [kN], P < p_star); status from the iteration cap and the energies

@@ -196,6 +196,15 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
                                       l == 0 ? ke64 : nullptr, st),
        "element matrices");
   CK(mlmcp::launch_coarse_setup(c.grid(H[L - 1], n, 0), ke[L - 1], n, c.free_dev[m], nf, ainv, st), "coarse setup");
+  const bool patch = c.cfg.smoother == 1;
+  std::vector<float*> pinv(L, nullptr);   // patch smoother: inverses per smoothed mesh
+  if (patch) {
+    for (int l = 0; l + 1 < L; ++l) pinv[l] = sc.take<float>((size_t)n * mlmcp::kPatchTypes * mlmcp::kPatchDofs *
+                                                             mlmcp::kPatchDofs);
+    CK(sc.err, "alloc");
+    for (int l = 0; l + 1 < L; ++l)
+      CK(mlmcp::launch_patch_setup(c.grid(H[l], n, 0), ke[l], n, pinv[l], st), "patch setup");
+  }
 
   // multigrid buffers (batch of nb entries) and the LOBPCG sets
   std::vector<PGrid> G(L);
@@ -236,8 +245,46 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
   float4 *X = V.v[0], *W = V.v[1], *P = V.v[2], *KX = V.v[3], *KW = V.v[4], *KP = V.v[5], *GX = V.v[6],
          *GW = V.v[7], *GP = V.v[8];
 
+  // patch smoother: one sweep over the nine colours (reversed: 8 .. 0) from x0 (null:
+  // zero); steps 0 .. 7 alternate between the scratch buffers s1 and s2, step 8 writes
+  // `last` (every step reads one buffer and writes another; x0 and last are neither s1
+  // nor s2)
+  auto patch_sweep = [&](int l, const float4* b, const float4* x0, float4* s1, float4* s2, bool reversed,
+                         float4* last) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    const float4* in = x0;
+    for (int k = 0; k < 9 && e == cudaSuccess; ++k) {
+      const int col = reversed ? 8 - k : k;
+      float4* o = k == 8 ? last : ((k & 1) ? s2 : s1);
+      e = mlmcp::launch_patch_color(G[l], ke[l], pinv[l], b, in, o, col % 3, col / 3, act, st);
+      in = o;
+    }
+    return e;
+  };
+  // one V(1,1) cycle with the patch smoother: out = T b0
+  auto vcycle_patch = [&](const float4* b0, float4* out) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l + 1 < L && e == cudaSuccess; ++l) {
+      const float4* b = l == 0 ? b0 : bb[l];
+      e = patch_sweep(l, b, nullptr, tt[l], rr[l], false, xx[l]);
+      if (e == cudaSuccess) e = mlmcp::launch_apply(G[l], ke[l], xx[l], b, rr[l], nullptr, act, true, st);
+      if (e == cudaSuccess) e = mlmcp::launch_restrict(G[l], G[l + 1], rr[l], bb[l + 1], act, st);
+    }
+    if (e != cudaSuccess) return e;
+    float4* coarse_out = L == 1 ? out : xx[L - 1];
+    e = mlmcp::launch_coarse_solve(G[L - 1], ainv, c.free_dev[m], nf, L == 1 ? b0 : bb[L - 1], coarse_out, act, st);
+    for (int l = L - 2; l >= 0 && e == cudaSuccess; --l) {
+      const float4* b = l == 0 ? b0 : bb[l];
+      const float4* below = xx[l + 1];   // every level's post-smoothed x ends in xx
+      e = mlmcp::launch_prolong(G[l], G[l + 1], below, xx[l], act, st);
+      // from xx through tt and rr (free now), ending in out (level 0) or xx
+      if (e == cudaSuccess) e = patch_sweep(l, b, xx[l], tt[l], rr[l], true, l == 0 ? out : xx[l]);
+    }
+    return e;
+  };
   // one V(2,2) cycle: out = T b0 (level-0 batch entries)
   auto vcycle = [&](const float4* b0, float4* out) -> cudaError_t {
+    if (patch) return vcycle_patch(b0, out);
     cudaError_t e = cudaSuccess;
     for (int l = 0; l + 1 < L && e == cudaSuccess; ++l) {
       const float4* b = l == 0 ? b0 : bb[l];
@@ -259,16 +306,22 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
     return e;
   };
 
+  // K and G images of a set of LOBPCG vectors: in double sums for thin plates (patch
+  // smoother mode), where single-precision sums lose the small transverse shear strain
+  auto images = [&](const float4* x, float4* kx, float4* gx) -> cudaError_t {
+    return patch ? mlmcp::launch_apply64(G[0], ke64, x, kx, gx, nullptr, nullptr, act, st)
+                 : mlmcp::launch_apply(G[0], ke[0], x, nullptr, kx, gx, act, true, st);
+  };
   // start: X = T G Z for a fixed pseudo-random w field Z, then Rayleigh-Ritz on X
   CK(mlmcp::launch_init_start(G[0], W, st), "start");
   CK(mlmcp::launch_apply(G[0], ke[0], W, nullptr, KW, R, act, true, st), "start");
   CK(vcycle(R, X), "start");
   CK(cudaMemsetAsync(W, 0, sizeof(float4) * v0, st), "memset");
   CK(cudaMemsetAsync(KW, 0, sizeof(float4) * v0, st), "memset");
-  CK(mlmcp::launch_apply(G[0], ke[0], X, nullptr, KX, GX, act, true, st), "apply");
+  CK(images(X, KX, GX), "apply");
   CK(mlmcp::launch_gram(G[0], E, V, st), "gram");
   CK(mlmcp::launch_rayleigh_ritz(E, n, c.tol, c.max_iter, true, st), "rayleigh-ritz");
-  CK(mlmcp::launch_update(G[0], E, V, st), "update");
+  CK(mlmcp::launch_update(G[0], E, V, patch, st), "update");
 
   int it = 0;
   const int check_every = 4;
@@ -280,14 +333,18 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
     CK(cudaMemsetAsync(E.count, 0, sizeof(int), st), "memset");
     // K and G images of the new X and P, recomputed (not updated by the Ritz
     // coefficients, whose single-precision drift raises the residual floor)
-    CK(mlmcp::launch_apply(G[0], ke[0], X, nullptr, KX, GX, act, true, st), "apply");
-    CK(mlmcp::launch_apply(G[0], ke[0], P, nullptr, KP, GP, act, true, st), "apply");
-    CK(mlmcp::launch_residual(G[0], E, KX, GX, R, st), "residual");
+    if (patch) {   // X's images and its residual G X - mu K X in one double-precision pass
+      CK(mlmcp::launch_apply64(G[0], ke64, X, KX, GX, R, E.mu, act, st), "apply");
+    } else {
+      CK(images(X, KX, GX), "apply");
+    }
+    CK(images(P, KP, GP), "apply");
+    if (!patch) CK(mlmcp::launch_residual(G[0], E, KX, GX, R, st), "residual");
     CK(vcycle(R, W), "v-cycle");
-    CK(mlmcp::launch_apply(G[0], ke[0], W, nullptr, KW, GW, act, true, st), "apply");
+    CK(images(W, KW, GW), "apply");
     CK(mlmcp::launch_gram(G[0], E, V, st), "gram");
     CK(mlmcp::launch_rayleigh_ritz(E, n, c.tol, c.max_iter, false, st), "rayleigh-ritz");
-    CK(mlmcp::launch_update(G[0], E, V, st), "update");
+    CK(mlmcp::launch_update(G[0], E, V, patch, st), "update");
     if (trace >= 0 && trace < n) {
       double h_mu[2], h_eta2;
       int h_act, h_it;

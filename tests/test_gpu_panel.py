@@ -168,3 +168,54 @@ def test_large_batch_is_chunked(B, ctx):
     B.mlmcp_solve_batch(ctx, [(0, 0, 500), (0, 0, 500 + n - 1)], q)
     assert abs(q[0] / qf[0] - 1.0) < RTOL and abs(q[2] / qf[2 * (n - 1)] - 1.0) < RTOL
     assert 0.0 < qf[0::2].min() and qf[0::2].max() < 400.0
+
+
+# ---------------------------------------------------------------- the thin square panel
+from workloads import PANEL_C5_4LEVEL as W5   # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx5(B):
+    h = B.mlmcp_create(B.configp_from_workload(W5))
+    yield h
+    B.mlmcp_destroy(h)
+
+
+@pytest.mark.parametrize("level,first,n", [(0, 0, 12), (1, 50, 4), (2, 9, 2), (3, 4, 1)])
+def test_thin_panel_level_pairs_match_oracle(B, ctx5, level, first, n):
+    """The 500 x 500 mm, 1 mm panel (b / t = 500) on 16^2 .. 128^2 with the 3 x 3-node
+    patch smoother: critical loads of level pairs within the stated 1e-6 of the oracle's
+    eigen-solves, in a bounded number of LOBPCG iterations."""
+    qf = np.zeros(2 * n)
+    qc = np.zeros(2 * n)
+    st = np.full(n, -1, dtype=np.int32)
+    B.mlmcp_sample_level(ctx5, level, first, n, qf, qc, st)
+    assert np.all(st == 0)
+    assert B.mlmcp_last_iters(ctx5) <= 60
+    rf, rc = P.level_pair(W5, level, np.arange(first, first + n))
+    for k in range(n):
+        assert abs(qf[2 * k] / rf[k][0] - 1.0) < RTOL, (level, k, qf[2 * k], rf[k][0])
+        if abs(rf[k][0] / W5["p_star"] - 1.0) > RTOL:
+            assert qf[2 * k + 1] == rf[k][1]
+        if level > 0:
+            assert abs(qc[2 * k] / rc[k][0] - 1.0) < RTOL
+
+
+def test_patch_and_nodal_smoothers_give_the_same_loads(B):
+    """On the paper's panel (24x8 .. 48x16, t = 6.4 mm) both smoothers precondition the
+    same eigenproblem: equal critical loads (1e-6); the patch smoother needs fewer
+    LOBPCG iterations."""
+    out, its = {}, {}
+    for sm in ("nodal", "patch"):
+        h = B.mlmcp_create(B.configp_from_workload(W, smoother=sm))
+        try:
+            q = np.zeros(2 * 6)
+            st = np.ones(6, dtype=np.int32)
+            B.mlmcp_solve_batch(h, [(1, 1, 20 + k) for k in range(6)], q, st)
+            assert np.all(st == 0)
+            out[sm] = q[0::2]
+            its[sm] = B.mlmcp_last_iters(h)
+        finally:
+            B.mlmcp_destroy(h)
+    np.testing.assert_allclose(out["patch"], out["nodal"], rtol=RTOL)
+    assert its["patch"] <= its["nodal"]

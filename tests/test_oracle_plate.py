@@ -24,7 +24,7 @@ import numpy as np
 import pytest
 
 from oracle import plate as P
-from workloads import PANEL_RM_4LEVEL as W
+from workloads import PANEL_C5_4LEVEL, PANEL_RM_4LEVEL as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -177,3 +177,29 @@ def test_soft_support_never_stiffer_than_hard():
             soft = P.solve_sample(W, nx, ny, phi, bc="soft")
             hard = P.solve_sample(W, nx, ny, phi, bc="hard")
             assert soft < hard
+
+
+def test_thin_cross_ply_panel_converges_to_mindlin_closed_form():
+    """b / t = 500: a 500 x 500 mm, 1 mm cross-ply [0/90]2s panel (D16 = D26 = 0, B = 0)
+    with the hard support; the selectively integrated Q4 does not lock, so the FE load
+    converges at O(h^2) to the Mindlin closed form (here within 1e-4 of Kirchhoff's)."""
+    w = dict(PANEL_C5_4LEVEL, plies_deg=(0, 90, 0, 90, 90, 0, 90, 0))
+    D, kgt = P.panel_stiffness(w, np.zeros(8))
+    assert abs(D[0, 2]) < 1e-9 * D[0, 0] and abs(D[1, 2]) < 1e-9 * D[0, 0]
+    ref = P.mindlin_navier(D, kgt, w["lx"], w["ly"])
+    assert ref == pytest.approx(P.kirchhoff_navier(D, w["lx"], w["ly"]), rel=2e-4)
+    err = [P.solve_sample(w, n, n, np.zeros(8), bc="hard") / ref - 1.0 for n in (16, 32, 64)]
+    assert all(e > 0 for e in err) and err[0] < 0.01
+    for a, b in zip(err, err[1:]):
+        assert 3.8 < a / b < 4.2
+
+
+def test_thin_panel_level_pair_uses_the_same_perturbations():
+    """Config of the thin panel: a level pair's coarse value is the sample's own solve on
+    the coarse mesh, and the two meshes' loads differ by little (h^2 convergence)."""
+    w = PANEL_C5_4LEVEL
+    qf, qc = P.level_pair(w, 1, [5, 6])
+    phi = P.sample_perturbations(w, 1, [5, 6])
+    for k in range(2):
+        assert qc[k][0] == pytest.approx(P.solve_mesh(w, 0, phi[k])[0], rel=1e-12)
+        assert abs(qf[k][0] / qc[k][0] - 1.0) < 0.01

@@ -94,7 +94,35 @@ PANEL_RM_4LEVEL = dict(
     max_iter=120,
 )
 
-WORKLOADS = {w["name"]: w for w in (STRIP_FP64_3LEVEL, STRIP_MIXED_5LEVEL, HEX8_MIXED_4LEVEL, PANEL_RM_4LEVEL)}
+# The thin square panel of the scope table's buckling row: 500 x 500 mm, eight plies
+# [45/-45/0/90]s of 0.125 mm (t = 1 mm, b / t = 500), each angle perturbed by N(0, 3 deg^2),
+# simply supported, meshes 16^2 .. 128^2. The ply constants are the paper's panel ply
+# (IM7-8552, Sec. 4.1; the row gives none) and the support is the hard one, as for the
+# paper's panel. At b / t = 500 the transverse shear is nearly held, so the multigrid
+# smooths with the 3 x 3-node patch smoother. p_star is the failure threshold of the
+# critical load (kN): the benchmark sets it to the 1/150 lower quantile of a seeded pilot
+# (seed 1, 4096 level-2 samples); the value here is a nominal one near that quantile.
+PANEL_C5_4LEVEL = dict(
+    name="panel-rm-q4-500mm-4level",
+    lx=500.0, ly=500.0,
+    nx0=16, ny0=16,
+    levels=4,
+    E11=130000.0, E22=9250.0, G12=5130.0, nu12=0.36,   # MPa
+    G13=5130.0, k_shear=5.0 / 6.0,
+    plies_deg=(45.0, -45.0, 0.0, 90.0, 90.0, 0.0, -45.0, 45.0),
+    t_ply=0.125,                # mm
+    ply_std_deg=3.0,
+    bc="hard",
+    p_star=0.41,                # kN (nominal; see above)
+    seed=0,
+    n_per_level=(4096, 1024, 256, 64),
+    tol=1e-4,
+    max_iter=120,
+    smoother="patch",
+)
+
+WORKLOADS = {w["name"]: w for w in (STRIP_FP64_3LEVEL, STRIP_MIXED_5LEVEL, HEX8_MIXED_4LEVEL, PANEL_RM_4LEVEL,
+                                    PANEL_C5_4LEVEL)}
 
 
 def mesh_dims(cfg, level):
