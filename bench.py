@@ -853,6 +853,81 @@ def run_panel(B, steps=2, warmup=1, parity=True, W=None, pilot=False):
             B.mlmcp_destroy(ctx)
 
 
+def run_panel_serving(B, W, threshold, seconds=3.0, load=0.5):
+    """The request loop on the thin panel: SELECTIVE requests of levels 0..3 in the
+    proportions of the MLMC level counts, failure P < threshold (the pilot's 1/150 lower
+    quantile); capacity from saturating bursts (median of five after a warm-up), then
+    Poisson arrivals at `load` of it for `seconds`: level-samples/s, latency p50/p99,
+    solves per request and the failure-probability estimates."""
+    counts = W["n_per_level"]
+    levels = list(range(W["levels"]))
+    srv = B.mlmcp_server_create(B.configp_from_workload(W, p_star=threshold), workers=4, max_batch=4096,
+                                hbm_budget_bytes=100e9, threshold=threshold, sr_factor=2.0, eps_rel=1e-6)
+    g = np.random.default_rng(4)
+    p_level = np.array(counts, dtype=float) / sum(counts)
+    next_id = [0] * len(levels)
+    tag = [0]
+
+    def make(n):
+        out = []
+        for l in g.choice(levels, size=n, p=p_level):
+            out.append((1, int(l), 0, next_id[l], tag[0]))
+            next_id[l] += 1
+            tag[0] += 1
+        return out
+
+    try:
+        results, caps = [], []
+        for b in range(6):
+            burst = make(2048)
+            t0 = time.perf_counter()
+            B.mlmc_server_submit(srv, burst)
+            B.mlmc_server_drain(srv, 600e3)
+            if b > 0:
+                caps.append(len(burst) / (time.perf_counter() - t0))
+            results += drain_all_of(B, srv)
+        cap = float(np.median(caps))
+        n_burst = tag[0]
+        rate = load * cap
+        n = int(rate * seconds)
+        arrivals = np.cumsum(g.exponential(1.0 / rate, size=n))
+        reqs = make(n)
+        t0 = time.perf_counter()
+        k = 0
+        while k < n:
+            now = time.perf_counter() - t0
+            j = int(np.searchsorted(arrivals, now, side="right"))
+            if j > k:
+                B.mlmc_server_submit(srv, reqs[k:j])
+                k = j
+            else:
+                time.sleep(min(0.001, max(0.0, arrivals[k] - now)))
+        B.mlmc_server_drain(srv, 600e3)
+        wall = time.perf_counter() - t0
+        stream = [r for r in drain_all_of(B, srv) if r["tag"] >= n_burst]
+        counters = B.mlmc_server_counters(srv)
+    finally:
+        B.mlmc_server_destroy(srv)
+    lat = np.array([r["latency_ms"] for r in stream])
+    ok = [r for r in results + stream if r["status"] == 0]
+    est_ml, _, _ = B.mlmc_failure_estimate(ok, threshold, k=1, two_level=False)
+    est_2l, _, _ = B.mlmc_failure_estimate(ok, threshold, k=1, two_level=True)
+    return {"workload": "selective refinement, P(critical load < 1/150 lower quantile of a seed-1 pilot), "
+                        "levels 0-3 in MLMC proportions, 4 workers, 100 GB budget",
+            "threshold_kn": threshold,
+            "capacity_requests_per_s": round(cap, 1), "capacity_bursts_per_s": [round(c, 1) for c in caps],
+            "offered_requests_per_s": round(rate, 1),
+            "value": round(len(stream) / wall, 1),
+            "unit": "level-samples/s (Poisson arrivals at %.0f%% of capacity)" % (100 * load),
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                           "p99": round(float(np.percentile(lat, 99)), 3)},
+            "solves_per_request": round(sum(r["solves"] for r in ok) / max(1, len(ok)), 3),
+            "stopped_early": round(sum(r["stop_level"] < r["level"] for r in ok) / max(1, len(ok)), 4),
+            "failure_probability": {"multilevel": est_ml, "two_level": est_2l,
+                                    "estimator": "biased (x + k)/(N + k), k = 1, trinomial moments"},
+            "failed_requests": len(results) + len(stream) - len(ok), "batches": counters["batches"]}
+
+
 def run_panel_case():
     """One step of the buckling panel (every level's samples), untimed: for profilers."""
     import torch
@@ -957,6 +1032,8 @@ def main():
         from workloads import PANEL_C5_4LEVEL
         out["panel"] = run_panel(B, parity=not a.no_cpu_baseline)
         out["panel_thin"] = run_panel(B, parity=not a.no_cpu_baseline, W=PANEL_C5_4LEVEL, pilot=True)
+        if a.serving:
+            out["panel_thin"]["serving"] = run_panel_serving(B, PANEL_C5_4LEVEL, out["panel_thin"]["p_star_kn"])
     if rank == 0 and out is not None:
         if world == 1 and not a.no_cpu_baseline and out.get("_gpu_q") is not None:
             cores = os.cpu_count() or 1

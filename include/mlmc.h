@@ -354,6 +354,7 @@ typedef struct {
   int32_t solves;       /* meshes solved for this request */
   double latency_ms;    /* from submission to completion */
   int32_t pcg_iterations[MLMC_SR_MAX_LEVELS];   /* PCG iterations of each solve, in order */
+  int32_t q_mesh0;      /* SELECTIVE: failure indicator of lambda_0 (the two-level estimator's) */
 } mlmc_result;
 
 typedef struct {
@@ -379,9 +380,9 @@ typedef struct {
    two_level == 0: the multilevel sum over the levels present,
      sum_l E[Y_l], Y_l = Q_l - Q_{l-1} (Y_0 = Q_0);
    two_level != 0: E[Q] ~ E[Q_0] + E[Y_{L,0}] with Q_0 from the level-0 results and
-     Y_{L,0} = Q_L - 1(lambda_0 > threshold) from the results of the highest level L
-     present (lambda_0 the sample's mesh-0 value, solved first by every SELECTIVE
-     request).
+     Y_{L,0} = Q_L - q_mesh0 from the results of the highest level L present (q_mesh0
+     the failure indicator of the sample's mesh-0 value lambda_0, solved first by every
+     SELECTIVE request; `threshold` is not used).
    Results with a nonzero status are skipped. mean[] and var[] (nullable, length
    MLMC_SR_MAX_LEVELS) receive each term's E and V (indexed by level; in the
    two-level form index 0 holds Q_0 and index L holds Y_{L,0}). */

@@ -112,6 +112,21 @@ mlmc_status mlmcp_apply(mlmcp_ctx* ctx, int32_t mesh_level, int32_t level, uint6
 /* LOBPCG iterations of the last solve (maximum over samples). */
 mlmc_status mlmcp_last_iters(mlmcp_ctx* ctx, int32_t* iters);
 
+/* ---- serving (the request loop of mlmc.h's serving section, for panel samples) ----
+   Starts a request loop whose workers solve panel samples (each worker one mlmcp
+   context on its own stream); mlmc_server_submit / poll / drain / counters / destroy /
+   last_error then work as for the strip. SOLVE requests return (P, indicator) on their
+   mesh; a SELECTIVE request runs Algorithm 2 (Sec. 2.4) on the critical load P
+   (quantity 0): from mesh j >= 1 it stops at the first j with
+   |P_j - p*| >= sr_factor max(eps_rel |P_j|, |P_j - P_{j-1}| / (m^alpha - 1)), and its
+   failure indicators are 1(P < p*) (Sec. 4.2's Q(lambda)), p* = scfg->threshold (kN).
+   mlmc_m, mlmc_alpha: the convergence constants of the bias estimate (e.g. 4 and 1).
+   Every solve starts from scratch (carry_iterates is ignored); a result's
+   pcg_iterations hold the LOBPCG iterations of the slowest sample of its batch. The
+   workers' solver workspace is stream-ordered device allocation per batch. */
+mlmc_status mlmcp_server_create(const mlmcp_config* cfg, const mlmc_server_config* scfg, double mlmc_m,
+                                double mlmc_alpha, mlmc_server** out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -184,10 +184,12 @@ def sr_stops(lam, j, level, threshold, m, alpha, sr_factor, eps_rel):
 
 
 def selective_refinement(cfg, level, sample_id, threshold, m=4.0, alpha=1.0, sr_factor=2.0, eps_rel=1e-6,
-                         basis=None, solve=None):
+                         basis=None, solve=None, below=False):
     """Algorithm 2 for one sample: (J, [lambda_0 .. lambda_J], lambda_l, lambda_{l-1}, Q_l, Q_{l-1}).
 
     `solve(mesh) -> lambda` defaults to the FE solve of this module on the sample's xi.
+    Failure is lambda > threshold, or lambda < threshold with below (a buckling load
+    under its threshold, Sec. 4.2's Q(lambda)); the stopping test is the same either way.
     """
     if solve is None:
         basis = basis or Basis(cfg)
@@ -205,8 +207,9 @@ def selective_refinement(cfg, level, sample_id, threshold, m=4.0, alpha=1.0, sr_
         j += 1
     lam_fine = lam[j]
     lam_coarse = lam[min(j, level - 1)] if level >= 1 else 0.0
-    q_fine = 1 if lam_fine > threshold else 0
-    q_coarse = (1 if lam_coarse > threshold else 0) if level >= 1 else 0
+    fails = (lambda v: v < threshold) if below else (lambda v: v > threshold)
+    q_fine = 1 if fails(lam_fine) else 0
+    q_coarse = (1 if fails(lam_coarse) else 0) if level >= 1 else 0
     return j, lam, lam_fine, lam_coarse, q_fine, q_coarse
 
 

@@ -74,7 +74,7 @@ class mlmc_result(ctypes.Structure):
                 ("lambda_", ctypes.c_double * SR_MAX_LEVELS), ("lambda_fine", ctypes.c_double),
                 ("lambda_coarse", ctypes.c_double), ("q_fine", ctypes.c_int32), ("q_coarse", ctypes.c_int32),
                 ("solves", ctypes.c_int32), ("latency_ms", ctypes.c_double),
-                ("pcg_iterations", ctypes.c_int32 * SR_MAX_LEVELS)]
+                ("pcg_iterations", ctypes.c_int32 * SR_MAX_LEVELS), ("q_mesh0", ctypes.c_int32)]
 
     def as_dict(self):
         return dict(tag=self.tag, kind=self.kind, level=self.level, mesh_level=self.mesh_level,
@@ -82,7 +82,8 @@ class mlmc_result(ctypes.Structure):
                     lambdas=list(self.lambda_[:self.stop_level + 1]), lambda_fine=self.lambda_fine,
                     lambda_coarse=self.lambda_coarse, q_fine=self.q_fine, q_coarse=self.q_coarse,
                     solves=self.solves, latency_ms=self.latency_ms,
-                    pcg_iterations=list(self.pcg_iterations[:min(self.solves, SR_MAX_LEVELS)]))
+                    pcg_iterations=list(self.pcg_iterations[:min(self.solves, SR_MAX_LEVELS)]),
+                    q_mesh0=self.q_mesh0)
 
 
 class mlmc_server_config(ctypes.Structure):
@@ -445,6 +446,7 @@ def mlmc_failure_estimate(results, threshold, k=1, two_level=False):
         for j, v in enumerate(r["lambdas"]):
             a.lambda_[j] = v
         a.lambda_fine, a.lambda_coarse, a.q_fine, a.q_coarse = r["lambda_fine"], r["lambda_coarse"], r["q_fine"], r["q_coarse"]
+        a.q_mesh0 = int(r.get("q_mesh0", 1 if r["lambdas"] and r["lambdas"][0] > threshold else 0))
     est = ctypes.c_double()
     mean = (ctypes.c_double * SR_MAX_LEVELS)()
     var = (ctypes.c_double * SR_MAX_LEVELS)()
@@ -621,6 +623,8 @@ def libp():
             "mlmcp_laminate": (I32, [P, I32, U64, I64, P, P]),
             "mlmcp_apply": (I32, [P, I32, I32, U64, I64, P, P, P]),
             "mlmcp_last_iters": (I32, [P, P]),
+            "mlmcp_server_create": (I32, [ctypes.POINTER(mlmcp_config), ctypes.POINTER(mlmc_server_config),
+                                          ctypes.c_double, ctypes.c_double, ctypes.POINTER(P)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -706,3 +710,19 @@ def mlmcp_last_iters(ctx):
     it = ctypes.c_int32()
     _checkp(ctx, libp().mlmcp_last_iters(ctx, ctypes.byref(it)))
     return it.value
+
+
+def mlmcp_server_create(cfg, workers=2, max_batch=4096, hbm_budget_bytes=8e9, threshold=0.0, sr_factor=2.0,
+                        eps_rel=1e-6, mlmc_m=4.0, mlmc_alpha=1.0):
+    """A request loop over panel samples (mlmcp_config cfg); the other mlmc_server_*
+    calls of this module work on it. SELECTIVE requests refine on the critical load P
+    (kN) and fail below `threshold`."""
+    L = libp()
+    sc = mlmc_server_config(workers, max_batch, float(hbm_budget_bytes), float(threshold), float(sr_factor),
+                            float(eps_rel), 0)
+    srv = ctypes.c_void_p()
+    st = L.mlmcp_server_create(ctypes.byref(cfg), ctypes.byref(sc), float(mlmc_m), float(mlmc_alpha),
+                               ctypes.byref(srv))
+    if st != 0:
+        raise MLMCError(st, L.mlmc_server_last_error(None).decode())
+    return srv

@@ -429,7 +429,8 @@ __global__ void __launch_bounds__(kThreads) k_patch_setup(PGrid g, const float* 
 __global__ void __launch_bounds__(kThreads) k_patch_color(PGrid g, const float* __restrict__ ke,
                                                           const float* __restrict__ pinv, const float4* __restrict__ b,
                                                           const float4* __restrict__ xin, float4* __restrict__ xout,
-                                                          int sx, int sy, const int* __restrict__ active) {
+                                                          int sx, int sy, int pinv_per_sample,
+                                                          const int* __restrict__ active) {
   const int e = blockIdx.y, s = e >> g.cshift;
   if (active && !active[s]) return;
   __shared__ float K[144];
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(kThreads) k_patch_color(PGrid g, const float* 
   }
   __syncwarp();
   if (lane < kPatchDofs) {
-    const float* M = pinv + ((size_t)s * kPatchTypes + type) * kPatchDofs * kPatchDofs;
+    const float* M = pinv + ((size_t)(pinv_per_sample ? s : 0) * kPatchTypes + type) * kPatchDofs * kPatchDofs;
     float d = 0.f;
 #pragma unroll 9
     for (int q = 0; q < kPatchDofs; ++q) d += M[q * kPatchDofs + lane] * rs[warp][q];
@@ -1028,13 +1029,14 @@ cudaError_t launch_patch_setup(const PGrid& g, const float* ke, int n_samples, f
   return cudaGetLastError();
 }
 
-cudaError_t launch_patch_color(const PGrid& g, const float* ke, const float* pinv, const float4* b, const float4* in,
-                               float4* out, int sx, int sy, const int* active, cudaStream_t st) {
+cudaError_t launch_patch_color(const PGrid& g, const float* ke, const float* pinv, bool pinv_per_sample,
+                               const float4* b, const float4* in, float4* out, int sx, int sy, const int* active,
+                               cudaStream_t st) {
   const int fx = sx == 2 ? -1 : sx, fy = sy == 2 ? -1 : sy;
   const int patches = ((g.nx + 1 - fx) / 3 + 1) * ((g.ny + 1 - fy) / 3 + 1);
   const int warps = kThreads / 32;
   k_patch_color<<<dim3((patches + warps - 1) / warps, g.nb), kThreads, 0, st>>>(g, ke, pinv, b, in, out, sx, sy,
-                                                                               active);
+                                                                               pinv_per_sample ? 1 : 0, active);
   return cudaGetLastError();
 }
 

@@ -67,9 +67,14 @@ cudaError_t launch_prolong(const PGrid& fine, const PGrid& coarse, const float4*
 constexpr int kPatchTypes = 49;
 constexpr int kPatchDofs = 27;
 cudaError_t launch_patch_setup(const PGrid& g, const float* ke, int n_samples, float* pinv, cudaStream_t st);
-// one colour step (in null: zero); in and out are different buffers
-cudaError_t launch_patch_color(const PGrid& g, const float* ke, const float* pinv, const float4* b, const float4* in,
-                               float4* out, int sx, int sy, const int* active, cudaStream_t st);
+// one colour step (in null: zero); in and out are different buffers. The residual uses
+// each sample's own element matrix ke; the patch inverses are each sample's
+// (pinv_per_sample) or one set shared by all samples (those of the pristine laminate:
+// the perturbed samples' patches differ from it by a few per cent, which a smoother
+// tolerates, and the setup is once per mesh instead of per sample)
+cudaError_t launch_patch_color(const PGrid& g, const float* ke, const float* pinv, bool pinv_per_sample,
+                               const float4* b, const float4* in, float4* out, int sx, int sy, const int* active,
+                               cudaStream_t st);
 
 // Coarsest mesh: per-sample dense inverse of K on the free DOFs (free[k] = 4 node + c)
 cudaError_t launch_coarse_setup(const PGrid& g, const float* ke, int n_samples, const int* free, int nf, float* ainv,

@@ -84,6 +84,9 @@ struct mlmcp_ctx {
   int last_iters = 0;
   double tol = 1e-4;
   int max_iter = 120;
+  // patch smoother: the pristine laminate's patch inverses per mesh size (nx, ny), made
+  // on first use and shared by every sample and solve
+  std::vector<std::pair<std::pair<int, int>, float*>> patch_cache;
 
   mlmc_status fail(mlmc_status s, const std::string& m) {
     err = m;
@@ -106,6 +109,7 @@ struct mlmcp_ctx {
     return g;
   }
   ~mlmcp_ctx() {
+    for (auto& kv : patch_cache) cudaFree(kv.second);
     for (int* p : free_dev) cudaFree(p);
     if (acc_dev) cudaFree(acc_dev);
   }
@@ -155,6 +159,32 @@ mlmc_status draw_xi(mlmcp_ctx& c, int level, uint64_t first_id, const int* level
   return MLMC_OK;
 }
 
+// The patch smoother's inverses on mesh m, built once from the pristine laminate (no
+// perturbation) and kept in the context.
+mlmc_status patch_inverses(mlmcp_ctx& c, const Mesh& m, float** out) {
+  for (auto& kv : c.patch_cache)
+    if (kv.first.first == m.nx && kv.first.second == m.ny) {
+      *out = kv.second;
+      return MLMC_OK;
+    }
+  Scratch sc{c.st};
+  double* xi0 = sc.take<double>(c.cfg.n_plies);
+  double* dstar = sc.take<double>(6);
+  double* kgt = sc.take<double>(1);
+  float* ke = sc.take<float>(144);
+  CK(sc.err, "alloc");
+  float* pinv = nullptr;
+  CK(cudaMalloc(&pinv, sizeof(float) * mlmcp::kPatchTypes * mlmcp::kPatchDofs * mlmcp::kPatchDofs), "alloc");
+  c.patch_cache.push_back({{m.nx, m.ny}, pinv});
+  CK(cudaMemsetAsync(xi0, 0, sizeof(double) * c.cfg.n_plies, c.st), "memset");
+  CK(mlmcp::launch_laminate(c.lam, xi0, 1, dstar, kgt, c.st), "laminate");
+  CK(mlmcp::launch_element_matrices(dstar, kgt, 1, c.cfg.lx / m.nx, c.cfg.ly / m.ny, ke, nullptr, c.st), "element");
+  CK(mlmcp::launch_patch_setup(c.grid(m, 1, 0), ke, 1, pinv, c.st), "patch setup");
+  CK(cudaStreamSynchronize(c.st), "patch setup");
+  *out = pinv;
+  return MLMC_OK;
+}
+
 // n samples (perturbations xi, device [n][plies]) on MLMC mesh m; q [n][2], status [n]
 // (device)
 mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int* status) {
@@ -197,13 +227,12 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
        "element matrices");
   CK(mlmcp::launch_coarse_setup(c.grid(H[L - 1], n, 0), ke[L - 1], n, c.free_dev[m], nf, ainv, st), "coarse setup");
   const bool patch = c.cfg.smoother == 1;
-  std::vector<float*> pinv(L, nullptr);   // patch smoother: inverses per smoothed mesh
+  std::vector<float*> pinv(L, nullptr);   // patch smoother: shared inverses per smoothed mesh
   if (patch) {
-    for (int l = 0; l + 1 < L; ++l) pinv[l] = sc.take<float>((size_t)n * mlmcp::kPatchTypes * mlmcp::kPatchDofs *
-                                                             mlmcp::kPatchDofs);
-    CK(sc.err, "alloc");
-    for (int l = 0; l + 1 < L; ++l)
-      CK(mlmcp::launch_patch_setup(c.grid(H[l], n, 0), ke[l], n, pinv[l], st), "patch setup");
+    for (int l = 0; l + 1 < L; ++l) {
+      const mlmc_status ps = patch_inverses(c, H[l], &pinv[l]);
+      if (ps != MLMC_OK) return ps;
+    }
   }
 
   // multigrid buffers (batch of nb entries) and the LOBPCG sets
@@ -256,7 +285,7 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
     for (int k = 0; k < 9 && e == cudaSuccess; ++k) {
       const int col = reversed ? 8 - k : k;
       float4* o = k == 8 ? last : ((k & 1) ? s2 : s1);
-      e = mlmcp::launch_patch_color(G[l], ke[l], pinv[l], b, in, o, col % 3, col / 3, act, st);
+      e = mlmcp::launch_patch_color(G[l], ke[l], pinv[l], false, b, in, o, col % 3, col / 3, act, st);
       in = o;
     }
     return e;

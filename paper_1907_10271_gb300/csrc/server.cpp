@@ -1,5 +1,7 @@
 // Request loop with continuous batching on one GPU, and the selective refinement of
-// Sec. 2.4 (Algorithm 2) as a request kind.
+// Sec. 2.4 (Algorithm 2) as a request kind, for the strip (mlmc.h) and the buckling
+// panel (mlmc_panel.h) alike: a backend supplies the per-worker contexts, the batch
+// solve, the footprint of a solve and the failure quantity.
 //
 // Host side only: a FIFO of pending requests (escalations of selective-refinement
 // samples go to its front), `workers` threads each owning an mlmc context on its own
@@ -18,11 +20,13 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
 
+#include "../../include/mlmc_panel.h"
 #include "engine.h"
 
 namespace {
@@ -63,12 +67,107 @@ struct IteratePool {
   }
 };
 
+// What a request loop needs from an engine.
+struct Backend {
+  virtual ~Backend() {}
+  virtual int levels() const = 0;
+  virtual double m_alpha_minus_one() const = 0;   // m^alpha - 1 of the bias estimate
+  virtual int quantity() const = 0;               // index of the selective-refinement quantity
+  virtual bool fails_below() const = 0;           // failure is lambda < lambda* (else >)
+  virtual double footprint(int mesh) const = 0;   // device bytes of one solve on mesh
+  virtual bool carries() const = 0;               // starting iterates across escalations
+  virtual int64_t iterate_values(int mesh) const = 0;
+  virtual mlmc_status add_worker(cudaStream_t st, double share, std::string& msg) = 0;
+  // one batch on worker w; iters (host) per item; guess / out: see solve_batch_carry
+  virtual mlmc_status solve(int w, const mlmc_item* items, int64_t n, double* q, int32_t* status,
+                            const double* const* guess, double* const* out, int32_t* iters, std::string& msg) = 0;
+};
+
+struct StripBackend : Backend {
+  mlmc_config cfg;
+  std::vector<mlmc_ctx*> ctx;
+  explicit StripBackend(const mlmc_config& c) : cfg(c) {}
+  ~StripBackend() override {
+    for (auto* c : ctx) mlmc_destroy(c);
+  }
+  int levels() const override { return cfg.levels; }
+  double m_alpha_minus_one() const override { return std::pow(cfg.mlmc_m, cfg.mlmc_alpha) - 1.0; }
+  int quantity() const override { return 1; }   // the centroid fibre stress
+  bool fails_below() const override { return false; }
+  double footprint(int mesh) const override { return mlmc::solve_bytes_per_sample(cfg, mesh); }
+  bool carries() const override { return true; }
+  int64_t iterate_values(int mesh) const override { return mlmc::iterate_values(cfg, mesh); }
+  mlmc_status add_worker(cudaStream_t st, double share, std::string& msg) override {
+    mlmc_ctx* c = nullptr;
+    mlmc_status e = mlmc_create(&cfg, st, &c);
+    if (e != MLMC_OK) {
+      msg = std::string("worker context: ") + mlmc_last_error(nullptr);
+      return e;
+    }
+    ctx.push_back(c);
+    mlmc::set_graph_replay(c, false);   // every batch differs: no graph to reuse
+    // the share, split like the footprint estimate: solver workspace and batch buffers
+    e = mlmc::reserve_workspace(c, (size_t)(0.85 * share), (size_t)(0.15 * share));
+    if (e != MLMC_OK) msg = std::string("worker workspace: ") + mlmc_last_error(c);
+    return e;
+  }
+  mlmc_status solve(int w, const mlmc_item* items, int64_t n, double* q, int32_t* status, const double* const* guess,
+                    double* const* out, int32_t* iters, std::string& msg) override {
+    const mlmc_status s = mlmc::solve_batch_carry(ctx[w], items, n, q, status, guess, out, iters);
+    if (s != MLMC_OK) msg = mlmc_last_error(ctx[w]);
+    return s;
+  }
+};
+
+// The buckling panel: the failure quantity is the critical load (quantity 0), failing
+// below its threshold (Sec. 4.2); solves from scratch (no carried iterates); the
+// engine's workspace is stream-ordered allocation per batch.
+struct PanelBackend : Backend {
+  mlmcp_config cfg;
+  double m = 4.0, alpha = 1.0;
+  std::vector<mlmcp_ctx*> ctx;
+  PanelBackend(const mlmcp_config& c, double m_, double a_) : cfg(c), m(m_), alpha(a_) {}
+  ~PanelBackend() override {
+    for (auto* c : ctx) mlmcp_destroy(c);
+  }
+  int levels() const override { return cfg.levels; }
+  double m_alpha_minus_one() const override { return std::pow(m, alpha) - 1.0; }
+  int quantity() const override { return 0; }
+  bool fails_below() const override { return true; }
+  double footprint(int mesh) const override {
+    // about 24 vectors of two columns of float4 per node over the hierarchy, the element
+    // matrices and the coarsest inverse
+    const double nodes = (double)((cfg.nx0 << mesh) + 1) * ((cfg.ny0 << mesh) + 1);
+    return nodes * 2.0 * 16.0 * 24.0 + 200.0e3;
+  }
+  bool carries() const override { return false; }
+  int64_t iterate_values(int) const override { return 0; }
+  mlmc_status add_worker(cudaStream_t st, double, std::string& msg) override {
+    mlmcp_ctx* c = nullptr;
+    const mlmc_status e = mlmcp_create(&cfg, st, &c);
+    if (e != MLMC_OK) {
+      msg = std::string("worker context: ") + mlmcp_last_error(nullptr);
+      return e;
+    }
+    ctx.push_back(c);
+    return MLMC_OK;
+  }
+  mlmc_status solve(int w, const mlmc_item* items, int64_t n, double* q, int32_t* status, const double* const*,
+                    double* const*, int32_t* iters, std::string& msg) override {
+    const mlmc_status s = mlmcp_solve_batch(ctx[w], items, n, q, status);
+    if (s != MLMC_OK) msg = mlmcp_last_error(ctx[w]);
+    int32_t it = 0;
+    mlmcp_last_iters(ctx[w], &it);
+    for (int64_t k = 0; k < n; ++k) iters[k] = it;   // the batch's slowest sample
+    return s;
+  }
+};
+
 }  // namespace
 
 struct mlmc_server {
-  mlmc_config cfg;
+  std::unique_ptr<Backend> be;
   mlmc_server_config scfg;
-  std::vector<mlmc_ctx*> ctx;
   std::vector<cudaStream_t> streams;
   std::vector<std::thread> threads;
   std::mutex mu;
@@ -109,10 +208,11 @@ struct mlmc_server {
       for (int j = 0; j <= stop_level; ++j) r.lambda[j] = p.lambda[j];
       const int l = p.req.level;
       r.lambda_fine = p.lambda[stop_level];
-      r.q_fine = r.lambda_fine > scfg.threshold ? 1 : 0;
+      r.q_fine = fails(r.lambda_fine) ? 1 : 0;
+      r.q_mesh0 = fails(p.lambda[0]) ? 1 : 0;
       if (l >= 1) {
         r.lambda_coarse = p.lambda[std::min(stop_level, l - 1)];
-        r.q_coarse = r.lambda_coarse > scfg.threshold ? 1 : 0;
+        r.q_coarse = fails(r.lambda_coarse) ? 1 : 0;
       }
     }
     r.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - p.t0).count();
@@ -120,12 +220,14 @@ struct mlmc_server {
     --outstanding;
   }
 
+  bool fails(double lambda) const { return be->fails_below() ? lambda < scfg.threshold : lambda > scfg.threshold; }
+
   // Stopping test of a selective-refinement sample after its solve on mesh j.
   bool sr_stops(const Pending& p, int j) const {
     if (j >= p.req.level) return true;
     if (j < 1) return false;   // no bias estimate before two meshes
     const double lj = p.lambda[j], lp = p.lambda[j - 1];
-    const double bias = std::fabs(lj - lp) / (std::pow(cfg.mlmc_m, cfg.mlmc_alpha) - 1.0);
+    const double bias = std::fabs(lj - lp) / be->m_alpha_minus_one();
     const double bound = scfg.sr_factor * std::max(scfg.eps_rel * std::fabs(lj), bias);
     return std::fabs(lj - scfg.threshold) >= bound;
   }
@@ -148,7 +250,7 @@ struct mlmc_server {
         cv_work.wait(lk, [&] { return stop || !queue.empty(); });
         if (stop) return;
         while (!queue.empty() && (int64_t)batch.size() < scfg.max_batch) {
-          const double b = mlmc::solve_bytes_per_sample(cfg, mesh_of(queue.front()));
+          const double b = be->footprint(mesh_of(queue.front()));
           if (batch.empty() && b > share) {   // can never fit
             Pending p = queue.front();
             queue.pop_front();
@@ -183,9 +285,10 @@ struct mlmc_server {
       q.assign(2 * batch.size(), 0.0);
       st.assign(batch.size(), 0);
       its.assign(batch.size(), 0);
-      const mlmc_status s = mlmc::solve_batch_carry(ctx[w], items.data(), (int64_t)items.size(), q.data(), st.data(),
-                                                    guess.data(), outp.data(), its.data());
-      if (s != MLMC_OK) record_error(mlmc_last_error(ctx[w]));
+      std::string msg;
+      const mlmc_status s = be->solve(w, items.data(), (int64_t)items.size(), q.data(), st.data(), guess.data(),
+                                      outp.data(), its.data(), msg);
+      if (s != MLMC_OK) record_error(msg);
       {
         std::lock_guard<std::mutex> g(mu);
         in_flight -= bytes;
@@ -207,7 +310,7 @@ struct mlmc_server {
             continue;
           }
           const int j = p.mesh;
-          p.lambda[j] = q[2 * k + 1];
+          p.lambda[j] = q[2 * k + be->quantity()];
           if (sr_stops(p, j)) {
             if (p.out >= 0) pool.give(j, p.out);
             p.out = -1;
@@ -232,17 +335,17 @@ namespace {
 std::string g_server_error;
 }
 
-extern "C" {
+namespace {
 
-mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config* scfg, mlmc_server** out) {
-  if (!cfg || !scfg || !out) return MLMC_ERR_INVALID_ARG;
-  *out = nullptr;
+// Common part of the two constructors: checks, the iterate pool (backends that carry),
+// streams, worker contexts and threads.
+mlmc_status start_server(std::unique_ptr<Backend> be, const mlmc_server_config* scfg, mlmc_server** out) {
   if (scfg->workers < 1 || scfg->workers > 64 || scfg->max_batch < 1 || !(scfg->hbm_budget_bytes > 0) ||
-      !(scfg->sr_factor >= 1.0) || !(scfg->eps_rel >= 0.0) || cfg->levels > MLMC_SR_MAX_LEVELS) {
+      !(scfg->sr_factor >= 1.0) || !(scfg->eps_rel >= 0.0) || be->levels() > MLMC_SR_MAX_LEVELS) {
     g_server_error = "bad server configuration";
     return MLMC_ERR_INVALID_ARG;
   }
-  if (!(cfg->mlmc_m > 1.0) || !(cfg->mlmc_alpha > 0.0)) {
+  if (!(be->m_alpha_minus_one() > 0.0)) {
     g_server_error = "selective refinement needs mlmc_m > 1 and mlmc_alpha > 0";
     return MLMC_ERR_INVALID_ARG;
   }
@@ -251,17 +354,18 @@ mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config*
     return MLMC_ERR_INVALID_ARG;
   }
   mlmc_server* s = new mlmc_server();
-  s->cfg = *cfg;
+  s->be = std::move(be);
   s->scfg = *scfg;
   cudaGetDevice(&s->device);
   // carried iterates: 1/8 of the budget, split evenly over the meshes a sample can
   // escalate from (0 .. levels - 2), at most four slots per request a batch holds
   double pool_bytes = 0.0;
-  if (scfg->carry_iterates && cfg->levels > 1) {
-    const int meshes = cfg->levels - 1;
+  const int levels = s->be->levels();
+  if (scfg->carry_iterates && s->be->carries() && levels > 1) {
+    const int meshes = levels - 1;
     const double per_mesh = scfg->hbm_budget_bytes / 8.0 / meshes;
     for (int m = 0; m < meshes; ++m) {
-      const int64_t vals = mlmc::iterate_values(*cfg, m);
+      const int64_t vals = s->be->iterate_values(m);
       const int64_t slots = std::min<int64_t>((int64_t)(per_mesh / (8.0 * vals)), 4 * scfg->max_batch * scfg->workers);
       double* base = nullptr;
       if (slots > 0 && cudaMalloc(&base, sizeof(double) * vals * slots) != cudaSuccess) {
@@ -281,7 +385,6 @@ mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config*
   s->share = (scfg->hbm_budget_bytes - pool_bytes) / scfg->workers;
   for (int w = 0; w < scfg->workers; ++w) {
     cudaStream_t st = nullptr;
-    mlmc_ctx* c = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       g_server_error = "stream creation failed";
@@ -289,18 +392,10 @@ mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config*
       return MLMC_ERR_CUDA;
     }
     s->streams.push_back(st);
-    mlmc_status e = mlmc_create(cfg, st, &c);
+    std::string msg;
+    const mlmc_status e = s->be->add_worker(st, s->share, msg);
     if (e != MLMC_OK) {
-      g_server_error = std::string("worker context: ") + mlmc_last_error(nullptr);
-      mlmc_server_destroy(s);
-      return e;
-    }
-    s->ctx.push_back(c);
-    mlmc::set_graph_replay(c, false);   // every batch differs: no graph to reuse
-    // the share, split like the footprint estimate: solver workspace and batch buffers
-    e = mlmc::reserve_workspace(c, (size_t)(0.85 * s->share), (size_t)(0.15 * s->share));
-    if (e != MLMC_OK) {
-      g_server_error = std::string("worker workspace: ") + mlmc_last_error(c);
+      g_server_error = msg;
       mlmc_server_destroy(s);
       return e;
     }
@@ -310,13 +405,30 @@ mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config*
   return MLMC_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+mlmc_status mlmc_server_create(const mlmc_config* cfg, const mlmc_server_config* scfg, mlmc_server** out) {
+  if (!cfg || !scfg || !out) return MLMC_ERR_INVALID_ARG;
+  *out = nullptr;
+  return start_server(std::unique_ptr<Backend>(new StripBackend(*cfg)), scfg, out);
+}
+
+mlmc_status mlmcp_server_create(const mlmcp_config* cfg, const mlmc_server_config* scfg, double mlmc_m,
+                                double mlmc_alpha, mlmc_server** out) {
+  if (!cfg || !scfg || !out) return MLMC_ERR_INVALID_ARG;
+  *out = nullptr;
+  return start_server(std::unique_ptr<Backend>(new PanelBackend(*cfg, mlmc_m, mlmc_alpha)), scfg, out);
+}
+
 mlmc_status mlmc_server_submit(mlmc_server* s, const mlmc_request* reqs, int64_t n) {
   if (!s || n < 0 || (n > 0 && !reqs)) return MLMC_ERR_INVALID_ARG;
   for (int64_t k = 0; k < n; ++k) {
     const mlmc_request& r = reqs[k];
-    const bool ok = r.level >= 0 && r.level < s->cfg.levels &&
-                    (r.kind == MLMC_REQ_SELECTIVE ||
-                     (r.kind == MLMC_REQ_SOLVE && r.mesh_level >= 0 && r.mesh_level < s->cfg.levels));
+    const int L = s->be->levels();
+    const bool ok = r.level >= 0 && r.level < L &&
+                    (r.kind == MLMC_REQ_SELECTIVE || (r.kind == MLMC_REQ_SOLVE && r.mesh_level >= 0 && r.mesh_level < L));
     if (!ok) {
       s->record_error("request with an invalid kind, level or mesh");
       return MLMC_ERR_INVALID_ARG;
@@ -374,7 +486,7 @@ void mlmc_server_destroy(mlmc_server* s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->threads) t.join();
-  for (auto* c : s->ctx) mlmc_destroy(c);
+  s->be.reset();   // the worker contexts, before their streams
   for (auto st : s->streams) cudaStreamDestroy(st);
   s->pool.release();
   delete s;
@@ -396,7 +508,7 @@ mlmc_status mlmc_failure_estimate(const mlmc_result* res, int64_t n, double thre
     } else if (!two_level) {
       y = r.q_fine - r.q_coarse;
     } else if (r.level == top) {
-      y = r.q_fine - (r.lambda[0] > threshold ? 1 : 0);
+      y = r.q_fine - r.q_mesh0;
     } else {
       continue;   // intermediate levels take no part in the two-level form
     }

@@ -246,3 +246,79 @@ def test_selective_result_is_the_same_alone_and_in_the_mix(B):
         assert a["status"] == 0 and m["status"] == 0
         assert a["stop_level"] == m["stop_level"]
         assert all(rel(x, y) < 1e-6 for x, y in zip(a["lambdas"], m["lambdas"]))
+
+
+# ---------------------------------------------------------------- panel requests
+def _panel_oracle_sr(W, level, sid, thr):
+    from oracle import plate as PL
+    phi = PL.sample_perturbations(W, level, [sid])[0]
+    return om.selective_refinement(W, level, sid, thr, m=4.0, alpha=1.0, sr_factor=2.0, eps_rel=1e-6,
+                                   solve=lambda mesh: PL.solve_mesh(W, mesh, phi)[0], below=True)
+
+
+def test_panel_selective_refinement_matches_the_oracle(B):
+    """Panel requests through the same request loop: Algorithm 2 on the critical load
+    P (failure below p*) gives the oracle's stopping meshes, loads (1e-6) and
+    indicators, and SOLVE requests return the oracle's load."""
+    from oracle import plate as PL
+    from workloads import PANEL_RM_4LEVEL as W
+    pilot = [PL.level_pair(W, 1, [k])[0][0, 0] for k in range(24)]
+    thr = float(np.quantile(pilot, 0.4))
+    W = dict(W, p_star=thr)
+    srv = B.mlmcp_server_create(B.configp_from_workload(W), workers=2, max_batch=16, hbm_budget_bytes=2e9,
+                                threshold=thr, sr_factor=2.0, eps_rel=1e-6)
+    reqs = [(SEL, l, 0, 500 + sid, 100 * l + sid) for l in range(3) for sid in range(6)]
+    reqs += [(SOLVE, 1, 1, 900 + k, 5000 + k) for k in range(3)]
+    try:
+        B.mlmc_server_submit(srv, reqs)
+        res = collect(B, srv, len(reqs))
+    finally:
+        B.mlmc_server_destroy(srv)
+    decided_early = 0
+    for kind, l, m, sid, tag in reqs:
+        r = res[tag]
+        assert r["status"] == 0
+        if kind == SOLVE:
+            ref = PL.solve_mesh(W, m, PL.sample_perturbations(W, l, [sid])[0])
+            assert rel(r["q"][0], ref[0]) < 1e-6
+            continue
+        J, lam, lf, lc, qf, qc = _panel_oracle_sr(W, l, sid, thr)
+        assert r["stop_level"] == J and r["solves"] == J + 1
+        assert all(rel(a, b) < 1e-6 for a, b in zip(r["lambdas"], lam))
+        assert (r["q_fine"], r["q_coarse"]) == (qf, qc)
+        assert r["q_mesh0"] == (1 if lam[0] < thr else 0)
+        decided_early += J < l
+    assert decided_early > 0
+
+
+def test_panel_result_is_the_same_alone_and_in_the_mix(B):
+    from workloads import PANEL_RM_4LEVEL as W
+    cfg = B.configp_from_workload(W)
+    probe = [(SOLVE, l, l, 60 + l, l) for l in range(3)] + [(SEL, 2, 0, 61, 10)]
+    alone = {}
+    srv = B.mlmcp_server_create(cfg, workers=1, max_batch=8, hbm_budget_bytes=1e9, threshold=272.47)
+    try:
+        for r in probe:
+            B.mlmc_server_submit(srv, [r])
+            alone.update(collect(B, srv, 1))
+    finally:
+        B.mlmc_server_destroy(srv)
+    g = np.random.default_rng(5)
+    noise = [(SOLVE, int(l), int(l), 7000 + k, 10 ** 6 + k) for k, l in enumerate(g.integers(0, 3, 40))]
+    traffic = probe + noise
+    order = g.permutation(len(traffic))
+    srv = B.mlmcp_server_create(cfg, workers=3, max_batch=12, hbm_budget_bytes=2e9, threshold=272.47)
+    try:
+        for chunk in np.array_split(order, 4):
+            B.mlmc_server_submit(srv, [traffic[i] for i in chunk])
+            time.sleep(0.02)
+        mix = collect(B, srv, len(traffic))
+    finally:
+        B.mlmc_server_destroy(srv)
+    for r in probe:
+        a, m = alone[r[4]], mix[r[4]]
+        assert a["status"] == 0 and m["status"] == 0
+        assert rel(m["q"][0], a["q"][0]) < 1e-6
+        if r[0] == SEL:
+            assert a["stop_level"] == m["stop_level"]
+            assert all(rel(x, y) < 1e-6 for x, y in zip(a["lambdas"], m["lambdas"]))
