@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(kThreads) k_patch_setup(PGrid g, const float* 
 // one warp per patch of colour (sx, sy): the residual at the patch's 9 nodes (lanes
 // 0..8, from `in`), the correction A_p^-1 r at its 27 slots (lanes 0..26; A_p^-1 is
 // symmetric, so lane l reads column l, coalesced), out = in + correction on the patch
-__global__ void __launch_bounds__(kThreads) k_patch_color(PGrid g, const float* __restrict__ ke,
+__global__ void __launch_bounds__(kThreads, 8) k_patch_color(PGrid g, const float* __restrict__ ke,
                                                           const float* __restrict__ pinv, const float4* __restrict__ b,
                                                           const float4* __restrict__ xin, float4* __restrict__ xout,
                                                           int sx, int sy, int pinv_per_sample,
@@ -450,7 +450,27 @@ __global__ void __launch_bounds__(kThreads) k_patch_color(PGrid g, const float* 
   const bool node_in = lane < 9 && li >= 0 && li <= g.nx && lj >= 0 && lj <= g.ny;
   float4 xo = make_float4(0.f, 0.f, 0.f, 0.f);
   if (node_in) {
-    const float4 kx = xin ? node_kx<false>(g, K, xin + o, li, lj, true, nullptr, nullptr) : xo;
+    // K x rows of the node, one element at a time (a rolled loop keeps registers low)
+    float4 kx = xo;
+    if (xin) {
+      const float4* xe = xin + o;
+#pragma unroll 1
+      for (int k = 0; k < 4; ++k) {
+        const int ox = k & 1, oy = k >> 1;
+        const int ei = li - ox, ej = lj - oy;
+        if (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) continue;
+        const float* Ka = K + 36 * corner_of(ox, oy);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int ni = ei + corner_x(c), nj = ej + corner_y(c);
+          const float4 v = masked(free_of(g, ni, nj), xe[nj * np + ni]);
+          const float* r = Ka + 3 * c;
+          kx.x += r[0] * v.x + r[1] * v.y + r[2] * v.z;
+          kx.y += r[12] * v.x + r[13] * v.y + r[14] * v.z;
+          kx.z += r[24] * v.x + r[25] * v.y + r[26] * v.z;
+        }
+      }
+    }
     const float4 bb = b[o + lj * np + li];
     const Free f = free_of(g, li, lj);
     if (xin) xo = xin[o + lj * np + li];
@@ -464,7 +484,7 @@ __global__ void __launch_bounds__(kThreads) k_patch_color(PGrid g, const float* 
   if (lane < kPatchDofs) {
     const float* M = pinv + ((size_t)(pinv_per_sample ? s : 0) * kPatchTypes + type) * kPatchDofs * kPatchDofs;
     float d = 0.f;
-#pragma unroll 9
+#pragma unroll 3
     for (int q = 0; q < kPatchDofs; ++q) d += M[q * kPatchDofs + lane] * rs[warp][q];
     ds[warp][lane] = d;
   }
