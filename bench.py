@@ -403,6 +403,16 @@ def run_gpu(a):
                 "avg_launch_us": round(ms / nl * 1e3, 2), "launches": nl,
                 "share_of_step": round(ms / (t_step * a.steps), 4),
                 "timing": "kernel timer steps (CUDA events around each launch), same workload"}
+    # the whole stencil / CG path: the algorithmic bytes of every timed CG kernel of a step
+    # over the step's own time (headline steps, no kernel timer)
+    path_bytes = sum(v[2] * BYTES_PER_NODE[k] for k, v in prof.items() if k in BYTES_PER_NODE) / a.steps
+    cg_path = {"algorithmic_bytes_per_step": round(path_bytes), "ms_per_step": round(t_step, 3),
+               "achieved": round(path_bytes / (t_step / 1e3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+               "frac": round(path_bytes / (t_step / 1e3) / 1e9 / peak, 4), "peak_kind": f"{peak_kind} hbm_gbs",
+               "kernels": sorted(k for k in prof if k in BYTES_PER_NODE),
+               "note": "summed algorithmic bytes of the PCG / multigrid kernels of one step (nodes each one "
+                       "processed x its bytes per node) over the whole step's time, everything else in the step "
+                       "(setup, KL synthesis, stress, moments, host checks) counted as time without bytes"}
     kernel_ms = t_prof
     kernels = {k: {"ms_per_step": round(v[0] / a.steps, 3), "launches_per_step": v[1] // a.steps,
                    "GB/s": (round(v[2] * BYTES_PER_NODE[k] / (v[0] / 1e3) / 1e9, 1)
@@ -473,7 +483,7 @@ def run_gpu(a):
                                "uint64, count int64 per level), which reach the device as kernel "
                                "arguments: per-sample inputs are (seed, level, id) counters and the "
                                "fields are synthesised on the device"},
-               "roofline": roofline, "kernels": kernels,
+               "roofline": roofline, "cg_path_roofline": cg_path, "kernels": kernels,
                "kernel_ms_per_step": round(kernel_ms, 3),
                "gpu_busy_fraction": round(kernel_ms / (sum(prof_times) / len(prof_times)), 3),
                "launches_by_name": by_name,
