@@ -121,8 +121,30 @@ PANEL_C5_4LEVEL = dict(
     smoother="patch",
 )
 
+# The paper's first test problem as published (Sec. 3): a Cosserat continuum on the
+# square [0, L]^2 of AS4/8552 with waviness from the exponential kernel (Eq.
+# covarianceFunction), omega_1 = 229 d, omega_2 = 61 d, s = 0.035 rad, L = 2.5 omega_1, the
+# strength quantity over the central square of side 1.25 omega_1 (Eq. failureCriterion),
+# level-0 mesh 8 x 8 (M_0 = 243) halved per level, N_KL = 50 + 50 l. Lengths in mm, moduli
+# in MPa. The constitutive readings (rule of mixtures, R = 2, tau_y = tau_c) are the
+# oracle's (oracle/cosserat.py). The end shortening is a strain of 1e-3 (the problem is
+# linear: the strength does not depend on it).
+_D_FIBRE = 7e-3
+COSSERAT_TEST1 = dict(
+    name="cosserat-test1-5level",
+    d=_D_FIBRE, L=2.5 * 229 * _D_FIBRE, omega_side=1.25 * 229 * _D_FIBRE,
+    omega1=229 * _D_FIBRE, omega2=61 * _D_FIBRE, kl_std=0.035,
+    vf=0.59, Ef=230e3, Em=9.25e3, Gf=95.83e3, Gm=5.13e3, nu12=0.3, nu23=0.45,
+    R_ratio=2.0, tau_y=114.0,
+    shortening=-1e-3 * 2.5 * 229 * _D_FIBRE,
+    n0=8, levels=5, kl_terms0=50, kl_terms_step=50,
+    seed=0,
+    n_per_level=(4096, 1024, 256, 64, 16),
+    rtol=1e-8,
+)
+
 WORKLOADS = {w["name"]: w for w in (STRIP_FP64_3LEVEL, STRIP_MIXED_5LEVEL, HEX8_MIXED_4LEVEL, PANEL_RM_4LEVEL,
-                                    PANEL_C5_4LEVEL)}
+                                    PANEL_C5_4LEVEL, COSSERAT_TEST1)}
 
 
 def mesh_dims(cfg, level):
