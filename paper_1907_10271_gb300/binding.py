@@ -726,3 +726,142 @@ def mlmcp_server_create(cfg, workers=2, max_batch=4096, hbm_budget_bytes=8e9, th
     if st != 0:
         raise MLMCError(st, L.mlmc_server_last_error(None).decode())
     return srv
+
+
+# ---------------------------------------------------------------- Cosserat strength (mlmc_cosserat.h)
+
+class mlmcc_config(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_double), ("omega_side", ctypes.c_double),
+        ("omega1", ctypes.c_double), ("omega2", ctypes.c_double), ("kl_std", ctypes.c_double),
+        ("d_fibre", ctypes.c_double), ("vf", ctypes.c_double), ("Ef", ctypes.c_double), ("Em", ctypes.c_double),
+        ("Gf", ctypes.c_double), ("Gm", ctypes.c_double), ("nu12", ctypes.c_double), ("nu23", ctypes.c_double),
+        ("R_ratio", ctypes.c_double), ("tau_y", ctypes.c_double), ("shortening", ctypes.c_double),
+        ("n0", ctypes.c_int32), ("levels", ctypes.c_int32), ("kl_terms0", ctypes.c_int32),
+        ("kl_terms_step", ctypes.c_int32), ("seed", ctypes.c_uint64), ("rtol", ctypes.c_double),
+        ("max_iter", ctypes.c_int32),
+    ]
+
+
+_SIGC = None
+
+
+def libc():
+    """The library with the Cosserat entry points' signatures set."""
+    global _SIGC
+    L = lib()
+    if _SIGC is None:
+        P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        sig = {
+            "mlmcc_create": (I32, [ctypes.POINTER(mlmcc_config), P, ctypes.POINTER(P)]),
+            "mlmcc_destroy": (None, [P]),
+            "mlmcc_last_error": (ctypes.c_char_p, [P]),
+            "mlmcc_sample_level": (I32, [P, I32, U64, I64, P, P, P]),
+            "mlmcc_sample_levels": (I32, [P, I32, P, P, P, P, P, P]),
+            "mlmcc_solve_batch": (I32, [P, P, I64, P, P]),
+            "mlmcc_level_stats_get": (I32, [P, I32, P]),
+            "mlmcc_reset_stats": (I32, [P]),
+            "mlmcc_field": (I32, [P, I32, I32, U64, I64, P]),
+            "mlmcc_apply": (I32, [P, I32, I32, U64, I64, P, P]),
+            "mlmcc_displacement": (I32, [P, I32, I32, U64, I64, P, P]),
+            "mlmcc_last_iters": (I32, [P, P, P]),
+            "mlmcc_launch_count": (I32, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _SIGC = True
+    return L
+
+
+def configc_from_workload(w, **overrides):
+    """mlmcc_config from a Cosserat workload dict (see workloads.py); keyword overrides win."""
+    w = dict(w)
+    w.update(overrides)
+    c = mlmcc_config()
+    for f in ("L", "omega_side", "omega1", "omega2", "kl_std", "vf", "Ef", "Em", "Gf", "Gm", "nu12", "nu23",
+              "R_ratio", "tau_y", "shortening"):
+        setattr(c, f, float(w[f]))
+    c.d_fibre = float(w["d"])
+    c.n0, c.levels = int(w["n0"]), int(w["levels"])
+    c.kl_terms0, c.kl_terms_step = int(w["kl_terms0"]), int(w["kl_terms_step"])
+    c.seed = int(w["seed"])
+    c.rtol = float(w.get("rtol", 0.0))
+    c.max_iter = int(w.get("max_iter", 0))
+    return c
+
+
+def _checkc(ctx, status):
+    if status != MLMC_OK:
+        raise MLMCError(status, libc().mlmcc_last_error(ctx).decode(errors="replace"))
+    return status
+
+
+def mlmcc_create(cfg, stream=None):
+    h = ctypes.c_void_p()
+    st = current_stream() if stream is None else stream
+    s = libc().mlmcc_create(ctypes.byref(cfg), ctypes.c_void_p(st), ctypes.byref(h))
+    if s != MLMC_OK:
+        raise MLMCError(s, libc().mlmcc_last_error(None).decode(errors="replace"))
+    return h
+
+
+def mlmcc_destroy(ctx):
+    libc().mlmcc_destroy(ctx)
+
+
+def mlmcc_sample_level(ctx, level, first_id, n, q_fine=None, q_coarse=None, status=None):
+    return _checkc(ctx, libc().mlmcc_sample_level(ctx, level, first_id, n, _ptr(q_fine, np.float64),
+                                                   _ptr(q_coarse, np.float64), _ptr(status, np.int32)))
+
+
+def mlmcc_sample_levels(ctx, levels, first_ids, counts, q_fine=None, q_coarse=None, status=None):
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    fi = np.ascontiguousarray(first_ids, dtype=np.uint64)
+    ct = np.ascontiguousarray(counts, dtype=np.int64)
+    return _checkc(ctx, libc().mlmcc_sample_levels(ctx, len(lv), _ptr(lv, np.int32), _ptr(fi, np.uint64),
+                                                    _ptr(ct, np.int64), _ptr(q_fine, np.float64),
+                                                    _ptr(q_coarse, np.float64), _ptr(status, np.int32)))
+
+
+def mlmcc_solve_batch(ctx, items, q=None, status=None):
+    arr = (mlmc_item * len(items))(*[mlmc_item(int(l), int(m), int(s)) for (l, m, s) in items])
+    return _checkc(ctx, libc().mlmcc_solve_batch(ctx, ctypes.cast(arr, ctypes.c_void_p), len(items),
+                                                  _ptr(q, np.float64), _ptr(status, np.int32)))
+
+
+def mlmcc_level_stats(ctx, level):
+    out = mlmc_level_stats()
+    _checkc(ctx, libc().mlmcc_level_stats_get(ctx, level, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def mlmcc_reset_stats(ctx):
+    return _checkc(ctx, libc().mlmcc_reset_stats(ctx))
+
+
+def mlmcc_field(ctx, level, mesh_level, first_id, n, phi):
+    return _checkc(ctx, libc().mlmcc_field(ctx, level, mesh_level, first_id, n, _ptr(phi, np.float64)))
+
+
+def mlmcc_apply(ctx, level, mesh_level, first_id, n, x, y):
+    return _checkc(ctx, libc().mlmcc_apply(ctx, level, mesh_level, first_id, n, _ptr(x, np.float64),
+                                            _ptr(y, np.float64)))
+
+
+def mlmcc_displacement(ctx, level, mesh_level, first_id, n, d, status=None):
+    return _checkc(ctx, libc().mlmcc_displacement(ctx, level, mesh_level, first_id, n, _ptr(d, np.float64),
+                                                   _ptr(status, np.int32)))
+
+
+def mlmcc_last_iters(ctx):
+    it, rf = ctypes.c_int32(), ctypes.c_int32()
+    _checkc(ctx, libc().mlmcc_last_iters(ctx, ctypes.byref(it), ctypes.byref(rf)))
+    return it.value, rf.value
+
+
+def mlmcc_launch_count(ctx):
+    n = ctypes.c_int64()
+    _checkc(ctx, libc().mlmcc_launch_count(ctx, ctypes.byref(n)))
+    return n.value

@@ -1,5 +1,5 @@
 """The C ABI library builds for sm_103a, loads without a GPU and exports every
-function that include/mlmc.h declares (no compute calls here)."""
+function that the headers under include/ declare (no compute calls here)."""
 import ctypes
 import os
 import re
@@ -15,7 +15,7 @@ def declared_functions():
         if f.endswith(".h"):
             text = open(os.path.join(ROOT, "include", f)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names += re.findall(r"\b(mlmc(?:3d|p)?_[a-z0-9_]+)\s*\(", text)
+            names += re.findall(r"\b(mlmc(?:3d|p|c)?_[a-z0-9_]+)\s*\(", text)
     return sorted(set(names))
 
 
@@ -23,7 +23,8 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("mlmc_create", "mlmc_destroy", "mlmc_sample_level", "mlmc_solve_batch",
                      "mlmc_estimate", "mlmc_last_error", "mlmc3d_create", "mlmc3d_sample_level",
-                     "mlmc3d_solve_batch", "mlmcp_create", "mlmcp_sample_level", "mlmcp_solve_batch"):
+                     "mlmc3d_solve_batch", "mlmcp_create", "mlmcp_sample_level", "mlmcp_solve_batch",
+                     "mlmcc_create", "mlmcc_sample_level", "mlmcc_sample_levels", "mlmcc_solve_batch"):
         assert required in names
 
 
