@@ -49,6 +49,24 @@ BYTES_PER_NODE = {
 }
 
 
+# Cosserat engine: algorithmic bytes per work item of each kernel kind (an item is a node
+# of the kernel's level; restrict and rap count coarse nodes): FP32 stencil 42 x 4 B,
+# block-Jacobi inverse 6 x 4 B, vectors 3 x 4 B (3 x 8 B in double), neighbours' values
+# counted once (they are other nodes' own data)
+BYTES_PER_ITEM_C = {
+    "cg_apply": 168 + 12 + 12 + 12 + 12,        # A ; z p_in ; p_out q
+    "pre": 168 + 24 + 12 + 24,                  # A Dinv r ; x t
+    "post": 168 + 24 + 12 + 12 + 12,            # A Dinv r x ; t
+    "cg_update": 12 + 12 + 24 + 24,             # p q ; c r (read + write)
+    "resid64": 336 + 24 + 24 + 12,              # A64 d64 b64 ; r (float)
+    "build_fine": 16 + 336 + 168 + 24 + 24 + 24,  # trig (per node) ; A64 A Dinv b64 d64
+    "restrict": 4 * 12 + 12,                    # t of 4 fine nodes per coarse node ; r
+    "prolong": 3 + 24,                          # coarse t (1/4 per fine node) ; x (read + write)
+    "rap": 4 * 168 + 168 + 24,                  # A of 4 fine nodes ; A Dinv
+    "accumulate": 48 + 24,                      # d64 c (read + write)
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -60,7 +78,9 @@ def parse():
                     help="skip the plain double-precision single-sample comparison")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the request-loop (selective refinement) measurement")
-    ap.add_argument("--case", choices=["full", "small", "hex3d", "panel"], default="full",
+    ap.add_argument("--no-cosserat", dest="cosserat", action="store_false",
+                    help="skip the Cosserat strength workload (the paper's first test problem)")
+    ap.add_argument("--case", choices=["full", "small", "hex3d", "panel", "cosserat"], default="full",
                     help="small: one untimed call with 1/4 of each level's samples; hex3d / panel: one "
                          "untimed step of the 3D Hex8 block / the buckling panel (all for profilers)")
     ap.add_argument("--no-hex3d", dest="hex3d", action="store_false",
@@ -938,6 +958,166 @@ def run_panel_serving(B, W, threshold, seconds=3.0, load=0.5):
             "failed_requests": len(results) + len(stream) - len(ok), "batches": counters["batches"]}
 
 
+def _cosserat_worker(args):
+    cfg, level, ids = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import cosserat as C
+    times, qf, qc = [], [], []
+    for i in ids:
+        t = time.perf_counter()
+        f, c = C.level_pair(cfg, level, [int(i)])
+        times.append(time.perf_counter() - t)
+        qf.append(f[0])
+        qc.append(c[0])
+    return level, list(ids), times, qf, qc
+
+
+def run_cosserat(B, steps=3, warmup=3, parity=True, W=None):
+    """The paper's first test problem as published (Sec. 3): compressive strength of a
+    fibre composite with exponential-kernel waviness on 8x8 .. 128x128 Cosserat Q1 meshes.
+    One MLMC step is every level's samples (4096/1024/256/64/16 level pairs) in one
+    mlmcc_sample_levels call with host outputs, timed with the device synchronised on both
+    sides. A profile step (CUDA events around every launch, no graphs) gives the kernel
+    shares and the dominant kernel's roofline. Parity: spread picks of the last timed
+    step's samples (levels 0 - 4) against the oracle's sparse direct solves, whose times
+    give the CPU baseline on the workload mix."""
+    import torch
+    if W is None:
+        from workloads import COSSERAT_TEST1 as W
+    counts = list(W["n_per_level"])
+    levels = list(range(len(counts)))
+    tot = sum(counts)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = B.mlmcc_create(B.configc_from_workload(W), stream.cuda_stream)
+        try:
+            qf, qc = np.zeros(2 * tot), np.zeros(2 * tot)
+            st = np.zeros(tot, dtype=np.int32)
+
+            def step(k):
+                B.mlmcc_sample_levels(ctx, levels, [k * 10 ** 6] * len(levels), counts, qf, qc, st)
+
+            for k in range(warmup):
+                step(k)
+            torch.cuda.synchronize()
+            l0 = B.mlmcc_launch_count(ctx)
+            with ClockSampler(torch.cuda.current_device()) as clk:
+                t0 = time.perf_counter()
+                for k in range(steps):
+                    step(warmup + k)
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t0) / steps * 1e3
+            launches = (B.mlmcc_launch_count(ctx) - l0) / steps
+            iters, refine = B.mlmcc_last_iters(ctx)
+            last = warmup + steps - 1
+            q_last = (qf.reshape(tot, 2).copy(), qc.reshape(tot, 2).copy())
+            failed = int((st != 0).sum())
+            off = np.cumsum([0] + counts)
+            means = [[round(float(x), 3) for x in qf.reshape(tot, 2)[off[l]:off[l + 1]].mean(0)] for l in levels]
+            ymeans = [[round(float(x), 4) for x in (qf - qc).reshape(tot, 2)[off[l]:off[l + 1]].mean(0)]
+                      for l in levels]
+            # profile step
+            B.mlmcc_profile_enable(ctx, True)
+            t1 = time.perf_counter()
+            step(last + 1)
+            torch.cuda.synchronize()
+            prof_wall = (time.perf_counter() - t1) * 1e3
+            prof = B.mlmcc_profile(ctx)
+            B.mlmcc_profile_enable(ctx, False)
+            ktot = sum(v[0] for v in prof.values())
+            kernels = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / ktot, 4),
+                           "avg_launch_us": round(v[0] / v[1] * 1e3, 2),
+                           "GB/s": (round(v[2] * BYTES_PER_ITEM_C[k] / (v[0] / 1e3) / 1e9, 1)
+                                    if k in BYTES_PER_ITEM_C and v[0] > 0 else None)}
+                       for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+            pk, pk_kind = peaks()
+            dom = max((k for k in prof if k in BYTES_PER_ITEM_C), key=lambda k: prof[k][0])
+            ms_d, n_d, it_d = prof[dom]
+            ach = it_d * BYTES_PER_ITEM_C[dom] / (ms_d / 1e3) / 1e9
+            path_bytes = sum(v[2] * BYTES_PER_ITEM_C[k] for k, v in prof.items() if k in BYTES_PER_ITEM_C)
+            out = {
+                "workload": W["name"],
+                "meshes": "%dx%d .. %dx%d Cosserat Q1 (u, v, theta_3), L = %.4g mm, Omega' side %.4g mm" % (
+                    W["n0"], W["n0"], W["n0"] << (W["levels"] - 1), W["n0"] << (W["levels"] - 1), W["L"],
+                    W["omega_side"]),
+                "kl_terms_per_level": [W["kl_terms0"] + W["kl_terms_step"] * l for l in levels],
+                "samples_per_level": counts, "metric": "level-pairs/s", "value": round(tot / ms * 1e3, 1),
+                "ms_per_step": round(ms, 3), "steps": steps, "warmup": warmup, "samples_failed": failed,
+                "rtol": W["rtol"], "correction_iterations": iters, "fp64_residuals": refine,
+                "gpu_launches_per_step": round(launches, 1), "clocks": clk.summary(),
+                "mean_q_fine_per_level": means, "mean_y_per_level": ymeans,
+                "kernels": kernels, "profile_step_ms": round(prof_wall, 2),
+                "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": pk,
+                             "unit": "GB/s", "frac": round(ach / pk, 4), "peak_kind": pk_kind + " hbm_gbs",
+                             "bytes_per_item": BYTES_PER_ITEM_C[dom], "items_per_launch": round(it_d / n_d),
+                             "avg_launch_us": round(ms_d / n_d * 1e3, 2), "traffic": None,
+                             "timing": "profile step: CUDA events around each launch on the context's stream"},
+                "stencil_path_roofline": {
+                    "achieved": round(path_bytes / (ktot / 1e3) / 1e9, 1), "unit": "GB/s",
+                    "frac": round(path_bytes / (ktot / 1e3) / 1e9 / pk, 4),
+                    "note": "summed algorithmic bytes of the stencil / CG / multigrid kernels over the summed "
+                            "event time of all kernels of the profile step"},
+                "note": "host outputs (mlmcc_sample_levels), all five meshes advance in one lock-stepped batch; "
+                        "FP32 CG corrections preconditioned by a V(1,1) Galerkin multigrid cycle inside FP64 "
+                        "refinement; KL synthesis in double from the analytic exponential-kernel modes",
+            }
+            if parity:
+                picks = {0: 6, 1: 4, 2: 3, 3: 2, 4: 1}
+                jobs = []
+                for l in levels:
+                    idx = spread_picks(counts[l], picks.get(l, 1))
+                    for i in idx:
+                        jobs.append((W, l, [last * 10 ** 6 + int(i)]))
+                jobs.sort(key=lambda j: -j[1])
+                import multiprocessing as mp
+                cores = min(os.cpu_count() or 1, len(jobs))
+                t2 = time.perf_counter()
+                with mp.get_context("spawn").Pool(cores) as pool:
+                    res = pool.map(_cosserat_worker, jobs, chunksize=1)
+                wall = time.perf_counter() - t2
+                err = [0.0, 0.0]
+                t_l = {l: [] for l in levels}
+                for lev, ids, times, rf, rc in res:
+                    t_l[lev] += times
+                    for i, f, c in zip(ids, rf, rc):
+                        k = off[lev] + (i - last * 10 ** 6)
+                        for qn in range(2):
+                            err[qn] = max(err[qn], abs(q_last[0][k, qn] / f[qn] - 1.0))
+                            if lev > 0:
+                                err[qn] = max(err[qn], abs(q_last[1][k, qn] / c[qn] - 1.0))
+                out["qoi_parity"] = {"solves": sum(2 if j[1] else 1 for j in jobs),
+                                     "max_rel_err": {"strength": float(err[0]), "reaction": float(err[1])},
+                                     "ids": "spread picks of the last timed step's samples, levels 0-4",
+                                     "note": "GPU vs oracle (FP64 sparse direct solves) on the same xi"}
+                tl = [float(np.mean(t_l[l])) for l in levels]
+                cpu_v = tot / (sum(n * t for n, t in zip(counts, tl)) / (os.cpu_count() or 1))
+                out["cpu_baseline"] = {"kind": "oracle", "value": round(cpu_v, 2), "unit": "level-pairs/s",
+                                       "cores": os.cpu_count() or 1,
+                                       "sample": "the parity pairs above (%s per level), per-pair times %s s, "
+                                                 "extrapolated to the workload mix" %
+                                                 ([picks[l] for l in levels], [round(t, 4) for t in tl]),
+                                       "wall_s": round(wall, 1)}
+            return out
+        finally:
+            B.mlmcc_destroy(ctx)
+
+
+def run_cosserat_case():
+    """One step of the Cosserat strength workload (every level's samples), untimed: for profilers."""
+    import torch
+    from paper_1907_10271_gb300 import binding as B
+    from workloads import COSSERAT_TEST1 as W
+    ctx = B.mlmcc_create(B.configc_from_workload(W), torch.cuda.current_stream().cuda_stream)
+    counts = list(W["n_per_level"])
+    tot = sum(counts)
+    qf, qc, st = np.zeros(2 * tot), np.zeros(2 * tot), np.zeros(tot, dtype=np.int32)
+    for k in range(2):
+        B.mlmcc_sample_levels(ctx, list(range(len(counts))), [k * 10 ** 6] * len(counts), counts, qf, qc, st)
+    torch.cuda.synchronize()
+    B.mlmcc_destroy(ctx)
+    print(json.dumps({"case": "cosserat", "level_pairs": tot, "failed": int((st != 0).sum())}))
+
+
 def run_panel_case():
     """One step of the buckling panel (every level's samples), untimed: for profilers."""
     import torch
@@ -1025,6 +1205,9 @@ def main():
     if a.case == "panel":
         run_panel_case()
         return
+    if a.case == "cosserat":
+        run_cosserat_case()
+        return
     if a.impl == "reference":
         if rank != 0:
             return
@@ -1044,6 +1227,9 @@ def main():
         out["panel_thin"] = run_panel(B, parity=not a.no_cpu_baseline, W=PANEL_C5_4LEVEL, pilot=True)
         if a.serving:
             out["panel_thin"]["serving"] = run_panel_serving(B, PANEL_C5_4LEVEL, out["panel_thin"]["p_star_kn"])
+    if rank == 0 and out is not None and world == 1 and a.cosserat:
+        from paper_1907_10271_gb300 import binding as B
+        out["cosserat"] = run_cosserat(B, parity=not a.no_cpu_baseline)
     if rank == 0 and out is not None:
         if world == 1 and not a.no_cpu_baseline and out.get("_gpu_q") is not None:
             cores = os.cpu_count() or 1

@@ -131,6 +131,16 @@ mlmc_status mlmcc_displacement(mlmcc_ctx* ctx, int32_t level, int32_t mesh_level
 mlmc_status mlmcc_last_iters(mlmcc_ctx* ctx, int32_t* iterations, int32_t* refinements);
 /* Kernels this context has launched so far (graph replays count every kernel node). */
 mlmc_status mlmcc_launch_count(mlmcc_ctx* ctx, int64_t* launches);
+/* Per-kernel profile. While enabled (on != 0; enabling clears the totals) every launch is
+   issued directly, without graphs, between two CUDA events on the context's stream, and
+   calls accumulate per kernel kind `op` (0 .. mlmcc_profile_name(op) == NULL) the event
+   time, the launches and the work items (threads' nodes, samples or elements). Kinds:
+   kl_coefficients, kl_synthesis, build_fine, rap, coarsest_inverse, pre, restrict,
+   coarse_solve, prolong, post, cg_apply, cg_update, scalars, resid64, accumulate, qoi,
+   moments, layout. */
+mlmc_status mlmcc_profile_enable(mlmcc_ctx* ctx, int32_t on);
+mlmc_status mlmcc_profile_get(mlmcc_ctx* ctx, int32_t op, double* ms, int64_t* launches, int64_t* items);
+const char* mlmcc_profile_name(int32_t op);
 
 #ifdef __cplusplus
 }

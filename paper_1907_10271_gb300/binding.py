@@ -766,6 +766,9 @@ def libc():
             "mlmcc_displacement": (I32, [P, I32, I32, U64, I64, P, P]),
             "mlmcc_last_iters": (I32, [P, P, P]),
             "mlmcc_launch_count": (I32, [P, P]),
+            "mlmcc_profile_enable": (I32, [P, I32]),
+            "mlmcc_profile_get": (I32, [P, I32, P, P, P]),
+            "mlmcc_profile_name": (ctypes.c_char_p, [I32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -865,3 +868,21 @@ def mlmcc_launch_count(ctx):
     n = ctypes.c_int64()
     _checkc(ctx, libc().mlmcc_launch_count(ctx, ctypes.byref(n)))
     return n.value
+
+
+def mlmcc_profile_enable(ctx, on=True):
+    return _checkc(ctx, libc().mlmcc_profile_enable(ctx, 1 if on else 0))
+
+
+def mlmcc_profile(ctx):
+    """{kernel kind: (ms, launches, items)} accumulated since profiling was enabled."""
+    out, k = {}, 0
+    while True:
+        name = libc().mlmcc_profile_name(k)
+        if name is None:
+            return out
+        ms, la, it = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        _checkc(ctx, libc().mlmcc_profile_get(ctx, k, ctypes.byref(ms), ctypes.byref(la), ctypes.byref(it)))
+        if la.value:
+            out[name.decode()] = (ms.value, la.value, it.value)
+        k += 1

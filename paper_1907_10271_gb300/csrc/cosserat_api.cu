@@ -30,6 +30,16 @@ bool dev_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// kernel kinds of the profile (mlmcc_profile_get)
+enum Op {
+  kOpXi, kOpSynth, kOpBuild, kOpRap, kOpInverse, kOpPre, kOpRestrict, kOpCoarse, kOpProlong, kOpPost,
+  kOpCgApply, kOpCgUpdate, kOpScalar, kOpResid64, kOpAccumulate, kOpQoi, kOpMoments, kOpLayout, kOpCount
+};
+const char* const kOpNames[kOpCount] = {
+    "kl_coefficients", "kl_synthesis", "build_fine", "rap", "coarsest_inverse", "pre", "restrict",
+    "coarse_solve", "prolong", "post", "cg_apply", "cg_update", "scalars", "resid64", "accumulate", "qoi",
+    "moments", "layout"};
+
 constexpr int kGraphIters = 4;        // correction iterations per graph replay (even)
 constexpr int kMaxRefine = 30;        // FP64 residual evaluations per solve
 constexpr size_t kArenaBudget = size_t(24) << 30;
@@ -76,6 +86,40 @@ struct mlmcc_ctx {
     int64_t kernels;
   };
   std::vector<GraphEntry> graphs;
+  // profile: CUDA events around every launch (graphs bypassed) while enabled
+  bool prof_on = false;
+  struct Pending {
+    int op;
+    int64_t items;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_free;
+  double prof_ms[kOpCount] = {};
+  int64_t prof_launches[kOpCount] = {}, prof_items[kOpCount] = {};
+  cudaEvent_t ev_get() {
+    if (!ev_free.empty()) {
+      cudaEvent_t e = ev_free.back();
+      ev_free.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // after a synchronize: fold the recorded launches into the totals
+  void prof_collect() {
+    for (const Pending& q : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) prof_ms[q.op] += ms;
+      prof_launches[q.op] += 1;
+      prof_items[q.op] += q.items;
+      ev_free.push_back(q.a);
+      ev_free.push_back(q.b);
+    }
+    pending.clear();
+    cudaGetLastError();
+  }
 
   mlmc_status fail(mlmc_status s, const std::string& m) {
     err = m;
@@ -93,6 +137,11 @@ struct mlmcc_ctx {
   }
   ~mlmcc_ctx() {
     drop_graphs();
+    for (const Pending& q : pending) {
+      cudaEventDestroy(q.a);
+      cudaEventDestroy(q.b);
+    }
+    for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
     for (double* b : basis)
       if (b) cudaFree(b);
     if (acc_dev) cudaFree(acc_dev);
@@ -281,18 +330,40 @@ mlmc_status ensure_arena(mlmcc_ctx& c, size_t bytes) {
   return MLMC_OK;
 }
 
-// counts every launch; returns false (with the context error set) on a launch error
+int64_t items_of(const Views& V) {
+  int64_t n = 0;
+  for (int k = 0; k < V.nv; ++k) n += V.v[k].items;
+  return n;
+}
+
+// Counts every launch (and times it while profiling); after a failure it launches
+// nothing more and keeps the first error.
 struct Launcher {
   mlmcc_ctx& c;
   mlmc_status status = MLMC_OK;
-  bool operator()(cudaError_t e, const char* what) {
+  template <class F>
+  bool operator()(int op, int64_t items, F launch) {
     if (status != MLMC_OK) return false;
+    cudaEvent_t a = nullptr;
+    if (c.prof_on) {
+      a = c.ev_get();
+      cudaEventRecord(a, c.st);
+    }
+    const cudaError_t e = launch();
+    if (c.prof_on) {
+      cudaEvent_t b = c.ev_get();
+      cudaEventRecord(b, c.st);
+      c.pending.push_back({op, items, a, b});
+    }
     ++c.launches;
     if (e != cudaSuccess) {
-      status = c.cuda_fail(e, what);
+      status = c.cuda_fail(e, kOpNames[op]);
       return false;
     }
     return true;
+  }
+  bool operator()(int op, const Views& V, cudaError_t (*fn)(const Views&, cudaStream_t)) {
+    return (*this)(op, items_of(V), [&] { return fn(V, c.st); });
   }
 };
 
@@ -300,23 +371,24 @@ struct Launcher {
 void vcycle(Launcher& L, const Sched& s, cudaStream_t st) {
   const int nd = (int)s.pre.size();
   for (int k = 0; k < nd; ++k) {
-    L(mlmcc::launch_pre(s.pre[k], st), "pre-smoothing");
-    L(mlmcc::launch_restrict(s.restr[k], st), "restriction");
+    L(kOpPre, s.pre[k], mlmcc::launch_pre);
+    L(kOpRestrict, s.restr[k], mlmcc::launch_restrict);
   }
-  L(mlmcc::launch_coarse_solve(s.coarse, st), "coarse solve");
+  L(kOpCoarse, s.coarse, mlmcc::launch_coarse_solve);
   for (int k = nd - 1; k >= 0; --k) {
-    L(mlmcc::launch_prolong(s.prol[k], st), "prolongation");
-    L(mlmcc::launch_post(s.post[k], k == 0, st), "post-smoothing");
+    L(kOpProlong, s.prol[k], mlmcc::launch_prolong);
+    const Views& V = s.post[k];
+    L(kOpPost, items_of(V), [&] { return mlmcc::launch_post(V, k == 0, st); });
   }
 }
 
 // One correction-CG iteration of every active sample.
 void cg_iteration(Launcher& L, const Sched& s, bool odd, int max_iter, cudaStream_t st) {
-  L(mlmcc::launch_cg_apply(s.fine, odd, st), "cg apply");
-  L(mlmcc::launch_scal_a(s.samples, st), "cg alpha");
-  L(mlmcc::launch_cg_update(s.fine, odd, st), "cg update");
+  L(kOpCgApply, items_of(s.fine), [&] { return mlmcc::launch_cg_apply(s.fine, odd, st); });
+  L(kOpScalar, s.samples, mlmcc::launch_scal_a);
+  L(kOpCgUpdate, items_of(s.fine), [&] { return mlmcc::launch_cg_update(s.fine, odd, st); });
   vcycle(L, s, st);
-  L(mlmcc::launch_scal_b(s.samples, max_iter, st), "cg beta");
+  L(kOpScalar, items_of(s.samples), [&] { return mlmcc::launch_scal_b(s.samples, max_iter, st); });
 }
 
 // kGraphIters iterations and the active count (into count_dev[0]), from a cached graph
@@ -326,11 +398,13 @@ mlmc_status iterations(mlmcc_ctx& c, const Sched& s, const std::vector<GroupBufs
   Launcher L{c};
   auto enqueue = [&]() {
     for (int k = 0; k < kGraphIters; ++k) cg_iteration(L, s, (k & 1) != 0, max_iter, c.st);
-    L(cudaMemsetAsync(count_dev, 0, sizeof(int), c.st), "memset");
-    --c.launches;   // the memset is not a kernel
-    L(mlmcc::launch_count_active(s.samples, count_dev, c.st), "count");
+    if (L.status == MLMC_OK) {
+      const cudaError_t e = cudaMemsetAsync(count_dev, 0, sizeof(int), c.st);
+      if (e != cudaSuccess) L.status = c.cuda_fail(e, "memset");
+    }
+    L(kOpScalar, items_of(s.samples), [&] { return mlmcc::launch_count_active(s.samples, count_dev, c.st); });
   };
-  if (!c.st) {
+  if (!c.st || c.prof_on) {
     enqueue();
     return L.status;
   }
@@ -411,12 +485,14 @@ mlmc_status run_once(mlmcc_ctx& c, const std::vector<Group>& groups, Mode mode, 
     const GroupBufs& b = G[g];
     CK(cudaMemcpyAsync(b.levels, groups[g].levels.data(), sizeof(int) * b.S, cudaMemcpyHostToDevice, c.st), "ids");
     CK(cudaMemcpyAsync(b.ids, groups[g].ids.data(), sizeof(uint64_t) * b.S, cudaMemcpyHostToDevice, c.st), "ids");
-    L(mlmc::launch_kl_coefficients(c.cfg.seed, 0, 0, b.levels, b.ids, b.S, b.nkl, b.xi, nullptr, count_dev + 1,
-                                   c.st),
-      "KL coefficients");
-    L(mlmc::launch_kl_synthesis<double>(b.xi, c.basis[b.mesh], b.S, b.n * b.n, b.nkl, b.trig, mode != Mode::Field,
-                                        c.st),
-      "KL synthesis");
+    L(kOpXi, b.S, [&] {
+      return mlmc::launch_kl_coefficients(c.cfg.seed, 0, 0, b.levels, b.ids, b.S, b.nkl, b.xi, nullptr,
+                                          count_dev + 1, c.st);
+    });
+    L(kOpSynth, (int64_t)b.S * b.n * b.n, [&] {
+      return mlmc::launch_kl_synthesis<double>(b.xi, c.basis[b.mesh], b.S, b.n * b.n, b.nkl, b.trig,
+                                               mode != Mode::Field, c.st);
+    });
   }
   if (L.status != MLMC_OK) return L.status;
   out.assign(G.size(), GroupOut{});
@@ -432,7 +508,7 @@ mlmc_status run_once(mlmcc_ctx& c, const std::vector<Group>& groups, Mode mode, 
     CK(cudaMemsetAsync(b.F.acc, 0, sizeof(double) * 4 * b.S, c.st), "memset");
     CK(cudaMemsetAsync(b.F.c, 0, sizeof(float) * 3 * b.S * b.N, c.st), "memset");
   }
-  L(mlmcc::launch_build_fine(sc.fine, c.st), "stencil");
+  L(kOpBuild, sc.fine, mlmcc::launch_build_fine);
   if (mode == Mode::Apply) {
     const GroupBufs& b = G[0];
     const size_t cnt = (size_t)b.S * 3 * b.N;
@@ -441,40 +517,40 @@ mlmc_status run_once(mlmcc_ctx& c, const std::vector<Group>& groups, Mode mode, 
     ys = xs + cnt;
     xa = ys + cnt;
     CK(cudaMemcpyAsync(xa, x_in, sizeof(double) * cnt, cudaMemcpyDefault, c.st), "apply input");
-    L(mlmcc::launch_aos_to_soa(xa, xs, b.S, b.N, c.st), "layout");
-    L(mlmcc::launch_apply64(sc.fine, xs, ys, c.st), "apply");
-    L(mlmcc::launch_soa_to_aos(ys, xa, b.S, b.n, false, 0.0, c.st), "layout");
+    L(kOpLayout, cnt, [&] { return mlmcc::launch_aos_to_soa(xa, xs, b.S, b.N, c.st); });
+    L(kOpResid64, items_of(sc.fine), [&] { return mlmcc::launch_apply64(sc.fine, xs, ys, c.st); });
+    L(kOpLayout, cnt, [&] { return mlmcc::launch_soa_to_aos(ys, xa, b.S, b.n, false, 0.0, c.st); });
     if (L.status == MLMC_OK) CK(cudaMemcpyAsync(y_out, xa, sizeof(double) * cnt, cudaMemcpyDefault, c.st), "copy");
     cudaFreeAsync(xs, c.st);
     CK(cudaStreamSynchronize(c.st), "apply");
     return L.status;
   }
-  for (size_t k = 0; k < sc.rap.size(); ++k) L(mlmcc::launch_rap(sc.rap[k], c.st), "galerkin");
-  L(mlmcc::launch_coarsest_inverse(sc.inverse, c.st), "coarsest inverse");
+  for (size_t k = 0; k < sc.rap.size(); ++k) L(kOpRap, sc.rap[k], mlmcc::launch_rap);
+  L(kOpInverse, sc.inverse, mlmcc::launch_coarsest_inverse);
   if (L.status != MLMC_OK) return L.status;
   const double rtol = c.cfg.rtol > 0 ? c.cfg.rtol : 1e-8;
   const int max_iter = c.cfg.max_iter > 0 ? c.cfg.max_iter : 400;
   for (int refine = 0; refine < kMaxRefine; ++refine) {
-    L(mlmcc::launch_resid64(sc.fine, c.st), "residual");
-    L(mlmcc::launch_outer_check(sc.samples, rtol, max_iter, c.st), "refinement");
+    L(kOpResid64, sc.fine, mlmcc::launch_resid64);
+    L(kOpScalar, items_of(sc.samples), [&] { return mlmcc::launch_outer_check(sc.samples, rtol, max_iter, c.st); });
     CK(cudaMemsetAsync(count_dev, 0, sizeof(int), c.st), "memset");
-    L(mlmcc::launch_count_active(sc.samples, count_dev, c.st), "count");
+    L(kOpScalar, items_of(sc.samples), [&] { return mlmcc::launch_count_active(sc.samples, count_dev, c.st); });
     if (L.status != MLMC_OK) return L.status;
     int act = 0;
     if ((s = read_count(c, count_dev, &act)) != MLMC_OK) return s;
     if (act == 0) break;
     vcycle(L, sc, c.st);
-    L(mlmcc::launch_scal_b(sc.samples, max_iter, c.st), "cg start");
+    L(kOpScalar, items_of(sc.samples), [&] { return mlmcc::launch_scal_b(sc.samples, max_iter, c.st); });
     if (L.status != MLMC_OK) return L.status;
     for (int rep = 0; rep < max_iter / kGraphIters + 2; ++rep) {
       if ((s = iterations(c, sc, G, count_dev, max_iter)) != MLMC_OK) return s;
       if ((s = read_count(c, count_dev, &act)) != MLMC_OK) return s;
       if (act == 0) break;
     }
-    L(mlmcc::launch_accumulate(sc.fine, c.st), "accumulate");
+    L(kOpAccumulate, sc.fine, mlmcc::launch_accumulate);
   }
-  L(mlmcc::launch_qoi(sc.qoi, c.st), "quantities");
-  L(mlmcc::launch_qoi_final(sc.samples, c.st), "quantities");
+  L(kOpQoi, sc.qoi, mlmcc::launch_qoi);
+  L(kOpScalar, sc.samples, mlmcc::launch_qoi_final);
   if (L.status != MLMC_OK) return L.status;
   for (size_t g = 0; g < G.size(); ++g) {
     if ((s = copy_from(c, G[g].F.q_out, 2 * (size_t)G[g].S, out[g].q)) != MLMC_OK) return s;
@@ -485,7 +561,7 @@ mlmc_status run_once(mlmcc_ctx& c, const std::vector<Group>& groups, Mode mode, 
     const size_t cnt = (size_t)b.S * 3 * b.N;
     double* tmp = nullptr;
     CK(cudaMallocAsync(&tmp, sizeof(double) * cnt, c.st), "alloc");
-    L(mlmcc::launch_soa_to_aos(b.F.d64, tmp, b.S, b.n, true, c.cfg.shortening, c.st), "layout");
+    L(kOpLayout, cnt, [&] { return mlmcc::launch_soa_to_aos(b.F.d64, tmp, b.S, b.n, true, c.cfg.shortening, c.st); });
     if (L.status == MLMC_OK) {
       out[0].d.resize(cnt);
       CK(cudaMemcpyAsync(out[0].d.data(), tmp, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.st), "copy");
@@ -495,6 +571,7 @@ mlmc_status run_once(mlmcc_ctx& c, const std::vector<Group>& groups, Mode mode, 
   }
   CK(cudaMemcpyAsync(c.pinned, count_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, c.st), "copy");
   CK(cudaStreamSynchronize(c.st), "solve");
+  if (c.prof_on) c.prof_collect();
   if (c.pinned[1]) return c.fail(MLMC_ERR_CUDA, "normal generator exceeded its draw cap");
   c.last_iters = std::max(c.last_iters, c.pinned[2]);
   c.last_refine = std::max(c.last_refine, c.pinned[3]);
@@ -709,12 +786,15 @@ mlmc_status mlmcc_sample_levels(mlmcc_ctx* h, int32_t n_req, const int32_t* leve
     CK(cudaMemcpyAsync(dqf, &qf[2 * base], sizeof(double) * 2 * n, cudaMemcpyHostToDevice, c.st), "copy");
     CK(cudaMemcpyAsync(dqc, &qc[2 * base], sizeof(double) * 2 * n, cudaMemcpyHostToDevice, c.st), "copy");
     CK(cudaMemcpyAsync(dst, &sts[base], sizeof(int) * n, cudaMemcpyHostToDevice, c.st), "copy");
-    CK(mlmc::launch_moments(dqf, lv > 0 ? dqc : nullptr, dst, (int64_t)n, c.acc_dev + lv, c.st), "moments");
-    ++c.launches;
+    Launcher L{c};
+    if (!L(kOpMoments, (int64_t)n,
+           [&] { return mlmc::launch_moments(dqf, lv > 0 ? dqc : nullptr, dst, (int64_t)n, c.acc_dev + lv, c.st); }))
+      return L.status;
     base += n;
   }
   cudaFreeAsync(tmp, c.st);
   CK(cudaStreamSynchronize(c.st), "moments");
+  if (c.prof_on) c.prof_collect();
   if ((s = copy_out(c, q_fine, qf.data(), qf.size())) != MLMC_OK) return s;
   if ((s = copy_out(c, q_coarse, qc.data(), qc.size())) != MLMC_OK) return s;
   return copy_out(c, status, sts.data(), sts.size());
@@ -844,6 +924,28 @@ mlmc_status mlmcc_last_iters(mlmcc_ctx* h, int32_t* iterations, int32_t* refinem
   if (refinements) *refinements = h->last_refine;
   return MLMC_OK;
 }
+
+mlmc_status mlmcc_profile_enable(mlmcc_ctx* h, int32_t on) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->st);
+  h->prof_collect();
+  h->prof_on = on != 0;
+  for (int k = 0; k < kOpCount; ++k) {
+    h->prof_ms[k] = 0.0;
+    h->prof_launches[k] = h->prof_items[k] = 0;
+  }
+  return MLMC_OK;
+}
+
+mlmc_status mlmcc_profile_get(mlmcc_ctx* h, int32_t op, double* ms, int64_t* launches, int64_t* items) {
+  if (!h || op < 0 || op >= kOpCount) return MLMC_ERR_INVALID_ARG;
+  if (ms) *ms = h->prof_ms[op];
+  if (launches) *launches = h->prof_launches[op];
+  if (items) *items = h->prof_items[op];
+  return MLMC_OK;
+}
+
+const char* mlmcc_profile_name(int32_t op) { return (op >= 0 && op < kOpCount) ? kOpNames[op] : nullptr; }
 
 mlmc_status mlmcc_launch_count(mlmcc_ctx* h, int64_t* launches) {
   if (!h || !launches) return MLMC_ERR_INVALID_ARG;
