@@ -176,113 +176,271 @@ __device__ __forceinline__ Item item_of(const Views& V, int per_sample) {
 }
 
 
+
+// ---------------------------------------------------------------- float-float arithmetic
+//
+// A value is hi + lo with |lo| <= ulp(hi) / 2 (about 48 significant bits). GB300's FP64
+// rate is a small fraction of its FP32 rate, so the parts that need more than FP32 (the
+// stencil of the refinement residual, the residual itself, the KL synthesis) run on the
+// FP32 pipes with the error-free transformations of Dekker and Knuth. Every operation
+// uses explicitly rounded intrinsics, so no contraction changes them.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_of(double a) {
+  const float h = __double2float_rn(a);
+  return {h, __double2float_rn(a - (double)h)};
+}
+__device__ __forceinline__ double ff_dbl(ff a) { return (double)a.hi + (double)a.lo; }
+// acc += a * b
+__device__ __forceinline__ void ff_fma(ff& acc, ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);          // exact error of the product
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(acc.hi, p);          // two-sum of acc.hi and p
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float t = __fadd_rn(err, __fadd_rn(e, acc.lo));
+  const float hi = __fadd_rn(s, t);              // renormalise
+  acc.lo = __fsub_rn(t, __fsub_rn(hi, s));
+  acc.hi = hi;
+}
+// acc += a * b with b a plain float
+__device__ __forceinline__ void ff_fma(ff& acc, ff a, float b) { ff_fma(acc, a, ff{b, 0.f}); }
+
+// y += (stencil row of node (i, j)) * x in float-float; the stencil is (Ah, Al).
+template <class XF>
+__device__ __forceinline__ void apply_node_ff(const float* __restrict__ Ah, const float* __restrict__ Al, int N, int n,
+                                              int i, int j, XF xf, ff y[3]) {
+  const int p = j * (n + 1) + i;
+  const int w = n + 1;
+  auto A = [&](int k, int q) { return ff{Ah[(size_t)k * N + q], Al[(size_t)k * N + q]}; };
+  {
+    ff v[3];
+    xf(p, v);
+    const ff a00 = A(0, p), a01 = A(1, p), a02 = A(2, p), a11 = A(3, p), a12 = A(4, p), a22 = A(5, p);
+    ff_fma(y[0], a00, v[0]);
+    ff_fma(y[0], a01, v[1]);
+    ff_fma(y[0], a02, v[2]);
+    ff_fma(y[1], a01, v[0]);
+    ff_fma(y[1], a11, v[1]);
+    ff_fma(y[1], a12, v[2]);
+    ff_fma(y[2], a02, v[0]);
+    ff_fma(y[2], a12, v[1]);
+    ff_fma(y[2], a22, v[2]);
+  }
+  auto fwd = [&](int k0, int q) {
+    ff v[3];
+    xf(q, v);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) ff_fma(y[a], A(k0 + 3 * a + b, p), v[b]);
+  };
+  auto bwd = [&](int k0, int q) {
+    ff v[3];
+    xf(q, v);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) ff_fma(y[a], A(k0 + 3 * b + a, q), v[b]);
+  };
+  if (i < n) fwd(kE, p + 1);
+  if (j < n) {
+    fwd(kN, p + w);
+    if (i < n) fwd(kNE, p + w + 1);
+    if (i > 0) fwd(kNW, p + w - 1);
+  }
+  if (i > 0) bwd(kE, p - 1);
+  if (j > 0) {
+    bwd(kN, p - w);
+    if (i > 0) bwd(kNE, p - w - 1);
+    if (i < n) bwd(kNW, p - w + 1);
+  }
+}
+
+// KL synthesis phi[s][e] = sum_k B[e][k] xi[s][k] in float-float: tiles of 128 elements
+// x 16 samples, 16-term slices of both operands in shared memory; each thread 8
+// elements (strided by 16) of one sample. Writes (cos 2 phi, sin 2 phi, cos 4 phi,
+// sin 4 phi) as float-float pairs when trig, else phi in double.
+constexpr int kSynE = 128, kSynS = 16, kSynK = 16;
+__global__ void __launch_bounds__(256) k_synth_ff(const double* __restrict__ xi, const float* __restrict__ Bh,
+                                                  const float* __restrict__ Bl, int S, int n_el, int K,
+                                                  void* __restrict__ out, bool trig) {
+  __shared__ float sBh[kSynK][kSynE], sBl[kSynK][kSynE];
+  __shared__ float sXh[kSynK][kSynS + 1], sXl[kSynK][kSynS + 1];
+  const int tid = threadIdx.x;
+  const int ls = tid >> 4, le = tid & 15;
+  const int e0 = blockIdx.x * kSynE, s0 = blockIdx.y * kSynS;
+  ff acc[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) acc[a] = ff{0.f, 0.f};
+  for (int k0 = 0; k0 < K; k0 += kSynK) {
+#pragma unroll
+    for (int r = 0; r < (kSynE * kSynK) / 256; ++r) {
+      const int idx = tid + 256 * r;
+      const int row = idx / kSynK, kk = idx % kSynK;
+      const int e = e0 + row, k = k0 + kk;
+      const bool in = e < n_el && k < K;
+      sBh[kk][row] = in ? Bh[(size_t)e * K + k] : 0.f;
+      sBl[kk][row] = in ? Bl[(size_t)e * K + k] : 0.f;
+    }
+    {
+      const int row = tid / kSynK, kk = tid % kSynK;   // 256 = 16 samples x 16 terms
+      const int sm = s0 + row, k = k0 + kk;
+      const ff x = (sm < S && k < K) ? ff_of(xi[(size_t)sm * K + k]) : ff{0.f, 0.f};
+      sXh[kk][row] = x.hi;
+      sXl[kk][row] = x.lo;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kSynK; ++kk) {
+      const ff x{sXh[kk][ls], sXl[kk][ls]};
+#pragma unroll
+      for (int a = 0; a < 8; ++a) ff_fma(acc[a], ff{sBh[kk][le + 16 * a], sBl[kk][le + 16 * a]}, x);
+    }
+    __syncthreads();
+  }
+  const int sm = s0 + ls;
+  if (sm >= S) return;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int e = e0 + le + 16 * a;
+    if (e >= n_el) continue;
+    const double ph = ff_dbl(acc[a]);
+    if (trig) {
+      double sn, cs;
+      sincos(2.0 * ph, &sn, &cs);
+      const ff t[4] = {ff_of(cs), ff_of(sn), ff_of(cs * cs - sn * sn), ff_of(2.0 * sn * cs)};
+      float* o = (float*)out + 8 * ((size_t)sm * n_el + e);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        o[2 * m] = t[m].hi;
+        o[2 * m + 1] = t[m].lo;
+      }
+    } else {
+      ((double*)out)[(size_t)sm * n_el + e] = ph;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- setup
 
-// Fine stencil of the solve mesh in double from the element matrices
-// K_e = sum_m t_m(phi_e) Km[m] (t = 1, c2, s2, c4, s4), the lifting right-hand side
-// b = -K d_prescribed (only u = shortening on x = L is non-zero), the masked FP32 copy
-// and the damped block-Jacobi inverses. Accumulates |b|^2 per sample.
+// Fine stencil of the solve mesh from the element matrices K_e = sum_m t_m(phi_e) Km[m]
+// (t = 1, c2, s2, c4, s4), summed in float-float: the FP32 stencil A is its high part
+// and Alo its low part (the refinement residual uses both). Five threads per node, one
+// per stored block (self, E, N, NE, NW; items ordered sample, block, node so that the
+// stores coalesce); the self-block thread also forms the damped block-Jacobi inverse,
+// the lifting right-hand side b = -K d_prescribed (only u = shortening on x = L is
+// non-zero), d = 0 and |b|^2 per sample.
 __global__ void __launch_bounds__(kThreads) k_build_fine(const __grid_constant__ Views V) {
-  const Item it = item_of(V, V.v[view_of(V)].f.N);
+  const Item it = item_of(V, 5 * V.v[view_of(V)].f.N);
   const View& W = V.v[it.v];
   const int n = W.f.n, N = W.f.N, s = it.s;
   double bb = 0.0;
   if (it.ok) {
-    const int p = it.p, i = p % (n + 1), j = p / (n + 1);
-    const double* __restrict__ Km = &V.cc->Km[W.F.mesh][0][0];
-    const double sh = V.cc->shortening;
-    double blk[5][9];   // self, E, N, NE, NW
+    const int slot = it.p / N, p = it.p - slot * N, i = p % (n + 1), j = p / (n + 1);
+    const float* __restrict__ Kh = &V.cc->Kmh[W.F.mesh][0][0];
+    const float* __restrict__ Kl = &V.cc->Kml[W.F.mesh][0][0];
+    const int oxs[5] = {0, 1, 0, 1, -1}, oys[5] = {0, 0, 1, 1, 1};
+    const int sx = oxs[slot], sy = oys[slot];
+    const bool self = slot == 0;
+    ff blk[9];
 #pragma unroll
-    for (int b = 0; b < 5; ++b)
-#pragma unroll
-      for (int k = 0; k < 9; ++k) blk[b][k] = 0.0;
-    double rhs[3] = {0.0, 0.0, 0.0};
-    // element q = (qx, qy) of the node's four lies at (i - 1 + qx, j - 1 + qy); both loops
-    // unroll, so the node's local index and each corner's block slot are constants
+    for (int k = 0; k < 9; ++k) blk[k] = ff{0.f, 0.f};
+    ff rhs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    const ff msh{V.cc->msh_hi, V.cc->msh_lo};
+    // element q = (qx, qy) of the node's four lies at (i - 1 + qx, j - 1 + qy); the
+    // node's local index a and each corner b's offset are constants after unrolling
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int qx = q & 1, qy = q >> 1;
       const int ie = i - 1 + qx, je = j - 1 + qy;
       if (ie < 0 || je < 0 || ie >= n || je >= n) continue;
       const int dx = 1 - qx, dy = 1 - qy;
-      const int a = dy == 0 ? dx : 3 - dx;   // local index of the node in the element
-      const double* tg = W.F.trig + 2 * ((size_t)s * n * n + (size_t)je * n + ie);
-      const double c2 = tg[0], s2 = tg[1];
-      const double t[5] = {1.0, c2, s2, c2 * c2 - s2 * s2, 2.0 * s2 * c2};
+      const int a = dy == 0 ? dx : 3 - dx;
+      // the corner b of this element at offset (sx, sy) from the node, if any
+      int bsel = -1;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int bx = (b == 1 || b == 2) ? 1 : 0, by = b >= 2 ? 1 : 0;
-        const int ox = bx - dx, oy = by - dy;
-        const int slot = (ox == 0 && oy == 0) ? 0
-                         : (ox == 1 && oy == 0) ? 1
-                         : (ox == 0 && oy == 1) ? 2
-                         : (ox == 1 && oy == 1) ? 3
-                         : (ox == -1 && oy == 1) ? 4 : -1;
-        const bool lift = ie + bx == n;   // corner b carries the prescribed u
-        if (slot < 0 && !lift) continue;
+        if (bx - dx == sx && by - dy == sy) bsel = b;
+      }
+      const bool lift_any = self && ie + 1 == n;   // the element touches x = L
+      if (bsel < 0 && !lift_any) continue;
+      const float* tg = W.F.trig + 8 * ((size_t)s * n * n + (size_t)je * n + ie);
+      const ff t[5] = {ff{1.f, 0.f}, ff{tg[0], tg[1]}, ff{tg[2], tg[3]}, ff{tg[4], tg[5]}, ff{tg[6], tg[7]}};
+      auto entry = [&](int b, int r, int c) {
+        const int off = (3 * a + r) * 12 + 3 * b + c;
+        ff k{0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < kTerms; ++m) ff_fma(k, t[m], ff{Kh[m * 144 + off], Kl[m * 144 + off]});
+        return k;
+      };
+      if (bsel >= 0) {
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            if (slot < 0 && c != 0) continue;
-            const int off = (3 * a + r) * 12 + 3 * b + c;
-            double k = 0.0;
+          for (int c = 0; c < 3; ++c) ff_fma(blk[3 * r + c], entry(bsel, r, c), 1.f);
+      }
+      if (lift_any) {
+        // corners 1 and 2 lie on x = L: rhs -= shortening * K[a, b][:, u]
 #pragma unroll
-            for (int m = 0; m < kTerms; ++m) k += t[m] * Km[m * 144 + off];
-            if (slot >= 0) blk[slot][3 * r + c] += k;
-            if (lift && c == 0) rhs[r] -= sh * k;
-          }
+        for (int b = 1; b <= 2; ++b)
+#pragma unroll
+          for (int r = 0; r < 3; ++r) ff_fma(rhs[r], entry(b, r, 0), msh);
       }
     }
     // Dirichlet rows / columns -> identity
     const int dm = dmask(i, j, n);
-    const int oxs[5] = {0, 1, 0, 1, -1}, oys[5] = {0, 0, 1, 1, 1};
+    const int qi = i + sx, qj = j + sy;
+    const bool in = qi >= 0 && qi <= n && qj <= n;
+    const int dq = in ? dmask(qi, qj, n) : 0;
 #pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      const int qi = i + oxs[b], qj = j + oys[b];
-      const bool in = qi >= 0 && qi <= n && qj <= n;
-      const int dq = in ? dmask(qi, qj, n) : 0;
+    for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const bool rowd = r < 2 && ((dm >> r) & 1), cold = c < 2 && ((dq >> c) & 1);
-          if (!in || rowd || cold) blk[b][3 * r + c] = 0.0;
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-      if ((dm >> r) & 1) {
-        blk[0][4 * r] = 1.0;
-        rhs[r] = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const bool rowd = r < 2 && ((dm >> r) & 1), cold = c < 2 && ((dq >> c) & 1);
+        if (!in || rowd || cold) blk[3 * r + c] = ff{0.f, 0.f};
       }
-    double* A64 = W.F.A64 + (size_t)s * kStencil * N;
-    float* A32 = W.f.A + (size_t)s * kStencil * N;
-    const double self[6] = {blk[0][0], blk[0][1], blk[0][2], blk[0][4], blk[0][5], blk[0][8]};
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      A64[(size_t)k * N + p] = self[k];
-      A32[(size_t)k * N + p] = (float)self[k];
-    }
-#pragma unroll
-    for (int b = 1; b < 5; ++b)
+    float* Ah = W.f.A + (size_t)s * kStencil * N;
+    float* Al = W.F.Alo + (size_t)s * kStencil * N;
+    if (!self) {
+      const int k0 = 6 + 9 * (slot - 1);
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        A64[(size_t)(6 + 9 * (b - 1) + k) * N + p] = blk[b][k];
-        A32[(size_t)(6 + 9 * (b - 1) + k) * N + p] = (float)blk[b][k];
+        Ah[(size_t)(k0 + k) * N + p] = blk[k].hi;
+        Al[(size_t)(k0 + k) * N + p] = blk[k].lo;
       }
-    double inv[6];
-    inv_sym3(self, inv);
-    float* Di = W.f.Dinv + (size_t)s * kDinv * N;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) Di[(size_t)k * N + p] = (float)((double)kOmega * inv[k]);
-    double* b64 = W.F.b64 + (size_t)s * 3 * N;
-    double* d64 = W.F.d64 + (size_t)s * 3 * N;
+      for (int r = 0; r < 2; ++r)
+        if ((dm >> r) & 1) {
+          blk[4 * r] = ff{1.f, 0.f};
+          rhs[r] = ff{0.f, 0.f};
+        }
+      const ff sb[6] = {blk[0], blk[1], blk[2], blk[4], blk[5], blk[8]};
+      float sf[6], inv[6];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      b64[(size_t)c * N + p] = rhs[c];
-      d64[(size_t)c * N + p] = 0.0;
-      bb += rhs[c] * rhs[c];
+      for (int k = 0; k < 6; ++k) {
+        Ah[(size_t)k * N + p] = sb[k].hi;
+        Al[(size_t)k * N + p] = sb[k].lo;
+        sf[k] = sb[k].hi;
+      }
+      inv_sym3(sf, inv);   // the smoother's inverse needs no more than FP32
+      float* Di = W.f.Dinv + (size_t)s * kDinv * N;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Di[(size_t)k * N + p] = kOmega * inv[k];
+      const size_t s3 = (size_t)s * 3 * N;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        W.F.bh[s3 + (size_t)c * N + p] = rhs[c].hi;
+        W.F.bl[s3 + (size_t)c * N + p] = rhs[c].lo;
+        W.F.dh[s3 + (size_t)c * N + p] = 0.f;
+        W.F.dl[s3 + (size_t)c * N + p] = 0.f;
+        bb += (double)rhs[c].hi * (double)rhs[c].hi;
+      }
     }
   }
   SampleState* st = W.F.st;
@@ -372,11 +530,12 @@ __global__ void __launch_bounds__(kThreads) k_rap(const __grid_constant__ Views 
 }
 
 // Dense inverse of the coarsest (2 x 2 elements, 27 DOFs, DOF 3 node + component)
-// operator: one warp per sample, Gauss-Jordan on [M | I] in shared memory (symmetric
-// positive definite: no pivoting; a non-positive pivot leaves the inverse zero).
-constexpr int kGJWarps = 4;
+// operator: one warp per sample, Gauss-Jordan on [M | I] in shared memory, FP32 (the
+// inverse only serves the preconditioner; symmetric positive definite: no pivoting, a
+// non-positive pivot leaves the inverse zero).
+constexpr int kGJWarps = kInverseWarps;
 __global__ void __launch_bounds__(32 * kGJWarps) k_coarsest_inverse(const __grid_constant__ Views V) {
-  __shared__ double M[kGJWarps][kCoarseDofs][2 * kCoarseDofs + 1];
+  __shared__ float M[kGJWarps][kCoarseDofs][2 * kCoarseDofs + 1];
   const int v = view_of(V);
   const View& W = V.v[v];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -384,10 +543,10 @@ __global__ void __launch_bounds__(32 * kGJWarps) k_coarsest_inverse(const __grid
   if (s >= W.f.S) return;   // whole warps
   const int n = W.f.n, N = W.f.N;
   const float* A = W.f.A + (size_t)s * kStencil * N;
-  double(*m)[2 * kCoarseDofs + 1] = M[wid];
+  float(*m)[2 * kCoarseDofs + 1] = M[wid];
   for (int k = lane; k < kCoarseDofs * 2 * kCoarseDofs; k += 32) {
     const int r = k / (2 * kCoarseDofs), c = k % (2 * kCoarseDofs);
-    m[r][c] = (c - kCoarseDofs == r) ? 1.0 : 0.0;
+    m[r][c] = (c - kCoarseDofs == r) ? 1.f : 0.f;
   }
   __syncwarp();
   if (lane < N) {
@@ -400,20 +559,20 @@ __global__ void __launch_bounds__(32 * kGJWarps) k_coarsest_inverse(const __grid
         block_of(A, N, n, i, j, ox, oy, B);
         const int q = qj * (n + 1) + qi;
         for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) m[3 * lane + a][3 * q + b] = (double)B[3 * a + b];
+          for (int b = 0; b < 3; ++b) m[3 * lane + a][3 * q + b] = B[3 * a + b];
       }
   }
   __syncwarp();
   bool ok = true;
   for (int k = 0; k < kCoarseDofs; ++k) {
-    const double piv = m[k][k];
-    ok = ok && piv > 0.0;
-    const double ip = piv > 0.0 ? 1.0 / piv : 0.0;
+    const float piv = m[k][k];
+    ok = ok && piv > 0.f;
+    const float ip = piv > 0.f ? 1.f / piv : 0.f;
     __syncwarp();
     for (int c = lane; c < 2 * kCoarseDofs; c += 32) m[k][c] *= ip;
     __syncwarp();
     if (lane < kCoarseDofs && lane != k) {
-      const double f = m[lane][k];
+      const float f = m[lane][k];
       for (int c = 0; c < 2 * kCoarseDofs; ++c) m[lane][c] -= f * m[k][c];
     }
     __syncwarp();
@@ -421,7 +580,7 @@ __global__ void __launch_bounds__(32 * kGJWarps) k_coarsest_inverse(const __grid
   float* out = W.Ainv + (size_t)s * kCoarseDofs * kCoarseDofs;
   for (int k = lane; k < kCoarseDofs * kCoarseDofs; k += 32) {
     const int r = k / kCoarseDofs, c = k % kCoarseDofs;
-    out[k] = ok ? (float)m[r][kCoarseDofs + c] : 0.f;
+    out[k] = ok ? m[r][kCoarseDofs + c] : 0.f;
   }
 }
 
@@ -691,8 +850,9 @@ __global__ void k_count_active(const __grid_constant__ Views V, int* count) {
 
 // ---------------------------------------------------------------- FP64 refinement
 
-// r = b - A64 d in double; the FP32 correction right-hand side r32 and |r|^2.
-__global__ void __launch_bounds__(kThreads) k_resid64(const __grid_constant__ Views V) {
+// r = b - A d with the float-float stencil and solution, in float-float; the FP32
+// correction right-hand side r32 and |r|^2. With first (d = 0) r = b.
+__global__ void __launch_bounds__(kThreads) k_resid64(const __grid_constant__ Views V, bool first) {
   const Item it = item_of(V, V.v[view_of(V)].f.N);
   const View& W = V.v[it.v];
   const bool ok = it.ok && !W.F.st[it.s].done;
@@ -700,22 +860,28 @@ __global__ void __launch_bounds__(kThreads) k_resid64(const __grid_constant__ Vi
   if (ok) {
     const int n = W.f.n, N = W.f.N, p = it.p, i = p % (n + 1), j = p / (n + 1);
     const size_t s3 = (size_t)it.s * 3 * N;
-    const double* __restrict__ A = W.F.A64 + (size_t)it.s * kStencil * N;
-    const double* __restrict__ d = W.F.d64 + s3;
-    const double* __restrict__ b = W.F.b64 + s3;
-    auto xf = [&](int q, double v[3]) {
-      v[0] = d[q];
-      v[1] = d[N + q];
-      v[2] = d[2 * N + q];
-    };
-    double y[3] = {0.0, 0.0, 0.0};
-    apply_node(A, N, n, i, j, xf, y);
+    ff y[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    if (!first) {
+      const float* __restrict__ Ah = W.f.A + (size_t)it.s * kStencil * N;
+      const float* __restrict__ Al = W.F.Alo + (size_t)it.s * kStencil * N;
+      const float* __restrict__ dh = W.F.dh + s3;
+      const float* __restrict__ dl = W.F.dl + s3;
+      auto xf = [&](int q, ff v[3]) {
+        v[0] = ff{dh[q], dl[q]};
+        v[1] = ff{dh[N + q], dl[N + q]};
+        v[2] = ff{dh[2 * N + q], dl[2 * N + q]};
+      };
+      apply_node_ff(Ah, Al, N, n, i, j, xf, y);
+    }
     float* r = W.f.r + s3;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double e = b[(size_t)c * N + p] - y[c];
-      r[(size_t)c * N + p] = (float)e;
-      rr += e * e;
+      // e = b - y: b + (-y) in float-float, then rounded
+      ff e{W.F.bh[s3 + (size_t)c * N + p], W.F.bl[s3 + (size_t)c * N + p]};
+      ff_fma(e, y[c], -1.f);
+      const float ev = __fadd_rn(e.hi, e.lo);
+      r[(size_t)c * N + p] = ev;
+      rr += (double)ev * (double)ev;
     }
   }
   SampleState* st = W.F.st;
@@ -748,19 +914,21 @@ __global__ void k_outer_check(const __grid_constant__ Views V, double rtol, int 
   st->r64n2 = 0.0;
 }
 
-// d += c, c = 0 (c is zero for samples that did not run).
+// d += c in float-float, c = 0 (c is zero for samples that did not run).
 __global__ void __launch_bounds__(kThreads) k_accumulate(const __grid_constant__ Views V) {
   const Item it = item_of(V, V.v[view_of(V)].f.N);
   if (!it.ok) return;
   const View& W = V.v[it.v];
   const int N = W.f.N;
   const size_t s3 = (size_t)it.s * 3 * N;
-  double* d = W.F.d64 + s3;
   float* c = W.F.c + s3;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const size_t o = (size_t)k * N + it.p;
-    d[o] += (double)c[o];
+    ff d{W.F.dh[s3 + o], W.F.dl[s3 + o]};
+    ff_fma(d, ff{c[o], 0.f}, 1.f);
+    W.F.dh[s3 + o] = d.hi;
+    W.F.dl[s3 + o] = d.lo;
     c[o] = 0.f;
   }
 }
@@ -789,19 +957,20 @@ __global__ void __launch_bounds__(kThreads) k_qoi(const __grid_constant__ Views 
       ie = n - 1;
       je = it.p - ncen * ncen;
     }
-    const double* __restrict__ d = W.F.d64 + (size_t)it.s * 3 * N;
+    const float* __restrict__ dh = W.F.dh + (size_t)it.s * 3 * N;
+    const float* __restrict__ dl = W.F.dl + (size_t)it.s * 3 * N;
     double de[12];
     const int cx[4] = {0, 1, 1, 0}, cy[4] = {0, 0, 1, 1};
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const int q = (je + cy[a]) * (n + 1) + ie + cx[a];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) de[3 * a + c] = d[(size_t)c * N + q];
+      for (int c = 0; c < 3; ++c) de[3 * a + c] = (double)dh[(size_t)c * N + q] + (double)dl[(size_t)c * N + q];
       if (ie + cx[a] == n) de[3 * a] += K.shortening;
     }
-    const double* tg = W.F.trig + 2 * ((size_t)it.s * n * n + (size_t)je * n + ie);
-    const double c2 = tg[0], s2 = tg[1];
-    const double t[5] = {1.0, c2, s2, c2 * c2 - s2 * s2, 2.0 * s2 * c2};
+    const float* tg = W.F.trig + 8 * ((size_t)it.s * n * n + (size_t)je * n + ie);
+    const double c2 = (double)tg[0] + (double)tg[1], s2 = (double)tg[2] + (double)tg[3];
+    const double t[5] = {1.0, c2, s2, (double)tg[4] + (double)tg[5], (double)tg[6] + (double)tg[7]};
     if (cen) {
       double Cg[16];
 #pragma unroll
@@ -895,17 +1064,18 @@ __global__ void __launch_bounds__(kThreads) k_apply64(const __grid_constant__ Vi
   const View& W = V.v[it.v];
   const int n = W.f.n, N = W.f.N, p = it.p, i = p % (n + 1), j = p / (n + 1);
   const size_t s3 = (size_t)it.s * 3 * N;
-  const double* A = W.F.A64 + (size_t)it.s * kStencil * N;
+  const float* Ah = W.f.A + (size_t)it.s * kStencil * N;
+  const float* Al = W.F.Alo + (size_t)it.s * kStencil * N;
   const double* xs = x + s3;
-  auto xf = [&](int q, double v[3]) {
-    v[0] = xs[q];
-    v[1] = xs[N + q];
-    v[2] = xs[2 * N + q];
+  auto xf = [&](int q, ff v[3]) {
+    v[0] = ff_of(xs[q]);
+    v[1] = ff_of(xs[N + q]);
+    v[2] = ff_of(xs[2 * N + q]);
   };
-  double o[3] = {0.0, 0.0, 0.0};
-  apply_node(A, N, n, i, j, xf, o);
+  ff o[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  apply_node_ff(Ah, Al, N, n, i, j, xf, o);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) y[s3 + (size_t)c * N + p] = o[c];
+  for (int c = 0; c < 3; ++c) y[s3 + (size_t)c * N + p] = ff_dbl(o[c]);
 }
 
 __global__ void k_aos_to_soa(const double* __restrict__ in, double* __restrict__ out, int S, int N) {
@@ -923,6 +1093,18 @@ __global__ void k_soa_to_aos(const double* __restrict__ in, double* __restrict__
   const int64_t s = k / (3 * N), r = k % (3 * N), p = r / 3, c = r % 3;
   double v = in[(s * 3 + c) * N + p];
   if (lift && c == 0 && p % (n + 1) == n) v += sh;
+  out[k] = v;
+}
+
+__global__ void k_ff_to_aos(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ out, int S,
+                            int n, double sh) {
+  const int N = (n + 1) * (n + 1);
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (int64_t)S * N * 3) return;
+  const int64_t s = k / (3 * N), r = k % (3 * N), p = r / 3, c = r % 3;
+  const int64_t o = (s * 3 + c) * N + p;
+  double v = (double)hi[o] + (double)lo[o];
+  if (c == 0 && p % (n + 1) == n) v += sh;
   out[k] = v;
 }
 
@@ -961,7 +1143,9 @@ cudaError_t launch_cg_apply(const Views& V, bool odd, cudaStream_t st) {
 cudaError_t launch_cg_update(const Views& V, bool odd, cudaStream_t st) {
   MLMCC_LAUNCH(k_cg_update, kThreads, V, odd);
 }
-cudaError_t launch_resid64(const Views& V, cudaStream_t st) { MLMCC_LAUNCH(k_resid64, kThreads, V); }
+cudaError_t launch_resid64(const Views& V, bool first, cudaStream_t st) {
+  MLMCC_LAUNCH(k_resid64, kThreads, V, first);
+}
 cudaError_t launch_accumulate(const Views& V, cudaStream_t st) { MLMCC_LAUNCH(k_accumulate, kThreads, V); }
 cudaError_t launch_qoi(const Views& V, cudaStream_t st) { MLMCC_LAUNCH(k_qoi, kThreads, V); }
 cudaError_t launch_apply64(const Views& V, const double* x, double* y, cudaStream_t st) {
@@ -989,6 +1173,21 @@ cudaError_t launch_qoi_final(const Views& V, cudaStream_t st) {
   k_qoi_final<<<per_sample_blocks(V), kThreads, 0, st>>>(V);
   return cudaGetLastError();
 }
+cudaError_t launch_synth_ff(const double* xi, const float* Bh, const float* Bl, int S, int n_el, int K, void* out,
+                            bool trig, cudaStream_t st) {
+  if (S <= 0 || n_el <= 0) return cudaSuccess;
+  dim3 grid((n_el + kSynE - 1) / kSynE, (S + kSynS - 1) / kSynS);
+  k_synth_ff<<<grid, 256, 0, st>>>(xi, Bh, Bl, S, n_el, K, out, trig);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ff_to_aos(const float* hi, const float* lo, double* out, int S, int n, double sh, cudaStream_t st) {
+  const int64_t cnt = (int64_t)S * (n + 1) * (n + 1) * 3;
+  if (cnt <= 0) return cudaSuccess;
+  k_ff_to_aos<<<(unsigned)((cnt + kThreads - 1) / kThreads), kThreads, 0, st>>>(hi, lo, out, S, n, sh);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_aos_to_soa(const double* in, double* out, int S, int N, cudaStream_t st) {
   const int64_t n = (int64_t)S * N * 3;
   if (n <= 0) return cudaSuccess;

@@ -28,6 +28,7 @@ constexpr int kTerms = 5;         // trig terms of the element matrix: 1, c2, s2
 constexpr int kCoarsest = 2;      // elements per side of the coarsest multigrid mesh
 constexpr int kCoarseDofs = 27;   // 3 (kCoarsest + 1)^2
 constexpr int kThreads = 256;
+constexpr int kInverseWarps = 8;   // samples (one warp each) per block of the coarsest inverse
 constexpr float kOmega = 0.6f;    // block-Jacobi damping
 
 // One multigrid level of one batch.
@@ -56,10 +57,10 @@ struct SampleState {
 
 // The solve mesh of one batch: FP64 system, CG vectors and per-element trig values.
 struct FineSys {
-  double* A64;    // [S][kStencil][N]
-  double* b64;    // [S][3][N]
-  double* d64;    // [S][3][N] solution without the prescribed values
-  const double* trig;   // [S][n * n][2] (cos 2 phi, sin 2 phi)
+  float* Alo;     // [S][kStencil][N] low part of the float-float stencil (high part: level 0's A)
+  float *bh, *bl;   // [S][3][N] right-hand side, float-float
+  float *dh, *dl;   // [S][3][N] solution without the prescribed values, float-float
+  const float* trig;   // [S][n * n][8]: cos 2 phi, sin 2 phi, cos 4 phi, sin 4 phi as (hi, lo) pairs
   float *c, *p0, *p1, *q;   // [S][3][N]
   SampleState* st;          // [S]
   double* acc;              // [S][4]: f*, int sigma_x, reaction, spare
@@ -92,13 +93,15 @@ struct Views {
 // cos 4 phi, sin 4 phi), and C*(phi) as sum_m t_m Cm[m] for the stresses.
 struct Consts {
   double Km[kMaxMeshes][kTerms][144];
+  float Kmh[kMaxMeshes][kTerms][144], Kml[kMaxMeshes][kTerms][144];   // Km split hi + lo
   double Cm[kTerms][16];
   double h[kMaxMeshes];
   double shortening, tau_y, R;
+  float msh_hi, msh_lo;   // -shortening, float-float
 };
 
 // setup
-cudaError_t launch_build_fine(const Views& v, cudaStream_t st);       // A64, b64, A (f level), Dinv, |b|^2
+cudaError_t launch_build_fine(const Views& v, cudaStream_t st);       // A + Alo, b64, Dinv, |b|^2
 cudaError_t launch_rap(const Views& v, cudaStream_t st);              // c-level A, Dinv from f-level A
 cudaError_t launch_coarsest_inverse(const Views& v, cudaStream_t st);  // Ainv from the f level (n = 2)
 // V-cycle
@@ -114,17 +117,25 @@ cudaError_t launch_cg_update(const Views& v, bool odd, cudaStream_t st);
 cudaError_t launch_scal_b(const Views& v, int max_iter, cudaStream_t st);
 cudaError_t launch_count_active(const Views& v, int* count, cudaStream_t st);
 // FP64 refinement
-cudaError_t launch_resid64(const Views& v, cudaStream_t st);
+cudaError_t launch_resid64(const Views& v, bool first, cudaStream_t st);   // first: d = 0
 cudaError_t launch_outer_check(const Views& v, double rtol, int max_iter, cudaStream_t st);
 cudaError_t launch_accumulate(const Views& v, cudaStream_t st);
 // quantities of interest
 cudaError_t launch_qoi(const Views& v, cudaStream_t st);
 cudaError_t launch_qoi_final(const Views& v, cudaStream_t st);
-// y = A64 x on the solve mesh (x, y [S][3][N] doubles)
+// y = A x on the solve mesh with the float-float stencil (x, y [S][3][N] doubles)
 cudaError_t launch_apply64(const Views& v, const double* x, double* y, cudaStream_t st);
+// KL synthesis in float-float: basis (hi, lo) [n_el][K] floats, xi [S][K] doubles ->
+// with trig, out = float [S][n_el][8] (cos 2 phi, sin 2 phi, cos 4 phi, sin 4 phi as
+// hi, lo pairs); else out = double phi [S][n_el]
+cudaError_t launch_synth_ff(const double* xi, const float* Bh, const float* Bl, int S, int n_el, int K, void* out,
+                            bool trig, cudaStream_t st);
 // [S][N][3] <-> [S][3][N] (doubles); add_lift adds the prescribed u = shortening on x = L
 cudaError_t launch_aos_to_soa(const double* in, double* out, int S, int N, cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double* in, double* out, int S, int n, bool add_lift, double shortening,
                               cudaStream_t st);
+// float-float [S][3][N] (hi, lo) -> double [S][N][3], adding u = shortening on x = L
+cudaError_t launch_ff_to_aos(const float* hi, const float* lo, double* out, int S, int n, double shortening,
+                             cudaStream_t st);
 
 }  // namespace mlmcc

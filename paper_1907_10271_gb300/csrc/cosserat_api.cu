@@ -57,7 +57,7 @@ struct GroupBufs {
   int* levels;
   uint64_t* ids;
   double* xi;
-  double* trig;
+  float* trig;   // [S][n_el][8] (or phi [S][n_el] doubles in field mode)
   mlmcc::FineSys F;
   std::vector<mlmcc::Lev> lev;
   float* Ainv;
@@ -71,7 +71,7 @@ struct mlmcc_ctx {
   std::string err;
   mlmcc::Consts consts;
   mlmcc::Consts* consts_dev = nullptr;
-  std::vector<double*> basis;   // per mesh [n_el][n_kl] (double), made on first use
+  std::vector<float*> basis;    // per mesh [2][n_el][n_kl]: hi, lo floats of the double basis, made on first use
   std::vector<int> klo, khi;
   mlmc::LevelAcc* acc_dev = nullptr;
   std::vector<mlmc::LevelAcc> acc_host;
@@ -142,7 +142,7 @@ struct mlmcc_ctx {
       cudaEventDestroy(q.b);
     }
     for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
-    for (double* b : basis)
+    for (float* b : basis)
       if (b) cudaFree(b);
     if (acc_dev) cudaFree(acc_dev);
     if (consts_dev) cudaFree(consts_dev);
@@ -192,10 +192,12 @@ size_t layout(const mlmcc_ctx& c, const std::vector<Group>& groups, char* base, 
     b.levels = (int*)take(S * sizeof(int));
     b.ids = (uint64_t*)take(S * sizeof(uint64_t));
     b.xi = (double*)take(S * b.nkl * sizeof(double));
-    b.trig = (double*)take(S * nel * 2 * sizeof(double));
-    b.F.A64 = (double*)take(S * mlmcc::kStencil * N * sizeof(double));
-    b.F.b64 = (double*)take(S * 3 * N * sizeof(double));
-    b.F.d64 = (double*)take(S * 3 * N * sizeof(double));
+    b.trig = (float*)take(S * nel * 8 * sizeof(float));
+    b.F.Alo = (float*)take(S * mlmcc::kStencil * N * sizeof(float));
+    b.F.bh = (float*)take(S * 3 * N * sizeof(float));
+    b.F.bl = (float*)take(S * 3 * N * sizeof(float));
+    b.F.dh = (float*)take(S * 3 * N * sizeof(float));
+    b.F.dl = (float*)take(S * 3 * N * sizeof(float));
     b.F.trig = b.trig;
     b.F.c = (float*)take(S * 3 * N * sizeof(float));
     b.F.p0 = (float*)take(S * 3 * N * sizeof(float));
@@ -228,7 +230,7 @@ size_t layout(const mlmcc_ctx& c, const std::vector<Group>& groups, char* base, 
   return off;
 }
 
-enum class Kind { Nodes, CoarseNodes, CoarseDofs, Inverse, Qoi, Samples };
+enum class Kind { Nodes, CoarseNodes, CoarseDofs, Inverse, Qoi, Samples, Build };
 
 // View table of one launch: batches with multigrid level k (f) and k + 1 (c);
 // `need` filters the batches (e.g. those whose coarsest level lies below k).
@@ -252,7 +254,7 @@ Views make_views(const std::vector<GroupBufs>& G, int k, Kind kind, Need need, c
       case Kind::CoarseDofs: v.items = b.S * mlmcc::kCoarseDofs; break;
       case Kind::Inverse:
         v.items = b.S;
-        threads = 4;   // samples per block of the inverse kernel (a warp each)
+        threads = mlmcc::kInverseWarps;   // samples per block of the inverse kernel
         break;
       case Kind::Qoi: {
         const int ncen = b.F.khi - b.F.klo + 1;
@@ -260,6 +262,7 @@ Views make_views(const std::vector<GroupBufs>& G, int k, Kind kind, Need need, c
         break;
       }
       case Kind::Samples: v.items = b.S; break;
+      case Kind::Build: v.items = b.S * 5 * v.f.N; break;
     }
     v.blk0 = blk;
     blk += (v.items + threads - 1) / threads;
@@ -272,7 +275,7 @@ Views make_views(const std::vector<GroupBufs>& G, int k, Kind kind, Need need, c
 // All view tables of one solve.
 struct Sched {
   int maxK = 0;
-  Views fine, samples, qoi, coarse, inverse;
+  Views fine, build, samples, qoi, coarse, inverse;
   std::vector<Views> pre, restr, prol, post, rap;
   int64_t vcycle_kernels = 0;
 };
@@ -282,6 +285,7 @@ Sched schedule(const std::vector<GroupBufs>& G, const mlmcc::Consts* cc) {
   auto all = [](const GroupBufs&) { return true; };
   for (const GroupBufs& b : G) s.maxK = std::max(s.maxK, b.K);
   s.fine = make_views(G, 0, Kind::Nodes, all, cc);
+  s.build = make_views(G, 0, Kind::Build, all, cc);
   s.samples = make_views(G, 0, Kind::Samples, all, cc);
   s.qoi = make_views(G, 0, Kind::Qoi, all, cc);
   s.coarse = make_views(G, 0, Kind::CoarseDofs, all, cc);
@@ -304,10 +308,16 @@ mlmc_status ensure_basis(mlmcc_ctx& c, int m) {
   const int n = c.mesh_n(m), nk = mlmcc::n_kl(c.cfg, m);
   std::vector<double> B;
   mlmcc::kl_basis(c.cfg, n, nk, B);
-  double* d = nullptr;
-  CK(cudaMalloc(&d, sizeof(double) * B.size()), "basis alloc");
+  // float-float split: hi = fl(b), lo = fl(b - hi)
+  std::vector<float> hl(2 * B.size());
+  for (size_t k = 0; k < B.size(); ++k) {
+    hl[k] = (float)B[k];
+    hl[B.size() + k] = (float)(B[k] - (double)hl[k]);
+  }
+  float* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(float) * hl.size()), "basis alloc");
   c.basis[m] = d;
-  CK(cudaMemcpyAsync(d, B.data(), sizeof(double) * B.size(), cudaMemcpyHostToDevice, c.st), "basis upload");
+  CK(cudaMemcpyAsync(d, hl.data(), sizeof(float) * hl.size(), cudaMemcpyHostToDevice, c.st), "basis upload");
   CK(cudaStreamSynchronize(c.st), "basis upload");
   return MLMC_OK;
 }
@@ -490,15 +500,17 @@ mlmc_status run_once(mlmcc_ctx& c, const std::vector<Group>& groups, Mode mode, 
                                           count_dev + 1, c.st);
     });
     L(kOpSynth, (int64_t)b.S * b.n * b.n, [&] {
-      return mlmc::launch_kl_synthesis<double>(b.xi, c.basis[b.mesh], b.S, b.n * b.n, b.nkl, b.trig,
-                                               mode != Mode::Field, c.st);
+      const size_t nb = (size_t)b.n * b.n * b.nkl;
+      return mlmcc::launch_synth_ff(b.xi, c.basis[b.mesh], c.basis[b.mesh] + nb, b.S, b.n * b.n, b.nkl, b.trig,
+                                    mode != Mode::Field, c.st);
     });
   }
   if (L.status != MLMC_OK) return L.status;
   out.assign(G.size(), GroupOut{});
   if (mode == Mode::Field) {
     for (size_t g = 0; g < G.size(); ++g)
-      if ((s = copy_from(c, G[g].trig, (size_t)G[g].S * G[g].n * G[g].n, out[g].phi)) != MLMC_OK) return s;
+      if ((s = copy_from(c, (const double*)G[g].trig, (size_t)G[g].S * G[g].n * G[g].n, out[g].phi)) != MLMC_OK)
+        return s;
     CK(cudaStreamSynchronize(c.st), "field");
     return MLMC_OK;
   }
@@ -508,7 +520,7 @@ mlmc_status run_once(mlmcc_ctx& c, const std::vector<Group>& groups, Mode mode, 
     CK(cudaMemsetAsync(b.F.acc, 0, sizeof(double) * 4 * b.S, c.st), "memset");
     CK(cudaMemsetAsync(b.F.c, 0, sizeof(float) * 3 * b.S * b.N, c.st), "memset");
   }
-  L(kOpBuild, sc.fine, mlmcc::launch_build_fine);
+  L(kOpBuild, sc.build, mlmcc::launch_build_fine);
   if (mode == Mode::Apply) {
     const GroupBufs& b = G[0];
     const size_t cnt = (size_t)b.S * 3 * b.N;
@@ -531,7 +543,7 @@ mlmc_status run_once(mlmcc_ctx& c, const std::vector<Group>& groups, Mode mode, 
   const double rtol = c.cfg.rtol > 0 ? c.cfg.rtol : 1e-8;
   const int max_iter = c.cfg.max_iter > 0 ? c.cfg.max_iter : 400;
   for (int refine = 0; refine < kMaxRefine; ++refine) {
-    L(kOpResid64, sc.fine, mlmcc::launch_resid64);
+    L(kOpResid64, items_of(sc.fine), [&] { return mlmcc::launch_resid64(sc.fine, refine == 0, c.st); });
     L(kOpScalar, items_of(sc.samples), [&] { return mlmcc::launch_outer_check(sc.samples, rtol, max_iter, c.st); });
     CK(cudaMemsetAsync(count_dev, 0, sizeof(int), c.st), "memset");
     L(kOpScalar, items_of(sc.samples), [&] { return mlmcc::launch_count_active(sc.samples, count_dev, c.st); });
@@ -561,7 +573,7 @@ mlmc_status run_once(mlmcc_ctx& c, const std::vector<Group>& groups, Mode mode, 
     const size_t cnt = (size_t)b.S * 3 * b.N;
     double* tmp = nullptr;
     CK(cudaMallocAsync(&tmp, sizeof(double) * cnt, c.st), "alloc");
-    L(kOpLayout, cnt, [&] { return mlmcc::launch_soa_to_aos(b.F.d64, tmp, b.S, b.n, true, c.cfg.shortening, c.st); });
+    L(kOpLayout, cnt, [&] { return mlmcc::launch_ff_to_aos(b.F.dh, b.F.dl, tmp, b.S, b.n, c.cfg.shortening, c.st); });
     if (L.status == MLMC_OK) {
       out[0].d.resize(cnt);
       CK(cudaMemcpyAsync(out[0].d.data(), tmp, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.st), "copy");
@@ -675,10 +687,19 @@ mlmc_status mlmcc_create(const mlmcc_config* cfg, void* cuda_stream, mlmcc_ctx**
     const double hh = cfg->L / c.mesh_n(lv);
     c.consts.h[lv] = hh;
     // the element matrix is linear in (C*, D*): the trig-basis matrices of K follow
-    for (int m = 0; m < mlmcc::kTerms; ++m) mlmcc::element_matrix(Cm[m], Dm[m], hh, c.consts.Km[lv][m]);
+    for (int m = 0; m < mlmcc::kTerms; ++m) {
+      mlmcc::element_matrix(Cm[m], Dm[m], hh, c.consts.Km[lv][m]);
+      for (int k = 0; k < 144; ++k) {
+        const double v = c.consts.Km[lv][m][k];
+        c.consts.Kmh[lv][m][k] = (float)v;
+        c.consts.Kml[lv][m][k] = (float)(v - (double)c.consts.Kmh[lv][m][k]);
+      }
+    }
     mlmcc::centre_range(*cfg, c.mesh_n(lv), &c.klo[lv], &c.khi[lv]);
   }
   c.consts.shortening = cfg->shortening;
+  c.consts.msh_hi = (float)(-cfg->shortening);
+  c.consts.msh_lo = (float)(-cfg->shortening - (double)c.consts.msh_hi);
   c.consts.tau_y = cfg->tau_y;
   c.consts.R = cfg->R_ratio;
   c.basis.assign(L, nullptr);
