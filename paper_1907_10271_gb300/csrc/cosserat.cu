@@ -7,6 +7,8 @@
 // Threads map to (sample, node) of the view's level in sample-major order.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "cosserat.cuh"
 
 namespace mlmcc {
@@ -29,88 +31,105 @@ __device__ __forceinline__ int dmask(int i, int j, int n) {
 // forward block offsets: E, N, NE, NW
 constexpr int kE = 6, kN = 15, kNE = 24, kNW = 33;
 
-// y += (stencil row of node (i, j)) * x, x given per node by xf(q, v[3])
-template <typename T, typename Acc, class XF>
-__device__ __forceinline__ void apply_node(const T* __restrict__ A, int N, int n, int i, int j, XF xf, Acc y[3]) {
+// Coefficients K0 .. K0 + NK - 1 of node q from the float4 groups of one sample's
+// stencil (group g of node q at A[g * N + q]); constant indices after unrolling.
+template <int K0, int NK>
+__device__ __forceinline__ void load_coef(const float4* __restrict__ A, int N, int q, float (&c)[NK]) {
+  constexpr int g0 = K0 / 4, g1 = (K0 + NK - 1) / 4;
+#pragma unroll
+  for (int g = g0; g <= g1; ++g) {
+    const float4 v = A[(size_t)g * N + q];
+    const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int k = 4 * g + l - K0;
+      if (k >= 0 && k < NK) c[k] = e[l];
+    }
+  }
+}
+
+template <int K0>
+__device__ __forceinline__ void fwd_blk(const float (&a)[kStencil], float4 v, float y[3]) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) y[r] += a[K0 + 3 * r] * v.x + a[K0 + 3 * r + 1] * v.y + a[K0 + 3 * r + 2] * v.z;
+}
+template <int K0>
+__device__ __forceinline__ void bwd_blk(const float4* __restrict__ A, int N, int q, float4 v, float y[3]) {
+  float b[9];
+  load_coef<K0, 9>(A, N, q, b);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) y[r] += b[r] * v.x + b[3 + r] * v.y + b[6 + r] * v.z;
+}
+
+// y += (stencil row of node (i, j)) * x, x per node as float4 (u, v, theta, -) from xf(q).
+// A: one sample's float4 coefficient groups.
+template <class XF>
+__device__ __forceinline__ void apply_node(const float4* __restrict__ A, int N, int n, int i, int j, XF xf,
+                                           float y[3]) {
   const int p = j * (n + 1) + i;
   const int w = n + 1;
+  float a[kStencil];
+  load_coef<0, kStencil>(A, N, p, a);
   {
-    Acc v[3];
-    xf(p, v);
-    const Acc a00 = A[p], a01 = A[N + p], a02 = A[2 * N + p], a11 = A[3 * N + p], a12 = A[4 * N + p],
-              a22 = A[5 * N + p];
-    y[0] += a00 * v[0] + a01 * v[1] + a02 * v[2];
-    y[1] += a01 * v[0] + a11 * v[1] + a12 * v[2];
-    y[2] += a02 * v[0] + a12 * v[1] + a22 * v[2];
+    const float4 v = xf(p);
+    y[0] += a[0] * v.x + a[1] * v.y + a[2] * v.z;
+    y[1] += a[1] * v.x + a[3] * v.y + a[4] * v.z;
+    y[2] += a[2] * v.x + a[4] * v.y + a[5] * v.z;
   }
-  auto fwd = [&](int k0, int q) {
-    Acc v[3];
-    xf(q, v);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      y[a] += (Acc)A[(k0 + 3 * a) * N + p] * v[0] + (Acc)A[(k0 + 3 * a + 1) * N + p] * v[1] +
-              (Acc)A[(k0 + 3 * a + 2) * N + p] * v[2];
-  };
-  auto bwd = [&](int k0, int q) {
-    Acc v[3];
-    xf(q, v);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      y[a] += (Acc)A[(k0 + a) * N + q] * v[0] + (Acc)A[(k0 + 3 + a) * N + q] * v[1] +
-              (Acc)A[(k0 + 6 + a) * N + q] * v[2];
-  };
-  if (i < n) fwd(kE, p + 1);
+  if (i < n) fwd_blk<kE>(a, xf(p + 1), y);
   if (j < n) {
-    fwd(kN, p + w);
-    if (i < n) fwd(kNE, p + w + 1);
-    if (i > 0) fwd(kNW, p + w - 1);
+    fwd_blk<kN>(a, xf(p + w), y);
+    if (i < n) fwd_blk<kNE>(a, xf(p + w + 1), y);
+    if (i > 0) fwd_blk<kNW>(a, xf(p + w - 1), y);
   }
-  if (i > 0) bwd(kE, p - 1);
+  if (i > 0) bwd_blk<kE>(A, N, p - 1, xf(p - 1), y);
   if (j > 0) {
-    bwd(kN, p - w);
-    if (i > 0) bwd(kNE, p - w - 1);
-    if (i < n) bwd(kNW, p - w + 1);
+    bwd_blk<kN>(A, N, p - w, xf(p - w), y);
+    if (i > 0) bwd_blk<kNE>(A, N, p - w - 1, xf(p - w - 1), y);
+    if (i < n) bwd_blk<kNW>(A, N, p - w + 1, xf(p - w + 1), y);
   }
 }
 
 // 3 x 3 block from node (i, j) to (i + ox, j + oy) (both inside), [row][column]
-template <typename T>
-__device__ __forceinline__ void block_of(const T* __restrict__ A, int N, int n, int i, int j, int ox, int oy,
-                                         T out[9]) {
+__device__ __forceinline__ void block_of(const float4* __restrict__ A, int N, int n, int i, int j, int ox, int oy,
+                                         float out[9]) {
   const int p = j * (n + 1) + i;
   const int w = n + 1;
   if (ox == 0 && oy == 0) {
-    out[0] = A[p];
-    out[1] = out[3] = A[N + p];
-    out[2] = out[6] = A[2 * N + p];
-    out[4] = A[3 * N + p];
-    out[5] = out[7] = A[4 * N + p];
-    out[8] = A[5 * N + p];
+    float c[6];
+    load_coef<0, 6>(A, N, p, c);
+    out[0] = c[0];
+    out[1] = out[3] = c[1];
+    out[2] = out[6] = c[2];
+    out[4] = c[3];
+    out[5] = out[7] = c[4];
+    out[8] = c[5];
     return;
   }
-  int k0, q;
+  float b[9];
   bool tr;
   if (oy == 0) {
     tr = ox < 0;
-    k0 = kE;
-    q = tr ? p - 1 : p;
+    load_coef<kE, 9>(A, N, tr ? p - 1 : p, b);
   } else if (ox == 0) {
     tr = oy < 0;
-    k0 = kN;
-    q = tr ? p - w : p;
+    load_coef<kN, 9>(A, N, tr ? p - w : p, b);
   } else if (ox == oy) {
     tr = ox < 0;
-    k0 = kNE;
-    q = tr ? p - w - 1 : p;
+    load_coef<kNE, 9>(A, N, tr ? p - w - 1 : p, b);
   } else {
     tr = oy < 0;   // (+1, -1): the NW block of the south-east node, transposed
-    k0 = kNW;
-    q = tr ? p - w + 1 : p;
+    load_coef<kNW, 9>(A, N, tr ? p - w + 1 : p, b);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) out[3 * a + b] = tr ? A[(k0 + 3 * b + a) * N + q] : A[(k0 + 3 * a + b) * N + q];
+    for (int c = 0; c < 3; ++c) out[3 * a + c] = tr ? b[3 * c + a] : b[3 * a + c];
+}
+
+// coefficient k of node p in a sample's float4 groups, as a plain float address
+__device__ __forceinline__ float* coef_at(float4* A, int N, int k, int p) {
+  return reinterpret_cast<float*>(A + (size_t)(k >> 2) * N + p) + (k & 3);
 }
 
 // inverse of a symmetric 3 x 3 (upper triangle a00 a01 a02 a11 a12 a22), upper triangle out
@@ -209,54 +228,56 @@ __device__ __forceinline__ void ff_fma(ff& acc, ff a, ff b) {
 // acc += a * b with b a plain float
 __device__ __forceinline__ void ff_fma(ff& acc, ff a, float b) { ff_fma(acc, a, ff{b, 0.f}); }
 
-// y += (stencil row of node (i, j)) * x in float-float; the stencil is (Ah, Al).
+// y += (stencil row of node (i, j)) * x in float-float; the stencil is (Ah, Al), both
+// float4 coefficient groups of one sample; xf(q, v[3]) gives x at node q.
 template <class XF>
-__device__ __forceinline__ void apply_node_ff(const float* __restrict__ Ah, const float* __restrict__ Al, int N, int n,
-                                              int i, int j, XF xf, ff y[3]) {
+__device__ __forceinline__ void apply_node_ff(const float4* __restrict__ Ah, const float4* __restrict__ Al, int N,
+                                              int n, int i, int j, XF xf, ff y[3]) {
   const int p = j * (n + 1) + i;
   const int w = n + 1;
-  auto A = [&](int k, int q) { return ff{Ah[(size_t)k * N + q], Al[(size_t)k * N + q]}; };
   {
+    float h[kStencil], l[kStencil];
+    load_coef<0, kStencil>(Ah, N, p, h);
+    load_coef<0, kStencil>(Al, N, p, l);
     ff v[3];
     xf(p, v);
-    const ff a00 = A(0, p), a01 = A(1, p), a02 = A(2, p), a11 = A(3, p), a12 = A(4, p), a22 = A(5, p);
-    ff_fma(y[0], a00, v[0]);
-    ff_fma(y[0], a01, v[1]);
-    ff_fma(y[0], a02, v[2]);
-    ff_fma(y[1], a01, v[0]);
-    ff_fma(y[1], a11, v[1]);
-    ff_fma(y[1], a12, v[2]);
-    ff_fma(y[2], a02, v[0]);
-    ff_fma(y[2], a12, v[1]);
-    ff_fma(y[2], a22, v[2]);
+    const int sym[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ff_fma(y[r], ff{h[sym[r][c]], l[sym[r][c]]}, v[c]);
+    auto fwd = [&](int k0, int q) {
+      ff u[3];
+      xf(q, u);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ff_fma(y[r], ff{h[k0 + 3 * r + c], l[k0 + 3 * r + c]}, u[c]);
+    };
+    if (i < n) fwd(kE, p + 1);
+    if (j < n) {
+      fwd(kN, p + w);
+      if (i < n) fwd(kNE, p + w + 1);
+      if (i > 0) fwd(kNW, p + w - 1);
+    }
   }
-  auto fwd = [&](int k0, int q) {
-    ff v[3];
-    xf(q, v);
+  auto bwd = [&](auto K0, int q) {
+    constexpr int k0 = decltype(K0)::value;
+    float h[9], l[9];
+    load_coef<k0, 9>(Ah, N, q, h);
+    load_coef<k0, 9>(Al, N, q, l);
+    ff u[3];
+    xf(q, u);
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) ff_fma(y[a], A(k0 + 3 * a + b, p), v[b]);
+      for (int c = 0; c < 3; ++c) ff_fma(y[r], ff{h[3 * c + r], l[3 * c + r]}, u[c]);
   };
-  auto bwd = [&](int k0, int q) {
-    ff v[3];
-    xf(q, v);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) ff_fma(y[a], A(k0 + 3 * b + a, q), v[b]);
-  };
-  if (i < n) fwd(kE, p + 1);
-  if (j < n) {
-    fwd(kN, p + w);
-    if (i < n) fwd(kNE, p + w + 1);
-    if (i > 0) fwd(kNW, p + w - 1);
-  }
-  if (i > 0) bwd(kE, p - 1);
+  if (i > 0) bwd(std::integral_constant<int, kE>{}, p - 1);
   if (j > 0) {
-    bwd(kN, p - w);
-    if (i > 0) bwd(kNE, p - w - 1);
-    if (i < n) bwd(kNW, p - w + 1);
+    bwd(std::integral_constant<int, kN>{}, p - w);
+    if (i > 0) bwd(std::integral_constant<int, kNE>{}, p - w - 1);
+    if (i < n) bwd(std::integral_constant<int, kNW>{}, p - w + 1);
   }
 }
 
@@ -404,14 +425,18 @@ __global__ void __launch_bounds__(kThreads) k_build_fine(const __grid_constant__
         const bool rowd = r < 2 && ((dm >> r) & 1), cold = c < 2 && ((dq >> c) & 1);
         if (!in || rowd || cold) blk[3 * r + c] = ff{0.f, 0.f};
       }
-    float* Ah = W.f.A + (size_t)s * kStencil * N;
-    float* Al = W.F.Alo + (size_t)s * kStencil * N;
+    float4* Ah = W.f.A + (size_t)s * kGroups * N;
+    float4* Al = W.F.Alo + (size_t)s * kGroups * N;
     if (!self) {
       const int k0 = 6 + 9 * (slot - 1);
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        Ah[(size_t)(k0 + k) * N + p] = blk[k].hi;
-        Al[(size_t)(k0 + k) * N + p] = blk[k].lo;
+        *coef_at(Ah, N, k0 + k, p) = blk[k].hi;
+        *coef_at(Al, N, k0 + k, p) = blk[k].lo;
+      }
+      if (slot == 4) {   // the two pad coefficients
+        *coef_at(Ah, N, 42, p) = *coef_at(Ah, N, 43, p) = 0.f;
+        *coef_at(Al, N, 42, p) = *coef_at(Al, N, 43, p) = 0.f;
       }
     } else {
 #pragma unroll
@@ -424,23 +449,21 @@ __global__ void __launch_bounds__(kThreads) k_build_fine(const __grid_constant__
       float sf[6], inv[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        Ah[(size_t)k * N + p] = sb[k].hi;
-        Al[(size_t)k * N + p] = sb[k].lo;
+        *coef_at(Ah, N, k, p) = sb[k].hi;
+        *coef_at(Al, N, k, p) = sb[k].lo;
         sf[k] = sb[k].hi;
       }
       inv_sym3(sf, inv);   // the smoother's inverse needs no more than FP32
-      float* Di = W.f.Dinv + (size_t)s * kDinv * N;
+      float4* Di = W.f.Dinv + (size_t)s * kDinvGroups * N;
+      Di[p] = make_float4(kOmega * inv[0], kOmega * inv[1], kOmega * inv[2], kOmega * inv[3]);
+      Di[N + p] = make_float4(kOmega * inv[4], kOmega * inv[5], 0.f, 0.f);
+      const size_t o = (size_t)s * N + p;
+      W.F.bh[o] = make_float4(rhs[0].hi, rhs[1].hi, rhs[2].hi, 0.f);
+      W.F.bl[o] = make_float4(rhs[0].lo, rhs[1].lo, rhs[2].lo, 0.f);
+      W.F.dh[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+      W.F.dl[o] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) Di[(size_t)k * N + p] = kOmega * inv[k];
-      const size_t s3 = (size_t)s * 3 * N;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        W.F.bh[s3 + (size_t)c * N + p] = rhs[c].hi;
-        W.F.bl[s3 + (size_t)c * N + p] = rhs[c].lo;
-        W.F.dh[s3 + (size_t)c * N + p] = 0.f;
-        W.F.dl[s3 + (size_t)c * N + p] = 0.f;
-        bb += (double)rhs[c].hi * (double)rhs[c].hi;
-      }
+      for (int c = 0; c < 3; ++c) bb += (double)rhs[c].hi * (double)rhs[c].hi;
     }
   }
   SampleState* st = W.F.st;
@@ -455,7 +478,7 @@ __global__ void __launch_bounds__(kThreads) k_rap(const __grid_constant__ Views 
   const View& W = V.v[it.v];
   const int nc = W.c.n, Nc = W.c.N, nf = W.f.n, Nf = W.f.N, s = it.s;
   const int P = it.p, I = P % (nc + 1), J = P / (nc + 1);
-  const float* Af = W.f.A + (size_t)s * kStencil * Nf;
+  const float4* Af = W.f.A + (size_t)s * kGroups * Nf;
   float acc[5][9];
 #pragma unroll
   for (int b = 0; b < 5; ++b)
@@ -512,21 +535,28 @@ __global__ void __launch_bounds__(kThreads) k_rap(const __grid_constant__ Views 
 #pragma unroll
   for (int r = 0; r < 2; ++r)
     if ((dm >> r) & 1) acc[0][4 * r] = 1.f;
-  float* Ac = W.c.A + (size_t)s * kStencil * Nc;
   // the diagonal block is symmetric up to rounding: keep the mean of the two triangles
-  const float self[6] = {acc[0][0], 0.5f * (acc[0][1] + acc[0][3]), 0.5f * (acc[0][2] + acc[0][6]), acc[0][4],
-                         0.5f * (acc[0][5] + acc[0][7]), acc[0][8]};
-#pragma unroll
-  for (int k = 0; k < 6; ++k) Ac[(size_t)k * Nc + P] = self[k];
+  float a[44];
+  a[0] = acc[0][0];
+  a[1] = 0.5f * (acc[0][1] + acc[0][3]);
+  a[2] = 0.5f * (acc[0][2] + acc[0][6]);
+  a[3] = acc[0][4];
+  a[4] = 0.5f * (acc[0][5] + acc[0][7]);
+  a[5] = acc[0][8];
 #pragma unroll
   for (int b = 1; b < 5; ++b)
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Ac[(size_t)(6 + 9 * (b - 1) + k) * Nc + P] = acc[b][k];
+    for (int k = 0; k < 9; ++k) a[6 + 9 * (b - 1) + k] = acc[b][k];
+  a[42] = a[43] = 0.f;
+  float4* Ac = W.c.A + (size_t)s * kGroups * Nc;
+#pragma unroll
+  for (int g = 0; g < kGroups; ++g) Ac[(size_t)g * Nc + P] = make_float4(a[4 * g], a[4 * g + 1], a[4 * g + 2], a[4 * g + 3]);
+  const float self[6] = {a[0], a[1], a[2], a[3], a[4], a[5]};
   float inv[6];
   inv_sym3(self, inv);
-  float* Di = W.c.Dinv + (size_t)s * kDinv * Nc;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) Di[(size_t)k * Nc + P] = kOmega * inv[k];
+  float4* Di = W.c.Dinv + (size_t)s * kDinvGroups * Nc;
+  Di[P] = make_float4(kOmega * inv[0], kOmega * inv[1], kOmega * inv[2], kOmega * inv[3]);
+  Di[Nc + P] = make_float4(kOmega * inv[4], kOmega * inv[5], 0.f, 0.f);
 }
 
 // Dense inverse of the coarsest (2 x 2 elements, 27 DOFs, DOF 3 node + component)
@@ -542,7 +572,7 @@ __global__ void __launch_bounds__(32 * kGJWarps) k_coarsest_inverse(const __grid
   const int s = (blockIdx.x - W.blk0) * kGJWarps + wid;
   if (s >= W.f.S) return;   // whole warps
   const int n = W.f.n, N = W.f.N;
-  const float* A = W.f.A + (size_t)s * kStencil * N;
+  const float4* A = W.f.A + (size_t)s * kGroups * N;
   float(*m)[2 * kCoarseDofs + 1] = M[wid];
   for (int k = lane; k < kCoarseDofs * 2 * kCoarseDofs; k += 32) {
     const int r = k / (2 * kCoarseDofs), c = k % (2 * kCoarseDofs);
@@ -588,6 +618,13 @@ __global__ void __launch_bounds__(32 * kGJWarps) k_coarsest_inverse(const __grid
 
 __device__ __forceinline__ bool active(const View& W, int s) { return s >= 0 && W.F.st[s].act; }
 
+__device__ __forceinline__ float4 f4(float a, float b, float c) { return make_float4(a, b, c, 0.f); }
+// x = Dinv r with the block inverse's two groups (d0 = 00 01 02 11, d1 = 12 22 - -)
+__device__ __forceinline__ float4 dmul(float4 d0, float4 d1, float4 r) {
+  return f4(d0.x * r.x + d0.y * r.y + d0.z * r.z, d0.y * r.x + d0.w * r.y + d1.x * r.z,
+            d0.z * r.x + d1.x * r.y + d1.y * r.z);
+}
+
 // Pre-smoothing from zero and the residual: x = Dinv r, t = r - A x (x of the
 // neighbours recomputed from their r).
 __global__ void __launch_bounds__(kThreads) k_pre(const __grid_constant__ Views V) {
@@ -595,28 +632,15 @@ __global__ void __launch_bounds__(kThreads) k_pre(const __grid_constant__ Views 
   const View& W = V.v[it.v];
   if (!it.ok || !active(W, it.s)) return;
   const int n = W.f.n, N = W.f.N, p = it.p, i = p % (n + 1), j = p / (n + 1);
-  const size_t s3 = (size_t)it.s * 3 * N;
-  const float* __restrict__ A = W.f.A + (size_t)it.s * kStencil * N;
-  const float* __restrict__ D = W.f.Dinv + (size_t)it.s * kDinv * N;
-  const float* __restrict__ r = W.f.r + s3;
-  auto xf = [&](int q, float v[3]) {
-    const float r0 = r[q], r1 = r[N + q], r2 = r[2 * N + q];
-    const float d0 = D[q], d1 = D[N + q], d2 = D[2 * N + q], d3 = D[3 * N + q], d4 = D[4 * N + q],
-                d5 = D[5 * N + q];
-    v[0] = d0 * r0 + d1 * r1 + d2 * r2;
-    v[1] = d1 * r0 + d3 * r1 + d4 * r2;
-    v[2] = d2 * r0 + d4 * r1 + d5 * r2;
-  };
-  float x[3], y[3] = {0.f, 0.f, 0.f};
-  xf(p, x);
+  const float4* __restrict__ A = W.f.A + (size_t)it.s * kGroups * N;
+  const float4* __restrict__ D = W.f.Dinv + (size_t)it.s * kDinvGroups * N;
+  const float4* __restrict__ r = W.f.r + (size_t)it.s * N;
+  auto xf = [&](int q) { return dmul(D[q], D[N + q], r[q]); };
+  float y[3] = {0.f, 0.f, 0.f};
   apply_node(A, N, n, i, j, xf, y);
-  float* xo = W.f.x + s3;
-  float* to = W.f.t + s3;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    xo[(size_t)c * N + p] = x[c];
-    to[(size_t)c * N + p] = r[(size_t)c * N + p] - y[c];
-  }
+  const float4 rp = r[p];
+  W.f.x[(size_t)it.s * N + p] = xf(p);
+  W.f.t[(size_t)it.s * N + p] = f4(rp.x - y[0], rp.y - y[1], rp.z - y[2]);
 }
 
 // Restriction c.r = P^T f.t, zero at the coarse Dirichlet DOFs.
@@ -625,7 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const __grid_constant__ V
   const View& W = V.v[it.v];
   if (!it.ok || !active(W, it.s)) return;
   const int nc = W.c.n, Nc = W.c.N, nf = W.f.n, Nf = W.f.N, P = it.p, I = P % (nc + 1), J = P / (nc + 1);
-  const float* __restrict__ t = W.f.t + (size_t)it.s * 3 * Nf;
+  const float4* __restrict__ t = W.f.t + (size_t)it.s * Nf;
   float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy)
@@ -634,30 +658,42 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const __grid_constant__ V
       const int pi = 2 * I + dx, pj = 2 * J + dy;
       if (pi < 0 || pj < 0 || pi > nf || pj > nf) continue;
       const float w = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f);
-      const int p = pj * (nf + 1) + pi;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc[c] += w * t[(size_t)c * Nf + p];
+      const float4 v = t[pj * (nf + 1) + pi];
+      acc[0] += w * v.x;
+      acc[1] += w * v.y;
+      acc[2] += w * v.z;
     }
   const int dm = dmask(I, J, nc);
   if (dm & 1) acc[0] = 0.f;
   if (dm & 2) acc[1] = 0.f;
-  float* rc = W.c.r + (size_t)it.s * 3 * Nc;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) rc[(size_t)c * Nc + P] = acc[c];
+  W.c.r[(size_t)it.s * Nc + P] = f4(acc[0], acc[1], acc[2]);
 }
 
-// Coarsest level: f.t = Ainv f.r, one thread per (sample, DOF).
+// Coarsest level: f.t = Ainv f.r, one thread per (sample, node) forming its 3 DOFs.
 __global__ void __launch_bounds__(kThreads) k_coarse_solve(const __grid_constant__ Views V) {
-  const Item it = item_of(V, kCoarseDofs);
+  const Item it = item_of(V, kCoarseDofs / 3);
   const View& W = V.v[it.v];
   if (!it.ok || !active(W, it.s)) return;
-  const int N = W.f.N, row = it.p;
-  const float* __restrict__ r = W.f.r + (size_t)it.s * 3 * N;
-  const float* __restrict__ M = W.Ainv + ((size_t)it.s * kCoarseDofs + row) * kCoarseDofs;
-  float acc = 0.f;
+  const int N = W.f.N, node = it.p;
+  const float4* __restrict__ r = W.f.r + (size_t)it.s * N;
+  float rv[kCoarseDofs];
 #pragma unroll
-  for (int k = 0; k < kCoarseDofs; ++k) acc += M[k] * r[(size_t)(k % 3) * N + k / 3];
-  W.f.t[(size_t)it.s * 3 * N + (size_t)(row % 3) * N + row / 3] = acc;
+  for (int q = 0; q < kCoarseDofs / 3; ++q) {
+    const float4 v = r[q];
+    rv[3 * q] = v.x;
+    rv[3 * q + 1] = v.y;
+    rv[3 * q + 2] = v.z;
+  }
+  const float* __restrict__ M = W.Ainv + ((size_t)it.s * kCoarseDofs + 3 * node) * kCoarseDofs;
+  float o[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < kCoarseDofs; ++k) acc += M[c * kCoarseDofs + k] * rv[k];
+    o[c] = acc;
+  }
+  W.f.t[(size_t)it.s * N + node] = f4(o[0], o[1], o[2]);
 }
 
 // Prolongation f.x += P c.t (bilinear).
@@ -666,22 +702,21 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const __grid_constant__ Vi
   const View& W = V.v[it.v];
   if (!it.ok || !active(W, it.s)) return;
   const int nf = W.f.n, Nf = W.f.N, nc = W.c.n, Nc = W.c.N, p = it.p, i = p % (nf + 1), j = p / (nf + 1);
-  const float* __restrict__ xc = W.c.t + (size_t)it.s * 3 * Nc;
+  const float4* __restrict__ xc = W.c.t + (size_t)it.s * Nc;
   const int I0 = i >> 1, J0 = j >> 1;
   const bool ox = i & 1, oy = j & 1;
-  float acc[3] = {0.f, 0.f, 0.f};
+  const float w = (ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f);
+  float4 x = W.f.x[(size_t)it.s * Nf + p];
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const int di = b & 1, dj = b >> 1;
     if ((di && !ox) || (dj && !oy)) continue;
-    const float w = (ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f);
-    const int P = (J0 + dj) * (nc + 1) + I0 + di;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c] += w * xc[(size_t)c * Nc + P];
+    const float4 v = xc[(J0 + dj) * (nc + 1) + I0 + di];
+    x.x += w * v.x;
+    x.y += w * v.y;
+    x.z += w * v.z;
   }
-  float* x = W.f.x + (size_t)it.s * 3 * Nf;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) x[(size_t)c * Nf + p] += acc[c];
+  W.f.x[(size_t)it.s * Nf + p] = x;
 }
 
 // Post-smoothing: f.t = x + Dinv (r - A x). On the solve mesh (top) f.t is the
@@ -693,29 +728,17 @@ __global__ void __launch_bounds__(kThreads) k_post(const __grid_constant__ Views
   double rz = 0.0;
   if (ok) {
     const int n = W.f.n, N = W.f.N, p = it.p, i = p % (n + 1), j = p / (n + 1);
-    const size_t s3 = (size_t)it.s * 3 * N;
-    const float* __restrict__ A = W.f.A + (size_t)it.s * kStencil * N;
-    const float* __restrict__ D = W.f.Dinv + (size_t)it.s * kDinv * N;
-    const float* __restrict__ r = W.f.r + s3;
-    const float* __restrict__ x = W.f.x + s3;
-    auto xf = [&](int q, float v[3]) {
-      v[0] = x[q];
-      v[1] = x[N + q];
-      v[2] = x[2 * N + q];
-    };
+    const float4* __restrict__ A = W.f.A + (size_t)it.s * kGroups * N;
+    const float4* __restrict__ D = W.f.Dinv + (size_t)it.s * kDinvGroups * N;
+    const float4* __restrict__ x = W.f.x + (size_t)it.s * N;
+    auto xf = [&](int q) { return x[q]; };
     float y[3] = {0.f, 0.f, 0.f};
     apply_node(A, N, n, i, j, xf, y);
-    const float e0 = r[p] - y[0], e1 = r[N + p] - y[1], e2 = r[2 * N + p] - y[2];
-    const float d0 = D[p], d1 = D[N + p], d2 = D[2 * N + p], d3 = D[3 * N + p], d4 = D[4 * N + p],
-                d5 = D[5 * N + p];
-    const float z0 = x[p] + d0 * e0 + d1 * e1 + d2 * e2;
-    const float z1 = x[N + p] + d1 * e0 + d3 * e1 + d4 * e2;
-    const float z2 = x[2 * N + p] + d2 * e0 + d4 * e1 + d5 * e2;
-    float* t = W.f.t + s3;
-    t[p] = z0;
-    t[N + p] = z1;
-    t[2 * N + p] = z2;
-    if (top) rz = (double)r[p] * z0 + (double)r[N + p] * z1 + (double)r[2 * N + p] * z2;
+    const float4 rp = W.f.r[(size_t)it.s * N + p], xp = x[p];
+    const float4 e = dmul(D[p], D[N + p], f4(rp.x - y[0], rp.y - y[1], rp.z - y[2]));
+    const float4 z = f4(xp.x + e.x, xp.y + e.y, xp.z + e.z);
+    W.f.t[(size_t)it.s * N + p] = z;
+    if (top) rz = (double)rp.x * z.x + (double)rp.y * z.y + (double)rp.z * z.z;
   }
   if (top) {
     SampleState* st = W.F.st;
@@ -733,36 +756,48 @@ __global__ void __launch_bounds__(kThreads) k_cg_apply(const __grid_constant__ V
   double pq = 0.0;
   if (ok) {
     const int n = W.f.n, N = W.f.N, p = it.p, i = p % (n + 1), j = p / (n + 1);
-    const size_t s3 = (size_t)it.s * 3 * N;
-    const float* __restrict__ A = W.f.A + (size_t)it.s * kStencil * N;
-    const float* __restrict__ z = W.f.t + s3;
-    const float* __restrict__ pin = (odd ? W.F.p1 : W.F.p0) + s3;
-    float* pout = (odd ? W.F.p0 : W.F.p1) + s3;
+    const size_t sN = (size_t)it.s * N;
+    const float4* __restrict__ A = W.f.A + (size_t)it.s * kGroups * N;
+    const float4* __restrict__ z = W.f.t + sN;
+    const float4* __restrict__ pin = (odd ? W.F.p1 : W.F.p0) + sN;
+    float4* pout = (odd ? W.F.p0 : W.F.p1) + sN;
     const float beta = (float)W.F.st[it.s].beta;
-    auto pf = [&](int q, float v[3]) {
-      if (beta == 0.f) {
-        v[0] = z[q];
-        v[1] = z[N + q];
-        v[2] = z[2 * N + q];
-      } else {
-        v[0] = z[q] + beta * pin[q];
-        v[1] = z[N + q] + beta * pin[N + q];
-        v[2] = z[2 * N + q] + beta * pin[2 * N + q];
-      }
+    auto pf = [&](int q) {
+      const float4 a = z[q];
+      if (beta == 0.f) return a;
+      const float4 b = pin[q];
+      return f4(a.x + beta * b.x, a.y + beta * b.y, a.z + beta * b.z);
     };
-    float pv[3], y[3] = {0.f, 0.f, 0.f};
-    pf(p, pv);
+    float y[3] = {0.f, 0.f, 0.f};
     apply_node(A, N, n, i, j, pf, y);
-    float* qv = W.F.q + s3;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      pout[(size_t)c * N + p] = pv[c];
-      qv[(size_t)c * N + p] = y[c];
-      pq += (double)pv[c] * y[c];
-    }
+    const float4 pv = pf(p);
+    pout[p] = pv;
+    W.F.q[sN + p] = f4(y[0], y[1], y[2]);
+    pq = (double)pv.x * y[0] + (double)pv.y * y[1] + (double)pv.z * y[2];
   }
   SampleState* st = W.F.st;
   warp_add_by_sample(pq, ok ? it.s : -1, [&](int k) { return &st[k].pq; });
+}
+
+// c += alpha p_out, r -= alpha q, |r|^2.
+__global__ void __launch_bounds__(kThreads) k_cg_update(const __grid_constant__ Views V, bool odd) {
+  const Item it = item_of(V, V.v[view_of(V)].f.N);
+  const View& W = V.v[it.v];
+  const bool ok = it.ok && active(W, it.s);
+  double rr = 0.0;
+  if (ok) {
+    const size_t o = (size_t)it.s * W.f.N + it.p;
+    const float a = (float)W.F.st[it.s].alpha;
+    const float4 pv = (odd ? W.F.p0 : W.F.p1)[o], qv = W.F.q[o];
+    float4 c = W.F.c[o], r = W.f.r[o];
+    c = f4(c.x + a * pv.x, c.y + a * pv.y, c.z + a * pv.z);
+    r = f4(r.x - a * qv.x, r.y - a * qv.y, r.z - a * qv.z);
+    W.F.c[o] = c;
+    W.f.r[o] = r;
+    rr = (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
+  }
+  SampleState* st = W.F.st;
+  warp_add_by_sample(rr, ok ? it.s : -1, [&](int k) { return &st[k].rr; });
 }
 
 // one thread per sample of every view
@@ -791,33 +826,6 @@ __global__ void k_scal_a(const __grid_constant__ Views V) {
     st->act = 0;   // breakdown: the refinement takes over
   }
   st->rr = 0.0;
-}
-
-// c += alpha p_out, r -= alpha q, |r|^2.
-__global__ void __launch_bounds__(kThreads) k_cg_update(const __grid_constant__ Views V, bool odd) {
-  const Item it = item_of(V, V.v[view_of(V)].f.N);
-  const View& W = V.v[it.v];
-  const bool ok = it.ok && active(W, it.s);
-  double rr = 0.0;
-  if (ok) {
-    const int N = W.f.N, p = it.p;
-    const size_t s3 = (size_t)it.s * 3 * N;
-    const float a = (float)W.F.st[it.s].alpha;
-    const float* __restrict__ pv = (odd ? W.F.p0 : W.F.p1) + s3;
-    const float* __restrict__ qv = W.F.q + s3;
-    float* c = W.F.c + s3;
-    float* r = W.f.r + s3;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const size_t o = (size_t)k * N + p;
-      c[o] += a * pv[o];
-      const float rn = r[o] - a * qv[o];
-      r[o] = rn;
-      rr += (double)rn * rn;
-    }
-  }
-  SampleState* st = W.F.st;
-  warp_add_by_sample(rr, ok ? it.s : -1, [&](int k) { return &st[k].rr; });
 }
 
 // After the preconditioner: convergence of the correction solve and the next beta.
@@ -859,30 +867,33 @@ __global__ void __launch_bounds__(kThreads) k_resid64(const __grid_constant__ Vi
   double rr = 0.0;
   if (ok) {
     const int n = W.f.n, N = W.f.N, p = it.p, i = p % (n + 1), j = p / (n + 1);
-    const size_t s3 = (size_t)it.s * 3 * N;
     ff y[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    const size_t sN = (size_t)it.s * N;
     if (!first) {
-      const float* __restrict__ Ah = W.f.A + (size_t)it.s * kStencil * N;
-      const float* __restrict__ Al = W.F.Alo + (size_t)it.s * kStencil * N;
-      const float* __restrict__ dh = W.F.dh + s3;
-      const float* __restrict__ dl = W.F.dl + s3;
+      const float4* __restrict__ Ah = W.f.A + (size_t)it.s * kGroups * N;
+      const float4* __restrict__ Al = W.F.Alo + (size_t)it.s * kGroups * N;
+      const float4* __restrict__ dh = W.F.dh + sN;
+      const float4* __restrict__ dl = W.F.dl + sN;
       auto xf = [&](int q, ff v[3]) {
-        v[0] = ff{dh[q], dl[q]};
-        v[1] = ff{dh[N + q], dl[N + q]};
-        v[2] = ff{dh[2 * N + q], dl[2 * N + q]};
+        const float4 h = dh[q], l = dl[q];
+        v[0] = ff{h.x, l.x};
+        v[1] = ff{h.y, l.y};
+        v[2] = ff{h.z, l.z};
       };
       apply_node_ff(Ah, Al, N, n, i, j, xf, y);
     }
-    float* r = W.f.r + s3;
+    const float4 bh = W.F.bh[sN + p], bl = W.F.bl[sN + p];
+    const ff b[3] = {ff{bh.x, bl.x}, ff{bh.y, bl.y}, ff{bh.z, bl.z}};
+    float ev[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       // e = b - y: b + (-y) in float-float, then rounded
-      ff e{W.F.bh[s3 + (size_t)c * N + p], W.F.bl[s3 + (size_t)c * N + p]};
+      ff e = b[c];
       ff_fma(e, y[c], -1.f);
-      const float ev = __fadd_rn(e.hi, e.lo);
-      r[(size_t)c * N + p] = ev;
-      rr += (double)ev * (double)ev;
+      ev[c] = __fadd_rn(e.hi, e.lo);
+      rr += (double)ev[c] * (double)ev[c];
     }
+    W.f.r[sN + p] = f4(ev[0], ev[1], ev[2]);
   }
   SampleState* st = W.F.st;
   warp_add_by_sample(rr, ok ? it.s : -1, [&](int k) { return &st[k].r64n2; });
@@ -919,18 +930,15 @@ __global__ void __launch_bounds__(kThreads) k_accumulate(const __grid_constant__
   const Item it = item_of(V, V.v[view_of(V)].f.N);
   if (!it.ok) return;
   const View& W = V.v[it.v];
-  const int N = W.f.N;
-  const size_t s3 = (size_t)it.s * 3 * N;
-  float* c = W.F.c + s3;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const size_t o = (size_t)k * N + it.p;
-    ff d{W.F.dh[s3 + o], W.F.dl[s3 + o]};
-    ff_fma(d, ff{c[o], 0.f}, 1.f);
-    W.F.dh[s3 + o] = d.hi;
-    W.F.dl[s3 + o] = d.lo;
-    c[o] = 0.f;
-  }
+  const size_t o = (size_t)it.s * W.f.N + it.p;
+  const float4 c = W.F.c[o], h = W.F.dh[o], l = W.F.dl[o];
+  ff d[3] = {ff{h.x, l.x}, ff{h.y, l.y}, ff{h.z, l.z}};
+  ff_fma(d[0], ff{c.x, 0.f}, 1.f);
+  ff_fma(d[1], ff{c.y, 0.f}, 1.f);
+  ff_fma(d[2], ff{c.z, 0.f}, 1.f);
+  W.F.dh[o] = f4(d[0].hi, d[1].hi, d[2].hi);
+  W.F.dl[o] = f4(d[0].lo, d[1].lo, d[2].lo);
+  W.F.c[o] = f4(0.f, 0.f, 0.f);
 }
 
 // ---------------------------------------------------------------- quantities of interest
@@ -957,15 +965,20 @@ __global__ void __launch_bounds__(kThreads) k_qoi(const __grid_constant__ Views 
       ie = n - 1;
       je = it.p - ncen * ncen;
     }
-    const float* __restrict__ dh = W.F.dh + (size_t)it.s * 3 * N;
-    const float* __restrict__ dl = W.F.dl + (size_t)it.s * 3 * N;
+    const float4* __restrict__ dh = W.F.dh + (size_t)it.s * N;
+    const float4* __restrict__ dl = W.F.dl + (size_t)it.s * N;
     double de[12];
     const int cx[4] = {0, 1, 1, 0}, cy[4] = {0, 0, 1, 1};
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const int q = (je + cy[a]) * (n + 1) + ie + cx[a];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) de[3 * a + c] = (double)dh[(size_t)c * N + q] + (double)dl[(size_t)c * N + q];
+      {
+        const float4 h = dh[q], l = dl[q];
+        de[3 * a] = (double)h.x + (double)l.x;
+        de[3 * a + 1] = (double)h.y + (double)l.y;
+        de[3 * a + 2] = (double)h.z + (double)l.z;
+      }
       if (ie + cx[a] == n) de[3 * a] += K.shortening;
     }
     const float* tg = W.F.trig + 8 * ((size_t)it.s * n * n + (size_t)je * n + ie);
@@ -1057,55 +1070,37 @@ __global__ void k_qoi_final(const __grid_constant__ Views V) {
   }
 }
 
+// y = A x with the float-float stencil; x, y [S][N][3] doubles (the C ABI's layout)
 __global__ void __launch_bounds__(kThreads) k_apply64(const __grid_constant__ Views V, const double* __restrict__ x,
                                                       double* __restrict__ y) {
   const Item it = item_of(V, V.v[view_of(V)].f.N);
   if (!it.ok) return;
   const View& W = V.v[it.v];
   const int n = W.f.n, N = W.f.N, p = it.p, i = p % (n + 1), j = p / (n + 1);
-  const size_t s3 = (size_t)it.s * 3 * N;
-  const float* Ah = W.f.A + (size_t)it.s * kStencil * N;
-  const float* Al = W.F.Alo + (size_t)it.s * kStencil * N;
-  const double* xs = x + s3;
+  const float4* Ah = W.f.A + (size_t)it.s * kGroups * N;
+  const float4* Al = W.F.Alo + (size_t)it.s * kGroups * N;
+  const double* xs = x + (size_t)it.s * N * 3;
   auto xf = [&](int q, ff v[3]) {
-    v[0] = ff_of(xs[q]);
-    v[1] = ff_of(xs[N + q]);
-    v[2] = ff_of(xs[2 * N + q]);
+    v[0] = ff_of(xs[3 * q]);
+    v[1] = ff_of(xs[3 * q + 1]);
+    v[2] = ff_of(xs[3 * q + 2]);
   };
   ff o[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   apply_node_ff(Ah, Al, N, n, i, j, xf, o);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) y[s3 + (size_t)c * N + p] = ff_dbl(o[c]);
+  for (int c = 0; c < 3; ++c) y[((size_t)it.s * N + p) * 3 + c] = ff_dbl(o[c]);
 }
 
-__global__ void k_aos_to_soa(const double* __restrict__ in, double* __restrict__ out, int S, int N) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= (int64_t)S * N * 3) return;
-  const int64_t s = k / (3 * N), r = k % (3 * N), p = r / 3, c = r % 3;
-  out[(s * 3 + c) * N + p] = in[k];
-}
-
-__global__ void k_soa_to_aos(const double* __restrict__ in, double* __restrict__ out, int S, int n, bool lift,
-                             double sh) {
+__global__ void k_ff_to_aos(const float4* __restrict__ hi, const float4* __restrict__ lo, double* __restrict__ out,
+                            int S, int n, double sh) {
   const int N = (n + 1) * (n + 1);
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= (int64_t)S * N * 3) return;
-  const int64_t s = k / (3 * N), r = k % (3 * N), p = r / 3, c = r % 3;
-  double v = in[(s * 3 + c) * N + p];
-  if (lift && c == 0 && p % (n + 1) == n) v += sh;
-  out[k] = v;
-}
-
-__global__ void k_ff_to_aos(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ out, int S,
-                            int n, double sh) {
-  const int N = (n + 1) * (n + 1);
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= (int64_t)S * N * 3) return;
-  const int64_t s = k / (3 * N), r = k % (3 * N), p = r / 3, c = r % 3;
-  const int64_t o = (s * 3 + c) * N + p;
-  double v = (double)hi[o] + (double)lo[o];
-  if (c == 0 && p % (n + 1) == n) v += sh;
-  out[k] = v;
+  if (k >= (int64_t)S * N) return;
+  const int p = (int)(k % N);
+  const float4 h = hi[k], l = lo[k];
+  out[3 * k] = (double)h.x + (double)l.x + (p % (n + 1) == n ? sh : 0.0);
+  out[3 * k + 1] = (double)h.y + (double)l.y;
+  out[3 * k + 2] = (double)h.z + (double)l.z;
 }
 
 }  // namespace
@@ -1181,25 +1176,13 @@ cudaError_t launch_synth_ff(const double* xi, const float* Bh, const float* Bl, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ff_to_aos(const float* hi, const float* lo, double* out, int S, int n, double sh, cudaStream_t st) {
-  const int64_t cnt = (int64_t)S * (n + 1) * (n + 1) * 3;
+cudaError_t launch_ff_to_aos(const float4* hi, const float4* lo, double* out, int S, int n, double sh,
+                             cudaStream_t st) {
+  const int64_t cnt = (int64_t)S * (n + 1) * (n + 1);
   if (cnt <= 0) return cudaSuccess;
   k_ff_to_aos<<<(unsigned)((cnt + kThreads - 1) / kThreads), kThreads, 0, st>>>(hi, lo, out, S, n, sh);
   return cudaGetLastError();
 }
 
-cudaError_t launch_aos_to_soa(const double* in, double* out, int S, int N, cudaStream_t st) {
-  const int64_t n = (int64_t)S * N * 3;
-  if (n <= 0) return cudaSuccess;
-  k_aos_to_soa<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(in, out, S, N);
-  return cudaGetLastError();
-}
-cudaError_t launch_soa_to_aos(const double* in, double* out, int S, int n, bool add_lift, double sh,
-                              cudaStream_t st) {
-  const int64_t cnt = (int64_t)S * (n + 1) * (n + 1) * 3;
-  if (cnt <= 0) return cudaSuccess;
-  k_soa_to_aos<<<(unsigned)((cnt + kThreads - 1) / kThreads), kThreads, 0, st>>>(in, out, S, n, add_lift, sh);
-  return cudaGetLastError();
-}
 
 }  // namespace mlmcc

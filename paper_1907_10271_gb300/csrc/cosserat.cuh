@@ -1,18 +1,20 @@
 // Cosserat engine (Sec. 3, the first test problem): device data layout and kernels.
 //
 // Layout. A batch of S samples on an n x n mesh has N = (n + 1)^2 nodes, node
-// p = j (n + 1) + i. Vectors are structure-of-arrays per sample, v[(s * 3 + c) * N + p]
-// (c = 0 u, 1 v, 2 theta_3), so a warp's 32 consecutive nodes load one line per
-// component. The operator is the assembled 9-point stencil of 3 x 3 blocks, stored
-// as half of it per node (the rest follows from symmetry): coefficient k of node p at
-// A[(s * kStencil + k) * N + p] with
+// p = j (n + 1) + i. A vector is one float4 (u, v, theta_3, 0) per node, v[s * N + p],
+// so that a thread loads a neighbour's three components in one instruction. The operator
+// is the assembled 9-point stencil of 3 x 3 blocks, stored as half of it per node (the
+// rest follows from symmetry), 42 coefficients k padded to 44 and grouped in float4s:
+// group g = k / 4 of node p at A[(s * kGroups + g) * N + p], component k % 4, so that a
+// warp's 32 consecutive nodes load one 512-byte line set per group. The coefficients:
 //   k 0 .. 5    the diagonal block, upper triangle (00, 01, 02, 11, 12, 22),
 //   k 6 .. 14   block to the east neighbour (+1, 0), row-major [row of p][column of q],
 //   k 15 .. 23  north (0, +1), k 24 .. 32 north-east (+1, +1), k 33 .. 41 north-west (-1, +1);
 // the blocks to the W, S, SW and SE neighbours are the transposes of those neighbours'
 // E, N, NE and NW blocks. Dirichlet DOFs (u on x = 0 and x = L, v on y = 0 and y = L)
 // have identity rows and columns. Dinv holds omega times the inverse of the diagonal
-// block (upper triangle, 6 values per node) for the block-Jacobi smoother.
+// block (upper triangle, 6 values padded to 8 in two float4 groups per node) for the
+// block-Jacobi smoother.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -23,7 +25,9 @@ namespace mlmcc {
 constexpr int kMaxViews = 8;      // meshes of one call (one per MLMC mesh level)
 constexpr int kMaxMeshes = 8;
 constexpr int kStencil = 42;
+constexpr int kGroups = 11;      // float4 groups of the stencil per node (44 floats)
 constexpr int kDinv = 6;
+constexpr int kDinvGroups = 2;
 constexpr int kTerms = 5;         // trig terms of the element matrix: 1, c2, s2, c4, s4
 constexpr int kCoarsest = 2;      // elements per side of the coarsest multigrid mesh
 constexpr int kCoarseDofs = 27;   // 3 (kCoarsest + 1)^2
@@ -34,11 +38,11 @@ constexpr float kOmega = 0.6f;    // block-Jacobi damping
 // One multigrid level of one batch.
 struct Lev {
   int n, N, S;
-  float* A;      // [S][kStencil][N]
-  float* Dinv;   // [S][kDinv][N]
-  float* r;      // [S][3][N] right-hand side of the level's correction equation
-  float* x;      // [S][3][N] iterate
-  float* t;      // [S][3][N] residual for restriction, then the smoothed result
+  float4* A;      // [S][kGroups][N]
+  float4* Dinv;   // [S][kDinvGroups][N]
+  float4* r;      // [S][N] right-hand side of the level's correction equation
+  float4* x;      // [S][N] iterate
+  float4* t;      // [S][N] residual for restriction, then the smoothed result
 };
 
 // Per-sample solver state (FP64 scalars of the correction CG and the refinement).
@@ -57,11 +61,11 @@ struct SampleState {
 
 // The solve mesh of one batch: FP64 system, CG vectors and per-element trig values.
 struct FineSys {
-  float* Alo;     // [S][kStencil][N] low part of the float-float stencil (high part: level 0's A)
-  float *bh, *bl;   // [S][3][N] right-hand side, float-float
-  float *dh, *dl;   // [S][3][N] solution without the prescribed values, float-float
+  float4* Alo;     // [S][kGroups][N] low part of the float-float stencil (high part: level 0's A)
+  float4 *bh, *bl;   // [S][N] right-hand side, float-float
+  float4 *dh, *dl;   // [S][N] solution without the prescribed values, float-float
   const float* trig;   // [S][n * n][8]: cos 2 phi, sin 2 phi, cos 4 phi, sin 4 phi as (hi, lo) pairs
-  float *c, *p0, *p1, *q;   // [S][3][N]
+  float4 *c, *p0, *p1, *q;   // [S][N]
   SampleState* st;          // [S]
   double* acc;              // [S][4]: f*, int sigma_x, reaction, spare
   double* q_out;            // [S][2]
@@ -123,19 +127,15 @@ cudaError_t launch_accumulate(const Views& v, cudaStream_t st);
 // quantities of interest
 cudaError_t launch_qoi(const Views& v, cudaStream_t st);
 cudaError_t launch_qoi_final(const Views& v, cudaStream_t st);
-// y = A x on the solve mesh with the float-float stencil (x, y [S][3][N] doubles)
+// y = A x on the solve mesh with the float-float stencil (x, y [S][N][3] doubles)
 cudaError_t launch_apply64(const Views& v, const double* x, double* y, cudaStream_t st);
 // KL synthesis in float-float: basis (hi, lo) [n_el][K] floats, xi [S][K] doubles ->
 // with trig, out = float [S][n_el][8] (cos 2 phi, sin 2 phi, cos 4 phi, sin 4 phi as
 // hi, lo pairs); else out = double phi [S][n_el]
 cudaError_t launch_synth_ff(const double* xi, const float* Bh, const float* Bl, int S, int n_el, int K, void* out,
                             bool trig, cudaStream_t st);
-// [S][N][3] <-> [S][3][N] (doubles); add_lift adds the prescribed u = shortening on x = L
-cudaError_t launch_aos_to_soa(const double* in, double* out, int S, int N, cudaStream_t st);
-cudaError_t launch_soa_to_aos(const double* in, double* out, int S, int n, bool add_lift, double shortening,
-                              cudaStream_t st);
-// float-float [S][3][N] (hi, lo) -> double [S][N][3], adding u = shortening on x = L
-cudaError_t launch_ff_to_aos(const float* hi, const float* lo, double* out, int S, int n, double shortening,
+// float-float [S][N] (hi, lo) float4s -> double [S][N][3], adding u = shortening on x = L
+cudaError_t launch_ff_to_aos(const float4* hi, const float4* lo, double* out, int S, int n, double shortening,
                              cudaStream_t st);
 
 }  // namespace mlmcc

@@ -193,16 +193,16 @@ size_t layout(const mlmcc_ctx& c, const std::vector<Group>& groups, char* base, 
     b.ids = (uint64_t*)take(S * sizeof(uint64_t));
     b.xi = (double*)take(S * b.nkl * sizeof(double));
     b.trig = (float*)take(S * nel * 8 * sizeof(float));
-    b.F.Alo = (float*)take(S * mlmcc::kStencil * N * sizeof(float));
-    b.F.bh = (float*)take(S * 3 * N * sizeof(float));
-    b.F.bl = (float*)take(S * 3 * N * sizeof(float));
-    b.F.dh = (float*)take(S * 3 * N * sizeof(float));
-    b.F.dl = (float*)take(S * 3 * N * sizeof(float));
+    b.F.Alo = (float4*)take(S * mlmcc::kGroups * N * sizeof(float4));
+    b.F.bh = (float4*)take(S * N * sizeof(float4));
+    b.F.bl = (float4*)take(S * N * sizeof(float4));
+    b.F.dh = (float4*)take(S * N * sizeof(float4));
+    b.F.dl = (float4*)take(S * N * sizeof(float4));
     b.F.trig = b.trig;
-    b.F.c = (float*)take(S * 3 * N * sizeof(float));
-    b.F.p0 = (float*)take(S * 3 * N * sizeof(float));
-    b.F.p1 = (float*)take(S * 3 * N * sizeof(float));
-    b.F.q = (float*)take(S * 3 * N * sizeof(float));
+    b.F.c = (float4*)take(S * N * sizeof(float4));
+    b.F.p0 = (float4*)take(S * N * sizeof(float4));
+    b.F.p1 = (float4*)take(S * N * sizeof(float4));
+    b.F.q = (float4*)take(S * N * sizeof(float4));
     b.F.st = (mlmcc::SampleState*)take(S * sizeof(mlmcc::SampleState));
     b.F.acc = (double*)take(S * 4 * sizeof(double));
     b.F.q_out = (double*)take(S * 2 * sizeof(double));
@@ -217,11 +217,11 @@ size_t layout(const mlmcc_ctx& c, const std::vector<Group>& groups, char* base, 
       l.n = n;
       l.N = (n + 1) * (n + 1);
       l.S = b.S;
-      l.A = (float*)take(S * mlmcc::kStencil * l.N * sizeof(float));
-      l.Dinv = (float*)take(S * mlmcc::kDinv * l.N * sizeof(float));
-      l.r = (float*)take(S * 3 * l.N * sizeof(float));
-      l.x = (float*)take(S * 3 * l.N * sizeof(float));
-      l.t = (float*)take(S * 3 * l.N * sizeof(float));
+      l.A = (float4*)take(S * mlmcc::kGroups * l.N * sizeof(float4));
+      l.Dinv = (float4*)take(S * mlmcc::kDinvGroups * l.N * sizeof(float4));
+      l.r = (float4*)take(S * l.N * sizeof(float4));
+      l.x = (float4*)take(S * l.N * sizeof(float4));
+      l.t = (float4*)take(S * l.N * sizeof(float4));
       b.lev.push_back(l);
     }
     b.Ainv = (float*)take(S * mlmcc::kCoarseDofs * mlmcc::kCoarseDofs * sizeof(float));
@@ -251,7 +251,7 @@ Views make_views(const std::vector<GroupBufs>& G, int k, Kind kind, Need need, c
     switch (kind) {
       case Kind::Nodes: v.items = b.S * v.f.N; break;
       case Kind::CoarseNodes: v.items = b.S * v.c.N; break;
-      case Kind::CoarseDofs: v.items = b.S * mlmcc::kCoarseDofs; break;
+      case Kind::CoarseDofs: v.items = b.S * (mlmcc::kCoarseDofs / 3); break;   // a thread per coarsest node
       case Kind::Inverse:
         v.items = b.S;
         threads = mlmcc::kInverseWarps;   // samples per block of the inverse kernel
@@ -518,21 +518,18 @@ mlmc_status run_once(mlmcc_ctx& c, const std::vector<Group>& groups, Mode mode, 
   for (const GroupBufs& b : G) {
     CK(cudaMemsetAsync(b.F.st, 0, sizeof(mlmcc::SampleState) * b.S, c.st), "memset");
     CK(cudaMemsetAsync(b.F.acc, 0, sizeof(double) * 4 * b.S, c.st), "memset");
-    CK(cudaMemsetAsync(b.F.c, 0, sizeof(float) * 3 * b.S * b.N, c.st), "memset");
+    CK(cudaMemsetAsync(b.F.c, 0, sizeof(float4) * b.S * b.N, c.st), "memset");
   }
   L(kOpBuild, sc.build, mlmcc::launch_build_fine);
   if (mode == Mode::Apply) {
     const GroupBufs& b = G[0];
     const size_t cnt = (size_t)b.S * 3 * b.N;
-    double *xs = nullptr, *ys = nullptr, *xa = nullptr;
-    CK(cudaMallocAsync(&xs, sizeof(double) * cnt * 3, c.st), "apply alloc");
-    ys = xs + cnt;
-    xa = ys + cnt;
-    CK(cudaMemcpyAsync(xa, x_in, sizeof(double) * cnt, cudaMemcpyDefault, c.st), "apply input");
-    L(kOpLayout, cnt, [&] { return mlmcc::launch_aos_to_soa(xa, xs, b.S, b.N, c.st); });
+    double* xs = nullptr;
+    CK(cudaMallocAsync(&xs, sizeof(double) * cnt * 2, c.st), "apply alloc");
+    double* ys = xs + cnt;
+    CK(cudaMemcpyAsync(xs, x_in, sizeof(double) * cnt, cudaMemcpyDefault, c.st), "apply input");
     L(kOpResid64, items_of(sc.fine), [&] { return mlmcc::launch_apply64(sc.fine, xs, ys, c.st); });
-    L(kOpLayout, cnt, [&] { return mlmcc::launch_soa_to_aos(ys, xa, b.S, b.n, false, 0.0, c.st); });
-    if (L.status == MLMC_OK) CK(cudaMemcpyAsync(y_out, xa, sizeof(double) * cnt, cudaMemcpyDefault, c.st), "copy");
+    if (L.status == MLMC_OK) CK(cudaMemcpyAsync(y_out, ys, sizeof(double) * cnt, cudaMemcpyDefault, c.st), "copy");
     cudaFreeAsync(xs, c.st);
     CK(cudaStreamSynchronize(c.st), "apply");
     return L.status;
