@@ -857,6 +857,17 @@ def run_panel(B, steps=2, warmup=1, parity=True, W=None, pilot=False):
                                                 "a V(2,2) multigrid cycle with the nodal block-Jacobi smoother") +
                         ", FP64 Gram matrices and final Rayleigh quotient",
             }
+            # the LOBPCG operator kernel alone (K x and G x), 1024 samples on the finest mesh
+            # (inputs far above L2), CUDA events around 20 launches
+            n_ab = 1024
+            ms_ab, by_ab = B.mlmcp_apply_bench(ctx, W["levels"] - 1, n_ab, 20)
+            pk, pk_kind = peaks()
+            out["roofline_k_apply"] = {"kernel": "k_apply", "bound": "hbm", "achieved": round(by_ab / (ms_ab / 1e3) / 1e9, 1),
+                                       "peak": pk, "unit": "GB/s", "frac": round(by_ab / (ms_ab / 1e3) / 1e9 / pk, 4),
+                                       "peak_kind": pk_kind + " hbm_gbs", "avg_launch_us": round(ms_ab * 1e3, 2),
+                                       "algorithmic_bytes_per_launch": int(by_ab),
+                                       "samples": n_ab, "mesh": "%dx%d" % (nx0 << (W["levels"] - 1), ny0 << (W["levels"] - 1)),
+                                       "timing": "mlmcp_apply_bench: CUDA events around 20 launches on the context's stream"}
             if parity:
                 from oracle import plate as P
                 ids = [10 ** 7 + k for k in range(4)]

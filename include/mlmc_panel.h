@@ -109,6 +109,12 @@ mlmc_status mlmcp_laminate(mlmcp_ctx* ctx, int32_t level, uint64_t first_id, int
 mlmc_status mlmcp_apply(mlmcp_ctx* ctx, int32_t mesh_level, int32_t level, uint64_t first_id, int64_t n,
                         const float* x, float* y, float* g);
 
+/* Times `reps` launches of the FP32 operator kernel that LOBPCG uses (K x and G x of n
+   samples of level mesh_level's stream on mesh mesh_level, every DOF) between CUDA events
+   on the context's stream: *ms = mean time per launch, *bytes (nullable) = its algorithmic
+   bytes (x read, K x and G x written: 48 B per node; 576 B per sample's element matrix).
+   n <= 65535. */
+mlmc_status mlmcp_apply_bench(mlmcp_ctx* ctx, int32_t mesh_level, int64_t n, int32_t reps, double* ms, double* bytes);
 /* LOBPCG iterations of the last solve (maximum over samples). */
 mlmc_status mlmcp_last_iters(mlmcp_ctx* ctx, int32_t* iters);
 

@@ -623,6 +623,7 @@ def libp():
             "mlmcp_laminate": (I32, [P, I32, U64, I64, P, P]),
             "mlmcp_apply": (I32, [P, I32, I32, U64, I64, P, P, P]),
             "mlmcp_last_iters": (I32, [P, P]),
+            "mlmcp_apply_bench": (I32, [P, I32, I64, I32, P, P]),
             "mlmcp_server_create": (I32, [ctypes.POINTER(mlmcp_config), ctypes.POINTER(mlmc_server_config),
                                           ctypes.c_double, ctypes.c_double, ctypes.POINTER(P)]),
         }
@@ -704,6 +705,13 @@ def mlmcp_laminate(ctx, level, first_id, n, dstar, kgt=None):
 def mlmcp_apply(ctx, mesh_level, level, first_id, n, x, y, g=None):
     return _checkp(ctx, libp().mlmcp_apply(ctx, mesh_level, level, first_id, n, _ptr(x, np.float32),
                                             _ptr(y, np.float32), _ptr(g, np.float32)))
+
+
+def mlmcp_apply_bench(ctx, mesh_level, n, reps=20):
+    """(ms per launch, algorithmic bytes per launch) of the FP32 K / G operator kernel."""
+    ms, by = ctypes.c_double(), ctypes.c_double()
+    _checkp(ctx, libp().mlmcp_apply_bench(ctx, mesh_level, n, reps, ctypes.byref(ms), ctypes.byref(by)))
+    return ms.value, by.value
 
 
 def mlmcp_last_iters(ctx):

@@ -149,7 +149,11 @@ __device__ __forceinline__ float4 node_kx(const PGrid& g, const float* K, const 
                                           float* gw, float* diag) {
   const int np = g.nx + 1;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f, gsum_all = 0.f;
+  // both loops unroll, so the node's corner index a in each element is a constant; the
+  // element matrix (16-byte aligned rows of 12) is read as float4s from shared memory
+#pragma unroll
   for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
     for (int ox = 0; ox < 2; ++ox) {
       const int ei = i - ox, ej = j - oy;   // element whose corner (ox, oy) is this node
       if (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) continue;
@@ -157,17 +161,26 @@ __device__ __forceinline__ float4 node_kx(const PGrid& g, const float* K, const 
       const float* Ka = K + 36 * a;   // rows 3a .. 3a+2
       float gs = 0.f;
       if (xe) {
+        float4 v[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int ni = ei + corner_x(c), nj = ej + corner_y(c);
-          float4 v = xe[nj * np + ni];
-          if (bc) v = masked(free_of(g, ni, nj), v);
-          const float* r = Ka + 3 * c;
-          a0 += r[0] * v.x + r[1] * v.y + r[2] * v.z;
-          a1 += r[12] * v.x + r[13] * v.y + r[14] * v.z;
-          a2 += r[24] * v.x + r[25] * v.y + r[26] * v.z;
-          gs += corner_x(c) ? v.x : -v.x;
+          v[c] = xe[nj * np + ni];
+          if (bc) v[c] = masked(free_of(g, ni, nj), v[c]);
+          gs += corner_x(c) ? v[c].x : -v[c].x;
         }
+        float acc[3];
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr) {
+          const float4* R = reinterpret_cast<const float4*>(Ka + 12 * rr);
+          const float4 k0 = R[0], k1 = R[1], k2 = R[2];   // columns 0-3, 4-7, 8-11
+          acc[rr] = k0.x * v[0].x + k0.y * v[0].y + k0.z * v[0].z + k0.w * v[1].x + k1.x * v[1].y +
+                    k1.y * v[1].z + k1.z * v[2].x + k1.w * v[2].y + k2.x * v[2].z + k2.y * v[3].x + k2.z * v[3].y +
+                    k2.w * v[3].z;
+        }
+        a0 += acc[0];
+        a1 += acc[1];
+        a2 += acc[2];
       }
       gsum_all += corner_x(a) ? gs : -gs;
       if (DIAG) {
@@ -189,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(PGrid g, const float* __rest
                                                     float4* __restrict__ gout, const int* __restrict__ active, int bc) {
   const int e = blockIdx.y, s = e >> g.cshift;
   if (active && !active[s]) return;
-  __shared__ float K[144];
+  __shared__ __align__(16) float K[144];
   for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke[(size_t)s * 144 + k];
   __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_smooth(PGrid g, const float* __res
                                                      const int* __restrict__ active) {
   const int e = blockIdx.y, s = e >> g.cshift;
   if (active && !active[s]) return;
-  __shared__ float K[144];
+  __shared__ __align__(16) float K[144];
   for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke[(size_t)s * 144 + k];
   __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -366,7 +379,7 @@ __device__ __forceinline__ bool free_comp(const Free& f, int c) { return c == 0 
 __global__ void __launch_bounds__(kThreads) k_patch_setup(PGrid g, const float* __restrict__ ke,
                                                           float* __restrict__ pinv) {
   const int type = blockIdx.x, s = blockIdx.y;
-  __shared__ float K[144];
+  __shared__ __align__(16) float K[144];
   __shared__ float A[kPatchDofs][kPatchDofs + 1];
   __shared__ float dsc[kPatchDofs], fcol[kPatchDofs];
   for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke[(size_t)s * 144 + k];
@@ -433,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_patch_color(PGrid g, const floa
                                                           const int* __restrict__ active) {
   const int e = blockIdx.y, s = e >> g.cshift;
   if (active && !active[s]) return;
-  __shared__ float K[144];
+  __shared__ __align__(16) float K[144];
   __shared__ float rs[kThreads / 32][32], ds[kThreads / 32][32];
   for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke[(size_t)s * 144 + k];
   __syncthreads();
@@ -504,7 +517,7 @@ __global__ void k_coarse_setup(PGrid g, const float* __restrict__ ke, const int*
   float* A = smem;                  // nf * nf
   float* col = A + nf * nf;         // nf
   int* map = reinterpret_cast<int*>(col + nf);   // nodes * 4
-  __shared__ float K[144];
+  __shared__ __align__(16) float K[144];
   __shared__ float pinv;
   const int s = blockIdx.x;
   const int nn = g.nodes();

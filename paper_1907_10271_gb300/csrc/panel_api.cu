@@ -87,6 +87,9 @@ struct mlmcp_ctx {
   // patch smoother: the pristine laminate's patch inverses per mesh size (nx, ny), made
   // on first use and shared by every sample and solve
   std::vector<std::pair<std::pair<int, int>, float*>> patch_cache;
+  // per MLMC mesh level: the executable graph of four LOBPCG iterations, updated with
+  // each call's pointers and sizes (cudaGraphExecUpdate) rather than re-instantiated
+  std::vector<cudaGraphExec_t> lobpcg_exec;
 
   mlmc_status fail(mlmc_status s, const std::string& m) {
     err = m;
@@ -109,6 +112,8 @@ struct mlmcp_ctx {
     return g;
   }
   ~mlmcp_ctx() {
+    for (cudaGraphExec_t g : lobpcg_exec)
+      if (g) cudaGraphExecDestroy(g);
     for (auto& kv : patch_cache) cudaFree(kv.second);
     for (int* p : free_dev) cudaFree(p);
     if (acc_dev) cudaFree(acc_dev);
@@ -358,22 +363,65 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
   // after every iteration of this solve (synchronising each time)
   const char* trace_env = std::getenv("MLMC_TRACE");
   const int trace = trace_env ? std::atoi(trace_env) : -1;
-  for (; it <= c.max_iter; ++it) {
-    CK(cudaMemsetAsync(E.count, 0, sizeof(int), st), "memset");
+  // one LOBPCG iteration of every active sample (launches only)
+  auto iteration = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(E.count, 0, sizeof(int), st);
     // K and G images of the new X and P, recomputed (not updated by the Ritz
-    // coefficients, whose single-precision drift raises the residual floor)
-    if (patch) {   // X's images and its residual G X - mu K X in one double-precision pass
-      CK(mlmcp::launch_apply64(G[0], ke64, X, KX, GX, R, E.mu, act, st), "apply");
-    } else {
-      CK(images(X, KX, GX), "apply");
+    // coefficients, whose single-precision drift raises the residual floor); in patch
+    // mode X's images and its residual G X - mu K X come from one double-precision pass
+    if (e == cudaSuccess)
+      e = patch ? mlmcp::launch_apply64(G[0], ke64, X, KX, GX, R, E.mu, act, st) : images(X, KX, GX);
+    if (e == cudaSuccess) e = images(P, KP, GP);
+    if (e == cudaSuccess && !patch) e = mlmcp::launch_residual(G[0], E, KX, GX, R, st);
+    if (e == cudaSuccess) e = vcycle(R, W);
+    if (e == cudaSuccess) e = images(W, KW, GW);
+    if (e == cudaSuccess) e = mlmcp::launch_gram(G[0], E, V, st);
+    if (e == cudaSuccess) e = mlmcp::launch_rayleigh_ritz(E, n, c.tol, c.max_iter, false, st);
+    if (e == cudaSuccess) e = mlmcp::launch_update(G[0], E, V, patch, st);
+    return e;
+  };
+  // check_every iterations per CUDA-graph replay on a capturable stream (the samples
+  // past max_iter are inactive, so a replay's last iterations cost only launches);
+  // the direct loop with the trace or on the legacy default stream
+  const bool graphs = st != nullptr && trace < 0;
+  if (graphs) {
+    if (c.lobpcg_exec.size() < (size_t)c.cfg.levels) c.lobpcg_exec.assign(c.cfg.levels, nullptr);
+    cudaGraphExec_t& ex = c.lobpcg_exec[m];
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "capture");
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < check_every && e == cudaSuccess; ++k) e = iteration();
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &gr);
+    if (e != cudaSuccess || ec != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      CK(e != cudaSuccess ? e : ec, "lobpcg capture");
     }
-    CK(images(P, KP, GP), "apply");
-    if (!patch) CK(mlmcp::launch_residual(G[0], E, KX, GX, R, st), "residual");
-    CK(vcycle(R, W), "v-cycle");
-    CK(images(W, KW, GW), "apply");
-    CK(mlmcp::launch_gram(G[0], E, V, st), "gram");
-    CK(mlmcp::launch_rayleigh_ritz(E, n, c.tol, c.max_iter, false, st), "rayleigh-ritz");
-    CK(mlmcp::launch_update(G[0], E, V, patch, st), "update");
+    if (ex) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(ex, gr, &info) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(ex);
+        ex = nullptr;
+      }
+    }
+    if (!ex) {
+      const cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
+      if (ei != cudaSuccess) ex = nullptr;
+      cudaGraphDestroy(gr);
+      CK(ei, "lobpcg graph");
+    } else {
+      cudaGraphDestroy(gr);
+    }
+    for (; it <= c.max_iter; it += check_every) {
+      CK(cudaGraphLaunch(ex, st), "lobpcg graph");
+      int h_count = 0;
+      CK(cudaMemcpyAsync(&h_count, E.count, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+      CK(cudaStreamSynchronize(st), "lobpcg");
+      if (h_count == 0) break;
+    }
+  }
+  for (; !graphs && it <= c.max_iter; ++it) {
+    CK(iteration(), "lobpcg");
     if (trace >= 0 && trace < n) {
       double h_mu[2], h_eta2;
       int h_act, h_it;
@@ -683,6 +731,46 @@ mlmc_status mlmcp_apply(mlmcp_ctx* h, int32_t mesh_level, int32_t level, uint64_
   s = copy_out(c, reinterpret_cast<float4*>(y), yd, nv);
   if (s == MLMC_OK && g) s = copy_out(c, reinterpret_cast<float4*>(g), gd, nv);
   return s;
+}
+
+mlmc_status mlmcp_apply_bench(mlmcp_ctx* h, int32_t mesh_level, int64_t n, int32_t reps, double* ms, double* bytes) {
+  if (!h || !ms || n <= 0 || n > 65535 || reps <= 0) return MLMC_ERR_INVALID_ARG;
+  mlmcp_ctx& c = *h;
+  if (mesh_level < 0 || mesh_level >= c.cfg.levels) return c.fail(MLMC_ERR_INVALID_ARG, "level out of range");
+  const Mesh M{c.cfg.nx0 << mesh_level, c.cfg.ny0 << mesh_level};
+  const PGrid pg = c.grid(M, (int)n, 0);
+  const size_t nv = (size_t)n * pg.nodes();
+  Scratch sc{c.st};
+  double* xi = sc.take<double>((size_t)n * c.cfg.n_plies);
+  double* ds = sc.take<double>((size_t)n * 6);
+  double* kg = sc.take<double>(n);
+  float* ke = sc.take<float>((size_t)n * 144);
+  float4* xd = sc.take<float4>(nv);
+  float4* yd = sc.take<float4>(nv);
+  float4* gd = sc.take<float4>(nv);
+  CK(sc.err, "alloc");
+  mlmc_status s = draw_xi(c, mesh_level, 0, nullptr, nullptr, (int)n, xi);
+  if (s != MLMC_OK) return s;
+  CK(mlmcp::launch_laminate(c.lam, xi, (int)n, ds, kg, c.st), "laminate");
+  CK(mlmcp::launch_element_matrices(ds, kg, (int)n, c.cfg.lx / M.nx, c.cfg.ly / M.ny, ke, nullptr, c.st), "element");
+  CK(cudaMemsetAsync(xd, 0, sizeof(float4) * nv, c.st), "memset");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  CK(mlmcp::launch_apply(pg, ke, xd, nullptr, yd, gd, nullptr, false, c.st), "apply");
+  CK(cudaEventRecord(e0, c.st), "event");
+  for (int r = 0; r < reps; ++r) CK(mlmcp::launch_apply(pg, ke, xd, nullptr, yd, gd, nullptr, false, c.st), "apply");
+  CK(cudaEventRecord(e1, c.st), "event");
+  CK(cudaEventSynchronize(e1), "event");
+  float t_ms = 0.f;
+  CK(cudaEventElapsedTime(&t_ms, e0, e1), "event");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t_ms / reps;
+  // per node: x read, K x and G x written (float4 each); per sample its element matrix
+  if (bytes) *bytes = 48.0 * (double)nv + 576.0 * (double)n;
+  CK(cudaStreamSynchronize(c.st), "apply_bench");
+  return MLMC_OK;
 }
 
 mlmc_status mlmcp_last_iters(mlmcp_ctx* h, int32_t* iters) {
