@@ -44,7 +44,8 @@
  * b - K d with the stencil assembled in double) around an FP32 conjugate-gradient
  * correction solve, preconditioned by one geometric-multigrid V(1,1) cycle: damped
  * (0.6) nodal 3 x 3 block Jacobi, bilinear transfers, Galerkin coarse operators down
- * to the 2 x 2 mesh, whose 27 x 27 operator is inverted. All meshes of one call advance
+ * to the 2 x 2 mesh, whose 27 x 27 operator is inverted; the meshes of at most 8 x 8
+ * elements run in one fused launch, a block per sample. All meshes of one call advance
  * together. A solve stops when ||b - K d||_2 <= rtol ||b||_2; samples that do not
  * reach it within max_iter correction iterations get status MLMC_ERR_NOT_CONVERGED.
  *
@@ -136,7 +137,7 @@ mlmc_status mlmcc_launch_count(mlmcc_ctx* ctx, int64_t* launches);
    calls accumulate per kernel kind `op` (0 .. mlmcc_profile_name(op) == NULL) the event
    time, the launches and the work items (threads' nodes, samples or elements). Kinds:
    kl_coefficients, kl_synthesis, build_fine, rap, coarsest_inverse, pre, restrict,
-   coarse_solve, prolong, post, cg_apply, cg_update, scalars, resid64, accumulate, qoi,
+   bottom, prolong, post, cg_apply, cg_update, scalars, resid64, accumulate, qoi,
    moments, layout. */
 mlmc_status mlmcc_profile_enable(mlmcc_ctx* ctx, int32_t on);
 mlmc_status mlmcc_profile_get(mlmcc_ctx* ctx, int32_t op, double* ms, int64_t* launches, int64_t* items);

@@ -669,33 +669,6 @@ __global__ void __launch_bounds__(kThreads) k_restrict(const __grid_constant__ V
   W.c.r[(size_t)it.s * Nc + P] = f4(acc[0], acc[1], acc[2]);
 }
 
-// Coarsest level: f.t = Ainv f.r, one thread per (sample, node) forming its 3 DOFs.
-__global__ void __launch_bounds__(kThreads) k_coarse_solve(const __grid_constant__ Views V) {
-  const Item it = item_of(V, kCoarseDofs / 3);
-  const View& W = V.v[it.v];
-  if (!it.ok || !active(W, it.s)) return;
-  const int N = W.f.N, node = it.p;
-  const float4* __restrict__ r = W.f.r + (size_t)it.s * N;
-  float rv[kCoarseDofs];
-#pragma unroll
-  for (int q = 0; q < kCoarseDofs / 3; ++q) {
-    const float4 v = r[q];
-    rv[3 * q] = v.x;
-    rv[3 * q + 1] = v.y;
-    rv[3 * q + 2] = v.z;
-  }
-  const float* __restrict__ M = W.Ainv + ((size_t)it.s * kCoarseDofs + 3 * node) * kCoarseDofs;
-  float o[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    float acc = 0.f;
-#pragma unroll
-    for (int k = 0; k < kCoarseDofs; ++k) acc += M[c * kCoarseDofs + k] * rv[k];
-    o[c] = acc;
-  }
-  W.f.t[(size_t)it.s * N + node] = f4(o[0], o[1], o[2]);
-}
-
 // Prolongation f.x += P c.t (bilinear).
 __global__ void __launch_bounds__(kThreads) k_prolong(const __grid_constant__ Views V) {
   const Item it = item_of(V, V.v[view_of(V)].f.N);
@@ -743,6 +716,140 @@ __global__ void __launch_bounds__(kThreads) k_post(const __grid_constant__ Views
   if (top) {
     SampleState* st = W.F.st;
     warp_add_by_sample(rz, ok ? it.s : -1, [&](int k) { return &st[k].rz_new; });
+  }
+}
+
+// Fused multigrid bottom: one block per sample runs the part of the V(1,1) cycle on
+// the meshes of at most kBottomN elements per side (entry mesh f, the next mesh c when
+// the entry is 8 x 8, and the 2 x 2 coarsest through Ainv), with the vectors in shared
+// memory and the stencils read from global memory: pre-smoothing and residual,
+// restriction, the dense coarsest solve, prolongation and post-smoothing, level by
+// level with a barrier between steps. Entry: f.r (written by the restriction from the
+// mesh above, or the CG residual when f is the solve mesh); exit: f.t, and r . t into
+// rz_new when f is the solve mesh (top). Replaces 4 launches per level and the coarse
+// solve, whose tiny grids cost launch latency rather than bandwidth.
+constexpr int kBotMaxN = (kBottomN + 1) * (kBottomN + 1);
+__global__ void __launch_bounds__(kBottomThreads) k_bottom(const __grid_constant__ Views V, int top_mask) {
+  __shared__ float4 sR[3][kBotMaxN], sX[3][kBotMaxN], sT[3][kBotMaxN];
+  __shared__ double red[kBottomThreads / 32];
+  const int v = view_of(V);
+  const View& W = V.v[v];
+  const int s = blockIdx.x - W.blk0;
+  if (s >= W.f.S || !W.F.st[s].act) return;   // uniform over the block
+  const int tid = threadIdx.x;
+  const bool top = (top_mask >> v) & 1;
+  // the chain of meshes: entry f (n = 8 or 4), then c when f is 8 x 8, then 2 x 2
+  const int nl = W.f.n == 2 * kCoarsest ? 2 : 3;
+  int nn[3], NN[3];
+  nn[0] = W.f.n;
+  for (int l = 1; l < nl; ++l) nn[l] = nn[l - 1] / 2;
+  for (int l = 0; l < nl; ++l) NN[l] = (nn[l] + 1) * (nn[l] + 1);
+  const float4* Al[2] = {W.f.A + (size_t)s * kGroups * NN[0], nl == 3 ? W.c.A + (size_t)s * kGroups * NN[1] : nullptr};
+  const float4* Dl[2] = {W.f.Dinv + (size_t)s * kDinvGroups * NN[0],
+                         nl == 3 ? W.c.Dinv + (size_t)s * kDinvGroups * NN[1] : nullptr};
+  for (int p = tid; p < NN[0]; p += blockDim.x) sR[0][p] = W.f.r[(size_t)s * NN[0] + p];
+  __syncthreads();
+  // descend: pre-smoothing from zero, residual, restriction
+  for (int l = 0; l + 1 < nl; ++l) {
+    const int n = nn[l], N = NN[l];
+    const float4* A = Al[l];
+    const float4* D = Dl[l];
+    for (int p = tid; p < N; p += blockDim.x) sX[l][p] = dmul(D[p], D[N + p], sR[l][p]);
+    __syncthreads();
+    for (int p = tid; p < N; p += blockDim.x) {
+      const int i = p % (n + 1), j = p / (n + 1);
+      float y[3] = {0.f, 0.f, 0.f};
+      apply_node(A, N, n, i, j, [&](int q) { return sX[l][q]; }, y);
+      const float4 r = sR[l][p];
+      sT[l][p] = f4(r.x - y[0], r.y - y[1], r.z - y[2]);
+    }
+    __syncthreads();
+    const int nc = nn[l + 1];
+    for (int P = tid; P < NN[l + 1]; P += blockDim.x) {
+      const int I = P % (nc + 1), J = P / (nc + 1);
+      float acc[3] = {0.f, 0.f, 0.f};
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int pi = 2 * I + dx, pj = 2 * J + dy;
+          if (pi < 0 || pj < 0 || pi > n || pj > n) continue;
+          const float w = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f);
+          const float4 t = sT[l][pj * (n + 1) + pi];
+          acc[0] += w * t.x;
+          acc[1] += w * t.y;
+          acc[2] += w * t.z;
+        }
+      const int dm = dmask(I, J, nc);
+      sR[l + 1][P] = f4((dm & 1) ? 0.f : acc[0], (dm & 2) ? 0.f : acc[1], acc[2]);
+    }
+    __syncthreads();
+  }
+  // coarsest: t = Ainv r, a thread per node
+  {
+    const int lc = nl - 1;
+    const float* __restrict__ M = W.Ainv + (size_t)s * kCoarseDofs * kCoarseDofs;
+    for (int node = tid; node < kCoarseDofs / 3; node += blockDim.x) {
+      float o[3];
+      for (int c = 0; c < 3; ++c) {
+        const float* row = M + (3 * node + c) * kCoarseDofs;
+        float acc = 0.f;
+        for (int q = 0; q < kCoarseDofs / 3; ++q) {
+          const float4 r = sR[lc][q];
+          acc += row[3 * q] * r.x + row[3 * q + 1] * r.y + row[3 * q + 2] * r.z;
+        }
+        o[c] = acc;
+      }
+      sT[lc][node] = f4(o[0], o[1], o[2]);
+    }
+    __syncthreads();
+  }
+  // ascend: prolongation, post-smoothing (the result in sT of each level)
+  double rz = 0.0;
+  for (int l = nl - 2; l >= 0; --l) {
+    const int n = nn[l], N = NN[l], nc = nn[l + 1];
+    for (int p = tid; p < N; p += blockDim.x) {
+      const int i = p % (n + 1), j = p / (n + 1);
+      const int I0 = i >> 1, J0 = j >> 1;
+      const bool ox = i & 1, oy = j & 1;
+      const float w = (ox ? 0.5f : 1.f) * (oy ? 0.5f : 1.f);
+      float4 x = sX[l][p];
+      for (int b = 0; b < 4; ++b) {
+        const int di = b & 1, dj = b >> 1;
+        if ((di && !ox) || (dj && !oy)) continue;
+        const float4 c = sT[l + 1][(J0 + dj) * (nc + 1) + I0 + di];
+        x.x += w * c.x;
+        x.y += w * c.y;
+        x.z += w * c.z;
+      }
+      sX[l][p] = x;
+    }
+    __syncthreads();
+    const float4* A = Al[l];
+    const float4* D = Dl[l];
+    for (int p = tid; p < N; p += blockDim.x) {
+      const int i = p % (n + 1), j = p / (n + 1);
+      float y[3] = {0.f, 0.f, 0.f};
+      apply_node(A, N, n, i, j, [&](int q) { return sX[l][q]; }, y);
+      const float4 r = sR[l][p], xp = sX[l][p];
+      const float4 e = dmul(D[p], D[N + p], f4(r.x - y[0], r.y - y[1], r.z - y[2]));
+      const float4 z = f4(xp.x + e.x, xp.y + e.y, xp.z + e.z);
+      sT[l][p] = z;
+      if (l == 0) {
+        W.f.t[(size_t)s * N + p] = z;
+        if (top) rz += (double)r.x * z.x + (double)r.y * z.y + (double)r.z * z.z;
+      }
+    }
+    __syncthreads();
+  }
+  if (top) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) rz += __shfl_down_sync(0xffffffffu, rz, o);
+    if ((tid & 31) == 0) red[tid >> 5] = rz;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int k = 0; k < kBottomThreads / 32; ++k) t += red[k];
+      atomicAdd(&W.F.st[s].rz_new, t);
+    }
   }
 }
 
@@ -1129,7 +1236,9 @@ cudaError_t launch_coarsest_inverse(const Views& V, cudaStream_t st) {
 }
 cudaError_t launch_pre(const Views& V, cudaStream_t st) { MLMCC_LAUNCH(k_pre, kThreads, V); }
 cudaError_t launch_restrict(const Views& V, cudaStream_t st) { MLMCC_LAUNCH(k_restrict, kThreads, V); }
-cudaError_t launch_coarse_solve(const Views& V, cudaStream_t st) { MLMCC_LAUNCH(k_coarse_solve, kThreads, V); }
+cudaError_t launch_bottom(const Views& V, int top_mask, cudaStream_t st) {
+  MLMCC_LAUNCH(k_bottom, kBottomThreads, V, top_mask);
+}
 cudaError_t launch_prolong(const Views& V, cudaStream_t st) { MLMCC_LAUNCH(k_prolong, kThreads, V); }
 cudaError_t launch_post(const Views& V, bool top, cudaStream_t st) { MLMCC_LAUNCH(k_post, kThreads, V, top); }
 cudaError_t launch_cg_apply(const Views& V, bool odd, cudaStream_t st) {

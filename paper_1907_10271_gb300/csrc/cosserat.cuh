@@ -34,6 +34,8 @@ constexpr int kCoarseDofs = 27;   // 3 (kCoarsest + 1)^2
 constexpr int kThreads = 256;
 constexpr int kInverseWarps = 8;   // samples (one warp each) per block of the coarsest inverse
 constexpr float kOmega = 0.6f;    // block-Jacobi damping
+constexpr int kBottomN = 8;       // the fused bottom covers the meshes of at most 8 x 8 elements
+constexpr int kBottomThreads = 96;
 
 // One multigrid level of one batch.
 struct Lev {
@@ -111,7 +113,9 @@ cudaError_t launch_coarsest_inverse(const Views& v, cudaStream_t st);  // Ainv f
 // V-cycle
 cudaError_t launch_pre(const Views& v, cudaStream_t st);               // x = Dinv r, t = r - A x
 cudaError_t launch_restrict(const Views& v, cudaStream_t st);          // c.r = P^T f.t (masked)
-cudaError_t launch_coarse_solve(const Views& v, cudaStream_t st);      // f.t = Ainv f.r (coarsest)
+// the cycle below and including f (n <= kBottomN) of each view in one block per sample;
+// bit v of top_mask: view v's f is its solve mesh (r . z into rz_new)
+cudaError_t launch_bottom(const Views& v, int top_mask, cudaStream_t st);
 cudaError_t launch_prolong(const Views& v, cudaStream_t st);           // f.x += P c.t
 cudaError_t launch_post(const Views& v, bool top, cudaStream_t st);    // f.t = x + Dinv (r - A x)
 // correction CG on the solve mesh (f = level 0)

@@ -37,7 +37,7 @@ enum Op {
 };
 const char* const kOpNames[kOpCount] = {
     "kl_coefficients", "kl_synthesis", "build_fine", "rap", "coarsest_inverse", "pre", "restrict",
-    "coarse_solve", "prolong", "post", "cg_apply", "cg_update", "scalars", "resid64", "accumulate", "qoi",
+    "bottom", "prolong", "post", "cg_apply", "cg_update", "scalars", "resid64", "accumulate", "qoi",
     "moments", "layout"};
 
 constexpr int kGraphIters = 4;        // correction iterations per graph replay (even)
@@ -230,7 +230,15 @@ size_t layout(const mlmcc_ctx& c, const std::vector<Group>& groups, char* base, 
   return off;
 }
 
-enum class Kind { Nodes, CoarseNodes, CoarseDofs, Inverse, Qoi, Samples, Build };
+enum class Kind { Nodes, CoarseNodes, Bottom, Inverse, Qoi, Samples, Build };
+
+// multigrid level at which a batch enters the fused bottom: its first mesh of at most
+// kBottomN elements per side
+int bottom_level(const GroupBufs& b) {
+  int k = 0;
+  while ((b.n >> k) > mlmcc::kBottomN) ++k;
+  return k;
+}
 
 // View table of one launch: batches with multigrid level k (f) and k + 1 (c);
 // `need` filters the batches (e.g. those whose coarsest level lies below k).
@@ -242,7 +250,7 @@ Views make_views(const std::vector<GroupBufs>& G, int k, Kind kind, Need need, c
   for (const GroupBufs& b : G) {
     if (!need(b) || V.nv >= mlmcc::kMaxViews) continue;
     View& v = V.v[V.nv];
-    const int kf = (kind == Kind::CoarseDofs || kind == Kind::Inverse) ? b.K - 1 : k;
+    const int kf = kind == Kind::Inverse ? b.K - 1 : (kind == Kind::Bottom ? bottom_level(b) : k);
     v.f = b.lev[kf];
     if (kf + 1 < b.K) v.c = b.lev[kf + 1];
     v.F = b.F;
@@ -251,7 +259,10 @@ Views make_views(const std::vector<GroupBufs>& G, int k, Kind kind, Need need, c
     switch (kind) {
       case Kind::Nodes: v.items = b.S * v.f.N; break;
       case Kind::CoarseNodes: v.items = b.S * v.c.N; break;
-      case Kind::CoarseDofs: v.items = b.S * (mlmcc::kCoarseDofs / 3); break;   // a thread per coarsest node
+      case Kind::Bottom:
+        v.items = b.S;
+        threads = 1;   // one block per sample
+        break;
       case Kind::Inverse:
         v.items = b.S;
         threads = mlmcc::kInverseWarps;   // samples per block of the inverse kernel
@@ -275,7 +286,8 @@ Views make_views(const std::vector<GroupBufs>& G, int k, Kind kind, Need need, c
 // All view tables of one solve.
 struct Sched {
   int maxK = 0;
-  Views fine, build, samples, qoi, coarse, inverse;
+  Views fine, build, samples, qoi, bottom, inverse;
+  int top_mask = 0;   // views of `bottom` whose entry mesh is their solve mesh
   std::vector<Views> pre, restr, prol, post, rap;
   int64_t vcycle_kernels = 0;
 };
@@ -288,15 +300,25 @@ Sched schedule(const std::vector<GroupBufs>& G, const mlmcc::Consts* cc) {
   s.build = make_views(G, 0, Kind::Build, all, cc);
   s.samples = make_views(G, 0, Kind::Samples, all, cc);
   s.qoi = make_views(G, 0, Kind::Qoi, all, cc);
-  s.coarse = make_views(G, 0, Kind::CoarseDofs, all, cc);
+  s.bottom = make_views(G, 0, Kind::Bottom, all, cc);
   s.inverse = make_views(G, 0, Kind::Inverse, all, cc);
+  int nb = 0;
+  for (const GroupBufs& b : G) {
+    if (bottom_level(b) == 0) s.top_mask |= 1 << nb;
+    ++nb;
+  }
+  int depth = 0;
+  for (const GroupBufs& b : G) depth = std::max(depth, bottom_level(b));
+  for (int k = 0; k < depth; ++k) {
+    auto above = [k](const GroupBufs& b) { return k < bottom_level(b); };
+    s.pre.push_back(make_views(G, k, Kind::Nodes, above, cc));
+    s.restr.push_back(make_views(G, k, Kind::CoarseNodes, above, cc));
+    s.prol.push_back(make_views(G, k, Kind::Nodes, above, cc));
+    s.post.push_back(make_views(G, k, Kind::Nodes, above, cc));
+  }
   for (int k = 0; k + 1 < s.maxK; ++k) {
     auto below = [k](const GroupBufs& b) { return k + 1 < b.K; };
-    s.pre.push_back(make_views(G, k, Kind::Nodes, below, cc));
-    s.restr.push_back(make_views(G, k, Kind::CoarseNodes, below, cc));
     s.rap.push_back(make_views(G, k, Kind::CoarseNodes, below, cc));
-    s.prol.push_back(make_views(G, k, Kind::Nodes, below, cc));
-    s.post.push_back(make_views(G, k, Kind::Nodes, below, cc));
   }
   s.vcycle_kernels = 4 * (int64_t)s.pre.size() + 1;
   return s;
@@ -384,7 +406,7 @@ void vcycle(Launcher& L, const Sched& s, cudaStream_t st) {
     L(kOpPre, s.pre[k], mlmcc::launch_pre);
     L(kOpRestrict, s.restr[k], mlmcc::launch_restrict);
   }
-  L(kOpCoarse, s.coarse, mlmcc::launch_coarse_solve);
+  L(kOpCoarse, items_of(s.bottom), [&] { return mlmcc::launch_bottom(s.bottom, s.top_mask, st); });
   for (int k = nd - 1; k >= 0; --k) {
     L(kOpProlong, s.prol[k], mlmcc::launch_prolong);
     const Views& V = s.post[k];
