@@ -627,7 +627,8 @@ __device__ __forceinline__ float4 dmul(float4 d0, float4 d1, float4 r) {
 
 // Pre-smoothing from zero and the residual: x = Dinv r, t = r - A x (x of the
 // neighbours recomputed from their r).
-__global__ void __launch_bounds__(kThreads) k_pre(const __grid_constant__ Views V) {
+// four resident blocks per SM (at most 64 registers, no spills): the kernel is latency-bound
+__global__ void __launch_bounds__(kThreads, 4) k_pre(const __grid_constant__ Views V) {
   const Item it = item_of(V, V.v[view_of(V)].f.N);
   const View& W = V.v[it.v];
   if (!it.ok || !active(W, it.s)) return;
@@ -694,7 +695,8 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const __grid_constant__ Vi
 
 // Post-smoothing: f.t = x + Dinv (r - A x). On the solve mesh (top) f.t is the
 // preconditioned residual z and r . z is accumulated into rz_new.
-__global__ void __launch_bounds__(kThreads) k_post(const __grid_constant__ Views V, bool top) {
+// four resident blocks per SM (at most 64 registers, no spills)
+__global__ void __launch_bounds__(kThreads, 4) k_post(const __grid_constant__ Views V, bool top) {
   const Item it = item_of(V, V.v[view_of(V)].f.N);
   const View& W = V.v[it.v];
   const bool ok = it.ok && active(W, it.s);
