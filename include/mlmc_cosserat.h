@@ -111,6 +111,20 @@ mlmc_status mlmcc_sample_levels(mlmcc_ctx* ctx, int32_t n_req, const int32_t* le
    stream solved on mesh `mesh_level`, any mesh of the context); q[n * 2], status[n]
    (nullable). Does not touch the moments. */
 mlmc_status mlmcc_solve_batch(mlmcc_ctx* ctx, const mlmc_item* items, int64_t n, double* q, int32_t* status);
+/* Algorithm 1 (Sec. 2.3) on quantity `qoi` (0 strength, 1 reaction): adds levels from 0
+   until the bias estimate |Y_hat_L| / (m^alpha - 1) (Eq. bias_estimate) falls below
+   sqrt(1 - theta) e, topping each level up to N_hat_l of Eq. optimal_Nl with
+   e_s^2 = theta e^2 (Eq. tausplit) and the cost of a level pair C_l = M_l^gamma +
+   M_{l-1}^gamma (M the DOFs of a mesh; the paper fits gamma = 1.3 for this problem).
+   Level l's samples are ids 0, 1, 2, .. in order, continuing from the samples the
+   context's moments already hold (mlmcc_reset_stats starts afresh). Writes the estimate
+   sum_l mean(Y_l), stats[0..L] (nullable, max_level + 1 entries) and *L_out (nullable).
+   Returns MLMC_ERR_NOT_CONVERGED if max_level was reached without passing the bias test
+   (outputs still written). Errors: MLMC_ERR_INVALID_ARG for e <= 0, theta outside (0, 1),
+   n_star < 1, max_level < 0, qoi not 0 or 1, m <= 1, alpha <= 0, gamma <= 0. */
+mlmc_status mlmcc_estimate(mlmcc_ctx* ctx, double e, double theta, int64_t n_star, int32_t max_level, int32_t qoi,
+                           double m, double alpha, double gamma, double* estimate, mlmc_level_stats* stats,
+                           int32_t* L_out);
 mlmc_status mlmcc_level_stats_get(mlmcc_ctx* ctx, int32_t level, mlmc_level_stats* out);
 mlmc_status mlmcc_reset_stats(mlmcc_ctx* ctx);
 

@@ -296,6 +296,12 @@ def kl_basis(cfg, n, n_kl):
 
 # ---------------------------------------------------------------- level pairs (Sec. 2.2)
 
+def dofs(cfg, mesh):
+    """M of mesh `mesh`: 3 (n + 1)^2 with n = n0 2^mesh (Sec. 3.2: M_0 = 243 for n0 = 8)."""
+    n = cfg["n0"] << mesh
+    return 3 * (n + 1) ** 2
+
+
 def n_kl(cfg, level):
     """N_KL of mesh `level`: 50 + 50 l (Sec. 3.2)."""
     return cfg["kl_terms0"] + cfg["kl_terms_step"] * level

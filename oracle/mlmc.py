@@ -125,10 +125,11 @@ def level_cost(cfg, level, gamma):
 
 
 def algorithm1(cfg, e, theta, n_star, max_level, qoi=0, alpha=1.0, gamma=1.0, m=4,
-               sampler=None):
+               sampler=None, cost=None):
     """Adaptive MLMC (Algorithm 1). Returns (estimate, per-level Y lists, L, converged).
 
-    `sampler(level, ids) -> Y[len(ids)]` defaults to the FE level pair of this module.
+    `sampler(level, ids) -> Y[len(ids)]` defaults to the FE level pair of this module;
+    `cost(level)`, the cost of one level pair, defaults to level_cost(cfg, level, gamma).
     """
     if sampler is None:
         basis = Basis(cfg)
@@ -148,7 +149,7 @@ def algorithm1(cfg, e, theta, n_star, max_level, qoi=0, alpha=1.0, gamma=1.0, m=
         L += 1
         Y.append(list(sampler(L, np.arange(n_star))))
         V = [moments(y)[2] for y in Y]
-        C = [level_cost(cfg, l, gamma) for l in range(L + 1)]
+        C = [cost(l) if cost is not None else level_cost(cfg, l, gamma) for l in range(L + 1)]
         N_hat = optimal_samples(V, C, es2)
         for l in range(L + 1):
             if len(Y[l]) < N_hat[l]:

@@ -768,6 +768,8 @@ def libc():
             "mlmcc_sample_levels": (I32, [P, I32, P, P, P, P, P, P]),
             "mlmcc_solve_batch": (I32, [P, P, I64, P, P]),
             "mlmcc_level_stats_get": (I32, [P, I32, P]),
+            "mlmcc_estimate": (I32, [P, ctypes.c_double, ctypes.c_double, I64, I32, I32, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, P, P, P]),
             "mlmcc_reset_stats": (I32, [P]),
             "mlmcc_field": (I32, [P, I32, I32, U64, I64, P]),
             "mlmcc_apply": (I32, [P, I32, I32, U64, I64, P, P]),
@@ -846,6 +848,18 @@ def mlmcc_level_stats(ctx, level):
     out = mlmc_level_stats()
     _checkc(ctx, libc().mlmcc_level_stats_get(ctx, level, ctypes.byref(out)))
     return out.as_dict()
+
+
+def mlmcc_estimate(ctx, e, theta=0.5, n_star=64, max_level=4, qoi=0, m=4.0, alpha=0.786, gamma=1.3):
+    """Algorithm 1 on the Cosserat engine: (estimate, [level stats dicts], L, converged)."""
+    stats = (mlmc_level_stats * (max_level + 1))()
+    est, L = ctypes.c_double(), ctypes.c_int32()
+    s = libc().mlmcc_estimate(ctx, float(e), float(theta), int(n_star), int(max_level), int(qoi), float(m),
+                              float(alpha), float(gamma), ctypes.byref(est), ctypes.cast(stats, ctypes.c_void_p),
+                              ctypes.byref(L))
+    if s not in (MLMC_OK, MLMC_ERR_NOT_CONVERGED):
+        _checkc(ctx, s)
+    return est.value, [stats[l].as_dict() for l in range(L.value + 1)], L.value, s == MLMC_OK
 
 
 def mlmcc_reset_stats(ctx):

@@ -80,6 +80,7 @@ struct mlmcc_ctx {
   int* pinned = nullptr;   // host-pinned count / iteration words
   int64_t launches = 0;
   int last_iters = 0, last_refine = 0;
+  std::vector<int64_t> next_id;   // ids mlmcc_estimate has drawn per level since the last reset
   struct GraphEntry {
     std::vector<int64_t> key;
     cudaGraphExec_t exec;
@@ -723,6 +724,7 @@ mlmc_status mlmcc_create(const mlmcc_config* cfg, void* cuda_stream, mlmcc_ctx**
   c.consts.R = cfg->R_ratio;
   c.basis.assign(L, nullptr);
   c.acc_host.assign(L, mlmc::LevelAcc{});
+  c.next_id.assign(L, 0);
   cudaError_t e = cudaMalloc(&c.consts_dev, sizeof(mlmcc::Consts));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c.consts_dev, &c.consts, sizeof(mlmcc::Consts), cudaMemcpyHostToDevice, c.st);
@@ -764,7 +766,6 @@ mlmc_status mlmcc_sample_levels(mlmcc_ctx* h, int32_t n_req, const int32_t* leve
   }
   if (total > (int64_t(1) << 24)) return c.fail(MLMC_ERR_INVALID_ARG, "too many samples");
   if (total == 0) return MLMC_OK;
-  if (!q_fine) return c.fail(MLMC_ERR_INVALID_ARG, "q_fine is required");
   // one batch per mesh: level m's fine solves and level m + 1's coarse solves
   std::vector<Group> groups;
   std::vector<int> gidx(c.cfg.levels, -1);
@@ -915,7 +916,66 @@ mlmc_status mlmcc_reset_stats(mlmcc_ctx* h) {
   mlmcc_ctx& c = *h;
   CK(cudaMemsetAsync(c.acc_dev, 0, sizeof(mlmc::LevelAcc) * c.cfg.levels, c.st), "reset");
   CK(cudaStreamSynchronize(c.st), "reset");
+  std::fill(c.next_id.begin(), c.next_id.end(), 0);
   return MLMC_OK;
+}
+
+mlmc_status mlmcc_estimate(mlmcc_ctx* h, double e, double theta, int64_t n_star, int32_t max_level, int32_t qoi,
+                           double m, double alpha, double gamma, double* estimate, mlmc_level_stats* stats,
+                           int32_t* L_out) {
+  if (!h) return MLMC_ERR_INVALID_ARG;
+  mlmcc_ctx& c = *h;
+  if (!(e > 0) || !(theta > 0 && theta < 1) || n_star < 1 || max_level < 0 || qoi < 0 || qoi > 1 || !(m > 1) ||
+      !(alpha > 0) || !(gamma > 0))
+    return c.fail(MLMC_ERR_INVALID_ARG, "bad Algorithm 1 parameters");
+  max_level = std::min<int32_t>(max_level, c.cfg.levels - 1);
+  const double es2 = theta * e * e, eb = std::sqrt(1.0 - theta) * e;
+  auto dofs = [&](int l) { return 3.0 * (c.mesh_n(l) + 1.0) * (c.mesh_n(l) + 1.0); };
+  auto cost = [&](int l) { return std::pow(dofs(l), gamma) + (l > 0 ? std::pow(dofs(l - 1), gamma) : 0.0); };
+  auto refresh = [&]() -> mlmc_status {
+    CK(cudaMemcpyAsync(c.acc_host.data(), c.acc_dev, sizeof(mlmc::LevelAcc) * c.cfg.levels, cudaMemcpyDeviceToHost,
+                       c.st),
+       "stats");
+    CK(cudaStreamSynchronize(c.st), "stats");
+    return MLMC_OK;
+  };
+  auto take = [&](int l, int64_t upto) -> mlmc_status {
+    if (c.next_id[l] >= upto) return MLMC_OK;
+    const int64_t cnt = upto - c.next_id[l];
+    const mlmc_status s = mlmcc_sample_level(h, l, (uint64_t)c.next_id[l], cnt, nullptr, nullptr, nullptr);
+    if (s != MLMC_OK) return s;
+    c.next_id[l] = upto;
+    return MLMC_OK;
+  };
+  int L = -1;
+  bool converged = false;
+  mlmc_status s = MLMC_OK;
+  while (!converged) {
+    if (L + 1 > max_level) break;
+    ++L;
+    if ((s = take(L, n_star)) != MLMC_OK || (s = refresh()) != MLMC_OK) return s;
+    std::vector<double> V(L + 1);
+    double tot = 0.0;
+    for (int l = 0; l <= L; ++l) {
+      const mlmc::LevelAcc& a = c.acc_host[l];
+      V[l] = a.n > 0 ? a.m2[qoi] / (double)a.n : 0.0;
+      tot += std::sqrt(V[l] * cost(l));
+    }
+    for (int l = 0; l <= L; ++l) {
+      const int64_t nhat = (int64_t)std::ceil(tot * std::sqrt(V[l] / cost(l)) / es2);
+      if ((s = take(l, nhat)) != MLMC_OK) return s;
+    }
+    if ((s = refresh()) != MLMC_OK) return s;
+    if (std::fabs(c.acc_host[L].mean[qoi]) / (std::pow(m, alpha) - 1.0) < eb) converged = true;
+  }
+  double est = 0.0;
+  for (int l = 0; l <= L; ++l) est += c.acc_host[l].mean[qoi];
+  if (estimate) *estimate = est;
+  if (L_out) *L_out = L;
+  if (stats)
+    for (int l = 0; l <= L; ++l)
+      if ((s = mlmcc_level_stats_get(h, l, &stats[l])) != MLMC_OK) return s;
+  return converged ? MLMC_OK : c.fail(MLMC_ERR_NOT_CONVERGED, "max_level reached before the bias test passed");
 }
 
 mlmc_status mlmcc_field(mlmcc_ctx* h, int32_t level, int32_t mesh_level, uint64_t first_id, int64_t n,

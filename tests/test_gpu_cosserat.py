@@ -198,3 +198,32 @@ def test_iteration_cap_reports_not_converged(B):
         assert np.isfinite(q2).all()
     finally:
         B.mlmcc_destroy(h)
+
+
+def test_algorithm1_matches_oracle(B):
+    """mlmcc_estimate (Algorithm 1 on the strength) against the oracle's Algorithm 1 driven
+    by the oracle's level pairs on the same ids: the same levels, the same N_l and the
+    same estimate (to the QoI tolerance)."""
+    from oracle import mlmc as M
+    cfg = dict(W, levels=3)
+    kw = dict(e=80.0, theta=0.5, n_star=8, max_level=2, qoi=0, m=4.0, alpha=0.786, gamma=1.3)
+    h = make(B, levels=3)
+    try:
+        B.mlmcc_reset_stats(h)
+        est, stats, L, conv = B.mlmcc_estimate(h, **kw)
+    finally:
+        B.mlmcc_destroy(h)
+
+    def sampler(level, ids):
+        qf, qc = C.level_pair(cfg, level, np.asarray(ids))
+        return qf[:, 0] - qc[:, 0]
+
+    def cost(level):
+        return C.dofs(cfg, level) ** 1.3 + (C.dofs(cfg, level - 1) ** 1.3 if level > 0 else 0.0)
+
+    ref, Y, L_ref, conv_ref = M.algorithm1(cfg, kw["e"], kw["theta"], kw["n_star"], kw["max_level"], qoi=0,
+                                           alpha=kw["alpha"], gamma=kw["gamma"], m=kw["m"], sampler=sampler,
+                                           cost=cost)
+    assert L == L_ref and conv == conv_ref
+    assert [s["n"] for s in stats] == [len(y) for y in Y]
+    assert abs(est / ref - 1.0) < 1e-6

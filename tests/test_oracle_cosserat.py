@@ -27,6 +27,7 @@ from workloads import COSSERAT_TEST1 as W
 def test_level0_dof_count():
     K = C.assemble(W, 8, np.zeros(64))
     assert K.shape == (243, 243)
+    assert C.dofs(W, 0) == 243 and C.dofs(W, 1) == C.assemble(W, 16, np.zeros(256)).shape[0]
 
 
 def test_rotation_identities():
