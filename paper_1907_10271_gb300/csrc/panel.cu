@@ -559,7 +559,8 @@ __global__ void k_coarse_setup(PGrid g, const float* __restrict__ ke, const int*
 }
 
 __global__ void k_coarse_solve(PGrid g, const float* __restrict__ ainv, const int* __restrict__ freedofs, int nf,
-                               const float4* __restrict__ b, float4* __restrict__ x, const int* __restrict__ active) {
+                               const float4* __restrict__ b, float4* __restrict__ x, const int* __restrict__ active,
+                               int shared) {
   const int e = blockIdx.x, s = e >> g.cshift;
   if (active && !active[s]) return;
   __shared__ float bl[kMaxCoarseFree];
@@ -569,7 +570,7 @@ __global__ void k_coarse_solve(PGrid g, const float* __restrict__ ainv, const in
   for (int k = threadIdx.x; k < nf; k += blockDim.x) bl[k] = bf[freedofs[k]];
   for (int k = threadIdx.x; k < 4 * nn; k += blockDim.x) xf[k] = 0.f;
   __syncthreads();
-  const float* A = ainv + (size_t)s * nf * nf;
+  const float* A = ainv + (shared ? (size_t)0 : (size_t)s * nf * nf);
   for (int r = threadIdx.x; r < nf; r += blockDim.x) {
     float acc = 0.f;
     for (int c = 0; c < nf; ++c) acc += A[r * nf + c] * bl[c];
@@ -1048,10 +1049,10 @@ cudaError_t launch_coarse_setup(const PGrid& g, const float* ke, int n_samples, 
 }
 
 cudaError_t launch_coarse_solve(const PGrid& g, const float* ainv, const int* freedofs, int nf, const float4* b,
-                                float4* x, const int* active, cudaStream_t st) {
+                                float4* x, const int* active, bool shared, cudaStream_t st) {
   if (g.nb <= 0) return cudaSuccess;
   if (nf <= 0 || nf > kMaxCoarseFree) return cudaErrorInvalidValue;
-  k_coarse_solve<<<g.nb, kThreads, 0, st>>>(g, ainv, freedofs, nf, b, x, active);
+  k_coarse_solve<<<g.nb, kThreads, 0, st>>>(g, ainv, freedofs, nf, b, x, active, shared ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -76,11 +76,13 @@ cudaError_t launch_patch_color(const PGrid& g, const float* ke, const float* pin
                                const float4* b, const float4* in, float4* out, int sx, int sy, const int* active,
                                cudaStream_t st);
 
-// Coarsest mesh: per-sample dense inverse of K on the free DOFs (free[k] = 4 node + c)
+// Coarsest mesh: dense inverse of K on the free DOFs (free[k] = 4 node + c), one per
+// sample of ke; the solve applies inverse s to entry s, or one inverse to every entry
+// with shared
 cudaError_t launch_coarse_setup(const PGrid& g, const float* ke, int n_samples, const int* free, int nf, float* ainv,
                                 cudaStream_t st);
 cudaError_t launch_coarse_solve(const PGrid& g, const float* ainv, const int* free, int nf, const float4* b,
-                                float4* x, const int* active, cudaStream_t st);
+                                float4* x, const int* active, bool shared, cudaStream_t st);
 
 // LOBPCG state of a solve (per sample unless noted).
 struct Eig {

@@ -87,6 +87,9 @@ struct mlmcp_ctx {
   // patch smoother: the pristine laminate's patch inverses per mesh size (nx, ny), made
   // on first use and shared by every sample and solve
   std::vector<std::pair<std::pair<int, int>, float*>> patch_cache;
+  // per MLMC mesh level: the coarsest mesh's inverse for the pristine laminate, shared by
+  // every sample's multigrid cycle
+  std::vector<float*> coarse_cache;
   // per MLMC mesh level: the executable graph of four LOBPCG iterations, updated with
   // each call's pointers and sizes (cudaGraphExecUpdate) rather than re-instantiated
   std::vector<cudaGraphExec_t> lobpcg_exec;
@@ -112,6 +115,8 @@ struct mlmcp_ctx {
     return g;
   }
   ~mlmcp_ctx() {
+    for (float* p : coarse_cache)
+      if (p) cudaFree(p);
     for (cudaGraphExec_t g : lobpcg_exec)
       if (g) cudaGraphExecDestroy(g);
     for (auto& kv : patch_cache) cudaFree(kv.second);
@@ -192,6 +197,35 @@ mlmc_status patch_inverses(mlmcp_ctx& c, const Mesh& m, float** out) {
 
 // n samples (perturbations xi, device [n][plies]) on MLMC mesh m; q [n][2], status [n]
 // (device)
+// The coarsest-mesh inverse of MLMC mesh level m's hierarchy for the pristine laminate
+// (no perturbation), made on first use and shared by every sample: the coarsest level
+// only preconditions, and the ply perturbations change its matrix by a few per cent.
+mlmc_status coarse_inverse(mlmcp_ctx& c, int m, float** out) {
+  if (c.coarse_cache.size() < (size_t)c.cfg.levels) c.coarse_cache.assign(c.cfg.levels, nullptr);
+  if (c.coarse_cache[m]) {
+    *out = c.coarse_cache[m];
+    return MLMC_OK;
+  }
+  const Mesh& M = c.hier[m].back();
+  const int nf = c.nfree[m];
+  Scratch sc{c.st};
+  double* xi0 = sc.take<double>(c.cfg.n_plies);
+  double* dstar = sc.take<double>(6);
+  double* kgt = sc.take<double>(1);
+  float* ke = sc.take<float>(144);
+  CK(sc.err, "alloc");
+  float* ainv = nullptr;
+  CK(cudaMalloc(&ainv, sizeof(float) * nf * nf), "alloc");
+  c.coarse_cache[m] = ainv;
+  CK(cudaMemsetAsync(xi0, 0, sizeof(double) * c.cfg.n_plies, c.st), "memset");
+  CK(mlmcp::launch_laminate(c.lam, xi0, 1, dstar, kgt, c.st), "laminate");
+  CK(mlmcp::launch_element_matrices(dstar, kgt, 1, c.cfg.lx / M.nx, c.cfg.ly / M.ny, ke, nullptr, c.st), "element");
+  CK(mlmcp::launch_coarse_setup(c.grid(M, 1, 0), ke, 1, c.free_dev[m], nf, ainv, c.st), "coarse setup");
+  CK(cudaStreamSynchronize(c.st), "coarse setup");
+  *out = ainv;
+  return MLMC_OK;
+}
+
 mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int* status) {
   if (n <= 0) return MLMC_OK;
   {
@@ -223,14 +257,17 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
   double* ke64 = sc.take<double>((size_t)n * 144);
   std::vector<float*> ke(L);
   for (int l = 0; l < L; ++l) ke[l] = sc.take<float>((size_t)n * 144);
-  float* ainv = sc.take<float>((size_t)n * nf * nf);
   CK(sc.err, "alloc");
+  float* ainv = nullptr;
+  {
+    const mlmc_status cs = coarse_inverse(c, m, &ainv);
+    if (cs != MLMC_OK) return cs;
+  }
   CK(mlmcp::launch_laminate(c.lam, xi, n, dstar, kgt, st), "laminate");
   for (int l = 0; l < L; ++l)
     CK(mlmcp::launch_element_matrices(dstar, kgt, n, c.cfg.lx / H[l].nx, c.cfg.ly / H[l].ny, ke[l],
                                       l == 0 ? ke64 : nullptr, st),
        "element matrices");
-  CK(mlmcp::launch_coarse_setup(c.grid(H[L - 1], n, 0), ke[L - 1], n, c.free_dev[m], nf, ainv, st), "coarse setup");
   const bool patch = c.cfg.smoother == 1;
   std::vector<float*> pinv(L, nullptr);   // patch smoother: shared inverses per smoothed mesh
   if (patch) {
@@ -306,7 +343,8 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
     }
     if (e != cudaSuccess) return e;
     float4* coarse_out = L == 1 ? out : xx[L - 1];
-    e = mlmcp::launch_coarse_solve(G[L - 1], ainv, c.free_dev[m], nf, L == 1 ? b0 : bb[L - 1], coarse_out, act, st);
+    e = mlmcp::launch_coarse_solve(G[L - 1], ainv, c.free_dev[m], nf, L == 1 ? b0 : bb[L - 1], coarse_out, act, true,
+                                    st);
     for (int l = L - 2; l >= 0 && e == cudaSuccess; --l) {
       const float4* b = l == 0 ? b0 : bb[l];
       const float4* below = xx[l + 1];   // every level's post-smoothed x ends in xx
@@ -329,7 +367,8 @@ mlmc_status solve_p(mlmcp_ctx& c, int m, int n, const double* xi, double* q, int
     }
     if (e != cudaSuccess) return e;
     float4* coarse_out = L == 1 ? out : xx[L - 1];
-    e = mlmcp::launch_coarse_solve(G[L - 1], ainv, c.free_dev[m], nf, L == 1 ? b0 : bb[L - 1], coarse_out, act, st);
+    e = mlmcp::launch_coarse_solve(G[L - 1], ainv, c.free_dev[m], nf, L == 1 ? b0 : bb[L - 1], coarse_out, act, true,
+                                    st);
     for (int l = L - 2; l >= 0 && e == cudaSuccess; --l) {
       const float4* b = l == 0 ? b0 : bb[l];
       const float4* below = (l + 1 == L - 1) ? xx[L - 1] : tt[l + 1];

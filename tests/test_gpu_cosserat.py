@@ -227,3 +227,18 @@ def test_algorithm1_matches_oracle(B):
     assert L == L_ref and conv == conv_ref
     assert [s["n"] for s in stats] == [len(y) for y in Y]
     assert abs(est / ref - 1.0) < 1e-6
+
+
+def test_level4_pair_matches_oracle(B):
+    """The largest mesh of the workload (128 x 128, 49,923 DOFs) against the oracle."""
+    h = make(B, levels=5)
+    try:
+        qf, qc = np.zeros(2), np.zeros(2)
+        st = np.ones(1, dtype=np.int32)
+        B.mlmcc_sample_level(h, 4, 77, 1, qf, qc, st)
+        assert st[0] == 0
+        ref_f, ref_c = C.level_pair(W, 4, [77])
+        np.testing.assert_allclose(qf, ref_f[0], rtol=1e-6)
+        np.testing.assert_allclose(qc, ref_c[0], rtol=1e-6)
+    finally:
+        B.mlmcc_destroy(h)
