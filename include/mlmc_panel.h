@@ -26,9 +26,11 @@
  *
  * Solver: per sample, block LOBPCG (two vectors) on (G, K) in FP32 with FP64 Gram
  * matrices and Rayleigh-Ritz, preconditioned by one geometric-multigrid V(2,2) cycle on
- * K (nodal 3x3 block Jacobi, bilinear transfers, rediscretised coarse operators, dense
- * coarsest inverse). The reported lambda is the Rayleigh quotient of the converged FP32
- * eigenvector evaluated in double, so its error is quadratic in the vector's.
+ * K (nodal 3x3 block Jacobi, bilinear transfers, rediscretised coarse operators, and the
+ * dense coarsest inverse of the pristine laminate shared by every sample), four
+ * iterations per CUDA-graph replay. The reported lambda is the Rayleigh quotient of the
+ * converged FP32 eigenvector evaluated in double, so its error is quadratic in the
+ * vector's.
  *
  * Memory, streams and errors as in mlmc.h: array arguments may be host or device
  * memory of the context's GPU; work is issued on the context's stream and the calls
