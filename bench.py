@@ -80,7 +80,7 @@ def parse():
                     help="skip the request-loop (selective refinement) measurement")
     ap.add_argument("--no-cosserat", dest="cosserat", action="store_false",
                     help="skip the Cosserat strength workload (the paper's first test problem)")
-    ap.add_argument("--case", choices=["full", "small", "hex3d", "panel", "cosserat"], default="full",
+    ap.add_argument("--case", choices=["full", "small", "hex3d", "panel", "panel_thin", "cosserat"], default="full",
                     help="small: one untimed call with 1/4 of each level's samples; hex3d / panel: one "
                          "untimed step of the 3D Hex8 block / the buckling panel (all for profilers)")
     ap.add_argument("--no-hex3d", dest="hex3d", action="store_false",
@@ -1144,11 +1144,12 @@ def run_cosserat_case():
     print(json.dumps({"case": "cosserat", "level_pairs": tot, "failed": int((st != 0).sum())}))
 
 
-def run_panel_case():
+def run_panel_case(W=None):
     """One step of the buckling panel (every level's samples), untimed: for profilers."""
     import torch
     from paper_1907_10271_gb300 import binding as B
-    from workloads import PANEL_RM_4LEVEL as W
+    if W is None:
+        from workloads import PANEL_RM_4LEVEL as W
     ctx = B.mlmcp_create(B.configp_from_workload(W), torch.cuda.current_stream().cuda_stream)
     failed = 0
     for lev, n in enumerate(W["n_per_level"]):
@@ -1157,7 +1158,7 @@ def run_panel_case():
         failed += int((st != 0).sum())
     torch.cuda.synchronize()
     B.mlmcp_destroy(ctx)
-    print(json.dumps({"case": "panel", "level_pairs": sum(W["n_per_level"]), "failed": failed}))
+    print(json.dumps({"case": W["name"], "level_pairs": sum(W["n_per_level"]), "failed": failed}))
 
 
 def run_hex3d_case():
@@ -1230,6 +1231,10 @@ def main():
         return
     if a.case == "panel":
         run_panel_case()
+        return
+    if a.case == "panel_thin":
+        from workloads import PANEL_C5_4LEVEL
+        run_panel_case(dict(PANEL_C5_4LEVEL, p_star=0.4172))   # the pilot's 1/150 quantile, kN
         return
     if a.case == "cosserat":
         run_cosserat_case()

@@ -58,6 +58,17 @@ __device__ __forceinline__ DF operator*(DF a, float b) {
 
 __device__ __forceinline__ DF operator*(float b, DF a) { return a * b; }
 
+// acc += a * b for float-float a and b: the exact product of the heads by FMA, the two
+// cross terms, then TwoSum into the accumulator.
+__device__ __forceinline__ void df_fma(DF& acc, DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const DF s = two_sum(acc.hi, p);
+  acc = fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, acc.lo)));
+}
+
 __device__ __forceinline__ DF shfl_down_df(DF a, int d) {
   return DF{__shfl_down_sync(0xffffffffu, a.hi, d), __shfl_down_sync(0xffffffffu, a.lo, d)};
 }

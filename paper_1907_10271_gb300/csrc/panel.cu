@@ -7,6 +7,7 @@
 // node-centric kernels keep it in shared memory and each node forms its own three rows
 // from the (up to) four elements around it. The geometric form with the 1-point rule
 // is sample-independent: G_e = hy / (4 hx) s s^T on the w-DOFs, s = (-1, 1, 1, -1).
+#include "dfloat.cuh"
 #include "panel.cuh"
 
 #include <algorithm>
@@ -222,32 +223,43 @@ __global__ void __launch_bounds__(kThreads) k_apply(PGrid g, const float* __rest
   if (gout) gout[o + t] = make_float4((bc && !f.w) ? 0.f : gw, 0.f, 0.f, 0.f);
 }
 
-// K x with the double element matrix and double sums (the vector itself single): for
-// thin plates, whose transverse shear strain grad w - theta is a small difference of
-// large terms, a single-precision sum keeps only a few digits of it. G x in single
-// precision (no cancellation). Rounded to single at the end.
+// K x with the element matrix of double accuracy and float-float sums (the vector itself
+// single, w in two parts): for thin plates, whose transverse shear strain grad w - theta
+// is a small difference of large terms, a single-precision sum keeps only a few digits
+// of it. The double element matrix is split into float-float pairs in shared memory and
+// every product and sum runs on the FP32 pipes (Knuth / Dekker transformations): GB300's
+// FP64 rate is a small fraction of its FP32 rate. G x in single precision (no
+// cancellation). Rounded to single at the end.
 __global__ void __launch_bounds__(kThreads) k_apply64(PGrid g, const double* __restrict__ ke64,
                                                       const float4* __restrict__ x, float4* __restrict__ out,
                                                       float4* __restrict__ gout, float4* __restrict__ rout,
                                                       const double* __restrict__ mu, const int* __restrict__ active) {
+  using mlmc::DF;
   const int e = blockIdx.y, s = e >> g.cshift;
   if (active && !active[s]) return;
-  __shared__ double K[144];
-  for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke64[(size_t)s * 144 + k];
+  __shared__ float Kh[144], Kl[144];
+  for (int k = threadIdx.x; k < 144; k += blockDim.x) {
+    const DF v = mlmc::df_from_double(ke64[(size_t)s * 144 + k]);
+    Kh[k] = v.hi;
+    Kl[k] = v.lo;
+  }
   __syncthreads();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int nn = g.nodes();
   if (t >= nn) return;
   const int i = t % (g.nx + 1), j = t / (g.nx + 1), np = g.nx + 1;
   const float4* xe = x + (size_t)e * nn;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, gsum = 0.0;
+  DF a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, gsum{0.f, 0.f};
+#pragma unroll
   for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
     for (int ox = 0; ox < 2; ++ox) {
       const int ei = i - ox, ej = j - oy;
       if (ei < 0 || ej < 0 || ei >= g.nx || ej >= g.ny) continue;
       const int a = corner_of(ox, oy);
-      const double* Ka = K + 36 * a;
-      double gs = 0.0;
+      const float* Ha = Kh + 36 * a;
+      const float* La = Kl + 36 * a;
+      DF gs{0.f, 0.f};
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int ni = ei + corner_x(c), nj = ej + corner_y(c);
@@ -255,24 +267,31 @@ __global__ void __launch_bounds__(kThreads) k_apply64(PGrid g, const double* __r
         const float4 v = xe[nj * np + ni];
         // w in two parts (high in x, low in w; the low part is zero for vectors kept in
         // one float)
-        const double vw = fc.w ? (double)v.x + (double)v.w : 0.0;
-        const double vx = fc.tx ? (double)v.y : 0.0, vy = fc.ty ? (double)v.z : 0.0;
-        const double* r = Ka + 3 * c;
-        a0 += r[0] * vw + r[1] * vx + r[2] * vy;
-        a1 += r[12] * vw + r[13] * vx + r[14] * vy;
-        a2 += r[24] * vw + r[25] * vx + r[26] * vy;
-        gs += corner_x(c) ? vw : -vw;
+        const DF vw = fc.w ? DF{v.x, v.w} : DF{0.f, 0.f};
+        const DF vx = mlmc::df(fc.tx ? v.y : 0.f), vy = mlmc::df(fc.ty ? v.z : 0.f);
+        const int r = 3 * c;
+        mlmc::df_fma(a0, DF{Ha[r], La[r]}, vw);
+        mlmc::df_fma(a0, DF{Ha[r + 1], La[r + 1]}, vx);
+        mlmc::df_fma(a0, DF{Ha[r + 2], La[r + 2]}, vy);
+        mlmc::df_fma(a1, DF{Ha[r + 12], La[r + 12]}, vw);
+        mlmc::df_fma(a1, DF{Ha[r + 13], La[r + 13]}, vx);
+        mlmc::df_fma(a1, DF{Ha[r + 14], La[r + 14]}, vy);
+        mlmc::df_fma(a2, DF{Ha[r + 24], La[r + 24]}, vw);
+        mlmc::df_fma(a2, DF{Ha[r + 25], La[r + 25]}, vx);
+        mlmc::df_fma(a2, DF{Ha[r + 26], La[r + 26]}, vy);
+        gs = corner_x(c) ? gs + vw : gs - vw;
       }
-      gsum += corner_x(a) ? gs : -gs;
+      gsum = corner_x(a) ? gsum + gs : gsum - gs;
     }
   const Free f = free_of(g, i, j);
-  const double gw = f.w ? gsum * ((double)g.hy / (4.0 * (double)g.hx)) : 0.0;
+  const double d0 = mlmc::df_to_double(a0), d1 = mlmc::df_to_double(a1), d2 = mlmc::df_to_double(a2);
+  const double gw = f.w ? mlmc::df_to_double(gsum) * ((double)g.hy / (4.0 * (double)g.hx)) : 0.0;
   const size_t o = (size_t)e * nn + t;
-  out[o] = masked(f, make_float4((float)a0, (float)a1, (float)a2, 0.f));
+  out[o] = masked(f, make_float4((float)d0, (float)d1, (float)d2, 0.f));
   if (gout) gout[o] = make_float4((float)gw, 0.f, 0.f, 0.f);
-  if (rout) {   // R = G x - mu K x of the entry's column, in double
+  if (rout) {   // R = G x - mu K x of the entry's column
     const double m = mu[(size_t)s * kCols + (e & ((1 << g.cshift) - 1))];
-    rout[o] = masked(f, make_float4((float)(gw - m * a0), (float)(-m * a1), (float)(-m * a2), 0.f));
+    rout[o] = masked(f, make_float4((float)(gw - m * d0), (float)(-m * d1), (float)(-m * d2), 0.f));
   }
 }
 
