@@ -358,6 +358,9 @@ __global__ void __launch_bounds__(128) k_apply(Grid3 g, const float4* __restrict
     k = (int)(r / g.ny);
   }
   float en = 0.f;
+  // a warp covers one x-row of elements when rows are whole multiples of 32 elements (and
+  // then every lane of a warp is valid or none is)
+  const bool row_warps = !boundary && g.nx % 32 == 0;
   if (valid) {
     const Cm<float> C = coef<float>(trig4[(int64_t)s * g.cols() + (int64_t)k * g.nx + i]);
     const int64_t base = (int64_t)s * g.nodes();
@@ -369,15 +372,42 @@ __global__ void __launch_bounds__(128) k_apply(Grid3 g, const float4* __restrict
 #pragma unroll
         for (int c = 0; c < 2; ++c) u[a][b][c] = load_v(x, base + node_of(g, i + a, j + b, k + c));
     element_apply<T, float>(C, g.h, u, f);
+    if (ENERGY) {
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+      for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < 2; ++b)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          add_node(y, base + node_of(g, i + a, j + b, k + c), f[a][b][c]);
-          if (ENERGY) en += dot_part(u[a][b][c], f[a][b][c]);
-        }
+          for (int c = 0; c < 2; ++c) en += dot_part(u[a][b][c], f[a][b][c]);
+    }
+    if constexpr (sizeof(T) == 4) {
+      if (row_warps) {
+        // the warp holds 32 consecutive elements of one x-row: node (i + 1, ., .) gets this
+        // lane's right-face forces and the next lane's left-face forces in one atomic
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            V3<T> nxt;
+            nxt.x = __shfl_down_sync(0xffffffffu, f[0][b][c].x, 1);
+            nxt.y = __shfl_down_sync(0xffffffffu, f[0][b][c].y, 1);
+            nxt.z = __shfl_down_sync(0xffffffffu, f[0][b][c].z, 1);
+            const V3<T> right = lane < 31 ? f[1][b][c] + nxt : f[1][b][c];
+            add_node(y, base + node_of(g, i + 1, j + b, k + c), right);
+            if (lane == 0) add_node(y, base + node_of(g, i, j + b, k + c), f[0][b][c]);
+          }
+        valid = false;   // scattered
+      }
+    }
+    if (valid) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) add_node(y, base + node_of(g, i + a, j + b, k + c), f[a][b][c]);
+    }
   }
   if (ENERGY) {   // every thread of the block reaches the reduction
     const double t = block_sum((double)en);
