@@ -152,6 +152,13 @@ typedef struct {
                                  (a warp strip may hold the end of one sample and the start of
                                  the next), so narrow meshes fill their warps; 0: every warp
                                  strip holds columns of one sample */
+  int32_t device_loop;        /* 1: with CUDA graphs, repeat the PCG batches and their
+                                 convergence test on the device (a conditional graph node,
+                                 at most max_iter / 4 batches) instead of reading the active
+                                 count on the host after each batch; same iterations and
+                                 results. 0 (default): host loop (measured 0.9 % faster on the
+                                 5-level workload: a replay of the conditional node costs
+                                 about what the host round trip did) */
 } mlmc_tuning;
 
 /* Times the level-pair workload {levels[k], counts[k]} (host arrays of n_req entries,

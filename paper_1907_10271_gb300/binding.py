@@ -294,12 +294,12 @@ PROFILE_OPS = ["pcg_update_presmooth", "presmooth", "postsmooth", "postsmooth_to
 class mlmc_tuning(ctypes.Structure):
     _fields_ = [("max_rows", ctypes.c_int32), ("min_rows", ctypes.c_int32), ("target_waves", ctypes.c_double),
                 ("nested_min_nodes", ctypes.c_int64), ("fused_bottom", ctypes.c_int32), ("step_ms", ctypes.c_double),
-                ("pack_samples", ctypes.c_int32)]
+                ("pack_samples", ctypes.c_int32), ("device_loop", ctypes.c_int32)]
 
     def as_dict(self):
         return dict(max_rows=self.max_rows, min_rows=self.min_rows, target_waves=self.target_waves,
                     nested_min_nodes=self.nested_min_nodes, fused_bottom=self.fused_bottom, step_ms=self.step_ms,
-                    pack_samples=self.pack_samples)
+                    pack_samples=self.pack_samples, device_loop=self.device_loop)
 
 
 def mlmc_autotune(ctx, levels, counts, reps=2):
@@ -316,8 +316,9 @@ def mlmc_get_tuning(ctx):
     return out.as_dict()
 
 
-def mlmc_set_tuning(ctx, max_rows, min_rows, target_waves, nested_min_nodes, fused_bottom=1, pack_samples=1):
-    t = mlmc_tuning(max_rows, min_rows, target_waves, nested_min_nodes, fused_bottom, 0.0, pack_samples)
+def mlmc_set_tuning(ctx, max_rows, min_rows, target_waves, nested_min_nodes, fused_bottom=1, pack_samples=1,
+                    device_loop=0):
+    t = mlmc_tuning(max_rows, min_rows, target_waves, nested_min_nodes, fused_bottom, 0.0, pack_samples, device_loop)
     return _check(ctx, lib().mlmc_set_tuning(ctx, ctypes.byref(t)))
 
 

@@ -820,6 +820,7 @@ mlmc_status mlmc_get_tuning(mlmc_ctx* h, mlmc_tuning* out) {
   out->nested_min_nodes = c.nested_min_nodes;
   out->fused_bottom = c.fused_bottom;
   out->pack_samples = c.pack_samples ? 1 : 0;
+  out->device_loop = c.device_loop ? 1 : 0;
   out->step_ms = 0.0;
   return MLMC_OK;
 }
@@ -829,10 +830,12 @@ mlmc_status mlmc_set_tuning(mlmc_ctx* h, const mlmc_tuning* t) {
   Context& c = h->c;
   if (t->max_rows < 1 || t->max_rows > 64 || t->min_rows < 1 || t->min_rows > t->max_rows ||
       !(t->target_waves >= 0.0 && t->target_waves <= 64.0) || t->nested_min_nodes < 0 ||
-      t->fused_bottom < 0 || t->fused_bottom > 2 || (t->pack_samples != 0 && t->pack_samples != 1))
+      t->fused_bottom < 0 || t->fused_bottom > 2 || (t->pack_samples != 0 && t->pack_samples != 1) ||
+      (t->device_loop != 0 && t->device_loop != 1))
     return c.fail(MLMC_ERR_INVALID_ARG, "tuning value out of range");
   c.fused_bottom = t->fused_bottom;
   c.pack_samples = t->pack_samples != 0;
+  c.device_loop = t->device_loop != 0;
   c.max_rows = t->max_rows;
   c.min_rows = t->min_rows;
   c.target_waves = t->target_waves;

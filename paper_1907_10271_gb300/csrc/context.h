@@ -128,6 +128,7 @@ struct Context {
   double floor_tol32 = 3e-6;      // tightest inner relative tolerance of the FP32 solve
   int check_every = 4;            // PCG iterations between host convergence checks
   bool graphs = true;             // replay PCG batches from a CUDA graph captured per solve
+  bool device_loop = false;       // with graphs: repeat the batches on the device (conditional node)
   int64_t nested_min_nodes = int64_t(1) << 22;   // finest-mesh nodes per call for nested iteration
   // launch shapes of the strip kernels (mlmc_autotune): row chunks of at most max_rows
   // rows; launches of fewer warps than target_waves resident waves split their chunks

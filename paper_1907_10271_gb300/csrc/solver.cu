@@ -144,6 +144,24 @@ ViewList<T> empty_list(const Context& ctx) {
 
 }  // namespace
 
+namespace {
+
+// Condition of the device-side batch loop: one more replay while samples are active and
+// fewer than max_reps replays have run.
+__global__ void k_loop_condition(cudaGraphConditionalHandle h, const int* __restrict__ count, int* reps,
+                                 int max_reps) {
+  const int r = ++(*reps);
+  cudaGraphSetConditional(h, (*count > 0 && r < max_reps) ? 1u : 0u);
+}
+
+cudaError_t launch_loop_condition(cudaGraphConditionalHandle h, const int* count, int* reps, int max_reps,
+                                  cudaStream_t st) {
+  k_loop_condition<<<1, 1, 0, st>>>(h, count, reps, max_reps);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 template <typename T>
 mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   cudaStream_t st = ctx.stream;
@@ -248,7 +266,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     alloc.template vec<int>(S.rpar, total);
     alloc.template vec<int>(S.exact, total);
     alloc.template vec<unsigned>(S.arrive, total);
-    alloc.template vec<int>(outer_count, 1);
+    alloc.template vec<int>(outer_count, 2);   // [0] refinement count, [1] device-loop replays
   };
   SizeAlloc sz;
   plan(sz);
@@ -266,7 +284,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   S.slot = 0;
   {
     char* state_begin = reinterpret_cast<char*>(S.alpha);
-    char* state_end = reinterpret_cast<char*>(outer_count + 1);
+    char* state_end = reinterpret_cast<char*>(outer_count + 2);
     if ((e = cudaMemsetAsync(state_begin, 0, (size_t)(state_end - state_begin), st)) != cudaSuccess)
       return ctx.cuda_fail(e, "memset");
   }
@@ -678,6 +696,59 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
     return MLMC_OK;
   };
 
+  // The replays of the batch and the convergence test run on the device: a conditional
+  // WHILE node repeats the batch while samples are active, at most max_iter / check_every
+  // times (its condition kernel counts the replays), so an inner solve is one graph
+  // launch and one host read instead of a host round trip per batch. A remainder of
+  // fewer than check_every iterations, or a capped solve, continues in the loop below.
+  cudaGraphExec_t loop_graph = nullptr;
+  GraphGuard loop_guard{&loop_graph};
+  int64_t loop_launches = 0;
+  const int loop_reps = ctx.check_every > 0 ? max_iter / ctx.check_every : 0;
+  auto build_loop = [&]() -> mlmc_status {
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaGraphCreate(&g, 0);
+    if (ce != cudaSuccess) return ctx.cuda_fail(ce, "loop graph");
+    struct Destroy {
+      cudaGraph_t* g;
+      ~Destroy() {
+        if (*g) cudaGraphDestroy(*g);
+      }
+    } destroy{&g};
+    cudaGraphConditionalHandle h;
+    if ((ce = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+      return ctx.cuda_fail(ce, "loop graph");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    if ((ce = cudaGraphAddNode(&cn, g, nullptr, nullptr, 0, &cp)) != cudaSuccess) return ctx.cuda_fail(ce, "loop graph");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((ce = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+      return ctx.cuda_fail(ce, "loop capture");
+    const int64_t l0 = ctx.timer.launches;
+    mlmc_status cs = MLMC_OK;
+    ce = cudaMemsetAsync(S.count, 0, sizeof(int) * ctx.check_every, st);
+    for (int b = 0; b < ctx.check_every && cs == MLMC_OK && ce == cudaSuccess; ++b) cs = run_vcycle_and_pcg(b & 1, b);
+    if (cs == MLMC_OK && ce == cudaSuccess)
+      ce = launch_loop_condition(h, S.count + (ctx.check_every - 1), outer_count + 1, loop_reps, st);
+    const cudaError_t ee = cudaStreamEndCapture(st, &body);
+    loop_launches = ctx.timer.launches - l0 + 1;   // the batch and the condition kernel
+    ctx.timer.launches = l0;
+    if (cs != MLMC_OK || ce != cudaSuccess || ee != cudaSuccess) {
+      cudaGetLastError();
+      return cs != MLMC_OK ? cs : ctx.cuda_fail(ce != cudaSuccess ? ce : ee, "loop capture");
+    }
+    if ((ce = cudaGraphInstantiate(&loop_graph, g, 0)) != cudaSuccess) {
+      loop_graph = nullptr;
+      return ctx.cuda_fail(ce, "loop instantiate");
+    }
+    return MLMC_OK;
+  };
+
   const double floor_tol = inner_double ? 1e-14 : ctx.floor_tol32;
   int outer = 0, max_it_seen = 0;
   for (;; ++outer) {
@@ -711,7 +782,25 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         return ctx.cuda_fail(e, "memset");
     }
     int it = 0;
-    while (it < max_iter) {
+    bool done_on_device = false;
+    if (graphs && ctx.device_loop && loop_reps > 0) {
+      if (!loop_graph) {
+        const mlmc_status cs = build_loop();
+        if (cs != MLMC_OK) return cs;
+      }
+      int h_loop[2] = {0, 0};
+      if ((e = cudaMemsetAsync(outer_count + 1, 0, sizeof(int), st)) != cudaSuccess ||
+          (e = cudaGraphLaunch(loop_graph, st)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(&h_loop[0], S.count + (ctx.check_every - 1), sizeof(int), cudaMemcpyDeviceToHost,
+                               st)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(&h_loop[1], outer_count + 1, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return ctx.cuda_fail(e, "device loop");
+      it = h_loop[1] * ctx.check_every;   // even: the host loop's buffer parity continues
+      ctx.timer.launches += loop_launches * h_loop[1];
+      done_on_device = h_loop[0] == 0;
+    }
+    while (!done_on_device && it < max_iter) {
       const int batch = std::min(ctx.check_every, max_iter - it);
       if (graphs && batch == ctx.check_every) {
         if (!batch_graph) {

@@ -396,3 +396,35 @@ def test_packed_strips_match_one_sample_per_strip(B, nested_min_nodes):
             B.mlmc_destroy(ctx)
     np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-6)
     np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-6, atol=0)
+
+
+def test_device_loop_matches_host_loop(B):
+    """With CUDA graphs (a non-legacy stream), repeating the PCG batches and their
+    convergence test on the device (tuning device_loop = 1: a conditional graph node)
+    takes the same batches as the host loop and gives the same quantities, for the
+    lock-stepped and the nested paths."""
+    import torch
+    w = STRIP_MIXED_5LEVEL
+    stream = torch.cuda.Stream()
+    for nested in (0, 1 << 40):
+        out = {}
+        with torch.cuda.stream(stream):
+            for dl in (1, 0):
+                ctx = B.mlmc_create(B.config_from_workload(w), stream.cuda_stream)
+                try:
+                    t = B.mlmc_get_tuning(ctx)
+                    B.mlmc_set_tuning(ctx, t["max_rows"], t["min_rows"], t["target_waves"], nested, t["fused_bottom"],
+                                      t["pack_samples"], dl)
+                    assert B.mlmc_get_tuning(ctx)["device_loop"] == dl
+                    counts = [64, 32, 16, 4, 2]
+                    tot = sum(counts)
+                    qf, qc = np.zeros(2 * tot), np.zeros(2 * tot)
+                    st = np.ones(tot, dtype=np.int32)
+                    B.mlmc_sample_levels(ctx, [0, 1, 2, 3, 4], [11] * 5, counts, qf, qc, st)
+                    stream.synchronize()
+                    assert np.all(st == 0)
+                    out[dl] = (qf, qc)
+                finally:
+                    B.mlmc_destroy(ctx)
+        np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-9)
+        np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-9, atol=0)
