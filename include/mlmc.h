@@ -159,16 +159,31 @@ typedef struct {
                                  results. 0 (default): host loop (measured 0.9 % faster on the
                                  5-level workload: a replay of the conditional node costs
                                  about what the host round trip did) */
+  int32_t wide_strips;        /* bit mask (MLMC_WIDE_*) of the mixed path's strip kernels that
+                                 hold a node pair per lane (60 output columns per warp strip,
+                                 the smoother's node pairs in one thread, samples side by side
+                                 at any mesh width when pack_samples is 1) instead of one node
+                                 column (28 or 30 output columns per strip). Same operations;
+                                 dot products summed in another order. Default: the two
+                                 post-smoothing kernels (MLMC_WIDE_POST | MLMC_WIDE_POST_TOP) */
 } mlmc_tuning;
+
+/* Bits of mlmc_tuning.wide_strips, one per strip kernel of the V-cycle-preconditioned CG */
+#define MLMC_WIDE_PRE_TOP 1    /* CG update and pre-smoothing on the solve mesh */
+#define MLMC_WIDE_PRE 2        /* restriction and pre-smoothing on a coarse mesh */
+#define MLMC_WIDE_POST 4       /* prolongation and post-smoothing on a coarse mesh */
+#define MLMC_WIDE_POST_TOP 8   /* prolongation and post-smoothing on the solve mesh, b . z */
+#define MLMC_WIDE_SEARCH 16    /* search direction p = z + beta p and q = K p */
+#define MLMC_WIDE_ALL 31
 
 /* Times the level-pair workload {levels[k], counts[k]} (host arrays of n_req entries,
    as for mlmc_sample_levels, on sample ids far from any the caller uses) under
    candidate launch shapes and nested-iteration settings, by coordinate descent
-   (nested iteration on / off, fused multigrid bottom 2 / 1 / 0, target_waves 0.75 /
-   1.5 / 3, max_rows 32 / 64, min_rows 4 / 6 / 8; one warm-up and `reps` timed calls
-   each, the median kept; the current values are timed first and a candidate replaces
-   them only when more than 1 % faster), and keeps
-   the fastest on the context. The level moments are left as they were. out
+   (nested iteration on / off, fused multigrid bottom 2 / 1 / 0, each bit of wide_strips
+   flipped, target_waves 0.75 / 1.5 / 3, max_rows 32 / 64, min_rows 4 / 6 / 8; one warm-up
+   and `reps` timed calls each, the median kept; the current values are timed first and
+   a candidate replaces them only when more than 1 % faster), and keeps the fastest on
+   the context. The level moments are left as they were. out
    (nullable) receives the chosen values. Errors as mlmc_sample_levels. */
 mlmc_status mlmc_autotune(mlmc_ctx* ctx, int32_t n_req, const int32_t* levels, const int64_t* counts, int32_t reps,
                           mlmc_tuning* out);

@@ -143,6 +143,9 @@ struct Context {
   int fused_bottom = 1;
   // strip kernels tile the samples of a view side by side (see View::packed)
   bool pack_samples = true;
+  // FP32 strip kernels with a node pair per lane (strip_wide.cu), bit mask over
+  // wide_strip_bit(op) (mlmc_tuning.wide_strips)
+  int wide_strips = MLMC_WIDE_POST | MLMC_WIDE_POST_TOP;
   int last_outer = 0;             // refinement steps of the last solve (diagnostic)
   int last_iters = 0;             // max PCG iterations of the last solve (diagnostic)
 

@@ -51,6 +51,7 @@ template <typename T>
 struct ViewList {
   int n;
   int prof_op;      // ProfOp of the launch (node counting when SampleState::units is set)
+  int wide;         // laid out for the node-pair strip kernels (launch_strip_wide)
   Invariants U;
   View<T> v[kMaxViews];
 };
@@ -87,6 +88,14 @@ enum class StripOp { Apply, PreTop, PreR, Post, PostTop, PcgP };
 
 // Output node columns per warp strip of a strip kernel (sets the views' tiles_x).
 int strip_cols(StripOp op);
+
+// The FP32 smoothing and PCG strip kernels with a node pair per lane (strip_wide.cu):
+// kWideCols output node columns per warp strip, views packed at any sample width, every
+// view's nx even. Same operand conventions as launch_strip.
+constexpr int kWideCols = 60;
+// bit of op in the node-pair mask (mlmc_tuning.wide_strips); -1: no node-pair kernel
+int wide_strip_bit(StripOp op);
+cudaError_t launch_strip_wide(StripOp op, const ViewList<float>& L, SampleState S, int total_warps, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_strip(StripOp op, const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st);

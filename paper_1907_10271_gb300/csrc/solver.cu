@@ -71,12 +71,21 @@ View<T> base_view(const GroupBuf<T>& g, int k) {
 // kernel (warps); returns the total. A mesh's node rows are cut into chunks of equal
 // height, at most ctx.max_rows (each chunk costs one extra element row and a pipeline
 // fill). A warp walks its rows one after another, so a launch of fewer warps than
-// ctx.target_waves waves (152 SMs x 28 resident warps each) is bound by that walk: its
-// views are cut into 2, 4 or 8 times as many chunks (at least ctx.min_rows rows each),
-// which shortens every warp's walk. mlmc_autotune picks the three parameters.
+// ctx.target_waves waves (152 SMs x 28 resident warps each, 16 for the node-pair
+// kernels) is bound by that walk: its views are cut into 2, 4 or 8 times as many chunks
+// (at least ctx.min_rows rows each), which shortens every warp's walk. mlmc_autotune
+// picks the three parameters.
+// Where ctx.wide_strips has op's bit the FP32 kernel holds a node pair per lane
+// (launch_strip_wide: 60 output columns per strip, views packed at any sample width);
+// that needs an even nx on every view, which every level above a hierarchy's coarsest has.
 template <typename T>
 int finalize_warps(const Context& ctx, ViewList<T>& L, StripOp op) {
-  const int target_warps = (int)(152 * 28 * ctx.target_waves);
+  const int bit = wide_strip_bit(op);
+  bool wide = std::is_same<T, float>::value && bit >= 0 && ((ctx.wide_strips >> bit) & 1);
+  for (int i = 0; i < L.n && wide; ++i) wide = L.v[i].g.nx % 2 == 0;
+  L.wide = wide ? 1 : 0;
+  // resident warps per SM: 28 of the one-column kernels, 16 of the node-pair kernels
+  const int target_warps = (int)(152 * (wide ? 16 : 28) * ctx.target_waves);
   const int min_rows = std::max(1, ctx.min_rows);
   const int max_rows = std::min(64, std::max(min_rows, ctx.max_rows));
   auto layout = [&](int split) {
@@ -90,9 +99,9 @@ int finalize_warps(const Context& ctx, ViewList<T>& L, StripOp op) {
       v.tiles_y = chunks_of(v.g.ny, v.rows);
       // samples side by side when a sample's width fills at least one strip (then a
       // warp's outputs span at most two samples)
-      const int cols = strip_cols(op);
+      const int cols = wide ? kWideCols : strip_cols(op);
       v.vw = v.g.nx + 2;
-      v.packed = ctx.pack_samples && v.vw >= cols ? 1 : 0;
+      v.packed = ctx.pack_samples && (wide || v.vw >= cols) ? 1 : 0;
       if (v.packed) {
         v.tiles_x = (int)(((int64_t)v.nsamp * v.vw + cols - 1) / cols);
         v.nwork = v.tiles_x * v.tiles_y;
@@ -108,6 +117,15 @@ int finalize_warps(const Context& ctx, ViewList<T>& L, StripOp op) {
   int split = 1, acc = layout(1);
   while (acc < target_warps && split < 8) acc = layout(split *= 2);
   return acc;
+}
+
+// A strip launch laid out by finalize_warps: the node-pair kernels when it chose them.
+template <typename T>
+cudaError_t strip_dispatch(StripOp op, const ViewList<T>& L, SampleState S, int total_warps, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.wide) return launch_strip_wide(op, L, S, total_warps, st);
+  }
+  return launch_strip<T>(op, L, S, total_warps, st);
 }
 
 template <typename T>
@@ -418,10 +436,10 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
       const int tw = finalize_warps(ctx, Lsm, d == 0 ? StripOp::PreTop : StripOp::PreR);
       if (d == 0) {
         Lsm.prof_op = kProfPreTop;
-        MLMC_LAUNCH(kProfPreTop, "pre_top", launch_strip<T>(StripOp::PreTop, Lsm, S, tw, st));
+        MLMC_LAUNCH(kProfPreTop, "pre_top", strip_dispatch<T>(StripOp::PreTop, Lsm, S, tw, st));
       } else {
         Lsm.prof_op = kProfPre;
-        MLMC_LAUNCH(kProfPre, "pre", launch_strip<T>(StripOp::PreR, Lsm, S, tw, st));
+        MLMC_LAUNCH(kProfPre, "pre", strip_dispatch<T>(StripOp::PreR, Lsm, S, tw, st));
       }
     }
     // every group's bottom: levels nl-4 .. nl-2 and the coarsest in one launch (a block
@@ -524,17 +542,17 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         L.prof_op = kProfPostTop;
         SampleState Ss = S;
         Ss.slot = slot;
-        MLMC_LAUNCH(kProfPostTop, "post_top", launch_strip<T>(StripOp::PostTop, L, Ss, tw, st));
+        MLMC_LAUNCH(kProfPostTop, "post_top", strip_dispatch<T>(StripOp::PostTop, L, Ss, tw, st));
       } else {
         L.prof_op = kProfPost;
-        MLMC_LAUNCH(kProfPost, "post", launch_strip<T>(StripOp::Post, L, S, tw, st));
+        MLMC_LAUNCH(kProfPost, "post", strip_dispatch<T>(StripOp::Post, L, S, tw, st));
       }
     }
     {   // its last warp per sample also forms alpha
       ViewList<T> L = top_list(StripOp::PcgP, parity);
       const int tw = finalize_warps(ctx, L, StripOp::PcgP);
       L.prof_op = kProfPcgP;
-      MLMC_LAUNCH(kProfPcgP, "pcg_p", launch_strip<T>(StripOp::PcgP, L, S, tw, st));
+      MLMC_LAUNCH(kProfPcgP, "pcg_p", strip_dispatch<T>(StripOp::PcgP, L, S, tw, st));
     }
     return MLMC_OK;
   };

@@ -428,3 +428,32 @@ def test_device_loop_matches_host_loop(B):
                     B.mlmc_destroy(ctx)
         np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-9)
         np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-9, atol=0)
+
+
+@pytest.mark.parametrize("nested_min_nodes", [0, 1 << 40])
+def test_wide_strips_match_one_column_strips(B, nested_min_nodes):
+    """The node-pair strip kernels (bits of tuning wide_strips: a lane holds columns 2l
+    and 2l + 1, 60 output columns per strip) do the operations of the one-column
+    kernels: the solves agree to rounding (the dot products are summed in another
+    order), checked at the stated 1e-6, with every kernel in pairs, with the default
+    mask, with samples side by side at every mesh width and with one sample per strip.
+    13 samples of every level, so that strips straddle samples."""
+    w = STRIP_MIXED_5LEVEL
+    out = {}
+    keys = ((B.MLMC_WIDE_ALL, 1), (B.MLMC_WIDE_ALL, 0), (B.MLMC_WIDE_POST | B.MLMC_WIDE_POST_TOP, 1))
+    for wide, pack in ((0, 1),) + keys:
+        ctx = B.mlmc_create(B.config_from_workload(w))
+        try:
+            B.mlmc_set_tuning(ctx, 64, 6, 1.5, nested_min_nodes, 1, pack, 0, wide)
+            assert B.mlmc_get_tuning(ctx)["wide_strips"] == wide
+            n = 13
+            qf, qc = np.zeros(2 * 5 * n), np.zeros(2 * 5 * n)
+            st = np.ones(5 * n, dtype=np.int32)
+            B.mlmc_sample_levels(ctx, [0, 1, 2, 3, 4], [7] * 5, [n] * 5, qf, qc, st)
+            assert np.all(st == 0)
+            out[(wide, pack)] = (qf, qc)
+        finally:
+            B.mlmc_destroy(ctx)
+    for key in keys:
+        np.testing.assert_allclose(out[key][0], out[(0, 1)][0], rtol=1e-6)
+        np.testing.assert_allclose(out[key][1], out[(0, 1)][1], rtol=1e-6, atol=0)
