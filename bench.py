@@ -89,6 +89,8 @@ def parse():
                     help="skip the panel-buckling measurement")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default launch shapes instead of running mlmc_autotune first")
+    ap.add_argument("--wide-mask", type=int, default=None,
+                    help="--case small: node-pair strip kernel mask (mlmc_tuning.wide_strips, 0 .. 31)")
     ap.add_argument("--cpu-fraction", type=float, default=1.0 / 32.0,
                     help="fraction of each level's samples the CPU oracle times")
     return ap.parse_args()
@@ -109,7 +111,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fem.cu", "common.cuh", "fem.cuh"):
+    for f in ("fem.cu", "common.cuh", "fem.cuh", "strip.cuh", "strip_wide.cu"):
         with open(os.path.join(ROOT, "paper_1907_10271_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -658,16 +660,21 @@ def drain_all_of(B, srv):
         res += got
 
 
-def run_small_case():
+def run_small_case(wide_mask=None):
     """One call of the workload with 1/4 of each level's samples, after one warm call:
     a short, bounded command for kernel captures (about 3 M nodes per nested-iteration
-    phase, above the L2 size in bytes; under 3 GB of device memory)."""
+    phase, above the L2 size in bytes; under 3 GB of device memory). wide_mask: the
+    node-pair kernel mask (mlmc_tuning.wide_strips) instead of the library's default."""
     import torch
     from paper_1907_10271_gb300 import binding as B
     cfg = STRIP_MIXED_5LEVEL
     counts = [n // 4 for n in cfg["n_per_level"]]
     total = sum(counts)
     ctx = B.mlmc_create(B.config_from_workload(cfg), torch.cuda.current_stream().cuda_stream)
+    if wide_mask is not None:
+        t = B.mlmc_get_tuning(ctx)
+        B.mlmc_set_tuning(ctx, t["max_rows"], t["min_rows"], t["target_waves"], t["nested_min_nodes"],
+                          t["fused_bottom"], t["pack_samples"], t["device_loop"], wide_mask)
     qf = torch.zeros(2 * total, dtype=torch.float64, device="cuda")
     qc = torch.zeros_like(qf)
     st = torch.zeros(total, dtype=torch.int32, device="cuda")
@@ -1224,7 +1231,7 @@ def main():
     a = parse()
     rank, _, world = dist_env()
     if a.case == "small":
-        run_small_case()
+        run_small_case(a.wide_mask)
         return
     if a.case == "hex3d":
         run_hex3d_case()

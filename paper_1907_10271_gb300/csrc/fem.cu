@@ -987,7 +987,7 @@ __global__ void k_trig_average(const __grid_constant__ ViewList<T> L) {
   const View<T>& V = L.v[vi];
   const int nx = V.g.nx, ny = V.g.ny, nxc = nx / 2, nyc = ny / 2;
   const int per = nxc * nyc;
-  const int s = (int)(loc / per);
+  const int s = (int)loc / per;   // launch totals are int: loc < 2^31
   if (s >= V.nsamp) return;
   const int e = (int)(loc - (int64_t)s * per);
   const int J = e / nxc, I = e - J * nxc;
@@ -1032,7 +1032,7 @@ __global__ void k_invdiag(const __grid_constant__ ViewList<T> L) {
   const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
   const int pairs = nx / 2 + 1;   // nx is even on every multigrid level
   const int per = pairs * (ny + 1);
-  const int s = (int)(loc / per);
+  const int s = (int)loc / per;   // launch totals are int: loc < 2^31
   if (s >= V.nsamp) return;
   const int r = (int)(loc - (int64_t)s * per);
   const int j = r / pairs, m = r - j * pairs;
@@ -1523,7 +1523,7 @@ __global__ void k_update_d(const __grid_constant__ ViewList<T> L, SampleState S)
   if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
   const View<T>& V = L.v[vi];
   const int64_t per = 2 * (int64_t)(V.g.nx + 1) * (V.g.ny + 1);
-  const int s = (int)(loc / per);
+  const int s = per > INT32_MAX ? 0 : (int)loc / (int)per;   // launch totals are int: loc < 2^31
   const int t = V.sbase + s;
   if (s >= V.nsamp || !S.outer_active[t]) return;
   DStore<T>::add(static_cast<double*>(V.ext1), loc, V.a[loc]);
@@ -1546,7 +1546,7 @@ __global__ void k_lift_resid(const __grid_constant__ ViewList<T> L, SampleState 
   const View<T>& V = L.v[vi];
   const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
   const int per = 2 * (ny + 1);
-  const int s = (int)(loc / per);
+  const int s = (int)loc / per;   // launch totals are int: loc < 2^31
   if (s >= V.nsamp) return;
   const int k = (int)(loc - (int64_t)s * per);
   const int j = k >> 1, c = k & 1, i = nx - 1 + c;
@@ -1593,7 +1593,7 @@ __global__ void k_prolong_d(const __grid_constant__ ViewList<TI> L) {
   const View<TI>& V = L.v[vi];
   const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
   const int per = nxp * (ny + 1);
-  const int s = (int)(loc / per);
+  const int s = (int)loc / per;   // launch totals are int: loc < 2^31
   if (s >= V.nsamp) return;
   const int node = (int)(loc - (int64_t)s * per);
   const int j = node / nxp, i = node - j * nxp;
@@ -1637,7 +1637,7 @@ __global__ void k_stress(const __grid_constant__ ViewList<double> L, SampleState
   if (!find_point(L, gw, vi, loc)) return;
   const View<double>& V = L.v[vi];
   const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
-  const int s = (int)(loc / ny);
+  const int s = (int)loc / ny;   // launch totals are int: loc < 2^31
   if (s >= V.nsamp) return;
   const int j = (int)(loc - (int64_t)s * ny);
   const int t = V.sbase + s;
@@ -1679,7 +1679,7 @@ __global__ void k_react_delta(const __grid_constant__ ViewList<T> L, SampleState
   if (!find_point(L, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, vi, loc)) return;
   const View<T>& V = L.v[vi];
   const int nx = V.g.nx, ny = V.g.ny, nxp = nx + 1;
-  const int s = (int)(loc / ny);
+  const int s = (int)loc / ny;   // launch totals are int: loc < 2^31
   if (s >= V.nsamp) return;
   const int t = V.sbase + s;
   if (!S.outer_active[t]) return;
@@ -1713,7 +1713,7 @@ __global__ void k_react_energy(const __grid_constant__ ViewList<T> L, SampleStat
   if (!find_point(L, gw, vi, loc)) return;
   const View<T>& V = L.v[vi];
   const int rows = V.g.ny + 1;
-  const int s = (int)(loc / rows);
+  const int s = (int)loc / rows;   // launch totals are int: loc < 2^31
   if (s >= V.nsamp) return;
   const int t = V.sbase + s;
   if (S.status[t] != 0) return;
