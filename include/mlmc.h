@@ -166,6 +166,15 @@ typedef struct {
                                  column (28 or 30 output columns per strip). Same operations;
                                  dot products summed in another order. Default: the two
                                  post-smoothing kernels (MLMC_WIDE_POST | MLMC_WIDE_POST_TOP) */
+  double omega;               /* damping of the pair-block Jacobi smoother, in (0, 1). The
+                                 V-cycle preconditioner is SPD for omega < 2 / lambda_max(B^-1 K)
+                                 (B the smoother's block diagonal): 1/2 for every angle field
+                                 (lambda_max <= 4), up to about 0.7 for fields near the fibre
+                                 axis (lambda_max about 2.75 at 0 degrees, 3.2 at 45, 3.8 at 60).
+                                 A call in which some sample does not converge at omega > 1/2 is
+                                 solved again at 1/2, so results never depend on it. Default 0.6 */
+  int64_t omega_retries;      /* (get only) solves done again at omega = 1/2 since the context
+                                 was created */
 } mlmc_tuning;
 
 /* Bits of mlmc_tuning.wide_strips, one per strip kernel of the V-cycle-preconditioned CG */
@@ -179,8 +188,8 @@ typedef struct {
 /* Times the level-pair workload {levels[k], counts[k]} (host arrays of n_req entries,
    as for mlmc_sample_levels, on sample ids far from any the caller uses) under
    candidate launch shapes and nested-iteration settings, by coordinate descent
-   (nested iteration on / off, fused multigrid bottom 2 / 1 / 0, each bit of wide_strips
-   flipped, target_waves 0.75 / 1.5 / 3, max_rows 32 / 64, min_rows 4 / 6 / 8; one warm-up
+   (nested iteration on / off, fused multigrid bottom 2 / 1 / 0, smoother damping 0.5 /
+   0.6 / 0.65, each bit of wide_strips flipped, target_waves 0.75 / 1.5 / 3, max_rows 32 / 64, min_rows 4 / 6 / 8; one warm-up
    and `reps` timed calls each, the median kept; the current values are timed first and
    a candidate replaces them only when more than 1 % faster), and keeps the fastest on
    the context. The level moments are left as they were. out

@@ -299,12 +299,14 @@ MLMC_WIDE_ALL = 31
 class mlmc_tuning(ctypes.Structure):
     _fields_ = [("max_rows", ctypes.c_int32), ("min_rows", ctypes.c_int32), ("target_waves", ctypes.c_double),
                 ("nested_min_nodes", ctypes.c_int64), ("fused_bottom", ctypes.c_int32), ("step_ms", ctypes.c_double),
-                ("pack_samples", ctypes.c_int32), ("device_loop", ctypes.c_int32), ("wide_strips", ctypes.c_int32)]
+                ("pack_samples", ctypes.c_int32), ("device_loop", ctypes.c_int32), ("wide_strips", ctypes.c_int32),
+                ("omega", ctypes.c_double), ("omega_retries", ctypes.c_int64)]
 
     def as_dict(self):
         return dict(max_rows=self.max_rows, min_rows=self.min_rows, target_waves=self.target_waves,
                     nested_min_nodes=self.nested_min_nodes, fused_bottom=self.fused_bottom, step_ms=self.step_ms,
-                    pack_samples=self.pack_samples, device_loop=self.device_loop, wide_strips=self.wide_strips)
+                    pack_samples=self.pack_samples, device_loop=self.device_loop, wide_strips=self.wide_strips,
+                    omega=self.omega, omega_retries=self.omega_retries)
 
 
 def mlmc_autotune(ctx, levels, counts, reps=2):
@@ -322,12 +324,15 @@ def mlmc_get_tuning(ctx):
 
 
 def mlmc_set_tuning(ctx, max_rows, min_rows, target_waves, nested_min_nodes, fused_bottom=1, pack_samples=1,
-                    device_loop=0, wide_strips=None):
-    """wide_strips None keeps the context's current choice."""
+                    device_loop=0, wide_strips=None, omega=None):
+    """wide_strips, omega None keep the context's current values."""
+    cur = mlmc_get_tuning(ctx)
     if wide_strips is None:
-        wide_strips = mlmc_get_tuning(ctx)["wide_strips"]
+        wide_strips = cur["wide_strips"]
+    if omega is None:
+        omega = cur["omega"]
     t = mlmc_tuning(max_rows, min_rows, target_waves, nested_min_nodes, fused_bottom, 0.0, pack_samples, device_loop,
-                    wide_strips)
+                    wide_strips, omega, 0)
     return _check(ctx, lib().mlmc_set_tuning(ctx, ctypes.byref(t)))
 
 

@@ -822,6 +822,8 @@ mlmc_status mlmc_get_tuning(mlmc_ctx* h, mlmc_tuning* out) {
   out->pack_samples = c.pack_samples ? 1 : 0;
   out->device_loop = c.device_loop ? 1 : 0;
   out->wide_strips = c.wide_strips;
+  out->omega = c.omega;
+  out->omega_retries = c.omega_retries;
   out->step_ms = 0.0;
   return MLMC_OK;
 }
@@ -832,12 +834,14 @@ mlmc_status mlmc_set_tuning(mlmc_ctx* h, const mlmc_tuning* t) {
   if (t->max_rows < 1 || t->max_rows > 64 || t->min_rows < 1 || t->min_rows > t->max_rows ||
       !(t->target_waves >= 0.0 && t->target_waves <= 64.0) || t->nested_min_nodes < 0 ||
       t->fused_bottom < 0 || t->fused_bottom > 2 || (t->pack_samples != 0 && t->pack_samples != 1) ||
-      (t->device_loop != 0 && t->device_loop != 1) || t->wide_strips < 0 || t->wide_strips > MLMC_WIDE_ALL)
+      (t->device_loop != 0 && t->device_loop != 1) || t->wide_strips < 0 || t->wide_strips > MLMC_WIDE_ALL ||
+      !(t->omega > 0.0 && t->omega < 1.0))
     return c.fail(MLMC_ERR_INVALID_ARG, "tuning value out of range");
   c.fused_bottom = t->fused_bottom;
   c.pack_samples = t->pack_samples != 0;
   c.device_loop = t->device_loop != 0;
   c.wide_strips = t->wide_strips;
+  c.omega = t->omega;
   c.max_rows = t->max_rows;
   c.min_rows = t->min_rows;
   c.target_waves = t->target_waves;
@@ -878,8 +882,9 @@ mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, con
     int max_rows, min_rows;
     int fused;
     int wide;
+    double omega;
   };
-  Cand best{c.nested_min_nodes, c.target_waves, c.max_rows, c.min_rows, c.fused_bottom, c.wide_strips};
+  Cand best{c.nested_min_nodes, c.target_waves, c.max_rows, c.min_rows, c.fused_bottom, c.wide_strips, c.omega};
   double best_ms = 1e300;
   mlmc_status s = MLMC_OK;
   auto measure = [&](const Cand& k, double& ms) -> mlmc_status {
@@ -889,6 +894,7 @@ mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, con
     c.min_rows = k.min_rows;
     c.fused_bottom = k.fused;
     c.wide_strips = k.wide;
+    c.omega = k.omega;
     std::vector<double> t;
     for (int r = 0; r <= reps; ++r) {
       cudaEventRecord(e0, c.stream);
@@ -920,21 +926,22 @@ mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, con
   const double wave_vals[3] = {0.75, 1.5, 3.0};
   const int max_vals[2] = {32, 64}, min_vals[3] = {4, 6, 8};
   s = consider(best);
-  for (int64_t v : nested_vals)
-    if (s == MLMC_OK) s = consider(Cand{v, best.waves, best.max_rows, best.min_rows, best.fused, best.wide});
-  for (int v : {1, 2, 0})
-    if (s == MLMC_OK) s = consider(Cand{best.nested, best.waves, best.max_rows, best.min_rows, v, best.wide});
-  for (int b = 0; b < 5; ++b)   // each node-pair kernel on / off
-    if (s == MLMC_OK)
-      s = consider(Cand{best.nested, best.waves, best.max_rows, best.min_rows, best.fused, best.wide ^ (1 << b)});
-  for (double v : wave_vals)
-    if (s == MLMC_OK) s = consider(Cand{best.nested, v, best.max_rows, best.min_rows, best.fused, best.wide});
+  auto with = [&](auto&& edit) {   // best with one coordinate changed
+    Cand k = best;
+    edit(k);
+    if (s == MLMC_OK) s = consider(k);
+  };
+  for (int64_t v : nested_vals) with([&](Cand& k) { k.nested = v; });
+  for (int v : {1, 2, 0}) with([&](Cand& k) { k.fused = v; });
+  for (double v : {0.5, 0.6, 0.65}) with([&](Cand& k) { k.omega = v; });   // smoother damping (solve_groups)
+  for (int b = 0; b < 5; ++b) with([&](Cand& k) { k.wide ^= 1 << b; });    // each node-pair kernel on / off
+  for (double v : wave_vals) with([&](Cand& k) { k.waves = v; });
   for (int v : max_vals)
-    if (s == MLMC_OK)
-      s = consider(Cand{best.nested, best.waves, v, std::min(best.min_rows, v), best.fused, best.wide});
-  for (int v : min_vals)
-    if (s == MLMC_OK)
-      s = consider(Cand{best.nested, best.waves, best.max_rows, std::min(v, best.max_rows), best.fused, best.wide});
+    with([&](Cand& k) {
+      k.max_rows = v;
+      k.min_rows = std::min(k.min_rows, v);
+    });
+  for (int v : min_vals) with([&](Cand& k) { k.min_rows = std::min(v, k.max_rows); });
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c.nested_min_nodes = best.nested;
@@ -943,6 +950,7 @@ mlmc_status mlmc_autotune(mlmc_ctx* h, int32_t n_req, const int32_t* levels, con
   c.min_rows = best.min_rows;
   c.fused_bottom = best.fused;
   c.wide_strips = best.wide;
+  c.omega = best.omega;
   if ((e = cudaMemcpyAsync(h->acc_dev, saved.data(), sizeof(mlmc::LevelAcc) * c.cfg.levels, cudaMemcpyHostToDevice,
                            c.stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(c.stream)) != cudaSuccess)

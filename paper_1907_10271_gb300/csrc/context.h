@@ -146,6 +146,10 @@ struct Context {
   // FP32 strip kernels with a node pair per lane (strip_wide.cu), bit mask over
   // wide_strip_bit(op) (mlmc_tuning.wide_strips)
   int wide_strips = MLMC_WIDE_POST | MLMC_WIDE_POST_TOP;
+  // damping of the pair-block Jacobi smoother (see solve_groups: calls that leave a
+  // sample unconverged at omega > kOmega are solved again at kOmega)
+  double omega = 0.6;
+  int64_t omega_retries = 0;
   int last_outer = 0;             // refinement steps of the last solve (diagnostic)
   int last_iters = 0;             // max PCG iterations of the last solve (diagnostic)
 

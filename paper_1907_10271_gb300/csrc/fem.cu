@@ -1065,7 +1065,7 @@ __global__ void k_invdiag(const __grid_constant__ ViewList<T> L) {
       if (c == 1) k += element_edge_uu<T>(C, rx, ry, w);
     }
   }
-  const T om = (T)kOmega;
+  const T om = V.param > 0 ? (T)V.param : (T)kOmega;
   const bool has_b = ib <= nx;
   const bool pair = has_b && !dir_u(ia, nx) && !dir_u(ib, nx);
   const T det = da.u * db.u - k * k;

@@ -180,8 +180,10 @@ cudaError_t launch_loop_condition(cudaGraphConditionalHandle h, const int* count
 
 }  // namespace
 
+// One solve of every group at the context's smoother damping; *failed (nullable) is
+// set when some sample ends without converging.
 template <typename T>
-mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
+mlmc_status solve_groups_once(Context& ctx, std::vector<SolveGroup<T>>& groups, bool* failed) {
   cudaStream_t st = ctx.stream;
   const bool inner_double = sizeof(T) == sizeof(double);
   if (groups.empty()) return MLMC_OK;
@@ -344,6 +346,7 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         View<T> v = base_view(g, k);
         v.o0 = g.winvd[k];
         v.o1 = g.wc[k];
+        v.param = ctx.omega;
         L.v[L.n++] = v;
         per.push_back((int64_t)(g.geo[k].nx / 2 + 1) * (g.geo[k].ny + 1));   // node pairs
       }
@@ -917,6 +920,8 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
         stv[t] = MLMC_ERR_NOT_CONVERGED;
         changed = true;
       }
+    if (failed)
+      for (int t = 0; t < total; ++t) *failed = *failed || stv[t] != 0;
     if (changed &&
         (e = cudaMemcpyAsync(S.status, stv.data(), sizeof(int) * total, cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return ctx.cuda_fail(e, "status");
@@ -967,6 +972,28 @@ mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
   }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return ctx.cuda_fail(e, "solve");
   return MLMC_OK;
+}
+
+// The V-cycle preconditioner is symmetric positive definite while the smoother's damping
+// stays below 2 / lambda_max(B^-1 K) (B the pair-block diagonal). kOmega = 1/2 keeps that
+// for every angle field (lambda_max <= 4 by the colouring bound); a larger ctx.omega
+// smooths better where lambda_max is smaller, which it is for fields near the fibre axis
+// (about 2.75 at 0 degrees). If a solve at such a damping leaves any sample
+// unconverged (an indefinite preconditioner shows as a breakdown or a stall), the whole
+// call is solved again at kOmega: its inputs (fields, nested-iteration starts) are
+// unchanged, and every output is overwritten.
+template <typename T>
+mlmc_status solve_groups(Context& ctx, std::vector<SolveGroup<T>>& groups) {
+  bool failed = false;
+  mlmc_status s = solve_groups_once(ctx, groups, ctx.omega > kOmega ? &failed : nullptr);
+  if (s == MLMC_OK && failed) {
+    const double om = ctx.omega;
+    ctx.omega = kOmega;
+    s = solve_groups_once<T>(ctx, groups, nullptr);
+    ctx.omega = om;
+    ++ctx.omega_retries;
+  }
+  return s;
 }
 
 template <typename T>

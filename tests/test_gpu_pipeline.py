@@ -457,3 +457,42 @@ def test_wide_strips_match_one_column_strips(B, nested_min_nodes):
     for key in keys:
         np.testing.assert_allclose(out[key][0], out[(0, 1)][0], rtol=1e-6)
         np.testing.assert_allclose(out[key][1], out[(0, 1)][1], rtol=1e-6, atol=0)
+
+
+def test_smoother_damping_and_its_retry(B):
+    """The smoother's damping changes the preconditioner, not the solution: solves at
+    omega = 0.65 (the V-cycle stays SPD while omega < 2 / lambda_max(B^-1 K), and
+    lambda_max is about 2.75 on these fields) agree with omega = 1/2 at the stated 1e-6.
+    A damping past that bound (0.95) makes the preconditioner indefinite: a call in
+    which a sample does not converge is solved again at 1/2, so every sample converges,
+    the results equal omega = 1/2's, and the retry counter moves."""
+    w = STRIP_MIXED_5LEVEL
+    counts = [8, 6, 4, 2]
+    out = {}
+    for om in (0.5, 0.65, 0.95):
+        ctx = B.mlmc_create(B.config_from_workload(w))
+        try:
+            t = B.mlmc_get_tuning(ctx)
+            assert t["omega"] == 0.6 and t["omega_retries"] == 0
+            B.mlmc_set_tuning(ctx, t["max_rows"], t["min_rows"], t["target_waves"], t["nested_min_nodes"],
+                              t["fused_bottom"], t["pack_samples"], 0, t["wide_strips"], om)
+            tot = sum(counts)
+            qf, qc = np.zeros(2 * tot), np.zeros(2 * tot)
+            st = np.ones(tot, dtype=np.int32)
+            B.mlmc_sample_levels(ctx, [0, 1, 2, 3], [3] * 4, counts, qf, qc, st)
+            assert np.all(st == 0)
+            t = B.mlmc_get_tuning(ctx)
+            assert t["omega"] == om
+            out[om] = (qf, qc, t["omega_retries"])
+        finally:
+            B.mlmc_destroy(ctx)
+    assert out[0.5][2] == 0 and out[0.65][2] == 0 and out[0.95][2] > 0
+    for om in (0.65, 0.95):
+        np.testing.assert_allclose(out[om][0], out[0.5][0], rtol=1e-6)
+        np.testing.assert_allclose(out[om][1], out[0.5][1], rtol=1e-6, atol=0)
+    with pytest.raises(B.MLMCError):
+        ctx = B.mlmc_create(B.config_from_workload(w))
+        try:
+            B.mlmc_set_tuning(ctx, 64, 6, 1.5, 0, omega=1.0)
+        finally:
+            B.mlmc_destroy(ctx)
