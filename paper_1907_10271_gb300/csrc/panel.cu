@@ -19,6 +19,7 @@ namespace mlmcp {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kPatchesPerWarp = 3;   // patches of one colour per warp in the patch sweep (27 of 32 lanes)
 
 // corner a of an element at offset (ox, oy) from its lower-left node
 __device__ __forceinline__ int corner_of(int ox, int oy) { return oy == 0 ? ox : 3 - ox; }
@@ -455,9 +456,11 @@ __global__ void __launch_bounds__(kThreads) k_patch_setup(PGrid g, const float* 
   }
 }
 
-// one warp per patch of colour (sx, sy): the residual at the patch's 9 nodes (lanes
-// 0..8, from `in`), the correction A_p^-1 r at its 27 slots (lanes 0..26; A_p^-1 is
-// symmetric, so lane l reads column l, coalesced), out = in + correction on the patch
+// kPatchesPerWarp consecutive patches of colour (sx, sy) per warp: the residual at each
+// patch's 9 nodes (lanes 9 t .. 9 t + 8 for the warp's patch t, from `in`), then each
+// patch's correction A_p^-1 r at its 27 slots (lanes 0..26 in turn; A_p^-1 is symmetric,
+// so lane l reads column l, coalesced), out = in + correction on the patch. The patches
+// of a colour tile the mesh, so every node is written.
 __global__ void __launch_bounds__(kThreads, 8) k_patch_color(PGrid g, const float* __restrict__ ke,
                                                           const float* __restrict__ pinv, const float4* __restrict__ b,
                                                           const float4* __restrict__ xin, float4* __restrict__ xout,
@@ -466,20 +469,24 @@ __global__ void __launch_bounds__(kThreads, 8) k_patch_color(PGrid g, const floa
   const int e = blockIdx.y, s = e >> g.cshift;
   if (active && !active[s]) return;
   __shared__ __align__(16) float K[144];
-  __shared__ float rs[kThreads / 32][32], ds[kThreads / 32][32];
+  __shared__ float rs[kThreads / 32][kPatchesPerWarp][kPatchDofs + 1], ds[kThreads / 32][kPatchesPerWarp][kPatchDofs + 1];
   for (int k = threadIdx.x; k < 144; k += blockDim.x) K[k] = ke[(size_t)s * 144 + k];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int fx = sx == 2 ? -1 : sx, fy = sy == 2 ? -1 : sy;   // first centres of the colour
   const int px_n = (g.nx + 1 - fx) / 3 + 1, py_n = (g.ny + 1 - fy) / 3 + 1;
-  const int pid = blockIdx.x * (kThreads / 32) + warp;
-  if (pid >= px_n * py_n) return;   // the whole warp
+  const int npatch = px_n * py_n;
+  const int pbase = (blockIdx.x * (kThreads / 32) + warp) * kPatchesPerWarp;
+  if (pbase >= npatch) return;   // the whole warp
+  // lanes 0 .. 26: node t % 9 of the warp's patch t / 9
+  const int t = lane / 9, nidx = lane - 9 * t;
+  const int pid = pbase + t;
+  const bool patch_ok = lane < 9 * kPatchesPerWarp && pid < npatch;
   const int ci = fx + 3 * (pid % px_n), cj = fy + 3 * (pid / px_n);
-  const int type = patch_case(ci, g.nx) + 7 * patch_case(cj, g.ny);
   const int np = g.nx + 1;
   const size_t o = (size_t)e * g.nodes();
-  const int li = ci + lane % 3 - 1, lj = cj + (lane / 3) % 3 - 1;   // node of lanes 0..8
-  const bool node_in = lane < 9 && li >= 0 && li <= g.nx && lj >= 0 && lj <= g.ny;
+  const int li = ci + nidx % 3 - 1, lj = cj + nidx / 3 - 1;
+  const bool node_in = patch_ok && li >= 0 && li <= g.nx && lj >= 0 && lj <= g.ny;
   float4 xo = make_float4(0.f, 0.f, 0.f, 0.f);
   if (node_in) {
     // K x rows of the node, one element at a time (a rolled loop keeps registers low)
@@ -506,25 +513,33 @@ __global__ void __launch_bounds__(kThreads, 8) k_patch_color(PGrid g, const floa
     const float4 bb = b[o + lj * np + li];
     const Free f = free_of(g, li, lj);
     if (xin) xo = xin[o + lj * np + li];
-    rs[warp][3 * lane] = f.w ? bb.x - kx.x : 0.f;
-    rs[warp][3 * lane + 1] = f.tx ? bb.y - kx.y : 0.f;
-    rs[warp][3 * lane + 2] = f.ty ? bb.z - kx.z : 0.f;
-  } else if (lane < 9) {
-    rs[warp][3 * lane] = rs[warp][3 * lane + 1] = rs[warp][3 * lane + 2] = 0.f;
+    rs[warp][t][3 * nidx] = f.w ? bb.x - kx.x : 0.f;
+    rs[warp][t][3 * nidx + 1] = f.tx ? bb.y - kx.y : 0.f;
+    rs[warp][t][3 * nidx + 2] = f.ty ? bb.z - kx.z : 0.f;
+  } else if (patch_ok) {
+    rs[warp][t][3 * nidx] = rs[warp][t][3 * nidx + 1] = rs[warp][t][3 * nidx + 2] = 0.f;
   }
   __syncwarp();
-  if (lane < kPatchDofs) {
-    const float* M = pinv + ((size_t)(pinv_per_sample ? s : 0) * kPatchTypes + type) * kPatchDofs * kPatchDofs;
-    float d = 0.f;
+  // the local solves: lane q forms DOF q of each patch's correction (the patches of a
+  // warp are neighbours along x and mostly of one type, so M comes from L1)
+#pragma unroll 1
+  for (int u = 0; u < kPatchesPerWarp; ++u) {
+    const int pu = pbase + u;
+    if (pu >= npatch) break;   // the same on every lane
+    if (lane < kPatchDofs) {
+      const int type = patch_case(fx + 3 * (pu % px_n), g.nx) + 7 * patch_case(fy + 3 * (pu / px_n), g.ny);
+      const float* M = pinv + ((size_t)(pinv_per_sample ? s : 0) * kPatchTypes + type) * kPatchDofs * kPatchDofs;
+      float d = 0.f;
 #pragma unroll 3
-    for (int q = 0; q < kPatchDofs; ++q) d += M[q * kPatchDofs + lane] * rs[warp][q];
-    ds[warp][lane] = d;
+      for (int q = 0; q < kPatchDofs; ++q) d += M[q * kPatchDofs + lane] * rs[warp][u][q];
+      ds[warp][u][lane] = d;
+    }
   }
   __syncwarp();
   if (node_in) {
     const Free f = free_of(g, li, lj);
-    xout[o + lj * np + li] = masked(f, make_float4(xo.x + ds[warp][3 * lane], xo.y + ds[warp][3 * lane + 1],
-                                                  xo.z + ds[warp][3 * lane + 2], 0.f));
+    xout[o + lj * np + li] = masked(f, make_float4(xo.x + ds[warp][t][3 * nidx], xo.y + ds[warp][t][3 * nidx + 1],
+                                                  xo.z + ds[warp][t][3 * nidx + 2], 0.f));
   }
 }
 
@@ -1087,9 +1102,9 @@ cudaError_t launch_patch_color(const PGrid& g, const float* ke, const float* pin
                                cudaStream_t st) {
   const int fx = sx == 2 ? -1 : sx, fy = sy == 2 ? -1 : sy;
   const int patches = ((g.nx + 1 - fx) / 3 + 1) * ((g.ny + 1 - fy) / 3 + 1);
-  const int warps = kThreads / 32;
-  k_patch_color<<<dim3((patches + warps - 1) / warps, g.nb), kThreads, 0, st>>>(g, ke, pinv, b, in, out, sx, sy,
-                                                                               pinv_per_sample ? 1 : 0, active);
+  const int per_block = kThreads / 32 * kPatchesPerWarp;
+  k_patch_color<<<dim3((patches + per_block - 1) / per_block, g.nb), kThreads, 0, st>>>(
+      g, ke, pinv, b, in, out, sx, sy, pinv_per_sample ? 1 : 0, active);
   return cudaGetLastError();
 }
 
