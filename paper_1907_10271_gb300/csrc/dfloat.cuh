@@ -46,6 +46,16 @@ __device__ __forceinline__ DF operator+(DF a, DF b) {
   return fast_two_sum(s.hi, s.lo);
 }
 
+// The shorter float-float sum: the heads by TwoSum, the tails added once. Its error is
+// about 2^-47 (|a| + |b|) rather than 2^-47 |a + b|: as good as operator+ where the
+// operands are no larger than the scale the result is needed at, not where two large
+// values cancel to a small one.
+__device__ __forceinline__ DF df_add_short(DF a, DF b) {
+  const DF s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_sub_short(DF a, DF b) { return df_add_short(a, DF{-b.hi, -b.lo}); }
+
 __device__ __forceinline__ DF operator-(DF a) { return DF{-a.hi, -a.lo}; }
 __device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
 

@@ -83,31 +83,38 @@ __device__ __forceinline__ V2<T> shfl_up2(V2<T> a) {
 }
 
 // K_e applied in float-float to float-float corner values, float stiffness: the same
-// steps as element_apply, with every intermediate kept to about 48 bits.
+// steps as element_apply, with every intermediate kept to about 48 bits. The corner
+// differences are the one place where large values (the displacements, up to the end
+// shortening) cancel to small ones (a strain times h), so they take the full
+// float-float sum; every later sum has operands at the scale of the differences or of
+// the element forces, where the shorter sum's error (relative to its operands) is as
+// small as the differences' own rounding, and takes df_add_short.
 __device__ __forceinline__ void element_apply_df(const Coef<float>& C, float rx, float ry, float w, V2<DF> n1,
                                                  V2<DF> n2, V2<DF> n3, V2<DF> n4, V2<DF>& o1, V2<DF>& o2,
                                                  V2<DF>& o3, V2<DF>& o4) {
   const DF du21 = n2.u - n1.u, du34 = n3.u - n4.u, du41 = n4.u - n1.u, du32 = n3.u - n2.u;
   const DF dv21 = n2.v - n1.v, dv34 = n3.v - n4.v, dv41 = n4.v - n1.v, dv32 = n3.v - n2.v;
-  const DF au = du21 + du34, bu = du41 + du32, gu = du34 - du21;
-  const DF av = dv21 + dv34, bv = dv41 + dv32, gv = dv34 - dv21;
-  const DF ex = au * rx, ey = bv * ry, exy = bu * ry + av * rx;
-  const DF sx = ex * C.c11 + ey * C.c12 + exy * C.c16;
-  const DF sy = ex * C.c12 + ey * C.c22 + exy * C.c26;
-  const DF sxy = ex * C.c16 + ey * C.c26 + exy * C.c66;
+  auto ad = [](DF a, DF b) { return df_add_short(a, b); };
+  auto sb = [](DF a, DF b) { return df_sub_short(a, b); };
+  const DF au = ad(du21, du34), bu = ad(du41, du32), gu = sb(du34, du21);
+  const DF av = ad(dv21, dv34), bv = ad(dv41, dv32), gv = sb(dv34, dv21);
+  const DF ex = au * rx, ey = bv * ry, exy = ad(bu * ry, av * rx);
+  const DF sx = ad(ad(ex * C.c11, ey * C.c12), exy * C.c16);
+  const DF sy = ad(ad(ex * C.c12, ey * C.c22), exy * C.c26);
+  const DF sxy = ad(ad(ex * C.c16, ey * C.c26), exy * C.c66);
   const DF gxi_y = gv * ry, gxi_g = gu * ry, get_x = gu * rx, get_g = gv * rx;
-  const DF sxi_y = gxi_y * C.c22 + gxi_g * C.c26;
-  const DF sxi_g = gxi_y * C.c26 + gxi_g * C.c66;
-  const DF set_x = get_x * C.c11 + get_g * C.c16;
-  const DF set_g = get_x * C.c16 + get_g * C.c66;
+  const DF sxi_y = ad(gxi_y * C.c22, gxi_g * C.c26);
+  const DF sxi_g = ad(gxi_y * C.c26, gxi_g * C.c66);
+  const DF set_x = ad(get_x * C.c11, get_g * C.c16);
+  const DF set_g = ad(get_x * C.c16, get_g * C.c66);
   const float third = (float)(1.0 / 3.0);
   const DF A = sx * (w * rx), B = sy * (w * ry), Cx = sxy * (w * ry), Cy = sxy * (w * rx);
-  const DF Hu = (sxi_g * ry + set_x * rx) * (w * third);
-  const DF Hv = (sxi_y * ry + set_g * rx) * (w * third);
-  o1.u = Hu - A - Cx;  o1.v = Hv - B - Cy;
-  o2.u = A - Cx - Hu;  o2.v = Cy - B - Hv;
-  o3.u = A + Cx + Hu;  o3.v = B + Cy + Hv;
-  o4.u = Cx - A - Hu;  o4.v = B - Cy - Hv;
+  const DF Hu = ad(sxi_g * ry, set_x * rx) * (w * third);
+  const DF Hv = ad(sxi_y * ry, set_g * rx) * (w * third);
+  o1.u = sb(sb(Hu, A), Cx);  o1.v = sb(sb(Hv, B), Cy);
+  o2.u = sb(sb(A, Cx), Hu);  o2.v = sb(sb(Cy, B), Hv);
+  o3.u = ad(ad(A, Cx), Hu);  o3.v = ad(ad(B, Cy), Hv);
+  o4.u = sb(sb(Cx, A), Hu);  o4.v = sb(sb(B, Cy), Hv);
 }
 
 // The refinement iterate d. The double path stores it as double; the mixed path as
