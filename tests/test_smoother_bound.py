@@ -61,3 +61,30 @@ def test_rough_fields_stay_under_the_colouring_bound(basis):
     for scale in (10.0, 45.0):   # standard deviations of 20 and 90 degrees
         ev = pair_block_spectrum(scale * kl.theta_field(basis, rng.standard_normal(basis.shape[1])))
         assert ev.max() <= 4.0
+
+
+def test_cosserat_block_jacobi_allows_damping_065():
+    """The Cosserat engine's nodal 3 x 3 block-Jacobi smoother (damping 0.65): on the
+    paper's first test problem (Sec. 3.2 fields, and fields ten times rougher, and
+    uniform angles) lambda_max(B^-1 A) of the oracle's assembly stays under 2 / 0.65."""
+    from oracle import cosserat as O
+    from workloads import COSSERAT_TEST1 as cfg
+    n = 8
+    dd, _ = O.dirichlet(n, cfg["shortening"])
+    m = 3 * (n + 1) ** 2
+    free = np.setdiff1d(np.arange(m), dd)
+
+    def lam_max(phi):
+        K = O.assemble(cfg, n, phi).toarray()
+        Bd = np.zeros_like(K)
+        for p in range((n + 1) ** 2):
+            idx = [3 * p, 3 * p + 1, 3 * p + 2]
+            Bd[np.ix_(idx, idx)] = K[np.ix_(idx, idx)]
+        return sla.eigh(K[np.ix_(free, free)], Bd[np.ix_(free, free)], eigvals_only=True).max()
+
+    Bk, _ = O.kl_basis(cfg, n, O.n_kl(cfg, 0))
+    rng = np.random.default_rng(5)
+    for scale in (1.0, 1.0, 10.0):
+        assert lam_max(scale * (Bk @ rng.standard_normal(Bk.shape[1]))) < 2.0 / 0.65
+    for deg in (0.0, 45.0, 90.0):
+        assert lam_max(np.full(n * n, np.radians(deg))) < 2.0 / 0.65
