@@ -48,6 +48,41 @@ template <typename T>
 __device__ __forceinline__ T zero_of() {
   return T{};
 }
+
+// A float-float value whose sums take the shorter form (mlmc::df_add_short): the
+// refinement operator's element pass after its edge differences. There the operands are
+// at the scale of the differences or of the element forces, so the shorter sum's error
+// (relative to its operands) is no larger than the differences' own rounding; the
+// differences themselves, where displacements cancel to a strain times h, keep the full
+// float-float sum.
+struct DFs {
+  float hi, lo;
+};
+__device__ __forceinline__ DFs operator+(DFs a, DFs b) {
+  const DF r = mlmc::df_add_short(DF{a.hi, a.lo}, DF{b.hi, b.lo});
+  return DFs{r.hi, r.lo};
+}
+__device__ __forceinline__ DFs operator-(DFs a, DFs b) {
+  const DF r = mlmc::df_sub_short(DF{a.hi, a.lo}, DF{b.hi, b.lo});
+  return DFs{r.hi, r.lo};
+}
+__device__ __forceinline__ DFs operator*(float s, DFs a) {
+  const DF r = DF{a.hi, a.lo} * s;
+  return DFs{r.hi, r.lo};
+}
+__device__ __forceinline__ DFs operator*(DFs a, float s) { return s * a; }
+__device__ __forceinline__ DFs to_arith(DF a, DFs) { return DFs{a.hi, a.lo}; }
+__device__ __forceinline__ float to_arith(float a, float) { return a; }
+__device__ __forceinline__ double to_arith(double a, double) { return a; }
+// the element pass's arithmetic type for a value type
+template <typename T>
+struct Arith {
+  using type = T;
+};
+template <>
+struct Arith<DF> {
+  using type = DFs;
+};
 template <typename T>
 __device__ __forceinline__ V3<T> zero3() {
   return V3<T>{zero_of<T>(), zero_of<T>(), zero_of<T>()};
@@ -114,61 +149,73 @@ __device__ __forceinline__ void interp2(const V3<T> in[2][2], V3<T> out[2][2]) {
 }
 
 // f = K_e u for the cube element of side h; u, f indexed [ax][ay][az]. T is the value
-// type (float, float-float or double), S the scalar type of the stiffness and weights.
-template <typename T, typename S>
-__device__ __forceinline__ void element_apply(const Cm<S>& C, S h, const V3<T> u[2][2][2], V3<T> f[2][2][2]) {
-  V3<T> D[2][2], Gx[2][2], Gy[2][2], Gz[2][2];
+// type (float, float-float or double), S the scalar type of the stiffness and weights,
+// TA the type of everything after the edge differences (Arith<T>).
+template <typename T, typename TA>
+__device__ __forceinline__ V3<TA> edge(V3<T> hi, V3<T> lo, float ih) {
+  const V3<T> d = ih * (hi - lo);
+  return V3<TA>{to_arith(d.x, TA{}), to_arith(d.y, TA{}), to_arith(d.z, TA{})};
+}
+template <typename T, typename TA>
+__device__ __forceinline__ V3<TA> edge(V3<T> hi, V3<T> lo, double ih) {
+  const V3<T> d = ih * (hi - lo);
+  return V3<TA>{to_arith(d.x, TA{}), to_arith(d.y, TA{}), to_arith(d.z, TA{})};
+}
+template <typename T, typename S, typename TA = T>
+__device__ __forceinline__ void element_apply(const Cm<S>& C, S h, const V3<T> u[2][2][2], V3<TA> f[2][2][2]) {
+  using T_ = TA;
+  V3<T_> D[2][2], Gx[2][2], Gy[2][2], Gz[2][2];
   const S ih = (S)1 / h;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) D[a][b] = ih * (u[1][a][b] - u[0][a][b]);   // x edges, [ay][az]
-  interp2<T, S>(D, Gx);                                                      // Gx[gy][gz]
+    for (int b = 0; b < 2; ++b) D[a][b] = edge<T, T_>(u[1][a][b], u[0][a][b], ih);   // x edges, [ay][az]
+  interp2<T_, S>(D, Gx);                                                              // Gx[gy][gz]
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) D[a][b] = ih * (u[a][1][b] - u[a][0][b]);   // y edges, [ax][az]
-  interp2<T, S>(D, Gy);                                                      // Gy[gx][gz]
+    for (int b = 0; b < 2; ++b) D[a][b] = edge<T, T_>(u[a][1][b], u[a][0][b], ih);   // y edges, [ax][az]
+  interp2<T_, S>(D, Gy);                                                              // Gy[gx][gz]
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) D[a][b] = ih * (u[a][b][1] - u[a][b][0]);   // z edges, [ax][ay]
-  interp2<T, S>(D, Gz);                                                      // Gz[gx][gy]
+    for (int b = 0; b < 2; ++b) D[a][b] = edge<T, T_>(u[a][b][1], u[a][b][0], ih);   // z edges, [ax][ay]
+  interp2<T_, S>(D, Gz);                                                              // Gz[gx][gy]
   // stresses at the 8 points, summed into the fluxes of each derivative direction
-  V3<T> Sx[2][2], Sy[2][2], Sz[2][2];
+  V3<T_> Sx[2][2], Sy[2][2], Sz[2][2];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) Sx[a][b] = Sy[a][b] = Sz[a][b] = zero3<T>();
+    for (int b = 0; b < 2; ++b) Sx[a][b] = Sy[a][b] = Sz[a][b] = zero3<T_>();
 #pragma unroll
   for (int gx = 0; gx < 2; ++gx)
 #pragma unroll
     for (int gy = 0; gy < 2; ++gy)
 #pragma unroll
       for (int gz = 0; gz < 2; ++gz) {
-        const V3<T> dx = Gx[gy][gz], dy = Gy[gx][gz], dz = Gz[gx][gy];   // d(u,v,w)/dx, /dy, /dz
-        const T e1 = dx.x, e2 = dy.y, e3 = dz.z;
-        const T e4 = dz.y + dy.z, e5 = dz.x + dx.z, e6 = dy.x + dx.y;
-        const T s1 = C.c11 * e1 + C.c12 * e2 + C.c13 * e3 + C.c15 * e5;
-        const T s2 = C.c12 * e1 + C.c22 * e2 + C.c23 * e3 + C.c25 * e5;
-        const T s3 = C.c13 * e1 + C.c23 * e2 + C.c33 * e3 + C.c35 * e5;
-        const T s4 = C.c44 * e4 + C.c46 * e6;
-        const T s5 = C.c15 * e1 + C.c25 * e2 + C.c35 * e3 + C.c55 * e5;
-        const T s6 = C.c46 * e4 + C.c66 * e6;
-        Sx[gy][gz] = Sx[gy][gz] + V3<T>{s1, s6, s5};
-        Sy[gx][gz] = Sy[gx][gz] + V3<T>{s6, s2, s4};
-        Sz[gx][gy] = Sz[gx][gy] + V3<T>{s5, s4, s3};
+        const V3<T_> dx = Gx[gy][gz], dy = Gy[gx][gz], dz = Gz[gx][gy];   // d(u,v,w)/dx, /dy, /dz
+        const T_ e1 = dx.x, e2 = dy.y, e3 = dz.z;
+        const T_ e4 = dz.y + dy.z, e5 = dz.x + dx.z, e6 = dy.x + dx.y;
+        const T_ s1 = C.c11 * e1 + C.c12 * e2 + C.c13 * e3 + C.c15 * e5;
+        const T_ s2 = C.c12 * e1 + C.c22 * e2 + C.c23 * e3 + C.c25 * e5;
+        const T_ s3 = C.c13 * e1 + C.c23 * e2 + C.c33 * e3 + C.c35 * e5;
+        const T_ s4 = C.c44 * e4 + C.c46 * e6;
+        const T_ s5 = C.c15 * e1 + C.c25 * e2 + C.c35 * e3 + C.c55 * e5;
+        const T_ s6 = C.c46 * e4 + C.c66 * e6;
+        Sx[gy][gz] = Sx[gy][gz] + V3<T_>{s1, s6, s5};
+        Sy[gx][gz] = Sy[gx][gz] + V3<T_>{s6, s2, s4};
+        Sz[gx][gy] = Sz[gx][gy] + V3<T_>{s5, s4, s3};
       }
   // transposed passes; Gauss weights 1, det J = (h / 2)^3, dN/dx = sign / h: (h / 2)^3 / h
   const S wj = h * h / (S)8;
-  V3<T> A[2][2];
+  V3<T_> A[2][2];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) f[a][b][c] = zero3<T>();
-  interp2<T, S>(Sx, A);
+      for (int c = 0; c < 2; ++c) f[a][b][c] = zero3<T_>();
+  interp2<T_, S>(Sx, A);
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -176,7 +223,7 @@ __device__ __forceinline__ void element_apply(const Cm<S>& C, S h, const V3<T> u
       f[1][a][b] = f[1][a][b] + wj * A[a][b];
       f[0][a][b] = f[0][a][b] - wj * A[a][b];
     }
-  interp2<T, S>(Sy, A);
+  interp2<T_, S>(Sy, A);
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -184,7 +231,7 @@ __device__ __forceinline__ void element_apply(const Cm<S>& C, S h, const V3<T> u
       f[a][1][b] = f[a][1][b] + wj * A[a][b];
       f[a][0][b] = f[a][0][b] - wj * A[a][b];
     }
-  interp2<T, S>(Sz, A);
+  interp2<T_, S>(Sz, A);
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -327,8 +374,12 @@ __device__ __forceinline__ void add_node(double* y, int64_t n, V3<DF> f) {
   atomicAdd(y + 4 * n + 2, (double)f.z.hi + (double)f.z.lo);
 }
 
+__device__ __forceinline__ void add_node(double* y, int64_t n, V3<DFs> f) {
+  add_node(y, n, V3<DF>{DF{f.x.hi, f.x.lo}, DF{f.y.hi, f.y.lo}, DF{f.z.hi, f.z.lo}});
+}
+
 __device__ __forceinline__ float dot_part(V3<float> a, V3<float> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float dot_part(V3<DF> a, V3<DF> b) { return 0.f; }
+__device__ __forceinline__ float dot_part(V3<DF> a, V3<DFs> b) { return 0.f; }
 
 // One thread per element; y (zeroed by the caller) += K x over all DOFs. T: value type
 // (float, or float-float for the refinement residual: the same FP32 stiffness, every
@@ -337,7 +388,7 @@ __device__ __forceinline__ float dot_part(V3<DF> a, V3<DF> b) { return 0.f; }
 // energy[s] += x . K x as the sum of the element energies x_e . K_e x_e (the PCG's
 // p . q when x vanishes on the prescribed DOFs).
 template <typename T, bool ENERGY, typename X, typename Y>
-__global__ void __launch_bounds__(128) k_apply(Grid3 g, const float4* __restrict__ trig4, const X* __restrict__ x,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 0 : 3) k_apply(Grid3 g, const float4* __restrict__ trig4, const X* __restrict__ x,
                                                Y* __restrict__ y, const int* __restrict__ active, int boundary,
                                                double* __restrict__ energy) {
   const int s = blockIdx.y;
@@ -364,14 +415,15 @@ __global__ void __launch_bounds__(128) k_apply(Grid3 g, const float4* __restrict
   if (valid) {
     const Cm<float> C = coef<float>(trig4[(int64_t)s * g.cols() + (int64_t)k * g.nx + i]);
     const int64_t base = (int64_t)s * g.nodes();
-    V3<T> u[2][2][2], f[2][2][2];
+    V3<T> u[2][2][2];
+    V3<typename Arith<T>::type> f[2][2][2];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
       for (int b = 0; b < 2; ++b)
 #pragma unroll
         for (int c = 0; c < 2; ++c) u[a][b][c] = load_v(x, base + node_of(g, i + a, j + b, k + c));
-    element_apply<T, float>(C, g.h, u, f);
+    element_apply<T, float, typename Arith<T>::type>(C, g.h, u, f);
     if (ENERGY) {
 #pragma unroll
       for (int a = 0; a < 2; ++a)
