@@ -5,7 +5,8 @@ removed). These pins check the values the library's damping rests on, from the o
 own assembly (Eq. matrixinplane): every field stays under the colouring bound 4 (so
 omega = 1/2 is always safe), fields of the benchmark workload (KL angles, 2 degrees
 standard deviation) under 2 / 0.65, and fields turned far from the fibre axis above
-2 / 0.6, which is why a larger damping needs the library's fall-back to 1/2."""
+2 / 0.6, which is why a larger damping needs the library's fall-back to 1/2. The last
+test pins the same bound for the Cosserat engine's nodal block-Jacobi smoother."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
